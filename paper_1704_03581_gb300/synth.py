@@ -1,0 +1,191 @@
+"""Seeded synthetic corpora drawn from the LDA generative process.
+
+The paper's corpora (Enron, NYT, PubMed; Table "corpora" in Section 4) are not
+available here, so every workload is synthetic and drawn from the LDA model
+itself (Figure "lda-dag"): theta_d ~ Dir(alpha_gen), phi_k ~ Dir(b * F),
+z ~ Cat(theta_d), w ~ Cat(phi_z).  F is either uniform (the tiny corpus) or a
+Zipf(s) law over a seeded permutation of the word ids, with concentration
+b = 0.05 V, so frequent words appear in every topic and rare words in few --
+the sparsity structure the doubly sparse sampler exploits.
+
+This module holds no part of the sampler's arithmetic: it only produces the
+inputs (word ids in document order and document offsets) that both the CUDA
+path and the CPU oracle consume.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Corpus:
+    """A corpus in CSR form: ``w[doc_off[d]:doc_off[d+1]]`` are document d's
+    word ids, in position order."""
+
+    w: np.ndarray        # int32 [N]
+    doc_off: np.ndarray  # int64 [D+1]
+    V: int
+    name: str = ""
+
+    @property
+    def D(self) -> int:
+        return int(self.doc_off.shape[0] - 1)
+
+    @property
+    def N(self) -> int:
+        return int(self.w.shape[0])
+
+    def slice_docs(self, d0: int, d1: int) -> "Corpus":
+        a, b = int(self.doc_off[d0]), int(self.doc_off[d1])
+        return Corpus(self.w[a:b].copy(), (self.doc_off[d0:d1 + 1] - a).astype(np.int64), self.V,
+                      f"{self.name}[{d0}:{d1}]")
+
+
+def lognormal_lengths(rng: np.random.Generator, D: int, mean: float, log_sd: float,
+                      lo: int = 1, hi: int | None = None) -> np.ndarray:
+    """Document lengths with arithmetic mean ``mean`` and log-sd ``log_sd``:
+    mu = ln(mean) - log_sd^2 / 2, rounded, floored at ``lo``, capped at ``hi``."""
+    mu = math.log(mean) - 0.5 * log_sd * log_sd
+    x = np.rint(rng.lognormal(mu, log_sd, size=D)).astype(np.int64)
+    x = np.maximum(x, lo)
+    if hi is not None:
+        x = np.minimum(x, hi)
+    return x
+
+
+def zipf_base(rng: np.random.Generator, V: int, s: float) -> np.ndarray:
+    """Zipf(s) probabilities over a seeded permutation of 0..V-1."""
+    ranks = rng.permutation(V)
+    p = (1.0 + ranks.astype(np.float64)) ** (-s)
+    return p / p.sum()
+
+
+def _dirichlet_rows(rng: np.random.Generator, shape_row: np.ndarray, rows: int) -> np.ndarray:
+    g = rng.standard_gamma(np.broadcast_to(shape_row, (rows, shape_row.shape[0])))
+    tot = g.sum(axis=1, keepdims=True)
+    tot[tot <= 0] = 1.0
+    g /= tot
+    return g
+
+
+def lda_corpus(seed: int, K: int, V: int, lengths: np.ndarray, alpha_gen: float,
+               phi_shape: np.ndarray, name: str = "", doc_chunk: int = 8192,
+               phi_seed: int | None = None) -> Corpus:
+    """Draw a corpus from the LDA generative process.
+
+    ``phi_shape`` is the Dirichlet parameter vector (length V) shared by every
+    topic's word distribution; ``alpha_gen`` the symmetric document-topic
+    parameter; ``lengths`` the document lengths.  The topics are drawn from
+    ``phi_seed`` (default ``seed + 1``), the rest from ``seed``, so two corpora
+    can share topics.
+    """
+    rng = np.random.default_rng(seed)
+    phi_rng = np.random.default_rng(seed + 1 if phi_seed is None else phi_seed)
+    lengths = np.asarray(lengths, dtype=np.int64)
+    D = lengths.shape[0]
+    doc_off = np.zeros(D + 1, dtype=np.int64)
+    np.cumsum(lengths, out=doc_off[1:])
+    N = int(doc_off[-1])
+    phi = _dirichlet_rows(phi_rng, np.asarray(phi_shape, dtype=np.float64), K)
+    z = np.empty(N, dtype=np.int32)
+    alpha_row = np.full(K, alpha_gen, dtype=np.float64)
+    for d0 in range(0, D, doc_chunk):
+        d1 = min(D, d0 + doc_chunk)
+        nd = d1 - d0
+        theta = _dirichlet_rows(rng, alpha_row, nd)
+        cum = np.cumsum(theta, axis=1)
+        cum[:, -1] = 1.0
+        flat = (cum + np.arange(nd, dtype=np.float64)[:, None]).ravel()
+        a, b = int(doc_off[d0]), int(doc_off[d1])
+        tok_doc = np.repeat(np.arange(nd, dtype=np.int64), lengths[d0:d1])
+        u = rng.random(b - a) + tok_doc
+        k = np.searchsorted(flat, u, side="right") - tok_doc * K
+        z[a:b] = np.clip(k, 0, K - 1)
+    w = np.empty(N, dtype=np.int32)
+    order = np.argsort(z, kind="stable")
+    counts = np.bincount(z, minlength=K)
+    start = 0
+    for k in range(K):
+        c = int(counts[k])
+        if c:
+            w[order[start:start + c]] = rng.choice(V, size=c, p=phi[k])
+        start += c
+    return Corpus(w, doc_off, V, name)
+
+
+# --------------------------------------------------------------------------
+# The workloads.  Sizes follow the five configurations the sampler is
+# measured on; seeds are fixed so every run sees the same corpus.
+# --------------------------------------------------------------------------
+
+ALPHA = 0.1
+BETA = 0.01
+
+
+def tiny(seed: int = 1) -> Corpus:
+    """K=20, V=1,000, D=1,000, lengths Poisson(100), phi_k ~ Dir(0.01),
+    theta_d ~ Dir(0.1): the full generative process (~100k tokens)."""
+    rng = np.random.default_rng(seed)
+    lengths = rng.poisson(100, size=1000)
+    return lda_corpus(seed + 1000, 20, 1000, lengths, 0.1, np.full(1000, 0.01), "tiny K=20 V=1000 D=1000")
+
+
+def zipf_corpus(seed: int, K: int, V: int, D: int, mean_len: float, log_sd: float, s: float,
+                name: str, hi: int | None = None) -> Corpus:
+    rng = np.random.default_rng(seed)
+    lengths = lognormal_lengths(rng, D, mean_len, log_sd, 1, hi)
+    F = zipf_base(np.random.default_rng(seed + 7), V, s)
+    return lda_corpus(seed + 1000, K, V, lengths, 0.1, 0.05 * V * F, name, phi_seed=seed + 11)
+
+
+def small(seed: int = 2) -> Corpus:
+    """D=1,500, V=12,375, lengths lognormal(mean 1,290, log-sd 0.5), Zipf(1.0),
+    generated with K=100 topics (~1.9M tokens)."""
+    return zipf_corpus(seed, 100, 12375, 1500, 1290.0, 0.5, 1.0, "small D=1500 V=12375 K=100")
+
+
+def large(seed: int = 3, D: int = 300_000) -> Corpus:
+    """D=300,000, V=100,000, lengths lognormal(mean 330, log-sd 0.8),
+    Zipf(1.05), generated with K=1,000 topics (~99M tokens)."""
+    return zipf_corpus(seed, 1000, 100_000, D, 330.0, 0.8, 1.05, f"large D={D} V=100000 K=1000")
+
+
+def batched_specs(n_chains: int = 32, seed: int = 4) -> list[dict]:
+    """Shapes of the batched-chains workload: D log-uniform in [1e3, 1e5],
+    mean length log-uniform in [50, 2000], V log-uniform in [5e3, 5e4],
+    K uniform over {50, 100, 200, 500}; chain seeds 100.."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(n_chains):
+        out.append(dict(
+            D=int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e5))))),
+            mean_len=float(math.exp(rng.uniform(math.log(50), math.log(2000)))),
+            V=int(round(math.exp(rng.uniform(math.log(5e3), math.log(5e4))))),
+            K=int(rng.choice([50, 100, 200, 500])),
+            seed=100 + c,
+        ))
+    return out
+
+
+def batched_corpus(spec: dict, scale: float = 1.0) -> Corpus:
+    D = max(1, int(round(spec["D"] * scale)))
+    return zipf_corpus(spec["seed"], spec["K"], spec["V"], D, spec["mean_len"], 0.8, 1.0,
+                       f"chain{spec['seed']} D={D} V={spec['V']} K={spec['K']}")
+
+
+def serving_requests(n: int, V: int, seed: int = 5, mean_len: float = 300.0, log_sd: float = 1.2,
+                     lo: int = 10, hi: int = 20000, rate: float = 5000.0, K_gen: int = 1000) -> tuple[Corpus, np.ndarray]:
+    """Fold-in requests: lengths lognormal(mean 300, log-sd 1.2) clipped to
+    [10, 20000], words from the large corpus's generator shape, Poisson
+    arrivals at ``rate`` docs/s.  Returns the requests as a corpus (one
+    document per request) and the arrival times in seconds."""
+    rng = np.random.default_rng(seed)
+    lengths = lognormal_lengths(rng, n, mean_len, log_sd, lo, hi)
+    F = zipf_base(np.random.default_rng(3 + 7), V, 1.05)       # the large corpus's word law
+    corpus = lda_corpus(seed + 1000, K_gen, V, lengths, 0.1, 0.05 * V * F, f"requests n={n}",
+                        phi_seed=3 + 11)                          # and its topics
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    return corpus, arrivals

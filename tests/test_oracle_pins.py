@@ -1,0 +1,387 @@
+"""Pins of the CPU oracle against things other than itself: published test
+vectors, textbook distributions, closed forms, brute force and exact
+enumeration of the stationary law.  No GPU is used here."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special, stats
+
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox
+
+def test_philox_known_answers():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(x, 16) for x in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        out = O.philox(r[0:4], r[4:6])
+        assert [int(x) for x in out] == r[6:10]
+
+
+# ------------------------------------------------------ alias tables (Vose)
+
+def alias_masses(thr, alias, n_out=None):
+    """Probability of each outcome implied by an alias table (exact up to the
+    2^-32 threshold grid)."""
+    n = thr.shape[0]
+    n_out = n if n_out is None else n_out
+    keep = thr.astype(np.float64) / 2.0 ** 32
+    mass = np.zeros(n_out)
+    np.add.at(mass, np.arange(n), keep / n)
+    np.add.at(mass, alias, (1.0 - keep) / n)
+    return mass
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_vose_reconstructs_weights(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 300))
+    W = rng.integers(0, 2 ** 40, size=n).astype(np.uint64)
+    W[rng.random(n) < 0.2] = 0
+    if W.sum() == 0:
+        W[0] = 1
+    thr, alias, T = O.vose(W)
+    assert T == int(W.astype(object).sum())
+    mass = alias_masses(thr, alias)
+    assert np.abs(mass - W.astype(np.float64) / T).max() <= 2.0 / 2 ** 32
+    # zero-weight outcomes can never be drawn
+    assert np.all(thr[W == 0] == 0)
+
+
+def test_vose_uniform_weights_are_all_full():
+    thr, alias, _ = O.vose(np.full(17, 5, dtype=np.uint64))
+    assert np.all(thr == 0xFFFFFFFF) and np.all(alias == np.arange(17))
+
+
+# ------------------------------------------ Poisson tables ("Efficient sampling of Phi")
+
+@pytest.mark.parametrize("lam", [0.01 + 1, 0.01 + 5, 0.01 + 37, 0.01 + 100, 3.7])
+def test_poisson_weights_are_the_pmf(lam):
+    lo, W = O.pois_weights(lam)
+    j = np.arange(lo, lo + W.shape[0])
+    pmf = stats.poisson.pmf(j, lam)
+    assert np.abs(W / W.sum() - pmf / pmf.sum()).max() < 1e-11
+    # the support keeps everything above 2^-40 of the mode and loses < 2^-35 of the mass
+    assert pmf.sum() > 1 - 2.0 ** -35
+    mode = stats.poisson.pmf(math.floor(lam), lam)
+    assert stats.poisson.pmf(lo - 1, lam) < mode * 2.0 ** -40 or lo == 0
+    assert stats.poisson.pmf(j[-1] + 1, lam) < mode * 2.0 ** -40
+
+
+def test_zero_truncated_weights():
+    lo, W = O.pois_weights(0.01, jmin=1)
+    assert lo == 1
+    j = np.arange(1, 1 + W.shape[0])
+    pmf = stats.poisson.pmf(j, 0.01)
+    assert np.abs(W / W.sum() - pmf / pmf.sum()).max() < 1e-11
+
+
+@pytest.mark.parametrize("l", [1, 2, 9, 50, 100])
+def test_context_alias_tables_give_poisson(l):
+    ctx = O.Ctx(0.01)
+    lo, thr, alias = ctx.table(l)
+    mass = alias_masses(thr, alias)
+    j = np.arange(lo, lo + thr.shape[0])
+    lam = float(np.float32(0.01)) + l
+    pmf = stats.poisson.pmf(j, lam)
+    assert np.abs(mass - pmf).max() < 3.0 * thr.shape[0] / 2 ** 32 + 1e-12
+
+
+# ------------------------------------------------ geometric gaps and Gaussian
+
+def test_geometric_gap_table_closed_form():
+    beta = float(np.float32(0.01))
+    thr = O.geo_table(beta)
+    g = np.arange(O.LG)
+    cdf = 1.0 - np.exp(-beta * (g + 1))
+    assert np.all(np.abs(thr / 2.0 ** 32 - cdf) <= 2.0 ** -32)
+    assert np.all(np.diff(thr.astype(np.int64)) >= 0)
+
+
+def test_gaussian_table_is_the_normal_quantile():
+    ctx = O.Ctx(0.01)
+    Q = ctx.gauss()
+    i = np.arange(1, O.GAUSS_CELLS // 2)
+    assert np.abs(Q[1:O.GAUSS_CELLS // 2] - special.ndtri(i / O.GAUSS_CELLS)).max() < 1e-12
+    assert abs(Q[0] - special.ndtri(2.0 ** -24)) < 1e-12
+    assert np.array_equal(Q[::-1], -Q)                      # the normal law is symmetric
+    assert np.all(np.diff(Q) > 0)
+
+
+def test_gaussian_draw_moments():
+    ctx = O.Ctx(0.01)
+    rng = np.random.default_rng(7)
+    x = rng.integers(0, 2 ** 32, size=(200000, 2), dtype=np.uint64)
+    g = np.array([ctx.gauss_draw(a, b) for a, b in x])
+    assert abs(g.mean()) < 0.01 and abs(g.var() - 1) < 0.01
+    assert stats.kstest(g, "norm").pvalue > 1e-3
+
+
+# --------------------------------------------------------------- the Phi-step
+
+def _phi_samples(n_vk, beta, sweeps, seed=11):
+    ctx = O.Ctx(beta)
+    out = []
+    for s in range(1, sweeps + 1):
+        c, S, _ = O.phi_draw(ctx, n_vk, seed, s)
+        out.append(c)
+    return np.stack(out)
+
+
+def _chi2_counts(sample, pmf_fn, min_exp=5.0):
+    vals, cnt = np.unique(sample, return_counts=True)
+    hi = int(vals.max()) + 1
+    obs = np.bincount(sample, minlength=hi).astype(np.float64)
+    exp = pmf_fn(np.arange(hi)) * sample.shape[0]
+    tail = 1.0 - exp.sum() / sample.shape[0]
+    # pool small cells into their neighbours from the left
+    o, e = [], []
+    acc_o = acc_e = 0.0
+    for a, b in zip(obs, exp):
+        acc_o += a
+        acc_e += b
+        if acc_e >= min_exp:
+            o.append(acc_o); e.append(acc_e); acc_o = acc_e = 0.0
+    if e:
+        o[-1] += acc_o
+        e[-1] += acc_e + tail * sample.shape[0]
+    o, e = np.array(o), np.array(e)
+    chi = ((o - e) ** 2 / e).sum()
+    return stats.chi2.sf(chi, len(o) - 1)
+
+
+def test_phi_entries_follow_poisson_beta_plus_n():
+    """Eq. (7): c_{k,v} ~ Pois(beta + n_{k,v}), independently; rounded Gaussian above L."""
+    beta = 0.01
+    V, K = 120, 40
+    n = np.zeros((V, K), dtype=np.int32)   # n[v, k]
+    n[0:20, :] = 5          # every topic has mass, so no row is ever redrawn
+    n[20:40, :] = 3
+    n[40:60, :] = 150       # above L = 100: rounded Gaussian
+    n[60:70, :] = 1
+    c = _phi_samples(n, beta, 60)
+    b = float(np.float32(beta))
+    assert _chi2_counts(c[:, 20:40].ravel(), lambda j: stats.poisson.pmf(j, b + 3)) > 1e-4
+    assert _chi2_counts(c[:, 0:20].ravel(), lambda j: stats.poisson.pmf(j, b + 5)) > 1e-4
+    assert _chi2_counts(c[:, 60:70].ravel(), lambda j: stats.poisson.pmf(j, b + 1)) > 1e-4
+    mu = b + 150
+    rg = lambda j: stats.norm.cdf((j + 0.5 - mu) / math.sqrt(mu)) - stats.norm.cdf((j - 0.5 - mu) / math.sqrt(mu))
+    assert _chi2_counts(c[:, 40:60].ravel(), rg) > 1e-4
+    # beta-only entries: Pois(beta), so P(c > 0) = 1 - e^-beta and the values are ZTP
+    zero = c[:, 70:].ravel()
+    p_hit = 1 - math.exp(-b)
+    hits = int((zero > 0).sum())
+    assert stats.binomtest(hits, zero.shape[0], p_hit).pvalue > 1e-4
+    assert _chi2_counts(zero, lambda j: stats.poisson.pmf(j, b)) > 1e-4
+
+
+def test_phi_row_sums_and_normalisation():
+    beta = 0.01
+    rng = np.random.default_rng(3)
+    V, K = 300, 25
+    n = rng.poisson(2.0, size=(V, K)).astype(np.int32)
+    ctx = O.Ctx(beta)
+    c, S, _ = O.phi_draw(ctx, n, 5, 1)
+    assert np.array_equal(S, c.sum(axis=0).astype(np.int64))
+    t = O.WordTables(c, S, np.full(K, 0.1, np.float32))
+    phi = t.phi_dense().astype(np.float64)
+    assert np.abs(phi.sum(axis=1) - 1).max() < 1e-6          # rows of Phi are distributions
+    nz = c.T > 0
+    assert np.array_equal(phi > 0, nz)                      # sparsity pattern of Phi = that of c
+    ref = (c.T.astype(np.float64) / S[:, None])
+    assert np.array_equal(phi[nz].astype(np.float32), ref[nz].astype(np.float32))
+
+
+def test_dead_rows_are_conditioned_on_nonzero_sum():
+    """Definition "Poisson Polya Urn": the normalisation needs a nonzero sum;
+    the hierarchical representation (Eq. 6) draws the total from Pois+.  A row
+    with S_k = 0 is redrawn, so its law is the Poisson law given S_k > 0."""
+    beta = 0.3
+    V, K = 3, 1
+    n = np.zeros((V, K), dtype=np.int32)
+    ctx = O.Ctx(beta)
+    b = float(np.float32(beta))
+    samples = []
+    dead_total = 0
+    for s in range(1, 6001):
+        c, S, dead = O.phi_draw(ctx, n, 21, s)
+        assert S[0] > 0
+        dead_total += dead
+        samples.append(tuple(int(x) for x in c[:, 0]))
+    assert dead_total > 1000                                 # P(S=0) = e^{-0.9} ~ 0.41
+    # exact conditional law over the states seen, pooled beyond total 3
+    p0 = math.exp(-3 * b)
+    def pmf(state):
+        return np.prod([stats.poisson.pmf(x, b) for x in state]) / (1 - p0)
+    keys = sorted(set(samples))
+    obs = np.array([samples.count(k) for k in keys], dtype=np.float64)
+    exp = np.array([pmf(k) for k in keys]) * len(samples)
+    big = exp < 5
+    o = np.append(obs[~big], obs[big].sum())
+    e = np.append(exp[~big], len(samples) - exp[~big].sum())
+    chi = ((o - e) ** 2 / e).sum()
+    assert stats.chi2.sf(chi, len(o) - 1) > 1e-4
+
+
+# ----------------------------------------------------- per-word z-step tables
+
+def test_word_tables_reproduce_the_conditional():
+    """The fixed-point weights give p(k) proportional to phi_{k,v}(alpha_k + m_k)
+    ("Efficient sampling of z") to within 2^-20 relative."""
+    rng = np.random.default_rng(5)
+    V, K = 50, 64
+    c = (rng.poisson(0.7, size=(V, K)) * rng.integers(1, 900, size=(V, K))).astype(np.uint32)
+    c[0] = 0
+    S = c.sum(axis=0).astype(np.int64)
+    S[S == 0] = 1
+    alpha = rng.uniform(0.05, 2.0, size=K).astype(np.float32)
+    t = O.WordTables(c, S, alpha)
+    for v in range(V):
+        top, q, athr, atop, phi32 = t.column(v)
+        assert top.shape[0] == int((c[v] > 0).sum())
+        if top.shape[0] == 0:
+            assert t.A[v] == 0
+            continue
+        assert np.all(np.diff(top) > 0)
+        assert 2 ** 23 <= q.max() <= 2 ** 24 and q.min() >= 1
+        m = rng.integers(0, 40, size=K)
+        phi = c[v, top].astype(np.float64) / S[top]
+        p = phi * (alpha[top].astype(np.float64) + m[top])
+        p /= p.sum()
+        a = np.floor(q.astype(np.float64) * alpha[top] * 2 ** 16 + 0.5)
+        w = a + q.astype(np.float64) * m[top] * 2 ** 16
+        assert int(a.sum()) == int(t.A[v])
+        # rounding q to an integer moves an entry by at most half a unit;
+        # the shared normalisation moves every entry by at most ~n 2^-24
+        rel = np.abs(w / w.sum() - p) / p
+        assert np.all(rel <= 0.5 / q + 2.0 ** -17)
+        assert rel[q >= 2 ** 20].max() < 2.0 ** -17
+        # the alias table draws topic top[j] with probability a_j / A
+        mass = alias_masses(athr, np.searchsorted(top, atop))
+        assert np.abs(mass - a / a.sum()).max() <= 2.0 * top.shape[0] / 2 ** 32
+
+
+# ----------------------------------------------------------------- the z-step
+
+def _tables_from_phi(phi_kv, alpha, scale=10 ** 6):
+    """Word tables whose phi equals phi_kv (given as exact ratios c/S)."""
+    K, V = phi_kv.shape
+    c = np.rint(phi_kv * scale).astype(np.uint32).T.copy()
+    S = np.full(K, scale, dtype=np.int64)
+    return O.WordTables(c, S, np.asarray(alpha, np.float32)), c.T.astype(np.float64) / scale
+
+
+def test_z_conditional_chi_square():
+    """p(z_i = k) proportional to phi_{k,v(i)} (alpha_k + m^{-i}_{d,k}) (Algorithm 2)."""
+    K, V = 6, 3
+    phi = np.array([[0.5, 0.2, 0.3],
+                    [0.1, 0.6, 0.3],
+                    [0.25, 0.25, 0.5],
+                    [0.7, 0.1, 0.2],
+                    [0.0, 0.5, 0.5],
+                    [0.3, 0.3, 0.4]])
+    alpha = np.array([0.1, 0.5, 0.2, 0.1, 0.3, 0.05], np.float32)
+    t, phi_x = _tables_from_phi(phi, alpha)
+    # token 0 (word 0, topic 1) first, then other tokens that define m^{-0}
+    w = np.array([0, 1, 2, 0, 0, 1, 2, 2], np.int32)
+    z0 = np.array([1, 3, 3, 0, 3, 5, 2, 0], np.int16)
+    doc_off = np.array([0, 8], np.int64)
+    m = np.bincount(z0[1:], minlength=K).astype(np.float64)  # m^{-0}; topic 1 has only token 0
+    p = phi_x[:, 0] * (alpha.astype(np.float64) + m)
+    p /= p.sum()
+    draws = np.array([O.z_step(doc_off, w, z0, t, 99, s)[0][0] for s in range(1, 40001)])
+    obs = np.bincount(draws, minlength=K)
+    assert obs[4] == 0                                      # phi_{4,0} = 0: never drawn
+    keep = p > 0
+    chi = ((obs[keep] - p[keep] * draws.shape[0]) ** 2 / (p[keep] * draws.shape[0])).sum()
+    assert stats.chi2.sf(chi, keep.sum() - 1) > 1e-4
+    # the removal of token i matters here: without it topic 1 would carry
+    # phi(alpha+1) instead of phi*alpha, far outside the statistical tolerance
+    assert obs[1] < 0.5 * draws.shape[0] * phi_x[1, 0] * (alpha[1] + 1) / (phi_x[:, 0] * (alpha + m + np.eye(K)[1])).sum()
+
+
+def test_z_step_stationary_law_by_enumeration():
+    """With Phi fixed, the z-step's stationary law is
+    p(z | Phi, w) proportional to prod_i phi_{z_i, w_i} prod_{d,k} Gamma(alpha_k + m_{d,k}),
+    the partially collapsed target of Algorithm 2 (theta integrated out).
+    2 topics, 3 words, 4 documents, 6 tokens: 64 states, enumerated exactly."""
+    K = 2
+    phi = np.array([[0.6, 0.3, 0.1],
+                    [0.1, 0.3, 0.6]])
+    alpha = np.array([0.5, 0.5], np.float32)
+    t, phi_x = _tables_from_phi(phi, alpha)
+    w = np.array([0, 2, 1, 0, 2, 1], np.int32)
+    doc_off = np.array([0, 2, 3, 5, 6], np.int64)
+    N = w.shape[0]
+    states = np.array([[(s >> i) & 1 for i in range(N)] for s in range(2 ** N)])
+    logp = np.zeros(2 ** N)
+    for si, zz in enumerate(states):
+        lp = np.log(phi_x[zz, w]).sum()
+        for d in range(4):
+            mm = np.bincount(zz[doc_off[d]:doc_off[d + 1]], minlength=K)
+            lp += special.gammaln(alpha.astype(np.float64) + mm).sum()
+        logp[si] = lp
+    p = np.exp(logp - logp.max())
+    p /= p.sum()
+    z = np.zeros(N, np.int16)
+    counts = np.zeros(2 ** N)
+    weights = 1 << np.arange(N)
+    n_sweeps = 300000
+    for s in range(1, n_sweeps + 1):
+        z, _ = O.z_step(doc_off, w, z, t, 7, s)
+        counts[int((z.astype(np.int64) * weights).sum())] += 1
+    tv = 0.5 * np.abs(counts / n_sweeps - p).sum()
+    assert tv < 0.015, tv
+    # a sampler that forgot alpha's Gamma terms (independent tokens) has a
+    # different law; the test can tell them apart
+    q = np.exp(np.array([np.log(phi_x[zz, w]).sum() for zz in states]))
+    q /= q.sum()
+    assert 0.5 * np.abs(q - p).sum() > 0.1
+
+
+# -------------------------------------------------------- counts and init
+
+def test_counts_brute_force():
+    rng = np.random.default_rng(8)
+    K, V, N = 7, 11, 500
+    w = rng.integers(0, V, N).astype(np.int32)
+    z = rng.integers(0, K, N).astype(np.int16)
+    n = O.count_n(w, z, K, V)
+    ref = np.zeros((V, K), np.int32)
+    for a, b in zip(w, z):
+        ref[a, b] += 1
+    assert np.array_equal(n, ref)
+    doc_off = np.array([0, 0, 100, 101, 400, 500], np.int64)   # includes an empty document
+    m = O.doc_topic(doc_off, z, K)
+    for d in range(5):
+        assert np.array_equal(m[d], np.bincount(z[doc_off[d]:doc_off[d + 1]], minlength=K))
+
+
+def test_init_is_uniform():
+    K = 37
+    z = O.init_z(200000, K, 3)
+    obs = np.bincount(z, minlength=K)
+    assert stats.chisquare(obs).pvalue > 1e-4
+
+
+def test_chain_invariants_tiny_corpus():
+    from paper_1704_03581_gb300 import synth
+    c = synth.tiny()
+    ch = O.Chain(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=0).sweep(3)
+    m = ch.m()
+    assert np.array_equal(m.sum(axis=1), np.diff(c.doc_off))           # sum_k m_{d,k} = N_d
+    n = ch.n()
+    assert n.sum() == c.N                                              # sum n = N
+    assert np.array_equal(n.sum(axis=0), np.bincount(ch.z, minlength=20))
+    assert ch.z.min() >= 0 and ch.z.max() < 20
+    assert np.abs(ch.tables.phi_dense().astype(np.float64).sum(axis=1) - 1).max() < 1e-6
+    assert ch.stats[0] == c.N
