@@ -1,0 +1,169 @@
+/*
+ * pulda.h -- C ABI of the GB300 Polya-urn partially collapsed LDA sampler
+ * (Terenin, Magnusson, Jonsson, Draper, "Polya Urn Latent Dirichlet
+ * Allocation: a doubly sparse massively parallel sampler", arXiv 1704.03581).
+ *
+ * One handle = one Markov chain on one GPU.  A sweep is Algorithm 2 of the
+ * paper (Section 3): draw Phi with the Poisson Polya urn, then resample every
+ * topic indicator z with the doubly sparse a/b split ("Efficient sampling of
+ * z").  Every step runs in CUDA kernels; the host only validates arguments,
+ * builds the fixed Poisson tables once, and copies data in and out.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_host are host memory, *_dev device memory.  Inputs are
+ *     read during the call and may be freed afterwards; the library keeps its
+ *     own device copies.  Outputs are written into caller-allocated buffers of
+ *     the stated size.
+ *   - Every call returns a pulda_status.  On PULDA_ERR_INVALID the handle's
+ *     state is unchanged; pulda_last_error() describes the problem.  A CUDA
+ *     failure returns PULDA_ERR_CUDA and leaves the handle unusable except for
+ *     pulda_free / pulda_last_error.
+ *   - A handle is not thread safe: one host thread at a time.
+ *   - Layouts: corpus in CSR form, word_ids[doc_offsets[d] .. doc_offsets[d+1])
+ *     are document d's word ids in position order.  Topic ids are int16,
+ *     0 <= k < K <= 16384.  Dense count outputs are row-major.
+ *   - Random numbers: counter-based Philox4x32-10 keyed by the 64-bit seed,
+ *     counter = (index_lo, index_hi, sweep, tag << 28 | aux); results depend
+ *     only on (corpus, K, V, alpha, beta, seed, sweep count), never on launch
+ *     shapes or timing.
+ */
+#ifndef PULDA_H
+#define PULDA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PULDA_OK = 0,
+    PULDA_ERR_INVALID = -1,     /* bad argument; state unchanged */
+    PULDA_ERR_OOM = -2,         /* device allocation failed */
+    PULDA_ERR_CUDA = -3,        /* a CUDA call or kernel failed */
+    PULDA_ERR_TIMEOUT = -4,     /* a bounded wait expired */
+    PULDA_ERR_DEGENERATE = -5,  /* a Phi row stayed all-zero after 2^20 redraws */
+    PULDA_ERR_BUSY = -6         /* the server's slots or token budget are full */
+} pulda_status;
+
+typedef struct pulda_handle pulda_handle;
+
+/* Launch options.  Zero-initialise and set what you need; NULL = defaults. */
+typedef struct {
+    void *stream;           /* cudaStream_t to run on; NULL = a stream the handle creates */
+    int32_t zstep_path;     /* 0 = auto (iterate the smaller of the document's and the
+                               word's nonzero topics), 1 = always iterate the word's Phi
+                               column, 2 = iterate the document's topics whenever K <= 1024 */
+    int32_t warps_per_block;/* z-step warps per CTA; 0 = chosen from K */
+    int32_t reserved[6];
+} pulda_options;
+
+/* Counters of the most recent z-step (and Phi-step), and running totals. */
+typedef struct {
+    int64_t tokens;          /* tokens resampled */
+    int64_t a_branch;        /* draws taken from the alias table of the alpha part */
+    int64_t sum_min;         /* sum over tokens of min(K_d^(m), K_v^(Phi)) (complexity theorem) */
+    int64_t zero_mass;       /* tokens whose conditional had zero total mass (kept their topic) */
+    int64_t dead_rows;       /* Phi rows redrawn because their Poisson counts summed to zero */
+    int64_t nnz_phi;         /* nonzero entries of Phi */
+    int64_t sweep;           /* sweep counter after the call */
+    int64_t cum_tokens;      /* the z-step counters summed over every z-step since pulda_init */
+    int64_t cum_a_branch;
+    int64_t cum_sum_min;
+    int64_t cum_zero_mass;
+} pulda_sweep_stats;
+
+/* pulda_init -- create a chain.
+ * Model: LDA (Section 1, Figure "lda-dag", Table "notation") with symmetric or
+ * per-topic alpha[K] and symmetric beta.  Topics start uniform (keyed by
+ * (seed, token, sweep 0)); the paper does not prescribe an initialisation.
+ *   word_ids_host   int32[N], N = doc_offsets_host[D]; every id in [0, V)
+ *   doc_offsets_host int64[D+1], doc_offsets[0] = 0, nondecreasing
+ *   K in [1, 16384], V >= 1, alpha[K] in (0, 256], beta in (0, 64]
+ *   opt             may be NULL
+ * Errors: PULDA_ERR_INVALID (bad sizes/ids/offsets/hyper-parameters; documents
+ * longer than 2^22 tokens), PULDA_ERR_OOM, PULDA_ERR_CUDA. */
+pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids_host, const int64_t *doc_offsets_host,
+                        int64_t D, int32_t K, int32_t V, const float *alpha_host, float beta,
+                        uint64_t seed, const pulda_options *opt);
+
+/* pulda_sweep -- n_sweeps iterations of Algorithm 2: for each, rebuild n from
+ * z (notation table), draw Phi ~ PPU(n_k + beta) row by row (Definition "Poisson
+ * Polya Urn", Eq. 7, "Efficient sampling of Phi"), then resample every z_{i,d}
+ * proportional to phi_{k,v(i)}(alpha_k + m^{-i}_{d,k}) ("Efficient sampling of
+ * z").  Asynchronous on the handle's stream; errors raised by kernels are
+ * reported by the next pulda_sync.  Errors: PULDA_ERR_INVALID (n_sweeps < 0). */
+pulda_status pulda_sweep(pulda_handle *h, int32_t n_sweeps);
+
+/* pulda_phi_step / pulda_z_step -- the two halves of one sweep, for callers
+ * that time or inspect them separately.  pulda_phi_step advances the sweep
+ * counter and draws Phi for it; pulda_z_step resamples z with that Phi.
+ * pulda_z_step before any pulda_phi_step returns PULDA_ERR_INVALID. */
+pulda_status pulda_phi_step(pulda_handle *h);
+pulda_status pulda_z_step(pulda_handle *h);
+
+/* pulda_sync -- wait for the handle's stream and report device-side errors
+ * (PULDA_ERR_DEGENERATE, PULDA_ERR_CUDA). */
+pulda_status pulda_sync(pulda_handle *h);
+
+/* pulda_get_z -- copy z (int16[N], corpus order) to host / device memory. */
+pulda_status pulda_get_z(pulda_handle *h, int16_t *z_host);
+pulda_status pulda_get_z_dev(pulda_handle *h, int16_t *z_dev);
+
+/* pulda_set_z -- replace z (int16[N], each in [0, K)) and set the sweep
+ * counter; with the z and counter of an earlier pulda_get_z / pulda_stats this
+ * resumes that chain exactly (n, m and Phi are functions of z and the keyed
+ * random streams).  Errors: PULDA_ERR_INVALID (topic out of range). */
+pulda_status pulda_set_z(pulda_handle *h, const int16_t *z_host, int64_t sweep);
+
+/* pulda_get_counts -- exact counts from the current z (notation table):
+ *   n_kv_host int32[K*V], n_kv[k*V + v] = #{i : z_i = k, w_i = v}, or NULL
+ *   m_dk_host int32[D*K], m_dk[d*K + k] = #{i in d : z_i = k}, or NULL */
+pulda_status pulda_get_counts(pulda_handle *h, int32_t *n_kv_host, int32_t *m_dk_host);
+
+/* pulda_get_phi -- the Phi drawn by the most recent Phi-step, sparse by word
+ * (column-compressed): entries col_ptr[v] .. col_ptr[v+1]-1 hold the nonzero
+ * phi_{k,v} = fp32(c_{k,v} / S_k) with topic ids in ascending order.
+ * Call with col_ptr/topic/phi NULL to query *nnz_inout; otherwise *nnz_inout
+ * is the capacity of topic/phi on entry and the entry count on return.
+ *   col_ptr_host int64[V+1], topic_host int16[nnz], phi_host float[nnz]
+ * Errors: PULDA_ERR_INVALID (no Phi drawn yet, capacity too small). */
+pulda_status pulda_get_phi(pulda_handle *h, int64_t *col_ptr_host, int16_t *topic_host, float *phi_host,
+                           int64_t *nnz_inout);
+
+/* pulda_get_word_tables -- the per-word z-step tables behind the current Phi
+ * (for inspection and tests): Poisson counts c (uint32), row sums S (int64[K]),
+ * fixed-point weights q (uint32), alpha-part masses A (uint64[V]) and the alias
+ * table (threshold uint32, alias topic int16), laid out like pulda_get_phi.
+ * Any output pointer may be NULL.  *nnz_inout as for pulda_get_phi. */
+pulda_status pulda_get_word_tables(pulda_handle *h, int64_t *col_ptr_host, int16_t *topic_host,
+                                   uint32_t *c_host, int64_t *S_host, uint32_t *q_host, uint64_t *A_host,
+                                   uint32_t *athr_host, int16_t *atopic_host, int64_t *nnz_inout);
+
+/* pulda_infer -- fold-in of new documents against the current Phi (Algorithm
+ * 2's z-step with Phi held fixed): topics start uniform, keyed by (seed,
+ * position in this call's token array, sweep 0), then n_sweeps z-steps with
+ * sweep counters 1..n_sweeps.  The chain's own state is not changed.
+ *   word_ids_host int32[N_new], doc_offsets_host int64[D_new+1]
+ *   z_out_host int16[N_new] or NULL; m_out_host int32[D_new*K] or NULL
+ * Errors: PULDA_ERR_INVALID (bad ids/offsets; no Phi drawn yet). */
+pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids_host, const int64_t *doc_offsets_host,
+                         int64_t D_new, int32_t n_sweeps, uint64_t seed, int16_t *z_out_host,
+                         int32_t *m_out_host);
+
+/* pulda_stats -- counters of the most recent sweep (synchronises). */
+pulda_status pulda_stats(pulda_handle *h, pulda_sweep_stats *out);
+
+/* pulda_last_error -- human-readable description of the handle's last
+ * failure, or ""; with h = NULL, the reason the calling thread's last
+ * pulda_init failed. */
+const char *pulda_last_error(const pulda_handle *h);
+
+/* pulda_free -- release every resource of the handle (NULL is a no-op). */
+void pulda_free(pulda_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

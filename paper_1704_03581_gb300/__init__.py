@@ -1,0 +1,269 @@
+"""pulda: Polya-urn partially collapsed LDA on one GB300 (sm_103a).
+
+A thin Python binding of the C ABI in include/pulda.h.  Each function has the
+C name and only marshals arguments: every step of the sampler runs in the
+CUDA kernels of ``_build/libpulda.so``.  There is no CPU fallback -- if the
+library has not been built (``paper_1704_03581_gb300.build.build()``), loading
+fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libpulda.so")
+
+PULDA_OK = 0
+STATUS = {0: "PULDA_OK", -1: "PULDA_ERR_INVALID", -2: "PULDA_ERR_OOM", -3: "PULDA_ERR_CUDA",
+          -4: "PULDA_ERR_TIMEOUT", -5: "PULDA_ERR_DEGENERATE", -6: "PULDA_ERR_BUSY"}
+
+EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "pulda_sync", "pulda_get_z",
+            "pulda_get_z_dev", "pulda_set_z", "pulda_get_counts", "pulda_get_phi", "pulda_get_word_tables",
+            "pulda_infer", "pulda_stats", "pulda_last_error", "pulda_free"]
+
+
+class PuldaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("zstep_path", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class SweepStats(ctypes.Structure):
+    _fields_ = [("tokens", ctypes.c_int64), ("a_branch", ctypes.c_int64), ("sum_min", ctypes.c_int64),
+                ("zero_mass", ctypes.c_int64), ("dead_rows", ctypes.c_int64), ("nnz_phi", ctypes.c_int64),
+                ("sweep", ctypes.c_int64), ("cum_tokens", ctypes.c_int64), ("cum_a_branch", ctypes.c_int64),
+                ("cum_sum_min", ctypes.c_int64), ("cum_zero_mass", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f[0]: int(getattr(self, f[0])) for f in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1704_03581_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64, u64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
+        sig = {
+            "pulda_init": [P, P, P, i64, i32, i32, P, f32, u64, P],
+            "pulda_sweep": [P, i32],
+            "pulda_phi_step": [P],
+            "pulda_z_step": [P],
+            "pulda_sync": [P],
+            "pulda_get_z": [P, P],
+            "pulda_get_z_dev": [P, P],
+            "pulda_set_z": [P, P, i64],
+            "pulda_get_counts": [P, P, P],
+            "pulda_get_phi": [P, P, P, P, P],
+            "pulda_get_word_tables": [P, P, P, P, P, P, P, P, P, P],
+            "pulda_infer": [P, P, P, i64, i32, u64, P, P],
+            "pulda_stats": [P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.pulda_last_error.argtypes = [P]
+        L.pulda_last_error.restype = ctypes.c_char_p
+        L.pulda_free.argtypes = [P]
+        L.pulda_free.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return int(a.data_ptr())          # a torch tensor
+
+
+def _check(h, status: int):
+    if status != PULDA_OK:
+        msg = lib().pulda_last_error(h)
+        raise PuldaError(status, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------- C-named calls
+
+def pulda_init(word_ids, doc_offsets, K: int, V: int, alpha, beta: float, seed: int, stream=None,
+               zstep_path: int = 0, warps_per_block: int = 0) -> int:
+    w = np.ascontiguousarray(word_ids, dtype=np.int32)
+    off = np.ascontiguousarray(doc_offsets, dtype=np.int64)
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, dtype=np.float32), (K,)))
+    opt = Options()
+    opt.stream = stream
+    opt.zstep_path = zstep_path
+    opt.warps_per_block = warps_per_block
+    h = ctypes.c_void_p()
+    st = lib().pulda_init(ctypes.byref(h), _ptr(w), _ptr(off), off.shape[0] - 1, K, V, _ptr(a), float(beta),
+                          int(seed) & (2 ** 64 - 1), ctypes.byref(opt))
+    _check(None, st)
+    return h.value
+
+
+def pulda_sweep(h, n_sweeps: int = 1):
+    _check(h, lib().pulda_sweep(h, n_sweeps))
+
+
+def pulda_phi_step(h):
+    _check(h, lib().pulda_phi_step(h))
+
+
+def pulda_z_step(h):
+    _check(h, lib().pulda_z_step(h))
+
+
+def pulda_sync(h):
+    _check(h, lib().pulda_sync(h))
+
+
+def pulda_get_z(h, out: np.ndarray):
+    _check(h, lib().pulda_get_z(h, _ptr(out)))
+    return out
+
+
+def pulda_get_z_dev(h, out_tensor):
+    _check(h, lib().pulda_get_z_dev(h, _ptr(out_tensor)))
+    return out_tensor
+
+
+def pulda_set_z(h, z: np.ndarray, sweep: int):
+    z = np.ascontiguousarray(z, dtype=np.int16)
+    _check(h, lib().pulda_set_z(h, _ptr(z), sweep))
+
+
+def pulda_get_counts(h, n_kv: np.ndarray | None, m_dk: np.ndarray | None):
+    _check(h, lib().pulda_get_counts(h, _ptr(n_kv), _ptr(m_dk)))
+
+
+def pulda_get_phi(h, V: int):
+    nnz = ctypes.c_int64(0)
+    _check(h, lib().pulda_get_phi(h, None, None, None, ctypes.byref(nnz)))
+    col = np.zeros(V + 1, np.int64)
+    top = np.zeros(max(nnz.value, 1), np.int16)
+    phi = np.zeros(max(nnz.value, 1), np.float32)
+    _check(h, lib().pulda_get_phi(h, _ptr(col), _ptr(top), _ptr(phi), ctypes.byref(nnz)))
+    return col, top[:nnz.value], phi[:nnz.value]
+
+
+def pulda_get_word_tables(h, K: int, V: int) -> dict:
+    nnz = ctypes.c_int64(0)
+    _check(h, lib().pulda_get_word_tables(h, None, None, None, None, None, None, None, None, ctypes.byref(nnz)))
+    n = max(nnz.value, 1)
+    out = dict(col_ptr=np.zeros(V + 1, np.int64), topic=np.zeros(n, np.int16), c=np.zeros(n, np.uint32),
+               S=np.zeros(K, np.int64), q=np.zeros(n, np.uint32), A=np.zeros(V, np.uint64),
+               athr=np.zeros(n, np.uint32), atopic=np.zeros(n, np.int16))
+    _check(h, lib().pulda_get_word_tables(h, *[_ptr(out[k]) for k in
+                                               ("col_ptr", "topic", "c", "S", "q", "A", "athr", "atopic")],
+                                          ctypes.byref(nnz)))
+    for k in ("topic", "c", "q", "athr", "atopic"):
+        out[k] = out[k][:nnz.value]
+    return out
+
+
+def pulda_infer(h, word_ids, doc_offsets, n_sweeps: int, seed: int, K: int, want_m: bool = False):
+    w = np.ascontiguousarray(word_ids, dtype=np.int32)
+    off = np.ascontiguousarray(doc_offsets, dtype=np.int64)
+    D = off.shape[0] - 1
+    z = np.zeros(max(w.shape[0], 1), np.int16)
+    m = np.zeros((D, K), np.int32) if want_m else None
+    _check(h, lib().pulda_infer(h, _ptr(w), _ptr(off), D, n_sweeps, int(seed) & (2 ** 64 - 1), _ptr(z), _ptr(m)))
+    return (z[:w.shape[0]], m) if want_m else z[:w.shape[0]]
+
+
+def pulda_stats(h) -> dict:
+    s = SweepStats()
+    _check(h, lib().pulda_stats(h, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def pulda_last_error(h) -> str:
+    m = lib().pulda_last_error(h)
+    return m.decode() if m else ""
+
+
+def pulda_free(h):
+    if h:
+        lib().pulda_free(h)
+
+
+class Sampler:
+    """One chain: ``Sampler(w, doc_off, K, V, alpha, beta, seed).sweep(n)``."""
+
+    def __init__(self, word_ids, doc_offsets, K: int, V: int, alpha=0.1, beta: float = 0.01, seed: int = 0,
+                 stream=None, zstep_path: int = 0, warps_per_block: int = 0):
+        self.K, self.V = K, V
+        self.N = int(np.asarray(doc_offsets)[-1])
+        self.D = int(np.asarray(doc_offsets).shape[0] - 1)
+        self.h = pulda_init(word_ids, doc_offsets, K, V, alpha, beta, seed, stream, zstep_path, warps_per_block)
+
+    def close(self):
+        if self.h:
+            pulda_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n: int = 1):
+        pulda_sweep(self.h, n)
+        return self
+
+    def phi_step(self):
+        pulda_phi_step(self.h)
+        return self
+
+    def z_step(self):
+        pulda_z_step(self.h)
+        return self
+
+    def sync(self):
+        pulda_sync(self.h)
+
+    def z(self) -> np.ndarray:
+        return pulda_get_z(self.h, np.zeros(max(self.N, 1), np.int16))[:self.N]
+
+    def set_z(self, z, sweep: int):
+        pulda_set_z(self.h, z, sweep)
+
+    def n(self) -> np.ndarray:
+        out = np.zeros((self.K, self.V), np.int32)
+        pulda_get_counts(self.h, out, None)
+        return out
+
+    def m(self) -> np.ndarray:
+        out = np.zeros((self.D, self.K), np.int32)
+        pulda_get_counts(self.h, None, out)
+        return out
+
+    def phi(self):
+        return pulda_get_phi(self.h, self.V)
+
+    def word_tables(self) -> dict:
+        return pulda_get_word_tables(self.h, self.K, self.V)
+
+    def infer(self, word_ids, doc_offsets, n_sweeps: int, seed: int, want_m: bool = False):
+        return pulda_infer(self.h, word_ids, doc_offsets, n_sweeps, seed, self.K, want_m)
+
+    def stats(self) -> dict:
+        return pulda_stats(self.h)

@@ -1,0 +1,468 @@
+// C ABI of the pulda sampler: argument validation, device buffers, and the
+// order of kernel launches that makes one sweep (Algorithm 2, Section 3).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pulda.h"
+#include "pulda_internal.h"
+
+using namespace pulda;
+
+struct pulda_handle {
+    std::string err;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    pulda_options opt{};
+    int device = 0;
+    int64_t N = 0, D = 0;
+    int K = 0, V = 0, KW = 0;
+    uint64_t seed = 0;
+    int64_t sweep = 0;
+    bool have_phi = false;
+    float beta = 0;
+    int z_warps = 8, z_grid = 0, phi_grid = 0;
+    std::vector<void *> allocs;
+    // corpus and state
+    int32_t *w = nullptr; int64_t *doc_off = nullptr; int16_t *z = nullptr; int32_t *doc_order = nullptr;
+    int32_t *perm = nullptr; int64_t *word_off = nullptr; int32_t *word_order = nullptr; int32_t *fill = nullptr;
+    float *alpha = nullptr;
+    // fixed tables
+    uint32_t *t_thr = nullptr; uint16_t *t_alias = nullptr; int32_t *t_off = nullptr, *t_lo = nullptr, *t_n = nullptr;
+    uint32_t *t_geo = nullptr; double *t_gauss = nullptr;
+    // Phi-step buffers
+    uint16_t *nst_k = nullptr; uint32_t *nst_n = nullptr; int32_t *nnz_n = nullptr;
+    uint16_t *cst_k = nullptr; uint32_t *cst_c = nullptr; int32_t *nnz_c = nullptr;
+    unsigned long long *S = nullptr; uint32_t *rowbuf = nullptr; int64_t *col_ptr = nullptr;
+    uint16_t *topic = nullptr; uint32_t *c = nullptr, *q = nullptr, *athr = nullptr; uint16_t *atopic = nullptr;
+    unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint32_t *bitmap = nullptr;
+    int *work = nullptr;
+    unsigned long long *stats = nullptr;
+    int64_t cap = 0;   // capacity of the per-word tables: K * V entries
+};
+
+namespace {
+
+thread_local std::string g_init_error;
+
+pulda_status fail(pulda_handle *h, pulda_status s, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return s;
+}
+
+#define CU(h, expr)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (expr);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA,        \
+                        "%s failed: %s", #expr, cudaGetErrorString(e_));                              \
+    } while (0)
+
+// inside pulda_init: record the failure and release the half-built handle
+#define CUI(expr)                                                                                     \
+    do {                                                                                              \
+        cudaError_t e_ = (expr);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            pulda_status s_ = e_ == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA;       \
+            fail(h, s_, "%s failed: %s", #expr, cudaGetErrorString(e_));                              \
+            return bail(s_);                                                                          \
+        }                                                                                             \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(pulda_handle *h, T **p, size_t count) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, sizeof(T) * std::max<size_t>(count, 1));
+    if (e == cudaSuccess) h->allocs.push_back(ptr);
+    *p = static_cast<T *>(ptr);
+    return e;
+}
+
+PhiArgs phi_args(pulda_handle *h) {
+    PhiArgs a{};
+    a.K = h->K; a.V = h->V; a.seed = h->seed; a.sweep = static_cast<uint32_t>(h->sweep);
+    a.perm = h->perm; a.word_off = h->word_off; a.word_order = h->word_order; a.z = h->z;
+    a.tab = DevTables{h->t_thr, h->t_alias, h->t_off, h->t_lo, h->t_n, h->t_geo, h->t_gauss, static_cast<double>(h->beta)};
+    a.nst_k = h->nst_k; a.nst_n = h->nst_n; a.nnz_n = h->nnz_n;
+    a.cst_k = h->cst_k; a.cst_c = h->cst_c; a.nnz_c = h->nnz_c;
+    a.S = h->S; a.rowbuf = h->rowbuf; a.col_ptr = h->col_ptr;
+    a.topic = h->topic; a.c = h->c; a.q = h->q; a.athr = h->athr; a.atopic = h->atopic;
+    a.A = h->A; a.vose_p = h->vose_p; a.vose_stack = h->vose_stack; a.bitmap = h->bitmap; a.KW = h->KW;
+    a.alpha = h->alpha; a.work = h->work; a.stats = h->stats;
+    return a;
+}
+
+ZArgs z_args(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, const int32_t *w,
+             int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
+    ZArgs a{};
+    a.doc_off = doc_off; a.doc_order = doc_order; a.D = D; a.w = w; a.z = z;
+    a.col_ptr = h->col_ptr; a.topic = h->topic; a.q = h->q; a.A = h->A; a.athr = h->athr; a.atopic = h->atopic;
+    a.bitmap = h->bitmap; a.K = h->K; a.KW = h->KW; a.seed = seed; a.sweep = sweep; a.index_base = index_base;
+    a.path = h->opt.zstep_path; a.work = h->work + 1; a.stats = h->stats;
+    return a;
+}
+
+pulda_status check_corpus(pulda_handle *h, const int32_t *w, const int64_t *off, int64_t D, int V,
+                          int64_t *N_out) {
+    if (D < 0) return fail(h, PULDA_ERR_INVALID, "D must be >= 0 (got %lld)", (long long)D);
+    if (D > 0 && !off) return fail(h, PULDA_ERR_INVALID, "doc_offsets is NULL");
+    if (D > 0 && off[0] != 0) return fail(h, PULDA_ERR_INVALID, "doc_offsets[0] must be 0");
+    for (int64_t d = 0; d < D; ++d) {
+        if (off[d + 1] < off[d]) return fail(h, PULDA_ERR_INVALID, "doc_offsets decrease at document %lld", (long long)d);
+        if (off[d + 1] - off[d] > (int64_t(1) << 22))
+            return fail(h, PULDA_ERR_INVALID, "document %lld is longer than 2^22 tokens", (long long)d);
+    }
+    const int64_t N = D > 0 ? off[D] : 0;
+    if (N >= (int64_t(1) << 31)) return fail(h, PULDA_ERR_INVALID, "corpus larger than 2^31-1 tokens");
+    if (N > 0 && !w) return fail(h, PULDA_ERR_INVALID, "word_ids is NULL");
+    for (int64_t i = 0; i < N; ++i)
+        if (w[i] < 0 || w[i] >= V)
+            return fail(h, PULDA_ERR_INVALID, "word id %d at token %lld is outside [0, %d)", w[i], (long long)i, V);
+    *N_out = N;
+    return PULDA_OK;
+}
+
+// Documents in decreasing length (ties by index), so the persistent z-step
+// starts the long ones first.
+std::vector<int32_t> length_order(const int64_t *off, int64_t D) {
+    std::vector<int32_t> o(D);
+    std::iota(o.begin(), o.end(), 0);
+    std::stable_sort(o.begin(), o.end(), [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    return o;
+}
+
+pulda_status run_z(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, const int32_t *w,
+                   int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
+    CU(h, cudaMemsetAsync(h->work + 1, 0, sizeof(int), h->stream));
+    ZArgs a = z_args(h, doc_off, doc_order, D, w, z, seed, sweep, index_base);
+    launch_z_step(a, h->z_warps, h->z_grid, h->stream);
+    CU(h, cudaGetLastError());
+    return PULDA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64_t *doc_offsets, int64_t D, int32_t K,
+                        int32_t V, const float *alpha, float beta, uint64_t seed, const pulda_options *opt) {
+    if (!out) return PULDA_ERR_INVALID;
+    *out = nullptr;
+    pulda_handle *h = new pulda_handle();
+    // the handle is returned only on success: keep the reason of a failure
+    // where pulda_last_error(NULL) finds it
+    auto bail = [&](pulda_status s) { g_init_error = h->err; pulda_free(h); return s; };
+    auto reject = bail;
+    g_init_error.clear();
+    if (K < 1 || K > kMaxK) { fail(h, PULDA_ERR_INVALID, "K must be in [1, %d] (got %d)", kMaxK, K); return reject(PULDA_ERR_INVALID); }
+    if (V < 1) { fail(h, PULDA_ERR_INVALID, "V must be >= 1 (got %d)", V); return reject(PULDA_ERR_INVALID); }
+    if (!(beta > 0.0f && beta <= 64.0f)) { fail(h, PULDA_ERR_INVALID, "beta must be in (0, 64]"); return reject(PULDA_ERR_INVALID); }
+    if (!alpha) { fail(h, PULDA_ERR_INVALID, "alpha is NULL"); return reject(PULDA_ERR_INVALID); }
+    for (int k = 0; k < K; ++k)
+        if (!(alpha[k] > 0.0f && alpha[k] <= 256.0f)) {
+            fail(h, PULDA_ERR_INVALID, "alpha[%d] must be in (0, 256]", k);
+            return reject(PULDA_ERR_INVALID);
+        }
+    int64_t N = 0;
+    if (check_corpus(h, word_ids, doc_offsets, D, V, &N) != PULDA_OK) return reject(PULDA_ERR_INVALID);
+    if (opt) h->opt = *opt;
+    if (h->opt.zstep_path < 0 || h->opt.zstep_path > 2) { fail(h, PULDA_ERR_INVALID, "zstep_path must be 0, 1 or 2"); return reject(PULDA_ERR_INVALID); }
+    h->N = N; h->D = D; h->K = K; h->V = V; h->seed = seed; h->beta = beta;
+    h->KW = (K + 31) / 32;
+    h->cap = static_cast<int64_t>(K) * V;
+    cudaGetDevice(&h->device);
+    if (h->opt.stream) {
+        h->stream = static_cast<cudaStream_t>(h->opt.stream);
+    } else {
+        CUI(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    HostTables tab;
+    if (build_host_tables(beta, &tab) != 0) { fail(h, PULDA_ERR_INVALID, "Poisson table construction failed"); return bail(PULDA_ERR_INVALID); }
+
+#define ALLOC(ptr, n) do { cudaError_t e_ = dalloc(h, &(ptr), (n)); if (e_ != cudaSuccess) { \
+        fail(h, PULDA_ERR_OOM, "cudaMalloc of %s (%zu entries) failed: %s", #ptr, (size_t)(n), cudaGetErrorString(e_)); \
+        return bail(PULDA_ERR_OOM); } } while (0)
+    ALLOC(h->w, N); ALLOC(h->doc_off, D + 1); ALLOC(h->z, N); ALLOC(h->doc_order, D);
+    ALLOC(h->perm, N); ALLOC(h->word_off, V + 1); ALLOC(h->word_order, V); ALLOC(h->fill, V);
+    ALLOC(h->alpha, K);
+    ALLOC(h->t_thr, tab.thr.size()); ALLOC(h->t_alias, tab.alias.size()); ALLOC(h->t_off, kL + 1);
+    ALLOC(h->t_lo, kL + 1); ALLOC(h->t_n, kL + 1); ALLOC(h->t_geo, kGeoLen); ALLOC(h->t_gauss, kGaussCells + 1);
+    ALLOC(h->nst_k, N); ALLOC(h->nst_n, N); ALLOC(h->nnz_n, V);
+    ALLOC(h->cst_k, h->cap); ALLOC(h->cst_c, h->cap); ALLOC(h->nnz_c, V);
+    ALLOC(h->S, K); ALLOC(h->rowbuf, V); ALLOC(h->col_ptr, V + 1);
+    ALLOC(h->topic, h->cap); ALLOC(h->c, h->cap); ALLOC(h->q, h->cap); ALLOC(h->athr, h->cap); ALLOC(h->atopic, h->cap);
+    ALLOC(h->A, V); ALLOC(h->vose_p, h->cap); ALLOC(h->vose_stack, h->cap);
+    if (K <= kMaxKBitmap) ALLOC(h->bitmap, static_cast<size_t>(V) * h->KW);
+    ALLOC(h->work, 4); ALLOC(h->stats, ST_TOTAL_SLOTS);
+#undef ALLOC
+    cudaStream_t st = h->stream;
+    CUI(cudaMemcpyAsync(h->w, word_ids, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+    std::vector<int64_t> off0(1, 0);
+    CUI(cudaMemcpyAsync(h->doc_off, D > 0 ? doc_offsets : off0.data(), sizeof(int64_t) * (D + 1), cudaMemcpyHostToDevice, st));
+    std::vector<int32_t> dord = length_order(doc_offsets, D);
+    CUI(cudaMemcpyAsync(h->doc_order, dord.data(), sizeof(int32_t) * D, cudaMemcpyHostToDevice, st));
+    CUI(cudaMemcpyAsync(h->alpha, alpha, sizeof(float) * K, cudaMemcpyHostToDevice, st));
+    CUI(cudaMemcpyAsync(h->t_thr, tab.thr.data(), sizeof(uint32_t) * tab.thr.size(), cudaMemcpyHostToDevice, st));
+    CUI(cudaMemcpyAsync(h->t_alias, tab.alias.data(), sizeof(uint16_t) * tab.alias.size(), cudaMemcpyHostToDevice, st));
+    CUI(cudaMemcpyAsync(h->t_off, tab.off.data(), sizeof(int32_t) * (kL + 1), cudaMemcpyHostToDevice, st));
+    CUI(cudaMemcpyAsync(h->t_lo, tab.lo.data(), sizeof(int32_t) * (kL + 1), cudaMemcpyHostToDevice, st));
+    CUI(cudaMemcpyAsync(h->t_n, tab.n.data(), sizeof(int32_t) * (kL + 1), cudaMemcpyHostToDevice, st));
+    CUI(cudaMemcpyAsync(h->t_geo, tab.geo.data(), sizeof(uint32_t) * kGeoLen, cudaMemcpyHostToDevice, st));
+    CUI(cudaMemcpyAsync(h->t_gauss, tab.gauss.data(), sizeof(double) * (kGaussCells + 1), cudaMemcpyHostToDevice, st));
+    // word-major permutation and the word schedule (most tokens first)
+    CUI(cudaGetLastError());            // nothing pending before the first launch
+    launch_word_perm(N, V, h->w, h->word_off, h->fill, h->perm, st);
+    CUI(cudaGetLastError());
+    std::vector<int64_t> woff(V + 1);
+    CUI(cudaMemcpyAsync(woff.data(), h->word_off, sizeof(int64_t) * (V + 1), cudaMemcpyDeviceToHost, st));
+    CUI(cudaStreamSynchronize(st));
+    std::vector<int32_t> word_order(V);
+    std::iota(word_order.begin(), word_order.end(), 0);
+    std::stable_sort(word_order.begin(), word_order.end(),
+                     [&](int32_t a, int32_t b) { return woff[a + 1] - woff[a] > woff[b + 1] - woff[b]; });
+    CUI(cudaMemcpyAsync(h->word_order, word_order.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, st));
+    CUI(cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * ST_TOTAL_SLOTS, st));
+    launch_init_z(N, K, seed, 0, h->z, st);
+    CUI(cudaGetLastError());
+    // launch shapes
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    int wpb = h->opt.warps_per_block;
+    if (wpb <= 0) wpb = 8;
+    while (wpb > 1 && z_step_smem(K, wpb) > 160 * 1024) wpb >>= 1;
+    h->z_warps = wpb;
+    h->z_grid = sms * z_step_blocks_per_sm(K, wpb);
+    CUI(cudaGetLastError());
+    h->phi_grid = sms * phi_counts_blocks_per_sm(K);
+    CUI(cudaGetLastError());
+    CUI(cudaStreamSynchronize(st));
+    *out = h;
+    return PULDA_OK;
+}
+
+pulda_status pulda_phi_step(pulda_handle *h) {
+    if (!h) return PULDA_ERR_INVALID;
+    h->sweep += 1;
+    cudaStream_t st = h->stream;
+    CU(h, cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
+    CU(h, cudaMemsetAsync(h->work, 0, sizeof(int), st));
+    CU(h, cudaMemsetAsync(h->S, 0, sizeof(unsigned long long) * h->K, st));
+    PhiArgs a = phi_args(h);
+    launch_phi_counts(a, true, h->phi_grid, st);
+    launch_phi_fixup(a, st);
+    launch_colptr_scan(a, st);
+    launch_phi_tables(a, st);
+    CU(h, cudaGetLastError());
+    h->have_phi = true;
+    return PULDA_OK;
+}
+
+pulda_status pulda_z_step(pulda_handle *h) {
+    if (!h) return PULDA_ERR_INVALID;
+    if (!h->have_phi) return fail(h, PULDA_ERR_INVALID, "no Phi drawn yet: call pulda_phi_step or pulda_sweep first");
+    CU(h, cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * 4, h->stream));
+    return run_z(h, h->doc_off, h->doc_order, h->D, h->w, h->z, h->seed, static_cast<uint32_t>(h->sweep), 0);
+}
+
+pulda_status pulda_sweep(pulda_handle *h, int32_t n_sweeps) {
+    if (!h) return PULDA_ERR_INVALID;
+    if (n_sweeps < 0) return fail(h, PULDA_ERR_INVALID, "n_sweeps must be >= 0");
+    for (int32_t s = 0; s < n_sweeps; ++s) {
+        pulda_status r = pulda_phi_step(h);
+        if (r != PULDA_OK) return r;
+        r = pulda_z_step(h);
+        if (r != PULDA_OK) return r;
+    }
+    return PULDA_OK;
+}
+
+pulda_status pulda_sync(pulda_handle *h) {
+    if (!h) return PULDA_ERR_INVALID;
+    CU(h, cudaStreamSynchronize(h->stream));
+    unsigned long long e = 0;
+    CU(h, cudaMemcpy(&e, h->stats + ST_ERROR, sizeof e, cudaMemcpyDeviceToHost));
+    if (e & ERR_DEGENERATE) return fail(h, PULDA_ERR_DEGENERATE, "a Phi row stayed all-zero after 2^20 redraws");
+    if (e & ERR_INTERNAL) return fail(h, PULDA_ERR_CUDA, "z-step invariant violated (draw beyond the total mass)");
+    return PULDA_OK;
+}
+
+pulda_status pulda_get_z(pulda_handle *h, int16_t *z_host) {
+    if (!h || (!z_host && h->N)) return fail(h, PULDA_ERR_INVALID, "z_host is NULL");
+    CU(h, cudaMemcpyAsync(z_host, h->z, sizeof(int16_t) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    return pulda_sync(h);
+}
+
+pulda_status pulda_get_z_dev(pulda_handle *h, int16_t *z_dev) {
+    if (!h || (!z_dev && h->N)) return fail(h, PULDA_ERR_INVALID, "z_dev is NULL");
+    CU(h, cudaMemcpyAsync(z_dev, h->z, sizeof(int16_t) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+    return PULDA_OK;
+}
+
+pulda_status pulda_set_z(pulda_handle *h, const int16_t *z_host, int64_t sweep) {
+    if (!h) return PULDA_ERR_INVALID;
+    if (sweep < 0 || sweep >= (int64_t(1) << 32)) return fail(h, PULDA_ERR_INVALID, "sweep out of range");
+    for (int64_t i = 0; i < h->N; ++i)
+        if (z_host[i] < 0 || z_host[i] >= h->K) return fail(h, PULDA_ERR_INVALID, "topic %d at token %lld out of range", z_host[i], (long long)i);
+    CU(h, cudaMemcpyAsync(h->z, z_host, sizeof(int16_t) * h->N, cudaMemcpyHostToDevice, h->stream));
+    h->sweep = sweep;
+    h->have_phi = false;
+    return pulda_sync(h);
+}
+
+pulda_status pulda_get_counts(pulda_handle *h, int32_t *n_kv, int32_t *m_dk) {
+    if (!h) return PULDA_ERR_INVALID;
+    cudaStream_t st = h->stream;
+    if (n_kv) {
+        // rebuild n from the current z (counts only, no draws)
+        PhiArgs a = phi_args(h);
+        CU(h, cudaMemsetAsync(h->work, 0, sizeof(int), st));
+        launch_phi_counts(a, false, h->phi_grid, st);
+        int32_t *dn = nullptr;
+        CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dn), sizeof(int32_t) * static_cast<size_t>(h->K) * h->V, st));
+        launch_n_dense(a, dn, st);
+        cudaError_t e = cudaMemcpyAsync(n_kv, dn, sizeof(int32_t) * static_cast<size_t>(h->K) * h->V, cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(dn, st);
+        CU(h, e);
+    }
+    if (m_dk && h->D > 0) {
+        int32_t *dm = nullptr;
+        CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dm), sizeof(int32_t) * static_cast<size_t>(h->K) * h->D, st));
+        launch_doc_topic(h->doc_off, h->D, h->z, h->K, dm, st);
+        cudaError_t e = cudaMemcpyAsync(m_dk, dm, sizeof(int32_t) * static_cast<size_t>(h->K) * h->D, cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(dm, st);
+        CU(h, e);
+    }
+    CU(h, cudaGetLastError());
+    return pulda_sync(h);
+}
+
+pulda_status pulda_get_word_tables(pulda_handle *h, int64_t *col_ptr, int16_t *topic, uint32_t *c, int64_t *S,
+                                   uint32_t *q, uint64_t *A, uint32_t *athr, int16_t *atopic, int64_t *nnz_inout) {
+    if (!h || !nnz_inout) return fail(h, PULDA_ERR_INVALID, "nnz_inout is NULL");
+    if (!h->have_phi) return fail(h, PULDA_ERR_INVALID, "no Phi drawn yet");
+    cudaStream_t st = h->stream;
+    int64_t nnz = 0;
+    CU(h, cudaMemcpyAsync(&nnz, h->col_ptr + h->V, sizeof nnz, cudaMemcpyDeviceToHost, st));
+    CU(h, cudaStreamSynchronize(st));
+    const bool want = col_ptr || topic || c || q || athr || atopic;
+    if (want && *nnz_inout < nnz) {
+        int64_t have = *nnz_inout;
+        *nnz_inout = nnz;
+        return fail(h, PULDA_ERR_INVALID, "capacity %lld < nnz %lld", (long long)have, (long long)nnz);
+    }
+    *nnz_inout = nnz;
+    if (col_ptr) CU(h, cudaMemcpyAsync(col_ptr, h->col_ptr, sizeof(int64_t) * (h->V + 1), cudaMemcpyDeviceToHost, st));
+    if (topic) CU(h, cudaMemcpyAsync(topic, h->topic, sizeof(uint16_t) * nnz, cudaMemcpyDeviceToHost, st));
+    if (c) CU(h, cudaMemcpyAsync(c, h->c, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st));
+    if (S) CU(h, cudaMemcpyAsync(S, h->S, sizeof(int64_t) * h->K, cudaMemcpyDeviceToHost, st));
+    if (q) CU(h, cudaMemcpyAsync(q, h->q, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st));
+    if (A) CU(h, cudaMemcpyAsync(A, h->A, sizeof(uint64_t) * h->V, cudaMemcpyDeviceToHost, st));
+    if (athr) CU(h, cudaMemcpyAsync(athr, h->athr, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st));
+    if (atopic) CU(h, cudaMemcpyAsync(atopic, h->atopic, sizeof(uint16_t) * nnz, cudaMemcpyDeviceToHost, st));
+    return pulda_sync(h);
+}
+
+pulda_status pulda_get_phi(pulda_handle *h, int64_t *col_ptr, int16_t *topic, float *phi, int64_t *nnz_inout) {
+    if (!h || !nnz_inout) return fail(h, PULDA_ERR_INVALID, "nnz_inout is NULL");
+    if (!h->have_phi) return fail(h, PULDA_ERR_INVALID, "no Phi drawn yet");
+    int64_t cap = *nnz_inout;
+    pulda_status s = pulda_get_word_tables(h, col_ptr, topic, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nnz_inout);
+    if (s != PULDA_OK) return s;
+    if (phi) {
+        const int64_t nnz = *nnz_inout;
+        if (cap < nnz) return fail(h, PULDA_ERR_INVALID, "capacity %lld < nnz %lld", (long long)cap, (long long)nnz);
+        cudaStream_t st = h->stream;
+        float *dp = nullptr;
+        CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dp), sizeof(float) * std::max<int64_t>(nnz, 1), st));
+        PhiArgs a = phi_args(h);
+        launch_phi_values(a, dp, st);
+        cudaError_t e = cudaMemcpyAsync(phi, dp, sizeof(float) * nnz, cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(dp, st);
+        CU(h, e);
+        return pulda_sync(h);
+    }
+    return PULDA_OK;
+}
+
+pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids, const int64_t *doc_offsets, int64_t D_new,
+                         int32_t n_sweeps, uint64_t seed, int16_t *z_out, int32_t *m_out) {
+    if (!h) return PULDA_ERR_INVALID;
+    if (!h->have_phi) return fail(h, PULDA_ERR_INVALID, "no Phi drawn yet: run a sweep before pulda_infer");
+    if (n_sweeps < 0) return fail(h, PULDA_ERR_INVALID, "n_sweeps must be >= 0");
+    int64_t N = 0;
+    pulda_status s = check_corpus(h, word_ids, doc_offsets, D_new, h->V, &N);
+    if (s != PULDA_OK) return s;
+    if (D_new == 0) return PULDA_OK;
+    cudaStream_t st = h->stream;
+    int32_t *dw = nullptr, *dord = nullptr, *dm = nullptr;
+    int64_t *doff = nullptr;
+    int16_t *dz = nullptr;
+    CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dw), sizeof(int32_t) * std::max<int64_t>(N, 1), st));
+    CU(h, cudaMallocAsync(reinterpret_cast<void **>(&doff), sizeof(int64_t) * (D_new + 1), st));
+    CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dord), sizeof(int32_t) * D_new, st));
+    CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dz), sizeof(int16_t) * std::max<int64_t>(N, 1), st));
+    std::vector<int32_t> ord = length_order(doc_offsets, D_new);
+    CU(h, cudaMemcpyAsync(dw, word_ids, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
+    CU(h, cudaMemcpyAsync(doff, doc_offsets, sizeof(int64_t) * (D_new + 1), cudaMemcpyHostToDevice, st));
+    CU(h, cudaMemcpyAsync(dord, ord.data(), sizeof(int32_t) * D_new, cudaMemcpyHostToDevice, st));
+    launch_init_z(N, h->K, seed, 0, dz, st);
+    CU(h, cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * 4, st));
+    for (int32_t sw = 1; sw <= n_sweeps; ++sw) {
+        s = run_z(h, doff, dord, D_new, dw, dz, seed, static_cast<uint32_t>(sw), 0);
+        if (s != PULDA_OK) return s;
+    }
+    if (z_out) CU(h, cudaMemcpyAsync(z_out, dz, sizeof(int16_t) * N, cudaMemcpyDeviceToHost, st));
+    if (m_out) {
+        CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dm), sizeof(int32_t) * static_cast<size_t>(D_new) * h->K, st));
+        launch_doc_topic(doff, D_new, dz, h->K, dm, st);
+        CU(h, cudaMemcpyAsync(m_out, dm, sizeof(int32_t) * static_cast<size_t>(D_new) * h->K, cudaMemcpyDeviceToHost, st));
+        cudaFreeAsync(dm, st);
+    }
+    cudaFreeAsync(dw, st); cudaFreeAsync(doff, st); cudaFreeAsync(dord, st); cudaFreeAsync(dz, st);
+    CU(h, cudaGetLastError());
+    return pulda_sync(h);
+}
+
+pulda_status pulda_stats(pulda_handle *h, pulda_sweep_stats *out) {
+    if (!h || !out) return PULDA_ERR_INVALID;
+    pulda_status s = pulda_sync(h);
+    if (s != PULDA_OK) return s;
+    unsigned long long st[ST_TOTAL_SLOTS];
+    CU(h, cudaMemcpy(st, h->stats, sizeof st, cudaMemcpyDeviceToHost));
+    out->tokens = static_cast<int64_t>(st[ST_TOKENS]);
+    out->a_branch = static_cast<int64_t>(st[ST_ABRANCH]);
+    out->sum_min = static_cast<int64_t>(st[ST_SUMMIN]);
+    out->zero_mass = static_cast<int64_t>(st[ST_ZEROMASS]);
+    out->dead_rows = static_cast<int64_t>(st[ST_DEADROWS]);
+    out->nnz_phi = static_cast<int64_t>(st[ST_NNZPHI]);
+    out->sweep = h->sweep;
+    out->cum_tokens = static_cast<int64_t>(st[ST_COUNT + ST_TOKENS]);
+    out->cum_a_branch = static_cast<int64_t>(st[ST_COUNT + ST_ABRANCH]);
+    out->cum_sum_min = static_cast<int64_t>(st[ST_COUNT + ST_SUMMIN]);
+    out->cum_zero_mass = static_cast<int64_t>(st[ST_COUNT + ST_ZEROMASS]);
+    return PULDA_OK;
+}
+
+const char *pulda_last_error(const pulda_handle *h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+void pulda_free(pulda_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,754 @@
+// CUDA kernels of the Polya-urn partially collapsed LDA sampler, sm_103a.
+//
+// One sweep = Algorithm 2 (Section 3):
+//   Phi-step  k_phi_counts   per word v: rebuild n_{.,v} from z (shared-memory
+//                            histogram over the word's tokens), draw
+//                            c_{k,v} ~ Pois(beta + n_{k,v}) for every k (Eq. 7,
+//                            "Efficient sampling of Phi"), accumulate S_k.
+//             k_phi_fixup    rows with S_k = 0 are redrawn until nonzero
+//                            (Definition "Poisson Polya Urn").
+//             k_colptr_scan  column offsets of the sparse Phi.
+//             k_phi_tables   phi = c/S, fixed-point weights, sigma_a and the
+//                            per-word alias table ("Efficient sampling of z").
+//   z-step    k_z_step       one warp per document, tokens in order, the
+//                            doubly sparse a/b draw.
+// The arithmetic that decides any draw is integer or IEEE double with
+// explicit rounding, so results are independent of launch shapes.
+#include <algorithm>
+#include <cstdint>
+
+#include "pulda_internal.h"
+
+namespace pulda {
+namespace {
+
+typedef unsigned long long u64;
+
+// ------------------------------------------------------------------ Philox
+struct U4 { uint32_t x, y, z, w; };
+
+// Philox4x32-10 (Salmon et al., SC'11).
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ U4 draw(uint64_t seed, uint32_t a, uint32_t b, uint32_t sweep, uint32_t tag, uint32_t aux) {
+    return philox(a, b, sweep, (tag << 28) | (aux & 0x0FFFFFFFu), static_cast<uint32_t>(seed),
+                  static_cast<uint32_t>(seed >> 32));
+}
+
+// ------------------------------------------------------- Phi-step draws
+// Alias-table draw from table t: slot floor(xs * n / 2^32), kept if xa < thr.
+__device__ __forceinline__ uint32_t table_draw(const DevTables &T, int t, uint32_t xs, uint32_t xa) {
+    const int off = T.off[t];
+    const uint32_t s = __umulhi(xs, static_cast<uint32_t>(T.n[t]));
+    const uint32_t j = xa < T.thr[off + s] ? s : static_cast<uint32_t>(T.alias[off + s]);
+    return static_cast<uint32_t>(T.lo[t] + static_cast<int>(j));
+}
+
+// c ~ Pois(beta + l) for l >= 1: alias table for l <= L, rounded Gaussian
+// mu + sqrt(mu) g, mu = beta + l, above.  g is interpolated linearly inside
+// one of 2^16 equiprobable cells of the normal law.
+__device__ uint32_t draw_entry(const DevTables &T, uint32_t l, uint32_t x0, uint32_t x1) {
+    if (l <= static_cast<uint32_t>(kL)) return table_draw(T, static_cast<int>(l), x0, x1);
+    const uint32_t cell = x0 >> 16;
+    const uint64_t frac48 = (static_cast<uint64_t>(x0 & 0xFFFFu) << 32) | x1;
+    const double f = __dmul_rn(static_cast<double>(frac48), 3.552713678800501e-15);   // 2^-48
+    const double a = T.gauss[cell], b = T.gauss[cell + 1];
+    const double g = __dadd_rn(a, __dmul_rn(__dsub_rn(b, a), f));
+    const double mu = __dadd_rn(T.beta, static_cast<double>(l));
+    const double sd = __dsqrt_rn(mu);
+    double r = floor(__dadd_rn(__dadd_rn(mu, __dmul_rn(sd, g)), 0.5));
+    if (r < 0.0) r = 0.0;
+    if (r > 4294967295.0) r = 4294967295.0;
+    return static_cast<uint32_t>(r);
+}
+
+// Smallest g with x < geo[g]; -1 when the gap is at least kGeoLen.
+__device__ __forceinline__ int geo_gap(const uint32_t *geo, uint32_t x) {
+    if (x >= geo[kGeoLen - 1]) return -1;
+    int lo = 0, hi = kGeoLen - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (x < geo[mid]) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------- block helpers
+template <int BLOCK>
+__device__ __forceinline__ int block_excl_scan(int v, int *tmp /* >= BLOCK/32 + 1 */, int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < BLOCK / 32 ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < BLOCK / 32) tmp[lane] = t;
+    }
+    __syncthreads();
+    total = tmp[BLOCK / 32 - 1];
+    const int base = warp ? tmp[warp - 1] : 0;
+    __syncthreads();
+    return base + x - v;
+}
+
+__device__ __forceinline__ u64 warp_sum64(u64 v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ u64 warp_incl_scan64(u64 v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_excl_scan32(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x - v;
+}
+
+// ================================================================= init
+__global__ void k_init_z(int64_t N, int K, uint64_t seed, int64_t base, int16_t *z) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t t = static_cast<uint64_t>(base + i);
+        const U4 x = draw(seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), 0, TAG_INIT, 0);
+        z[i] = static_cast<int16_t>(__umulhi(x.x, static_cast<uint32_t>(K)));
+    }
+}
+
+// word-major permutation: counting sort of token ids by word id
+__global__ void k_word_hist(int64_t N, const int32_t *w, int32_t *cnt) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        atomicAdd(&cnt[w[i]], 1);
+}
+
+// Exclusive scan of cnt[0..n) into out[0..n] (out[n] = total), one block.
+template <typename TIn>
+__global__ void k_scan_single(const TIn *cnt, int64_t n, int64_t *out, unsigned long long *total_slot) {
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t a = t * per, b = min(n, a + per);
+    int64_t s = 0;
+    for (int64_t i = a; i < b; ++i) s += cnt[i];
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < static_cast<int>(blockDim.x); ++i) { const int64_t v = part[i]; part[i] = run; run += v; }
+        out[n] = run;
+        if (total_slot) *total_slot = static_cast<unsigned long long>(run);
+    }
+    __syncthreads();
+    int64_t run = part[t];
+    for (int64_t i = a; i < b; ++i) { out[i] = run; run += cnt[i]; }
+}
+
+__global__ void k_word_scatter(int64_t N, const int32_t *w, const int64_t *word_off, int32_t *fill, int32_t *perm) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int v = w[i];
+        const int pos = atomicAdd(&fill[v], 1);
+        perm[word_off[v] + pos] = static_cast<int32_t>(i);
+    }
+}
+
+// ======================================================== Phi-step: counts
+constexpr int kPhiBlock = 256;
+
+// Per word (dynamically scheduled, most frequent first): histogram of the
+// word's topics -> n_{.,v}; compacted n column; when `draw`, the Poisson
+// draws c_{.,v}, the compacted c column, and S_k += c_{k,v}.
+__global__ void __launch_bounds__(kPhiBlock) k_phi_counts(PhiArgs a, bool do_draw) {
+    extern __shared__ uint32_t sm[];
+    uint32_t *hist = sm;
+    uint32_t *cbin = sm + a.K;
+    __shared__ int scan_tmp[kPhiBlock / 32 + 1];
+    __shared__ int s_item;
+    const int K = a.K;
+    const int per = (K + kPhiBlock - 1) / kPhiBlock;     // bins owned by each thread, contiguous
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= a.V) break;
+        const int v = a.word_order[item];
+        const int64_t wbeg = a.word_off[v], wend = a.word_off[v + 1];
+        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
+        __syncthreads();
+        for (int64_t t = wbeg + threadIdx.x; t < wend; t += kPhiBlock) atomicAdd(&hist[a.z[a.perm[t]]], 1u);
+        __syncthreads();
+        if (do_draw) {
+            // entries with n_{k,v} = l >= 1: c ~ Pois(beta + l)
+            for (int k = threadIdx.x; k < K; k += kPhiBlock) {
+                const uint32_t l = hist[k];
+                if (l) {
+                    const U4 x = draw(a.seed, static_cast<uint32_t>(v), static_cast<uint32_t>(k), a.sweep, TAG_POIS, 0);
+                    cbin[k] = draw_entry(a.tab, l, x.x, x.y);
+                }
+            }
+            // entries with n_{k,v} = 0: Pois(beta) by geometric skip-ahead
+            if (threadIdx.x == 0) {
+                int64_t pos = -1;
+                uint32_t h = 0;
+                for (;;) {
+                    const U4 x = draw(a.seed, static_cast<uint32_t>(v), h++, a.sweep, TAG_BETA, 0);
+                    const int g = geo_gap(a.tab.geo, x.x);
+                    if (g < 0) {
+                        pos += kGeoLen;
+                        if (pos >= K - 1) break;
+                        continue;
+                    }
+                    pos += g + 1;
+                    if (pos >= K) break;
+                    if (hist[pos] == 0) cbin[pos] = table_draw(a.tab, 0, x.y, x.z);
+                }
+            }
+            __syncthreads();
+        }
+        // compaction in ascending topic order
+        const int k0 = threadIdx.x * per, k1 = min(K, k0 + per);
+        int cn = 0, cc = 0;
+        for (int k = k0; k < k1; ++k) { cn += hist[k] != 0; cc += cbin[k] != 0; }
+        int tn, tc;
+        int pn = block_excl_scan<kPhiBlock>(cn, scan_tmp, tn);
+        int pc = block_excl_scan<kPhiBlock>(cc, scan_tmp, tc);
+        for (int k = k0; k < k1; ++k) {
+            const uint32_t l = hist[k];
+            if (l) { a.nst_k[wbeg + pn] = static_cast<uint16_t>(k); a.nst_n[wbeg + pn] = l; ++pn; }
+            if (do_draw) {
+                const uint32_t c = cbin[k];
+                if (c) {
+                    const int64_t o = static_cast<int64_t>(v) * K + pc;
+                    a.cst_k[o] = static_cast<uint16_t>(k);
+                    a.cst_c[o] = c;
+                    atomicAdd(&a.S[k], static_cast<u64>(c));
+                    ++pc;
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            a.nnz_n[v] = tn;
+            if (do_draw) a.nnz_c[v] = tc;
+        }
+        __syncthreads();
+    }
+}
+
+// n_{k,v} from the compacted n column of word v (binary search), 0 if absent.
+__device__ uint32_t lookup_n(const PhiArgs &a, int v, int k) {
+    const int64_t b = a.word_off[v];
+    int lo = 0, hi = a.nnz_n[v];
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const int km = a.nst_k[b + mid];
+        if (km < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < a.nnz_n[v] && a.nst_k[b + lo] == k) ? a.nst_n[b + lo] : 0u;
+}
+
+constexpr int kFixBlock = 1024;
+
+// Rows whose Poisson counts summed to zero are redrawn whole (attempt
+// a = 1, 2, ...) until the sum is nonzero: the urn total is Pois+ (the
+// hierarchical representation, Eq. 6).  Accepted rows are inserted into the
+// word columns.  Single block; almost always just checks S and exits.
+__global__ void __launch_bounds__(kFixBlock) k_phi_fixup(PhiArgs a) {
+    __shared__ u64 red[kFixBlock / 32];
+    __shared__ u64 s_sum;
+    for (int k = 0; k < a.K; ++k) {
+        if (a.S[k] != 0) continue;
+        if (threadIdx.x == 0) atomicAdd(&a.stats[ST_DEADROWS], 1ull);
+        uint32_t att = 1;
+        for (; att <= kMaxRedraw; ++att) {
+            u64 part = 0;
+            for (int v = threadIdx.x; v < a.V; v += kFixBlock) {
+                const uint32_t l = lookup_n(a, v, k);
+                uint32_t val = 0;
+                if (l) {
+                    const U4 x = draw(a.seed, static_cast<uint32_t>(v), static_cast<uint32_t>(k), a.sweep, TAG_REDRAW_POIS, att);
+                    val = draw_entry(a.tab, l, x.x, x.y);
+                }
+                a.rowbuf[v] = val;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int64_t pos = -1;
+                uint32_t h = 0;
+                for (;;) {
+                    const U4 x = draw(a.seed, static_cast<uint32_t>(k), h++, a.sweep, TAG_REDRAW_BETA, att);
+                    const int g = geo_gap(a.tab.geo, x.x);
+                    if (g < 0) {
+                        pos += kGeoLen;
+                        if (pos >= a.V - 1) break;
+                        continue;
+                    }
+                    pos += g + 1;
+                    if (pos >= a.V) break;
+                    if (lookup_n(a, static_cast<int>(pos), k) == 0) a.rowbuf[pos] = table_draw(a.tab, 0, x.y, x.z);
+                }
+            }
+            __syncthreads();
+            for (int v = threadIdx.x; v < a.V; v += kFixBlock) part += a.rowbuf[v];
+            part = warp_sum64(part);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                u64 s = 0;
+                for (int i = 0; i < kFixBlock / 32; ++i) s += red[i];
+                s_sum = s;
+            }
+            __syncthreads();
+            const u64 sum = s_sum;
+            if (sum > 0) {
+                for (int v = threadIdx.x; v < a.V; v += kFixBlock) {
+                    const uint32_t val = a.rowbuf[v];
+                    if (!val) continue;
+                    const int64_t base = static_cast<int64_t>(v) * a.K;
+                    int n = a.nnz_c[v];
+                    int p = n;
+                    while (p > 0 && a.cst_k[base + p - 1] > k) {
+                        a.cst_k[base + p] = a.cst_k[base + p - 1];
+                        a.cst_c[base + p] = a.cst_c[base + p - 1];
+                        --p;
+                    }
+                    a.cst_k[base + p] = static_cast<uint16_t>(k);
+                    a.cst_c[base + p] = val;
+                    a.nnz_c[v] = n + 1;
+                }
+                if (threadIdx.x == 0) a.S[k] = sum;
+                __syncthreads();
+                break;
+            }
+            __syncthreads();
+        }
+        if (att > kMaxRedraw) {
+            if (threadIdx.x == 0) atomicOr(&a.stats[ST_ERROR], ERR_DEGENERATE);
+            return;
+        }
+    }
+}
+
+// =================================================== Phi-step: tables
+// Per word (one thread each): phi = fp32(c/S); fixed-point weights q with
+// 24 bits relative to the column maximum (q >= 1); alpha-part masses
+// a = round(q alpha 2^16), A = sigma_a; Vose alias table over a; bitmap of
+// the word's nonzero topics.
+__global__ void k_phi_tables(PhiArgs a) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) {
+        const int n = a.nnz_c[v];
+        const int64_t src = static_cast<int64_t>(v) * a.K;
+        const int64_t out = a.col_ptr[v];
+        if (a.bitmap) {
+            uint32_t *bm = a.bitmap + static_cast<int64_t>(v) * a.KW;
+            int j = 0;
+            for (int wi = 0; wi < a.KW; ++wi) {
+                uint32_t bits = 0;
+                while (j < n && (a.cst_k[src + j] >> 5) == wi) { bits |= 1u << (a.cst_k[src + j] & 31); ++j; }
+                bm[wi] = bits;
+            }
+        }
+        if (n == 0) { a.A[v] = 0; continue; }
+        double phimax = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const int k = a.cst_k[src + j];
+            const double p = __ddiv_rn(static_cast<double>(a.cst_c[src + j]), static_cast<double>(a.S[k]));
+            phimax = p > phimax ? p : phimax;
+        }
+        // phimax = f 2^e with f in [1/2, 1); scale = 2^(24 - e) (exact)
+        const long long bits = __double_as_longlong(phimax);
+        const int e = static_cast<int>((bits >> 52) & 0x7FF) - 1022;
+        const double scale = __longlong_as_double(static_cast<long long>(1023 + 24 - e) << 52);
+        u64 Asum = 0;
+        for (int j = 0; j < n; ++j) {
+            const int k = a.cst_k[src + j];
+            const uint32_t c = a.cst_c[src + j];
+            const double p = __ddiv_rn(static_cast<double>(c), static_cast<double>(a.S[k]));
+            const double qq = floor(__dadd_rn(__dmul_rn(p, scale), 0.5));
+            const uint32_t qv = qq < 1.0 ? 1u : static_cast<uint32_t>(qq);
+            const double at = __dmul_rn(__dmul_rn(static_cast<double>(qv), static_cast<double>(a.alpha[k])), 65536.0);
+            const u64 am = static_cast<u64>(floor(__dadd_rn(at, 0.5)));
+            a.topic[out + j] = static_cast<uint16_t>(k);
+            a.c[out + j] = c;
+            a.q[out + j] = qv;
+            a.vose_p[out + j] = am;
+            Asum += am;
+        }
+        a.A[v] = Asum;
+        // Vose: small stack grows up from 0, large stack down from n-1
+        u64 *P = a.vose_p + out;
+        uint16_t *stk = a.vose_stack + out;
+        int ns = 0, nl = 0;
+        for (int j = 0; j < n; ++j) {
+            a.athr[out + j] = 0xFFFFFFFFu;
+            a.atopic[out + j] = a.topic[out + j];
+        }
+        if (Asum == 0) continue;
+        for (int j = 0; j < n; ++j) {
+            P[j] *= static_cast<u64>(n);
+            if (P[j] < Asum) stk[ns++] = static_cast<uint16_t>(j);
+            else { stk[n - 1 - nl] = static_cast<uint16_t>(j); ++nl; }
+        }
+        while (ns > 0 && nl > 0) {
+            const int s = stk[--ns];
+            --nl;
+            const int l = stk[n - 1 - nl];
+            a.athr[out + s] = static_cast<uint32_t>((static_cast<unsigned __int128>(P[s]) << 32) / Asum);
+            a.atopic[out + s] = a.topic[out + l];
+            P[l] -= Asum - P[s];
+            if (P[l] < Asum) stk[ns++] = static_cast<uint16_t>(l);
+            else { stk[n - 1 - nl] = static_cast<uint16_t>(l); ++nl; }
+        }
+    }
+}
+
+// ============================================================== z-step
+// One warp per document (dynamically scheduled, longest first).  m_d lives
+// in shared memory as a dense count array; for K <= 1024 each lane also holds
+// the 32-topic bitmap word of m_d's nonzero topics it owns.  Tokens are
+// visited in position order: remove token i (m^{-i}), compute
+// sigma_b = sum_k q_{k,v} m_k over the smaller of {k : m_k > 0} and
+// {k : phi_{k,v} > 0} (complexity theorem), draw r = floor(u (A + 2^16 B)),
+// take the alias draw if r < A, else the first topic where the running sum
+// of q m passes (r - A) / 2^16; add the token back.
+__global__ void k_z_step(ZArgs a) {
+    extern __shared__ uint32_t zsm[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int K = a.K;
+    uint32_t *m = zsm + static_cast<size_t>(warp) * K;
+    const bool use_bm = a.bitmap != nullptr && a.path != 1;
+    u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.work, 1);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item >= a.D) break;
+        const int d = a.doc_order[item];
+        const int64_t s = a.doc_off[d], e = a.doc_off[d + 1];
+        if (e == s) continue;
+        for (int k = lane; k < K; k += 32) m[k] = 0;
+        __syncwarp();
+        for (int64_t i = s + lane; i < e; i += 32) atomicAdd(&m[a.z[i]], 1u);
+        __syncwarp();
+        uint32_t mbits = 0;
+        int kd = 0;
+        if (use_bm) {
+            for (int g = 0; g < a.KW; ++g) {
+                const int k = g * 32 + lane;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k < K && m[k] > 0);
+                if (lane == g) mbits = bal;
+                kd += __popc(bal);
+            }
+        } else {
+            int cnt = 0;
+            for (int k = lane; k < K; k += 32) cnt += m[k] > 0;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+            kd = cnt;
+        }
+        for (int64_t i0 = s; i0 < e; i0 += 32) {
+            const int64_t i = i0 + lane;
+            const bool valid = i < e;
+            int wv = 0, zo = 0, nw = 0, ta = 0;
+            int64_t cb = 0;
+            u64 Av = 0;
+            U4 x{0, 0, 0, 0};
+            if (valid) {
+                wv = a.w[i];
+                zo = a.z[i];
+                const uint64_t t = static_cast<uint64_t>(a.index_base + i);
+                x = draw(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), a.sweep, TAG_Z, 0);
+                cb = a.col_ptr[wv];
+                nw = static_cast<int>(a.col_ptr[wv + 1] - cb);
+                Av = a.A[wv];
+                if (nw > 0) {
+                    const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
+                    ta = x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl];
+                }
+            }
+            int znew = zo;
+            const int cnt = static_cast<int>(min(static_cast<int64_t>(32), e - i0));
+            for (int tt = 0; tt < cnt; ++tt) {
+                const int v = __shfl_sync(0xFFFFFFFFu, wv, tt);
+                const int kold = __shfl_sync(0xFFFFFFFFu, zo, tt);
+                const int64_t col = __shfl_sync(0xFFFFFFFFu, cb, tt);
+                const int n_w = __shfl_sync(0xFFFFFFFFu, nw, tt);
+                const u64 At = __shfl_sync(0xFFFFFFFFu, Av, tt);
+                const u64 U = (static_cast<u64>(__shfl_sync(0xFFFFFFFFu, x.x, tt)) << 32) |
+                              __shfl_sync(0xFFFFFFFFu, x.y, tt);
+                const int ka = __shfl_sync(0xFFFFFFFFu, ta, tt);
+                // remove token i: m^{-i}
+                const uint32_t old = m[kold];
+                __syncwarp();
+                if (lane == 0) m[kold] = old - 1;
+                if (old == 1) {
+                    --kd;
+                    if (use_bm && lane == (kold >> 5)) mbits &= ~(1u << (kold & 31));
+                }
+                __syncwarp();
+                st_min += static_cast<u64>(kd < n_w ? kd : n_w);
+                const bool docside = use_bm && (a.path == 2 || kd < n_w);
+                uint32_t phib = 0, rank = 0, inter = 0;
+                u64 acc = 0;
+                if (docside) {
+                    phib = lane < a.KW ? a.bitmap[static_cast<int64_t>(v) * a.KW + lane] : 0u;
+                    rank = warp_excl_scan32(__popc(phib));
+                    inter = phib & mbits;
+                    for (uint32_t bb = inter; bb; bb &= bb - 1) {
+                        const int b = __ffs(bb) - 1;
+                        const int64_t idx = col + rank + __popc(phib & ((1u << b) - 1u));
+                        acc += static_cast<u64>(a.q[idx]) * m[lane * 32 + b];
+                    }
+                } else {
+                    for (int j = lane; j < n_w; j += 32) acc += static_cast<u64>(a.q[col + j]) * m[a.topic[col + j]];
+                }
+                const u64 B = warp_sum64(acc);
+                const u64 T = At + (B << kFracBits);
+                int knew = kold;
+                if (T == 0) {
+                    ++st_zero;
+                } else {
+                    const u64 r = __umul64hi(U, T);
+                    if (r < At) {
+                        knew = ka;
+                        ++st_ab;
+                    } else {
+                        const u64 rb = (r - At) >> kFracBits;
+                        int found = -1;
+                        if (docside) {
+                            const u64 incl = warp_incl_scan64(acc);
+                            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, rb < incl);
+                            if (bal) {
+                                const int L = __ffs(bal) - 1;
+                                int f = -1;
+                                if (lane == L) {
+                                    u64 run = incl - acc;
+                                    for (uint32_t bb = inter; bb; bb &= bb - 1) {
+                                        const int b = __ffs(bb) - 1;
+                                        const int64_t idx = col + rank + __popc(phib & ((1u << b) - 1u));
+                                        run += static_cast<u64>(a.q[idx]) * m[lane * 32 + b];
+                                        if (rb < run) { f = lane * 32 + b; break; }
+                                    }
+                                }
+                                found = __shfl_sync(0xFFFFFFFFu, f, L);
+                            }
+                        } else {
+                            u64 carry = 0;
+                            for (int j0 = 0; j0 < n_w; j0 += 32) {
+                                const int j = j0 + lane;
+                                u64 b = 0;
+                                int k = 0;
+                                if (j < n_w) { k = a.topic[col + j]; b = static_cast<u64>(a.q[col + j]) * m[k]; }
+                                const u64 incl = warp_incl_scan64(b);
+                                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, j < n_w && rb < carry + incl);
+                                if (bal) { found = __shfl_sync(0xFFFFFFFFu, k, __ffs(bal) - 1); break; }
+                                carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+                            }
+                        }
+                        if (found < 0) {
+                            if (lane == 0) atomicOr(&a.stats[ST_ERROR], ERR_INTERNAL);
+                        } else {
+                            knew = found;
+                        }
+                    }
+                }
+                // add token i back with its new topic
+                const uint32_t old2 = m[knew];
+                __syncwarp();
+                if (lane == 0) m[knew] = old2 + 1;
+                if (old2 == 0) {
+                    ++kd;
+                    if (use_bm && lane == (knew >> 5)) mbits |= 1u << (knew & 31);
+                }
+                __syncwarp();
+                if (lane == tt) znew = knew;
+            }
+            if (valid) a.z[i] = static_cast<int16_t>(znew);
+            st_tok += static_cast<u64>(cnt);
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&a.stats[ST_TOKENS], st_tok);
+        atomicAdd(&a.stats[ST_ABRANCH], st_ab);
+        atomicAdd(&a.stats[ST_SUMMIN], st_min);
+        atomicAdd(&a.stats[ST_ZEROMASS], st_zero);
+        atomicAdd(&a.stats[ST_COUNT + ST_TOKENS], st_tok);
+        atomicAdd(&a.stats[ST_COUNT + ST_ABRANCH], st_ab);
+        atomicAdd(&a.stats[ST_COUNT + ST_SUMMIN], st_min);
+        atomicAdd(&a.stats[ST_COUNT + ST_ZEROMASS], st_zero);
+    }
+}
+
+// ============================================================== exports
+// m_{d,k}, dense row-major [D, K]: one warp per document.
+__global__ void k_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K, int32_t *m_dk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t d = gw; d < D; d += nw) {
+        int32_t *row = m_dk + d * K;
+        for (int64_t i = doc_off[d] + lane; i < doc_off[d + 1]; i += 32) atomicAdd(&row[z[i]], 1);
+    }
+}
+
+// n_{k,v}, dense row-major [K, V], from the compacted n columns.
+__global__ void k_n_dense(PhiArgs a, int32_t *n_kv) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) {
+        const int64_t b = a.word_off[v];
+        for (int j = 0; j < a.nnz_n[v]; ++j) n_kv[static_cast<int64_t>(a.nst_k[b + j]) * a.V + v] = static_cast<int32_t>(a.nst_n[b + j]);
+    }
+}
+
+// phi_{k,v} = fp32(c_{k,v} / S_k) for every stored entry.
+__global__ void k_phi_values(PhiArgs a, float *phi) {
+    const int64_t nnz = a.col_ptr[a.V];
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        phi[e] = static_cast<float>(__ddiv_rn(static_cast<double>(a.c[e]), static_cast<double>(a.S[a.topic[e]])));
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace
+
+// ============================================================ launchers
+void launch_init_z(int64_t N, int K, uint64_t seed, int64_t index_base, int16_t *z, cudaStream_t st) {
+    if (N <= 0) return;
+    const int grid = static_cast<int>(std::min<int64_t>((N + 255) / 256, 8LL * sm_count() * 8));
+    k_init_z<<<grid, 256, 0, st>>>(N, K, seed, index_base, z);
+}
+
+void launch_word_perm(int64_t N, int V, const int32_t *w, int64_t *word_off, int32_t *fill, int32_t *perm,
+                      cudaStream_t st) {
+    cudaMemsetAsync(fill, 0, sizeof(int32_t) * V, st);
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 8LL * sm_count() * 8)));
+    if (N > 0) k_word_hist<<<grid, 256, 0, st>>>(N, w, fill);
+    k_scan_single<int32_t><<<1, 1024, 0, st>>>(fill, V, word_off, nullptr);
+    cudaMemsetAsync(fill, 0, sizeof(int32_t) * V, st);
+    if (N > 0) k_word_scatter<<<grid, 256, 0, st>>>(N, w, word_off, fill, perm);
+}
+
+size_t phi_counts_smem(int K) { return sizeof(uint32_t) * 2 * static_cast<size_t>(K); }
+
+// The dynamic shared-memory opt-in is a per-kernel attribute shared by every
+// handle in the process, so it is set once to the device maximum.
+int smem_optin() {
+    static int v = 0;
+    if (!v) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (v <= 0) v = 48 * 1024;
+    }
+    return v;
+}
+
+// Opt a kernel in to the largest dynamic shared memory it can use next to
+// its static shared memory.
+template <typename F>
+void allow_dynamic_smem(F *kernel) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+    const int room = smem_optin() - static_cast<int>(fa.sharedSizeBytes);
+    if (room > 0) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
+}
+
+int phi_counts_blocks_per_sm(int K) {
+    const size_t smem = phi_counts_smem(K);
+    allow_dynamic_smem(k_phi_counts);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_phi_counts, kPhiBlock, smem);
+    return b > 0 ? b : 1;
+}
+
+void launch_phi_counts(const PhiArgs &a, bool draw, int grid, cudaStream_t st) {
+    const size_t smem = phi_counts_smem(a.K);
+    k_phi_counts<<<grid, kPhiBlock, smem, st>>>(a, draw);
+}
+
+void launch_phi_fixup(const PhiArgs &a, cudaStream_t st) { k_phi_fixup<<<1, kFixBlock, 0, st>>>(a); }
+
+void launch_colptr_scan(const PhiArgs &a, cudaStream_t st) {
+    k_scan_single<int32_t><<<1, 1024, 0, st>>>(a.nnz_c, a.V, a.col_ptr, &a.stats[ST_NNZPHI]);
+}
+
+void launch_phi_tables(const PhiArgs &a, cudaStream_t st) {
+    const int grid = (a.V + 127) / 128;
+    k_phi_tables<<<grid, 128, 0, st>>>(a);
+}
+
+size_t z_step_smem(int K, int warps_per_block) { return sizeof(uint32_t) * static_cast<size_t>(K) * warps_per_block; }
+
+int z_step_blocks_per_sm(int K, int warps_per_block) {
+    const size_t smem = z_step_smem(K, warps_per_block);
+    allow_dynamic_smem(k_z_step);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_z_step, 32 * warps_per_block, smem);
+    return b > 0 ? b : 1;
+}
+
+void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st) {
+    k_z_step<<<grid, 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(a);
+}
+
+void launch_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K, int32_t *m_dk, cudaStream_t st) {
+    if (D <= 0) return;
+    cudaMemsetAsync(m_dk, 0, sizeof(int32_t) * static_cast<size_t>(D) * K, st);
+    const int grid = static_cast<int>(std::min<int64_t>((D * 32 + 255) / 256, 8LL * sm_count() * 8));
+    k_doc_topic<<<grid, 256, 0, st>>>(doc_off, D, z, K, m_dk);
+}
+
+void launch_n_dense(const PhiArgs &a, int32_t *n_kv, cudaStream_t st) {
+    cudaMemsetAsync(n_kv, 0, sizeof(int32_t) * static_cast<size_t>(a.K) * a.V, st);
+    k_n_dense<<<(a.V + 255) / 256, 256, 0, st>>>(a, n_kv);
+}
+
+void launch_phi_values(const PhiArgs &a, float *phi, cudaStream_t st) {
+    k_phi_values<<<4 * sm_count(), 256, 0, st>>>(a, phi);
+}
+
+}  // namespace pulda

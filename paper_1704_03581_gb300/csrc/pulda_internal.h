@@ -1,0 +1,128 @@
+// Internal declarations of the pulda CUDA library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace pulda {
+
+// Alias tables are built for Poisson rates beta + l with l <= kL; larger
+// counts use a rounded Gaussian ("Efficient sampling of Phi", L = 100).
+constexpr int kL = 100;
+// Length of the geometric-gap CDF table used to skip over entries whose
+// Poisson rate is beta alone.
+constexpr int kGeoLen = 1024;
+// Equiprobable cells of the inverse-normal table.
+constexpr int kGaussCells = 65536;
+// The alpha part of the z conditional is held in units of 2^-16 q.
+constexpr int kFracBits = 16;
+// Dead-row redraw attempts before giving up.
+constexpr uint32_t kMaxRedraw = 1u << 20;
+// Largest K the kernels' shared-memory layouts accept.
+constexpr int kMaxK = 16384;
+// The bitmap intersection path of the z-step holds one 32-topic word per lane.
+constexpr int kMaxKBitmap = 1024;
+
+// Philox stream tags (counter word 3 = tag << 28 | aux).
+enum : uint32_t { TAG_INIT = 1, TAG_POIS = 2, TAG_BETA = 3, TAG_REDRAW_POIS = 4, TAG_REDRAW_BETA = 5, TAG_Z = 6 };
+
+// Slots of the per-sweep counter block on the device.
+enum : int { ST_TOKENS = 0, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_DEADROWS, ST_NNZPHI, ST_ERROR, ST_COUNT = 8 };
+// Running totals of the first four slots live at ST_COUNT + slot and are
+// cleared only at pulda_init.
+constexpr int ST_TOTAL_SLOTS = 2 * ST_COUNT;
+enum : unsigned long long { ERR_DEGENERATE = 1, ERR_INTERNAL = 2 };
+
+// Fixed tables of one beta, built on the host once.
+struct HostTables {
+    std::vector<uint32_t> thr;     // alias thresholds of every table, concatenated
+    std::vector<uint16_t> alias;   // alias outcome, as an offset from the table's lo
+    std::vector<int32_t> off;      // [kL+1] start of table t (t = 0: zero-truncated Pois(beta); t = l: Pois(beta+l))
+    std::vector<int32_t> lo;       // [kL+1] smallest value of table t
+    std::vector<int32_t> n;        // [kL+1] support size of table t
+    std::vector<uint32_t> geo;     // [kGeoLen] P(gap <= g) * 2^32
+    std::vector<double> gauss;     // [kGaussCells+1] inverse-normal nodes
+};
+int build_host_tables(float beta, HostTables *out);
+
+// Device view of the same tables.
+struct DevTables {
+    const uint32_t *thr;
+    const uint16_t *alias;
+    const int32_t *off;
+    const int32_t *lo;
+    const int32_t *n;
+    const uint32_t *geo;
+    const double *gauss;
+    double beta;
+};
+
+// Everything the Phi-step kernels read and write.
+struct PhiArgs {
+    int K, V;
+    uint64_t seed;
+    uint32_t sweep;
+    const int32_t *perm;        // [N] token ids grouped by word
+    const int64_t *word_off;    // [V+1]
+    const int32_t *word_order;  // [V] words by decreasing token count
+    const int16_t *z;           // [N]
+    DevTables tab;
+    // staging: n columns at word_off, c columns at v*K (capacity K each)
+    uint16_t *nst_k; uint32_t *nst_n; int32_t *nnz_n;
+    uint16_t *cst_k; uint32_t *cst_c; int32_t *nnz_c;
+    unsigned long long *S;      // [K] row sums S_k
+    uint32_t *rowbuf;           // [V] scratch of the dead-row redraw
+    int64_t *col_ptr;           // [V+1]
+    // final per-word tables, at col_ptr
+    uint16_t *topic; uint32_t *c; uint32_t *q; uint32_t *athr; uint16_t *atopic;
+    unsigned long long *A;      // [V]
+    unsigned long long *vose_p; // [cap] scratch
+    uint16_t *vose_stack;       // [cap] scratch
+    uint32_t *bitmap;           // [V * KW] or null
+    int KW;
+    const float *alpha;         // [K]
+    int *work;                  // dynamic word counter
+    unsigned long long *stats;  // [ST_COUNT]
+};
+
+struct ZArgs {
+    const int64_t *doc_off;     // [D+1]
+    const int32_t *doc_order;   // [D] documents by decreasing length
+    int64_t D;
+    const int32_t *w;           // [N]
+    int16_t *z;                 // [N]
+    const int64_t *col_ptr;
+    const uint16_t *topic;
+    const uint32_t *q;
+    const unsigned long long *A;
+    const uint32_t *athr;
+    const uint16_t *atopic;
+    const uint32_t *bitmap;     // null when K > kMaxKBitmap
+    int K, KW;
+    uint64_t seed;
+    uint32_t sweep;
+    int64_t index_base;         // RNG index of token 0
+    int path;                   // 0 auto, 1 column, 2 document topics
+    int *work;
+    unsigned long long *stats;
+};
+
+// Launchers (kernels.cu).  All are asynchronous on `st`.
+void launch_init_z(int64_t N, int K, uint64_t seed, int64_t index_base, int16_t *z, cudaStream_t st);
+void launch_word_perm(int64_t N, int V, const int32_t *w, int64_t *word_off, int32_t *fill, int32_t *perm,
+                      cudaStream_t st);
+void launch_phi_counts(const PhiArgs &a, bool draw, int grid, cudaStream_t st);
+void launch_phi_fixup(const PhiArgs &a, cudaStream_t st);
+void launch_colptr_scan(const PhiArgs &a, cudaStream_t st);
+void launch_phi_tables(const PhiArgs &a, cudaStream_t st);
+void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st);
+size_t z_step_smem(int K, int warps_per_block);
+size_t phi_counts_smem(int K);
+void launch_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K, int32_t *m_dk, cudaStream_t st);
+void launch_n_dense(const PhiArgs &a, int32_t *n_kv, cudaStream_t st);
+void launch_phi_values(const PhiArgs &a, float *phi, cudaStream_t st);
+int z_step_blocks_per_sm(int K, int warps_per_block);
+int phi_counts_blocks_per_sm(int K);
+
+}  // namespace pulda

@@ -16,6 +16,8 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
+import tempfile
 
 import numpy as np
 
@@ -147,10 +149,36 @@ def small(seed: int = 2) -> Corpus:
     return zipf_corpus(seed, 100, 12375, 1500, 1290.0, 0.5, 1.0, "small D=1500 V=12375 K=100")
 
 
+GENERATOR_VERSION = 1
+
+
+def _cached(key: str, make) -> Corpus:
+    """Drawing the large corpus takes about a minute; keep one copy per
+    machine (``PULDA_SYNTH_CACHE``, default /tmp/pulda_synth_cache)."""
+    d = os.environ.get("PULDA_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "pulda_synth_cache"))
+    path = os.path.join(d, f"{key}_v{GENERATOR_VERSION}.npz")
+    if os.path.exists(path):
+        try:
+            with np.load(path) as f:
+                return Corpus(f["w"], f["doc_off"], int(f["V"]), str(f["name"]))
+        except Exception:
+            pass
+    c = make()
+    try:
+        os.makedirs(d, exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp.npz"
+        np.savez(tmp, w=c.w, doc_off=c.doc_off, V=c.V, name=c.name)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return c
+
+
 def large(seed: int = 3, D: int = 300_000) -> Corpus:
     """D=300,000, V=100,000, lengths lognormal(mean 330, log-sd 0.8),
     Zipf(1.05), generated with K=1,000 topics (~99M tokens)."""
-    return zipf_corpus(seed, 1000, 100_000, D, 330.0, 0.8, 1.05, f"large D={D} V=100000 K=1000")
+    return _cached(f"large_s{seed}_D{D}", lambda: zipf_corpus(seed, 1000, 100_000, D, 330.0, 0.8, 1.05,
+                                                              f"large D={D} V=100000 K=1000"))
 
 
 def batched_specs(n_chains: int = 32, seed: int = 4) -> list[dict]:

@@ -1,0 +1,56 @@
+"""The C-ABI library builds, loads without a GPU, and exports every entry
+point that include/pulda.h declares; the Python binding names the same calls."""
+import ctypes
+import os
+import re
+
+import paper_1704_03581_gb300 as P
+from paper_1704_03581_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "pulda.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pulda_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    names = declared_symbols()
+    assert sorted(P.EXPORTED) == names
+    for n in names:
+        assert callable(getattr(P, n)), n
+
+
+def test_init_rejects_bad_arguments_without_a_gpu():
+    """Validation happens before any device work, so it is testable on CPU."""
+    import numpy as np
+    w = np.array([0, 1, 2], np.int32)
+    off = np.array([0, 3], np.int64)
+    for kwargs, frag in [(dict(K=0), "K must be"), (dict(K=20000), "K must be"), (dict(V=2), "outside"),
+                         (dict(alpha=-1.0), "alpha"), (dict(beta=0.0), "beta")]:
+        args = dict(K=4, V=3, alpha=0.1, beta=0.01)
+        args.update(kwargs)
+        try:
+            P.pulda_init(w, off, args["K"], args["V"], args["alpha"], args["beta"], 0)
+        except P.PuldaError as e:
+            assert e.status == -1 and frag in str(e), str(e)
+        else:
+            raise AssertionError("accepted " + repr(kwargs))
+    bad_off = np.array([0, 2, 1, 3], np.int64)
+    try:
+        P.pulda_init(w, bad_off, 4, 3, 0.1, 0.01, 0)
+    except P.PuldaError as e:
+        assert "decrease" in str(e)
+    else:
+        raise AssertionError("accepted decreasing offsets")

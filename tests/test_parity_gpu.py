@@ -1,0 +1,163 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1704_03581_gb300 import synth
+from parity_util import compare_tables, first_mismatch, lockstep
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03581_gb300 import build
+    build.build()
+
+
+def corpus_from_lengths(rng, lengths, V, zipf=1.0):
+    off = np.zeros(len(lengths) + 1, np.int64)
+    np.cumsum(lengths, out=off[1:])
+    p = (1.0 + np.arange(V)) ** -zipf
+    w = rng.choice(V, size=int(off[-1]), p=p / p.sum()).astype(np.int32)
+    return w, off
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+def test_tiny_corpus_lockstep(path):
+    """K=20, V=1,000, D=1,000, ~100k tokens from the LDA generative process."""
+    c = synth.tiny()
+    s, ch = lockstep(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=0, sweeps=6, path=path, check_counts_every=3)
+    s.close()
+
+
+def test_small_corpus_lockstep():
+    """Small-corpus shape: D=1,500, V=12,375, ~1.9M tokens, K=100."""
+    c = synth.small()
+    s, ch = lockstep(c.w, c.doc_off, 100, c.V, 0.1, 0.01, seed=1, sweeps=3)
+    s.close()
+
+
+@pytest.mark.parametrize("K", [1, 31, 33, 1000, 1024, 1025, 3000])
+def test_topic_counts_around_tile_edges(K):
+    """K around the 32-topic word of the bitmap path and its 1024 limit."""
+    rng = np.random.default_rng(K)
+    lengths = rng.integers(0, 90, size=120)
+    lengths[3] = 0
+    lengths[5] = 1
+    lengths[7] = 33
+    w, off = corpus_from_lengths(rng, lengths, 700)
+    s, _ = lockstep(w, off, K, 700, rng.uniform(0.05, 0.5, K).astype(np.float32), 0.02, seed=K, sweeps=3,
+                    check_counts_every=3)
+    s.close()
+
+
+def test_ragged_and_degenerate_inputs():
+    """Empty documents, unused words (empty Phi columns keep their tokens'
+    topics), a long document spanning many 32-token batches, and tiny V with
+    small beta so whole Phi rows die and are redrawn."""
+    rng = np.random.default_rng(5)
+    lengths = np.array([0, 1, 2, 0, 31, 32, 33, 1000, 0, 7])
+    w, off = corpus_from_lengths(rng, lengths, 3, zipf=0.5)
+    s, ch = lockstep(w, off, 12, 6, 0.3, 0.001, seed=9, sweeps=8, check_counts_every=2)
+    s.close()
+
+
+def test_dead_rows_are_redrawn_like_the_oracle():
+    rng = np.random.default_rng(6)
+    w, off = corpus_from_lengths(rng, np.array([3, 2, 4]), 4)
+    total_dead = 0
+    s, ch = lockstep(w, off, 9, 4, 0.5, 0.05, seed=3, sweeps=1)
+    for it in range(2, 12):
+        s.phi_step()
+        ch.sweep_index += 1
+        ch.phi_step(ch.sweep_index)
+        compare_tables(s.word_tables(), ch, f"sweep {it}")
+        total_dead += ch.dead_rows
+        assert s.stats()["dead_rows"] == ch.dead_rows
+        s.z_step()
+        ch.z, ch.stats = O.z_step(ch.doc_off, ch.w, ch.z, ch.tables, ch.seed, ch.sweep_index)
+        assert not first_mismatch(s.z(), ch.z, off)
+    assert total_dead > 20          # the redraw path was exercised
+    s.close()
+
+
+def test_phi_export_and_invariants():
+    c = synth.tiny()
+    s, ch = lockstep(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=4, sweeps=2)
+    col, top, phi = s.phi()
+    o = ch.tables
+    mask = np.arange(20)[None, :] < o.ncol[:, None]
+    assert np.array_equal(top, o.topic[mask]) and np.array_equal(phi.view(np.uint32), o.phi32[mask].view(np.uint32))
+    dense = np.zeros((20, c.V))
+    dense[top.astype(np.int64), np.repeat(np.arange(c.V), np.diff(col))] = phi
+    assert np.abs(dense.sum(axis=1) - 1).max() < 1e-6
+    m = s.m()
+    assert np.array_equal(m.sum(axis=1), np.diff(c.doc_off))
+    n = s.n()
+    assert n.sum() == c.N
+    s.close()
+
+
+def test_resume_from_checkpoint_is_exact():
+    c = synth.tiny()
+    import paper_1704_03581_gb300 as P
+    a = P.Sampler(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=8).sweep(4)
+    z4 = a.z()
+    a.sweep(3)
+    b = P.Sampler(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=8)
+    b.set_z(z4, 4)
+    b.sweep(3)
+    assert np.array_equal(a.z(), b.z())
+    a.close(); b.close()
+
+
+def test_fold_in_matches_oracle():
+    """pulda_infer: Algorithm 2's z-step with Phi held fixed, on new documents."""
+    c = synth.tiny()
+    s, ch = lockstep(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=2, sweeps=3)
+    new = c.slice_docs(0, 50)
+    zg, mg = s.infer(new.w, new.doc_off, 10, seed=77, want_m=True)
+    zo = O.infer(ch.tables, new.w, new.doc_off, 10, 77)
+    assert not first_mismatch(zg, zo, new.doc_off)
+    assert np.array_equal(mg, O.doc_topic(new.doc_off, zo, 20))
+    # the chain itself is untouched by a fold-in
+    assert np.array_equal(s.z(), ch.z)
+    s.close()
+
+
+def test_large_corpus_sampled_parity():
+    """The large workload (D=300,000, V=100,000, ~99M tokens, K=1,000) in the
+    launch configuration the benchmark times: one full sweep on the GPU; the
+    oracle recomputes the whole Phi-step and the z-step of 3,000 sampled
+    documents (documents are independent given Phi)."""
+    import paper_1704_03581_gb300 as P
+    c = synth.large()
+    K = 1000
+    s = P.Sampler(c.w, c.doc_off, K, c.V, 0.1, 0.01, seed=0)
+    z0 = s.z()
+    assert np.array_equal(z0, O.init_z(c.N, K, 0))
+    s.phi_step()
+    ctx = O.Ctx(0.01)
+    n = O.count_n(c.w, z0, K, c.V)
+    cc, S, dead = O.phi_draw(ctx, n, 0, 1)
+    del n
+    tab = O.WordTables(cc, S, np.full(K, 0.1, np.float32))
+
+    class _Ch:
+        pass
+    ch = _Ch()
+    ch.K, ch.V, ch.S, ch.c, ch.tables = K, c.V, S, cc, tab
+    compare_tables(s.word_tables(), ch, "large sweep 1")
+    s.z_step()
+    z1 = s.z()
+    rng = np.random.default_rng(0)
+    docs = np.sort(rng.choice(c.D, size=3000, replace=False))
+    for d in docs[:3000]:
+        a, b = int(c.doc_off[d]), int(c.doc_off[d + 1])
+        zo, _ = O.z_step(np.array([0, b - a], np.int64), c.w[a:b], z0[a:b], tab, 0, 1, index_base=a)
+        assert np.array_equal(z1[a:b], zo), f"document {d} differs"
+    s.close()
