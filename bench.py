@@ -47,8 +47,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["pulda", "reference"], default="pulda")
     ap.add_argument("--cpu-docs", type=int, default=20000, help="documents in the CPU oracle's bounded sample")
+    ap.add_argument("--ref-docs", type=int, default=5000,
+                    help="documents in each step of the reference (oracle) arm's bounded sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--docs", type=int, default=300_000,
+                    help="documents of the large corpus (300,000 = the full workload; fewer for profiling)")
     return ap.parse_args()
 
 
@@ -166,7 +170,7 @@ def run_reference(args, corpus):
     steps, warm = args.steps, args.warmup
     tot_tok, tot_t = 0, 0.0
     from oracle import oracle as O
-    sub = corpus.slice_docs(0, min(args.cpu_docs, corpus.D))
+    sub = corpus.slice_docs(0, min(args.ref_docs, corpus.D))
     ch = O.Chain(sub.w, sub.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=0)
     for _ in range(warm):
         ch.sweep(1)
@@ -311,7 +315,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        corpus = synth.large()
+        corpus = synth.large(D=args.docs)
         run_reference(args, corpus)
         return
     import torch
@@ -326,7 +330,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    corpus = synth.large()
+    corpus = synth.large(D=args.docs)
     run_pulda(args, corpus, rank, world)
     if world > 1:
         import torch.distributed as dist
