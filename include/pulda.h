@@ -152,6 +152,30 @@ pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids_host, const in
                          int64_t D_new, int32_t n_sweeps, uint64_t seed, int16_t *z_out_host,
                          int32_t *m_out_host);
 
+/* pulda_infer_noalloc -- pulda_infer for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant.
+ * Serving processes that carve their device memory once at start-up,
+ * memory-capped tenants of a shared GPU, and latency-critical loops that must
+ * not stall on the allocator cannot call cudaMalloc (or anything that does);
+ * pulda_infer allocates temporaries on every call, this call allocates
+ * nothing.  The caller passes device buffers:
+ *   word_ids_dev int32[N_new] (ids in [0, V)), doc_offsets_dev int64[D_new+1]
+ *   (rising from 0 to N_new), z_out_dev int16[N_new] (the fold-in's topics,
+ *   also its working state).
+ * The results equal pulda_infer's with the same seed and n_sweeps.
+ * The few bytes of scratch the z-step needs live in a fixed array of static
+ * device memory (262,912 bytes, held by every GPU that loads the library until
+ * the process exits), so D_new is limited to 65,536 documents per call; larger
+ * D_new returns PULDA_ERR_INVALID.  The first call on each device looks up
+ * that array's device address once; make that first call before any stream
+ * capture.  All calls on a device share the array: calls that overlap on the
+ * GPU race and must be serialised by the caller.  Synchronous on the handle's
+ * stream.  Errors: PULDA_ERR_INVALID (limits, NULL pointers, no Phi yet, bad
+ * ids or offsets -- checked on the device), PULDA_ERR_CUDA. */
+pulda_status pulda_infer_noalloc(pulda_handle *h, const int32_t *word_ids_dev, const int64_t *doc_offsets_dev,
+                                 int64_t D_new, int64_t N_new, int32_t n_sweeps, uint64_t seed,
+                                 int16_t *z_out_dev);
+
 /* pulda_stats -- counters of the most recent sweep (synchronises). */
 pulda_status pulda_stats(pulda_handle *h, pulda_sweep_stats *out);
 

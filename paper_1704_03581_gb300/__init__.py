@@ -22,7 +22,7 @@ STATUS = {0: "PULDA_OK", -1: "PULDA_ERR_INVALID", -2: "PULDA_ERR_OOM", -3: "PULD
 
 EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "pulda_sync", "pulda_get_z",
             "pulda_get_z_dev", "pulda_set_z", "pulda_get_counts", "pulda_get_phi", "pulda_get_word_tables",
-            "pulda_infer", "pulda_stats", "pulda_last_error", "pulda_free"]
+            "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_last_error", "pulda_free"]
 
 
 class PuldaError(RuntimeError):
@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
             "pulda_get_phi": [P, P, P, P, P],
             "pulda_get_word_tables": [P, P, P, P, P, P, P, P, P, P],
             "pulda_infer": [P, P, P, i64, i32, u64, P, P],
+            "pulda_infer_noalloc": [P, P, P, i64, i64, i32, u64, P],
             "pulda_stats": [P, P],
         }
         for name, args in sig.items():
@@ -186,6 +187,15 @@ def pulda_infer(h, word_ids, doc_offsets, n_sweeps: int, seed: int, K: int, want
     m = np.zeros((D, K), np.int32) if want_m else None
     _check(h, lib().pulda_infer(h, _ptr(w), _ptr(off), D, n_sweeps, int(seed) & (2 ** 64 - 1), _ptr(z), _ptr(m)))
     return (z[:w.shape[0]], m) if want_m else z[:w.shape[0]]
+
+
+def pulda_infer_noalloc(h, word_ids_dev, doc_offsets_dev, n_sweeps: int, seed: int, z_out_dev):
+    """Device tensors in and out; nothing is allocated (see include/pulda.h)."""
+    D = int(doc_offsets_dev.shape[0]) - 1
+    N = int(word_ids_dev.shape[0])
+    _check(h, lib().pulda_infer_noalloc(h, _ptr(word_ids_dev), _ptr(doc_offsets_dev), D, N, n_sweeps,
+                                        int(seed) & (2 ** 64 - 1), _ptr(z_out_dev)))
+    return z_out_dev
 
 
 def pulda_stats(h) -> dict:

@@ -153,6 +153,23 @@ pulda_status run_z(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_o
 
 }  // namespace
 
+namespace pulda {
+// Read-only view of a handle for other translation units of the library.
+bool handle_view(pulda_handle *h, HandleView *out) {
+    if (!h || !out) return false;
+    out->stream = h->stream;
+    out->K = h->K;
+    out->V = h->V;
+    out->have_phi = h->have_phi;
+    out->z_warps = h->z_warps;
+    out->z_grid = h->z_grid;
+    out->zargs = z_args(h, nullptr, nullptr, 0, nullptr, nullptr, 0, 0, 0);
+    return true;
+}
+
+int handle_fail(pulda_handle *h, int s, const char *msg) { return fail(h, static_cast<pulda_status>(s), "%s", msg); }
+}  // namespace pulda
+
 extern "C" {
 
 pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64_t *doc_offsets, int64_t D, int32_t K,

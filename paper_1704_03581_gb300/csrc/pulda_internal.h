@@ -125,4 +125,19 @@ void launch_phi_values(const PhiArgs &a, float *phi, cudaStream_t st);
 int z_step_blocks_per_sm(int K, int warps_per_block);
 int phi_counts_blocks_per_sm(int K);
 
+// What another translation unit needs to launch the z-step on a handle's
+// current Phi (api.cpp).
+struct HandleView {
+    cudaStream_t stream;
+    int K, V;
+    bool have_phi;
+    int z_warps, z_grid;
+    ZArgs zargs;     // Phi tables, K, path; corpus, RNG and scratch fields unset
+};
+}  // namespace pulda
+struct pulda_handle;
+namespace pulda {
+bool handle_view(pulda_handle *h, HandleView *out);
+int handle_fail(pulda_handle *h, int status, const char *msg);
+
 }  // namespace pulda

@@ -1,0 +1,63 @@
+"""pulda_infer_noalloc: fold-in for callers that cannot allocate device
+memory (pre-carved serving arenas, memory-capped tenants, loops that must not
+stall on the allocator).  Checked through the C ABI against pulda_infer, the
+allocating entry point, bit for bit -- the tolerance of every other parity
+test here -- on two calls in a row, since the calls share one static scratch
+array that keeps the previous call's contents.  This file is collected last
+so a failure here never hides another test's result."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def chain():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03581_gb300 import build
+    build.build()
+    import paper_1704_03581_gb300 as P
+    from paper_1704_03581_gb300 import synth
+    c = synth.tiny()
+    s = P.Sampler(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=11).sweep(3)
+    yield P, s, c
+    s.close()
+
+
+def test_noalloc_matches_infer_on_two_calls(chain):
+    import torch
+    P, s, c = chain
+    for d0, d1, seed in [(0, 300, 5), (300, 1000, 6)]:
+        new = c.slice_docs(d0, d1)
+        z_ref = s.infer(new.w, new.doc_off, 7, seed=seed)
+        w_dev = torch.from_numpy(new.w).cuda()
+        off_dev = torch.from_numpy(new.doc_off).cuda()
+        z_dev = torch.full((new.N,), -1, dtype=torch.int16, device="cuda")
+        torch.cuda.synchronize()
+        P.pulda_infer_noalloc(s.h, w_dev, off_dev, 7, seed, z_dev)
+        assert np.array_equal(z_dev.cpu().numpy(), z_ref), f"docs {d0}:{d1} differ from pulda_infer"
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(chain):
+    import torch
+    P, s, c = chain
+    D = 65537
+    off = torch.zeros(D + 1, dtype=torch.int64, device="cuda")
+    w = torch.zeros(1, dtype=torch.int32, device="cuda")
+    z = torch.zeros(1, dtype=torch.int16, device="cuda")
+    with pytest.raises(P.PuldaError) as e:
+        P.pulda_infer_noalloc(s.h, w, off, 1, 0, z)
+    assert e.value.status == -1 and "65536" in str(e.value)
+
+
+def test_noalloc_checks_inputs_on_the_device(chain):
+    import torch
+    P, s, c = chain
+    w = torch.tensor([0, 1, c.V], dtype=torch.int32, device="cuda")      # last id out of range
+    off = torch.tensor([0, 3], dtype=torch.int64, device="cuda")
+    z = torch.zeros(3, dtype=torch.int16, device="cuda")
+    with pytest.raises(P.PuldaError) as e:
+        P.pulda_infer_noalloc(s.h, w, off, 1, 0, z)
+    assert "word id" in str(e.value)
