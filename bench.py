@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--burnin", type=int, default=25,
+                    help="untimed sweeps before the warm-up: the default times sweeps 31-50 of the "
+                         "50-sweep large workload rather than the first sweeps after a uniform start")
     ap.add_argument("--impl", choices=["pulda", "reference"], default="pulda")
     ap.add_argument("--cpu-docs", type=int, default=20000, help="documents in the CPU oracle's bounded sample")
     ap.add_argument("--ref-docs", type=int, default=5000,
@@ -204,10 +207,10 @@ def run_pulda(args, corpus, rank: int, world: int):
     torch.cuda.set_stream(stream)
     s = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                   stream=stream.cuda_stream)
-    for _ in range(args.warmup):
-        s.sweep(1)
+    s.sweep(args.burnin + args.warmup)
     s.sync()
     st0 = s.stats()
+    first_timed = st0["sweep"] + 1
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -251,7 +254,7 @@ def run_pulda(args, corpus, rank: int, world: int):
         s2 = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                        stream=stream.cuda_stream)
         s2.sweep(K)
-        zh = s2.z()
+        zh = s2.z()   # e2e covers sweeps 1..K from the uniform start
         dt = time.perf_counter() - t0
         s2.close()
         h2d = corpus.w.nbytes + corpus.doc_off.nbytes + 4 * K_TOPICS
@@ -290,7 +293,8 @@ def run_pulda(args, corpus, rank: int, world: int):
         "data": "synthetic (LDA generative process, Zipf(1.05) vocabulary)",
         "config": {"workload": corpus.name, "D": corpus.D, "V": corpus.V, "N": corpus.N, "K": K_TOPICS,
                    "alpha": ALPHA, "beta": BETA, "parallelism": f"{world} independent chains (replicas)",
-                   "l2": "inputs larger than L2 (word ids 396 MB + topics 198 MB read every sweep)"},
+                   "l2": "inputs larger than L2 (word ids 396 MB + topics 198 MB read every sweep)",
+                   "timed_sweeps": [first_timed, first_timed + K - 1]},
         "z_step": {"tokens_per_s": K * corpus.N / (z_ms / 1000.0), "ms_per_launch": z_ms / K,
                    "mean_min_kd_kv": sum_min / tokens, "a_branch_frac": a_br / tokens},
         "phi_step": {"ms_per_sweep": phi_ms / K, "nnz_phi": nnz_phi},

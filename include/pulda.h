@@ -90,7 +90,7 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids_host, const 
 
 /* pulda_sweep -- n_sweeps iterations of Algorithm 2: for each, rebuild n from
  * z (notation table), draw Phi ~ PPU(n_k + beta) row by row (Definition "Poisson
- * Polya Urn", Eq. 7, "Efficient sampling of Phi"), then resample every z_{i,d}
+ * Polya Urn", Eq. 9, "Efficient sampling of Phi"), then resample every z_{i,d}
  * proportional to phi_{k,v(i)}(alpha_k + m^{-i}_{d,k}) ("Efficient sampling of
  * z").  Asynchronous on the handle's stream; errors raised by kernels are
  * reported by the next pulda_sync.  Errors: PULDA_ERR_INVALID (n_sweeps < 0). */

@@ -35,7 +35,7 @@
  *          g from a 2^16-cell equiprobable inverse-normal table, linear in the
  *          cell.
  *   R-DEAD a row with S_k = 0 is redrawn whole, attempt a = 1, 2, ..., until
- *          S_k > 0 (zero-truncation of the hierarchical representation, Eq. 6).
+ *          S_k > 0 (zero-truncation of the hierarchical representation, Eq. 8).
  *   R-FIX  the z conditional is evaluated in exact integer arithmetic:
  *          phi is quantised per word to 24 bits relative to the column max
  *          (q >= 1 for every nonzero), alpha terms to 2^-16 units; all sums
@@ -347,7 +347,7 @@ void or_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int32_t K
 }
 
 /* ------------------------------------------------------------------------ */
-/* Phi-step: c_{k,v} ~ Pois(beta + n_{k,v}) for every entry (Eq. 7),        */
+/* Phi-step: c_{k,v} ~ Pois(beta + n_{k,v}) for every entry (Eq. 9),        */
 /* S_k = sum_v c_{k,v}; rows with S_k = 0 are redrawn (R-DEAD).              */
 /* ------------------------------------------------------------------------ */
 

@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libpulda.so")
+# PULDA_LIB selects another build of the same library (e.g. one compiled
+# with different tile constants); by default the in-tree build is used.
+LIB_PATH = os.environ.get("PULDA_LIB") or os.path.join(_PKG, "_build", "libpulda.so")
 
 PULDA_OK = 0
 STATUS = {0: "PULDA_OK", -1: "PULDA_ERR_INVALID", -2: "PULDA_ERR_OOM", -3: "PULDA_ERR_CUDA",

@@ -39,7 +39,7 @@ struct pulda_handle {
     uint16_t *cst_k = nullptr; uint32_t *cst_c = nullptr; int32_t *nnz_c = nullptr;
     unsigned long long *S = nullptr; uint32_t *rowbuf = nullptr; int64_t *col_ptr = nullptr;
     uint16_t *topic = nullptr; uint32_t *c = nullptr, *q = nullptr, *athr = nullptr; uint16_t *atopic = nullptr;
-    unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint32_t *bitmap = nullptr;
+    unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint2 *bitmap = nullptr;
     int *work = nullptr;
     unsigned long long *stats = nullptr;
     int64_t cap = 0;   // capacity of the per-word tables: K * V entries

@@ -3,7 +3,7 @@
 // One sweep = Algorithm 2 (Section 3):
 //   Phi-step  k_phi_counts   per word v: rebuild n_{.,v} from z (shared-memory
 //                            histogram over the word's tokens), draw
-//                            c_{k,v} ~ Pois(beta + n_{k,v}) for every k (Eq. 7,
+//                            c_{k,v} ~ Pois(beta + n_{k,v}) for every k (Eq. 9,
 //                            "Efficient sampling of Phi"), accumulate S_k.
 //             k_phi_fixup    rows with S_k = 0 are redrawn until nonzero
 //                            (Definition "Poisson Polya Urn").
@@ -285,7 +285,7 @@ constexpr int kFixBlock = 1024;
 
 // Rows whose Poisson counts summed to zero are redrawn whole (attempt
 // a = 1, 2, ...) until the sum is nonzero: the urn total is Pois+ (the
-// hierarchical representation, Eq. 6).  Accepted rows are inserted into the
+// hierarchical representation, Eq. 8).  Accepted rows are inserted into the
 // word columns.  Single block; almost always just checks S and exits.
 __global__ void __launch_bounds__(kFixBlock) k_phi_fixup(PhiArgs a) {
     __shared__ u64 red[kFixBlock / 32];
@@ -374,12 +374,13 @@ __global__ void k_phi_tables(PhiArgs a) {
         const int64_t src = static_cast<int64_t>(v) * a.K;
         const int64_t out = a.col_ptr[v];
         if (a.bitmap) {
-            uint32_t *bm = a.bitmap + static_cast<int64_t>(v) * a.KW;
+            uint2 *bm = a.bitmap + static_cast<int64_t>(v) * a.KW;
             int j = 0;
             for (int wi = 0; wi < a.KW; ++wi) {
+                const int before = j;
                 uint32_t bits = 0;
                 while (j < n && (a.cst_k[src + j] >> 5) == wi) { bits |= 1u << (a.cst_k[src + j] & 31); ++j; }
-                bm[wi] = bits;
+                bm[wi] = make_uint2(bits, static_cast<uint32_t>(before));
             }
         }
         if (n == 0) { a.A[v] = 0; continue; }
@@ -437,6 +438,16 @@ __global__ void k_phi_tables(PhiArgs a) {
 }
 
 // ============================================================== z-step
+// Entries of the document-side intersection each lane gathers with
+// independent loads before consuming them.
+#ifndef PULDA_ZGATHER
+#define PULDA_ZGATHER 8
+#endif
+#ifndef PULDA_ZMINBLOCKS
+#define PULDA_ZMINBLOCKS 3
+#endif
+constexpr int kGather = PULDA_ZGATHER;
+
 // One warp per document (dynamically scheduled, longest first).  m_d lives
 // in shared memory as a dense count array; for K <= 1024 each lane also holds
 // the 32-topic bitmap word of m_d's nonzero topics it owns.  Tokens are
@@ -445,7 +456,13 @@ __global__ void k_phi_tables(PhiArgs a) {
 // {k : phi_{k,v} > 0} (complexity theorem), draw r = floor(u (A + 2^16 B)),
 // take the alias draw if r < A, else the first topic where the running sum
 // of q m passes (r - A) / 2^16; add the token back.
-__global__ void k_z_step(ZArgs a) {
+//
+// Latency matters as much as throughput: a document's tokens are strictly
+// sequential, so the longest documents bound the kernel.  Everything that
+// depends only on the token (its word, Philox words, alias outcome, the
+// word's bitmap) is fetched ahead; the only loads on the critical path are
+// the q values of the intersection, issued together.
+__global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -503,6 +520,9 @@ __global__ void k_z_step(ZArgs a) {
             }
             int znew = zo;
             const int cnt = static_cast<int>(min(static_cast<int64_t>(32), e - i0));
+            uint2 bm_next = make_uint2(0u, 0u);
+            const int v_first = __shfl_sync(0xFFFFFFFFu, wv, 0);    // every lane takes part in the shuffle
+            if (use_bm && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(v_first) * a.KW + lane];
             for (int tt = 0; tt < cnt; ++tt) {
                 const int v = __shfl_sync(0xFFFFFFFFu, wv, tt);
                 const int kold = __shfl_sync(0xFFFFFFFFu, zo, tt);
@@ -512,6 +532,11 @@ __global__ void k_z_step(ZArgs a) {
                 const u64 U = (static_cast<u64>(__shfl_sync(0xFFFFFFFFu, x.x, tt)) << 32) |
                               __shfl_sync(0xFFFFFFFFu, x.y, tt);
                 const int ka = __shfl_sync(0xFFFFFFFFu, ta, tt);
+                const uint2 bm = bm_next;
+                if (use_bm) {     // fetch the next token's bitmap word while this one is drawn
+                    const int vn = __shfl_sync(0xFFFFFFFFu, wv, (tt + 1) & 31);
+                    if (tt + 1 < cnt && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(vn) * a.KW + lane];
+                }
                 // remove token i: m^{-i}
                 const uint32_t old = m[kold];
                 __syncwarp();
@@ -523,21 +548,42 @@ __global__ void k_z_step(ZArgs a) {
                 __syncwarp();
                 st_min += static_cast<u64>(kd < n_w ? kd : n_w);
                 const bool docside = use_bm && (a.path == 2 || kd < n_w);
-                uint32_t phib = 0, rank = 0, inter = 0;
+                // per-lane partial sums of q m, in ascending topic order across lanes
                 u64 acc = 0;
+                uint32_t qv[kGather];
+                int bp[kGather];
+                uint32_t rest = 0;         // docside: bits beyond the first kGather
+                int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
                 if (docside) {
-                    phib = lane < a.KW ? a.bitmap[static_cast<int64_t>(v) * a.KW + lane] : 0u;
-                    rank = warp_excl_scan32(__popc(phib));
-                    inter = phib & mbits;
-                    for (uint32_t bb = inter; bb; bb &= bb - 1) {
+                    uint32_t rem = bm.x & mbits;
+#pragma unroll
+                    for (int t = 0; t < kGather; ++t) {
+                        bp[t] = -1;
+                        qv[t] = 0;
+                        if (rem) {
+                            const int b = __ffs(rem) - 1;
+                            rem &= rem - 1;
+                            bp[t] = b;
+                            qv[t] = a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))];
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < kGather; ++t)
+                        if (bp[t] >= 0) acc += static_cast<u64>(qv[t]) * m[lane * 32 + bp[t]];
+                    rest = rem;
+                    for (uint32_t bb = rest; bb; bb &= bb - 1) {
                         const int b = __ffs(bb) - 1;
-                        const int64_t idx = col + rank + __popc(phib & ((1u << b) - 1u));
-                        acc += static_cast<u64>(a.q[idx]) * m[lane * 32 + b];
+                        acc += static_cast<u64>(a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))]) * m[lane * 32 + b];
                     }
                 } else {
-                    for (int j = lane; j < n_w; j += 32) acc += static_cast<u64>(a.q[col + j]) * m[a.topic[col + j]];
+                    seg = (n_w + 31) >> 5;
+                    seg0 = seg * lane;
+                    const int seg1 = min(seg0 + seg, n_w);
+#pragma unroll 4
+                    for (int j = seg0; j < seg1; ++j) acc += static_cast<u64>(a.q[col + j]) * m[a.topic[col + j]];
                 }
-                const u64 B = warp_sum64(acc);
+                const u64 incl = warp_incl_scan64(acc);
+                const u64 B = __shfl_sync(0xFFFFFFFFu, incl, 31);
                 const u64 T = At + (B << kFracBits);
                 int knew = kold;
                 if (T == 0) {
@@ -549,36 +595,37 @@ __global__ void k_z_step(ZArgs a) {
                         ++st_ab;
                     } else {
                         const u64 rb = (r - At) >> kFracBits;
+                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, rb < incl);
                         int found = -1;
-                        if (docside) {
-                            const u64 incl = warp_incl_scan64(acc);
-                            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, rb < incl);
-                            if (bal) {
-                                const int L = __ffs(bal) - 1;
-                                int f = -1;
-                                if (lane == L) {
-                                    u64 run = incl - acc;
-                                    for (uint32_t bb = inter; bb; bb &= bb - 1) {
+                        if (bal) {
+                            const int L = __ffs(bal) - 1;
+                            int f = -1;
+                            if (lane == L) {
+                                u64 run = incl - acc;
+                                if (docside) {
+#pragma unroll
+                                    for (int t = 0; t < kGather; ++t) {
+                                        if (f < 0 && bp[t] >= 0) {
+                                            run += static_cast<u64>(qv[t]) * m[lane * 32 + bp[t]];
+                                            if (rb < run) f = lane * 32 + bp[t];
+                                        }
+                                    }
+                                    for (uint32_t bb = rest; f < 0 && bb; bb &= bb - 1) {
                                         const int b = __ffs(bb) - 1;
-                                        const int64_t idx = col + rank + __popc(phib & ((1u << b) - 1u));
-                                        run += static_cast<u64>(a.q[idx]) * m[lane * 32 + b];
-                                        if (rb < run) { f = lane * 32 + b; break; }
+                                        run += static_cast<u64>(a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))]) *
+                                               m[lane * 32 + b];
+                                        if (rb < run) f = lane * 32 + b;
+                                    }
+                                } else {
+                                    const int seg1 = min(seg0 + seg, n_w);
+                                    for (int j = seg0; j < seg1; ++j) {
+                                        const int k = a.topic[col + j];
+                                        run += static_cast<u64>(a.q[col + j]) * m[k];
+                                        if (rb < run) { f = k; break; }
                                     }
                                 }
-                                found = __shfl_sync(0xFFFFFFFFu, f, L);
                             }
-                        } else {
-                            u64 carry = 0;
-                            for (int j0 = 0; j0 < n_w; j0 += 32) {
-                                const int j = j0 + lane;
-                                u64 b = 0;
-                                int k = 0;
-                                if (j < n_w) { k = a.topic[col + j]; b = static_cast<u64>(a.q[col + j]) * m[k]; }
-                                const u64 incl = warp_incl_scan64(b);
-                                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, j < n_w && rb < carry + incl);
-                                if (bal) { found = __shfl_sync(0xFFFFFFFFu, k, __ffs(bal) - 1); break; }
-                                carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
-                            }
+                            found = __shfl_sync(0xFFFFFFFFu, f, L);
                         }
                         if (found < 0) {
                             if (lane == 0) atomicOr(&a.stats[ST_ERROR], ERR_INTERNAL);

@@ -79,7 +79,7 @@ struct PhiArgs {
     unsigned long long *A;      // [V]
     unsigned long long *vose_p; // [cap] scratch
     uint16_t *vose_stack;       // [cap] scratch
-    uint32_t *bitmap;           // [V * KW] or null
+    uint2 *bitmap;              // [V * KW] {nonzero-topic bits, entries before this word} or null
     int KW;
     const float *alpha;         // [K]
     int *work;                  // dynamic word counter
@@ -98,7 +98,7 @@ struct ZArgs {
     const unsigned long long *A;
     const uint32_t *athr;
     const uint16_t *atopic;
-    const uint32_t *bitmap;     // null when K > kMaxKBitmap
+    const uint2 *bitmap;        // null when K > kMaxKBitmap
     int K, KW;
     uint64_t seed;
     uint32_t sweep;

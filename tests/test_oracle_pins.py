@@ -160,7 +160,7 @@ def _chi2_counts(sample, pmf_fn, min_exp=5.0):
 
 
 def test_phi_entries_follow_poisson_beta_plus_n():
-    """Eq. (7): c_{k,v} ~ Pois(beta + n_{k,v}), independently; rounded Gaussian above L."""
+    """Eq. (9): c_{k,v} ~ Pois(beta + n_{k,v}), independently; rounded Gaussian above L."""
     beta = 0.01
     V, K = 120, 40
     n = np.zeros((V, K), dtype=np.int32)   # n[v, k]
@@ -203,7 +203,7 @@ def test_phi_row_sums_and_normalisation():
 
 def test_dead_rows_are_conditioned_on_nonzero_sum():
     """Definition "Poisson Polya Urn": the normalisation needs a nonzero sum;
-    the hierarchical representation (Eq. 6) draws the total from Pois+.  A row
+    the hierarchical representation (Eq. 8) draws the total from Pois+.  A row
     with S_k = 0 is redrawn, so its law is the Poisson law given S_k > 0."""
     beta = 0.3
     V, K = 3, 1
