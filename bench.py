@@ -54,6 +54,7 @@ def parse():
                     help="documents in each step of the reference (oracle) arm's bounded sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--docs-per-warp", type=int, default=0, help="z-step documents per warp: 0 auto, 1 or 4")
     ap.add_argument("--docs", type=int, default=300_000,
                     help="documents of the large corpus (300,000 = the full workload; fewer for profiling)")
     return ap.parse_args()
@@ -206,7 +207,7 @@ def run_pulda(args, corpus, rank: int, world: int):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
-                  stream=stream.cuda_stream)
+                  stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp)
     s.sweep(args.burnin + args.warmup)
     s.sync()
     st0 = s.stats()
@@ -252,7 +253,7 @@ def run_pulda(args, corpus, rank: int, world: int):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
-                       stream=stream.cuda_stream)
+                       stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp)
         s2.sweep(K)
         zh = s2.z()   # e2e covers sweeps 1..K from the uniform start
         dt = time.perf_counter() - t0
@@ -303,6 +304,7 @@ def run_pulda(args, corpus, rank: int, world: int):
                      "kernel": "k_z_step", "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "algorithmic_bytes_per_launch": zbytes / K},
         "gpu_launches": KERNELS_PER_SWEEP * K,
+        "z_kernel": "four documents per warp" if args.docs_per_warp == 4 else "one document per warp",
         "clocks": clk,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -55,8 +55,11 @@ typedef struct {
     int32_t zstep_path;     /* 0 = auto (iterate the smaller of the document's and the
                                word's nonzero topics), 1 = always iterate the word's Phi
                                column, 2 = iterate the document's topics whenever K <= 1024 */
-    int32_t warps_per_block;/* z-step warps per CTA; 0 = chosen from K */
-    int32_t reserved[6];
+    int32_t warps_per_block;/* warp-per-document z-step: warps per CTA; 0 = chosen from K */
+    int32_t docs_per_warp;  /* z-step documents per warp: 0 = auto (one), 1 = one, 4 = four
+                               (needs K <= 1024; documents longer than 65,535 tokens still
+                               go one per warp); results are identical */
+    int32_t reserved[5];
 } pulda_options;
 
 /* Counters of the most recent z-step (and Phi-step), and running totals. */

@@ -26,6 +26,9 @@ struct pulda_handle {
     bool have_phi = false;
     float beta = 0;
     int z_warps = 8, z_grid = 0, phi_grid = 0;
+    bool z_groups = false;      // grouped z-step (four documents per warp) in use
+    int zg_grid = 0;
+    int64_t n_long = 0;         // documents too long for the grouped z-step (first in doc_order)
     std::vector<void *> allocs;
     // corpus and state
     int32_t *w = nullptr; int64_t *doc_off = nullptr; int16_t *z = nullptr; int32_t *doc_order = nullptr;
@@ -142,11 +145,34 @@ std::vector<int32_t> length_order(const int64_t *off, int64_t D) {
     return o;
 }
 
-pulda_status run_z(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, const int32_t *w,
-                   int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
-    CU(h, cudaMemsetAsync(h->work + 1, 0, sizeof(int), h->stream));
+// Number of leading documents of a length-ordered schedule that the grouped
+// z-step cannot take (longer than kMaxGroupDocLen tokens).
+int64_t count_long(const int64_t *off, const std::vector<int32_t> &order) {
+    int64_t n = 0;
+    while (n < static_cast<int64_t>(order.size()) && off[order[n] + 1] - off[order[n]] > kMaxGroupDocLen) ++n;
+    return n;
+}
+
+// One z-step over the documents doc_order[0..D): the documents too long for
+// the grouped kernel (the first n_long) one per warp, the rest four per warp.
+pulda_status run_z(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, int64_t n_long,
+                   const int32_t *w, int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
+    CU(h, cudaMemsetAsync(h->work + 1, 0, 2 * sizeof(int), h->stream));
     ZArgs a = z_args(h, doc_off, doc_order, D, w, z, seed, sweep, index_base);
-    launch_z_step(a, h->z_warps, h->z_grid, h->stream);
+    if (!h->z_groups) {
+        launch_z_step(a, h->z_warps, h->z_grid, h->stream);
+    } else {
+        if (n_long > 0) {
+            ZArgs al = a;
+            al.D = n_long;
+            launch_z_step(al, h->z_warps, h->z_grid, h->stream);
+        }
+        ZArgs ag = a;
+        ag.doc_order = doc_order + n_long;
+        ag.D = D - n_long;
+        ag.work = h->work + 2;
+        launch_z_step_groups(ag, h->zg_grid, h->stream);
+    }
     CU(h, cudaGetLastError());
     return PULDA_OK;
 }
@@ -262,6 +288,23 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     h->z_warps = wpb;
     h->z_grid = sms * z_step_blocks_per_sm(K, wpb);
     CUI(cudaGetLastError());
+    if (h->opt.docs_per_warp != 0 && h->opt.docs_per_warp != 1 && h->opt.docs_per_warp != 4) {
+        fail(h, PULDA_ERR_INVALID, "docs_per_warp must be 0 (auto), 1 or 4");
+        return bail(PULDA_ERR_INVALID);
+    }
+    if (h->opt.docs_per_warp == 4 && K > kMaxKBitmap) {
+        fail(h, PULDA_ERR_INVALID, "docs_per_warp = 4 needs K <= 1024");
+        return bail(PULDA_ERR_INVALID);
+    }
+    // Measured on the large workload (sweeps 31-50, |J| ~ 130 per token) one
+    // document per warp is 2x faster: the grouped kernel's lanes each carry 4x
+    // longer chains of dependent loads.  It is kept for small intersections.
+    h->z_groups = h->opt.docs_per_warp == 4;
+    h->n_long = count_long(doc_offsets, dord);
+    if (h->z_groups) {
+        h->zg_grid = sms * z_groups_blocks_per_sm(K);
+        CUI(cudaGetLastError());
+    }
     h->phi_grid = sms * phi_counts_blocks_per_sm(K);
     CUI(cudaGetLastError());
     CUI(cudaStreamSynchronize(st));
@@ -290,7 +333,7 @@ pulda_status pulda_z_step(pulda_handle *h) {
     if (!h) return PULDA_ERR_INVALID;
     if (!h->have_phi) return fail(h, PULDA_ERR_INVALID, "no Phi drawn yet: call pulda_phi_step or pulda_sweep first");
     CU(h, cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * 4, h->stream));
-    return run_z(h, h->doc_off, h->doc_order, h->D, h->w, h->z, h->seed, static_cast<uint32_t>(h->sweep), 0);
+    return run_z(h, h->doc_off, h->doc_order, h->D, h->n_long, h->w, h->z, h->seed, static_cast<uint32_t>(h->sweep), 0);
 }
 
 pulda_status pulda_sweep(pulda_handle *h, int32_t n_sweeps) {
@@ -436,8 +479,9 @@ pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids, const int64_t
     CU(h, cudaMemcpyAsync(dord, ord.data(), sizeof(int32_t) * D_new, cudaMemcpyHostToDevice, st));
     launch_init_z(N, h->K, seed, 0, dz, st);
     CU(h, cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * 4, st));
+    const int64_t n_long = count_long(doc_offsets, ord);
     for (int32_t sw = 1; sw <= n_sweeps; ++sw) {
-        s = run_z(h, doff, dord, D_new, dw, dz, seed, static_cast<uint32_t>(sw), 0);
+        s = run_z(h, doff, dord, D_new, n_long, dw, dz, seed, static_cast<uint32_t>(sw), 0);
         if (s != PULDA_OK) return s;
     }
     if (z_out) CU(h, cudaMemcpyAsync(z_out, dz, sizeof(int16_t) * N, cudaMemcpyDeviceToHost, st));

@@ -123,6 +123,12 @@ void launch_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K
 void launch_n_dense(const PhiArgs &a, int32_t *n_kv, cudaStream_t st);
 void launch_phi_values(const PhiArgs &a, float *phi, cudaStream_t st);
 int z_step_blocks_per_sm(int K, int warps_per_block);
+// Grouped z-step: 4 documents per warp, K <= kMaxKBitmap, documents of at
+// most kMaxGroupDocLen tokens; 8 warps per CTA.
+constexpr int kMaxGroupDocLen = 65535;
+void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st);
+size_t z_groups_smem(int K);
+int z_groups_blocks_per_sm(int K);
 int phi_counts_blocks_per_sm(int K);
 
 // What another translation unit needs to launch the z-step on a handle's

@@ -46,9 +46,9 @@ def first_mismatch(z_gpu: np.ndarray, z_or: np.ndarray, doc_off: np.ndarray) -> 
 
 
 def lockstep(w, doc_off, K: int, V: int, alpha, beta: float, seed: int, sweeps: int, path: int = 0,
-             check_tables: bool = True, check_counts_every: int = 0):
+             check_tables: bool = True, check_counts_every: int = 0, docs_per_warp: int = 0):
     """Run both sides for `sweeps` sweeps, comparing after each half-sweep."""
-    s = P.Sampler(w, doc_off, K, V, alpha, beta, seed, zstep_path=path)
+    s = P.Sampler(w, doc_off, K, V, alpha, beta, seed, zstep_path=path, docs_per_warp=docs_per_warp)
     ch = O.Chain(w, doc_off, K, V, alpha, beta, seed)
     try:
         zg = s.z()

@@ -26,24 +26,31 @@ def corpus_from_lengths(rng, lengths, V, zipf=1.0):
     return w, off
 
 
+@pytest.mark.parametrize("dpw", [4, 1], ids=["4docs-per-warp", "1doc-per-warp"])
 @pytest.mark.parametrize("path", [0, 1, 2])
-def test_tiny_corpus_lockstep(path):
+def test_tiny_corpus_lockstep(path, dpw):
     """K=20, V=1,000, D=1,000, ~100k tokens from the LDA generative process."""
     c = synth.tiny()
-    s, ch = lockstep(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=0, sweeps=6, path=path, check_counts_every=3)
+    s, ch = lockstep(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=0, sweeps=6, path=path, check_counts_every=3,
+                     docs_per_warp=dpw)
     s.close()
 
 
-def test_small_corpus_lockstep():
+@pytest.mark.parametrize("dpw", [4, 1], ids=["4docs-per-warp", "1doc-per-warp"])
+def test_small_corpus_lockstep(dpw):
     """Small-corpus shape: D=1,500, V=12,375, ~1.9M tokens, K=100."""
     c = synth.small()
-    s, ch = lockstep(c.w, c.doc_off, 100, c.V, 0.1, 0.01, seed=1, sweeps=3)
+    s, ch = lockstep(c.w, c.doc_off, 100, c.V, 0.1, 0.01, seed=1, sweeps=3, docs_per_warp=dpw)
     s.close()
 
 
-@pytest.mark.parametrize("K", [1, 31, 33, 1000, 1024, 1025, 3000])
-def test_topic_counts_around_tile_edges(K):
-    """K around the 32-topic word of the bitmap path and its 1024 limit."""
+@pytest.mark.parametrize("dpw", [4, 1], ids=["4docs-per-warp", "1doc-per-warp"])
+@pytest.mark.parametrize("K", [1, 31, 33, 200, 1000, 1024, 1025, 3000])
+def test_topic_counts_around_tile_edges(K, dpw):
+    """K around the 32-topic words, the 128 topics a lane owns in the grouped
+    kernel, and the 1024 limit of the bitmap paths."""
+    if dpw == 4 and K > 1024:
+        pytest.skip("four documents per warp needs K <= 1024")
     rng = np.random.default_rng(K)
     lengths = rng.integers(0, 90, size=120)
     lengths[3] = 0
@@ -51,7 +58,19 @@ def test_topic_counts_around_tile_edges(K):
     lengths[7] = 33
     w, off = corpus_from_lengths(rng, lengths, 700)
     s, _ = lockstep(w, off, K, 700, rng.uniform(0.05, 0.5, K).astype(np.float32), 0.02, seed=K, sweeps=3,
-                    check_counts_every=3)
+                    check_counts_every=3, docs_per_warp=dpw)
+    s.close()
+
+
+@pytest.mark.parametrize("path", [0, 1, 2])
+def test_documents_longer_than_the_grouped_kernel_takes(path):
+    """Documents over 65,535 tokens go to the one-document-per-warp kernel in
+    the same z-step as the grouped kernel's documents."""
+    rng = np.random.default_rng(17)
+    lengths = np.concatenate([[70000, 65535, 65536], rng.integers(1, 400, size=37)])
+    w, off = corpus_from_lengths(rng, lengths, 500)
+    s, _ = lockstep(w, off, 50, 500, 0.1, 0.01, seed=5, sweeps=2, path=path, check_counts_every=2,
+                    docs_per_warp=4)
     s.close()
 
 
@@ -64,6 +83,12 @@ def test_ragged_and_degenerate_inputs():
     w, off = corpus_from_lengths(rng, lengths, 3, zipf=0.5)
     s, ch = lockstep(w, off, 12, 6, 0.3, 0.001, seed=9, sweeps=8, check_counts_every=2)
     s.close()
+
+
+def test_four_documents_per_warp_rejects_large_K():
+    import paper_1704_03581_gb300 as P
+    with pytest.raises(P.PuldaError):
+        P.Sampler(np.zeros(3, np.int32), np.array([0, 3]), 1025, 2, 0.1, 0.01, 0, docs_per_warp=4)
 
 
 def test_dead_rows_are_redrawn_like_the_oracle():
@@ -115,10 +140,11 @@ def test_resume_from_checkpoint_is_exact():
     a.close(); b.close()
 
 
-def test_fold_in_matches_oracle():
+@pytest.mark.parametrize("dpw", [4, 1], ids=["4docs-per-warp", "1doc-per-warp"])
+def test_fold_in_matches_oracle(dpw):
     """pulda_infer: Algorithm 2's z-step with Phi held fixed, on new documents."""
     c = synth.tiny()
-    s, ch = lockstep(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=2, sweeps=3)
+    s, ch = lockstep(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=2, sweeps=3, docs_per_warp=dpw)
     new = c.slice_docs(0, 50)
     zg, mg = s.infer(new.w, new.doc_off, 10, seed=77, want_m=True)
     zo = O.infer(ch.tables, new.w, new.doc_off, 10, 77)
