@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--docs-per-warp", type=int, default=0, help="z-step documents per warp: 0 auto, 1 or 4")
+    ap.add_argument("--form", choices=["sweep", "batched"], default="sweep",
+                    help="sweep: the large corpus (the headline line); batched: 32 uneven chains in one graph "
+                         "launch per sweep against 32 sequential single-chain runs")
+    ap.add_argument("--batch-scale", type=float, default=0.25,
+                    help="fraction of each batched chain's documents (1.0 = the full 267M-token workload)")
     ap.add_argument("--docs", type=int, default=300_000,
                     help="documents of the large corpus (300,000 = the full workload; fewer for profiling)")
     return ap.parse_args()
@@ -312,6 +317,71 @@ def run_pulda(args, corpus, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """32 independent corpora (uneven D, N, K, V) advanced together by one
+    CUDA-graph launch per sweep, against the same 32 chains run one after
+    another through single-chain handles; both must give identical topics."""
+    import torch
+    import paper_1704_03581_gb300 as P
+    from paper_1704_03581_gb300 import synth
+
+    specs = synth.batched_specs(32)
+    corpora = [synth.batched_corpus(sp, args.batch_scale) for sp in specs]
+    chains = [dict(w=c.w, doc_off=c.doc_off, K=sp["K"], V=sp["V"], alpha=ALPHA, beta=BETA, seed=sp["seed"])
+              for c, sp in zip(corpora, specs)]
+    N = sum(c.N for c in corpora)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    K, W = args.steps, max(args.warmup, 3)
+    b = P.Batch(chains, stream=stream.cuda_stream)
+    b.sweep(W)                          # the first sweeps also time the tuning candidates
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    b.sweep(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    b.sync()
+    ms_b = e0.elapsed_time(e1)
+    zb = [b.z(i) for i in range(len(chains))]
+    warps, _ = b.tuning()
+    b.close()
+    # the same chains, one after another, one handle each
+    singles = [P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"],
+                         stream=stream.cuda_stream) for c in chains]
+    for s in singles:
+        s.sweep(W)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in singles:
+        s.sweep(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    same = all(np.array_equal(zb[i], s.z()) for i, s in enumerate(singles))
+    for s in singles:
+        s.close()
+    line = {
+        "metric": "batched chains: tokens/s of 32 uneven chains in one graph launch per sweep vs 32 sequential "
+                  "single-chain runs",
+        "value": N * K / (ms_b / 1000.0), "unit": "tokens/s", "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": ms_b / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"32 chains, D scaled by {args.batch_scale}", "N": N,
+                   "K": sorted({sp['K'] for sp in specs}), "z_warps_tuned": warps},
+        "sequential": {"value": N * K / (ms_s / 1000.0), "ms_per_step": ms_s / K},
+        "speedup_vs_sequential": ms_s / ms_b,
+        "identical_topics": same,
+        "gpu_launches": 6 * K,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -327,6 +397,12 @@ def main():
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.form == "batched":
+        from paper_1704_03581_gb300 import build
+        build.build()
+        if rank == 0:
+            run_batched(args)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

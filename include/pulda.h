@@ -179,6 +179,47 @@ pulda_status pulda_infer_noalloc(pulda_handle *h, const int32_t *word_ids_dev, c
                                  int64_t D_new, int64_t N_new, int32_t n_sweeps, uint64_t seed,
                                  int16_t *z_out_dev);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent chains advanced together (the batched form of Algorithm
+ * 2): each chain is exactly the chain a handle with the same arguments would
+ * run -- bit for bit -- but every kernel of a sweep runs once over all chains'
+ * words and documents (longest first across chains), and the six launches of
+ * a sweep are captured into one CUDA graph that is replayed every sweep.  The
+ * z-step CTA size is chosen by timing the candidates on the first sweeps
+ * (launch shapes never change results).  Chains may differ in D, N, K, V,
+ * alpha, beta and seed; all share the batch's stream. */
+typedef struct {
+    const int32_t *word_ids_host;    /* int32[N] */
+    const int64_t *doc_offsets_host; /* int64[D+1] */
+    int64_t D;
+    int32_t K, V;
+    const float *alpha_host;         /* float[K] */
+    float beta;
+    uint64_t seed;
+} pulda_chain_desc;
+
+typedef struct pulda_batch pulda_batch;
+
+/* pulda_batch_init -- validate and set up every chain as pulda_init would
+ * (same limits and errors, reported with the chain's index).  opt->stream, if
+ * set, is used for all chains; opt->warps_per_block > 0 fixes the z-step CTA
+ * size instead of tuning it; docs_per_warp must be 0 or 1. */
+pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains, int32_t n_chains,
+                              const pulda_options *opt);
+/* pulda_batch_sweep -- n_sweeps sweeps of every chain (asynchronous, except
+ * the first sweeps, which time the tuning candidates). */
+pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps);
+pulda_status pulda_batch_sync(pulda_batch *b);
+/* pulda_batch_get_z / pulda_batch_stats -- as pulda_get_z / pulda_stats for
+ * chain `chain` (0-based); PULDA_ERR_INVALID if out of range. */
+pulda_status pulda_batch_get_z(pulda_batch *b, int32_t chain, int16_t *z_host);
+pulda_status pulda_batch_stats(pulda_batch *b, int32_t chain, pulda_sweep_stats *out);
+/* pulda_batch_tuning -- the z-step warps per CTA in use and whether tuning is over. */
+pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *tuned);
+/* pulda_batch_last_error -- as pulda_last_error; NULL = last failed pulda_batch_init. */
+const char *pulda_batch_last_error(const pulda_batch *b);
+void pulda_batch_free(pulda_batch *b);
+
 /* pulda_stats -- counters of the most recent sweep (synchronises). */
 pulda_status pulda_stats(pulda_handle *h, pulda_sweep_stats *out);
 

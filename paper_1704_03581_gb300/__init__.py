@@ -24,7 +24,9 @@ STATUS = {0: "PULDA_OK", -1: "PULDA_ERR_INVALID", -2: "PULDA_ERR_OOM", -3: "PULD
 
 EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "pulda_sync", "pulda_get_z",
             "pulda_get_z_dev", "pulda_set_z", "pulda_get_counts", "pulda_get_phi", "pulda_get_word_tables",
-            "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_last_error", "pulda_free"]
+            "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_last_error", "pulda_free",
+            "pulda_batch_init", "pulda_batch_sweep", "pulda_batch_sync", "pulda_batch_get_z", "pulda_batch_stats",
+            "pulda_batch_tuning", "pulda_batch_last_error", "pulda_batch_free"]
 
 
 class PuldaError(RuntimeError):
@@ -76,6 +78,14 @@ def lib() -> ctypes.CDLL:
             "pulda_infer_noalloc": [P, P, P, i64, i64, i32, u64, P],
             "pulda_stats": [P, P],
         }
+        sig.update({
+            "pulda_batch_init": [P, P, i32, P],
+            "pulda_batch_sweep": [P, i32],
+            "pulda_batch_sync": [P],
+            "pulda_batch_get_z": [P, i32, P],
+            "pulda_batch_stats": [P, i32, P],
+            "pulda_batch_tuning": [P, P, P],
+        })
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -84,6 +94,10 @@ def lib() -> ctypes.CDLL:
         L.pulda_last_error.restype = ctypes.c_char_p
         L.pulda_free.argtypes = [P]
         L.pulda_free.restype = None
+        L.pulda_batch_last_error.argtypes = [P]
+        L.pulda_batch_last_error.restype = ctypes.c_char_p
+        L.pulda_batch_free.argtypes = [P]
+        L.pulda_batch_free.restype = None
         _lib = L
     return _lib
 
@@ -281,3 +295,107 @@ class Sampler:
 
     def stats(self) -> dict:
         return pulda_stats(self.h)
+
+
+# ------------------------------------------------------------------ batches
+
+class ChainDesc(ctypes.Structure):
+    _fields_ = [("word_ids_host", ctypes.c_void_p), ("doc_offsets_host", ctypes.c_void_p), ("D", ctypes.c_int64),
+                ("K", ctypes.c_int32), ("V", ctypes.c_int32), ("alpha_host", ctypes.c_void_p),
+                ("beta", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+def _bcheck(b, status: int):
+    if status != PULDA_OK:
+        msg = lib().pulda_batch_last_error(b)
+        raise PuldaError(status, msg.decode() if msg else "")
+
+
+def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0):
+    """chains: dicts with w, doc_off, K, V, alpha, beta, seed."""
+    keep = []
+    arr = (ChainDesc * len(chains))()
+    for i, c in enumerate(chains):
+        w = np.ascontiguousarray(c["w"], dtype=np.int32)
+        off = np.ascontiguousarray(c["doc_off"], dtype=np.int64)
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(c.get("alpha", 0.1), np.float32), (c["K"],)))
+        keep += [w, off, a]
+        arr[i] = ChainDesc(_ptr(w), _ptr(off), off.shape[0] - 1, c["K"], c["V"], _ptr(a), float(c.get("beta", 0.01)),
+                           int(c.get("seed", 0)) & (2 ** 64 - 1))
+    opt = Options()
+    opt.stream = stream
+    opt.warps_per_block = warps_per_block
+    b = ctypes.c_void_p()
+    _bcheck(None, lib().pulda_batch_init(ctypes.byref(b), arr, len(chains), ctypes.byref(opt)))
+    return b.value
+
+
+def pulda_batch_sweep(b, n_sweeps: int = 1):
+    _bcheck(b, lib().pulda_batch_sweep(b, n_sweeps))
+
+
+def pulda_batch_sync(b):
+    _bcheck(b, lib().pulda_batch_sync(b))
+
+
+def pulda_batch_get_z(b, chain: int, out: np.ndarray):
+    _bcheck(b, lib().pulda_batch_get_z(b, chain, _ptr(out)))
+    return out
+
+
+def pulda_batch_stats(b, chain: int) -> dict:
+    s = SweepStats()
+    _bcheck(b, lib().pulda_batch_stats(b, chain, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def pulda_batch_tuning(b) -> tuple[int, bool]:
+    w, t = ctypes.c_int32(0), ctypes.c_int32(0)
+    _bcheck(b, lib().pulda_batch_tuning(b, ctypes.byref(w), ctypes.byref(t)))
+    return w.value, bool(t.value)
+
+
+def pulda_batch_last_error(b) -> str:
+    m = lib().pulda_batch_last_error(b)
+    return m.decode() if m else ""
+
+
+def pulda_batch_free(b):
+    if b:
+        lib().pulda_batch_free(b)
+
+
+class Batch:
+    """Many chains advanced together: ``Batch(chains).sweep(n)``."""
+
+    def __init__(self, chains: list[dict], stream=None, warps_per_block: int = 0):
+        self.sizes = [int(np.asarray(c["doc_off"])[-1]) for c in chains]
+        self.b = pulda_batch_init(chains, stream, warps_per_block)
+
+    def close(self):
+        if self.b:
+            pulda_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sweep(self, n: int = 1):
+        pulda_batch_sweep(self.b, n)
+        return self
+
+    def sync(self):
+        pulda_batch_sync(self.b)
+
+    def z(self, chain: int) -> np.ndarray:
+        n = self.sizes[chain]
+        return pulda_batch_get_z(self.b, chain, np.zeros(max(n, 1), np.int16))[:n]
+
+    def stats(self, chain: int) -> dict:
+        return pulda_batch_stats(self.b, chain)
+
+    def tuning(self):
+        return pulda_batch_tuning(self.b)

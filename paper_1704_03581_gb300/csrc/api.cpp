@@ -9,44 +9,10 @@
 #include <vector>
 
 #include "../../include/pulda.h"
+#include "handle.h"
 #include "pulda_internal.h"
 
 using namespace pulda;
-
-struct pulda_handle {
-    std::string err;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    pulda_options opt{};
-    int device = 0;
-    int64_t N = 0, D = 0;
-    int K = 0, V = 0, KW = 0;
-    uint64_t seed = 0;
-    int64_t sweep = 0;
-    bool have_phi = false;
-    float beta = 0;
-    int z_warps = 8, z_grid = 0, phi_grid = 0;
-    bool z_groups = false;      // grouped z-step (four documents per warp) in use
-    int zg_grid = 0;
-    int64_t n_long = 0;         // documents too long for the grouped z-step (first in doc_order)
-    std::vector<void *> allocs;
-    // corpus and state
-    int32_t *w = nullptr; int64_t *doc_off = nullptr; int16_t *z = nullptr; int32_t *doc_order = nullptr;
-    int32_t *perm = nullptr; int64_t *word_off = nullptr; int32_t *word_order = nullptr; int32_t *fill = nullptr;
-    float *alpha = nullptr;
-    // fixed tables
-    uint32_t *t_thr = nullptr; uint16_t *t_alias = nullptr; int32_t *t_off = nullptr, *t_lo = nullptr, *t_n = nullptr;
-    uint32_t *t_geo = nullptr; double *t_gauss = nullptr;
-    // Phi-step buffers
-    uint16_t *nst_k = nullptr; uint32_t *nst_n = nullptr; int32_t *nnz_n = nullptr;
-    uint16_t *cst_k = nullptr; uint32_t *cst_c = nullptr; int32_t *nnz_c = nullptr;
-    unsigned long long *S = nullptr; uint32_t *rowbuf = nullptr; int64_t *col_ptr = nullptr;
-    uint16_t *topic = nullptr; uint32_t *c = nullptr, *q = nullptr, *athr = nullptr; uint16_t *atopic = nullptr;
-    unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint2 *bitmap = nullptr;
-    int *work = nullptr;
-    unsigned long long *stats = nullptr;
-    int64_t cap = 0;   // capacity of the per-word tables: K * V entries
-};
 
 namespace {
 
@@ -90,30 +56,6 @@ cudaError_t dalloc(pulda_handle *h, T **p, size_t count) {
     if (e == cudaSuccess) h->allocs.push_back(ptr);
     *p = static_cast<T *>(ptr);
     return e;
-}
-
-PhiArgs phi_args(pulda_handle *h) {
-    PhiArgs a{};
-    a.K = h->K; a.V = h->V; a.seed = h->seed; a.sweep = static_cast<uint32_t>(h->sweep);
-    a.perm = h->perm; a.word_off = h->word_off; a.word_order = h->word_order; a.z = h->z;
-    a.tab = DevTables{h->t_thr, h->t_alias, h->t_off, h->t_lo, h->t_n, h->t_geo, h->t_gauss, static_cast<double>(h->beta)};
-    a.nst_k = h->nst_k; a.nst_n = h->nst_n; a.nnz_n = h->nnz_n;
-    a.cst_k = h->cst_k; a.cst_c = h->cst_c; a.nnz_c = h->nnz_c;
-    a.S = h->S; a.rowbuf = h->rowbuf; a.col_ptr = h->col_ptr;
-    a.topic = h->topic; a.c = h->c; a.q = h->q; a.athr = h->athr; a.atopic = h->atopic;
-    a.A = h->A; a.vose_p = h->vose_p; a.vose_stack = h->vose_stack; a.bitmap = h->bitmap; a.KW = h->KW;
-    a.alpha = h->alpha; a.work = h->work; a.stats = h->stats;
-    return a;
-}
-
-ZArgs z_args(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, const int32_t *w,
-             int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
-    ZArgs a{};
-    a.doc_off = doc_off; a.doc_order = doc_order; a.D = D; a.w = w; a.z = z;
-    a.col_ptr = h->col_ptr; a.topic = h->topic; a.q = h->q; a.A = h->A; a.athr = h->athr; a.atopic = h->atopic;
-    a.bitmap = h->bitmap; a.K = h->K; a.KW = h->KW; a.seed = seed; a.sweep = sweep; a.index_base = index_base;
-    a.path = h->opt.zstep_path; a.work = h->work + 1; a.stats = h->stats;
-    return a;
 }
 
 pulda_status check_corpus(pulda_handle *h, const int32_t *w, const int64_t *off, int64_t D, int V,
@@ -180,6 +122,31 @@ pulda_status run_z(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_o
 }  // namespace
 
 namespace pulda {
+PhiArgs phi_args(pulda_handle *h) {
+    PhiArgs a{};
+    a.K = h->K; a.V = h->V; a.seed = h->seed; a.sweep = static_cast<uint32_t>(h->sweep);
+    a.perm = h->perm; a.word_off = h->word_off; a.word_order = h->word_order; a.z = h->z;
+    a.tab = DevTables{h->t_thr, h->t_alias, h->t_off, h->t_lo, h->t_n, h->t_geo, h->t_gauss, static_cast<double>(h->beta)};
+    a.nst_k = h->nst_k; a.nst_n = h->nst_n; a.nnz_n = h->nnz_n;
+    a.cst_k = h->cst_k; a.cst_c = h->cst_c; a.nnz_c = h->nnz_c;
+    a.S = h->S; a.rowbuf = h->rowbuf; a.col_ptr = h->col_ptr;
+    a.topic = h->topic; a.c = h->c; a.q = h->q; a.athr = h->athr; a.atopic = h->atopic;
+    a.A = h->A; a.vose_p = h->vose_p; a.vose_stack = h->vose_stack; a.bitmap = h->bitmap; a.KW = h->KW;
+    a.alpha = h->alpha; a.work = h->work; a.stats = h->stats;
+    return a;
+}
+
+ZArgs z_args(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, const int32_t *w,
+             int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
+    ZArgs a{};
+    a.doc_off = doc_off; a.doc_order = doc_order; a.D = D; a.w = w; a.z = z;
+    a.col_ptr = h->col_ptr; a.topic = h->topic; a.q = h->q; a.A = h->A; a.athr = h->athr; a.atopic = h->atopic;
+    a.bitmap = h->bitmap; a.K = h->K; a.KW = h->KW; a.seed = seed; a.sweep = sweep; a.index_base = index_base;
+    a.path = h->opt.zstep_path; a.work = h->work + 1; a.stats = h->stats;
+    return a;
+}
+
+
 // Read-only view of a handle for other translation units of the library.
 bool handle_view(pulda_handle *h, HandleView *out) {
     if (!h || !out) return false;

@@ -1,0 +1,291 @@
+// Many independent chains (corpora of uneven D, N, K, V) advanced together:
+// every kernel of a sweep runs once over all chains' work items, and the six
+// launches of a sweep are captured once into a CUDA graph and replayed.  The
+// z-step CTA size is picked by timing the candidates on the first sweeps (a
+// launch shape never changes a result, so tuning costs no extra sweeps).
+#include <algorithm>
+#include <cstdio>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pulda.h"
+#include "handle.h"
+#include "pulda_internal.h"
+
+using namespace pulda;
+
+struct pulda_batch {
+    std::string err;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<pulda_handle *> ch;
+    std::vector<void *> allocs;
+    BatchLaunch bl{};
+    int sms = 1;
+    int64_t sweep = 0;
+    std::vector<int> cand;          // z-step warps per CTA to try
+    std::vector<float> cand_ms;
+    bool tuned = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+pulda_status bfail(pulda_batch *b, pulda_status s, const std::string &msg) {
+    if (b) b->err = msg;
+    return s;
+}
+
+#define BCU(b, expr)                                                                                \
+    do {                                                                                            \
+        cudaError_t e_ = (expr);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA,     \
+                         std::string(#expr " failed: ") + cudaGetErrorString(e_));                  \
+    } while (0)
+
+template <typename T>
+cudaError_t balloc(pulda_batch *b, T **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * std::max<size_t>(n, 1));
+    if (e == cudaSuccess) b->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return e;
+}
+
+thread_local std::string g_batch_init_error;
+
+pulda_status launch_one_sweep(pulda_batch *b) {
+    launch_batch_sweep(b->bl, b->stream);
+    BCU(b, cudaGetLastError());
+    return PULDA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains, int32_t n_chains,
+                              const pulda_options *opt) {
+    if (!out) return PULDA_ERR_INVALID;
+    *out = nullptr;
+    g_batch_init_error.clear();
+    if (!chains || n_chains < 1) {
+        g_batch_init_error = "n_chains must be >= 1 and chains non-NULL";
+        return PULDA_ERR_INVALID;
+    }
+    pulda_batch *b = new pulda_batch();
+    auto bail = [&](pulda_status s) {
+        g_batch_init_error = b->err;
+        pulda_batch_free(b);
+        return s;
+    };
+    pulda_options o{};
+    if (opt) o = *opt;
+    if (o.docs_per_warp == 4) {
+        b->err = "batched chains run one document per warp (docs_per_warp must be 0 or 1)";
+        return bail(PULDA_ERR_INVALID);
+    }
+    if (o.stream) {
+        b->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            b->err = "cudaStreamCreate failed";
+            return bail(PULDA_ERR_CUDA);
+        }
+        b->own_stream = true;
+    }
+    o.stream = b->stream;
+    o.docs_per_warp = 1;
+    for (int32_t c = 0; c < n_chains; ++c) {
+        const pulda_chain_desc &d = chains[c];
+        pulda_handle *h = nullptr;
+        pulda_status s = pulda_init(&h, d.word_ids_host, d.doc_offsets_host, d.D, d.K, d.V, d.alpha_host, d.beta,
+                                    d.seed, &o);
+        if (s != PULDA_OK) {
+            b->err = "chain " + std::to_string(c) + ": " + pulda_last_error(nullptr);
+            return bail(s);
+        }
+        b->ch.push_back(h);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    // per-chain descriptors, reading the sweep counter from device memory
+    uint32_t *d_sweep = nullptr;
+    int *d_work = nullptr;
+    PhiArgs *d_phi = nullptr;
+    ZArgs *d_z = nullptr;
+    if (balloc(b, &d_sweep, 1) != cudaSuccess || balloc(b, &d_work, 4) != cudaSuccess ||
+        balloc(b, &d_phi, n_chains) != cudaSuccess || balloc(b, &d_z, n_chains) != cudaSuccess) {
+        b->err = "device allocation of the batch descriptors failed";
+        return bail(PULDA_ERR_OOM);
+    }
+    std::vector<PhiArgs> hp(n_chains);
+    std::vector<ZArgs> hz(n_chains);
+    std::vector<std::pair<int64_t, int2>> wi, di;    // (weight, (chain, item))
+    int kmax = 1;
+    for (int32_t c = 0; c < n_chains; ++c) {
+        pulda_handle *h = b->ch[c];
+        hp[c] = phi_args(h);
+        hp[c].sweep_ptr = d_sweep;
+        hz[c] = z_args(h, h->doc_off, h->doc_order, h->D, h->w, h->z, h->seed, 0, 0);
+        hz[c].sweep_ptr = d_sweep;
+        kmax = std::max(kmax, h->K);
+        std::vector<int64_t> woff(h->V + 1);
+        if (cudaMemcpy(woff.data(), h->word_off, sizeof(int64_t) * (h->V + 1), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            b->err = "reading word offsets failed";
+            return bail(PULDA_ERR_CUDA);
+        }
+        for (int v = 0; v < h->V; ++v) wi.push_back({woff[v + 1] - woff[v], make_int2(c, v)});
+        const int64_t *off = chains[c].doc_offsets_host;
+        for (int64_t d = 0; d < h->D; ++d) di.push_back({off[d + 1] - off[d], make_int2(c, static_cast<int>(d))});
+    }
+    auto heavy_first = [](const std::pair<int64_t, int2> &x, const std::pair<int64_t, int2> &y) {
+        return x.first > y.first;
+    };
+    std::stable_sort(wi.begin(), wi.end(), heavy_first);
+    std::stable_sort(di.begin(), di.end(), heavy_first);
+    std::vector<int2> wlist(wi.size()), dlist(di.size());
+    for (size_t i = 0; i < wi.size(); ++i) wlist[i] = wi[i].second;
+    for (size_t i = 0; i < di.size(); ++i) dlist[i] = di[i].second;
+    int2 *d_wl = nullptr, *d_dl = nullptr;
+    if (balloc(b, &d_wl, wlist.size()) != cudaSuccess || balloc(b, &d_dl, dlist.size()) != cudaSuccess) {
+        b->err = "device allocation of the work lists failed";
+        return bail(PULDA_ERR_OOM);
+    }
+    cudaStream_t st = b->stream;
+    const uint32_t zero = 0;
+    if (cudaMemcpyAsync(d_phi, hp.data(), sizeof(PhiArgs) * n_chains, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_z, hz.data(), sizeof(ZArgs) * n_chains, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_wl, wlist.data(), sizeof(int2) * wlist.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_dl, dlist.data(), sizeof(int2) * dlist.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_sweep, &zero, sizeof zero, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        b->err = "uploading the batch descriptors failed";
+        return bail(PULDA_ERR_CUDA);
+    }
+    BatchLaunch &bl = b->bl;
+    bl.phi = d_phi;
+    bl.z = d_z;
+    bl.n_chains = n_chains;
+    bl.phi_items = d_wl;
+    bl.n_phi_items = static_cast<int>(wlist.size());
+    bl.z_items = d_dl;
+    bl.n_z_items = static_cast<int>(dlist.size());
+    bl.sweep = d_sweep;
+    bl.work = d_work;
+    bl.kmax = kmax;
+    bl.phi_grid = b->sms * batch_phi_blocks_per_sm(kmax);
+    for (int w : {2, 4, 8})
+        if (sizeof(uint32_t) * static_cast<size_t>(kmax) * w <= 160 * 1024) b->cand.push_back(w);
+    if (b->cand.empty()) b->cand.push_back(1);
+    if (o.warps_per_block > 0) {
+        b->cand.assign(1, o.warps_per_block);
+        b->tuned = true;
+    }
+    bl.z_warps = b->cand.front();
+    bl.z_grid = b->sms * batch_z_blocks_per_sm(kmax, bl.z_warps);
+    if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+        cudaGetLastError() != cudaSuccess) {
+        b->err = "CUDA set-up of the batch failed";
+        return bail(PULDA_ERR_CUDA);
+    }
+    *out = b;
+    return PULDA_OK;
+}
+
+pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps) {
+    if (!b) return PULDA_ERR_INVALID;
+    if (n_sweeps < 0) return bfail(b, PULDA_ERR_INVALID, "n_sweeps must be >= 0");
+    for (int32_t s = 0; s < n_sweeps; ++s) {
+        if (!b->tuned) {
+            // time the next candidate on a real sweep
+            const int w = b->cand[b->cand_ms.size()];
+            b->bl.z_warps = w;
+            b->bl.z_grid = b->sms * batch_z_blocks_per_sm(b->bl.kmax, w);
+            BCU(b, cudaEventRecord(b->ev0, b->stream));
+            pulda_status r = launch_one_sweep(b);
+            if (r != PULDA_OK) return r;
+            BCU(b, cudaEventRecord(b->ev1, b->stream));
+            BCU(b, cudaEventSynchronize(b->ev1));
+            float ms = 0;
+            BCU(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+            b->cand_ms.push_back(ms);
+            if (b->cand_ms.size() == b->cand.size()) {
+                const size_t best = std::min_element(b->cand_ms.begin(), b->cand_ms.end()) - b->cand_ms.begin();
+                b->bl.z_warps = b->cand[best];
+                b->bl.z_grid = b->sms * batch_z_blocks_per_sm(b->bl.kmax, b->bl.z_warps);
+                b->tuned = true;
+            }
+        } else {
+            if (!b->exec) {
+                BCU(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                launch_batch_sweep(b->bl, b->stream);
+                cudaError_t ce = cudaStreamEndCapture(b->stream, &b->graph);
+                if (ce != cudaSuccess) return bfail(b, PULDA_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce));
+                BCU(b, cudaGraphInstantiate(&b->exec, b->graph, 0));
+            }
+            BCU(b, cudaGraphLaunch(b->exec, b->stream));
+        }
+        b->sweep += 1;
+    }
+    for (pulda_handle *h : b->ch) {
+        h->sweep = b->sweep;
+        h->have_phi = h->have_phi || b->sweep > 0;
+    }
+    return PULDA_OK;
+}
+
+pulda_status pulda_batch_sync(pulda_batch *b) {
+    if (!b) return PULDA_ERR_INVALID;
+    BCU(b, cudaStreamSynchronize(b->stream));
+    for (size_t c = 0; c < b->ch.size(); ++c) {
+        pulda_status s = pulda_sync(b->ch[c]);
+        if (s != PULDA_OK) return bfail(b, s, "chain " + std::to_string(c) + ": " + pulda_last_error(b->ch[c]));
+    }
+    return PULDA_OK;
+}
+
+pulda_status pulda_batch_get_z(pulda_batch *b, int32_t chain, int16_t *z_host) {
+    if (!b) return PULDA_ERR_INVALID;
+    if (chain < 0 || chain >= static_cast<int32_t>(b->ch.size())) return bfail(b, PULDA_ERR_INVALID, "chain out of range");
+    pulda_status s = pulda_get_z(b->ch[chain], z_host);
+    if (s != PULDA_OK) return bfail(b, s, pulda_last_error(b->ch[chain]));
+    return PULDA_OK;
+}
+
+pulda_status pulda_batch_stats(pulda_batch *b, int32_t chain, pulda_sweep_stats *out) {
+    if (!b) return PULDA_ERR_INVALID;
+    if (chain < 0 || chain >= static_cast<int32_t>(b->ch.size())) return bfail(b, PULDA_ERR_INVALID, "chain out of range");
+    pulda_status s = pulda_stats(b->ch[chain], out);
+    if (s != PULDA_OK) return bfail(b, s, pulda_last_error(b->ch[chain]));
+    return PULDA_OK;
+}
+
+pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *tuned) {
+    if (!b) return PULDA_ERR_INVALID;
+    if (z_warps) *z_warps = b->bl.z_warps;
+    if (tuned) *tuned = b->tuned ? 1 : 0;
+    return PULDA_OK;
+}
+
+const char *pulda_batch_last_error(const pulda_batch *b) { return b ? b->err.c_str() : g_batch_init_error.c_str(); }
+
+void pulda_batch_free(pulda_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    for (pulda_handle *h : b->ch) pulda_free(h);
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

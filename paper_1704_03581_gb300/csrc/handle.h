@@ -1,0 +1,52 @@
+// The state behind a pulda_handle (internal to the library).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pulda.h"
+#include "pulda_internal.h"
+
+struct pulda_handle {
+    std::string err;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    pulda_options opt{};
+    int device = 0;
+    int64_t N = 0, D = 0;
+    int K = 0, V = 0, KW = 0;
+    uint64_t seed = 0;
+    int64_t sweep = 0;
+    bool have_phi = false;
+    float beta = 0;
+    int z_warps = 8, z_grid = 0, phi_grid = 0;
+    bool z_groups = false;      // grouped z-step (four documents per warp) in use
+    int zg_grid = 0;
+    int64_t n_long = 0;         // documents too long for the grouped z-step (first in doc_order)
+    std::vector<void *> allocs;
+    // corpus and state
+    int32_t *w = nullptr; int64_t *doc_off = nullptr; int16_t *z = nullptr; int32_t *doc_order = nullptr;
+    int32_t *perm = nullptr; int64_t *word_off = nullptr; int32_t *word_order = nullptr; int32_t *fill = nullptr;
+    float *alpha = nullptr;
+    // fixed tables
+    uint32_t *t_thr = nullptr; uint16_t *t_alias = nullptr; int32_t *t_off = nullptr, *t_lo = nullptr, *t_n = nullptr;
+    uint32_t *t_geo = nullptr; double *t_gauss = nullptr;
+    // Phi-step buffers
+    uint16_t *nst_k = nullptr; uint32_t *nst_n = nullptr; int32_t *nnz_n = nullptr;
+    uint16_t *cst_k = nullptr; uint32_t *cst_c = nullptr; int32_t *nnz_c = nullptr;
+    unsigned long long *S = nullptr; uint32_t *rowbuf = nullptr; int64_t *col_ptr = nullptr;
+    uint16_t *topic = nullptr; uint32_t *c = nullptr, *q = nullptr, *athr = nullptr; uint16_t *atopic = nullptr;
+    unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint2 *bitmap = nullptr;
+    int *work = nullptr;
+    unsigned long long *stats = nullptr;
+    int64_t cap = 0;   // capacity of the per-word tables: K * V entries
+};
+
+
+namespace pulda {
+PhiArgs phi_args(pulda_handle *h);
+ZArgs z_args(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, const int32_t *w,
+             int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base);
+}  // namespace pulda

@@ -127,17 +127,6 @@ __device__ __forceinline__ u64 warp_incl_scan64(u64 v) {
     return v;
 }
 
-__device__ __forceinline__ uint32_t warp_excl_scan32(uint32_t v) {
-    const int lane = threadIdx.x & 31;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= o) x += y;
-    }
-    return x - v;
-}
-
 // ================================================================= init
 __global__ void k_init_z(int64_t N, int K, uint64_t seed, int64_t base, int16_t *z) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < N;
@@ -189,83 +178,109 @@ __global__ void k_word_scatter(int64_t N, const int32_t *w, const int64_t *word_
 // ======================================================== Phi-step: counts
 constexpr int kPhiBlock = 256;
 
-// Per word (dynamically scheduled, most frequent first): histogram of the
-// word's topics -> n_{.,v}; compacted n column; when `draw`, the Poisson
-// draws c_{.,v}, the compacted c column, and S_k += c_{k,v}.
+// Sweep counter of a chain: from device memory when the launch is replayed
+// from a CUDA graph (one graph serves every sweep), else the launch value.
+__device__ __forceinline__ uint32_t sweep_of(const PhiArgs &a) { return a.sweep_ptr ? *a.sweep_ptr : a.sweep; }
+__device__ __forceinline__ uint32_t sweep_of(const ZArgs &a) { return a.sweep_ptr ? *a.sweep_ptr : a.sweep; }
+
+// One word v of one chain, by the whole CTA: histogram of the word's topics
+// -> n_{.,v}; compacted n column; when `draw`, the Poisson draws c_{.,v},
+// the compacted c column, and S_k += c_{k,v}.  hist/cbin hold K entries each.
+__device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, uint32_t *cbin, int *scan_tmp) {
+    const int K = a.K;
+    const uint32_t sweep = sweep_of(a);
+    const int per = (K + kPhiBlock - 1) / kPhiBlock;     // bins owned by each thread, contiguous
+    const int64_t wbeg = a.word_off[v], wend = a.word_off[v + 1];
+    for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
+    __syncthreads();
+    for (int64_t t = wbeg + threadIdx.x; t < wend; t += kPhiBlock) atomicAdd(&hist[a.z[a.perm[t]]], 1u);
+    __syncthreads();
+    if (do_draw) {
+        // entries with n_{k,v} = l >= 1: c ~ Pois(beta + l)
+        for (int k = threadIdx.x; k < K; k += kPhiBlock) {
+            const uint32_t l = hist[k];
+            if (l) {
+                const U4 x = draw(a.seed, static_cast<uint32_t>(v), static_cast<uint32_t>(k), sweep, TAG_POIS, 0);
+                cbin[k] = draw_entry(a.tab, l, x.x, x.y);
+            }
+        }
+        // entries with n_{k,v} = 0: Pois(beta) by geometric skip-ahead
+        if (threadIdx.x == 0) {
+            int64_t pos = -1;
+            uint32_t h = 0;
+            for (;;) {
+                const U4 x = draw(a.seed, static_cast<uint32_t>(v), h++, sweep, TAG_BETA, 0);
+                const int g = geo_gap(a.tab.geo, x.x);
+                if (g < 0) {
+                    pos += kGeoLen;
+                    if (pos >= K - 1) break;
+                    continue;
+                }
+                pos += g + 1;
+                if (pos >= K) break;
+                if (hist[pos] == 0) cbin[pos] = table_draw(a.tab, 0, x.y, x.z);
+            }
+        }
+        __syncthreads();
+    }
+    // compaction in ascending topic order
+    const int k0 = threadIdx.x * per, k1 = min(K, k0 + per);
+    int cn = 0, cc = 0;
+    for (int k = k0; k < k1; ++k) { cn += hist[k] != 0; cc += cbin[k] != 0; }
+    int tn, tc;
+    int pn = block_excl_scan<kPhiBlock>(cn, scan_tmp, tn);
+    int pc = block_excl_scan<kPhiBlock>(cc, scan_tmp, tc);
+    for (int k = k0; k < k1; ++k) {
+        const uint32_t l = hist[k];
+        if (l) { a.nst_k[wbeg + pn] = static_cast<uint16_t>(k); a.nst_n[wbeg + pn] = l; ++pn; }
+        if (do_draw) {
+            const uint32_t c = cbin[k];
+            if (c) {
+                const int64_t o = static_cast<int64_t>(v) * K + pc;
+                a.cst_k[o] = static_cast<uint16_t>(k);
+                a.cst_c[o] = c;
+                atomicAdd(&a.S[k], static_cast<u64>(c));
+                ++pc;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        a.nnz_n[v] = tn;
+        if (do_draw) a.nnz_c[v] = tc;
+    }
+    __syncthreads();
+}
+
+// One chain's words, dynamically scheduled, most frequent first.
 __global__ void __launch_bounds__(kPhiBlock) k_phi_counts(PhiArgs a, bool do_draw) {
     extern __shared__ uint32_t sm[];
-    uint32_t *hist = sm;
-    uint32_t *cbin = sm + a.K;
     __shared__ int scan_tmp[kPhiBlock / 32 + 1];
     __shared__ int s_item;
-    const int K = a.K;
-    const int per = (K + kPhiBlock - 1) / kPhiBlock;     // bins owned by each thread, contiguous
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
         __syncthreads();
         const int item = s_item;
         __syncthreads();
         if (item >= a.V) break;
-        const int v = a.word_order[item];
-        const int64_t wbeg = a.word_off[v], wend = a.word_off[v + 1];
-        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
+        phi_word(a, a.word_order[item], do_draw, sm, sm + a.K, scan_tmp);
+    }
+}
+
+// Many chains: the work list holds (chain, word) pairs, most frequent first
+// across all chains; shared memory is sized for the largest K.
+__global__ void __launch_bounds__(kPhiBlock) k_phi_counts_multi(const PhiArgs *chains, const int2 *items,
+                                                                 int n_items, int *work, int kmax, bool do_draw) {
+    extern __shared__ uint32_t sm[];
+    __shared__ int scan_tmp[kPhiBlock / 32 + 1];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
         __syncthreads();
-        for (int64_t t = wbeg + threadIdx.x; t < wend; t += kPhiBlock) atomicAdd(&hist[a.z[a.perm[t]]], 1u);
+        const int item = s_item;
         __syncthreads();
-        if (do_draw) {
-            // entries with n_{k,v} = l >= 1: c ~ Pois(beta + l)
-            for (int k = threadIdx.x; k < K; k += kPhiBlock) {
-                const uint32_t l = hist[k];
-                if (l) {
-                    const U4 x = draw(a.seed, static_cast<uint32_t>(v), static_cast<uint32_t>(k), a.sweep, TAG_POIS, 0);
-                    cbin[k] = draw_entry(a.tab, l, x.x, x.y);
-                }
-            }
-            // entries with n_{k,v} = 0: Pois(beta) by geometric skip-ahead
-            if (threadIdx.x == 0) {
-                int64_t pos = -1;
-                uint32_t h = 0;
-                for (;;) {
-                    const U4 x = draw(a.seed, static_cast<uint32_t>(v), h++, a.sweep, TAG_BETA, 0);
-                    const int g = geo_gap(a.tab.geo, x.x);
-                    if (g < 0) {
-                        pos += kGeoLen;
-                        if (pos >= K - 1) break;
-                        continue;
-                    }
-                    pos += g + 1;
-                    if (pos >= K) break;
-                    if (hist[pos] == 0) cbin[pos] = table_draw(a.tab, 0, x.y, x.z);
-                }
-            }
-            __syncthreads();
-        }
-        // compaction in ascending topic order
-        const int k0 = threadIdx.x * per, k1 = min(K, k0 + per);
-        int cn = 0, cc = 0;
-        for (int k = k0; k < k1; ++k) { cn += hist[k] != 0; cc += cbin[k] != 0; }
-        int tn, tc;
-        int pn = block_excl_scan<kPhiBlock>(cn, scan_tmp, tn);
-        int pc = block_excl_scan<kPhiBlock>(cc, scan_tmp, tc);
-        for (int k = k0; k < k1; ++k) {
-            const uint32_t l = hist[k];
-            if (l) { a.nst_k[wbeg + pn] = static_cast<uint16_t>(k); a.nst_n[wbeg + pn] = l; ++pn; }
-            if (do_draw) {
-                const uint32_t c = cbin[k];
-                if (c) {
-                    const int64_t o = static_cast<int64_t>(v) * K + pc;
-                    a.cst_k[o] = static_cast<uint16_t>(k);
-                    a.cst_c[o] = c;
-                    atomicAdd(&a.S[k], static_cast<u64>(c));
-                    ++pc;
-                }
-            }
-        }
-        if (threadIdx.x == 0) {
-            a.nnz_n[v] = tn;
-            if (do_draw) a.nnz_c[v] = tc;
-        }
-        __syncthreads();
+        if (item >= n_items) break;
+        const int2 it = items[item];
+        phi_word(chains[it.x], it.y, do_draw, sm, sm + kmax, scan_tmp);
     }
 }
 
@@ -287,9 +302,9 @@ constexpr int kFixBlock = 1024;
 // a = 1, 2, ...) until the sum is nonzero: the urn total is Pois+ (the
 // hierarchical representation, Eq. 8).  Accepted rows are inserted into the
 // word columns.  Single block; almost always just checks S and exits.
-__global__ void __launch_bounds__(kFixBlock) k_phi_fixup(PhiArgs a) {
-    __shared__ u64 red[kFixBlock / 32];
-    __shared__ u64 s_sum;
+__device__ void phi_fixup_chain(const PhiArgs &a, u64 *red, u64 *s_sum_p) {
+    u64 &s_sum = *s_sum_p;
+    const uint32_t sweep = sweep_of(a);
     for (int k = 0; k < a.K; ++k) {
         if (a.S[k] != 0) continue;
         if (threadIdx.x == 0) atomicAdd(&a.stats[ST_DEADROWS], 1ull);
@@ -300,7 +315,7 @@ __global__ void __launch_bounds__(kFixBlock) k_phi_fixup(PhiArgs a) {
                 const uint32_t l = lookup_n(a, v, k);
                 uint32_t val = 0;
                 if (l) {
-                    const U4 x = draw(a.seed, static_cast<uint32_t>(v), static_cast<uint32_t>(k), a.sweep, TAG_REDRAW_POIS, att);
+                    const U4 x = draw(a.seed, static_cast<uint32_t>(v), static_cast<uint32_t>(k), sweep, TAG_REDRAW_POIS, att);
                     val = draw_entry(a.tab, l, x.x, x.y);
                 }
                 a.rowbuf[v] = val;
@@ -310,7 +325,7 @@ __global__ void __launch_bounds__(kFixBlock) k_phi_fixup(PhiArgs a) {
                 int64_t pos = -1;
                 uint32_t h = 0;
                 for (;;) {
-                    const U4 x = draw(a.seed, static_cast<uint32_t>(k), h++, a.sweep, TAG_REDRAW_BETA, att);
+                    const U4 x = draw(a.seed, static_cast<uint32_t>(k), h++, sweep, TAG_REDRAW_BETA, att);
                     const int g = geo_gap(a.tab.geo, x.x);
                     if (g < 0) {
                         pos += kGeoLen;
@@ -363,13 +378,49 @@ __global__ void __launch_bounds__(kFixBlock) k_phi_fixup(PhiArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(kFixBlock) k_phi_fixup(PhiArgs a) {
+    __shared__ u64 red[kFixBlock / 32];
+    __shared__ u64 s_sum;
+    phi_fixup_chain(a, red, &s_sum);
+}
+
+// Many chains: one CTA per chain.
+__global__ void __launch_bounds__(kFixBlock) k_phi_fixup_multi(const PhiArgs *chains) {
+    __shared__ u64 red[kFixBlock / 32];
+    __shared__ u64 s_sum;
+    phi_fixup_chain(chains[blockIdx.x], red, &s_sum);
+}
+
+// Column offsets of every chain's Phi: one CTA per chain.
+__global__ void k_colptr_scan_multi(const PhiArgs *chains) {
+    const PhiArgs &a = chains[blockIdx.x];
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int64_t n = a.V;
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = t * per, hi = min(n, lo + per);
+    int64_t sum = 0;
+    for (int64_t i = lo; i < hi; ++i) sum += a.nnz_c[i];
+    part[t] = sum;
+    __syncthreads();
+    if (t == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < static_cast<int>(blockDim.x); ++i) { const int64_t v = part[i]; part[i] = run; run += v; }
+        a.col_ptr[n] = run;
+        a.stats[ST_NNZPHI] = static_cast<unsigned long long>(run);
+    }
+    __syncthreads();
+    int64_t run = part[t];
+    for (int64_t i = lo; i < hi; ++i) { a.col_ptr[i] = run; run += a.nnz_c[i]; }
+}
+
 // =================================================== Phi-step: tables
 // Per word (one thread each): phi = fp32(c/S); fixed-point weights q with
 // 24 bits relative to the column maximum (q >= 1); alpha-part masses
 // a = round(q alpha 2^16), A = sigma_a; Vose alias table over a; bitmap of
 // the word's nonzero topics.
-__global__ void k_phi_tables(PhiArgs a) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) {
+__device__ void phi_tables_word(const PhiArgs &a, int v) {
+    {
         const int n = a.nnz_c[v];
         const int64_t src = static_cast<int64_t>(v) * a.K;
         const int64_t out = a.col_ptr[v];
@@ -383,7 +434,7 @@ __global__ void k_phi_tables(PhiArgs a) {
                 bm[wi] = make_uint2(bits, static_cast<uint32_t>(before));
             }
         }
-        if (n == 0) { a.A[v] = 0; continue; }
+        if (n == 0) { a.A[v] = 0; return; }
         double phimax = 0.0;
         for (int j = 0; j < n; ++j) {
             const int k = a.cst_k[src + j];
@@ -418,7 +469,7 @@ __global__ void k_phi_tables(PhiArgs a) {
             a.athr[out + j] = 0xFFFFFFFFu;
             a.atopic[out + j] = a.topic[out + j];
         }
-        if (Asum == 0) continue;
+        if (Asum == 0) return;
         for (int j = 0; j < n; ++j) {
             P[j] *= static_cast<u64>(n);
             if (P[j] < Asum) stk[ns++] = static_cast<uint16_t>(j);
@@ -434,6 +485,17 @@ __global__ void k_phi_tables(PhiArgs a) {
             if (P[l] < Asum) stk[ns++] = static_cast<uint16_t>(l);
             else { stk[n - 1 - nl] = static_cast<uint16_t>(l); ++nl; }
         }
+    }
+}
+
+__global__ void k_phi_tables(PhiArgs a) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) phi_tables_word(a, v);
+}
+
+__global__ void k_phi_tables_multi(const PhiArgs *chains, const int2 *items, int n_items) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_items; i += gridDim.x * blockDim.x) {
+        const int2 it = items[i];
+        phi_tables_word(chains[it.x], it.y);
     }
 }
 
@@ -462,202 +524,263 @@ constexpr int kGather = PULDA_ZGATHER;
 // depends only on the token (its word, Philox words, alias outcome, the
 // word's bitmap) is fetched ahead; the only loads on the critical path are
 // the q values of the intersection, issued together.
+// One document's run: where its tokens live and where its Markov chain is.
+struct DocRun {
+    const int32_t *w;        // word ids, position 0 first
+    int16_t *z;              // topics, updated in place
+    int len;
+    uint64_t seed;
+    int64_t index_base;      // RNG index of position 0
+    uint32_t sweep;          // sweep counter of the pass that starts at `pos`
+    int pos;                 // first position to resample
+    int64_t budget;          // tokens to resample in this call (passes continue past the end)
+    int max_pass_end;        // stop when the pass counter reaches sweep + this many passes
+};
+
+// Resamples the tokens of one document, by one warp, in position order,
+// pass after pass, until `budget` tokens are done or `max_pass_end` passes
+// have been completed.  m (K entries of shared memory) is rebuilt from the
+// current topics first: with positions < pos already resampled in this pass
+// that is exactly m of the sequential sampler at `pos`.  Returns the run's
+// final (sweep, pos) through r.
+__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, u64 &st_ab, u64 &st_min,
+                           u64 &st_zero) {
+    const int lane = threadIdx.x & 31;
+    const int K = a.K;
+    const bool use_bm = a.bitmap != nullptr && a.path != 1;
+    if (r.len == 0 || r.budget <= 0) return;
+    for (int k = lane; k < K; k += 32) m[k] = 0;
+    __syncwarp();
+    for (int i = lane; i < r.len; i += 32) atomicAdd(&m[r.z[i]], 1u);
+    __syncwarp();
+    uint32_t mbits = 0;
+    int kd = 0;
+    if (use_bm) {
+        for (int g = 0; g < a.KW; ++g) {
+            const int k = g * 32 + lane;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k < K && m[k] > 0);
+            if (lane == g) mbits = bal;
+            kd += __popc(bal);
+        }
+    } else {
+        int cnt = 0;
+        for (int k = lane; k < K; k += 32) cnt += m[k] > 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+        kd = cnt;
+    }
+    const uint32_t sweep_end = r.sweep + static_cast<uint32_t>(r.max_pass_end);
+    while (r.budget > 0 && r.sweep != sweep_end) {
+        const int i0 = r.pos;
+        const int64_t left = static_cast<int64_t>(r.len - i0);
+        const int cnt = static_cast<int>(min(static_cast<int64_t>(32), min(left, r.budget)));
+        const int i = i0 + lane;
+        const bool valid = lane < cnt;
+        int wv = 0, zo = 0, nw = 0, ta = 0;
+        int64_t cb = 0;
+        u64 Av = 0;
+        U4 x{0, 0, 0, 0};
+        if (valid) {
+            wv = r.w[i];
+            zo = r.z[i];
+            const uint64_t t = static_cast<uint64_t>(r.index_base + i);
+            x = draw(r.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), r.sweep, TAG_Z, 0);
+            cb = a.col_ptr[wv];
+            nw = static_cast<int>(a.col_ptr[wv + 1] - cb);
+            Av = a.A[wv];
+            if (nw > 0) {
+                const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
+                ta = x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl];
+            }
+        }
+        int znew = zo;
+        uint2 bm_next = make_uint2(0u, 0u);
+        const int v_first = __shfl_sync(0xFFFFFFFFu, wv, 0);    // every lane takes part in the shuffle
+        if (use_bm && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(v_first) * a.KW + lane];
+        for (int tt = 0; tt < cnt; ++tt) {
+            const int v = __shfl_sync(0xFFFFFFFFu, wv, tt);
+            const int kold = __shfl_sync(0xFFFFFFFFu, zo, tt);
+            const int64_t col = __shfl_sync(0xFFFFFFFFu, cb, tt);
+            const int n_w = __shfl_sync(0xFFFFFFFFu, nw, tt);
+            const u64 At = __shfl_sync(0xFFFFFFFFu, Av, tt);
+            const u64 U = (static_cast<u64>(__shfl_sync(0xFFFFFFFFu, x.x, tt)) << 32) |
+                          __shfl_sync(0xFFFFFFFFu, x.y, tt);
+            const int ka = __shfl_sync(0xFFFFFFFFu, ta, tt);
+            const uint2 bm = bm_next;
+            if (use_bm) {     // fetch the next token's bitmap word while this one is drawn
+                const int vn = __shfl_sync(0xFFFFFFFFu, wv, (tt + 1) & 31);
+                if (tt + 1 < cnt && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(vn) * a.KW + lane];
+            }
+            // remove token i: m^{-i}
+            const uint32_t old = m[kold];
+            __syncwarp();
+            if (lane == 0) m[kold] = old - 1;
+            if (old == 1) {
+                --kd;
+                if (use_bm && lane == (kold >> 5)) mbits &= ~(1u << (kold & 31));
+            }
+            __syncwarp();
+            st_min += static_cast<u64>(kd < n_w ? kd : n_w);
+            const bool docside = use_bm && (a.path == 2 || kd < n_w);
+            // per-lane partial sums of q m, in ascending topic order across lanes
+            u64 acc = 0;
+            uint32_t qv[kGather];
+            int bp[kGather];
+            uint32_t rest = 0;         // docside: bits beyond the first kGather
+            int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
+            if (docside) {
+                uint32_t rem = bm.x & mbits;
+#pragma unroll
+                for (int t = 0; t < kGather; ++t) {
+                    bp[t] = -1;
+                    qv[t] = 0;
+                    if (rem) {
+                        const int b = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        bp[t] = b;
+                        qv[t] = a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))];
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < kGather; ++t)
+                    if (bp[t] >= 0) acc += static_cast<u64>(qv[t]) * m[lane * 32 + bp[t]];
+                rest = rem;
+                for (uint32_t bb = rest; bb; bb &= bb - 1) {
+                    const int b = __ffs(bb) - 1;
+                    acc += static_cast<u64>(a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))]) * m[lane * 32 + b];
+                }
+            } else {
+                seg = (n_w + 31) >> 5;
+                seg0 = seg * lane;
+                const int seg1 = min(seg0 + seg, n_w);
+#pragma unroll 4
+                for (int j = seg0; j < seg1; ++j) acc += static_cast<u64>(a.q[col + j]) * m[a.topic[col + j]];
+            }
+            const u64 incl = warp_incl_scan64(acc);
+            const u64 B = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            const u64 T = At + (B << kFracBits);
+            int knew = kold;
+            if (T == 0) {
+                ++st_zero;
+            } else {
+                const u64 rr = __umul64hi(U, T);
+                if (rr < At) {
+                    knew = ka;
+                    ++st_ab;
+                } else {
+                    const u64 rb = (rr - At) >> kFracBits;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, rb < incl);
+                    int found = -1;
+                    if (bal) {
+                        const int L = __ffs(bal) - 1;
+                        int f = -1;
+                        if (lane == L) {
+                            u64 run = incl - acc;
+                            if (docside) {
+#pragma unroll
+                                for (int t = 0; t < kGather; ++t) {
+                                    if (f < 0 && bp[t] >= 0) {
+                                        run += static_cast<u64>(qv[t]) * m[lane * 32 + bp[t]];
+                                        if (rb < run) f = lane * 32 + bp[t];
+                                    }
+                                }
+                                for (uint32_t bb = rest; f < 0 && bb; bb &= bb - 1) {
+                                    const int b = __ffs(bb) - 1;
+                                    run += static_cast<u64>(a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))]) *
+                                           m[lane * 32 + b];
+                                    if (rb < run) f = lane * 32 + b;
+                                }
+                            } else {
+                                const int seg1 = min(seg0 + seg, n_w);
+                                for (int j = seg0; j < seg1; ++j) {
+                                    const int k = a.topic[col + j];
+                                    run += static_cast<u64>(a.q[col + j]) * m[k];
+                                    if (rb < run) { f = k; break; }
+                                }
+                            }
+                        }
+                        found = __shfl_sync(0xFFFFFFFFu, f, L);
+                    }
+                    if (found < 0) {
+                        if (lane == 0) atomicOr(&a.stats[ST_ERROR], ERR_INTERNAL);
+                    } else {
+                        knew = found;
+                    }
+                }
+            }
+            // add token i back with its new topic
+            const uint32_t old2 = m[knew];
+            __syncwarp();
+            if (lane == 0) m[knew] = old2 + 1;
+            if (old2 == 0) {
+                ++kd;
+                if (use_bm && lane == (knew >> 5)) mbits |= 1u << (knew & 31);
+            }
+            __syncwarp();
+            if (lane == tt) znew = knew;
+        }
+        if (valid) r.z[i] = static_cast<int16_t>(znew);
+        st_tok += static_cast<u64>(cnt);
+        r.budget -= cnt;
+        r.pos += cnt;
+        if (r.pos == r.len) { r.pos = 0; r.sweep += 1; }
+        __syncwarp();
+    }
+}
+
+__device__ void flush_z_stats(unsigned long long *stats, u64 st_tok, u64 st_ab, u64 st_min, u64 st_zero) {
+    atomicAdd(&stats[ST_TOKENS], st_tok);
+    atomicAdd(&stats[ST_ABRANCH], st_ab);
+    atomicAdd(&stats[ST_SUMMIN], st_min);
+    atomicAdd(&stats[ST_ZEROMASS], st_zero);
+    atomicAdd(&stats[ST_COUNT + ST_TOKENS], st_tok);
+    atomicAdd(&stats[ST_COUNT + ST_ABRANCH], st_ab);
+    atomicAdd(&stats[ST_COUNT + ST_SUMMIN], st_min);
+    atomicAdd(&stats[ST_COUNT + ST_ZEROMASS], st_zero);
+}
+
+// One chain, one document per warp (dynamically scheduled, longest first),
+// one pass.
 __global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int K = a.K;
-    uint32_t *m = zsm + static_cast<size_t>(warp) * K;
-    const bool use_bm = a.bitmap != nullptr && a.path != 1;
+    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * a.K;
     u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
+    const uint32_t sweep = sweep_of(a);
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.work, 1);
         item = __shfl_sync(0xFFFFFFFFu, item, 0);
         if (item >= a.D) break;
         const int d = a.doc_order[item];
-        const int64_t s = a.doc_off[d], e = a.doc_off[d + 1];
-        if (e == s) continue;
-        for (int k = lane; k < K; k += 32) m[k] = 0;
-        __syncwarp();
-        for (int64_t i = s + lane; i < e; i += 32) atomicAdd(&m[a.z[i]], 1u);
-        __syncwarp();
-        uint32_t mbits = 0;
-        int kd = 0;
-        if (use_bm) {
-            for (int g = 0; g < a.KW; ++g) {
-                const int k = g * 32 + lane;
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k < K && m[k] > 0);
-                if (lane == g) mbits = bal;
-                kd += __popc(bal);
-            }
-        } else {
-            int cnt = 0;
-            for (int k = lane; k < K; k += 32) cnt += m[k] > 0;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-            kd = cnt;
-        }
-        for (int64_t i0 = s; i0 < e; i0 += 32) {
-            const int64_t i = i0 + lane;
-            const bool valid = i < e;
-            int wv = 0, zo = 0, nw = 0, ta = 0;
-            int64_t cb = 0;
-            u64 Av = 0;
-            U4 x{0, 0, 0, 0};
-            if (valid) {
-                wv = a.w[i];
-                zo = a.z[i];
-                const uint64_t t = static_cast<uint64_t>(a.index_base + i);
-                x = draw(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), a.sweep, TAG_Z, 0);
-                cb = a.col_ptr[wv];
-                nw = static_cast<int>(a.col_ptr[wv + 1] - cb);
-                Av = a.A[wv];
-                if (nw > 0) {
-                    const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
-                    ta = x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl];
-                }
-            }
-            int znew = zo;
-            const int cnt = static_cast<int>(min(static_cast<int64_t>(32), e - i0));
-            uint2 bm_next = make_uint2(0u, 0u);
-            const int v_first = __shfl_sync(0xFFFFFFFFu, wv, 0);    // every lane takes part in the shuffle
-            if (use_bm && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(v_first) * a.KW + lane];
-            for (int tt = 0; tt < cnt; ++tt) {
-                const int v = __shfl_sync(0xFFFFFFFFu, wv, tt);
-                const int kold = __shfl_sync(0xFFFFFFFFu, zo, tt);
-                const int64_t col = __shfl_sync(0xFFFFFFFFu, cb, tt);
-                const int n_w = __shfl_sync(0xFFFFFFFFu, nw, tt);
-                const u64 At = __shfl_sync(0xFFFFFFFFu, Av, tt);
-                const u64 U = (static_cast<u64>(__shfl_sync(0xFFFFFFFFu, x.x, tt)) << 32) |
-                              __shfl_sync(0xFFFFFFFFu, x.y, tt);
-                const int ka = __shfl_sync(0xFFFFFFFFu, ta, tt);
-                const uint2 bm = bm_next;
-                if (use_bm) {     // fetch the next token's bitmap word while this one is drawn
-                    const int vn = __shfl_sync(0xFFFFFFFFu, wv, (tt + 1) & 31);
-                    if (tt + 1 < cnt && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(vn) * a.KW + lane];
-                }
-                // remove token i: m^{-i}
-                const uint32_t old = m[kold];
-                __syncwarp();
-                if (lane == 0) m[kold] = old - 1;
-                if (old == 1) {
-                    --kd;
-                    if (use_bm && lane == (kold >> 5)) mbits &= ~(1u << (kold & 31));
-                }
-                __syncwarp();
-                st_min += static_cast<u64>(kd < n_w ? kd : n_w);
-                const bool docside = use_bm && (a.path == 2 || kd < n_w);
-                // per-lane partial sums of q m, in ascending topic order across lanes
-                u64 acc = 0;
-                uint32_t qv[kGather];
-                int bp[kGather];
-                uint32_t rest = 0;         // docside: bits beyond the first kGather
-                int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
-                if (docside) {
-                    uint32_t rem = bm.x & mbits;
-#pragma unroll
-                    for (int t = 0; t < kGather; ++t) {
-                        bp[t] = -1;
-                        qv[t] = 0;
-                        if (rem) {
-                            const int b = __ffs(rem) - 1;
-                            rem &= rem - 1;
-                            bp[t] = b;
-                            qv[t] = a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))];
-                        }
-                    }
-#pragma unroll
-                    for (int t = 0; t < kGather; ++t)
-                        if (bp[t] >= 0) acc += static_cast<u64>(qv[t]) * m[lane * 32 + bp[t]];
-                    rest = rem;
-                    for (uint32_t bb = rest; bb; bb &= bb - 1) {
-                        const int b = __ffs(bb) - 1;
-                        acc += static_cast<u64>(a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))]) * m[lane * 32 + b];
-                    }
-                } else {
-                    seg = (n_w + 31) >> 5;
-                    seg0 = seg * lane;
-                    const int seg1 = min(seg0 + seg, n_w);
-#pragma unroll 4
-                    for (int j = seg0; j < seg1; ++j) acc += static_cast<u64>(a.q[col + j]) * m[a.topic[col + j]];
-                }
-                const u64 incl = warp_incl_scan64(acc);
-                const u64 B = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                const u64 T = At + (B << kFracBits);
-                int knew = kold;
-                if (T == 0) {
-                    ++st_zero;
-                } else {
-                    const u64 r = __umul64hi(U, T);
-                    if (r < At) {
-                        knew = ka;
-                        ++st_ab;
-                    } else {
-                        const u64 rb = (r - At) >> kFracBits;
-                        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, rb < incl);
-                        int found = -1;
-                        if (bal) {
-                            const int L = __ffs(bal) - 1;
-                            int f = -1;
-                            if (lane == L) {
-                                u64 run = incl - acc;
-                                if (docside) {
-#pragma unroll
-                                    for (int t = 0; t < kGather; ++t) {
-                                        if (f < 0 && bp[t] >= 0) {
-                                            run += static_cast<u64>(qv[t]) * m[lane * 32 + bp[t]];
-                                            if (rb < run) f = lane * 32 + bp[t];
-                                        }
-                                    }
-                                    for (uint32_t bb = rest; f < 0 && bb; bb &= bb - 1) {
-                                        const int b = __ffs(bb) - 1;
-                                        run += static_cast<u64>(a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))]) *
-                                               m[lane * 32 + b];
-                                        if (rb < run) f = lane * 32 + b;
-                                    }
-                                } else {
-                                    const int seg1 = min(seg0 + seg, n_w);
-                                    for (int j = seg0; j < seg1; ++j) {
-                                        const int k = a.topic[col + j];
-                                        run += static_cast<u64>(a.q[col + j]) * m[k];
-                                        if (rb < run) { f = k; break; }
-                                    }
-                                }
-                            }
-                            found = __shfl_sync(0xFFFFFFFFu, f, L);
-                        }
-                        if (found < 0) {
-                            if (lane == 0) atomicOr(&a.stats[ST_ERROR], ERR_INTERNAL);
-                        } else {
-                            knew = found;
-                        }
-                    }
-                }
-                // add token i back with its new topic
-                const uint32_t old2 = m[knew];
-                __syncwarp();
-                if (lane == 0) m[knew] = old2 + 1;
-                if (old2 == 0) {
-                    ++kd;
-                    if (use_bm && lane == (knew >> 5)) mbits |= 1u << (knew & 31);
-                }
-                __syncwarp();
-                if (lane == tt) znew = knew;
-            }
-            if (valid) a.z[i] = static_cast<int16_t>(znew);
-            st_tok += static_cast<u64>(cnt);
-        }
+        const int64_t s = a.doc_off[d];
+        DocRun r{a.w + s, a.z + s, static_cast<int>(a.doc_off[d + 1] - s), a.seed, a.index_base + s, sweep, 0,
+                 a.doc_off[d + 1] - s, 1};
+        z_doc_warp(a, m, r, st_tok, st_ab, st_min, st_zero);
     }
-    if (lane == 0) {
-        atomicAdd(&a.stats[ST_TOKENS], st_tok);
-        atomicAdd(&a.stats[ST_ABRANCH], st_ab);
-        atomicAdd(&a.stats[ST_SUMMIN], st_min);
-        atomicAdd(&a.stats[ST_ZEROMASS], st_zero);
-        atomicAdd(&a.stats[ST_COUNT + ST_TOKENS], st_tok);
-        atomicAdd(&a.stats[ST_COUNT + ST_ABRANCH], st_ab);
-        atomicAdd(&a.stats[ST_COUNT + ST_SUMMIN], st_min);
-        atomicAdd(&a.stats[ST_COUNT + ST_ZEROMASS], st_zero);
+    if (lane == 0) flush_z_stats(a.stats, st_tok, st_ab, st_min, st_zero);
+}
+
+// Many chains: the work list holds (chain, document) pairs, longest first
+// across all chains; shared memory per warp is sized for the largest K.
+__global__ void __launch_bounds__(256, 2) k_z_step_multi(const ZArgs *chains, const int2 *items,
+                                                                        int n_items, int *work, int kmax) {
+    extern __shared__ uint32_t zsm[];
+    const int lane = threadIdx.x & 31;
+    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * kmax;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(work, 1);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item >= n_items) break;
+        const int2 it = items[item];
+        const ZArgs &a = chains[it.x];
+        const int64_t s = a.doc_off[it.y];
+        DocRun r{a.w + s, a.z + s, static_cast<int>(a.doc_off[it.y + 1] - s), a.seed, a.index_base + s, sweep_of(a),
+                 0, a.doc_off[it.y + 1] - s, 1};
+        u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
+        z_doc_warp(a, m, r, st_tok, st_ab, st_min, st_zero);
+        if (lane == 0) flush_z_stats(a.stats, st_tok, st_ab, st_min, st_zero);
     }
 }
 
@@ -952,6 +1075,19 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
     }
 }
 
+// ============================================================ batches
+// Start of a sweep of many chains (one CTA): advance the shared sweep counter
+// and clear every chain's row sums, per-sweep counters and the work queues.
+__global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_t *sweep, int *work) {
+    if (threadIdx.x == 0) *sweep += 1u;
+    if (threadIdx.x < 4) work[threadIdx.x] = 0;
+    for (int c = 0; c < n_chains; ++c) {
+        const PhiArgs &a = chains[c];
+        for (int k = threadIdx.x; k < a.K; k += blockDim.x) a.S[k] = 0;
+        for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) a.stats[i] = 0;
+    }
+}
+
 // ============================================================== exports
 // m_{d,k}, dense row-major [D, K]: one warp per document.
 __global__ void k_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K, int32_t *m_dk) {
@@ -1087,6 +1223,32 @@ void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st) {
 
 void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st) {
     k_z_step<<<grid, 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(a);
+}
+
+void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
+    k_batch_begin_sweep<<<1, 256, 0, st>>>(b.phi, b.n_chains, b.sweep, b.work);
+    k_phi_counts_multi<<<b.phi_grid, kPhiBlock, phi_counts_smem(b.kmax), st>>>(b.phi, b.phi_items, b.n_phi_items,
+                                                                                b.work, b.kmax, true);
+    k_phi_fixup_multi<<<b.n_chains, kFixBlock, 0, st>>>(b.phi);
+    k_colptr_scan_multi<<<b.n_chains, 1024, 0, st>>>(b.phi);
+    k_phi_tables_multi<<<(b.n_phi_items + 127) / 128, 128, 0, st>>>(b.phi, b.phi_items, b.n_phi_items);
+    k_z_step_multi<<<b.z_grid, 32 * b.z_warps, sizeof(uint32_t) * static_cast<size_t>(b.kmax) * b.z_warps, st>>>(
+        b.z, b.z_items, b.n_z_items, b.work + 1, b.kmax);
+}
+
+int batch_phi_blocks_per_sm(int kmax) {
+    allow_dynamic_smem(k_phi_counts_multi);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_phi_counts_multi, kPhiBlock, phi_counts_smem(kmax));
+    return n > 0 ? n : 1;
+}
+
+int batch_z_blocks_per_sm(int kmax, int warps) {
+    allow_dynamic_smem(k_z_step_multi);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_z_step_multi, 32 * warps,
+                                                  sizeof(uint32_t) * static_cast<size_t>(kmax) * warps);
+    return n > 0 ? n : 1;
 }
 
 void launch_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K, int32_t *m_dk, cudaStream_t st) {

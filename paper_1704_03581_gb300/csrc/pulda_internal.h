@@ -63,6 +63,7 @@ struct PhiArgs {
     int K, V;
     uint64_t seed;
     uint32_t sweep;
+    const uint32_t *sweep_ptr;  // if set, the sweep counter is read here (graph replay)
     const int32_t *perm;        // [N] token ids grouped by word
     const int64_t *word_off;    // [V+1]
     const int32_t *word_order;  // [V] words by decreasing token count
@@ -102,6 +103,7 @@ struct ZArgs {
     int K, KW;
     uint64_t seed;
     uint32_t sweep;
+    const uint32_t *sweep_ptr;  // if set, the sweep counter is read here (graph replay)
     int64_t index_base;         // RNG index of token 0
     int path;                   // 0 auto, 1 column, 2 document topics
     int *work;
@@ -130,6 +132,25 @@ void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st);
 size_t z_groups_smem(int K);
 int z_groups_blocks_per_sm(int K);
 int phi_counts_blocks_per_sm(int K);
+
+// One sweep of many chains: six launches, every kernel over all chains'
+// work items.  Pointers are device memory.
+struct BatchLaunch {
+    const PhiArgs *phi;          // [n_chains], sweep_ptr = sweep
+    const ZArgs *z;              // [n_chains], sweep_ptr = sweep
+    int n_chains;
+    const int2 *phi_items;       // (chain, word), most tokens first
+    int n_phi_items;
+    const int2 *z_items;         // (chain, document), longest first
+    int n_z_items;
+    uint32_t *sweep;             // shared sweep counter, advanced by the first launch
+    int *work;                   // [4] dynamic work queues
+    int kmax;                    // largest K of the chains
+    int phi_grid, z_grid, z_warps;
+};
+void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st);
+int batch_phi_blocks_per_sm(int kmax);
+int batch_z_blocks_per_sm(int kmax, int warps);
 
 // What another translation unit needs to launch the z-step on a handle's
 // current Phi (api.cpp).

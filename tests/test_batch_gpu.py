@@ -1,0 +1,78 @@
+"""Batched chains: every chain of a batch equals, bit for bit, the chain a
+single handle with the same arguments runs (and hence the oracle), whatever
+the z-step CTA size the autotuner picks and across CUDA-graph replays."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1704_03581_gb300 import build
+    build.build()
+
+
+def make_chains():
+    """Uneven chains: K from 1 to 1500 (bitmap and column paths, the largest K
+    sizing shared memory), V, D, lengths, alpha, beta and seeds all differ."""
+    rng = np.random.default_rng(3)
+    out = []
+    for i, (K, V, D, mean) in enumerate([(1, 50, 10, 5), (37, 400, 300, 40), (100, 2000, 120, 300),
+                                         (500, 3000, 60, 150), (1024, 800, 40, 90), (1500, 1200, 80, 60)]):
+        lengths = rng.poisson(mean, size=D)
+        lengths[0] = 0
+        off = np.zeros(D + 1, np.int64)
+        np.cumsum(lengths, out=off[1:])
+        p = (1.0 + np.arange(V)) ** -1.0
+        w = rng.choice(V, size=int(off[-1]), p=p / p.sum()).astype(np.int32)
+        alpha = rng.uniform(0.05, 0.5, K).astype(np.float32)
+        out.append(dict(w=w, doc_off=off, K=K, V=V, alpha=alpha, beta=float(rng.uniform(0.005, 0.05)), seed=100 + i))
+    return out
+
+
+@pytest.mark.parametrize("warps", [0, 4])
+def test_batch_equals_single_chains(warps):
+    import paper_1704_03581_gb300 as P
+    chains = make_chains()
+    b = P.Batch(chains, warps_per_block=warps)
+    b.sweep(2)
+    b.sweep(4)            # tuning sweeps, then graph replays across two calls
+    w, tuned = b.tuning()
+    assert tuned and w in (2, 4, 8)
+    for i, c in enumerate(chains):
+        s = P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"])
+        s.sweep(6)
+        assert np.array_equal(b.z(i), s.z()), f"chain {i} differs from its single-chain run"
+        sb, ss = b.stats(i), s.stats()
+        for k in ("tokens", "a_branch", "sum_min", "zero_mass", "dead_rows", "nnz_phi", "sweep",
+                  "cum_tokens", "cum_a_branch", "cum_sum_min"):
+            assert sb[k] == ss[k], (i, k, sb[k], ss[k])
+        s.close()
+    b.close()
+
+
+def test_batch_chain_matches_oracle():
+    import paper_1704_03581_gb300 as P
+    chains = make_chains()
+    b = P.Batch(chains)
+    b.sweep(5)
+    for i in (1, 3):
+        c = chains[i]
+        ch = O.Chain(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"]).sweep(5)
+        assert np.array_equal(b.z(i), ch.z), f"chain {i} differs from the oracle"
+    b.close()
+
+
+def test_batch_reports_the_failing_chain():
+    import paper_1704_03581_gb300 as P
+    chains = make_chains()[:3]
+    chains[2] = dict(chains[2], V=5)          # word ids beyond V
+    with pytest.raises(P.PuldaError) as e:
+        P.Batch(chains)
+    assert "chain 2" in str(e.value)
