@@ -55,7 +55,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--docs-per-warp", type=int, default=0, help="z-step documents per warp: 0 auto, 1 or 4")
-    ap.add_argument("--form", choices=["sweep", "batched"], default="sweep",
+    ap.add_argument("--rates", type=str, default="2000,5000,10000,20000,50000",
+                    help="serving: Poisson arrival rates, documents per second")
+    ap.add_argument("--serve-seconds", type=float, default=1.5, help="serving: arrival window per rate")
+    ap.add_argument("--slice", type=int, default=2048, help="serving: tokens a request advances per launch")
+    ap.add_argument("--serve-sweeps", type=int, default=50, help="serving: z-sweeps per request")
+    ap.add_argument("--plain-requests", type=int, default=150,
+                    help="serving: requests the one-at-a-time baseline serves (the first ones, at the lowest rate)")
+    ap.add_argument("--form", choices=["sweep", "batched", "serving"], default="sweep",
                     help="sweep: the large corpus (the headline line); batched: 32 uneven chains in one graph "
                          "launch per sweep against 32 sequential single-chain runs")
     ap.add_argument("--batch-scale", type=float, default=0.25,
@@ -382,6 +389,101 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Fold-in requests (lognormal(300, 1.2) tokens clipped to [10, 20000], 50
+    sweeps each) arriving as a Poisson process, served against the large
+    model's Phi: continuous batching vs one request at a time."""
+    import threading
+    import torch
+    import paper_1704_03581_gb300 as P
+    from paper_1704_03581_gb300 import synth
+
+    corpus = synth.large()
+    model = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=0)
+    model.sweep(30)
+    model.sync()
+    rates = [float(r) for r in args.rates.split(",")]
+    n_max = int(max(rates) * args.serve_seconds) + args.plain_requests
+    reqs, _ = synth.serving_requests(n_max, corpus.V, rate=1.0)
+    lens = np.diff(reqs.doc_off)
+    rng = np.random.default_rng(11)
+    results = []
+    for rate in rates:
+        n = int(rate * args.serve_seconds)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        srv = P.Server(model, token_budget=1 << 25, max_slots=8192, slice_tokens=args.slice)
+        done = {}
+        stop = threading.Event()
+
+        def poller():
+            deadline = time.monotonic() + 300.0
+            while (not stop.is_set() or len(done) < n) and time.monotonic() < deadline:
+                for r in srv.poll(max_results=4096, timeout_ms=50):
+                    done[r["req_id"]] = r
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.monotonic_ns()
+        i = 0
+        while i < n:
+            now = (time.monotonic_ns() - t0) / 1e9
+            while i < n and arrivals[i] <= now:
+                a, b = int(reqs.doc_off[i]), int(reqs.doc_off[i + 1])
+                srv.submit(i, 7919 * i + 1, reqs.w[a:b], args.serve_sweeps)
+                i += 1
+            if i < n:
+                time.sleep(max(0.0, min(arrivals[i] - now, 0.001)))
+        stop.set()
+        th.join()
+        t_end = max(r["done_ns"] for r in done.values())
+        lat = np.array([(done[j]["done_ns"] - t0) / 1e6 - arrivals[j] * 1e3 for j in range(n)])
+        toks = int(lens[:n].sum())
+        results.append({"rate_docs_per_s": rate, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99)),
+                        "docs_per_s": n / ((t_end - t0) / 1e9),
+                        "token_sweeps_per_s": toks * args.serve_sweeps / ((t_end - t0) / 1e9)})
+        # a sample of requests re-run alone must give the same topics
+        check = list(range(0, n, max(1, n // 20)))[:20]
+        same = True
+        for j in check:
+            a, b = int(reqs.doc_off[j]), int(reqs.doc_off[j + 1])
+            alone = model.infer(reqs.w[a:b], np.array([0, b - a]), args.serve_sweeps, seed=7919 * j + 1)
+            same &= bool(np.array_equal(alone, done[j]["z"]))
+        results[-1]["identical_to_alone"] = same
+        srv.close()
+    # one request at a time (pulda_infer), the first requests at the lowest rate
+    rate = min(rates)
+    m = args.plain_requests
+    arrivals = np.cumsum(np.random.default_rng(12).exponential(1.0 / rate, size=m))
+    t0 = time.monotonic_ns()
+    lat = []
+    for j in range(m):
+        now = (time.monotonic_ns() - t0) / 1e9
+        if arrivals[j] > now:
+            time.sleep(arrivals[j] - now)
+        a, b = int(reqs.doc_off[j]), int(reqs.doc_off[j + 1])
+        model.infer(reqs.w[a:b], np.array([0, b - a]), args.serve_sweeps, seed=7919 * j + 1)
+        lat.append((time.monotonic_ns() - t0) / 1e6 - arrivals[j] * 1e3)
+    t_plain = (time.monotonic_ns() - t0) / 1e9
+    plain = {"rate_docs_per_s": rate, "requests": m, "p50_ms": float(np.percentile(lat, 50)),
+             "p99_ms": float(np.percentile(lat, 99)), "docs_per_s": m / t_plain,
+             "token_sweeps_per_s": int(lens[:m].sum()) * args.serve_sweeps / t_plain}
+    model.close()
+    low = results[0]
+    line = {
+        "metric": "serving p50/p99 vs plain (fold-in, 50 sweeps per request, K=1000, V=100000)",
+        "value": low["p99_ms"], "unit": "ms (p99 at the lowest rate)", "n_gpus": 1, "steps": len(rates),
+        "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic requests, lognormal(300, 1.2) tokens clipped to [10, 20000], Poisson arrivals",
+        "config": {"workload": "fold-in against the large model's Phi after 30 sweeps", "slice_tokens": args.slice,
+                   "sweeps_per_request": args.serve_sweeps},
+        "continuous_batching": results,
+        "one_at_a_time": plain,
+        "p99_speedup_at_lowest_rate": plain["p99_ms"] / low["p99_ms"],
+        "throughput_speedup": max(r["docs_per_s"] for r in results) / plain["docs_per_s"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -397,11 +499,11 @@ def main():
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if args.form == "batched":
+    if args.form in ("batched", "serving"):
         from paper_1704_03581_gb300 import build
         build.build()
         if rank == 0:
-            run_batched(args)
+            (run_batched if args.form == "batched" else run_serving)(args)
         return
     if world > 1:
         import torch.distributed as dist

@@ -220,6 +220,54 @@ pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *tuned
 const char *pulda_batch_last_error(const pulda_batch *b);
 void pulda_batch_free(pulda_batch *b);
 
+/* ---------------------------------------------------------------- serving
+ * A continuous-batching fold-in server on a handle's current Phi (Algorithm
+ * 2's z-step with Phi held fixed, on documents that arrive over time).  A
+ * worker thread admits waiting requests while a slot and a contiguous range
+ * of the token arena are free (memory-based admission, first come first
+ * served), advances every admitted request by up to `slice_tokens` tokens per
+ * launch (one warp per request, sweeps continuing within a launch) and copies
+ * finished topics out.  A request's result equals pulda_infer on that
+ * document alone with the same seed and n_sweeps: its random streams are keyed
+ * by its own seed and token positions, never by its neighbours.
+ * Do not run pulda_sweep / pulda_phi_step on the handle while a server is open
+ * on it (Phi would change under the requests). */
+typedef struct pulda_server pulda_server;
+
+typedef struct {
+    uint64_t req_id;
+    int32_t status;      /* PULDA_OK, or PULDA_ERR_CUDA if a kernel reported an error */
+    int32_t len;         /* tokens */
+    int64_t submit_ns;   /* CLOCK_MONOTONIC at pulda_serve_submit */
+    int64_t done_ns;     /* CLOCK_MONOTONIC when z_out had been written */
+} pulda_result;
+
+/* pulda_serve_open -- token_budget: tokens the arena holds (6 bytes each on
+ * the device); max_slots: requests in flight; slice_tokens: tokens a request
+ * advances per launch.  Errors: PULDA_ERR_INVALID (no Phi yet, a size < 1),
+ * PULDA_ERR_OOM, PULDA_ERR_CUDA. */
+pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max_slots, int64_t slice_tokens,
+                              pulda_server **out);
+/* pulda_serve_submit -- enqueue one document (thread safe).  words_host
+ * int32[len] is copied; z_out_host int16[len] receives the topics and must stay
+ * valid until the request is returned by pulda_serve_poll.  Errors:
+ * PULDA_ERR_INVALID (len < 1 or beyond the arena, ids outside [0, V),
+ * n_sweeps < 1, server closing), PULDA_ERR_BUSY (2^22 requests waiting),
+ * PULDA_ERR_CUDA (the worker failed). */
+pulda_status pulda_serve_submit(pulda_server *s, uint64_t req_id, uint64_t seed, const int32_t *words_host,
+                                int32_t len, int32_t n_sweeps, int16_t *z_out_host);
+/* pulda_serve_poll -- wait up to timeout_ms for finished requests and return
+ * up to max_results of them (thread safe).  PULDA_ERR_TIMEOUT if none finished
+ * in time; the wait is bounded, never indefinite. */
+pulda_status pulda_serve_poll(pulda_server *s, pulda_result *out, int32_t max_results, int32_t *n_out,
+                              int32_t timeout_ms);
+/* pulda_serve_pending -- requests waiting for admission, requests in flight,
+ * and launches so far (any pointer may be NULL). */
+pulda_status pulda_serve_pending(pulda_server *s, int64_t *waiting, int64_t *running, int64_t *launches);
+/* pulda_serve_close -- stop accepting, finish every submitted request, release
+ * the server.  Returns the worker's error status, if any. */
+pulda_status pulda_serve_close(pulda_server *s);
+
 /* pulda_stats -- counters of the most recent sweep (synchronises). */
 pulda_status pulda_stats(pulda_handle *h, pulda_sweep_stats *out);
 

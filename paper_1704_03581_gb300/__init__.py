@@ -26,7 +26,8 @@ EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "puld
             "pulda_get_z_dev", "pulda_set_z", "pulda_get_counts", "pulda_get_phi", "pulda_get_word_tables",
             "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_last_error", "pulda_free",
             "pulda_batch_init", "pulda_batch_sweep", "pulda_batch_sync", "pulda_batch_get_z", "pulda_batch_stats",
-            "pulda_batch_tuning", "pulda_batch_last_error", "pulda_batch_free"]
+            "pulda_batch_tuning", "pulda_batch_last_error", "pulda_batch_free",
+            "pulda_serve_open", "pulda_serve_submit", "pulda_serve_poll", "pulda_serve_pending", "pulda_serve_close"]
 
 
 class PuldaError(RuntimeError):
@@ -85,6 +86,11 @@ def lib() -> ctypes.CDLL:
             "pulda_batch_get_z": [P, i32, P],
             "pulda_batch_stats": [P, i32, P],
             "pulda_batch_tuning": [P, P, P],
+            "pulda_serve_open": [P, i64, i32, i64, P],
+            "pulda_serve_submit": [P, u64, u64, P, i32, i32, P],
+            "pulda_serve_poll": [P, P, i32, P, i32],
+            "pulda_serve_pending": [P, P, P, P],
+            "pulda_serve_close": [P],
         })
         for name, args in sig.items():
             f = getattr(L, name)
@@ -399,3 +405,79 @@ class Batch:
 
     def tuning(self):
         return pulda_batch_tuning(self.b)
+
+
+# ------------------------------------------------------------------ serving
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("len", ctypes.c_int32),
+                ("submit_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64)]
+
+
+def pulda_serve_open(h, token_budget: int, max_slots: int, slice_tokens: int) -> int:
+    s = ctypes.c_void_p()
+    _check(h, lib().pulda_serve_open(h, token_budget, max_slots, slice_tokens, ctypes.byref(s)))
+    return s.value
+
+
+def pulda_serve_submit(s, req_id: int, seed: int, words: np.ndarray, n_sweeps: int, z_out: np.ndarray):
+    st = lib().pulda_serve_submit(s, req_id, int(seed) & (2 ** 64 - 1), _ptr(words), int(words.shape[0]), n_sweeps,
+                                  _ptr(z_out))
+    if st != PULDA_OK:
+        raise PuldaError(st, "submit rejected")
+
+
+def pulda_serve_poll(s, max_results: int = 1024, timeout_ms: int = 100) -> list[dict]:
+    buf = (ServeResult * max_results)()
+    n = ctypes.c_int32(0)
+    st = lib().pulda_serve_poll(s, buf, max_results, ctypes.byref(n), timeout_ms)
+    if st == -4:          # PULDA_ERR_TIMEOUT
+        return []
+    if st != PULDA_OK:
+        raise PuldaError(st, "serving failed")
+    return [dict(req_id=int(r.req_id), status=int(r.status), len=int(r.len), submit_ns=int(r.submit_ns),
+                 done_ns=int(r.done_ns)) for r in buf[:n.value]]
+
+
+def pulda_serve_pending(s) -> tuple[int, int, int]:
+    a, b, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    st = lib().pulda_serve_pending(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if st != PULDA_OK:
+        raise PuldaError(st, "serve_pending failed")
+    return a.value, b.value, c.value
+
+
+def pulda_serve_close(s):
+    st = lib().pulda_serve_close(s)
+    if st != PULDA_OK:
+        raise PuldaError(st, "server reported an error")
+
+
+class Server:
+    """Continuous-batching fold-in against a sampler's current Phi."""
+
+    def __init__(self, sampler: Sampler, token_budget: int = 1 << 24, max_slots: int = 4096,
+                 slice_tokens: int = 4096):
+        self.s = pulda_serve_open(sampler.h, token_budget, max_slots, slice_tokens)
+        self._keep = {}
+
+    def submit(self, req_id: int, seed: int, words, n_sweeps: int) -> np.ndarray:
+        w = np.ascontiguousarray(words, dtype=np.int32)
+        z = np.zeros(w.shape[0], np.int16)
+        self._keep[req_id] = (w, z)
+        pulda_serve_submit(self.s, req_id, seed, w, n_sweeps, z)
+        return z
+
+    def poll(self, max_results: int = 1024, timeout_ms: int = 100) -> list[dict]:
+        out = pulda_serve_poll(self.s, max_results, timeout_ms)
+        for r in out:
+            r["z"] = self._keep.pop(r["req_id"])[1]
+        return out
+
+    def pending(self):
+        return pulda_serve_pending(self.s)
+
+    def close(self):
+        if self.s:
+            pulda_serve_close(self.s)
+            self.s = None

@@ -78,7 +78,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
                 raise RuntimeError(f"nvcc failed on {cmd[-3]}")
     if force or jobs or _stale(lib, objs):
         tmp = lib + f".{os.getpid()}.tmp"
-        cmd = [nvcc, "-gencode", GENCODE, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc, "-gencode", GENCODE, "-shared", "-o", tmp, *objs, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)

@@ -1088,6 +1088,49 @@ __global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_
     }
 }
 
+// ============================================================ serving
+// One step of the fold-in server: each active slot (a request's document,
+// resampled with Phi fixed) advances by up to `slice` tokens, continuing
+// across passes, one warp per slot.  A slot whose pass counter is 0 first
+// gets its uniform initial topics (counter 0, as pulda_infer).  The slot's
+// (pass, position) is written back for the host's completion check.
+__global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_serve_step(ZArgs a, ServeSlot *slots, const int32_t *active,
+                                                                     int n_active, const int32_t *arena_w,
+                                                                     int16_t *arena_z, int64_t slice, int *work) {
+    extern __shared__ uint32_t zsm[];
+    const int lane = threadIdx.x & 31;
+    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * a.K;
+    u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(work, 1);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item >= n_active) break;
+        const int idx = active[item];
+        const ServeSlot sl = slots[idx];
+        int16_t *z = arena_z + sl.off;
+        uint32_t sweep = sl.sweep;
+        int pos = sl.pos;
+        if (sweep == 0) {
+            for (int i = lane; i < sl.len; i += 32) {
+                const U4 x = draw(sl.seed, static_cast<uint32_t>(i), 0u, 0u, TAG_INIT, 0);
+                z[i] = static_cast<int16_t>(__umulhi(x.x, static_cast<uint32_t>(a.K)));
+            }
+            __syncwarp();
+            sweep = 1;
+            pos = 0;
+        }
+        DocRun r{arena_w + sl.off, z, sl.len, sl.seed, 0, sweep, pos, slice,
+                 static_cast<int>(sl.sweep_end - sweep)};
+        z_doc_warp(a, m, r, st_tok, st_ab, st_min, st_zero);
+        if (lane == 0) {
+            slots[idx].sweep = r.sweep;
+            slots[idx].pos = r.pos;
+        }
+    }
+    if (lane == 0) flush_z_stats(a.stats, st_tok, st_ab, st_min, st_zero);
+}
+
 // ============================================================== exports
 // m_{d,k}, dense row-major [D, K]: one warp per document.
 __global__ void k_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K, int32_t *m_dk) {
@@ -1248,6 +1291,22 @@ int batch_z_blocks_per_sm(int kmax, int warps) {
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_z_step_multi, 32 * warps,
                                                   sizeof(uint32_t) * static_cast<size_t>(kmax) * warps);
+    return n > 0 ? n : 1;
+}
+
+void launch_serve_step(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active, const int32_t *arena_w,
+                       int16_t *arena_z, int64_t slice, int *work, int warps_per_block, int grid, cudaStream_t st) {
+    if (n_active <= 0) return;
+    cudaMemsetAsync(work, 0, sizeof(int), st);
+    const int need = (n_active + warps_per_block - 1) / warps_per_block;
+    k_serve_step<<<std::min(grid, need), 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(
+        a, slots, active, n_active, arena_w, arena_z, slice, work);
+}
+
+int serve_blocks_per_sm(int K, int warps_per_block) {
+    allow_dynamic_smem(k_serve_step);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_serve_step, 32 * warps_per_block, z_step_smem(K, warps_per_block));
     return n > 0 ? n : 1;
 }
 

@@ -152,6 +152,19 @@ void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st);
 int batch_phi_blocks_per_sm(int kmax);
 int batch_z_blocks_per_sm(int kmax, int warps);
 
+// A request being folded in by the server (device slot table entry).
+struct ServeSlot {
+    int64_t off;          // first token in the arena
+    int32_t len;          // tokens (>= 1)
+    int32_t pos;          // next position of the current pass
+    uint32_t sweep;       // current pass; 0 = initial topics not drawn yet
+    uint32_t sweep_end;   // 1 + sweeps requested: done when sweep reaches it
+    uint64_t seed;        // the request's Philox key
+};
+void launch_serve_step(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active, const int32_t *arena_w,
+                       int16_t *arena_z, int64_t slice, int *work, int warps_per_block, int grid, cudaStream_t st);
+int serve_blocks_per_sm(int K, int warps_per_block);
+
 // What another translation unit needs to launch the z-step on a handle's
 // current Phi (api.cpp).
 struct HandleView {

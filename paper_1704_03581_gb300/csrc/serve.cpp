@@ -1,0 +1,333 @@
+// Continuous-batching fold-in server: new documents, of uneven length,
+// resampled against a fixed Phi (Algorithm 2's z-step with Phi held) as they
+// arrive.  A worker thread owns the GPU side: it admits waiting requests while
+// a slot and a contiguous range of the token arena are free (memory-based
+// admission, first come first served), advances every admitted request by up
+// to `slice` tokens per launch -- one warp per request, passes continuing
+// within the launch -- and hands finished requests back.  Each request's
+// random streams are keyed by its own seed and token positions, so its result
+// does not depend on which other requests shared the GPU with it: it equals
+// pulda_infer on that document alone.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <time.h>
+
+#include "../../include/pulda.h"
+#include "handle.h"
+#include "pulda_internal.h"
+
+using namespace pulda;
+
+namespace {
+
+int64_t now_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return static_cast<int64_t>(ts.tv_sec) * 1000000000LL + ts.tv_nsec;
+}
+
+struct Request {
+    uint64_t id = 0, seed = 0;
+    std::vector<int32_t> words;
+    int32_t n_sweeps = 0;
+    int16_t *z_out = nullptr;
+    int64_t submit_ns = 0;
+    int64_t off = -1;
+};
+
+// First-fit allocator of contiguous token ranges of the arena.
+class Arena {
+public:
+    explicit Arena(int64_t n) { if (n > 0) free_[0] = n; }
+    int64_t alloc(int64_t len) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= len) {
+                const int64_t off = it->first, rest = it->second - len;
+                free_.erase(it);
+                if (rest > 0) free_[off + len] = rest;
+                return off;
+            }
+        }
+        return -1;
+    }
+    void release(int64_t off, int64_t len) {
+        auto it = free_.emplace(off, len).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+        }
+    }
+private:
+    std::map<int64_t, int64_t> free_;
+};
+
+constexpr size_t kMaxPending = size_t(1) << 22;
+
+}  // namespace
+
+struct pulda_server {
+    pulda_handle *h = nullptr;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t budget = 0, slice = 0;
+    int32_t max_slots = 0;
+    int z_warps = 8, grid = 1;
+    ZArgs tabs{};
+    // device state
+    int32_t *arena_w = nullptr;
+    int16_t *arena_z = nullptr;
+    ServeSlot *d_slots = nullptr;
+    int32_t *d_active = nullptr;
+    int *d_work = nullptr;
+    unsigned long long *d_stats = nullptr;
+    ServeSlot *h_slots = nullptr;        // pinned mirror
+    // host state
+    Arena arena{0};
+    std::vector<Request> slot_req;
+    std::vector<int32_t> free_slots, active;
+    std::deque<Request> pending;
+    std::deque<pulda_result> done;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::string err;
+    pulda_status err_status = PULDA_OK;
+    std::thread worker;
+    int64_t launches = 0;
+};
+
+namespace {
+
+bool check(pulda_server *s, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return true;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->err = std::string(what) + ": " + cudaGetErrorString(e);
+    s->err_status = PULDA_ERR_CUDA;
+    s->cv_done.notify_all();
+    return false;
+}
+
+void worker_loop(pulda_server *s) {
+    cudaSetDevice(s->device);
+    std::vector<std::pair<int32_t, int64_t>> admitted;
+    std::vector<int32_t> finished;
+    for (;;) {
+        admitted.clear();
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            for (;;) {
+                while (!s->pending.empty() && !s->free_slots.empty()) {
+                    Request &r = s->pending.front();
+                    const int64_t off = s->arena.alloc(static_cast<int64_t>(r.words.size()));
+                    if (off < 0) break;                         // wait for memory to free up
+                    const int32_t slot = s->free_slots.back();
+                    s->free_slots.pop_back();
+                    r.off = off;
+                    s->slot_req[slot] = std::move(r);
+                    s->pending.pop_front();
+                    admitted.push_back({slot, off});
+                }
+                if (!s->active.empty() || !admitted.empty()) break;
+                if (s->stop && s->pending.empty()) return;
+                s->cv_work.wait_for(lock, std::chrono::milliseconds(2));
+            }
+        }
+        for (auto &sa : admitted) {
+            const int32_t slot = sa.first;
+            Request &r = s->slot_req[slot];
+            const int64_t len = static_cast<int64_t>(r.words.size());
+            if (!check(s, cudaMemcpyAsync(s->arena_w + sa.second, r.words.data(), sizeof(int32_t) * len,
+                                          cudaMemcpyHostToDevice, s->stream), "upload of a request")) return;
+            ServeSlot e{sa.second, static_cast<int32_t>(len), 0, 0, static_cast<uint32_t>(1 + r.n_sweeps), r.seed};
+            s->h_slots[slot] = e;
+            if (!check(s, cudaMemcpyAsync(s->d_slots + slot, s->h_slots + slot, sizeof(ServeSlot),
+                                          cudaMemcpyHostToDevice, s->stream), "upload of a slot")) return;
+            s->active.push_back(slot);
+        }
+        const int n = static_cast<int>(s->active.size());
+        if (!check(s, cudaMemcpyAsync(s->d_active, s->active.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                                      s->stream), "upload of the active list")) return;
+        launch_serve_step(s->tabs, s->d_slots, s->d_active, n, s->arena_w, s->arena_z, s->slice, s->d_work,
+                          s->z_warps, s->grid, s->stream);
+        if (!check(s, cudaGetLastError(), "serving launch")) return;
+        ++s->launches;
+        if (!check(s, cudaMemcpyAsync(s->h_slots, s->d_slots, sizeof(ServeSlot) * s->max_slots, cudaMemcpyDeviceToHost,
+                                      s->stream), "slot read-back")) return;
+        if (!check(s, cudaStreamSynchronize(s->stream), "serving step")) return;
+        finished.clear();
+        std::vector<int32_t> still;
+        for (int32_t slot : s->active) {
+            const ServeSlot &e = s->h_slots[slot];
+            if (e.sweep >= e.sweep_end) {
+                Request &r = s->slot_req[slot];
+                if (r.z_out && !check(s, cudaMemcpyAsync(r.z_out, s->arena_z + r.off, sizeof(int16_t) * r.words.size(),
+                                                         cudaMemcpyDeviceToHost, s->stream), "result copy")) return;
+                finished.push_back(slot);
+            } else {
+                still.push_back(slot);
+            }
+        }
+        s->active.swap(still);
+        if (!finished.empty()) {
+            unsigned long long err = 0;
+            if (!check(s, cudaMemcpyAsync(&err, s->d_stats + ST_ERROR, sizeof err, cudaMemcpyDeviceToHost, s->stream),
+                       "error read-back")) return;
+            if (!check(s, cudaStreamSynchronize(s->stream), "result copies")) return;
+            const int64_t t = now_ns();
+            std::lock_guard<std::mutex> lock(s->mu);
+            for (int32_t slot : finished) {
+                Request &r = s->slot_req[slot];
+                pulda_result res{};
+                res.req_id = r.id;
+                res.status = err ? PULDA_ERR_CUDA : PULDA_OK;
+                res.len = static_cast<int32_t>(r.words.size());
+                res.submit_ns = r.submit_ns;
+                res.done_ns = t;
+                s->done.push_back(res);
+                s->arena.release(r.off, static_cast<int64_t>(r.words.size()));
+                r = Request();
+                s->free_slots.push_back(slot);
+            }
+            s->cv_done.notify_all();
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max_slots, int64_t slice_tokens,
+                              pulda_server **out) {
+    if (!h || !out) return PULDA_ERR_INVALID;
+    *out = nullptr;
+    if (!h->have_phi) return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID, "no Phi drawn yet: run a sweep first"));
+    if (token_budget < 1 || max_slots < 1 || slice_tokens < 1)
+        return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID, "token_budget, max_slots and slice_tokens must be >= 1"));
+    pulda_server *s = new pulda_server();
+    s->h = h;
+    s->budget = token_budget;
+    s->slice = slice_tokens;
+    s->max_slots = max_slots;
+    s->arena = Arena(token_budget);
+    s->slot_req.resize(max_slots);
+    for (int32_t i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    cudaGetDevice(&s->device);
+    auto bad = [&](cudaError_t e, const char *what) {
+        handle_fail(h, e == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA, what);
+        pulda_serve_close(s);
+        return e == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete s; return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_CUDA, "stream creation failed")); }
+    if ((e = cudaMalloc(&s->arena_w, sizeof(int32_t) * token_budget)) != cudaSuccess) return bad(e, "arena allocation failed");
+    if ((e = cudaMalloc(&s->arena_z, sizeof(int16_t) * token_budget)) != cudaSuccess) return bad(e, "arena allocation failed");
+    if ((e = cudaMalloc(&s->d_slots, sizeof(ServeSlot) * max_slots)) != cudaSuccess) return bad(e, "slot table allocation failed");
+    if ((e = cudaMalloc(&s->d_active, sizeof(int32_t) * max_slots)) != cudaSuccess) return bad(e, "slot table allocation failed");
+    if ((e = cudaMalloc(&s->d_work, sizeof(int) * 4)) != cudaSuccess) return bad(e, "allocation failed");
+    if ((e = cudaMalloc(&s->d_stats, sizeof(unsigned long long) * ST_TOTAL_SLOTS)) != cudaSuccess) return bad(e, "allocation failed");
+    if ((e = cudaMallocHost(&s->h_slots, sizeof(ServeSlot) * max_slots)) != cudaSuccess) return bad(e, "pinned allocation failed");
+    if ((e = cudaMemset(s->d_stats, 0, sizeof(unsigned long long) * ST_TOTAL_SLOTS)) != cudaSuccess) return bad(e, "memset failed");
+    std::memset(s->h_slots, 0, sizeof(ServeSlot) * max_slots);
+    HandleView hv{};
+    handle_view(h, &hv);
+    s->tabs = hv.zargs;
+    s->tabs.stats = s->d_stats;
+    s->z_warps = hv.z_warps;
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    s->grid = sms * serve_blocks_per_sm(hv.K, hv.z_warps);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bad(e, "set-up failed");
+    s->worker = std::thread(worker_loop, s);
+    *out = s;
+    return PULDA_OK;
+}
+
+pulda_status pulda_serve_submit(pulda_server *s, uint64_t req_id, uint64_t seed, const int32_t *words, int32_t len,
+                                int32_t n_sweeps, int16_t *z_out_host) {
+    if (!s) return PULDA_ERR_INVALID;
+    if (len < 1 || !words) return PULDA_ERR_INVALID;
+    if (len > s->budget || len > (1 << 22)) return PULDA_ERR_INVALID;
+    if (n_sweeps < 1) return PULDA_ERR_INVALID;
+    const int V = s->tabs.col_ptr ? s->h->V : 0;
+    for (int32_t i = 0; i < len; ++i)
+        if (words[i] < 0 || words[i] >= V) return PULDA_ERR_INVALID;
+    Request r;
+    r.id = req_id;
+    r.seed = seed;
+    r.words.assign(words, words + len);
+    r.n_sweeps = n_sweeps;
+    r.z_out = z_out_host;
+    r.submit_ns = now_ns();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->err_status != PULDA_OK) return s->err_status;
+        if (s->stop) return PULDA_ERR_INVALID;
+        if (s->pending.size() >= kMaxPending) return PULDA_ERR_BUSY;
+        s->pending.push_back(std::move(r));
+    }
+    s->cv_work.notify_one();
+    return PULDA_OK;
+}
+
+pulda_status pulda_serve_poll(pulda_server *s, pulda_result *out, int32_t max_results, int32_t *n_out,
+                              int32_t timeout_ms) {
+    if (!s || !n_out || (max_results > 0 && !out)) return PULDA_ERR_INVALID;
+    *n_out = 0;
+    std::unique_lock<std::mutex> lock(s->mu);
+    const bool ready = s->cv_done.wait_for(lock, std::chrono::milliseconds(std::max(timeout_ms, 0)),
+                                           [&] { return !s->done.empty() || s->err_status != PULDA_OK; });
+    if (s->err_status != PULDA_OK && s->done.empty()) return s->err_status;
+    if (!ready) return PULDA_ERR_TIMEOUT;
+    int32_t n = 0;
+    while (n < max_results && !s->done.empty()) {
+        out[n++] = s->done.front();
+        s->done.pop_front();
+    }
+    *n_out = n;
+    return PULDA_OK;
+}
+
+pulda_status pulda_serve_pending(pulda_server *s, int64_t *waiting, int64_t *running, int64_t *launches) {
+    if (!s) return PULDA_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (waiting) *waiting = static_cast<int64_t>(s->pending.size());
+    if (running) *running = static_cast<int64_t>(s->max_slots - s->free_slots.size());
+    if (launches) *launches = s->launches;
+    return PULDA_OK;
+}
+
+pulda_status pulda_serve_close(pulda_server *s) {
+    if (!s) return PULDA_ERR_INVALID;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    pulda_status st = s->err_status;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    cudaFree(s->arena_w);
+    cudaFree(s->arena_z);
+    cudaFree(s->d_slots);
+    cudaFree(s->d_active);
+    cudaFree(s->d_work);
+    cudaFree(s->d_stats);
+    if (s->h_slots) cudaFreeHost(s->h_slots);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return st;
+}
+
+}  // extern "C"
