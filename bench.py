@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--rates", type=str, default="2000,5000,10000,20000,50000",
                     help="serving: Poisson arrival rates, documents per second")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="serving: arrival window per rate")
-    ap.add_argument("--slice", type=int, default=2048, help="serving: tokens a request advances per launch")
+    ap.add_argument("--slice", type=int, default=0,
+                    help="serving: tokens a request advances per launch (0 = tuned by the server)")
     ap.add_argument("--serve-sweeps", type=int, default=50, help="serving: z-sweeps per request")
     ap.add_argument("--plain-requests", type=int, default=150,
                     help="serving: requests the one-at-a-time baseline serves (the first ones, at the lowest rate)")
@@ -449,6 +450,10 @@ def run_serving(args):
             alone = model.infer(reqs.w[a:b], np.array([0, b - a]), args.serve_sweeps, seed=7919 * j + 1)
             same &= bool(np.array_equal(alone, done[j]["z"]))
         results[-1]["identical_to_alone"] = same
+        st = srv.stats()
+        results[-1]["server"] = {"launches": st["launches"], "final_slice": st["slice"],
+                                 "max_requests_per_launch": st["max_active"],
+                                 "kernel_share": st["kernel_ns"] / max(1, t_end - t0)}
         srv.close()
     # one request at a time (pulda_infer), the first requests at the lowest rate
     rate = min(rates)

@@ -243,8 +243,11 @@ typedef struct {
 } pulda_result;
 
 /* pulda_serve_open -- token_budget: tokens the arena holds (6 bytes each on
- * the device); max_slots: requests in flight; slice_tokens: tokens a request
- * advances per launch.  Errors: PULDA_ERR_INVALID (no Phi yet, a size < 1),
+ * the device, 6 pinned on the host); max_slots: requests in flight;
+ * slice_tokens: tokens a request
+ * advances per launch, or 0 to let the server tune it toward launches of
+ * about 2 ms (results do not depend on it).  Errors: PULDA_ERR_INVALID (no
+ * Phi yet, token_budget or max_slots < 1, slice_tokens < 0),
  * PULDA_ERR_OOM, PULDA_ERR_CUDA. */
 pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max_slots, int64_t slice_tokens,
                               pulda_server **out);
@@ -264,6 +267,11 @@ pulda_status pulda_serve_poll(pulda_server *s, pulda_result *out, int32_t max_re
 /* pulda_serve_pending -- requests waiting for admission, requests in flight,
  * and launches so far (any pointer may be NULL). */
 pulda_status pulda_serve_pending(pulda_server *s, int64_t *waiting, int64_t *running, int64_t *launches);
+/* pulda_serve_stats -- out int64[8]: launches, requests completed, token
+ * steps completed (tokens x sweeps), kernel nanoseconds, current slice,
+ * largest number of requests in one launch, requests waiting, requests in
+ * flight. */
+pulda_status pulda_serve_stats(pulda_server *s, int64_t *out);
 /* pulda_serve_close -- stop accepting, finish every submitted request, release
  * the server.  Returns the worker's error status, if any. */
 pulda_status pulda_serve_close(pulda_server *s);

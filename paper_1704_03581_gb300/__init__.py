@@ -27,7 +27,8 @@ EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "puld
             "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_last_error", "pulda_free",
             "pulda_batch_init", "pulda_batch_sweep", "pulda_batch_sync", "pulda_batch_get_z", "pulda_batch_stats",
             "pulda_batch_tuning", "pulda_batch_last_error", "pulda_batch_free",
-            "pulda_serve_open", "pulda_serve_submit", "pulda_serve_poll", "pulda_serve_pending", "pulda_serve_close"]
+            "pulda_serve_open", "pulda_serve_submit", "pulda_serve_poll", "pulda_serve_pending", "pulda_serve_stats",
+            "pulda_serve_close"]
 
 
 class PuldaError(RuntimeError):
@@ -90,6 +91,7 @@ def lib() -> ctypes.CDLL:
             "pulda_serve_submit": [P, u64, u64, P, i32, i32, P],
             "pulda_serve_poll": [P, P, i32, P, i32],
             "pulda_serve_pending": [P, P, P, P],
+            "pulda_serve_stats": [P, P],
             "pulda_serve_close": [P],
         })
         for name, args in sig.items():
@@ -447,6 +449,15 @@ def pulda_serve_pending(s) -> tuple[int, int, int]:
     return a.value, b.value, c.value
 
 
+def pulda_serve_stats(s) -> dict:
+    out = np.zeros(8, np.int64)
+    st = lib().pulda_serve_stats(s, _ptr(out))
+    if st != PULDA_OK:
+        raise PuldaError(st, "serve_stats failed")
+    keys = ["launches", "completed", "token_steps", "kernel_ns", "slice", "max_active", "waiting", "running"]
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
 def pulda_serve_close(s):
     st = lib().pulda_serve_close(s)
     if st != PULDA_OK:
@@ -476,6 +487,9 @@ class Server:
 
     def pending(self):
         return pulda_serve_pending(self.s)
+
+    def stats(self) -> dict:
+        return pulda_serve_stats(self.s)
 
     def close(self):
         if self.s:

@@ -91,7 +91,15 @@ struct pulda_server {
     int32_t *d_active = nullptr;
     int *d_work = nullptr;
     unsigned long long *d_stats = nullptr;
-    ServeSlot *h_slots = nullptr;        // pinned mirror
+    ServeSlot *h_slots = nullptr;        // pinned: slot states read back after each launch
+    ServeSlot *h_new = nullptr;          // pinned: entries of newly admitted slots
+    int32_t *h_active = nullptr;         // pinned: the active list of the next launch
+    int32_t *pin_w = nullptr;            // pinned mirror of the arena's word ids
+    int16_t *pin_z = nullptr;            // pinned mirror of the arena's topics
+    bool auto_slice = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // counters: iterations, admitted, completed, token steps, kernel ns, current slice, max active
+    int64_t ctr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // host state
     Arena arena{0};
     std::vector<Request> slot_req;
@@ -104,7 +112,6 @@ struct pulda_server {
     std::string err;
     pulda_status err_status = PULDA_OK;
     std::thread worker;
-    int64_t launches = 0;
 };
 
 namespace {
@@ -118,89 +125,127 @@ bool check(pulda_server *s, cudaError_t e, const char *what) {
     return false;
 }
 
+// Moves waiting requests into free slots while the arena has room (first come
+// first served) and enqueues their uploads; called with s->mu held.
+void admit_locked(pulda_server *s, std::vector<int32_t> &newly) {
+    while (!s->pending.empty() && !s->free_slots.empty()) {
+        Request &r = s->pending.front();
+        const int64_t len = static_cast<int64_t>(r.words.size());
+        const int64_t off = s->arena.alloc(len);
+        if (off < 0) break;                         // wait for memory to free up
+        const int32_t slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        r.off = off;
+        std::memcpy(s->pin_w + off, r.words.data(), sizeof(int32_t) * len);
+        s->h_new[slot] = ServeSlot{off, static_cast<int32_t>(len), 0, 0, static_cast<uint32_t>(1 + r.n_sweeps), r.seed};
+        s->slot_req[slot] = std::move(r);
+        s->pending.pop_front();
+        newly.push_back(slot);
+    }
+}
+
+bool upload(pulda_server *s, const std::vector<int32_t> &newly) {
+    for (int32_t slot : newly) {
+        const ServeSlot &e = s->h_new[slot];
+        if (!check(s, cudaMemcpyAsync(s->arena_w + e.off, s->pin_w + e.off, sizeof(int32_t) * e.len,
+                                      cudaMemcpyHostToDevice, s->stream), "upload of a request")) return false;
+        if (!check(s, cudaMemcpyAsync(s->d_slots + slot, s->h_new + slot, sizeof(ServeSlot), cudaMemcpyHostToDevice,
+                                      s->stream), "upload of a slot")) return false;
+    }
+    return true;
+}
+
 void worker_loop(pulda_server *s) {
     cudaSetDevice(s->device);
-    std::vector<std::pair<int32_t, int64_t>> admitted;
-    std::vector<int32_t> finished;
+    std::vector<int32_t> newly, finished, still;
     for (;;) {
-        admitted.clear();
-        {
+        // requests admitted during the previous launch are already uploaded;
+        // if nothing runs, wait for arrivals
+        if (s->active.empty() && newly.empty()) {
             std::unique_lock<std::mutex> lock(s->mu);
             for (;;) {
-                while (!s->pending.empty() && !s->free_slots.empty()) {
-                    Request &r = s->pending.front();
-                    const int64_t off = s->arena.alloc(static_cast<int64_t>(r.words.size()));
-                    if (off < 0) break;                         // wait for memory to free up
-                    const int32_t slot = s->free_slots.back();
-                    s->free_slots.pop_back();
-                    r.off = off;
-                    s->slot_req[slot] = std::move(r);
-                    s->pending.pop_front();
-                    admitted.push_back({slot, off});
-                }
-                if (!s->active.empty() || !admitted.empty()) break;
+                admit_locked(s, newly);
+                if (!newly.empty()) break;
                 if (s->stop && s->pending.empty()) return;
                 s->cv_work.wait_for(lock, std::chrono::milliseconds(2));
             }
+            lock.unlock();
+            if (!upload(s, newly)) return;
         }
-        for (auto &sa : admitted) {
-            const int32_t slot = sa.first;
-            Request &r = s->slot_req[slot];
-            const int64_t len = static_cast<int64_t>(r.words.size());
-            if (!check(s, cudaMemcpyAsync(s->arena_w + sa.second, r.words.data(), sizeof(int32_t) * len,
-                                          cudaMemcpyHostToDevice, s->stream), "upload of a request")) return;
-            ServeSlot e{sa.second, static_cast<int32_t>(len), 0, 0, static_cast<uint32_t>(1 + r.n_sweeps), r.seed};
-            s->h_slots[slot] = e;
-            if (!check(s, cudaMemcpyAsync(s->d_slots + slot, s->h_slots + slot, sizeof(ServeSlot),
-                                          cudaMemcpyHostToDevice, s->stream), "upload of a slot")) return;
-            s->active.push_back(slot);
-        }
+        for (int32_t slot : newly) s->active.push_back(slot);
+        newly.clear();
         const int n = static_cast<int>(s->active.size());
-        if (!check(s, cudaMemcpyAsync(s->d_active, s->active.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+        std::memcpy(s->h_active, s->active.data(), sizeof(int32_t) * n);
+        if (!check(s, cudaMemcpyAsync(s->d_active, s->h_active, sizeof(int32_t) * n, cudaMemcpyHostToDevice,
                                       s->stream), "upload of the active list")) return;
+        cudaEventRecord(s->ev0, s->stream);
         launch_serve_step(s->tabs, s->d_slots, s->d_active, n, s->arena_w, s->arena_z, s->slice, s->d_work,
                           s->z_warps, s->grid, s->stream);
         if (!check(s, cudaGetLastError(), "serving launch")) return;
-        ++s->launches;
+        cudaEventRecord(s->ev1, s->stream);
         if (!check(s, cudaMemcpyAsync(s->h_slots, s->d_slots, sizeof(ServeSlot) * s->max_slots, cudaMemcpyDeviceToHost,
                                       s->stream), "slot read-back")) return;
+        // admit and upload the next requests while the launch runs
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            admit_locked(s, newly);
+        }
+        if (!upload(s, newly)) return;
         if (!check(s, cudaStreamSynchronize(s->stream), "serving step")) return;
+        float kms = 0.f;
+        cudaEventElapsedTime(&kms, s->ev0, s->ev1);
+        s->ctr[0] += 1;
+        s->ctr[4] += static_cast<int64_t>(kms * 1e6);
+        s->ctr[6] = std::max<int64_t>(s->ctr[6], n);
+        if (s->auto_slice) {
+            // aim at launches of about 2 ms: long enough to amortise the loop,
+            // short enough that new requests start soon
+            const double target = 2.0;
+            double next = static_cast<double>(s->slice) * target / std::max(0.05, static_cast<double>(kms));
+            next = std::min(std::max(next, 0.5 * s->slice), 2.0 * s->slice);
+            s->slice = std::min<int64_t>(std::max<int64_t>(static_cast<int64_t>(next), 64), 1 << 16);
+        }
+        s->ctr[5] = s->slice;
         finished.clear();
-        std::vector<int32_t> still;
+        still.clear();
         for (int32_t slot : s->active) {
             const ServeSlot &e = s->h_slots[slot];
             if (e.sweep >= e.sweep_end) {
-                Request &r = s->slot_req[slot];
-                if (r.z_out && !check(s, cudaMemcpyAsync(r.z_out, s->arena_z + r.off, sizeof(int16_t) * r.words.size(),
-                                                         cudaMemcpyDeviceToHost, s->stream), "result copy")) return;
+                if (!check(s, cudaMemcpyAsync(s->pin_z + e.off, s->arena_z + e.off, sizeof(int16_t) * e.len,
+                                              cudaMemcpyDeviceToHost, s->stream), "result copy")) return;
                 finished.push_back(slot);
             } else {
                 still.push_back(slot);
             }
         }
         s->active.swap(still);
-        if (!finished.empty()) {
-            unsigned long long err = 0;
-            if (!check(s, cudaMemcpyAsync(&err, s->d_stats + ST_ERROR, sizeof err, cudaMemcpyDeviceToHost, s->stream),
-                       "error read-back")) return;
-            if (!check(s, cudaStreamSynchronize(s->stream), "result copies")) return;
-            const int64_t t = now_ns();
-            std::lock_guard<std::mutex> lock(s->mu);
-            for (int32_t slot : finished) {
-                Request &r = s->slot_req[slot];
-                pulda_result res{};
-                res.req_id = r.id;
-                res.status = err ? PULDA_ERR_CUDA : PULDA_OK;
-                res.len = static_cast<int32_t>(r.words.size());
-                res.submit_ns = r.submit_ns;
-                res.done_ns = t;
-                s->done.push_back(res);
-                s->arena.release(r.off, static_cast<int64_t>(r.words.size()));
-                r = Request();
-                s->free_slots.push_back(slot);
-            }
-            s->cv_done.notify_all();
+        if (finished.empty()) continue;
+        unsigned long long err = 0;
+        if (!check(s, cudaMemcpyAsync(&err, s->d_stats + ST_ERROR, sizeof err, cudaMemcpyDeviceToHost, s->stream),
+                   "error read-back")) return;
+        if (!check(s, cudaStreamSynchronize(s->stream), "result copies")) return;
+        for (int32_t slot : finished) {
+            Request &r = s->slot_req[slot];
+            if (r.z_out) std::memcpy(r.z_out, s->pin_z + r.off, sizeof(int16_t) * r.words.size());
         }
+        const int64_t t = now_ns();
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (int32_t slot : finished) {
+            Request &r = s->slot_req[slot];
+            pulda_result res{};
+            res.req_id = r.id;
+            res.status = err ? PULDA_ERR_CUDA : PULDA_OK;
+            res.len = static_cast<int32_t>(r.words.size());
+            res.submit_ns = r.submit_ns;
+            res.done_ns = t;
+            s->done.push_back(res);
+            s->ctr[2] += 1;
+            s->ctr[3] += static_cast<int64_t>(r.words.size()) * (r.n_sweeps);
+            s->arena.release(r.off, static_cast<int64_t>(r.words.size()));
+            r = Request();
+            s->free_slots.push_back(slot);
+        }
+        s->cv_done.notify_all();
     }
 }
 
@@ -213,12 +258,14 @@ pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max
     if (!h || !out) return PULDA_ERR_INVALID;
     *out = nullptr;
     if (!h->have_phi) return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID, "no Phi drawn yet: run a sweep first"));
-    if (token_budget < 1 || max_slots < 1 || slice_tokens < 1)
-        return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID, "token_budget, max_slots and slice_tokens must be >= 1"));
+    if (token_budget < 1 || max_slots < 1 || slice_tokens < 0)
+        return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID,
+                                                     "token_budget and max_slots must be >= 1, slice_tokens >= 0"));
     pulda_server *s = new pulda_server();
     s->h = h;
     s->budget = token_budget;
-    s->slice = slice_tokens;
+    s->auto_slice = slice_tokens == 0;
+    s->slice = slice_tokens == 0 ? 1024 : slice_tokens;
     s->max_slots = max_slots;
     s->arena = Arena(token_budget);
     s->slot_req.resize(max_slots);
@@ -238,6 +285,12 @@ pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max
     if ((e = cudaMalloc(&s->d_work, sizeof(int) * 4)) != cudaSuccess) return bad(e, "allocation failed");
     if ((e = cudaMalloc(&s->d_stats, sizeof(unsigned long long) * ST_TOTAL_SLOTS)) != cudaSuccess) return bad(e, "allocation failed");
     if ((e = cudaMallocHost(&s->h_slots, sizeof(ServeSlot) * max_slots)) != cudaSuccess) return bad(e, "pinned allocation failed");
+    if ((e = cudaMallocHost(&s->h_new, sizeof(ServeSlot) * max_slots)) != cudaSuccess) return bad(e, "pinned allocation failed");
+    if ((e = cudaMallocHost(&s->h_active, sizeof(int32_t) * max_slots)) != cudaSuccess) return bad(e, "pinned allocation failed");
+    if ((e = cudaMallocHost(&s->pin_w, sizeof(int32_t) * token_budget)) != cudaSuccess) return bad(e, "pinned allocation failed");
+    if ((e = cudaMallocHost(&s->pin_z, sizeof(int16_t) * token_budget)) != cudaSuccess) return bad(e, "pinned allocation failed");
+    if ((e = cudaEventCreate(&s->ev0)) != cudaSuccess || (e = cudaEventCreate(&s->ev1)) != cudaSuccess)
+        return bad(e, "event creation failed");
     if ((e = cudaMemset(s->d_stats, 0, sizeof(unsigned long long) * ST_TOTAL_SLOTS)) != cudaSuccess) return bad(e, "memset failed");
     std::memset(s->h_slots, 0, sizeof(ServeSlot) * max_slots);
     HandleView hv{};
@@ -304,7 +357,21 @@ pulda_status pulda_serve_pending(pulda_server *s, int64_t *waiting, int64_t *run
     std::lock_guard<std::mutex> lock(s->mu);
     if (waiting) *waiting = static_cast<int64_t>(s->pending.size());
     if (running) *running = static_cast<int64_t>(s->max_slots - s->free_slots.size());
-    if (launches) *launches = s->launches;
+    if (launches) *launches = s->ctr[0];
+    return PULDA_OK;
+}
+
+pulda_status pulda_serve_stats(pulda_server *s, int64_t *out) {
+    if (!s || !out) return PULDA_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(s->mu);
+    out[0] = s->ctr[0];
+    out[1] = s->ctr[2];
+    out[2] = s->ctr[3];
+    out[3] = s->ctr[4];
+    out[4] = s->ctr[5];
+    out[5] = s->ctr[6];
+    out[6] = static_cast<int64_t>(s->pending.size());
+    out[7] = static_cast<int64_t>(s->max_slots - s->free_slots.size());
     return PULDA_OK;
 }
 
@@ -325,6 +392,12 @@ pulda_status pulda_serve_close(pulda_server *s) {
     cudaFree(s->d_work);
     cudaFree(s->d_stats);
     if (s->h_slots) cudaFreeHost(s->h_slots);
+    if (s->h_new) cudaFreeHost(s->h_new);
+    if (s->h_active) cudaFreeHost(s->h_active);
+    if (s->pin_w) cudaFreeHost(s->pin_w);
+    if (s->pin_z) cudaFreeHost(s->pin_z);
+    if (s->ev0) cudaEventDestroy(s->ev0);
+    if (s->ev1) cudaEventDestroy(s->ev1);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return st;
