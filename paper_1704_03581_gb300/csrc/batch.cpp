@@ -181,7 +181,7 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     bl.kmax = kmax;
     bl.phi_grid = b->sms * batch_phi_blocks_per_sm(kmax);
     for (int w : {2, 4, 8})
-        if (sizeof(uint32_t) * static_cast<size_t>(kmax) * w <= 160 * 1024) b->cand.push_back(w);
+        if (z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back(w);
     if (b->cand.empty()) b->cand.push_back(1);
     if (o.warps_per_block > 0) {
         b->cand.assign(1, o.warps_per_block);

@@ -524,6 +524,12 @@ constexpr int kGather = PULDA_ZGATHER;
 // depends only on the token (its word, Philox words, alias outcome, the
 // word's bitmap) is fetched ahead; the only loads on the critical path are
 // the q values of the intersection, issued together.
+// m_d is stored skewed, topic k at k + k/32, so the lanes of a warp reading
+// topics 32 l + b (lane l, bit b) hit distinct shared-memory banks.
+__host__ __device__ __forceinline__ int mi(int k) { return k + (k >> 5); }
+// Shared memory of one z-step warp, in 32-bit words.
+__host__ __device__ __forceinline__ int z_warp_words(int K) { return K + (K >> 5) + 1; }
+
 // One document's run: where its tokens live and where its Markov chain is.
 struct DocRun {
     const int32_t *w;        // word ids, position 0 first
@@ -549,22 +555,22 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
     const int K = a.K;
     const bool use_bm = a.bitmap != nullptr && a.path != 1;
     if (r.len == 0 || r.budget <= 0) return;
-    for (int k = lane; k < K; k += 32) m[k] = 0;
+    for (int k = lane; k < K; k += 32) m[mi(k)] = 0;
     __syncwarp();
-    for (int i = lane; i < r.len; i += 32) atomicAdd(&m[r.z[i]], 1u);
+    for (int i = lane; i < r.len; i += 32) atomicAdd(&m[mi(r.z[i])], 1u);
     __syncwarp();
     uint32_t mbits = 0;
     int kd = 0;
     if (use_bm) {
         for (int g = 0; g < a.KW; ++g) {
             const int k = g * 32 + lane;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k < K && m[k] > 0);
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k < K && m[mi(k)] > 0);
             if (lane == g) mbits = bal;
             kd += __popc(bal);
         }
     } else {
         int cnt = 0;
-        for (int k = lane; k < K; k += 32) cnt += m[k] > 0;
+        for (int k = lane; k < K; k += 32) cnt += m[mi(k)] > 0;
 #pragma unroll
         for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
         kd = cnt;
@@ -612,9 +618,9 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
                 if (tt + 1 < cnt && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(vn) * a.KW + lane];
             }
             // remove token i: m^{-i}
-            const uint32_t old = m[kold];
+            const uint32_t old = m[mi(kold)];
             __syncwarp();
-            if (lane == 0) m[kold] = old - 1;
+            if (lane == 0) m[mi(kold)] = old - 1;
             if (old == 1) {
                 --kd;
                 if (use_bm && lane == (kold >> 5)) mbits &= ~(1u << (kold & 31));
@@ -622,6 +628,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
             __syncwarp();
             st_min += static_cast<u64>(kd < n_w ? kd : n_w);
             const bool docside = use_bm && (a.path == 2 || kd < n_w);
+            const uint32_t *qcol = a.q + col;
             // per-lane partial sums of q m, in ascending topic order across lanes
             u64 acc = 0;
             uint32_t qv[kGather];
@@ -638,23 +645,23 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
                         const int b = __ffs(rem) - 1;
                         rem &= rem - 1;
                         bp[t] = b;
-                        qv[t] = a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))];
+                        qv[t] = qcol[bm.y + __popc(bm.x & ((1u << b) - 1u))];
                     }
                 }
 #pragma unroll
                 for (int t = 0; t < kGather; ++t)
-                    if (bp[t] >= 0) acc += static_cast<u64>(qv[t]) * m[lane * 32 + bp[t]];
+                    if (bp[t] >= 0) acc += static_cast<u64>(qv[t]) * m[lane * 33 + bp[t]];
                 rest = rem;
                 for (uint32_t bb = rest; bb; bb &= bb - 1) {
                     const int b = __ffs(bb) - 1;
-                    acc += static_cast<u64>(a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))]) * m[lane * 32 + b];
+                    acc += static_cast<u64>(qcol[bm.y + __popc(bm.x & ((1u << b) - 1u))]) * m[lane * 33 + b];
                 }
             } else {
                 seg = (n_w + 31) >> 5;
                 seg0 = seg * lane;
                 const int seg1 = min(seg0 + seg, n_w);
 #pragma unroll 4
-                for (int j = seg0; j < seg1; ++j) acc += static_cast<u64>(a.q[col + j]) * m[a.topic[col + j]];
+                for (int j = seg0; j < seg1; ++j) acc += static_cast<u64>(qcol[j]) * m[mi(a.topic[col + j])];
             }
             const u64 incl = warp_incl_scan64(acc);
             const u64 B = __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -679,22 +686,23 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
                             if (docside) {
 #pragma unroll
                                 for (int t = 0; t < kGather; ++t) {
-                                    if (f < 0 && bp[t] >= 0) {
-                                        run += static_cast<u64>(qv[t]) * m[lane * 32 + bp[t]];
+                                    if (f >= 0 || bp[t] < 0) break;
+                                    {
+                                        run += static_cast<u64>(qv[t]) * m[lane * 33 + bp[t]];
                                         if (rb < run) f = lane * 32 + bp[t];
                                     }
                                 }
                                 for (uint32_t bb = rest; f < 0 && bb; bb &= bb - 1) {
                                     const int b = __ffs(bb) - 1;
-                                    run += static_cast<u64>(a.q[col + bm.y + __popc(bm.x & ((1u << b) - 1u))]) *
-                                           m[lane * 32 + b];
+                                    run += static_cast<u64>(qcol[bm.y + __popc(bm.x & ((1u << b) - 1u))]) *
+                                           m[lane * 33 + b];
                                     if (rb < run) f = lane * 32 + b;
                                 }
                             } else {
                                 const int seg1 = min(seg0 + seg, n_w);
                                 for (int j = seg0; j < seg1; ++j) {
                                     const int k = a.topic[col + j];
-                                    run += static_cast<u64>(a.q[col + j]) * m[k];
+                                    run += static_cast<u64>(qcol[j]) * m[mi(k)];
                                     if (rb < run) { f = k; break; }
                                 }
                             }
@@ -709,9 +717,9 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
                 }
             }
             // add token i back with its new topic
-            const uint32_t old2 = m[knew];
+            const uint32_t old2 = m[mi(knew)];
             __syncwarp();
-            if (lane == 0) m[knew] = old2 + 1;
+            if (lane == 0) m[mi(knew)] = old2 + 1;
             if (old2 == 0) {
                 ++kd;
                 if (use_bm && lane == (knew >> 5)) mbits |= 1u << (knew & 31);
@@ -744,7 +752,7 @@ __device__ void flush_z_stats(unsigned long long *stats, u64 st_tok, u64 st_ab, 
 __global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
-    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * a.K;
+    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
     u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
     const uint32_t sweep = sweep_of(a);
     for (;;) {
@@ -767,7 +775,7 @@ __global__ void __launch_bounds__(256, 2) k_z_step_multi(const ZArgs *chains, co
                                                                         int n_items, int *work, int kmax) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
-    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * kmax;
+    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(kmax);
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(work, 1);
@@ -1099,7 +1107,7 @@ __global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_serve_step(ZArgs a, S
                                                                      int16_t *arena_z, int64_t slice, int *work) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
-    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * a.K;
+    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
     u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
     for (;;) {
         int item = 0;
@@ -1238,7 +1246,7 @@ void launch_phi_tables(const PhiArgs &a, cudaStream_t st) {
     k_phi_tables<<<grid, 128, 0, st>>>(a);
 }
 
-size_t z_step_smem(int K, int warps_per_block) { return sizeof(uint32_t) * static_cast<size_t>(K) * warps_per_block; }
+size_t z_step_smem(int K, int warps_per_block) { return sizeof(uint32_t) * static_cast<size_t>(z_warp_words(K)) * warps_per_block; }
 
 int z_step_blocks_per_sm(int K, int warps_per_block) {
     const size_t smem = z_step_smem(K, warps_per_block);
@@ -1275,7 +1283,7 @@ void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
     k_phi_fixup_multi<<<b.n_chains, kFixBlock, 0, st>>>(b.phi);
     k_colptr_scan_multi<<<b.n_chains, 1024, 0, st>>>(b.phi);
     k_phi_tables_multi<<<(b.n_phi_items + 127) / 128, 128, 0, st>>>(b.phi, b.phi_items, b.n_phi_items);
-    k_z_step_multi<<<b.z_grid, 32 * b.z_warps, sizeof(uint32_t) * static_cast<size_t>(b.kmax) * b.z_warps, st>>>(
+    k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), st>>>(
         b.z, b.z_items, b.n_z_items, b.work + 1, b.kmax);
 }
 
@@ -1289,8 +1297,7 @@ int batch_phi_blocks_per_sm(int kmax) {
 int batch_z_blocks_per_sm(int kmax, int warps) {
     allow_dynamic_smem(k_z_step_multi);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_z_step_multi, 32 * warps,
-                                                  sizeof(uint32_t) * static_cast<size_t>(kmax) * warps);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_z_step_multi, 32 * warps, z_step_smem(kmax, warps));
     return n > 0 ? n : 1;
 }
 
