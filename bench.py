@@ -256,6 +256,8 @@ def run_pulda(args, corpus, rank: int, world: int):
     tokens = st1["cum_tokens"] - st0["cum_tokens"]
     sum_min = st1["cum_sum_min"] - st0["cum_sum_min"]
     a_br = st1["cum_a_branch"] - st0["cum_a_branch"]
+    sum_int = st1["cum_sum_inter"] - st0["cum_sum_inter"]
+    docside = st1["cum_docside"] - st0["cum_docside"]
     assert tokens == K * corpus.N, (tokens, K * corpus.N)
     nnz_phi = st1["nnz_phi"]
     s.close()
@@ -310,7 +312,8 @@ def run_pulda(args, corpus, rank: int, world: int):
                    "l2": "inputs larger than L2 (word ids 396 MB + topics 198 MB read every sweep)",
                    "timed_sweeps": [first_timed, first_timed + K - 1]},
         "z_step": {"tokens_per_s": K * corpus.N / (z_ms / 1000.0), "ms_per_launch": z_ms / K,
-                   "mean_min_kd_kv": sum_min / tokens, "a_branch_frac": a_br / tokens},
+                   "mean_min_kd_kv": sum_min / tokens, "mean_intersection": sum_int / tokens,
+                   "docside_frac": docside / tokens, "a_branch_frac": a_br / tokens},
         "phi_step": {"ms_per_sweep": phi_ms / K, "nnz_phi": nnz_phi},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

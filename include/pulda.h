@@ -75,6 +75,10 @@ typedef struct {
     int64_t cum_a_branch;
     int64_t cum_sum_min;
     int64_t cum_zero_mass;
+    int64_t sum_inter;       /* sum over tokens of |J|: topics nonzero in both m_d^{-i} and Phi's column */
+    int64_t docside;         /* tokens with K_d < K_v (the document side is the smaller) */
+    int64_t cum_sum_inter;
+    int64_t cum_docside;
 } pulda_sweep_stats;
 
 /* pulda_init -- create a chain.

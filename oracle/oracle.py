@@ -232,11 +232,11 @@ class WordTables:
 
 def z_step(doc_off: np.ndarray, w: np.ndarray, z: np.ndarray, tables: WordTables, seed: int, sweep: int,
            index_base: int = 0) -> tuple[np.ndarray, np.ndarray]:
-    """One z-step; returns (new z, stats[tokens, a_branch, sum_min, zero_mass])."""
+    """One z-step; returns (new z, stats[tokens, a_branch, sum_min, zero_mass, sum_inter, docside])."""
     z = np.array(z, dtype=np.int16, copy=True)
     doc_off = np.ascontiguousarray(doc_off, dtype=np.int64)
     w = np.ascontiguousarray(w, dtype=np.int32)
-    stats = np.zeros(4, dtype=np.int64)
+    stats = np.zeros(6, dtype=np.int64)
     t = tables
     rc = lib().or_z_step(_p(doc_off), doc_off.shape[0] - 1, _p(w), _p(z), t.K, t.V, _p(t.ncol), _p(t.topic),
                          _p(t.q), _p(t.A), _p(t.athr), _p(t.atopic), seed, sweep, index_base, _p(stats))
@@ -265,7 +265,7 @@ class Chain:
         self.tables: WordTables | None = None
         self.S = None
         self.c = None
-        self.stats = np.zeros(4, dtype=np.int64)
+        self.stats = np.zeros(6, dtype=np.int64)
         self.dead_rows = 0
 
     def phi_step(self, sweep: int):

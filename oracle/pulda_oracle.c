@@ -475,7 +475,9 @@ void or_word_tables(const uint32_t *c_vk, const int64_t *S, const float *alpha, 
 /* in order; p(z_i = k) proportional to phi_{k,v}(alpha_k + m^{-i}_{d,k}),  */
 /* split into a (alpha part, alias table) and b (m part, iterated).         */
 /* stats[0] += tokens, stats[1] += a-branch draws, stats[2] += sum over      */
-/* tokens of min(K_d, K_v), stats[3] += zero-mass tokens kept.              */
+/* tokens of min(K_d, K_v), stats[3] += zero-mass tokens kept, stats[4] +=   */
+/* |J| (topics nonzero in both m^{-i} and the column), stats[5] += tokens    */
+/* with K_d < K_v.                                                           */
 /* ------------------------------------------------------------------------ */
 int32_t or_z_step(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *z, int32_t K, int32_t V,
                   const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
@@ -498,7 +500,11 @@ int32_t or_z_step(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *
             int32_t nv = ncol[v];
             /* sigma_b = sum_k q_{k,v} m^{-i}_{d,k}; every term is exact */
             uint64_t B = 0;
-            for (int32_t j = 0; j < nv; j++) B += (uint64_t)q[base + j] * (uint64_t)m[topic[base + j]];
+            for (int32_t j = 0; j < nv; j++) {
+                B += (uint64_t)q[base + j] * (uint64_t)m[topic[base + j]];
+                if (m[topic[base + j]] > 0) stats[4]++;
+            }
+            if (kd < nv) stats[5]++;
             uint64_t T = A[v] + (B << OR_FRAC_BITS);
             int32_t knew = kold;
             uint64_t t = (uint64_t)(index_base + i);

@@ -46,7 +46,8 @@ class SweepStats(ctypes.Structure):
     _fields_ = [("tokens", ctypes.c_int64), ("a_branch", ctypes.c_int64), ("sum_min", ctypes.c_int64),
                 ("zero_mass", ctypes.c_int64), ("dead_rows", ctypes.c_int64), ("nnz_phi", ctypes.c_int64),
                 ("sweep", ctypes.c_int64), ("cum_tokens", ctypes.c_int64), ("cum_a_branch", ctypes.c_int64),
-                ("cum_sum_min", ctypes.c_int64), ("cum_zero_mass", ctypes.c_int64)]
+                ("cum_sum_min", ctypes.c_int64), ("cum_zero_mass", ctypes.c_int64), ("sum_inter", ctypes.c_int64),
+                ("docside", ctypes.c_int64), ("cum_sum_inter", ctypes.c_int64), ("cum_docside", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f[0]: int(getattr(self, f[0])) for f in self._fields_}

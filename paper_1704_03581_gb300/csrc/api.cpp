@@ -78,6 +78,13 @@ pulda_status check_corpus(pulda_handle *h, const int32_t *w, const int64_t *off,
     return PULDA_OK;
 }
 
+// The per-sweep z-step counters start from zero at every z-step.
+cudaError_t clear_z_counters(pulda_handle *h) {
+    cudaError_t e = cudaMemsetAsync(h->stats + ST_TOKENS, 0, sizeof(unsigned long long) * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->stats + ST_SUMINT, 0, sizeof(unsigned long long) * 2, h->stream);
+    return e;
+}
+
 // Documents in decreasing length (ties by index), so the persistent z-step
 // starts the long ones first.
 std::vector<int32_t> length_order(const int64_t *off, int64_t D) {
@@ -299,7 +306,7 @@ pulda_status pulda_phi_step(pulda_handle *h) {
 pulda_status pulda_z_step(pulda_handle *h) {
     if (!h) return PULDA_ERR_INVALID;
     if (!h->have_phi) return fail(h, PULDA_ERR_INVALID, "no Phi drawn yet: call pulda_phi_step or pulda_sweep first");
-    CU(h, cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * 4, h->stream));
+    CU(h, clear_z_counters(h));
     return run_z(h, h->doc_off, h->doc_order, h->D, h->n_long, h->w, h->z, h->seed, static_cast<uint32_t>(h->sweep), 0);
 }
 
@@ -445,7 +452,7 @@ pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids, const int64_t
     CU(h, cudaMemcpyAsync(doff, doc_offsets, sizeof(int64_t) * (D_new + 1), cudaMemcpyHostToDevice, st));
     CU(h, cudaMemcpyAsync(dord, ord.data(), sizeof(int32_t) * D_new, cudaMemcpyHostToDevice, st));
     launch_init_z(N, h->K, seed, 0, dz, st);
-    CU(h, cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * 4, st));
+    CU(h, clear_z_counters(h));
     const int64_t n_long = count_long(doc_offsets, ord);
     for (int32_t sw = 1; sw <= n_sweeps; ++sw) {
         s = run_z(h, doff, dord, D_new, n_long, dw, dz, seed, static_cast<uint32_t>(sw), 0);
@@ -480,6 +487,10 @@ pulda_status pulda_stats(pulda_handle *h, pulda_sweep_stats *out) {
     out->cum_a_branch = static_cast<int64_t>(st[ST_COUNT + ST_ABRANCH]);
     out->cum_sum_min = static_cast<int64_t>(st[ST_COUNT + ST_SUMMIN]);
     out->cum_zero_mass = static_cast<int64_t>(st[ST_COUNT + ST_ZEROMASS]);
+    out->sum_inter = static_cast<int64_t>(st[ST_SUMINT]);
+    out->docside = static_cast<int64_t>(st[ST_DOCSIDE]);
+    out->cum_sum_inter = static_cast<int64_t>(st[ST_COUNT + ST_SUMINT]);
+    out->cum_docside = static_cast<int64_t>(st[ST_COUNT + ST_DOCSIDE]);
     return PULDA_OK;
 }
 

@@ -549,8 +549,8 @@ struct DocRun {
 // current topics first: with positions < pos already resampled in this pass
 // that is exactly m of the sequential sampler at `pos`.  Returns the run's
 // final (sweep, pos) through r.
-__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, u64 &st_ab, u64 &st_min,
-                           u64 &st_zero) {
+__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 (&st)[6]) {
+    u64 &st_tok = st[0], &st_ab = st[1], &st_min = st[2], &st_zero = st[3], &st_int = st[4], &st_doc = st[5];
     const int lane = threadIdx.x & 31;
     const int K = a.K;
     const bool use_bm = a.bitmap != nullptr && a.path != 1;
@@ -627,6 +627,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
             }
             __syncwarp();
             st_min += static_cast<u64>(kd < n_w ? kd : n_w);
+            st_doc += kd < n_w ? 1u : 0u;
             const bool docside = use_bm && (a.path == 2 || kd < n_w);
             const uint32_t *qcol = a.q + col;
             // per-lane partial sums of q m, in ascending topic order across lanes
@@ -637,6 +638,8 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
             int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
             if (docside) {
                 uint32_t rem = bm.x & mbits;
+                const int nj = __reduce_add_sync(0xFFFFFFFFu, static_cast<unsigned>(__popc(rem)));
+                st_int += static_cast<u64>(nj);
 #pragma unroll
                 for (int t = 0; t < kGather; ++t) {
                     bp[t] = -1;
@@ -660,8 +663,14 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
                 seg = (n_w + 31) >> 5;
                 seg0 = seg * lane;
                 const int seg1 = min(seg0 + seg, n_w);
+                unsigned nj = 0;
 #pragma unroll 4
-                for (int j = seg0; j < seg1; ++j) acc += static_cast<u64>(qcol[j]) * m[mi(a.topic[col + j])];
+                for (int j = seg0; j < seg1; ++j) {
+                    const uint32_t mk = m[mi(a.topic[col + j])];
+                    acc += static_cast<u64>(qcol[j]) * mk;
+                    nj += mk != 0u;
+                }
+                st_int += static_cast<u64>(__reduce_add_sync(0xFFFFFFFFu, nj));
             }
             const u64 incl = warp_incl_scan64(acc);
             const u64 B = __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -736,15 +745,16 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 &st_tok, 
     }
 }
 
-__device__ void flush_z_stats(unsigned long long *stats, u64 st_tok, u64 st_ab, u64 st_min, u64 st_zero) {
-    atomicAdd(&stats[ST_TOKENS], st_tok);
-    atomicAdd(&stats[ST_ABRANCH], st_ab);
-    atomicAdd(&stats[ST_SUMMIN], st_min);
-    atomicAdd(&stats[ST_ZEROMASS], st_zero);
-    atomicAdd(&stats[ST_COUNT + ST_TOKENS], st_tok);
-    atomicAdd(&stats[ST_COUNT + ST_ABRANCH], st_ab);
-    atomicAdd(&stats[ST_COUNT + ST_SUMMIN], st_min);
-    atomicAdd(&stats[ST_COUNT + ST_ZEROMASS], st_zero);
+// Adds a warp's z-step counters to the sweep's and the running totals.
+// c = {tokens, a-branch draws, sum min(K_d,K_v), zero-mass tokens,
+//      sum |J|, tokens with K_d < K_v}.
+__device__ void flush_z_stats(unsigned long long *stats, const u64 (&c)[6]) {
+    const int slot[6] = {ST_TOKENS, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_SUMINT, ST_DOCSIDE};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        atomicAdd(&stats[slot[i]], c[i]);
+        atomicAdd(&stats[ST_COUNT + slot[i]], c[i]);
+    }
 }
 
 // One chain, one document per warp (dynamically scheduled, longest first),
@@ -753,7 +763,7 @@ __global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
     uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
-    u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
+    u64 st[6] = {0, 0, 0, 0, 0, 0};
     const uint32_t sweep = sweep_of(a);
     for (;;) {
         int item = 0;
@@ -764,9 +774,9 @@ __global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
         const int64_t s = a.doc_off[d];
         DocRun r{a.w + s, a.z + s, static_cast<int>(a.doc_off[d + 1] - s), a.seed, a.index_base + s, sweep, 0,
                  a.doc_off[d + 1] - s, 1};
-        z_doc_warp(a, m, r, st_tok, st_ab, st_min, st_zero);
+        z_doc_warp(a, m, r, st);
     }
-    if (lane == 0) flush_z_stats(a.stats, st_tok, st_ab, st_min, st_zero);
+    if (lane == 0) flush_z_stats(a.stats, st);
 }
 
 // Many chains: the work list holds (chain, document) pairs, longest first
@@ -786,9 +796,9 @@ __global__ void __launch_bounds__(256, 2) k_z_step_multi(const ZArgs *chains, co
         const int64_t s = a.doc_off[it.y];
         DocRun r{a.w + s, a.z + s, static_cast<int>(a.doc_off[it.y + 1] - s), a.seed, a.index_base + s, sweep_of(a),
                  0, a.doc_off[it.y + 1] - s, 1};
-        u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
-        z_doc_warp(a, m, r, st_tok, st_ab, st_min, st_zero);
-        if (lane == 0) flush_z_stats(a.stats, st_tok, st_ab, st_min, st_zero);
+        u64 st[6] = {0, 0, 0, 0, 0, 0};
+        z_doc_warp(a, m, r, st);
+        if (lane == 0) flush_z_stats(a.stats, st);
     }
 }
 
@@ -834,7 +844,7 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
     uint32_t *m32 = reinterpret_cast<uint32_t *>(m);
     const bool use_bm = a.bitmap != nullptr && a.path != 1;
     const int w0 = gl * kWordsPerLane;         // first bitmap word of this lane
-    u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
+    u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0, st_int = 0, st_doc = 0;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.work, 1);
@@ -946,6 +956,7 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
                         }
                     }
                     if (gl == 0) st_min += static_cast<u64>(kd < n_w ? kd : n_w);
+                    if (gl == 0 && kd < n_w) ++st_doc;
                 }
                 __syncwarp();
                 const bool docside = act && use_bm && (a.path == 2 || kd < n_w);
@@ -987,6 +998,18 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
                 } else if (act) {
 #pragma unroll 4
                     for (int j = j0; j < j1; ++j) s0 += static_cast<u64>(a.q[col + j]) * m[a.topic[col + j]];
+                }
+                {
+                    // |J| of this token: the group's count of intersection entries
+                    int nj = 0;
+                    if (docside) {
+                        nj = __popc(c0.x & mb0) + __popc(c1.x & mb1) + __popc(c2.x & mb2) + __popc(c3.x & mb3);
+                    } else if (act) {
+                        for (int j = j0; j < j1; ++j) nj += m[a.topic[col + j]] != 0;
+                    }
+#pragma unroll
+                    for (int o = 1; o < kGroup; o <<= 1) nj += __shfl_xor_sync(0xFFFFFFFFu, nj, o);
+                    if (gl == 0 && act) st_int += static_cast<u64>(nj);
                 }
                 const u64 acc = s0 + s1 + s2 + s3;
                 const u64 incl = group_incl_scan64(acc, gl);
@@ -1069,18 +1092,10 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
             if (gl == 0) st_tok += static_cast<u64>(max(0, min(kGroup, len - t0)));
         }
     }
-    // one atomic per warp
-    st_tok = warp_sum64(st_tok); st_ab = warp_sum64(st_ab); st_min = warp_sum64(st_min); st_zero = warp_sum64(st_zero);
-    if (lane == 0) {
-        atomicAdd(&a.stats[ST_TOKENS], st_tok);
-        atomicAdd(&a.stats[ST_ABRANCH], st_ab);
-        atomicAdd(&a.stats[ST_SUMMIN], st_min);
-        atomicAdd(&a.stats[ST_ZEROMASS], st_zero);
-        atomicAdd(&a.stats[ST_COUNT + ST_TOKENS], st_tok);
-        atomicAdd(&a.stats[ST_COUNT + ST_ABRANCH], st_ab);
-        atomicAdd(&a.stats[ST_COUNT + ST_SUMMIN], st_min);
-        atomicAdd(&a.stats[ST_COUNT + ST_ZEROMASS], st_zero);
-    }
+    // one set of atomics per warp
+    const u64 c[6] = {warp_sum64(st_tok), warp_sum64(st_ab), warp_sum64(st_min), warp_sum64(st_zero),
+                      warp_sum64(st_int), warp_sum64(st_doc)};
+    if (lane == 0) flush_z_stats(a.stats, c);
 }
 
 // ============================================================ batches
@@ -1108,7 +1123,7 @@ __global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_serve_step(ZArgs a, S
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
     uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
-    u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0;
+    u64 st[6] = {0, 0, 0, 0, 0, 0};
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(work, 1);
@@ -1130,13 +1145,13 @@ __global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_serve_step(ZArgs a, S
         }
         DocRun r{arena_w + sl.off, z, sl.len, sl.seed, 0, sweep, pos, slice,
                  static_cast<int>(sl.sweep_end - sweep)};
-        z_doc_warp(a, m, r, st_tok, st_ab, st_min, st_zero);
+        z_doc_warp(a, m, r, st);
         if (lane == 0) {
             slots[idx].sweep = r.sweep;
             slots[idx].pos = r.pos;
         }
     }
-    if (lane == 0) flush_z_stats(a.stats, st_tok, st_ab, st_min, st_zero);
+    if (lane == 0) flush_z_stats(a.stats, st);
 }
 
 // ============================================================== exports

@@ -28,9 +28,10 @@ constexpr int kMaxKBitmap = 1024;
 enum : uint32_t { TAG_INIT = 1, TAG_POIS = 2, TAG_BETA = 3, TAG_REDRAW_POIS = 4, TAG_REDRAW_BETA = 5, TAG_Z = 6 };
 
 // Slots of the per-sweep counter block on the device.
-enum : int { ST_TOKENS = 0, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_DEADROWS, ST_NNZPHI, ST_ERROR, ST_COUNT = 8 };
-// Running totals of the first four slots live at ST_COUNT + slot and are
-// cleared only at pulda_init.
+enum : int { ST_TOKENS = 0, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_DEADROWS, ST_NNZPHI, ST_ERROR, ST_SUMINT,
+             ST_DOCSIDE, ST_COUNT = 12 };
+// Running totals of the z-step slots live at ST_COUNT + slot and are cleared
+// only at pulda_init.
 constexpr int ST_TOTAL_SLOTS = 2 * ST_COUNT;
 enum : unsigned long long { ERR_DEGENERATE = 1, ERR_INTERNAL = 2 };
 

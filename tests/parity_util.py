@@ -66,7 +66,8 @@ def lockstep(w, doc_off, K: int, V: int, alpha, beta: float, seed: int, sweeps: 
             assert not msg, f"sweep {it}: " + msg
             st = s.stats()
             assert st["tokens"] == ch.stats[0] and st["a_branch"] == ch.stats[1] and \
-                st["sum_min"] == ch.stats[2] and st["zero_mass"] == ch.stats[3], f"sweep {it}: stats {st} vs {ch.stats}"
+                st["sum_min"] == ch.stats[2] and st["zero_mass"] == ch.stats[3] and \
+                st["sum_inter"] == ch.stats[4] and st["docside"] == ch.stats[5], f"sweep {it}: stats {st} vs {ch.stats}"
             assert st["dead_rows"] == ch.dead_rows, f"sweep {it}: dead rows {st['dead_rows']} vs {ch.dead_rows}"
             if check_counts_every and it % check_counts_every == 0:
                 assert np.array_equal(s.n(), ch.n().T), f"sweep {it}: n differs"
