@@ -78,6 +78,15 @@ pulda_status check_corpus(pulda_handle *h, const int32_t *w, const int64_t *off,
     return PULDA_OK;
 }
 
+// Topic histograms of the most frequent words, before the per-word pass.
+cudaError_t run_heavy(pulda_handle *h) {
+    if (h->n_heavy == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(h->heavy_hist, 0, sizeof(uint32_t) * static_cast<size_t>(h->n_heavy) * h->K, h->stream);
+    if (e != cudaSuccess) return e;
+    launch_heavy_hist(h->d_self, h->d_heavy_chunks, static_cast<int>(h->heavy_chunks.size()), h->K, h->stream);
+    return cudaGetLastError();
+}
+
 // The per-sweep z-step counters start from zero at every z-step.
 cudaError_t clear_z_counters(pulda_handle *h) {
     cudaError_t e = cudaMemsetAsync(h->stats + ST_TOKENS, 0, sizeof(unsigned long long) * 4, h->stream);
@@ -140,6 +149,7 @@ PhiArgs phi_args(pulda_handle *h) {
     a.topic = h->topic; a.c = h->c; a.q = h->q; a.athr = h->athr; a.atopic = h->atopic;
     a.A = h->A; a.vose_p = h->vose_p; a.vose_stack = h->vose_stack; a.bitmap = h->bitmap; a.KW = h->KW;
     a.alpha = h->alpha; a.work = h->work; a.stats = h->stats;
+    a.heavy_row = h->heavy_row; a.heavy_hist = h->heavy_hist; a.n_heavy = h->n_heavy;
     return a;
 }
 
@@ -223,7 +233,6 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     ALLOC(h->A, V); ALLOC(h->vose_p, h->cap); ALLOC(h->vose_stack, h->cap);
     if (K <= kMaxKBitmap) ALLOC(h->bitmap, static_cast<size_t>(V) * h->KW);
     ALLOC(h->work, 4); ALLOC(h->stats, ST_TOTAL_SLOTS);
-#undef ALLOC
     cudaStream_t st = h->stream;
     CUI(cudaMemcpyAsync(h->w, word_ids, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
     std::vector<int64_t> off0(1, 0);
@@ -250,6 +259,31 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     std::stable_sort(word_order.begin(), word_order.end(),
                      [&](int32_t a, int32_t b) { return woff[a + 1] - woff[a] > woff[b + 1] - woff[b]; });
     CUI(cudaMemcpyAsync(h->word_order, word_order.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, st));
+    // the most frequent words are histogrammed in chunks by many CTAs
+    {
+        std::vector<int32_t> row(V, -1);
+        for (int32_t v : word_order) {
+            const int64_t cnt = woff[v + 1] - woff[v];
+            if (cnt <= kHeavyWord) break;
+            row[v] = h->n_heavy;
+            for (int64_t b = woff[v]; b < woff[v + 1]; b += kHeavyChunk)
+                h->heavy_chunks.push_back(HeavyChunk{0, h->n_heavy, v, 0, b, std::min(woff[v + 1], b + kHeavyChunk)});
+            ++h->n_heavy;
+        }
+        ALLOC(h->heavy_row, V);
+        ALLOC(h->d_self, 1);
+        if (h->n_heavy > 0) {
+            ALLOC(h->heavy_hist, static_cast<size_t>(h->n_heavy) * K);
+            ALLOC(h->d_heavy_chunks, h->heavy_chunks.size());
+            CUI(cudaMemcpyAsync(h->d_heavy_chunks, h->heavy_chunks.data(), sizeof(HeavyChunk) * h->heavy_chunks.size(),
+                                cudaMemcpyHostToDevice, st));
+        }
+        CUI(cudaMemcpyAsync(h->heavy_row, row.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, st));
+        PhiArgs self = phi_args(h);
+        CUI(cudaMemcpyAsync(h->d_self, &self, sizeof(PhiArgs), cudaMemcpyHostToDevice, st));
+        CUI(cudaStreamSynchronize(st));
+    }
+#undef ALLOC
     CUI(cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * ST_TOTAL_SLOTS, st));
     launch_init_z(N, K, seed, 0, h->z, st);
     CUI(cudaGetLastError());
@@ -294,6 +328,7 @@ pulda_status pulda_phi_step(pulda_handle *h) {
     CU(h, cudaMemsetAsync(h->work, 0, sizeof(int), st));
     CU(h, cudaMemsetAsync(h->S, 0, sizeof(unsigned long long) * h->K, st));
     PhiArgs a = phi_args(h);
+    CU(h, run_heavy(h));
     launch_phi_counts(a, true, h->phi_grid, st);
     launch_phi_fixup(a, st);
     launch_colptr_scan(a, st);
@@ -362,6 +397,7 @@ pulda_status pulda_get_counts(pulda_handle *h, int32_t *n_kv, int32_t *m_dk) {
         // rebuild n from the current z (counts only, no draws)
         PhiArgs a = phi_args(h);
         CU(h, cudaMemsetAsync(h->work, 0, sizeof(int), st));
+        CU(h, run_heavy(h));
         launch_phi_counts(a, false, h->phi_grid, st);
         int32_t *dn = nullptr;
         CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dn), sizeof(int32_t) * static_cast<size_t>(h->K) * h->V, st));

@@ -126,6 +126,7 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     }
     std::vector<PhiArgs> hp(n_chains);
     std::vector<ZArgs> hz(n_chains);
+    std::vector<HeavyChunk> heavy;
     std::vector<std::pair<int64_t, int2>> wi, di;    // (weight, (chain, item))
     int kmax = 1;
     for (int32_t c = 0; c < n_chains; ++c) {
@@ -135,6 +136,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         hz[c] = z_args(h, h->doc_off, h->doc_order, h->D, h->w, h->z, h->seed, 0, 0);
         hz[c].sweep_ptr = d_sweep;
         kmax = std::max(kmax, h->K);
+        for (HeavyChunk hc : h->heavy_chunks) {
+            hc.chain = c;
+            heavy.push_back(hc);
+        }
         std::vector<int64_t> woff(h->V + 1);
         if (cudaMemcpy(woff.data(), h->word_off, sizeof(int64_t) * (h->V + 1), cudaMemcpyDeviceToHost) != cudaSuccess) {
             b->err = "reading word offsets failed";
@@ -153,7 +158,9 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     for (size_t i = 0; i < wi.size(); ++i) wlist[i] = wi[i].second;
     for (size_t i = 0; i < di.size(); ++i) dlist[i] = di[i].second;
     int2 *d_wl = nullptr, *d_dl = nullptr;
-    if (balloc(b, &d_wl, wlist.size()) != cudaSuccess || balloc(b, &d_dl, dlist.size()) != cudaSuccess) {
+    HeavyChunk *d_heavy = nullptr;
+    if (balloc(b, &d_wl, wlist.size()) != cudaSuccess || balloc(b, &d_dl, dlist.size()) != cudaSuccess ||
+        balloc(b, &d_heavy, heavy.size()) != cudaSuccess) {
         b->err = "device allocation of the work lists failed";
         return bail(PULDA_ERR_OOM);
     }
@@ -164,6 +171,8 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         cudaMemcpyAsync(d_wl, wlist.data(), sizeof(int2) * wlist.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(d_dl, dlist.data(), sizeof(int2) * dlist.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(d_sweep, &zero, sizeof zero, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (!heavy.empty() && cudaMemcpyAsync(d_heavy, heavy.data(), sizeof(HeavyChunk) * heavy.size(),
+                                           cudaMemcpyHostToDevice, st) != cudaSuccess) ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         b->err = "uploading the batch descriptors failed";
         return bail(PULDA_ERR_CUDA);
@@ -171,6 +180,8 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     BatchLaunch &bl = b->bl;
     bl.phi = d_phi;
     bl.z = d_z;
+    bl.heavy = d_heavy;
+    bl.n_heavy = static_cast<int>(heavy.size());
     bl.n_chains = n_chains;
     bl.phi_items = d_wl;
     bl.n_phi_items = static_cast<int>(wlist.size());

@@ -42,6 +42,13 @@ struct pulda_handle {
     int *work = nullptr;
     unsigned long long *stats = nullptr;
     int64_t cap = 0;   // capacity of the per-word tables: K * V entries
+    // words histogrammed by several CTAs (more than kHeavyWord tokens)
+    int32_t *heavy_row = nullptr;
+    uint32_t *heavy_hist = nullptr;
+    int n_heavy = 0;
+    std::vector<pulda::HeavyChunk> heavy_chunks;     // host copy (chain 0)
+    pulda::HeavyChunk *d_heavy_chunks = nullptr;
+    pulda::PhiArgs *d_self = nullptr;         // this chain's PhiArgs on the device (for the heavy pass)
 };
 
 

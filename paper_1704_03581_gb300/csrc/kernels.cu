@@ -186,15 +186,23 @@ __device__ __forceinline__ uint32_t sweep_of(const ZArgs &a) { return a.sweep_pt
 // One word v of one chain, by the whole CTA: histogram of the word's topics
 // -> n_{.,v}; compacted n column; when `draw`, the Poisson draws c_{.,v},
 // the compacted c column, and S_k += c_{k,v}.  hist/cbin hold K entries each.
-__device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, uint32_t *cbin, int *scan_tmp) {
+__device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, uint32_t *cbin, int *scan_tmp,
+                         const uint32_t *geo) {
     const int K = a.K;
     const uint32_t sweep = sweep_of(a);
     const int per = (K + kPhiBlock - 1) / kPhiBlock;     // bins owned by each thread, contiguous
     const int64_t wbeg = a.word_off[v], wend = a.word_off[v + 1];
-    for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
-    __syncthreads();
-    for (int64_t t = wbeg + threadIdx.x; t < wend; t += kPhiBlock) atomicAdd(&hist[a.z[a.perm[t]]], 1u);
-    __syncthreads();
+    const int hrow = a.heavy_row ? a.heavy_row[v] : -1;
+    if (hrow >= 0) {
+        const uint32_t *hh = a.heavy_hist + static_cast<int64_t>(hrow) * K;
+        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = hh[k]; cbin[k] = 0; }
+        __syncthreads();
+    } else {
+        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
+        __syncthreads();
+        for (int64_t t = wbeg + threadIdx.x; t < wend; t += kPhiBlock) atomicAdd(&hist[a.z[a.perm[t]]], 1u);
+        __syncthreads();
+    }
     if (do_draw) {
         // entries with n_{k,v} = l >= 1: c ~ Pois(beta + l)
         for (int k = threadIdx.x; k < K; k += kPhiBlock) {
@@ -204,21 +212,30 @@ __device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, 
                 cbin[k] = draw_entry(a.tab, l, x.x, x.y);
             }
         }
-        // entries with n_{k,v} = 0: Pois(beta) by geometric skip-ahead
-        if (threadIdx.x == 0) {
-            int64_t pos = -1;
-            uint32_t h = 0;
-            for (;;) {
-                const U4 x = draw(a.seed, static_cast<uint32_t>(v), h++, sweep, TAG_BETA, 0);
-                const int g = geo_gap(a.tab.geo, x.x);
-                if (g < 0) {
-                    pos += kGeoLen;
-                    if (pos >= K - 1) break;
-                    continue;
+        // entries with n_{k,v} = 0: Pois(beta) by geometric skip-ahead.  The
+        // walk's draws h = 0, 1, ... do not depend on where it stands, so
+        // warp 0 draws 32 of them at once and a prefix sum of the gaps places
+        // them -- the same hits, in the same order, as one thread walking.
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int pos = -1;
+            for (uint32_t h0 = 0;; h0 += 32) {
+                const U4 x = draw(a.seed, static_cast<uint32_t>(v), h0 + lane, sweep, TAG_BETA, 0);
+                const int g = geo_gap(geo, x.x);
+                const int step = g < 0 ? kGeoLen : g + 1;      // positions advanced by this draw
+                int incl = step;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
                 }
-                pos += g + 1;
-                if (pos >= K) break;
-                if (hist[pos] == 0) cbin[pos] = table_draw(a.tab, 0, x.y, x.z);
+                const int p = pos + incl;                       // the hit's position (or where a skip ends)
+                const bool stop = g < 0 ? p >= K - 1 : p >= K;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, stop);
+                const int first_stop = bal ? __ffs(bal) - 1 : 32;
+                if (lane < first_stop && g >= 0 && hist[p] == 0) cbin[p] = table_draw(a.tab, 0, x.y, x.z);
+                if (bal) break;
+                pos = __shfl_sync(0xFFFFFFFFu, p, 31);
             }
         }
         __syncthreads();
@@ -256,13 +273,15 @@ __global__ void __launch_bounds__(kPhiBlock) k_phi_counts(PhiArgs a, bool do_dra
     extern __shared__ uint32_t sm[];
     __shared__ int scan_tmp[kPhiBlock / 32 + 1];
     __shared__ int s_item;
+    __shared__ uint32_t geo[kGeoLen];
+    for (int i = threadIdx.x; i < kGeoLen; i += kPhiBlock) geo[i] = a.tab.geo[i];
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
         __syncthreads();
         const int item = s_item;
         __syncthreads();
         if (item >= a.V) break;
-        phi_word(a, a.word_order[item], do_draw, sm, sm + a.K, scan_tmp);
+        phi_word(a, a.word_order[item], do_draw, sm, sm + a.K, scan_tmp, geo);
     }
 }
 
@@ -273,6 +292,8 @@ __global__ void __launch_bounds__(kPhiBlock) k_phi_counts_multi(const PhiArgs *c
     extern __shared__ uint32_t sm[];
     __shared__ int scan_tmp[kPhiBlock / 32 + 1];
     __shared__ int s_item;
+    __shared__ uint32_t geo[kGeoLen];
+    int geo_chain = -1;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(work, 1);
         __syncthreads();
@@ -280,8 +301,30 @@ __global__ void __launch_bounds__(kPhiBlock) k_phi_counts_multi(const PhiArgs *c
         __syncthreads();
         if (item >= n_items) break;
         const int2 it = items[item];
-        phi_word(chains[it.x], it.y, do_draw, sm, sm + kmax, scan_tmp);
+        if (it.x != geo_chain) {          // the geometric table depends on the chain's beta
+            for (int i = threadIdx.x; i < kGeoLen; i += kPhiBlock) geo[i] = chains[it.x].tab.geo[i];
+            geo_chain = it.x;
+            __syncthreads();
+        }
+        phi_word(chains[it.x], it.y, do_draw, sm, sm + kmax, scan_tmp, geo);
     }
+}
+
+// Topic histograms of the most frequent words, one chunk of a word's tokens
+// per CTA, added into the word's row of heavy_hist (zeroed before).
+__global__ void __launch_bounds__(kPhiBlock) k_heavy_hist(const PhiArgs *chains, const HeavyChunk *chunks, int kmax) {
+    extern __shared__ uint32_t hs[];
+    const HeavyChunk c = chunks[blockIdx.x];
+    const PhiArgs &a = chains[c.chain];
+    const int K = a.K;
+    for (int k = threadIdx.x; k < K; k += kPhiBlock) hs[k] = 0;
+    __syncthreads();
+    for (int64_t t = c.begin + threadIdx.x; t < c.end; t += kPhiBlock) atomicAdd(&hs[a.z[a.perm[t]]], 1u);
+    __syncthreads();
+    uint32_t *row = a.heavy_hist + static_cast<int64_t>(c.row) * K;
+    for (int k = threadIdx.x; k < K; k += kPhiBlock)
+        if (hs[k]) atomicAdd(&row[k], hs[k]);
+    (void)kmax;
 }
 
 // n_{k,v} from the compacted n column of word v (binary search), 0 if absent.
@@ -415,87 +458,103 @@ __global__ void k_colptr_scan_multi(const PhiArgs *chains) {
 }
 
 // =================================================== Phi-step: tables
-// Per word (one thread each): phi = fp32(c/S); fixed-point weights q with
+// Per word: phi = fp32(c/S); fixed-point weights q with
 // 24 bits relative to the column maximum (q >= 1); alpha-part masses
 // a = round(q alpha 2^16), A = sigma_a; Vose alias table over a; bitmap of
 // the word's nonzero topics.
-__device__ void phi_tables_word(const PhiArgs &a, int v) {
-    {
-        const int n = a.nnz_c[v];
-        const int64_t src = static_cast<int64_t>(v) * a.K;
-        const int64_t out = a.col_ptr[v];
-        if (a.bitmap) {
-            uint2 *bm = a.bitmap + static_cast<int64_t>(v) * a.KW;
-            int j = 0;
-            for (int wi = 0; wi < a.KW; ++wi) {
-                const int before = j;
-                uint32_t bits = 0;
-                while (j < n && (a.cst_k[src + j] >> 5) == wi) { bits |= 1u << (a.cst_k[src + j] & 31); ++j; }
-                bm[wi] = make_uint2(bits, static_cast<uint32_t>(before));
-            }
+// The same per-word tables, one warp per word: the per-entry arithmetic in
+// parallel, the Vose pairing (sequential by definition) in lane 0.
+__device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
+    const int lane = threadIdx.x & 31;
+    const int n = a.nnz_c[v];
+    const int64_t src = static_cast<int64_t>(v) * a.K;
+    const int64_t out = a.col_ptr[v];
+    if (a.bitmap) {
+        uint2 *bm = a.bitmap + static_cast<int64_t>(v) * a.KW;
+        for (int wi = lane; wi < a.KW; wi += 32) {
+            int lo = 0, hi = n;                       // first entry with topic >= 32 wi
+            while (lo < hi) { const int mid = (lo + hi) >> 1; if (a.cst_k[src + mid] < 32 * wi) lo = mid + 1; else hi = mid; }
+            uint32_t bits = 0;
+            for (int j = lo; j < n && (a.cst_k[src + j] >> 5) == wi; ++j) bits |= 1u << (a.cst_k[src + j] & 31);
+            bm[wi] = make_uint2(bits, static_cast<uint32_t>(lo));
         }
-        if (n == 0) { a.A[v] = 0; return; }
-        double phimax = 0.0;
-        for (int j = 0; j < n; ++j) {
-            const int k = a.cst_k[src + j];
-            const double p = __ddiv_rn(static_cast<double>(a.cst_c[src + j]), static_cast<double>(a.S[k]));
-            phimax = p > phimax ? p : phimax;
-        }
-        // phimax = f 2^e with f in [1/2, 1); scale = 2^(24 - e) (exact)
-        const long long bits = __double_as_longlong(phimax);
-        const int e = static_cast<int>((bits >> 52) & 0x7FF) - 1022;
-        const double scale = __longlong_as_double(static_cast<long long>(1023 + 24 - e) << 52);
-        u64 Asum = 0;
-        for (int j = 0; j < n; ++j) {
-            const int k = a.cst_k[src + j];
-            const uint32_t c = a.cst_c[src + j];
-            const double p = __ddiv_rn(static_cast<double>(c), static_cast<double>(a.S[k]));
-            const double qq = floor(__dadd_rn(__dmul_rn(p, scale), 0.5));
-            const uint32_t qv = qq < 1.0 ? 1u : static_cast<uint32_t>(qq);
-            const double at = __dmul_rn(__dmul_rn(static_cast<double>(qv), static_cast<double>(a.alpha[k])), 65536.0);
-            const u64 am = static_cast<u64>(floor(__dadd_rn(at, 0.5)));
-            a.topic[out + j] = static_cast<uint16_t>(k);
-            a.c[out + j] = c;
-            a.q[out + j] = qv;
-            a.vose_p[out + j] = am;
-            Asum += am;
-        }
-        a.A[v] = Asum;
-        // Vose: small stack grows up from 0, large stack down from n-1
-        u64 *P = a.vose_p + out;
-        uint16_t *stk = a.vose_stack + out;
-        int ns = 0, nl = 0;
-        for (int j = 0; j < n; ++j) {
-            a.athr[out + j] = 0xFFFFFFFFu;
-            a.atopic[out + j] = a.topic[out + j];
-        }
-        if (Asum == 0) return;
-        for (int j = 0; j < n; ++j) {
-            P[j] *= static_cast<u64>(n);
-            if (P[j] < Asum) stk[ns++] = static_cast<uint16_t>(j);
-            else { stk[n - 1 - nl] = static_cast<uint16_t>(j); ++nl; }
-        }
-        while (ns > 0 && nl > 0) {
-            const int s = stk[--ns];
-            --nl;
-            const int l = stk[n - 1 - nl];
-            a.athr[out + s] = static_cast<uint32_t>((static_cast<unsigned __int128>(P[s]) << 32) / Asum);
-            a.atopic[out + s] = a.topic[out + l];
-            P[l] -= Asum - P[s];
-            if (P[l] < Asum) stk[ns++] = static_cast<uint16_t>(l);
-            else { stk[n - 1 - nl] = static_cast<uint16_t>(l); ++nl; }
-        }
+    }
+    if (n == 0) {
+        if (lane == 0) a.A[v] = 0;
+        return;
+    }
+    double phimax = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        const int k = a.cst_k[src + j];
+        const double p = __ddiv_rn(static_cast<double>(a.cst_c[src + j]), static_cast<double>(a.S[k]));
+        a.vose_p[out + j] = static_cast<u64>(__double_as_longlong(p));    // phi, kept for the second pass
+        phimax = p > phimax ? p : phimax;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const double y = __shfl_xor_sync(0xFFFFFFFFu, phimax, o);
+        phimax = y > phimax ? y : phimax;
+    }
+    // phimax = f 2^e with f in [1/2, 1); scale = 2^(24 - e) (exact)
+    const long long bits = __double_as_longlong(phimax);
+    const int e = static_cast<int>((bits >> 52) & 0x7FF) - 1022;
+    const double scale = __longlong_as_double(static_cast<long long>(1023 + 24 - e) << 52);
+    u64 asum = 0;
+    for (int j = lane; j < n; j += 32) {
+        const int k = a.cst_k[src + j];
+        const uint32_t c = a.cst_c[src + j];
+        const double p = __longlong_as_double(static_cast<long long>(a.vose_p[out + j]));
+        const double qq = floor(__dadd_rn(__dmul_rn(p, scale), 0.5));
+        const uint32_t qv = qq < 1.0 ? 1u : static_cast<uint32_t>(qq);
+        const double at = __dmul_rn(__dmul_rn(static_cast<double>(qv), static_cast<double>(a.alpha[k])), 65536.0);
+        const u64 am = static_cast<u64>(floor(__dadd_rn(at, 0.5)));
+        a.topic[out + j] = static_cast<uint16_t>(k);
+        a.c[out + j] = c;
+        a.q[out + j] = qv;
+        a.vose_p[out + j] = am * static_cast<u64>(n);   // scaled so each slot holds A units
+        a.athr[out + j] = 0xFFFFFFFFu;
+        a.atopic[out + j] = static_cast<uint16_t>(k);
+        asum += am;
+    }
+    asum = warp_sum64(asum);
+    if (lane == 0) a.A[v] = asum;
+    __syncwarp();
+    if (lane != 0 || asum == 0) return;
+    // Vose: small stack grows up from 0, large stack down from n-1
+    u64 *P = a.vose_p + out;
+    uint16_t *stk = a.vose_stack + out;
+    int ns = 0, nl = 0;
+    for (int j = 0; j < n; ++j) {
+        if (P[j] < asum) stk[ns++] = static_cast<uint16_t>(j);
+        else { stk[n - 1 - nl] = static_cast<uint16_t>(j); ++nl; }
+    }
+    while (ns > 0 && nl > 0) {
+        const int s = stk[--ns];
+        --nl;
+        const int l = stk[n - 1 - nl];
+        const u64 ps = P[s];
+        a.athr[out + s] = static_cast<uint32_t>((static_cast<unsigned __int128>(ps) << 32) / asum);
+        a.atopic[out + s] = a.topic[out + l];
+        const u64 pl = P[l] - (asum - ps);
+        P[l] = pl;
+        if (pl < asum) stk[ns++] = static_cast<uint16_t>(l);
+        else { stk[n - 1 - nl] = static_cast<uint16_t>(l); ++nl; }
     }
 }
 
+// One warp per word, most frequent first (their columns are the longest).
 __global__ void k_phi_tables(PhiArgs a) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) phi_tables_word(a, v);
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = wid; i < a.V; i += nwarps) phi_tables_word_warp(a, a.word_order[i]);
 }
 
 __global__ void k_phi_tables_multi(const PhiArgs *chains, const int2 *items, int n_items) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_items; i += gridDim.x * blockDim.x) {
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = wid; i < n_items; i += nwarps) {
         const int2 it = items[i];
-        phi_tables_word(chains[it.x], it.y);
+        phi_tables_word_warp(chains[it.x], it.y);
     }
 }
 
@@ -1108,6 +1167,8 @@ __global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_
         const PhiArgs &a = chains[c];
         for (int k = threadIdx.x; k < a.K; k += blockDim.x) a.S[k] = 0;
         for (int i = threadIdx.x; i < ST_COUNT; i += blockDim.x) a.stats[i] = 0;
+        if (a.heavy_hist)
+            for (int64_t i = threadIdx.x; i < static_cast<int64_t>(a.n_heavy) * a.K; i += blockDim.x) a.heavy_hist[i] = 0;
     }
 }
 
@@ -1257,8 +1318,20 @@ void launch_colptr_scan(const PhiArgs &a, cudaStream_t st) {
 }
 
 void launch_phi_tables(const PhiArgs &a, cudaStream_t st) {
-    const int grid = (a.V + 127) / 128;
-    k_phi_tables<<<grid, 128, 0, st>>>(a);
+    const int grid = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(a.V) * 32 + 255) / 256, 16LL * sm_count()));
+    k_phi_tables<<<std::max(grid, 1), 256, 0, st>>>(a);
+}
+
+void launch_phi_tables_multi(const PhiArgs *chains, const int2 *items, int n_items, cudaStream_t st) {
+    const int grid = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(n_items) * 32 + 255) / 256, 16LL * sm_count()));
+    k_phi_tables_multi<<<std::max(grid, 1), 256, 0, st>>>(chains, items, n_items);
+}
+
+void launch_heavy_hist(const PhiArgs *chains, const HeavyChunk *chunks, int n_chunks, int kmax, cudaStream_t st) {
+    if (n_chunks <= 0) return;
+    static bool opted_in = false;
+    if (!opted_in) { allow_dynamic_smem(k_heavy_hist); opted_in = true; }
+    k_heavy_hist<<<n_chunks, kPhiBlock, sizeof(uint32_t) * static_cast<size_t>(kmax), st>>>(chains, chunks, kmax);
 }
 
 size_t z_step_smem(int K, int warps_per_block) { return sizeof(uint32_t) * static_cast<size_t>(z_warp_words(K)) * warps_per_block; }
@@ -1293,11 +1366,12 @@ void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t s
 
 void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
     k_batch_begin_sweep<<<1, 256, 0, st>>>(b.phi, b.n_chains, b.sweep, b.work);
+    launch_heavy_hist(b.phi, b.heavy, b.n_heavy, b.kmax, st);
     k_phi_counts_multi<<<b.phi_grid, kPhiBlock, phi_counts_smem(b.kmax), st>>>(b.phi, b.phi_items, b.n_phi_items,
                                                                                 b.work, b.kmax, true);
     k_phi_fixup_multi<<<b.n_chains, kFixBlock, 0, st>>>(b.phi);
     k_colptr_scan_multi<<<b.n_chains, 1024, 0, st>>>(b.phi);
-    k_phi_tables_multi<<<(b.n_phi_items + 127) / 128, 128, 0, st>>>(b.phi, b.phi_items, b.n_phi_items);
+    launch_phi_tables_multi(b.phi, b.phi_items, b.n_phi_items, st);
     k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), st>>>(
         b.z, b.z_items, b.n_z_items, b.work + 1, b.kmax);
 }

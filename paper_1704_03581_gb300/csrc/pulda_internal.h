@@ -86,7 +86,24 @@ struct PhiArgs {
     const float *alpha;         // [K]
     int *work;                  // dynamic word counter
     unsigned long long *stats;  // [ST_COUNT]
+    // words with more than kHeavyWord tokens get their topic histogram from a
+    // separate pass split over many CTAs
+    const int32_t *heavy_row;   // [V] row of the word in heavy_hist, or -1
+    uint32_t *heavy_hist;       // [n_heavy * K]
+    int n_heavy;
 };
+
+// A word with more tokens than this is histogrammed in chunks of kHeavyChunk
+// tokens by several CTAs before the per-word Phi-step pass.
+constexpr int64_t kHeavyWord = int64_t(1) << 17;
+constexpr int64_t kHeavyChunk = int64_t(1) << 16;
+// One chunk of a heavy word: chain, row in heavy_hist, word, token range.
+struct HeavyChunk {
+    int32_t chain, row, v, pad;
+    int64_t begin, end;
+};
+void launch_heavy_hist(const PhiArgs *chains, const HeavyChunk *chunks, int n_chunks, int kmax, cudaStream_t st);
+void launch_phi_tables_multi(const PhiArgs *chains, const int2 *items, int n_items, cudaStream_t st);
 
 struct ZArgs {
     const int64_t *doc_off;     // [D+1]
@@ -137,6 +154,8 @@ int phi_counts_blocks_per_sm(int K);
 // One sweep of many chains: six launches, every kernel over all chains'
 // work items.  Pointers are device memory.
 struct BatchLaunch {
+    const HeavyChunk *heavy;     // heavy-word histogram chunks of every chain
+    int n_heavy;
     const PhiArgs *phi;          // [n_chains], sweep_ptr = sweep
     const ZArgs *z;              // [n_chains], sweep_ptr = sweep
     int n_chains;
