@@ -161,6 +161,25 @@ def z_bytes(tokens: int, sum_min: int, a_branch: int, docs: int) -> int:
     return 24 * tokens + 6 * sum_min + 6 * a_branch + 8 * docs
 
 
+def reduce_max(x: float, world: int, device=None) -> float:
+    """Max of x over all ranks (identity on one rank).  NCCL reduces device
+    tensors, gloo host tensors."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = device if device is not None else ("cuda" if dist.get_backend() == "nccl" else "cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_tokens_per_s(tokens_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank resamples its own chain of the same
+    size, so the job does world x tokens x steps in the slowest rank's time."""
+    return world * tokens_per_rank * steps / (ms_max / 1000.0)
+
+
 def cpu_count() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -248,11 +267,9 @@ def run_pulda(args, corpus, rank: int, world: int):
     phi_ms = sum(ev[k][0].elapsed_time(ev[k][1]) for k in range(K))
     z_ms = sum(ev[k][1].elapsed_time(ev[k][2]) for k in range(K))
     st1 = s.stats()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    ms_max = reduce_max(ms, world)
     if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-    ms_max = float(t.item())
     tokens = st1["cum_tokens"] - st0["cum_tokens"]
     sum_min = st1["cum_sum_min"] - st0["cum_sum_min"]
     a_br = st1["cum_a_branch"] - st0["cum_a_branch"]
@@ -275,10 +292,8 @@ def run_pulda(args, corpus, rank: int, world: int):
         s2.close()
         h2d = corpus.w.nbytes + corpus.doc_off.nbytes + 4 * K_TOPICS
         d2h = zh.nbytes
-        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * K * corpus.N / float(tt.item()), "unit": "tokens/s",
+        dt_max = reduce_max(dt, world)
+        e2e = {"value": aggregate_tokens_per_s(corpus.N, K, world, 1000.0 * dt_max), "unit": "tokens/s",
                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                "note": "pulda_init from host buffers + K sweeps + pulda_get_z to host, host clock"}
 
@@ -296,7 +311,7 @@ def run_pulda(args, corpus, rank: int, world: int):
                          f"{min(args.cpu_docs, corpus.D)} documents ({n_tok} tokens) of the same corpus, K=1000"}
     line = {
         "metric": METRIC,
-        "value": world * K * corpus.N / (ms_max / 1000.0),
+        "value": aggregate_tokens_per_s(corpus.N, K, world, ms_max),
         "unit": "tokens/s",
         "n_gpus": world,
         "steps": K,
