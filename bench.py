@@ -242,6 +242,7 @@ def run_pulda(args, corpus, rank: int, world: int):
                   stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp)
     s.sweep(args.burnin + args.warmup)
     s.sync()
+    lp_before = s.log_posterior()[0]          # the diagnostic, outside the timed region
     st0 = s.stats()
     first_timed = st0["sweep"] + 1
     K = args.steps
@@ -277,6 +278,10 @@ def run_pulda(args, corpus, rank: int, world: int):
     docside = st1["cum_docside"] - st0["cum_docside"]
     assert tokens == K * corpus.N, (tokens, K * corpus.N)
     nnz_phi = st1["nnz_phi"]
+    torch.cuda.synchronize()
+    t_lp = time.perf_counter()
+    lp_after = s.log_posterior()[0]
+    lp_ms = 1000.0 * (time.perf_counter() - t_lp)
     s.close()
 
     e2e = None
@@ -330,6 +335,8 @@ def run_pulda(args, corpus, rank: int, world: int):
                    "mean_min_kd_kv": sum_min / tokens, "mean_intersection": sum_int / tokens,
                    "docside_frac": docside / tokens, "a_branch_frac": a_br / tokens},
         "phi_step": {"ms_per_sweep": phi_ms / K, "nnz_phi": nnz_phi},
+        "log_posterior": {"before_timed": lp_before, "after_timed": lp_after, "ms_per_evaluation": lp_ms,
+                          "note": "collapsed log p(w, z | alpha, beta), not timed"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_z_step", "peak_kind": f"{peak_kind} HBM copy bandwidth",

@@ -55,7 +55,8 @@ typedef struct {
     int32_t zstep_path;     /* 0 = auto (iterate the smaller of the document's and the
                                word's nonzero topics), 1 = always iterate the word's Phi
                                column, 2 = iterate the document's topics whenever K <= 1024 */
-    int32_t warps_per_block;/* warp-per-document z-step: warps per CTA; 0 = chosen from K */
+    int32_t warps_per_block;/* warp-per-document z-step: warps per CTA, 1..4; 0 = 4, halved
+                               while the CTA's shared memory would pass 160 KB */
     int32_t docs_per_warp;  /* z-step documents per warp: 0 = auto (one), 1 = one, 4 = four
                                (needs K <= 1024; documents longer than 65,535 tokens still
                                go one per warp); results are identical */
@@ -128,6 +129,21 @@ pulda_status pulda_set_z(pulda_handle *h, const int16_t *z_host, int64_t sweep);
  *   n_kv_host int32[K*V], n_kv[k*V + v] = #{i : z_i = k, w_i = v}, or NULL
  *   m_dk_host int32[D*K], m_dk[d*K + k] = #{i in d : z_i = k}, or NULL */
 pulda_status pulda_get_counts(pulda_handle *h, int32_t *n_kv_host, int32_t *m_dk_host);
+
+/* pulda_log_posterior -- the diagnostic of the paper's experiments (Section 5,
+ * log-posterior trace plots): the collapsed log joint of the current topics,
+ * Theta and Phi integrated out of Dirichlet-multinomial LDA,
+ *   log p(w, z | alpha, beta)
+ *     = sum_d [lgamma(A) - lgamma(A + N_d) + sum_k (lgamma(alpha_k + m_dk) - lgamma(alpha_k))]
+ *     + sum_k [lgamma(V beta) - lgamma(V beta + n_k) + sum_v (lgamma(beta + n_kv) - lgamma(beta))],
+ * A = sum_k alpha_k, n_k = sum_v n_kv; up to a constant it is log p(z | w).
+ *   out_host double[3] = {total, document sum, topic sum}
+ * beta is the handle's float beta widened to double.  The counts are rebuilt
+ * from the current z on the GPU and every sum runs in a fixed order, so equal
+ * topics give equal bits.  Synchronous; uses 8 (D + V + K + 3) bytes of
+ * temporary device memory.  Errors: PULDA_ERR_INVALID (NULL out),
+ * PULDA_ERR_CUDA. */
+pulda_status pulda_log_posterior(pulda_handle *h, double *out_host);
 
 /* pulda_get_phi -- the Phi drawn by the most recent Phi-step, sparse by word
  * (column-compressed): entries col_ptr[v] .. col_ptr[v+1]-1 hold the nonzero
@@ -206,8 +222,8 @@ typedef struct pulda_batch pulda_batch;
 
 /* pulda_batch_init -- validate and set up every chain as pulda_init would
  * (same limits and errors, reported with the chain's index).  opt->stream, if
- * set, is used for all chains; opt->warps_per_block > 0 fixes the z-step CTA
- * size instead of tuning it; docs_per_warp must be 0 or 1. */
+ * set, is used for all chains; opt->warps_per_block in 1..8 fixes the z-step
+ * CTA size instead of tuning it over {2, 4, 8}; docs_per_warp must be 0 or 1. */
 pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains, int32_t n_chains,
                               const pulda_options *opt);
 /* pulda_batch_sweep -- n_sweeps sweeps of every chain (asynchronous, except

@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
             "or_phi_draw": (i32, [P, P, i32, i32, u64, u32, P, P, P]),
             "or_word_tables": (None, [P, P, P, i32, i32, P, P, P, P, P, P, P]),
             "or_z_step": (i32, [P, i64, P, P, i32, i32, P, P, P, P, P, P, u64, u32, i64, P]),
+            "or_log_posterior": (i32, [P, i64, P, P, i32, i32, P, f64, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -183,6 +184,19 @@ def doc_topic(doc_off: np.ndarray, z: np.ndarray, K: int) -> np.ndarray:
     z = np.ascontiguousarray(z, dtype=np.int16)
     lib().or_doc_topic(_p(doc_off), D, _p(z), K, _p(m))
     return m
+
+
+def log_posterior(doc_off, w, z, K: int, V: int, alpha, beta: float) -> np.ndarray:
+    """[total, document part, topic part] of the collapsed log p(w, z | alpha, beta)
+    (the log-posterior diagnostic of Section 5)."""
+    doc_off = np.ascontiguousarray(doc_off, dtype=np.int64)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    z = np.ascontiguousarray(z, dtype=np.int16)
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, dtype=np.float32), (K,)))
+    out = np.zeros(3, dtype=np.float64)
+    if lib().or_log_posterior(_p(doc_off), doc_off.shape[0] - 1, _p(w), _p(z), K, V, _p(a), float(beta), _p(out)):
+        raise MemoryError("oracle log posterior: out of memory")
+    return out
 
 
 def phi_draw(ctx: Ctx, n_vk: np.ndarray, seed: int, sweep: int) -> tuple[np.ndarray, np.ndarray, int]:

@@ -539,3 +539,55 @@ int32_t or_z_step(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *
     free(m);
     return 0;
 }
+
+/* ------------------------------------------------------------------ log posterior
+ * Diagnostic of the experiments (Section 5, the log-posterior trace plots):
+ * the collapsed log joint of the topic indicators and the words, with Theta
+ * and Phi integrated out of the Dirichlet-multinomial LDA model (notation
+ * table, Section 1):
+ *
+ *   log p(w, z | alpha, beta)
+ *     = sum_d [ lgamma(sum_k alpha_k) - lgamma(sum_k alpha_k + N_d)
+ *               + sum_k ( lgamma(alpha_k + m_{d,k}) - lgamma(alpha_k) ) ]
+ *     + sum_k [ lgamma(V beta) - lgamma(V beta + n_k)
+ *               + sum_v ( lgamma(beta + n_{k,v}) - lgamma(beta) ) ],
+ *
+ * n_k = sum_v n_{k,v}.  As a function of z it is the unnormalised marginal
+ * posterior p(z | w).  out[0] = total, out[1] = the document sum, out[2] =
+ * the topic sum.  Terms with a zero count are exactly zero and skipped; every
+ * sum runs in index order in double.  Returns -1 on allocation failure. */
+int32_t or_log_posterior(const int64_t *doc_off, int64_t D, const int32_t *w, const int16_t *z,
+                         int32_t K, int32_t V, const float *alpha, double beta, double out[3])
+{
+    int64_t N = doc_off[D];
+    double asum = 0.0;
+    for (int32_t k = 0; k < K; k++) asum += (double)alpha[k];
+    int32_t *m = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
+    int32_t *n = (int32_t *)malloc(sizeof(int32_t) * (size_t)K * (size_t)V);
+    int64_t *nk = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    if (!m || !n || !nk) { free(m); free(n); free(nk); return -1; }
+    double docs = 0.0;
+    for (int64_t d = 0; d < D; d++) {
+        memset(m, 0, sizeof(int32_t) * (size_t)K);
+        for (int64_t i = doc_off[d]; i < doc_off[d + 1]; i++) m[z[i]]++;
+        double t = lgamma(asum) - lgamma(asum + (double)(doc_off[d + 1] - doc_off[d]));
+        for (int32_t k = 0; k < K; k++)
+            if (m[k] > 0) t += lgamma((double)alpha[k] + (double)m[k]) - lgamma((double)alpha[k]);
+        docs += t;
+    }
+    or_count_n(N, w, z, K, V, n);
+    double topics = 0.0;
+    for (int32_t k = 0; k < K; k++) {
+        double t = 0.0;
+        for (int32_t v = 0; v < V; v++) {
+            int32_t c = n[(int64_t)v * K + k];
+            if (c > 0) { t += lgamma(beta + (double)c) - lgamma(beta); nk[k] += c; }
+        }
+        topics += t + lgamma((double)V * beta) - lgamma((double)V * beta + (double)nk[k]);
+    }
+    free(m); free(n); free(nk);
+    out[0] = docs + topics;
+    out[1] = docs;
+    out[2] = topics;
+    return 0;
+}

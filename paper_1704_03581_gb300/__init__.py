@@ -23,7 +23,8 @@ STATUS = {0: "PULDA_OK", -1: "PULDA_ERR_INVALID", -2: "PULDA_ERR_OOM", -3: "PULD
           -4: "PULDA_ERR_TIMEOUT", -5: "PULDA_ERR_DEGENERATE", -6: "PULDA_ERR_BUSY"}
 
 EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "pulda_sync", "pulda_get_z",
-            "pulda_get_z_dev", "pulda_set_z", "pulda_get_counts", "pulda_get_phi", "pulda_get_word_tables",
+            "pulda_get_z_dev", "pulda_set_z", "pulda_get_counts", "pulda_log_posterior", "pulda_get_phi",
+            "pulda_get_word_tables",
             "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_last_error", "pulda_free",
             "pulda_batch_init", "pulda_batch_sweep", "pulda_batch_sync", "pulda_batch_get_z", "pulda_batch_stats",
             "pulda_batch_tuning", "pulda_batch_last_error", "pulda_batch_free",
@@ -75,6 +76,7 @@ def lib() -> ctypes.CDLL:
             "pulda_get_z_dev": [P, P],
             "pulda_set_z": [P, P, i64],
             "pulda_get_counts": [P, P, P],
+            "pulda_log_posterior": [P, P],
             "pulda_get_phi": [P, P, P, P, P],
             "pulda_get_word_tables": [P, P, P, P, P, P, P, P, P, P],
             "pulda_infer": [P, P, P, i64, i32, u64, P, P],
@@ -178,6 +180,13 @@ def pulda_set_z(h, z: np.ndarray, sweep: int):
 
 def pulda_get_counts(h, n_kv: np.ndarray | None, m_dk: np.ndarray | None):
     _check(h, lib().pulda_get_counts(h, _ptr(n_kv), _ptr(m_dk)))
+
+
+def pulda_log_posterior(h) -> np.ndarray:
+    """[total, document sum, topic sum] of log p(w, z | alpha, beta) for the current z."""
+    out = np.zeros(3, np.float64)
+    _check(h, lib().pulda_log_posterior(h, _ptr(out)))
+    return out
 
 
 def pulda_get_phi(h, V: int):
@@ -292,6 +301,9 @@ class Sampler:
         out = np.zeros((self.D, self.K), np.int32)
         pulda_get_counts(self.h, None, out)
         return out
+
+    def log_posterior(self) -> np.ndarray:
+        return pulda_log_posterior(self.h)
 
     def phi(self):
         return pulda_get_phi(self.h, self.V)

@@ -205,7 +205,20 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     if (check_corpus(h, word_ids, doc_offsets, D, V, &N) != PULDA_OK) return reject(PULDA_ERR_INVALID);
     if (opt) h->opt = *opt;
     if (h->opt.zstep_path < 0 || h->opt.zstep_path > 2) { fail(h, PULDA_ERR_INVALID, "zstep_path must be 0, 1 or 2"); return reject(PULDA_ERR_INVALID); }
+    if (h->opt.warps_per_block < 0 || h->opt.warps_per_block > kZWarps) {
+        fail(h, PULDA_ERR_INVALID, "warps_per_block must be in [0, %d] (got %d)", kZWarps, h->opt.warps_per_block);
+        return reject(PULDA_ERR_INVALID);
+    }
+    if (h->opt.docs_per_warp != 0 && h->opt.docs_per_warp != 1 && h->opt.docs_per_warp != 4) {
+        fail(h, PULDA_ERR_INVALID, "docs_per_warp must be 0 (auto), 1 or 4");
+        return reject(PULDA_ERR_INVALID);
+    }
+    if (h->opt.docs_per_warp == 4 && K > kMaxKBitmap) {
+        fail(h, PULDA_ERR_INVALID, "docs_per_warp = 4 needs K <= 1024");
+        return reject(PULDA_ERR_INVALID);
+    }
     h->N = N; h->D = D; h->K = K; h->V = V; h->seed = seed; h->beta = beta;
+    for (int k = 0; k < K; ++k) h->alpha_sum += static_cast<double>(alpha[k]);
     h->KW = (K + 31) / 32;
     h->cap = static_cast<int64_t>(K) * V;
     cudaGetDevice(&h->device);
@@ -291,19 +304,11 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     int wpb = h->opt.warps_per_block;
-    if (wpb <= 0) wpb = 8;
+    if (wpb <= 0) wpb = kZWarps;
     while (wpb > 1 && z_step_smem(K, wpb) > 160 * 1024) wpb >>= 1;
     h->z_warps = wpb;
     h->z_grid = sms * z_step_blocks_per_sm(K, wpb);
     CUI(cudaGetLastError());
-    if (h->opt.docs_per_warp != 0 && h->opt.docs_per_warp != 1 && h->opt.docs_per_warp != 4) {
-        fail(h, PULDA_ERR_INVALID, "docs_per_warp must be 0 (auto), 1 or 4");
-        return bail(PULDA_ERR_INVALID);
-    }
-    if (h->opt.docs_per_warp == 4 && K > kMaxKBitmap) {
-        fail(h, PULDA_ERR_INVALID, "docs_per_warp = 4 needs K <= 1024");
-        return bail(PULDA_ERR_INVALID);
-    }
     // Measured on the large workload (sweeps 31-50, |J| ~ 130 per token) one
     // document per warp is 2x faster: the grouped kernel's lanes each carry 4x
     // longer chains of dependent loads.  It is kept for small intersections.
@@ -415,6 +420,25 @@ pulda_status pulda_get_counts(pulda_handle *h, int32_t *n_kv, int32_t *m_dk) {
         CU(h, e);
     }
     CU(h, cudaGetLastError());
+    return pulda_sync(h);
+}
+
+pulda_status pulda_log_posterior(pulda_handle *h, double *out) {
+    if (!h) return PULDA_ERR_INVALID;
+    if (!out) return fail(h, PULDA_ERR_INVALID, "out is NULL");
+    cudaStream_t st = h->stream;
+    // n from the current z (counts only, no draws), then the three reductions
+    PhiArgs a = phi_args(h);
+    CU(h, cudaMemsetAsync(h->work, 0, sizeof(int), st));
+    CU(h, run_heavy(h));
+    launch_phi_counts(a, false, h->phi_grid, st);
+    void *scratch = nullptr;
+    CU(h, cudaMallocAsync(&scratch, log_posterior_scratch_bytes(h->D, h->V, h->K), st));
+    launch_log_posterior(h->doc_off, h->D, h->z, h->K, h->alpha, h->alpha_sum, a, static_cast<double>(h->beta), scratch, st);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, scratch, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(scratch, st);
+    CU(h, e);
     return pulda_sync(h);
 }
 

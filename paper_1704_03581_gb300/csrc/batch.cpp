@@ -89,6 +89,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = "batched chains run one document per warp (docs_per_warp must be 0 or 1)";
         return bail(PULDA_ERR_INVALID);
     }
+    if (o.warps_per_block < 0 || o.warps_per_block > 8) {
+        b->err = "warps_per_block must be in [0, 8] (got " + std::to_string(o.warps_per_block) + ")";
+        return bail(PULDA_ERR_INVALID);
+    }
     if (o.stream) {
         b->stream = static_cast<cudaStream_t>(o.stream);
     } else {
@@ -100,11 +104,15 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     }
     o.stream = b->stream;
     o.docs_per_warp = 1;
+    // the chains' own z-step launch shape is not used: the batch launches its
+    // own kernel, whose CTA size is o.warps_per_block or tuned
+    pulda_options oc = o;
+    oc.warps_per_block = 0;
     for (int32_t c = 0; c < n_chains; ++c) {
         const pulda_chain_desc &d = chains[c];
         pulda_handle *h = nullptr;
         pulda_status s = pulda_init(&h, d.word_ids_host, d.doc_offsets_host, d.D, d.K, d.V, d.alpha_host, d.beta,
-                                    d.seed, &o);
+                                    d.seed, &oc);
         if (s != PULDA_OK) {
             b->err = "chain " + std::to_string(c) + ": " + pulda_last_error(nullptr);
             return bail(s);

@@ -21,6 +21,7 @@ struct pulda_handle {
     int64_t sweep = 0;
     bool have_phi = false;
     float beta = 0;
+    double alpha_sum = 0;       // sum_k alpha_k in double, index order
     int z_warps = 8, z_grid = 0, phi_grid = 0;
     bool z_groups = false;      // grouped z-step (four documents per warp) in use
     int zg_grid = 0;

@@ -562,12 +562,23 @@ __global__ void k_phi_tables_multi(const PhiArgs *chains, const int2 *items, int
 // Entries of the document-side intersection each lane gathers with
 // independent loads before consuming them.
 #ifndef PULDA_ZGATHER
-#define PULDA_ZGATHER 8
+#define PULDA_ZGATHER 4
 #endif
+// 4-warp CTAs, at least 7 per SM: the kernel fits 64 registers without
+// spilling and 32 warps share each SM (issue slots are what bound it; fewer
+// warps leave them idle while each warp waits on its dependent chain).
 #ifndef PULDA_ZMINBLOCKS
-#define PULDA_ZMINBLOCKS 3
+#define PULDA_ZMINBLOCKS 7
+#endif
+// The document side is iterated when K_d * kDocRatio < K_v * 16.  An element
+// of the document side costs about twice one of the column side (a bit scan
+// and a rank per element) and the lanes' shares of it are uneven, while the
+// column side splits evenly; either side gives the same exact sums.
+#ifndef PULDA_ZDOCRATIO
+#define PULDA_ZDOCRATIO 16
 #endif
 constexpr int kGather = PULDA_ZGATHER;
+constexpr int kDocRatio = PULDA_ZDOCRATIO;
 
 // One warp per document (dynamically scheduled, longest first).  m_d lives
 // in shared memory as a dense count array; for K <= 1024 each lane also holds
@@ -586,8 +597,24 @@ constexpr int kGather = PULDA_ZGATHER;
 // m_d is stored skewed, topic k at k + k/32, so the lanes of a warp reading
 // topics 32 l + b (lane l, bit b) hit distinct shared-memory banks.
 __host__ __device__ __forceinline__ int mi(int k) { return k + (k >> 5); }
-// Shared memory of one z-step warp, in 32-bit words.
-__host__ __device__ __forceinline__ int z_warp_words(int K) { return K + (K >> 5) + 1; }
+// Shared memory of one z-step warp, in 32-bit words: m_d (skewed, rounded up
+// to 16 bytes), then the staging records of the 32 tokens in flight.
+__host__ __device__ __forceinline__ int z_m_words(int K) { return (K + (K >> 5) + 1 + 3) & ~3; }
+constexpr int kTokRecWords = 8;     // two uint4 per token
+__host__ __device__ __forceinline__ int z_warp_words(int K) { return z_m_words(K) + 32 * kTokRecWords; }
+
+// Counters of a z-step warp.  The warp-uniform ones are held one per lane
+// (lane j holds counter j), which keeps five 64-bit values out of every
+// lane's registers; the intersection size is summed per lane.
+// Counter order: tokens, a-branch draws, sum min(K_d,K_v), zero-mass tokens,
+// (lane 4 unused: sum |J| is `inter`), tokens with K_d < K_v.
+struct ZCount {
+    u64 mine = 0;     // this lane's warp-uniform counter
+    u64 inter = 0;    // this lane's share of sum |J|
+    __device__ __forceinline__ void add(int j, u64 x) {
+        if ((threadIdx.x & 31) == j) mine += x;
+    }
+};
 
 // One document's run: where its tokens live and where its Markov chain is.
 struct DocRun {
@@ -608,8 +635,7 @@ struct DocRun {
 // current topics first: with positions < pos already resampled in this pass
 // that is exactly m of the sequential sampler at `pos`.  Returns the run's
 // final (sweep, pos) through r.
-__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 (&st)[6]) {
-    u64 &st_tok = st[0], &st_ab = st[1], &st_min = st[2], &st_zero = st[3], &st_int = st[4], &st_doc = st[5];
+__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
     const int lane = threadIdx.x & 31;
     const int K = a.K;
     const bool use_bm = a.bitmap != nullptr && a.path != 1;
@@ -641,41 +667,47 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 (&st)[6])
         const int cnt = static_cast<int>(min(static_cast<int64_t>(32), min(left, r.budget)));
         const int i = i0 + lane;
         const bool valid = lane < cnt;
-        int wv = 0, zo = 0, nw = 0, ta = 0;
-        int64_t cb = 0;
-        u64 Av = 0;
-        U4 x{0, 0, 0, 0};
+        int znew = 0;
+        // Everything that depends only on the token is fetched for 32 tokens at
+        // once, one per lane, and staged in shared memory:
+        //   rec[2t]   = {column start (low 32), column start >> 32 | alias outcome << 16, sigma_a (lo, hi)}
+        //   rec[2t+1] = {Philox x0, x1, word, K_v | old topic << 16}
+        // (column starts are below 2^48, K_v <= 16384, topics < 16384).
+        uint4 *rec = reinterpret_cast<uint4 *>(m + z_m_words(K));
         if (valid) {
-            wv = r.w[i];
-            zo = r.z[i];
+            const int wv = r.w[i];
+            const int zo = r.z[i];
+            znew = zo;
             const uint64_t t = static_cast<uint64_t>(r.index_base + i);
-            x = draw(r.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), r.sweep, TAG_Z, 0);
-            cb = a.col_ptr[wv];
-            nw = static_cast<int>(a.col_ptr[wv + 1] - cb);
-            Av = a.A[wv];
+            const U4 x = draw(r.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), r.sweep, TAG_Z, 0);
+            const int64_t cb = a.col_ptr[wv];
+            const int nw = static_cast<int>(a.col_ptr[wv + 1] - cb);
+            const u64 Av = a.A[wv];
+            int ta = 0;
             if (nw > 0) {
                 const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
                 ta = x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl];
             }
+            rec[2 * lane] = make_uint4(static_cast<uint32_t>(cb),
+                                       static_cast<uint32_t>(static_cast<u64>(cb) >> 32) | (static_cast<uint32_t>(ta) << 16),
+                                       static_cast<uint32_t>(Av), static_cast<uint32_t>(Av >> 32));
+            rec[2 * lane + 1] = make_uint4(x.x, x.y, static_cast<uint32_t>(wv),
+                                           static_cast<uint32_t>(nw) | (static_cast<uint32_t>(zo) << 16));
         }
-        int znew = zo;
+        __syncwarp();
         uint2 bm_next = make_uint2(0u, 0u);
-        const int v_first = __shfl_sync(0xFFFFFFFFu, wv, 0);    // every lane takes part in the shuffle
-        if (use_bm && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(v_first) * a.KW + lane];
+        if (use_bm && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(rec[1].z) * a.KW + lane];
         for (int tt = 0; tt < cnt; ++tt) {
-            const int v = __shfl_sync(0xFFFFFFFFu, wv, tt);
-            const int kold = __shfl_sync(0xFFFFFFFFu, zo, tt);
-            const int64_t col = __shfl_sync(0xFFFFFFFFu, cb, tt);
-            const int n_w = __shfl_sync(0xFFFFFFFFu, nw, tt);
-            const u64 At = __shfl_sync(0xFFFFFFFFu, Av, tt);
-            const u64 U = (static_cast<u64>(__shfl_sync(0xFFFFFFFFu, x.x, tt)) << 32) |
-                          __shfl_sync(0xFFFFFFFFu, x.y, tt);
-            const int ka = __shfl_sync(0xFFFFFFFFu, ta, tt);
+            const uint4 t0 = rec[2 * tt], t1 = rec[2 * tt + 1];
+            const int kold = static_cast<int>(t1.w >> 16);
+            const int64_t col = static_cast<int64_t>((static_cast<u64>(t0.y & 0xFFFFu) << 32) | t0.x);
+            const int n_w = static_cast<int>(t1.w & 0xFFFFu);
+            const u64 At = (static_cast<u64>(t0.w) << 32) | t0.z;
+            const u64 U = (static_cast<u64>(t1.x) << 32) | t1.y;
+            const int ka = static_cast<int>(t0.y >> 16);
             const uint2 bm = bm_next;
-            if (use_bm) {     // fetch the next token's bitmap word while this one is drawn
-                const int vn = __shfl_sync(0xFFFFFFFFu, wv, (tt + 1) & 31);
-                if (tt + 1 < cnt && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(vn) * a.KW + lane];
-            }
+            if (use_bm && tt + 1 < cnt && lane < a.KW)   // the next token's bitmap word, fetched while this one is drawn
+                bm_next = a.bitmap[static_cast<int64_t>(rec[2 * tt + 3].z) * a.KW + lane];
             // remove token i: m^{-i}
             const uint32_t old = m[mi(kold)];
             __syncwarp();
@@ -685,9 +717,9 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 (&st)[6])
                 if (use_bm && lane == (kold >> 5)) mbits &= ~(1u << (kold & 31));
             }
             __syncwarp();
-            st_min += static_cast<u64>(kd < n_w ? kd : n_w);
-            st_doc += kd < n_w ? 1u : 0u;
-            const bool docside = use_bm && (a.path == 2 || kd < n_w);
+            st.add(2, static_cast<u64>(kd < n_w ? kd : n_w));
+            st.add(5, kd < n_w ? 1u : 0u);
+            const bool docside = use_bm && (a.path == 2 || kd * kDocRatio < n_w * 16);
             const uint32_t *qcol = a.q + col;
             // per-lane partial sums of q m, in ascending topic order across lanes
             u64 acc = 0;
@@ -697,8 +729,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 (&st)[6])
             int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
             if (docside) {
                 uint32_t rem = bm.x & mbits;
-                const int nj = __reduce_add_sync(0xFFFFFFFFu, static_cast<unsigned>(__popc(rem)));
-                st_int += static_cast<u64>(nj);
+                st.inter += static_cast<u64>(__popc(rem));
 #pragma unroll
                 for (int t = 0; t < kGather; ++t) {
                     bp[t] = -1;
@@ -729,19 +760,19 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 (&st)[6])
                     acc += static_cast<u64>(qcol[j]) * mk;
                     nj += mk != 0u;
                 }
-                st_int += static_cast<u64>(__reduce_add_sync(0xFFFFFFFFu, nj));
+                st.inter += static_cast<u64>(nj);
             }
             const u64 incl = warp_incl_scan64(acc);
             const u64 B = __shfl_sync(0xFFFFFFFFu, incl, 31);
             const u64 T = At + (B << kFracBits);
             int knew = kold;
             if (T == 0) {
-                ++st_zero;
+                st.add(3, 1);
             } else {
                 const u64 rr = __umul64hi(U, T);
                 if (rr < At) {
                     knew = ka;
-                    ++st_ab;
+                    st.add(1, 1);
                 } else {
                     const u64 rb = (rr - At) >> kFracBits;
                     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, rb < incl);
@@ -796,7 +827,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 (&st)[6])
             if (lane == tt) znew = knew;
         }
         if (valid) r.z[i] = static_cast<int16_t>(znew);
-        st_tok += static_cast<u64>(cnt);
+        st.add(0, static_cast<u64>(cnt));
         r.budget -= cnt;
         r.pos += cnt;
         if (r.pos == r.len) { r.pos = 0; r.sweep += 1; }
@@ -816,13 +847,29 @@ __device__ void flush_z_stats(unsigned long long *stats, const u64 (&c)[6]) {
     }
 }
 
+// The same from a warp running z_doc_warp: lanes 0-3 and 5 hold their
+// counters, sum |J| is summed over the lanes.  Every lane calls it.
+__device__ void flush_warp_z_stats(unsigned long long *stats, ZCount &c) {
+    const u64 inter = warp_sum64(c.inter);
+    const int lane = threadIdx.x & 31;
+    const int slot[6] = {ST_TOKENS, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_SUMINT, ST_DOCSIDE};
+    if (lane < 6) {
+        const u64 v = lane == 4 ? inter : c.mine;
+        if (v) {
+            atomicAdd(&stats[slot[lane]], v);
+            atomicAdd(&stats[ST_COUNT + slot[lane]], v);
+        }
+    }
+    c = ZCount{};
+}
+
 // One chain, one document per warp (dynamically scheduled, longest first),
 // one pass.
-__global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
+__global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
     uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
-    u64 st[6] = {0, 0, 0, 0, 0, 0};
+    ZCount st;
     const uint32_t sweep = sweep_of(a);
     for (;;) {
         int item = 0;
@@ -835,12 +882,12 @@ __global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
                  a.doc_off[d + 1] - s, 1};
         z_doc_warp(a, m, r, st);
     }
-    if (lane == 0) flush_z_stats(a.stats, st);
+    flush_warp_z_stats(a.stats, st);
 }
 
 // Many chains: the work list holds (chain, document) pairs, longest first
 // across all chains; shared memory per warp is sized for the largest K.
-__global__ void __launch_bounds__(256, 2) k_z_step_multi(const ZArgs *chains, const int2 *items,
+__global__ void __launch_bounds__(256, 3) k_z_step_multi(const ZArgs *chains, const int2 *items,
                                                                         int n_items, int *work, int kmax) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
@@ -855,9 +902,9 @@ __global__ void __launch_bounds__(256, 2) k_z_step_multi(const ZArgs *chains, co
         const int64_t s = a.doc_off[it.y];
         DocRun r{a.w + s, a.z + s, static_cast<int>(a.doc_off[it.y + 1] - s), a.seed, a.index_base + s, sweep_of(a),
                  0, a.doc_off[it.y + 1] - s, 1};
-        u64 st[6] = {0, 0, 0, 0, 0, 0};
+        ZCount st;
         z_doc_warp(a, m, r, st);
-        if (lane == 0) flush_z_stats(a.stats, st);
+        flush_warp_z_stats(a.stats, st);
     }
 }
 
@@ -1178,13 +1225,13 @@ __global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_
 // across passes, one warp per slot.  A slot whose pass counter is 0 first
 // gets its uniform initial topics (counter 0, as pulda_infer).  The slot's
 // (pass, position) is written back for the host's completion check.
-__global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_serve_step(ZArgs a, ServeSlot *slots, const int32_t *active,
+__global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_serve_step(ZArgs a, ServeSlot *slots, const int32_t *active,
                                                                      int n_active, const int32_t *arena_w,
                                                                      int16_t *arena_z, int64_t slice, int *work) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
     uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
-    u64 st[6] = {0, 0, 0, 0, 0, 0};
+    ZCount st;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(work, 1);
@@ -1212,7 +1259,7 @@ __global__ void __launch_bounds__(256, PULDA_ZMINBLOCKS) k_serve_step(ZArgs a, S
             slots[idx].pos = r.pos;
         }
     }
-    if (lane == 0) flush_z_stats(a.stats, st);
+    flush_warp_z_stats(a.stats, st);
 }
 
 // ============================================================== exports

@@ -23,6 +23,12 @@ constexpr uint32_t kMaxRedraw = 1u << 20;
 constexpr int kMaxK = 16384;
 // The bitmap intersection path of the z-step holds one 32-topic word per lane.
 constexpr int kMaxKBitmap = 1024;
+// Warps per CTA of the warp-per-document z-step: the default and the largest
+// accepted (the kernel's launch bounds are sized for it).
+#ifndef PULDA_ZWARPS
+#define PULDA_ZWARPS 4
+#endif
+constexpr int kZWarps = PULDA_ZWARPS;
 
 // Philox stream tags (counter word 3 = tag << 28 | aux).
 enum : uint32_t { TAG_INIT = 1, TAG_POIS = 2, TAG_BETA = 3, TAG_REDRAW_POIS = 4, TAG_REDRAW_BETA = 5, TAG_Z = 6 };
@@ -150,6 +156,14 @@ void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st);
 size_t z_groups_smem(int K);
 int z_groups_blocks_per_sm(int K);
 int phi_counts_blocks_per_sm(int K);
+
+// Log-posterior diagnostic (diag.cu).  `counts` holds the n columns rebuilt
+// from the current z (the count-only Phi-step pass); `scratch` is device
+// memory of log_posterior_scratch_bytes(D, V, K) bytes whose first three
+// doubles receive {total, document sum, topic sum}.
+size_t log_posterior_scratch_bytes(int64_t D, int V, int K);
+void launch_log_posterior(const int64_t *doc_off, int64_t D, const int16_t *z, int K, const float *alpha, double asum,
+                          const PhiArgs &counts, double beta, void *scratch, cudaStream_t st);
 
 // One sweep of many chains: six launches, every kernel over all chains'
 // work items.  Pointers are device memory.

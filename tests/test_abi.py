@@ -47,6 +47,14 @@ def test_init_rejects_bad_arguments_without_a_gpu():
             assert e.status == -1 and frag in str(e), str(e)
         else:
             raise AssertionError("accepted " + repr(kwargs))
+    for kwargs, frag in [(dict(zstep_path=3), "zstep_path"), (dict(warps_per_block=9), "warps_per_block"),
+                         (dict(warps_per_block=-1), "warps_per_block"), (dict(docs_per_warp=2), "docs_per_warp")]:
+        try:
+            P.pulda_init(w, off, 4, 3, 0.1, 0.01, 0, **kwargs)
+        except P.PuldaError as e:
+            assert e.status == -1 and frag in str(e), str(e)
+        else:
+            raise AssertionError("accepted " + repr(kwargs))
     bad_off = np.array([0, 2, 1, 3], np.int64)
     try:
         P.pulda_init(w, bad_off, 4, 3, 0.1, 0.01, 0)

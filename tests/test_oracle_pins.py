@@ -385,3 +385,62 @@ def test_chain_invariants_tiny_corpus():
     assert ch.z.min() >= 0 and ch.z.max() < 20
     assert np.abs(ch.tables.phi_dense().astype(np.float64).sum(axis=1) - 1).max() < 1e-6
     assert ch.stats[0] == c.N
+
+
+# ---------------------------------------------------------------- log posterior
+# The diagnostic of Section 5 is the collapsed log joint log p(w, z | alpha, beta)
+# of Dirichlet-multinomial LDA.  It is pinned by what the model itself fixes:
+# a probability law over every (w, z) of a given shape sums to one; its ratios
+# are the collapsed Gibbs conditional; a one-token corpus has a closed form.
+
+@pytest.mark.parametrize("K,V,alpha,beta,k", [(2, 3, [0.25, 0.75], 0.5, 1), (5, 7, [0.125] * 5, 0.03125, 3),
+                                               (1, 1, [2.0], 1.5, 0)])
+def test_log_posterior_single_token_closed_form(K, V, alpha, beta, k):
+    """One document of one token, word 0, topic k: p(z=k) = alpha_k / sum(alpha), p(w | z) = 1/V."""
+    out = O.log_posterior(np.array([0, 1]), np.array([0]), np.array([k]), K, V, alpha, beta)
+    want = math.log(alpha[k] / sum(alpha)) - math.log(V)
+    assert abs(out[0] - want) < 1e-12
+    assert abs(out[0] - out[1] - out[2]) < 1e-12
+
+
+@pytest.mark.parametrize("lengths,K,V,alpha,beta", [((2, 1), 2, 2, [0.25, 1.75], 0.375),
+                                                     ((1, 0, 2), 3, 2, [0.5, 0.125, 1.0], 0.75),
+                                                     ((4,), 2, 3, [0.5, 0.5], 0.0625)])
+def test_log_posterior_sums_to_one_over_every_corpus(lengths, K, V, alpha, beta):
+    """sum over all words w in V^N and topics z in K^N of p(w, z | alpha, beta) = 1
+    for fixed document lengths (an empty document contributes a factor 1)."""
+    import itertools
+    doc_off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    N = int(doc_off[-1])
+    total = 0.0
+    for w in itertools.product(range(V), repeat=N):
+        for z in itertools.product(range(K), repeat=N):
+            total += math.exp(O.log_posterior(doc_off, np.array(w), np.array(z), K, V, alpha, beta)[0])
+    assert abs(total - 1.0) < 1e-12
+
+
+def test_log_posterior_ratios_are_the_collapsed_gibbs_conditional():
+    """exp(LP(z_i = k) - LP(z_i = k0)) = f(k) / f(k0) with
+    f(k) = (m^-i_{d,k} + alpha_k) (n^-i_{k,w_i} + beta) / (n^-i_k + V beta)  (Griffiths and Steyvers, 2004)."""
+    rng = np.random.default_rng(11)
+    K, V, beta = 4, 6, 0.2
+    alpha = np.array([0.1, 0.5, 0.25, 1.5], dtype=np.float32)
+    doc_off = np.array([0, 5, 9, 16], np.int64)
+    N = int(doc_off[-1])
+    w = rng.integers(0, V, N).astype(np.int32)
+    z = rng.integers(0, K, N).astype(np.int16)
+    for i in (0, 4, 7, 15):
+        d = int(np.searchsorted(doc_off, i, side="right") - 1)
+        keep = np.arange(N) != i
+        zi = z[keep]
+        m = np.bincount(z[doc_off[d]:doc_off[d + 1]][np.arange(doc_off[d], doc_off[d + 1]) != i], minlength=K)
+        n_kv = np.zeros((K, V))
+        np.add.at(n_kv, (zi, w[keep]), 1)
+        f = (m + alpha.astype(np.float64)) * (n_kv[:, w[i]] + beta) / (n_kv.sum(1) + V * beta)
+        lp = []
+        for k in range(K):
+            zz = z.copy()
+            zz[i] = k
+            lp.append(O.log_posterior(doc_off, w, zz, K, V, alpha, beta)[0])
+        got = np.exp(np.array(lp) - lp[0])
+        assert np.allclose(got, f / f[0], rtol=1e-11, atol=0), (i, got, f / f[0])
