@@ -69,6 +69,11 @@ def lib() -> ctypes.CDLL:
             "or_word_tables": (None, [P, P, P, i32, i32, P, P, P, P, P, P, P]),
             "or_z_step": (i32, [P, i64, P, P, i32, i32, P, P, P, P, P, P, u64, u32, i64, P]),
             "or_log_posterior": (i32, [P, i64, P, P, i32, i32, P, f64, P]),
+            "or_logf": (f32, [f32]),
+            "or_expf": (f32, [f32]),
+            "or_gamma_draw": (f32, [P, f32, u64, u32, u32, u32, P]),
+            "or_phi_draw_dir": (i32, [P, P, i32, i32, u64, u32, P, P]),
+            "or_word_tables_dir": (None, [P, P, P, i32, i32, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -212,10 +217,42 @@ def phi_draw(ctx: Ctx, n_vk: np.ndarray, seed: int, sweep: int) -> tuple[np.ndar
     return c, S, int(dead[0])
 
 
-class WordTables:
-    """Per-word z-step tables, dense [V, K] with the first ncol[v] entries valid."""
+def logf(x: float) -> float:
+    """The oracle's own float natural log (R-GAMMA)."""
+    return lib().or_logf(float(x))
 
-    def __init__(self, c_vk: np.ndarray, S: np.ndarray, alpha: np.ndarray):
+
+def expf(x: float) -> float:
+    """The oracle's own float exponential (R-GAMMA)."""
+    return lib().or_expf(float(x))
+
+
+def gamma_draw(ctx: Ctx, a: float, seed: int, v: int, k: int, sweep: int) -> float:
+    """One G(a, 1) draw keyed by (v, k, sweep) (R-GAMMA)."""
+    err = np.zeros(1, dtype=np.int32)
+    g = lib().or_gamma_draw(ctx.h, float(np.float32(a)), seed, v, k, sweep, _p(err))
+    if err[0]:
+        raise RuntimeError("Gamma draw did not accept")
+    return g
+
+
+def phi_draw_dir(ctx: Ctx, n_vk: np.ndarray, seed: int, sweep: int) -> tuple[np.ndarray, np.ndarray]:
+    """Algorithm 1: gamma[v, k] ~ G(beta + n[v, k], 1); S[k] = sum_v gamma[v, k] (R-DIRSUM)."""
+    V, K = n_vk.shape
+    n_vk = np.ascontiguousarray(n_vk, dtype=np.int32)
+    g = np.zeros((V, K), dtype=np.float32)
+    S = np.zeros(K, dtype=np.float64)
+    if lib().or_phi_draw_dir(ctx.h, _p(n_vk), K, V, seed, sweep, _p(g), _p(S)) != 0:
+        raise RuntimeError("Gamma draw did not accept")
+    return g, S
+
+
+class WordTables:
+    """Per-word z-step tables, dense [V, K] with the first ncol[v] entries valid.
+    From Polya-urn counts c (uint32) and row sums S (int64), or, with
+    ``dirichlet=True``, from Gamma draws (float32) and row sums S (float64)."""
+
+    def __init__(self, c_vk: np.ndarray, S: np.ndarray, alpha: np.ndarray, dirichlet: bool = False):
         V, K = c_vk.shape
         self.V, self.K = V, K
         self.ncol = np.zeros(V, dtype=np.int32)
@@ -225,11 +262,17 @@ class WordTables:
         self.athr = np.zeros((V, K), dtype=np.uint32)
         self.atopic = np.zeros((V, K), dtype=np.int16)
         self.phi32 = np.zeros((V, K), dtype=np.float32)
-        c_vk = np.ascontiguousarray(c_vk, dtype=np.uint32)
-        S = np.ascontiguousarray(S, dtype=np.int64)
         alpha = np.ascontiguousarray(alpha, dtype=np.float32)
-        lib().or_word_tables(_p(c_vk), _p(S), _p(alpha), K, V, _p(self.ncol), _p(self.topic), _p(self.q),
-                             _p(self.A), _p(self.athr), _p(self.atopic), _p(self.phi32))
+        if dirichlet:
+            g = np.ascontiguousarray(c_vk, dtype=np.float32)
+            S = np.ascontiguousarray(S, dtype=np.float64)
+            fn = lib().or_word_tables_dir
+        else:
+            g = np.ascontiguousarray(c_vk, dtype=np.uint32)
+            S = np.ascontiguousarray(S, dtype=np.int64)
+            fn = lib().or_word_tables
+        fn(_p(g), _p(S), _p(alpha), K, V, _p(self.ncol), _p(self.topic), _p(self.q),
+           _p(self.A), _p(self.athr), _p(self.atopic), _p(self.phi32))
 
     def column(self, v: int):
         n = int(self.ncol[v])
@@ -267,7 +310,8 @@ class Chain:
     topics use counter 0.
     """
 
-    def __init__(self, w, doc_off, K: int, V: int, alpha, beta: float, seed: int, z=None, sweep: int = 0):
+    def __init__(self, w, doc_off, K: int, V: int, alpha, beta: float, seed: int, z=None, sweep: int = 0,
+                 dirichlet: bool = False):
         self.w = np.ascontiguousarray(w, dtype=np.int32)
         self.doc_off = np.ascontiguousarray(doc_off, dtype=np.int64)
         self.K, self.V, self.seed = K, V, int(seed)
@@ -281,11 +325,16 @@ class Chain:
         self.c = None
         self.stats = np.zeros(6, dtype=np.int64)
         self.dead_rows = 0
+        self.dirichlet = dirichlet      # Algorithm 1's Dirichlet Phi instead of the Polya urn
 
     def phi_step(self, sweep: int):
         n = count_n(self.w, self.z, self.K, self.V)
-        self.c, self.S, self.dead_rows = phi_draw(self.ctx, n, self.seed, sweep)
-        self.tables = WordTables(self.c, self.S, self.alpha)
+        if self.dirichlet:
+            self.c, self.S = phi_draw_dir(self.ctx, n, self.seed, sweep)
+            self.dead_rows = 0
+        else:
+            self.c, self.S, self.dead_rows = phi_draw(self.ctx, n, self.seed, sweep)
+        self.tables = WordTables(self.c, self.S, self.alpha, dirichlet=self.dirichlet)
 
     def sweep(self, n_sweeps: int = 1):
         for _ in range(n_sweeps):

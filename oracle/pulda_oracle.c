@@ -540,6 +540,168 @@ int32_t or_z_step(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *
     return 0;
 }
 
+/* ------------------------------------------------------------------ Dirichlet Phi (Algorithm 1)
+ * The partially collapsed sampler the Polya urn approximates (Algorithm 1,
+ * "Efficient sampling of Phi"): phi_k ~ Dir(n_k + beta), drawn through the
+ * Gamma representation gamma_{k,v} ~ G(beta + n_{k,v}, 1), phi_{k,v} =
+ * gamma_{k,v} / sum_v gamma_{k,v}, with Gammas by Marsaglia and Tsang (2000).
+ * Readings (the paper fixes none of these):
+ *   R-GAMMA  float arithmetic, each operation rounded to float; normals from
+ *            the rounded-normal table (R-GAUSS), uniforms with 23 bits
+ *            u = (2 floor(x / 2^9) + 1) 2^-24; Philox counter (v, k, sweep,
+ *            7 << 28 | attempt) per attempt, (v, k, sweep, 8 << 28) for the
+ *            boost u^(1/a) of shapes a < 1 (Marsaglia and Tsang, Section 6);
+ *            log and exp are this file's own (below), not libm's.
+ *   R-DIRSUM S_k = sum over chunks of 256 words, in ascending order, of the
+ *            chunk's sum of gamma_{k,v} in ascending v, all in double.
+ *   R-DIRFIX phi_{k,v} = gamma_{k,v} * (1 / S_k) in double; q as in R-FIX
+ *            but without the floor at 1: entries whose q rounds to 0 (phi
+ *            below 2^(e-25), the column maximum lying in [2^(e-1), 2^e), so
+ *            below 2^-24 of the maximum) leave the column.  This is the
+ *            Dirichlet counterpart of Phi's sparsity; it drops at most
+ *            K 2^-24 of a column's largest entry.
+ */
+#define OR_TAG_GAMMA 7u
+#define OR_TAG_GAMMA_BOOST 8u
+#define OR_DIR_CHUNK 256
+#define OR_MAX_GAMMA_TRY (1u << 16)
+
+static float f_bits(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
+static uint32_t bits_f(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
+
+/* ln x for finite x > 0: x = m 2^e with m in [sqrt(1/2), sqrt(2)];
+ * ln m = 2 atanh(s), s = (m - 1) / (m + 1), |s| <= 0.1716, by its series to
+ * s^9 (the next term is below 2^-28 relative); ln 2 split Cody-Waite style. */
+float or_logf(float x)
+{
+    int32_t e = 0;
+    uint32_t b = bits_f(x);
+    if (b < 0x00800000u) { x = x * 16777216.0f; b = bits_f(x); e = -24; }   /* subnormal: scale by 2^24 */
+    e += (int32_t)(b >> 23) - 127;
+    float m = f_bits((b & 0x007FFFFFu) | 0x3F800000u);                     /* [1, 2) */
+    if (m > 1.41421354f) { m = m * 0.5f; e += 1; }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float poly = s * (2.0f + s2 * (0.666666687f + s2 * (0.400000006f + s2 * (0.285714298f + s2 * 0.222222224f))));
+    float ef = (float)e;
+    return ef * 0.693359375f + (ef * -2.12194442e-4f + poly);
+}
+
+/* e^x for x <= 88: x = k ln 2 + r, |r| <= ln 2 / 2, e^r by its Taylor series
+ * to r^7 (next term below 2^-27 relative), scaled by 2^k; 0 below -104. */
+float or_expf(float x)
+{
+    if (x < -104.0f) return 0.0f;
+    float kf = floorf(x * 1.44269502f + 0.5f);
+    int32_t k = (int32_t)kf;
+    float r = (x - kf * 0.693359375f) - kf * -2.12194442e-4f;
+    float p = 1.0f + r * (1.0f + r * (0.5f + r * (0.166666672f + r * (0.0416666679f + r * (0.00833333377f +
+              r * (0.00138888892f + r * 0.000198412701f))))));
+    if (k >= -126) return p * f_bits((uint32_t)(k + 127) << 23);
+    return (p * f_bits((uint32_t)(k + 64 + 127) << 23)) * f_bits((uint32_t)(127 - 64) << 23);
+}
+
+static float unif23(uint32_t x)
+{
+    return (float)(2u * (x >> 9) + 1u) * 5.96046448e-08f;   /* (2 floor(x/2^9) + 1) 2^-24 */
+}
+
+/* gamma ~ G(a, 1), a > 0 (R-GAMMA).  *err is set when no attempt in
+ * OR_MAX_GAMMA_TRY was accepted (probability below 0.05^65536). */
+float or_gamma_draw(const or_ctx *c, float a, uint64_t seed, uint32_t v, uint32_t k, uint32_t sweep, int32_t *err)
+{
+    float sh = a < 1.0f ? a + 1.0f : a;
+    float d = sh - 0.333333343f;
+    float cc = 1.0f / sqrtf(9.0f * d);
+    for (uint32_t t = 0; t < OR_MAX_GAMMA_TRY; t++) {
+        uint32_t x[4];
+        draw4(seed, v, k, sweep, OR_TAG_GAMMA, t, x);
+        float g = (float)or_gauss_draw(c, x[0], x[1]);
+        float y = 1.0f + cc * g;
+        if (y <= 0.0f) continue;
+        float v3 = (y * y) * y;
+        float u = unif23(x[2]);
+        float g2 = g * g;
+        if (u < 1.0f - 0.0331f * (g2 * g2) || or_logf(u) < 0.5f * g2 + d * ((1.0f - v3) + or_logf(v3))) {
+            float r = d * v3;
+            if (a < 1.0f) {
+                uint32_t xb[4];
+                draw4(seed, v, k, sweep, OR_TAG_GAMMA_BOOST, 0, xb);
+                r = r * or_expf(or_logf(unif23(xb[0])) / a);
+            }
+            return r;
+        }
+    }
+    *err = 1;
+    return 0.0f;
+}
+
+/* Algorithm 1, first bullet: gamma_{k,v} ~ G(beta + n_{k,v}, 1) for every
+ * entry (g_vk[v*K + k], shape beta + n rounded to float) and S_k (R-DIRSUM). */
+int32_t or_phi_draw_dir(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V, uint64_t seed, uint32_t sweep,
+                        float *g_vk, double *S)
+{
+    int32_t err = 0;
+    float bf = (float)c->beta;
+    for (int32_t v = 0; v < V; v++)
+        for (int32_t k = 0; k < K; k++) {
+            int64_t o = (int64_t)v * K + k;
+            g_vk[o] = or_gamma_draw(c, bf + (float)n_vk[o], seed, (uint32_t)v, (uint32_t)k, sweep, &err);
+        }
+    for (int32_t k = 0; k < K; k++) {
+        double tot = 0.0;
+        for (int32_t v0 = 0; v0 < V; v0 += OR_DIR_CHUNK) {
+            double part = 0.0;
+            for (int32_t v = v0; v < V && v < v0 + OR_DIR_CHUNK; v++) part += (double)g_vk[(int64_t)v * K + k];
+            tot += part;
+        }
+        S[k] = tot;
+    }
+    return err ? -1 : 0;
+}
+
+/* Per-word tables of the Dirichlet Phi (R-DIRFIX); the rest as or_word_tables. */
+void or_word_tables_dir(const float *g_vk, const double *S, const float *alpha, int32_t K, int32_t V,
+                        int32_t *ncol, int16_t *topic, uint32_t *q, uint64_t *A,
+                        uint32_t *athr, int16_t *atopic, float *phi32)
+{
+    double *inv = (double *)malloc(sizeof(double) * (size_t)K);
+    double *p = (double *)malloc(sizeof(double) * (size_t)K);
+    uint64_t *a = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K);
+    int32_t *al = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
+    for (int32_t k = 0; k < K; k++) inv[k] = 1.0 / S[k];
+    for (int32_t v = 0; v < V; v++) {
+        int64_t base = (int64_t)v * K;
+        double phimax = 0.0;
+        for (int32_t k = 0; k < K; k++) {
+            p[k] = (double)g_vk[base + k] * inv[k];
+            if (p[k] > phimax) phimax = p[k];
+        }
+        int32_t n = 0;
+        uint64_t tot = 0;
+        if (phimax > 0.0) {
+            int e;
+            frexp(phimax, &e);
+            for (int32_t k = 0; k < K; k++) {
+                double qq = floor(ldexp(p[k], 24 - e) + 0.5);
+                if (qq < 1.0) continue;            /* below 2^-25 of the column maximum */
+                topic[base + n] = (int16_t)k;
+                q[base + n] = (uint32_t)qq;
+                phi32[base + n] = (float)p[k];
+                a[n] = (uint64_t)floor(ldexp(qq * (double)alpha[k], OR_FRAC_BITS) + 0.5);
+                tot += a[n];
+                n++;
+            }
+        }
+        ncol[v] = n;
+        A[v] = tot;
+        if (n == 0) continue;
+        or_vose(a, n, athr + base, al);
+        for (int32_t j = 0; j < n; j++) atopic[base + j] = topic[base + al[j]];
+    }
+    free(inv); free(p); free(a); free(al);
+}
+
 /* ------------------------------------------------------------------ log posterior
  * Diagnostic of the experiments (Section 5, the log-posterior trace plots):
  * the collapsed log joint of the topic indicators and the words, with Theta

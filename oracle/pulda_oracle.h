@@ -51,4 +51,12 @@ int32_t or_z_step(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *
                   uint64_t seed, uint32_t sweep, int64_t index_base, int64_t *stats);
 int32_t or_log_posterior(const int64_t *doc_off, int64_t D, const int32_t *w, const int16_t *z,
                          int32_t K, int32_t V, const float *alpha, double beta, double out[3]);
+float or_logf(float x);
+float or_expf(float x);
+float or_gamma_draw(const or_ctx *c, float a, uint64_t seed, uint32_t v, uint32_t k, uint32_t sweep, int32_t *err);
+int32_t or_phi_draw_dir(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V, uint64_t seed, uint32_t sweep,
+                        float *g_vk, double *S);
+void or_word_tables_dir(const float *g_vk, const double *S, const float *alpha, int32_t K, int32_t V,
+                        int32_t *ncol, int16_t *topic, uint32_t *q, uint64_t *A,
+                        uint32_t *athr, int16_t *atopic, float *phi32);
 #endif

@@ -444,3 +444,127 @@ def test_log_posterior_ratios_are_the_collapsed_gibbs_conditional():
             lp.append(O.log_posterior(doc_off, w, zz, K, V, alpha, beta)[0])
         got = np.exp(np.array(lp) - lp[0])
         assert np.allclose(got, f / f[0], rtol=1e-11, atol=0), (i, got, f / f[0])
+
+
+# ------------------------------------------------------- Dirichlet Phi (Algorithm 1)
+# phi_k ~ Dir(n_k + beta) through Gamma draws (Marsaglia and Tsang), with the
+# oracle's own float log and exp.  Pinned to libm, to scipy's Gamma and Beta
+# laws, and to the z conditional.
+
+def _ulps(a, b):
+    ia = int(np.array(np.float32(a)).view(np.int32))
+    ib = int(np.array(np.float32(b)).view(np.int32))
+    return abs(ia - ib)
+
+
+def test_own_logf_expf_within_two_ulps():
+    """Against the double-precision library result rounded to float, over normal and subnormal
+    arguments of log and the arguments exp takes (|x| <= 104; subnormal results included)."""
+    rng = np.random.default_rng(21)
+    xs = np.concatenate([rng.uniform(0, 1, 3000), np.exp(rng.uniform(-100, 88, 3000)),
+                         np.float32(2.0) ** rng.integers(-149, -126, 100) * rng.uniform(1, 2, 100),
+                         [1.0, 0.5, 2.0, 1.41421354, 1.4142137, 1e-45]]).astype(np.float32)
+    for x in xs[xs > 0]:
+        assert _ulps(O.logf(x), np.log(np.float64(x))) <= 2, x
+    for t in np.concatenate([rng.uniform(-104, 0, 3000), rng.uniform(-1, 1, 1000), rng.uniform(0, 88, 1000)]):
+        t = np.float32(t)
+        assert _ulps(O.expf(t), np.exp(np.float64(t))) <= 2, t
+    assert O.expf(-104.5) == 0.0
+
+
+@pytest.mark.parametrize("a", [0.01, 0.1, 0.5, 1.0, 3.7, 40.0, 1500.0])
+def test_gamma_draws_follow_the_gamma_law(a):
+    """20,000 keyed draws against G(a, 1): KS test, and the mean.  At a = 0.01 about
+    36% of the law lies below the smallest float, where draws underflow to 0; there
+    a chi-square over logarithmic bins (the first holding the zeros) replaces KS."""
+    ctx = O.Ctx(0.01)
+    n = 20000
+    g = np.array([O.gamma_draw(ctx, a, 77, 3, k, 5) for k in range(n)], dtype=np.float64)
+    assert np.all(g >= 0)
+    a32 = float(np.float32(a))
+    law = stats.gamma(a32)
+    if a32 < 0.05:
+        edges = np.array([0.0, 1e-40, 1e-30, 1e-20, 1e-10, 1e-5, 1e-3, 1e-2, 0.1, np.inf])
+        obs = np.histogram(g, bins=edges)[0]
+        exp = n * np.diff(law.cdf(edges))
+        assert stats.chisquare(obs, exp).pvalue > 1e-4, (obs, exp)
+    else:
+        assert stats.kstest(g, law.cdf).pvalue > 1e-4
+    assert abs(g.mean() - a32) < 5 * math.sqrt(a32 / n)
+
+
+def test_dirichlet_phi_marginals_are_beta():
+    """Algorithm 1: phi_{k,.} ~ Dir(n_{k,.} + beta), so phi_{k,v} ~ Beta(n_{k,v} + beta, sum_v (n + beta) - (n_{k,v} + beta)).
+    KS over 3,000 sweeps of the keyed draws; every row sums to 1."""
+    beta = 0.5
+    ctx = O.Ctx(beta)
+    n_vk = np.array([[0, 3, 1], [2, 0, 0], [5, 1, 0], [0, 0, 0], [1, 7, 2]], dtype=np.int32)    # V=5, K=3
+    V, K = n_vk.shape
+    phis = []
+    for sw in range(1, 3001):
+        g, S = O.phi_draw_dir(ctx, n_vk, 9, sw)
+        phi = g.astype(np.float64) / S
+        assert np.allclose(phi.sum(axis=0), 1.0, atol=1e-6)
+        phis.append(phi)
+    phis = np.array(phis)
+    tot = n_vk.sum(axis=0) + V * beta
+    for v, k in [(0, 0), (0, 1), (2, 0), (3, 2), (4, 1)]:
+        a = n_vk[v, k] + beta
+        assert stats.kstest(phis[:, v, k], stats.beta(a, tot[k] - a).cdf).pvalue > 1e-4, (v, k)
+
+
+def test_dirichlet_row_sums_are_the_row_totals():
+    """S_k is the sum of row k of the Gamma draws, to within V eps S_k of the exact sum."""
+    rng = np.random.default_rng(4)
+    ctx = O.Ctx(0.01)
+    n_vk = rng.integers(0, 3, size=(700, 6)).astype(np.int32)
+    g, S = O.phi_draw_dir(ctx, n_vk, 3, 2)
+    for k in range(6):
+        exact = math.fsum(g[:, k].astype(np.float64))
+        assert abs(S[k] - exact) <= 700 * 2.0 ** -53 * exact
+
+
+def test_dirichlet_word_tables_reproduce_the_conditional():
+    """Weights from Gamma draws give p(k) proportional to phi_{k,v}(alpha_k + m_k) to within
+    0.5/(q - 0.5) + 2^-17 for kept entries; dropped entries have phi below 2^-24 of the column maximum."""
+    rng = np.random.default_rng(6)
+    ctx = O.Ctx(0.01)
+    V, K = 40, 96
+    n_vk = (rng.poisson(0.5, size=(V, K)) * rng.integers(1, 50, size=(V, K))).astype(np.int32)
+    g, S = O.phi_draw_dir(ctx, n_vk, 11, 3)
+    alpha = rng.uniform(0.05, 2.0, size=K).astype(np.float32)
+    t = O.WordTables(g, S, alpha, dirichlet=True)
+    for v in range(V):
+        top, q, athr, atop, phi32 = t.column(v)
+        phi_all = g[v].astype(np.float64) * (1.0 / S)
+        keep = np.zeros(K, bool)
+        keep[top] = True
+        assert np.all(np.diff(top) > 0)
+        # kept iff phi >= 2^(e-25), the column maximum being in [2^(e-1), 2^e)
+        e = math.frexp(phi_all.max())[1]
+        assert np.all(phi_all[~keep] < 2.0 ** (e - 25)) and np.all(phi_all[keep] >= 2.0 ** (e - 25) * (1 - 2.0 ** -30))
+        assert np.all(phi_all[~keep] < 2.0 ** -24 * phi_all.max())
+        assert 2 ** 23 <= q.max() <= 2 ** 24 and q.min() >= 1
+        m = rng.integers(0, 40, size=K)
+        p = phi_all[top] * (alpha[top].astype(np.float64) + m[top])
+        p /= p.sum()
+        a = np.floor(q.astype(np.float64) * alpha[top] * 2 ** 16 + 0.5)
+        w = a + q.astype(np.float64) * m[top] * 2 ** 16
+        assert int(a.sum()) == int(t.A[v])
+        rel = np.abs(w / w.sum() - p) / p
+        assert np.all(rel <= 0.5 / (q - 0.5) + 2.0 ** -17)   # round to nearest: x >= q - 1/2
+        mass = alias_masses(athr, np.searchsorted(top, atop))
+        assert np.abs(mass - a / a.sum()).max() <= 2.0 * top.shape[0] / 2 ** 32
+
+
+def test_dirichlet_chain_invariants():
+    """The oracle chain in Dirichlet mode keeps its counts consistent and its topics in range."""
+    rng = np.random.default_rng(8)
+    lengths = rng.integers(1, 40, size=30)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    w = rng.integers(0, 25, int(off[-1])).astype(np.int32)
+    ch = O.Chain(w, off, 7, 25, 0.3, 0.05, seed=4, dirichlet=True)
+    ch.sweep(3)
+    assert ch.z.min() >= 0 and ch.z.max() < 7
+    assert ch.m().sum(axis=1).tolist() == lengths.tolist()
+    assert ch.n().sum() == off[-1]
