@@ -37,7 +37,13 @@ sys.path.insert(0, ROOT)
 METRIC = "z-step tokens/s/GPU at K=1000 (% HBM roofline); serving p50/p99 vs plain"
 K_TOPICS = 1000
 ALPHA, BETA = 0.1, 0.01
-KERNELS_PER_SWEEP = 5   # phi counts+draws, dead-row fix-up, column scan, per-word tables, z-step
+def kernels_per_sweep(w: np.ndarray, phi_mode: int) -> int:
+    """Library kernels one sweep launches: the frequent-word histogram (when a
+    word has more than 2^17 tokens), then Polya urn: counts+draws, dead-row
+    fix-up, column scan, per-word tables; Dirichlet: counts, Gamma draws, two
+    row-sum passes, selection, column scan, per-word tables; then the z-step."""
+    heavy = 1 if np.bincount(w).max(initial=0) > (1 << 17) else 0
+    return heavy + (4 if phi_mode == 0 else 7) + 1
 
 
 def parse():
@@ -55,6 +61,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--docs-per-warp", type=int, default=0, help="z-step documents per warp: 0 auto, 1 or 4")
+    ap.add_argument("--phi-mode", type=int, default=0, choices=[0, 1],
+                    help="sweep form: 0 = Polya-urn Phi (Algorithm 2), 1 = Dirichlet Phi (Algorithm 1)")
     ap.add_argument("--rates", type=str, default="2000,5000,10000,20000,50000",
                     help="serving: Poisson arrival rates, documents per second")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="serving: arrival window per rate")
@@ -63,9 +71,12 @@ def parse():
     ap.add_argument("--serve-sweeps", type=int, default=50, help="serving: z-sweeps per request")
     ap.add_argument("--plain-requests", type=int, default=150,
                     help="serving: requests the one-at-a-time baseline serves (the first ones, at the lowest rate)")
-    ap.add_argument("--form", choices=["sweep", "batched", "serving"], default="sweep",
+    ap.add_argument("--form", choices=["sweep", "batched", "serving", "trace"], default="sweep",
                     help="sweep: the large corpus (the headline line); batched: 32 uneven chains in one graph "
-                         "launch per sweep against 32 sequential single-chain runs")
+                         "launch per sweep against 32 sequential single-chain runs; trace: the log posterior "
+                         "after every sweep, Polya urn against Dirichlet Phi, on the same corpus and seed")
+    ap.add_argument("--trace-corpus", choices=["small", "large"], default="small")
+    ap.add_argument("--trace-sweeps", type=int, default=100)
     ap.add_argument("--batch-scale", type=float, default=0.25,
                     help="fraction of each batched chain's documents (1.0 = the full 267M-token workload)")
     ap.add_argument("--docs", type=int, default=300_000,
@@ -239,7 +250,8 @@ def run_pulda(args, corpus, rank: int, world: int):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     s = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
-                  stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp)
+                  stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp,
+                  phi_mode=args.phi_mode)
     s.sweep(args.burnin + args.warmup)
     s.sync()
     lp_before = s.log_posterior()[0]          # the diagnostic, outside the timed region
@@ -290,7 +302,8 @@ def run_pulda(args, corpus, rank: int, world: int):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
-                       stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp)
+                       stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp,
+                  phi_mode=args.phi_mode)
         s2.sweep(K)
         zh = s2.z()   # e2e covers sweeps 1..K from the uniform start
         dt = time.perf_counter() - t0
@@ -330,7 +343,8 @@ def run_pulda(args, corpus, rank: int, world: int):
         "config": {"workload": corpus.name, "D": corpus.D, "V": corpus.V, "N": corpus.N, "K": K_TOPICS,
                    "alpha": ALPHA, "beta": BETA, "parallelism": f"{world} independent chains (replicas)",
                    "l2": "inputs larger than L2 (word ids 396 MB + topics 198 MB read every sweep)",
-                   "timed_sweeps": [first_timed, first_timed + K - 1]},
+                   "timed_sweeps": [first_timed, first_timed + K - 1],
+                   "phi": "Dirichlet (Algorithm 1)" if args.phi_mode == 1 else "Poisson Polya urn (Algorithm 2)"},
         "z_step": {"tokens_per_s": K * corpus.N / (z_ms / 1000.0), "ms_per_launch": z_ms / K,
                    "mean_min_kd_kv": sum_min / tokens, "mean_intersection": sum_int / tokens,
                    "docside_frac": docside / tokens, "a_branch_frac": a_br / tokens},
@@ -341,11 +355,64 @@ def run_pulda(args, corpus, rank: int, world: int):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_z_step", "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "algorithmic_bytes_per_launch": zbytes / K},
-        "gpu_launches": KERNELS_PER_SWEEP * K,
+        "gpu_launches": kernels_per_sweep(corpus.w, args.phi_mode) * K,
         "z_kernel": "four documents per warp" if args.docs_per_warp == 4 else "one document per warp",
         "clocks": clk,
         "cpu_baseline": cpu,
         "e2e": e2e,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_trace(args):
+    """The paper's mixing comparison (Section 5, log-posterior per iteration) and
+    its Phi-step comparison: the same corpus and seed run under the Polya-urn
+    Phi (Algorithm 2) and the Dirichlet Phi (Algorithm 1), the collapsed log
+    p(w, z) recorded after every sweep (not timed) and each half-step timed
+    with CUDA events."""
+    import torch
+    import paper_1704_03581_gb300 as P
+    from paper_1704_03581_gb300 import synth
+
+    if args.trace_corpus == "small":
+        corpus, K = synth.small(), 100
+    else:
+        corpus, K = synth.large(D=args.docs), K_TOPICS
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {}
+    for mode, name in ((0, "polya_urn"), (1, "dirichlet")):
+        s = P.Sampler(corpus.w, corpus.doc_off, K, corpus.V, ALPHA, BETA, seed=0, stream=stream.cuda_stream,
+                      phi_mode=mode)
+        lp, phi_ms, z_ms, nnz = [float(s.log_posterior()[0])], [], [], []
+        for _ in range(args.trace_sweeps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            P.pulda_phi_step(s.h)
+            e[1].record(stream)
+            P.pulda_z_step(s.h)
+            e[2].record(stream)
+            lp.append(float(s.log_posterior()[0]))       # synchronises
+            phi_ms.append(e[0].elapsed_time(e[1]))
+            z_ms.append(e[1].elapsed_time(e[2]))
+            nnz.append(s.stats()["nnz_phi"])
+        s.close()
+        tail = max(1, args.trace_sweeps // 5)
+        out[name] = {"log_posterior": lp, "phi_ms": float(np.median(phi_ms)), "z_ms": float(np.median(z_ms)),
+                     "nnz_phi_last": int(nnz[-1]), "mean_last_fifth": float(np.mean(lp[-tail:]))}
+    a, b = out["polya_urn"], out["dirichlet"]
+    line = {
+        "metric": "log-posterior trace per sweep: Polya urn (Algorithm 2) vs Dirichlet (Algorithm 1)",
+        "value": (a["mean_last_fifth"] - b["mean_last_fifth"]) / abs(b["mean_last_fifth"]),
+        "unit": "relative difference of the mean log posterior over the last fifth of the sweeps",
+        "n_gpus": 1, "steps": args.trace_sweeps, "higher_is_better": False, "dtype": "int64",
+        "data": "synthetic (LDA generative process)",
+        "config": {"workload": corpus.name, "D": corpus.D, "V": corpus.V, "N": corpus.N, "K": K,
+                   "alpha": ALPHA, "beta": BETA, "seed": 0},
+        "phi_step_ms": {"polya_urn": a["phi_ms"], "dirichlet": b["phi_ms"], "ratio": b["phi_ms"] / a["phi_ms"]},
+        "z_step_ms": {"polya_urn": a["z_ms"], "dirichlet": b["z_ms"], "ratio": b["z_ms"] / a["z_ms"]},
+        "nnz_phi_last": {"polya_urn": a["nnz_phi_last"], "dirichlet": b["nnz_phi_last"]},
+        "traces": {"polya_urn": a["log_posterior"], "dirichlet": b["log_posterior"]},
     }
     print(json.dumps(line), flush=True)
 
@@ -529,11 +596,11 @@ def main():
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if args.form in ("batched", "serving"):
+    if args.form in ("batched", "serving", "trace"):
         from paper_1704_03581_gb300 import build
         build.build()
         if rank == 0:
-            (run_batched if args.form == "batched" else run_serving)(args)
+            {"batched": run_batched, "serving": run_serving, "trace": run_trace}[args.form](args)
         return
     if world > 1:
         import torch.distributed as dist

@@ -60,7 +60,10 @@ typedef struct {
     int32_t docs_per_warp;  /* z-step documents per warp: 0 = auto (one), 1 = one, 4 = four
                                (needs K <= 1024; documents longer than 65,535 tokens still
                                go one per warp); results are identical */
-    int32_t reserved[5];
+    int32_t phi_mode;       /* 0 = Poisson Polya urn (Algorithm 2), 1 = Dirichlet (Algorithm 1:
+                               phi_k ~ Dir(n_k + beta) through Gamma draws, entries below 2^-24
+                               of their column's maximum dropped); the batched form takes 0 only */
+    int32_t reserved[4];
 } pulda_options;
 
 /* Counters of the most recent z-step (and Phi-step), and running totals. */
@@ -140,14 +143,15 @@ pulda_status pulda_get_counts(pulda_handle *h, int32_t *n_kv_host, int32_t *m_dk
  *   out_host double[3] = {total, document sum, topic sum}
  * beta is the handle's float beta widened to double.  The counts are rebuilt
  * from the current z on the GPU and every sum runs in a fixed order, so equal
- * topics give equal bits.  Synchronous; uses 8 (D + V + K + 3) bytes of
- * temporary device memory.  Errors: PULDA_ERR_INVALID (NULL out),
+ * topics give equal bits.  Synchronous; uses 8 (D + V + 257 K + 4099) bytes
+ * of temporary device memory.  Errors: PULDA_ERR_INVALID (NULL out),
  * PULDA_ERR_CUDA. */
 pulda_status pulda_log_posterior(pulda_handle *h, double *out_host);
 
 /* pulda_get_phi -- the Phi drawn by the most recent Phi-step, sparse by word
  * (column-compressed): entries col_ptr[v] .. col_ptr[v+1]-1 hold the nonzero
- * phi_{k,v} = fp32(c_{k,v} / S_k) with topic ids in ascending order.
+ * phi_{k,v} = fp32(c_{k,v} / S_k) with topic ids in ascending order (Dirichlet
+ * mode: fp32(gamma_{k,v} (1 / S_k)) over the entries kept).
  * Call with col_ptr/topic/phi NULL to query *nnz_inout; otherwise *nnz_inout
  * is the capacity of topic/phi on entry and the entry count on return.
  *   col_ptr_host int64[V+1], topic_host int16[nnz], phi_host float[nnz]
@@ -159,6 +163,8 @@ pulda_status pulda_get_phi(pulda_handle *h, int64_t *col_ptr_host, int16_t *topi
  * (for inspection and tests): Poisson counts c (uint32), row sums S (int64[K]),
  * fixed-point weights q (uint32), alpha-part masses A (uint64[V]) and the alias
  * table (threshold uint32, alias topic int16), laid out like pulda_get_phi.
+ * In Dirichlet mode c holds the bits of the float Gamma draws and S the bits
+ * of the double row sums.
  * Any output pointer may be NULL.  *nnz_inout as for pulda_get_phi. */
 pulda_status pulda_get_word_tables(pulda_handle *h, int64_t *col_ptr_host, int16_t *topic_host,
                                    uint32_t *c_host, int64_t *S_host, uint32_t *q_host, uint64_t *A_host,

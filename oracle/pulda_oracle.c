@@ -669,7 +669,7 @@ void or_word_tables_dir(const float *g_vk, const double *S, const float *alpha, 
     double *p = (double *)malloc(sizeof(double) * (size_t)K);
     uint64_t *a = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K);
     int32_t *al = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
-    for (int32_t k = 0; k < K; k++) inv[k] = 1.0 / S[k];
+    for (int32_t k = 0; k < K; k++) inv[k] = S[k] > 0.0 ? 1.0 / S[k] : 0.0;   /* a row of underflows: phi_k = 0 */
     for (int32_t v = 0; v < V; v++) {
         int64_t base = (int64_t)v * K;
         double phimax = 0.0;

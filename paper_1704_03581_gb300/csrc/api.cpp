@@ -150,6 +150,7 @@ PhiArgs phi_args(pulda_handle *h) {
     a.A = h->A; a.vose_p = h->vose_p; a.vose_stack = h->vose_stack; a.bitmap = h->bitmap; a.KW = h->KW;
     a.alpha = h->alpha; a.work = h->work; a.stats = h->stats;
     a.heavy_row = h->heavy_row; a.heavy_hist = h->heavy_hist; a.n_heavy = h->n_heavy;
+    a.gam = h->gam; a.Sd = h->Sd; a.invS = h->invS; a.dpart = h->dpart;
     return a;
 }
 
@@ -205,6 +206,10 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     if (check_corpus(h, word_ids, doc_offsets, D, V, &N) != PULDA_OK) return reject(PULDA_ERR_INVALID);
     if (opt) h->opt = *opt;
     if (h->opt.zstep_path < 0 || h->opt.zstep_path > 2) { fail(h, PULDA_ERR_INVALID, "zstep_path must be 0, 1 or 2"); return reject(PULDA_ERR_INVALID); }
+    if (h->opt.phi_mode != 0 && h->opt.phi_mode != 1) {
+        fail(h, PULDA_ERR_INVALID, "phi_mode must be 0 (Polya urn) or 1 (Dirichlet)");
+        return reject(PULDA_ERR_INVALID);
+    }
     if (h->opt.warps_per_block < 0 || h->opt.warps_per_block > kZWarps) {
         fail(h, PULDA_ERR_INVALID, "warps_per_block must be in [0, %d] (got %d)", kZWarps, h->opt.warps_per_block);
         return reject(PULDA_ERR_INVALID);
@@ -245,6 +250,9 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     ALLOC(h->topic, h->cap); ALLOC(h->c, h->cap); ALLOC(h->q, h->cap); ALLOC(h->athr, h->cap); ALLOC(h->atopic, h->cap);
     ALLOC(h->A, V); ALLOC(h->vose_p, h->cap); ALLOC(h->vose_stack, h->cap);
     if (K <= kMaxKBitmap) ALLOC(h->bitmap, static_cast<size_t>(V) * h->KW);
+    if (h->opt.phi_mode == 1) {
+        ALLOC(h->gam, h->cap); ALLOC(h->Sd, K); ALLOC(h->invS, K); ALLOC(h->dpart, dir_part_count(V, K));
+    }
     ALLOC(h->work, 4); ALLOC(h->stats, ST_TOTAL_SLOTS);
     cudaStream_t st = h->stream;
     CUI(cudaMemcpyAsync(h->w, word_ids, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
@@ -334,8 +342,15 @@ pulda_status pulda_phi_step(pulda_handle *h) {
     CU(h, cudaMemsetAsync(h->S, 0, sizeof(unsigned long long) * h->K, st));
     PhiArgs a = phi_args(h);
     CU(h, run_heavy(h));
-    launch_phi_counts(a, true, h->phi_grid, st);
-    launch_phi_fixup(a, st);
+    if (h->gam) {
+        // Algorithm 1: n columns, every Gamma draw, row sums, kept entries
+        launch_phi_counts(a, false, h->phi_grid, st);
+        launch_dir_phi(a, st);
+    } else {
+        // Algorithm 2: n columns with the Poisson draws, dead rows redrawn
+        launch_phi_counts(a, true, h->phi_grid, st);
+        launch_phi_fixup(a, st);
+    }
     launch_colptr_scan(a, st);
     launch_phi_tables(a, st);
     CU(h, cudaGetLastError());
@@ -369,6 +384,7 @@ pulda_status pulda_sync(pulda_handle *h) {
     CU(h, cudaMemcpy(&e, h->stats + ST_ERROR, sizeof e, cudaMemcpyDeviceToHost));
     if (e & ERR_DEGENERATE) return fail(h, PULDA_ERR_DEGENERATE, "a Phi row stayed all-zero after 2^20 redraws");
     if (e & ERR_INTERNAL) return fail(h, PULDA_ERR_CUDA, "z-step invariant violated (draw beyond the total mass)");
+    if (e & ERR_GAMMA) return fail(h, PULDA_ERR_DEGENERATE, "a Gamma draw was rejected 2^16 times");
     return PULDA_OK;
 }
 
@@ -460,7 +476,8 @@ pulda_status pulda_get_word_tables(pulda_handle *h, int64_t *col_ptr, int16_t *t
     if (col_ptr) CU(h, cudaMemcpyAsync(col_ptr, h->col_ptr, sizeof(int64_t) * (h->V + 1), cudaMemcpyDeviceToHost, st));
     if (topic) CU(h, cudaMemcpyAsync(topic, h->topic, sizeof(uint16_t) * nnz, cudaMemcpyDeviceToHost, st));
     if (c) CU(h, cudaMemcpyAsync(c, h->c, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st));
-    if (S) CU(h, cudaMemcpyAsync(S, h->S, sizeof(int64_t) * h->K, cudaMemcpyDeviceToHost, st));
+    if (S) CU(h, cudaMemcpyAsync(S, h->gam ? static_cast<const void *>(h->Sd) : static_cast<const void *>(h->S),
+                                 sizeof(int64_t) * h->K, cudaMemcpyDeviceToHost, st));
     if (q) CU(h, cudaMemcpyAsync(q, h->q, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st));
     if (A) CU(h, cudaMemcpyAsync(A, h->A, sizeof(uint64_t) * h->V, cudaMemcpyDeviceToHost, st));
     if (athr) CU(h, cudaMemcpyAsync(athr, h->athr, sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost, st));

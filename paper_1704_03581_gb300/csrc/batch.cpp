@@ -89,6 +89,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = "batched chains run one document per warp (docs_per_warp must be 0 or 1)";
         return bail(PULDA_ERR_INVALID);
     }
+    if (o.phi_mode != 0) {
+        b->err = "batched chains draw the Polya-urn Phi (phi_mode must be 0)";
+        return bail(PULDA_ERR_INVALID);
+    }
     if (o.warps_per_block < 0 || o.warps_per_block > 8) {
         b->err = "warps_per_block must be in [0, 8] (got " + std::to_string(o.warps_per_block) + ")";
         return bail(PULDA_ERR_INVALID);

@@ -8,10 +8,11 @@
 //     + sum_k [ lgamma(V beta) - lgamma(V beta + n_k) + sum_v ( lgamma(beta + n_{k,v}) - lgamma(beta) ) ],
 //
 // A = sum_k alpha_k, n_k = sum_v n_{k,v}; terms with a zero count vanish.
-// Three kernels: one warp per document (m_d in shared memory), one warp per
-// word (the word's n column, rebuilt from z by the Phi-step's count pass),
-// and one CTA that adds the per-document and per-word sums in a fixed order,
-// so the same topics always give the same bits.
+// Four kernels: a table of the small-count terms, one warp per document (m_d
+// in shared memory), one warp per word (the word's n column, rebuilt from z
+// by the Phi-step's count pass), and one CTA that adds the per-document and
+// per-word sums in a fixed order, so the same topics always give the same
+// bits.
 #include <algorithm>
 #include <cstdint>
 
@@ -21,6 +22,26 @@ namespace pulda {
 namespace {
 
 constexpr int kDiagWarps = 8;
+// Most counts are small: the terms lgamma(alpha_k + c) - lgamma(alpha_k) for
+// c < kTabA and lgamma(beta + n) - lgamma(beta) for n < kTabB are tabulated
+// once per evaluation, with the same expression, so each term keeps its bits.
+constexpr int kTabA = 256;
+constexpr int kTabB = 4096;
+
+// ta[k * kTabA + c] = lgamma(alpha_k + c) - lgamma(alpha_k);  tb[n] = lgamma(beta + n) - lgamma(beta).
+__global__ void k_lp_tables(const float *alpha, int K, double beta, double *ta, double *tb) {
+    const int64_t na = static_cast<int64_t>(K) * kTabA;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < na + kTabB;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        if (e < na) {
+            const double ak = static_cast<double>(alpha[e / kTabA]);
+            ta[e] = lgamma(ak + static_cast<double>(e % kTabA)) - lgamma(ak);
+        } else {
+            const int n = static_cast<int>(e - na);
+            tb[n] = lgamma(beta + static_cast<double>(n)) - lgamma(beta);
+        }
+    }
+}
 
 // Butterfly sum: every lane ends with the same, order-fixed value.
 __device__ __forceinline__ double warp_sum_f64(double v) {
@@ -32,7 +53,7 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
 // doc_lp[d] = lgamma(A) - lgamma(A + N_d) + sum_{k: m_{d,k} > 0} (lgamma(alpha_k + m_{d,k}) - lgamma(alpha_k)).
 // Documents are assigned to warps statically.
 __global__ void k_lp_docs(const int64_t *doc_off, int64_t D, const int16_t *z, int K, const float *alpha, double asum,
-                          double *doc_lp) {
+                          const double *ta, double *doc_lp) {
     extern __shared__ uint32_t dsm[];
     const int lane = threadIdx.x & 31;
     uint32_t *m = dsm + static_cast<size_t>(threadIdx.x >> 5) * K;
@@ -48,8 +69,12 @@ __global__ void k_lp_docs(const int64_t *doc_off, int64_t D, const int16_t *z, i
         for (int k = lane; k < K; k += 32) {
             const uint32_t c = m[k];
             if (c) {
-                const double ak = static_cast<double>(alpha[k]);
-                t += lgamma(ak + static_cast<double>(c)) - lgamma(ak);
+                if (c < kTabA) {
+                    t += ta[static_cast<int64_t>(k) * kTabA + c];
+                } else {
+                    const double ak = static_cast<double>(alpha[k]);
+                    t += lgamma(ak + static_cast<double>(c)) - lgamma(ak);
+                }
                 m[k] = 0;
             }
         }
@@ -62,7 +87,8 @@ __global__ void k_lp_docs(const int64_t *doc_off, int64_t D, const int16_t *z, i
 // word_lp[v] = sum_{k: n_{k,v} > 0} (lgamma(beta + n_{k,v}) - lgamma(beta)); n_k accumulated
 // (integer atomics, so in any order).  Words are assigned to warps statically.
 __global__ void k_lp_words(const int64_t *word_off, const uint16_t *nst_k, const uint32_t *nst_n,
-                           const int32_t *nnz_n, int V, double beta, double *word_lp, unsigned long long *nk) {
+                           const int32_t *nnz_n, int V, double beta, const double *tb, double *word_lp,
+                           unsigned long long *nk) {
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     const double lgb = lgamma(beta);
@@ -72,7 +98,7 @@ __global__ void k_lp_words(const int64_t *word_off, const uint16_t *nst_k, const
         double t = 0.0;
         for (int j = lane; j < cnt; j += 32) {
             const uint32_t n = nst_n[b + j];
-            t += lgamma(beta + static_cast<double>(n)) - lgb;
+            t += n < static_cast<uint32_t>(kTabB) ? tb[n] : lgamma(beta + static_cast<double>(n)) - lgb;
             atomicAdd(&nk[nst_k[b + j]], static_cast<unsigned long long>(n));
         }
         t = warp_sum_f64(t);
@@ -121,7 +147,7 @@ int device_attr(cudaDeviceAttr what) {
 }  // namespace
 
 size_t log_posterior_scratch_bytes(int64_t D, int V, int K) {
-    return sizeof(double) * (static_cast<size_t>(D) + static_cast<size_t>(V) + 3) +
+    return sizeof(double) * (static_cast<size_t>(D) + static_cast<size_t>(V) + 3 + static_cast<size_t>(K) * kTabA + kTabB) +
            sizeof(unsigned long long) * static_cast<size_t>(K);
 }
 
@@ -130,9 +156,12 @@ void launch_log_posterior(const int64_t *doc_off, int64_t D, const int16_t *z, i
     double *out = static_cast<double *>(scratch);
     double *doc_lp = out + 3;
     double *word_lp = doc_lp + D;
-    unsigned long long *nk = reinterpret_cast<unsigned long long *>(word_lp + counts.V);
+    double *ta = word_lp + counts.V;
+    double *tb = ta + static_cast<size_t>(K) * kTabA;
+    unsigned long long *nk = reinterpret_cast<unsigned long long *>(tb + kTabB);
     cudaMemsetAsync(nk, 0, sizeof(unsigned long long) * static_cast<size_t>(K), st);
     const int sms = std::max(1, device_attr(cudaDevAttrMultiProcessorCount));
+    k_lp_tables<<<4 * sms, 256, 0, st>>>(alpha, K, beta, ta, tb);
     if (D > 0) {
         // m_d of one warp: K counts; the CTA shrinks for large K
         int warps = kDiagWarps;
@@ -144,11 +173,11 @@ void launch_log_posterior(const int64_t *doc_off, int64_t D, const int16_t *z, i
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lp_docs, 32 * warps, smem);
         const int64_t need = (D + warps - 1) / warps;
         const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(sms) * std::max(1, per_sm))));
-        k_lp_docs<<<grid, 32 * warps, smem, st>>>(doc_off, D, z, K, alpha, asum, doc_lp);
+        k_lp_docs<<<grid, 32 * warps, smem, st>>>(doc_off, D, z, K, alpha, asum, ta, doc_lp);
     }
     const int wgrid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((counts.V + kDiagWarps - 1) / kDiagWarps, 8LL * sms)));
     k_lp_words<<<wgrid, 32 * kDiagWarps, 0, st>>>(counts.word_off, counts.nst_k, counts.nst_n, counts.nnz_n, counts.V, beta,
-                                                   word_lp, nk);
+                                                   tb, word_lp, nk);
     k_lp_final<<<1, kFinalThreads, 0, st>>>(doc_lp, D, word_lp, counts.V, nk, K, beta, out);
 }
 

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "device_rng.cuh"
 #include "pulda_internal.h"
 
 namespace pulda {
@@ -24,26 +25,6 @@ namespace {
 
 typedef unsigned long long u64;
 
-// ------------------------------------------------------------------ Philox
-struct U4 { uint32_t x, y, z, w; };
-
-// Philox4x32-10 (Salmon et al., SC'11).
-__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-    }
-    return U4{c0, c1, c2, c3};
-}
-
-__device__ __forceinline__ U4 draw(uint64_t seed, uint32_t a, uint32_t b, uint32_t sweep, uint32_t tag, uint32_t aux) {
-    return philox(a, b, sweep, (tag << 28) | (aux & 0x0FFFFFFFu), static_cast<uint32_t>(seed),
-                  static_cast<uint32_t>(seed >> 32));
-}
 
 // ------------------------------------------------------- Phi-step draws
 // Alias-table draw from table t: slot floor(xs * n / 2^32), kept if xa < thr.
@@ -59,11 +40,7 @@ __device__ __forceinline__ uint32_t table_draw(const DevTables &T, int t, uint32
 // one of 2^16 equiprobable cells of the normal law.
 __device__ uint32_t draw_entry(const DevTables &T, uint32_t l, uint32_t x0, uint32_t x1) {
     if (l <= static_cast<uint32_t>(kL)) return table_draw(T, static_cast<int>(l), x0, x1);
-    const uint32_t cell = x0 >> 16;
-    const uint64_t frac48 = (static_cast<uint64_t>(x0 & 0xFFFFu) << 32) | x1;
-    const double f = __dmul_rn(static_cast<double>(frac48), 3.552713678800501e-15);   // 2^-48
-    const double a = T.gauss[cell], b = T.gauss[cell + 1];
-    const double g = __dadd_rn(a, __dmul_rn(__dsub_rn(b, a), f));
+    const double g = gauss_draw(T, x0, x1);
     const double mu = __dadd_rn(T.beta, static_cast<double>(l));
     const double sd = __dsqrt_rn(mu);
     double r = floor(__dadd_rn(__dadd_rn(mu, __dmul_rn(sd, g)), 0.5));
@@ -458,7 +435,8 @@ __global__ void k_colptr_scan_multi(const PhiArgs *chains) {
 }
 
 // =================================================== Phi-step: tables
-// Per word: phi = fp32(c/S); fixed-point weights q with
+// Per word: phi = fp32(c/S) (Dirichlet mode: gamma (1/S), over the entries
+// the selection kept); fixed-point weights q with
 // 24 bits relative to the column maximum (q >= 1); alpha-part masses
 // a = round(q alpha 2^16), A = sigma_a; Vose alias table over a; bitmap of
 // the word's nonzero topics.
@@ -486,7 +464,9 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
     double phimax = 0.0;
     for (int j = lane; j < n; j += 32) {
         const int k = a.cst_k[src + j];
-        const double p = __ddiv_rn(static_cast<double>(a.cst_c[src + j]), static_cast<double>(a.S[k]));
+        // Polya urn: c / S_k; Dirichlet: gamma (1 / S_k), gamma's float bits staged in cst_c
+        const double p = a.gam ? __dmul_rn(static_cast<double>(__uint_as_float(a.cst_c[src + j])), a.invS[k])
+                               : __ddiv_rn(static_cast<double>(a.cst_c[src + j]), static_cast<double>(a.S[k]));
         a.vose_p[out + j] = static_cast<u64>(__double_as_longlong(p));    // phi, kept for the second pass
         phimax = p > phimax ? p : phimax;
     }
@@ -1282,12 +1262,14 @@ __global__ void k_n_dense(PhiArgs a, int32_t *n_kv) {
     }
 }
 
-// phi_{k,v} = fp32(c_{k,v} / S_k) for every stored entry.
+// phi_{k,v} = fp32(c_{k,v} / S_k) for every stored entry (Dirichlet mode:
+// fp32(gamma_{k,v} (1 / S_k))).
 __global__ void k_phi_values(PhiArgs a, float *phi) {
     const int64_t nnz = a.col_ptr[a.V];
     for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        phi[e] = static_cast<float>(__ddiv_rn(static_cast<double>(a.c[e]), static_cast<double>(a.S[a.topic[e]])));
+        phi[e] = a.gam ? static_cast<float>(__dmul_rn(static_cast<double>(__uint_as_float(a.c[e])), a.invS[a.topic[e]]))
+                       : static_cast<float>(__ddiv_rn(static_cast<double>(a.c[e]), static_cast<double>(a.S[a.topic[e]])));
 }
 
 int sm_count() {

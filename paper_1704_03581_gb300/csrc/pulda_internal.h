@@ -31,7 +31,12 @@ constexpr int kMaxKBitmap = 1024;
 constexpr int kZWarps = PULDA_ZWARPS;
 
 // Philox stream tags (counter word 3 = tag << 28 | aux).
-enum : uint32_t { TAG_INIT = 1, TAG_POIS = 2, TAG_BETA = 3, TAG_REDRAW_POIS = 4, TAG_REDRAW_BETA = 5, TAG_Z = 6 };
+enum : uint32_t { TAG_INIT = 1, TAG_POIS = 2, TAG_BETA = 3, TAG_REDRAW_POIS = 4, TAG_REDRAW_BETA = 5, TAG_Z = 6,
+                  TAG_GAMMA = 7, TAG_GAMMA_BOOST = 8 };
+// Dirichlet Phi-step (Algorithm 1): rows are summed in chunks of this many
+// words, and a Gamma draw gives up after this many rejected attempts.
+constexpr int kDirChunk = 256;
+constexpr uint32_t kMaxGammaTry = 1u << 16;
 
 // Slots of the per-sweep counter block on the device.
 enum : int { ST_TOKENS = 0, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_DEADROWS, ST_NNZPHI, ST_ERROR, ST_SUMINT,
@@ -39,7 +44,7 @@ enum : int { ST_TOKENS = 0, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_DEADROWS, ST_
 // Running totals of the z-step slots live at ST_COUNT + slot and are cleared
 // only at pulda_init.
 constexpr int ST_TOTAL_SLOTS = 2 * ST_COUNT;
-enum : unsigned long long { ERR_DEGENERATE = 1, ERR_INTERNAL = 2 };
+enum : unsigned long long { ERR_DEGENERATE = 1, ERR_INTERNAL = 2, ERR_GAMMA = 4 };
 
 // Fixed tables of one beta, built on the host once.
 struct HostTables {
@@ -97,6 +102,11 @@ struct PhiArgs {
     const int32_t *heavy_row;   // [V] row of the word in heavy_hist, or -1
     uint32_t *heavy_hist;       // [n_heavy * K]
     int n_heavy;
+    // Dirichlet Phi (Algorithm 1); gam is null for the Polya urn
+    float *gam;                 // [V * K] Gamma draws, word-major
+    double *Sd;                 // [K] row sums
+    double *invS;               // [K] 1 / S_k (0 for an all-zero row)
+    double *dpart;              // [ceil(V / kDirChunk) * K] chunk sums of the rows
 };
 
 // A word with more tokens than this is histogrammed in chunks of kHeavyChunk
@@ -156,6 +166,13 @@ void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st);
 size_t z_groups_smem(int K);
 int z_groups_blocks_per_sm(int K);
 int phi_counts_blocks_per_sm(int K);
+
+// Dirichlet Phi-step (dirichlet.cu), after the count-only pass has built the
+// n columns: Gamma draws, row sums, and the kept entries staged in cst_k /
+// cst_c (the draws' float bits) with nnz_c; the column scan and the table
+// kernel follow as for the Polya urn.
+void launch_dir_phi(const PhiArgs &a, cudaStream_t st);
+size_t dir_part_count(int V, int K);
 
 // Log-posterior diagnostic (diag.cu).  `counts` holds the n columns rebuilt
 // from the current z (the count-only Phi-step pass); `scratch` is device

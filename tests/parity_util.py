@@ -22,14 +22,25 @@ def oracle_tables_flat(t: O.WordTables) -> dict:
 
 
 def compare_tables(gpu: dict, ch: O.Chain, where: str = ""):
+    """Bitwise: in Dirichlet mode S is compared as the bits of the double row sums and c
+    as the bits of the float Gamma draws of the kept entries."""
     o = oracle_tables_flat(ch.tables)
-    assert np.array_equal(gpu["S"], ch.S), f"{where}: row sums S differ"
+    dirichlet = getattr(ch, "dirichlet", False)
+    if dirichlet:
+        bad = np.nonzero(gpu["S"] != ch.S.view(np.int64))[0]
+        assert bad.size == 0, f"{where}: row sums S differ at {bad[:10]} (gpu {gpu['S'][bad[:3]].view(np.float64)} " \
+            f"oracle {ch.S[bad[:3]]})"
+    else:
+        assert np.array_equal(gpu["S"], ch.S), f"{where}: row sums S differ"
     assert np.array_equal(gpu["col_ptr"], o["col_ptr"]), f"{where}: Phi sparsity (column sizes) differs " \
         f"at words {np.nonzero(np.diff(gpu['col_ptr']) != np.diff(o['col_ptr']))[0][:10]}"
     mask = np.arange(ch.K)[None, :] < ch.tables.ncol[:, None]
     assert np.array_equal(gpu["topic"], o["topic"]), f"{where}: Phi topic ids differ"
-    assert np.array_equal(gpu["c"], ch.c[np.arange(ch.V)[:, None], ch.tables.topic.astype(np.int64)][mask]), \
-        f"{where}: Poisson counts c differ"
+    want_c = ch.c[np.arange(ch.V)[:, None], ch.tables.topic.astype(np.int64)][mask]
+    if dirichlet:
+        want_c = want_c.view(np.uint32)
+    what = "Gamma draws" if dirichlet else "Poisson counts c"
+    assert np.array_equal(gpu["c"], want_c), f"{where}: {what} differ"
     for k in ("q", "athr", "atopic", "A"):
         bad = np.nonzero(gpu[k] != o[k])[0]
         assert bad.size == 0, f"{where}: {k} differs at {bad[:10]} (gpu {gpu[k][bad[:5]]} oracle {o[k][bad[:5]]})"
@@ -46,10 +57,12 @@ def first_mismatch(z_gpu: np.ndarray, z_or: np.ndarray, doc_off: np.ndarray) -> 
 
 
 def lockstep(w, doc_off, K: int, V: int, alpha, beta: float, seed: int, sweeps: int, path: int = 0,
-             check_tables: bool = True, check_counts_every: int = 0, docs_per_warp: int = 0):
-    """Run both sides for `sweeps` sweeps, comparing after each half-sweep."""
-    s = P.Sampler(w, doc_off, K, V, alpha, beta, seed, zstep_path=path, docs_per_warp=docs_per_warp)
-    ch = O.Chain(w, doc_off, K, V, alpha, beta, seed)
+             check_tables: bool = True, check_counts_every: int = 0, docs_per_warp: int = 0, phi_mode: int = 0):
+    """Run both sides for `sweeps` sweeps, comparing after each half-sweep.
+    phi_mode 1 runs both in Algorithm 1's Dirichlet mode."""
+    s = P.Sampler(w, doc_off, K, V, alpha, beta, seed, zstep_path=path, docs_per_warp=docs_per_warp,
+                  phi_mode=phi_mode)
+    ch = O.Chain(w, doc_off, K, V, alpha, beta, seed, dirichlet=phi_mode == 1)
     try:
         zg = s.z()
         assert np.array_equal(zg, ch.z), "initial topics differ: " + first_mismatch(zg, ch.z, doc_off)

@@ -48,7 +48,8 @@ def test_init_rejects_bad_arguments_without_a_gpu():
         else:
             raise AssertionError("accepted " + repr(kwargs))
     for kwargs, frag in [(dict(zstep_path=3), "zstep_path"), (dict(warps_per_block=9), "warps_per_block"),
-                         (dict(warps_per_block=-1), "warps_per_block"), (dict(docs_per_warp=2), "docs_per_warp")]:
+                         (dict(warps_per_block=-1), "warps_per_block"), (dict(docs_per_warp=2), "docs_per_warp"),
+                         (dict(phi_mode=2), "phi_mode")]:
         try:
             P.pulda_init(w, off, 4, 3, 0.1, 0.01, 0, **kwargs)
         except P.PuldaError as e:
