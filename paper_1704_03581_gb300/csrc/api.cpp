@@ -148,6 +148,7 @@ PhiArgs phi_args(pulda_handle *h) {
     a.S = h->S; a.rowbuf = h->rowbuf; a.col_ptr = h->col_ptr;
     a.topic = h->topic; a.c = h->c; a.q = h->q; a.athr = h->athr; a.atopic = h->atopic;
     a.A = h->A; a.vose_p = h->vose_p; a.vose_stack = h->vose_stack; a.bitmap = h->bitmap; a.KW = h->KW;
+    a.qdense = h->qdense; a.dense_slot = h->dense_slot;
     a.alpha = h->alpha; a.work = h->work; a.stats = h->stats;
     a.heavy_row = h->heavy_row; a.heavy_hist = h->heavy_hist; a.n_heavy = h->n_heavy;
     a.gam = h->gam; a.Sd = h->Sd; a.invS = h->invS; a.dpart = h->dpart;
@@ -160,6 +161,7 @@ ZArgs z_args(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, 
     a.doc_off = doc_off; a.doc_order = doc_order; a.D = D; a.w = w; a.z = z;
     a.col_ptr = h->col_ptr; a.topic = h->topic; a.q = h->q; a.A = h->A; a.athr = h->athr; a.atopic = h->atopic;
     a.bitmap = h->bitmap; a.K = h->K; a.KW = h->KW; a.seed = seed; a.sweep = sweep; a.index_base = index_base;
+    a.qdense = h->qdense; a.dense_slot = h->dense_slot;
     a.path = h->opt.zstep_path; a.work = h->work + 1; a.stats = h->stats;
     return a;
 }
@@ -280,6 +282,23 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     std::stable_sort(word_order.begin(), word_order.end(),
                      [&](int32_t a, int32_t b) { return woff[a + 1] - woff[a] > woff[b + 1] - woff[b]; });
     CUI(cudaMemcpyAsync(h->word_order, word_order.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, st));
+    // dense q rows for the most frequent words, within kDenseBytes
+    if (K <= kMaxKBitmap && kDenseBytes > 0) {
+        const int64_t cap = std::min<int64_t>(V, kDenseBytes / (static_cast<int64_t>(sizeof(uint32_t)) * K));
+        std::vector<int32_t> slot(V, -1);
+        int32_t n = 0;
+        for (int32_t v : word_order) {
+            if (n >= cap || woff[v + 1] - woff[v] < kDenseMinTokens) break;
+            slot[v] = n++;
+        }
+        if (n > 0) {
+            ALLOC(h->dense_slot, V);
+            ALLOC(h->qdense, static_cast<size_t>(n) * K);
+            CUI(cudaMemcpyAsync(h->dense_slot, slot.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, st));
+            CUI(cudaStreamSynchronize(st));
+        }
+        h->n_dense = n;
+    }
     // the most frequent words are histogrammed in chunks by many CTAs
     {
         std::vector<int32_t> row(V, -1);

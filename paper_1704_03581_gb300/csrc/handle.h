@@ -38,6 +38,8 @@ struct pulda_handle {
     uint16_t *nst_k = nullptr; uint32_t *nst_n = nullptr; int32_t *nnz_n = nullptr;
     uint16_t *cst_k = nullptr; uint32_t *cst_c = nullptr; int32_t *nnz_c = nullptr;
     unsigned long long *S = nullptr; uint32_t *rowbuf = nullptr; int64_t *col_ptr = nullptr;
+    // dense q rows of the most frequent words (z-step document side)
+    uint32_t *qdense = nullptr; int32_t *dense_slot = nullptr; int n_dense = 0;
     // Dirichlet Phi (Algorithm 1), allocated in that mode only
     float *gam = nullptr; double *Sd = nullptr, *invS = nullptr, *dpart = nullptr;
     uint16_t *topic = nullptr; uint32_t *c = nullptr, *q = nullptr, *athr = nullptr; uint16_t *atopic = nullptr;

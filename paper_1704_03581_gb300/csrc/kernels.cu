@@ -457,6 +457,16 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
             bm[wi] = make_uint2(bits, static_cast<uint32_t>(lo));
         }
     }
+    // a word with a dense q row: zero it (the column's entries are written below)
+    uint32_t *qrow = nullptr;
+    if (a.dense_slot) {
+        const int slot = a.dense_slot[v];
+        if (slot >= 0) {
+            qrow = a.qdense + static_cast<int64_t>(slot) * a.K;
+            for (int k = lane; k < a.K; k += 32) qrow[k] = 0;
+            __syncwarp();
+        }
+    }
     if (n == 0) {
         if (lane == 0) a.A[v] = 0;
         return;
@@ -491,6 +501,7 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
         a.topic[out + j] = static_cast<uint16_t>(k);
         a.c[out + j] = c;
         a.q[out + j] = qv;
+        if (qrow) qrow[k] = qv;
         a.vose_p[out + j] = am * static_cast<u64>(n);   // scaled so each slot holds A units
         a.athr[out + j] = 0xFFFFFFFFu;
         a.atopic[out + j] = static_cast<uint16_t>(k);
@@ -542,13 +553,13 @@ __global__ void k_phi_tables_multi(const PhiArgs *chains, const int2 *items, int
 // Entries of the document-side intersection each lane gathers with
 // independent loads before consuming them.
 #ifndef PULDA_ZGATHER
-#define PULDA_ZGATHER 4
+#define PULDA_ZGATHER 6
 #endif
-// 4-warp CTAs, at least 7 per SM: the kernel fits 64 registers without
+// 4-warp CTAs, 8 per SM: the kernel fits 64 registers without
 // spilling and 32 warps share each SM (issue slots are what bound it; fewer
 // warps leave them idle while each warp waits on its dependent chain).
 #ifndef PULDA_ZMINBLOCKS
-#define PULDA_ZMINBLOCKS 7
+#define PULDA_ZMINBLOCKS 8
 #endif
 // The document side is iterated when K_d * kDocRatio < K_v * 16.  An element
 // of the document side costs about twice one of the column side (a bit scan
@@ -580,7 +591,7 @@ __host__ __device__ __forceinline__ int mi(int k) { return k + (k >> 5); }
 // Shared memory of one z-step warp, in 32-bit words: m_d (skewed, rounded up
 // to 16 bytes), then the staging records of the 32 tokens in flight.
 __host__ __device__ __forceinline__ int z_m_words(int K) { return (K + (K >> 5) + 1 + 3) & ~3; }
-constexpr int kTokRecWords = 8;     // two uint4 per token
+constexpr int kTokRecWords = 9;     // two uint4 per token, and the offset of its word's dense q row
 __host__ __device__ __forceinline__ int z_warp_words(int K) { return z_m_words(K) + 32 * kTokRecWords; }
 
 // Counters of a z-step warp.  The warp-uniform ones are held one per lane
@@ -654,6 +665,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
         //   rec[2t+1] = {Philox x0, x1, word, K_v | old topic << 16}
         // (column starts are below 2^48, K_v <= 16384, topics < 16384).
         uint4 *rec = reinterpret_cast<uint4 *>(m + z_m_words(K));
+        uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);   // q row offset of the token's word, or ~0
         if (valid) {
             const int wv = r.w[i];
             const int zo = r.z[i];
@@ -673,10 +685,14 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
                                        static_cast<uint32_t>(Av), static_cast<uint32_t>(Av >> 32));
             rec[2 * lane + 1] = make_uint4(x.x, x.y, static_cast<uint32_t>(wv),
                                            static_cast<uint32_t>(nw) | (static_cast<uint32_t>(zo) << 16));
+            const int ds = a.dense_slot ? a.dense_slot[wv] : -1;
+            drow_of[lane] = ds >= 0 ? static_cast<uint32_t>(ds) * static_cast<uint32_t>(K) : 0xFFFFFFFFu;
         }
         __syncwarp();
-        uint2 bm_next = make_uint2(0u, 0u);
-        if (use_bm && lane < a.KW) bm_next = a.bitmap[static_cast<int64_t>(rec[1].z) * a.KW + lane];
+        // the bits half of the word's bitmap entries (32 topics per lane)
+        const uint32_t *bits = reinterpret_cast<const uint32_t *>(a.bitmap);
+        uint32_t bm_next = 0u;
+        if (use_bm && lane < a.KW) bm_next = bits[2 * (static_cast<int64_t>(rec[1].z) * a.KW + lane)];
         for (int tt = 0; tt < cnt; ++tt) {
             const uint4 t0 = rec[2 * tt], t1 = rec[2 * tt + 1];
             const int kold = static_cast<int>(t1.w >> 16);
@@ -685,9 +701,9 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
             const u64 At = (static_cast<u64>(t0.w) << 32) | t0.z;
             const u64 U = (static_cast<u64>(t1.x) << 32) | t1.y;
             const int ka = static_cast<int>(t0.y >> 16);
-            const uint2 bm = bm_next;
+            const uint32_t bm = bm_next;
             if (use_bm && tt + 1 < cnt && lane < a.KW)   // the next token's bitmap word, fetched while this one is drawn
-                bm_next = a.bitmap[static_cast<int64_t>(rec[2 * tt + 3].z) * a.KW + lane];
+                bm_next = bits[2 * (static_cast<int64_t>(rec[2 * tt + 3].z) * a.KW + lane)];
             // remove token i: m^{-i}
             const uint32_t old = m[mi(kold)];
             __syncwarp();
@@ -699,8 +715,12 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
             __syncwarp();
             st.add(2, static_cast<u64>(kd < n_w ? kd : n_w));
             st.add(5, kd < n_w ? 1u : 0u);
-            const bool docside = use_bm && (a.path == 2 || kd * kDocRatio < n_w * 16);
+            // The document side needs the word's dense q row (q of topic 32 lane + b
+            // at qd[b]); a word without one is iterated on the column side.
+            const uint32_t drow = drow_of[tt];
+            const bool docside = use_bm && drow != 0xFFFFFFFFu && (a.path == 2 || kd * kDocRatio < n_w * 16);
             const uint32_t *qcol = a.q + col;
+            const uint32_t *qd = a.qdense + drow + lane * 32;
             // per-lane partial sums of q m, in ascending topic order across lanes
             u64 acc = 0;
             uint32_t qv[kGather];
@@ -708,7 +728,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
             uint32_t rest = 0;         // docside: bits beyond the first kGather
             int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
             if (docside) {
-                uint32_t rem = bm.x & mbits;
+                uint32_t rem = bm & mbits;
                 st.inter += static_cast<u64>(__popc(rem));
 #pragma unroll
                 for (int t = 0; t < kGather; ++t) {
@@ -718,7 +738,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
                         const int b = __ffs(rem) - 1;
                         rem &= rem - 1;
                         bp[t] = b;
-                        qv[t] = qcol[bm.y + __popc(bm.x & ((1u << b) - 1u))];
+                        qv[t] = qd[b];
                     }
                 }
 #pragma unroll
@@ -727,7 +747,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
                 rest = rem;
                 for (uint32_t bb = rest; bb; bb &= bb - 1) {
                     const int b = __ffs(bb) - 1;
-                    acc += static_cast<u64>(qcol[bm.y + __popc(bm.x & ((1u << b) - 1u))]) * m[lane * 33 + b];
+                    acc += static_cast<u64>(qd[b]) * m[lane * 33 + b];
                 }
             } else {
                 seg = (n_w + 31) >> 5;
@@ -773,8 +793,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
                                 }
                                 for (uint32_t bb = rest; f < 0 && bb; bb &= bb - 1) {
                                     const int b = __ffs(bb) - 1;
-                                    run += static_cast<u64>(qcol[bm.y + __popc(bm.x & ((1u << b) - 1u))]) *
-                                           m[lane * 33 + b];
+                                    run += static_cast<u64>(qd[b]) * m[lane * 33 + b];
                                     if (rb < run) f = lane * 32 + b;
                                 }
                             } else {
@@ -1205,7 +1224,9 @@ __global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_
 // across passes, one warp per slot.  A slot whose pass counter is 0 first
 // gets its uniform initial topics (counter 0, as pulda_infer).  The slot's
 // (pass, position) is written back for the host's completion check.
-__global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_serve_step(ZArgs a, ServeSlot *slots, const int32_t *active,
+// Its slot bookkeeping needs a few more registers than k_z_step: 7 CTAs per
+// SM keep it free of spills.
+__global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSlot *slots, const int32_t *active,
                                                                      int n_active, const int32_t *arena_w,
                                                                      int16_t *arena_z, int64_t slice, int *work) {
     extern __shared__ uint32_t zsm[];

@@ -29,6 +29,15 @@ constexpr int kMaxKBitmap = 1024;
 #define PULDA_ZWARPS 4
 #endif
 constexpr int kZWarps = PULDA_ZWARPS;
+// Words with tokens, most frequent first, also keep their fixed-point
+// weights q as dense K-entry rows, up to this many bytes (K <= kMaxKBitmap):
+// the z-step's document side reads q at topic k there.  A word without a row
+// is always iterated on its column side (the same sums).
+#ifndef PULDA_DENSE_BYTES
+#define PULDA_DENSE_BYTES (256ll << 20)
+#endif
+constexpr long long kDenseBytes = PULDA_DENSE_BYTES;
+constexpr int64_t kDenseMinTokens = 1;
 
 // Philox stream tags (counter word 3 = tag << 28 | aux).
 enum : uint32_t { TAG_INIT = 1, TAG_POIS = 2, TAG_BETA = 3, TAG_REDRAW_POIS = 4, TAG_REDRAW_BETA = 5, TAG_Z = 6,
@@ -94,6 +103,8 @@ struct PhiArgs {
     uint16_t *vose_stack;       // [cap] scratch
     uint2 *bitmap;              // [V * KW] {nonzero-topic bits, entries before this word} or null
     int KW;
+    uint32_t *qdense;           // [n_dense * K] q by topic (0 off the column) or null
+    const int32_t *dense_slot;  // [V] row of the word in qdense, or -1
     const float *alpha;         // [K]
     int *work;                  // dynamic word counter
     unsigned long long *stats;  // [ST_COUNT]
@@ -134,6 +145,8 @@ struct ZArgs {
     const uint32_t *athr;
     const uint16_t *atopic;
     const uint2 *bitmap;        // null when K > kMaxKBitmap
+    const uint32_t *qdense;     // dense q rows of the most frequent words, or null
+    const int32_t *dense_slot;  // [V] row in qdense or -1
     int K, KW;
     uint64_t seed;
     uint32_t sweep;
