@@ -511,7 +511,13 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
     if (lane == 0) a.A[v] = asum;
     __syncwarp();
     if (lane != 0 || asum == 0) return;
-    // Vose: small stack grows up from 0, large stack down from n-1
+    // Vose: small stack grows up from 0, large stack down from n-1.
+    // Thresholds floor(P 2^32 / A) divide by the word's invariant A:
+    // Moller and Granlund's 2/1 division with a reciprocal of the normalised
+    // divisor, one 128-bit division per word instead of one per slot (exact).
+    const int sh = __clzll(static_cast<long long>(asum));
+    const u64 dn = asum << sh;
+    const u64 vinv = static_cast<u64>((~static_cast<unsigned __int128>(0)) / dn);   // floor((2^128-1)/dn) - 2^64
     u64 *P = a.vose_p + out;
     uint16_t *stk = a.vose_stack + out;
     int ns = 0, nl = 0;
@@ -524,7 +530,21 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
         --nl;
         const int l = stk[n - 1 - nl];
         const u64 ps = P[s];
-        a.athr[out + s] = static_cast<uint32_t>((static_cast<unsigned __int128>(ps) << 32) / asum);
+        {   // (u1, u0) = ps 2^32 2^sh, u1 < dn since ps < asum
+            const u64 hi = ps >> 32, lo = ps << 32;
+            const u64 u1 = sh ? (hi << sh) | (lo >> (64 - sh)) : hi;
+            const u64 u0 = lo << sh;
+            u64 q0 = vinv * u1;
+            u64 q1 = __umul64hi(vinv, u1);
+            const u64 t = q0 + u0;
+            q1 += u1 + (t < q0 ? 1ull : 0ull);
+            q0 = t;
+            q1 += 1;
+            u64 r = u0 - q1 * dn;
+            if (r > q0) { q1 -= 1; r += dn; }
+            if (r >= dn) q1 += 1;
+            a.athr[out + s] = static_cast<uint32_t>(q1);
+        }
         a.atopic[out + s] = a.topic[out + l];
         const u64 pl = P[l] - (asum - ps);
         P[l] = pl;
