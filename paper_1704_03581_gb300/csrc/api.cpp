@@ -6,6 +6,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/pulda.h"
@@ -58,6 +59,25 @@ cudaError_t dalloc(pulda_handle *h, T **p, size_t count) {
     return e;
 }
 
+// Smallest i in [0, n) with bad(i), else n, using up to 16 host threads.
+template <typename F>
+int64_t parallel_first(int64_t n, F bad) {
+    const int64_t kChunk = int64_t(1) << 22;
+    const int nt = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>({int64_t(16), (n + kChunk - 1) / kChunk,
+                                                         static_cast<int64_t>(std::max(1u, std::thread::hardware_concurrency()))})));
+    std::vector<int64_t> first(nt, n);
+    auto scan = [&](int t) {
+        const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+        for (int64_t i = lo; i < hi; ++i)
+            if (bad(i)) { first[t] = i; return; }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(scan, t);
+    scan(0);
+    for (auto &x : th) x.join();
+    return *std::min_element(first.begin(), first.end());
+}
+
 pulda_status check_corpus(pulda_handle *h, const int32_t *w, const int64_t *off, int64_t D, int V,
                           int64_t *N_out) {
     if (D < 0) return fail(h, PULDA_ERR_INVALID, "D must be >= 0 (got %lld)", (long long)D);
@@ -71,9 +91,11 @@ pulda_status check_corpus(pulda_handle *h, const int32_t *w, const int64_t *off,
     const int64_t N = D > 0 ? off[D] : 0;
     if (N >= (int64_t(1) << 31)) return fail(h, PULDA_ERR_INVALID, "corpus larger than 2^31-1 tokens");
     if (N > 0 && !w) return fail(h, PULDA_ERR_INVALID, "word_ids is NULL");
-    for (int64_t i = 0; i < N; ++i)
-        if (w[i] < 0 || w[i] >= V)
-            return fail(h, PULDA_ERR_INVALID, "word id %d at token %lld is outside [0, %d)", w[i], (long long)i, V);
+    // the first word id outside [0, V): chunks scanned by host threads, the
+    // smallest bad position wins (the same answer as one scan)
+    const int64_t bad = parallel_first(N, [&](int64_t i) { return w[i] < 0 || w[i] >= V; });
+    if (bad < N)
+        return fail(h, PULDA_ERR_INVALID, "word id %d at token %lld is outside [0, %d)", w[bad], (long long)bad, V);
     *N_out = N;
     return PULDA_OK;
 }

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <thread>
 
 #include "pulda_internal.h"
 
@@ -103,7 +104,15 @@ const std::vector<double> &gauss_nodes() {
         const int half = kGaussCells / 2;
         nodes.assign(kGaussCells + 1, 0.0);
         nodes[0] = normal_quantile(5.9604644775390625e-08);
-        for (int i = 1; i < half; ++i) nodes[i] = normal_quantile(static_cast<double>(i) / kGaussCells);
+        // every node is its own bisection: split over host threads
+        const int nt = static_cast<int>(std::max(1u, std::min(16u, std::thread::hardware_concurrency())));
+        auto fill = [&](int t) {
+            for (int i = 1 + t; i < half; i += nt) nodes[i] = normal_quantile(static_cast<double>(i) / kGaussCells);
+        };
+        std::vector<std::thread> th;
+        for (int t = 1; t < nt; ++t) th.emplace_back(fill, t);
+        fill(0);
+        for (auto &x : th) x.join();
         nodes[half] = 0.0;
         for (int i = 0; i < half; ++i) nodes[kGaussCells - i] = -nodes[i];
     });
