@@ -173,7 +173,7 @@ PhiArgs phi_args(pulda_handle *h) {
     a.qdense = h->qdense; a.dense_slot = h->dense_slot;
     a.alpha = h->alpha; a.work = h->work; a.stats = h->stats;
     a.heavy_row = h->heavy_row; a.heavy_hist = h->heavy_hist; a.n_heavy = h->n_heavy;
-    a.gam = h->gam; a.Sd = h->Sd; a.invS = h->invS; a.dpart = h->dpart;
+    a.gam = h->gam; a.Sd = h->Sd; a.invS = h->invS; a.invSf = h->invSf; a.dpart = h->dpart;
     return a;
 }
 
@@ -275,7 +275,8 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     ALLOC(h->A, V); ALLOC(h->vose_p, h->cap); ALLOC(h->vose_stack, h->cap);
     if (K <= kMaxKBitmap) ALLOC(h->bitmap, static_cast<size_t>(V) * h->KW);
     if (h->opt.phi_mode == 1) {
-        ALLOC(h->gam, h->cap); ALLOC(h->Sd, K); ALLOC(h->invS, K); ALLOC(h->dpart, dir_part_count(V, K));
+        ALLOC(h->gam, h->cap); ALLOC(h->Sd, K); ALLOC(h->invS, K); ALLOC(h->invSf, K);
+        ALLOC(h->dpart, dir_part_count(V, K));
     }
     ALLOC(h->work, 4); ALLOC(h->stats, ST_TOTAL_SLOTS);
     cudaStream_t st = h->stream;

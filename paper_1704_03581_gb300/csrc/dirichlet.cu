@@ -110,26 +110,31 @@ __device__ float gamma_draw(const DevTables &T, float a, uint64_t seed, uint32_t
     return 0.0f;
 }
 
-// One CTA per word (grid-stride): the word's n column into a dense shared
-// array, then gamma_{k,v} for every topic, written word-major.
-__global__ void __launch_bounds__(kDirBlock) k_dir_gamma(PhiArgs a) {
-    extern __shared__ uint32_t nrow[];
+// One warp per word (grid-stride): the word's n column into a dense array in
+// the warp's shared memory, then gamma_{k,v} for every topic, word-major.
+// Warps do not wait on one another between words.
+__global__ void k_dir_gamma(PhiArgs a) {
+    extern __shared__ uint32_t nsm[];
     const int K = a.K;
+    const int lane = threadIdx.x & 31;
+    uint32_t *nrow = nsm + static_cast<size_t>(threadIdx.x >> 5) * K;
+    const int wpb = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpb;
     const uint32_t sweep = a.sweep_ptr ? *a.sweep_ptr : a.sweep;
     const float bf = static_cast<float>(a.tab.beta);
     bool fail = false;
-    for (int v = blockIdx.x; v < a.V; v += gridDim.x) {
-        for (int k = threadIdx.x; k < K; k += kDirBlock) nrow[k] = 0;
-        __syncthreads();
+    for (int v = blockIdx.x * wpb + (threadIdx.x >> 5); v < a.V; v += nwarps) {
+        for (int k = lane; k < K; k += 32) nrow[k] = 0;
+        __syncwarp();
         const int64_t b = a.word_off[v];
-        for (int j = threadIdx.x; j < a.nnz_n[v]; j += kDirBlock) nrow[a.nst_k[b + j]] = a.nst_n[b + j];
-        __syncthreads();
+        for (int j = lane; j < a.nnz_n[v]; j += 32) nrow[a.nst_k[b + j]] = a.nst_n[b + j];
+        __syncwarp();
         float *out = a.gam + static_cast<int64_t>(v) * K;
-        for (int k = threadIdx.x; k < K; k += kDirBlock) {
+        for (int k = lane; k < K; k += 32) {
             const float shape = __fadd_rn(bf, static_cast<float>(nrow[k]));
             out[k] = gamma_draw(a.tab, shape, a.seed, static_cast<uint32_t>(v), static_cast<uint32_t>(k), sweep, &fail);
         }
-        __syncthreads();
+        __syncwarp();
     }
     if (fail) atomicOr(&a.stats[ST_ERROR], ERR_GAMMA);
 }
@@ -153,22 +158,38 @@ __global__ void k_dir_rowsum_final(PhiArgs a, int n_chunks) {
         for (int c = 0; c < n_chunks; ++c) tot = __dadd_rn(tot, a.dpart[static_cast<int64_t>(c) * a.K + k]);
         a.Sd[k] = tot;
         a.invS[k] = tot > 0.0 ? __ddiv_rn(1.0, tot) : 0.0;
+        a.invSf[k] = __double2float_rn(a.invS[k]);
     }
 }
 
-// One warp per word: phi = gamma (1/S_k); the column maximum fixes the
-// fixed-point scale 2^(24 - e); entries whose weight rounds to 0 are dropped,
-// the rest staged in ascending topic order (cst_k, cst_c = the draw's bits).
+// One warp per word: phi = gamma (1/S_k) in double; the column maximum fixes
+// the fixed-point scale 2^(24 - e); entries whose weight rounds to 0 are
+// dropped, the rest staged in ascending topic order (cst_k, cst_c = the
+// draw's bits).  FP64 is scarce on this GPU, so a float product screens every
+// entry (relative error below 2^-22): the maximum is taken exactly over the
+// entries within 2^-12 of the float maximum, and an entry is decided by the
+// double test only within 0.1% of the threshold 2^(e-25).  Tiny columns (float
+// maximum or threshold below 2^-100, where float products lose precision) take
+// the double path throughout.  The decisions are those of the double test.
 __global__ void k_dir_select(PhiArgs a) {
     const int lane = threadIdx.x & 31;
     const int K = a.K;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const float kTiny = 7.88860905e-31f;      // 2^-100
     for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < a.V; v += nwarps) {
         const float *g = a.gam + static_cast<int64_t>(v) * K;
+        float fmax = 0.0f;
+        for (int k = lane; k < K; k += 32) fmax = fmaxf(fmax, __fmul_rn(g[k], a.invSf[k]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) fmax = fmaxf(fmax, __shfl_xor_sync(0xFFFFFFFFu, fmax, o));
+        const bool exact_all = fmax < kTiny;
+        const float fcut = __fmul_rn(fmax, 0.999755859f);       // 1 - 2^-12
         double pmax = 0.0;
         for (int k = lane; k < K; k += 32) {
-            const double p = __dmul_rn(static_cast<double>(g[k]), a.invS[k]);
-            pmax = p > pmax ? p : pmax;
+            if (exact_all || __fmul_rn(g[k], a.invSf[k]) >= fcut) {
+                const double p = __dmul_rn(static_cast<double>(g[k]), a.invS[k]);
+                pmax = p > pmax ? p : pmax;
+            }
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
@@ -180,6 +201,10 @@ __global__ void k_dir_select(PhiArgs a) {
             const long long bits = __double_as_longlong(pmax);
             const int e = static_cast<int>((bits >> 52) & 0x7FF) - 1022;
             const double scale = __longlong_as_double(static_cast<long long>(1023 + 24 - e) << 52);
+            // threshold 2^(e-25) in float, when it is a normal float well above the subnormals
+            const bool screen = !exact_all && e - 25 >= -100;
+            const float thr = screen ? __uint_as_float(static_cast<uint32_t>(e - 25 + 127) << 23) : 0.0f;
+            const float hi = __fmul_rn(thr, 1.001f), lo = __fmul_rn(thr, 0.999f);
             const int64_t dst = static_cast<int64_t>(v) * K;
             for (int k0 = 0; k0 < K; k0 += 32) {
                 const int k = k0 + lane;
@@ -187,8 +212,13 @@ __global__ void k_dir_select(PhiArgs a) {
                 float gk = 0.0f;
                 if (k < K) {
                     gk = g[k];
-                    const double p = __dmul_rn(static_cast<double>(gk), a.invS[k]);
-                    keep = floor(__dadd_rn(__dmul_rn(p, scale), 0.5)) >= 1.0;
+                    const float pf = screen ? __fmul_rn(gk, a.invSf[k]) : 0.0f;
+                    if (screen && pf >= hi) {
+                        keep = true;
+                    } else if (!screen || pf > lo) {
+                        const double p = __dmul_rn(static_cast<double>(gk), a.invS[k]);
+                        keep = floor(__dadd_rn(__dmul_rn(p, scale), 0.5)) >= 1.0;
+                    }
                 }
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
                 if (keep) {
@@ -218,14 +248,19 @@ size_t dir_part_count(int V, int K) {
 
 void launch_dir_phi(const PhiArgs &a, cudaStream_t st) {
     const int n = sms();
-    const size_t smem = sizeof(uint32_t) * static_cast<size_t>(a.K);
+    // one warp per word, its n row (K counts) in shared memory: up to 8 warps
+    // per CTA within 96 KB (one warp of up to 64 KB for the largest K)
+    int wpb = 8;
+    while (wpb > 1 && static_cast<size_t>(wpb) * a.K * sizeof(uint32_t) > 96 * 1024) wpb >>= 1;
+    const size_t smem = static_cast<size_t>(wpb) * a.K * sizeof(uint32_t);
     if (smem > 48 * 1024) {
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncSetAttribute(k_dir_gamma, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     }
-    k_dir_gamma<<<std::min(a.V, 8 * n), kDirBlock, smem, st>>>(a);
+    const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((a.V + wpb - 1) / wpb, 16LL * n)));
+    k_dir_gamma<<<grid, 32 * wpb, smem, st>>>(a);
     const int n_chunks = (a.V + kDirChunk - 1) / kDirChunk;
     k_dir_rowsum_part<<<n_chunks, kDirBlock, 0, st>>>(a);
     k_dir_rowsum_final<<<(a.K + 255) / 256, 256, 0, st>>>(a, n_chunks);

@@ -41,7 +41,7 @@ struct pulda_handle {
     // dense q rows of the most frequent words (z-step document side)
     uint32_t *qdense = nullptr; int32_t *dense_slot = nullptr; int n_dense = 0;
     // Dirichlet Phi (Algorithm 1), allocated in that mode only
-    float *gam = nullptr; double *Sd = nullptr, *invS = nullptr, *dpart = nullptr;
+    float *gam = nullptr, *invSf = nullptr; double *Sd = nullptr, *invS = nullptr, *dpart = nullptr;
     uint16_t *topic = nullptr; uint32_t *c = nullptr, *q = nullptr, *athr = nullptr; uint16_t *atopic = nullptr;
     unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint2 *bitmap = nullptr;
     int *work = nullptr;

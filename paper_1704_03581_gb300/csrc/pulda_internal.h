@@ -117,6 +117,7 @@ struct PhiArgs {
     float *gam;                 // [V * K] Gamma draws, word-major
     double *Sd;                 // [K] row sums
     double *invS;               // [K] 1 / S_k (0 for an all-zero row)
+    float *invSf;               // [K] 1 / S_k rounded to float (screening only)
     double *dpart;              // [ceil(V / kDirChunk) * K] chunk sums of the rows
 };
 
