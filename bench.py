@@ -149,18 +149,41 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic() -> float | None:
-    """DRAM bytes per z-step launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+def recorded_profile() -> dict:
+    """The committed ncu record of one full-size z-step launch, if it was taken
+    on the current kernel source, else {}."""
     p = os.path.join(ROOT, "profiles", "z_step_large_traffic.json")
     try:
         with open(p) as f:
             rec = json.load(f)
         if rec.get("kernels_cu_sha") == kernel_source_hash():
-            return float(rec["dram_bytes_per_launch"])
+            return rec
     except Exception:
         pass
-    return None
+    return {}
+
+
+def recorded_traffic() -> float | None:
+    """DRAM bytes per z-step launch from the committed ncu record, or None."""
+    rec = recorded_profile()
+    return float(rec["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in rec else None
+
+
+def issue_roofline(tokens_per_s: float, sm_mhz: float | None) -> dict | None:
+    """The z-step against the SMs' instruction-issue rate: warp instructions per
+    token (ncu, one full-size launch) times the measured tokens/s, against
+    SMs x 4 schedulers x 1 warp instruction per cycle at the sampled SM clock."""
+    rec = recorded_profile()
+    if "warp_instructions_per_token" not in rec:
+        return None
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    peak = sms * 4 * mhz * 1e6
+    achieved = float(rec["warp_instructions_per_token"]) * tokens_per_s
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_token": rec["warp_instructions_per_token"],
+            "peak_kind": f"{sms} SMs x 4 schedulers x 1 instruction/cycle at {mhz:.0f} MHz"}
 
 
 def z_bytes(tokens: int, sum_min: int, a_branch: int, docs: int) -> int:
@@ -351,6 +374,7 @@ def run_pulda(args, corpus, rank: int, world: int):
         "phi_step": {"ms_per_sweep": phi_ms / K, "nnz_phi": nnz_phi},
         "log_posterior": {"before_timed": lp_before, "after_timed": lp_after, "ms_per_evaluation": lp_ms,
                           "note": "collapsed log p(w, z | alpha, beta), not timed"},
+        "roofline_issue": issue_roofline(K * corpus.N / (z_ms / 1000.0), (clk or {}).get("sm_mhz")),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_z_step", "peak_kind": f"{peak_kind} HBM copy bandwidth",
