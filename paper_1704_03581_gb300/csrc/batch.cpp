@@ -93,8 +93,9 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = "batched chains draw the Polya-urn Phi (phi_mode must be 0)";
         return bail(PULDA_ERR_INVALID);
     }
-    if (o.warps_per_block < 0 || o.warps_per_block > 8) {
-        b->err = "warps_per_block must be in [0, 8] (got " + std::to_string(o.warps_per_block) + ")";
+    if (o.warps_per_block < 0 || o.warps_per_block > kMultiWarps) {
+        b->err = "warps_per_block must be in [0, " + std::to_string(kMultiWarps) + "] (got " +
+                 std::to_string(o.warps_per_block) + ")";
         return bail(PULDA_ERR_INVALID);
     }
     if (o.stream) {
@@ -204,7 +205,7 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     bl.kmax = kmax;
     bl.phi_grid = b->sms * batch_phi_blocks_per_sm(kmax);
     for (int w : {2, 4, 8})
-        if (z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back(w);
+        if (w <= kMultiWarps && z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back(w);
     if (b->cand.empty()) b->cand.push_back(1);
     if (o.warps_per_block > 0) {
         b->cand.assign(1, o.warps_per_block);

@@ -906,7 +906,7 @@ __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs
 
 // Many chains: the work list holds (chain, document) pairs, longest first
 // across all chains; shared memory per warp is sized for the largest K.
-__global__ void __launch_bounds__(256, 3) k_z_step_multi(const ZArgs *chains, const int2 *items,
+__global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_multi(const ZArgs *chains, const int2 *items,
                                                                         int n_items, int *work, int kmax) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;

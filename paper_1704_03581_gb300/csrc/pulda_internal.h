@@ -29,6 +29,16 @@ constexpr int kMaxKBitmap = 1024;
 #define PULDA_ZWARPS 4
 #endif
 constexpr int kZWarps = PULDA_ZWARPS;
+// The batched (many-chain) z-step: the largest CTA in warps (its tuning
+// candidates are the powers of two up to it) and the CTAs per SM its launch
+// bounds ask for.
+#ifndef PULDA_MULTI_WARPS
+#define PULDA_MULTI_WARPS 8
+#endif
+#ifndef PULDA_MULTI_MINB
+#define PULDA_MULTI_MINB 3
+#endif
+constexpr int kMultiWarps = PULDA_MULTI_WARPS;
 // Words with tokens, most frequent first, also keep their fixed-point
 // weights q as dense K-entry rows, up to this many bytes (K <= kMaxKBitmap):
 // the z-step's document side reads q at topic k there.  A word without a row
