@@ -63,3 +63,24 @@ def test_init_rejects_bad_arguments_without_a_gpu():
         assert "decrease" in str(e)
     else:
         raise AssertionError("accepted decreasing offsets")
+
+
+def test_batch_rejects_bad_options_without_a_gpu():
+    """The batched form draws the Polya-urn Phi only and caps its CTA at the batched kernel's
+    size; both are checked before any device work."""
+    import ctypes
+    import numpy as np
+    w = np.array([0, 1], np.int32)
+    off = np.array([0, 2], np.int64)
+    a = np.full(3, 0.1, np.float32)
+    arr = (P.ChainDesc * 1)()
+    arr[0] = P.ChainDesc(P._ptr(w), P._ptr(off), 1, 3, 2, P._ptr(a), 0.01, 0)
+    for field, value, frag in [("phi_mode", 1, b"phi_mode"), ("warps_per_block", 9, b"warps_per_block"),
+                               ("docs_per_warp", 4, b"docs_per_warp")]:
+        opt = P.Options()
+        setattr(opt, field, value)
+        b = ctypes.c_void_p()
+        st = P.lib().pulda_batch_init(ctypes.byref(b), arr, 1, ctypes.byref(opt))
+        assert st == -1 and not b.value
+        assert frag in P.lib().pulda_batch_last_error(None), P.lib().pulda_batch_last_error(None)
+

@@ -51,3 +51,18 @@ def test_reference_arm_non_zero_rank_exits_without_work():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_launch_count_and_profile_record_follow_the_source(tmp_path, monkeypatch):
+    """Library kernels per sweep depend on the Phi mode and on a word above 2^17 tokens; the ncu
+    record is used only while the kernel source hashes to the value it was taken on."""
+    import numpy as np
+    import bench
+    assert bench.kernels_per_sweep(np.zeros(10, np.int32), 0) == 5
+    assert bench.kernels_per_sweep(np.zeros(1 << 18, np.int32), 0) == 6
+    assert bench.kernels_per_sweep(np.arange(10, dtype=np.int32), 1) == 8
+    rec = bench.recorded_profile()
+    if rec:
+        assert rec["kernels_cu_sha"] == bench.kernel_source_hash()
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
+    assert bench.recorded_profile() == {} and bench.recorded_traffic() is None

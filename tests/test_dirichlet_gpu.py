@@ -79,3 +79,27 @@ def test_dirichlet_fold_in_matches_oracle():
     zo = O.infer(ch.tables, w2, off2, 3, 17)
     assert np.array_equal(z, zo)
     s.close()
+
+
+def test_dirichlet_serving():
+    """Against a Dirichlet Phi, the server's results equal pulda_infer on each document alone."""
+    import time
+    c = synth.tiny()
+    s = P.Sampler(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=8, phi_mode=1).sweep(2)
+    rng = np.random.default_rng(12)
+    reqs = [dict(id=i, seed=int(rng.integers(1, 2 ** 62)), words=rng.integers(0, c.V, int(L)).astype(np.int32),
+                 sweeps=int(rng.integers(1, 6))) for i, L in enumerate(rng.choice([1, 33, 300, 1000], size=12))]
+    srv = P.Server(s, token_budget=4000, max_slots=8, slice_tokens=64)
+    for r in reqs:
+        srv.submit(r["id"], r["seed"], r["words"], r["sweeps"])
+    got, t0 = {}, time.time()
+    while len(got) < len(reqs):
+        for res in srv.poll(timeout_ms=200):
+            assert res["status"] == 0
+            got[res["req_id"]] = res["z"]
+        assert time.time() - t0 < 120, "server made no progress"
+    srv.close()
+    for r in reqs:
+        alone = s.infer(r["words"], np.array([0, len(r["words"])]), r["sweeps"], seed=r["seed"])
+        assert np.array_equal(got[r["id"]], alone)
+    s.close()

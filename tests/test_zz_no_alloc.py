@@ -61,3 +61,21 @@ def test_noalloc_checks_inputs_on_the_device(chain):
     with pytest.raises(P.PuldaError) as e:
         P.pulda_infer_noalloc(s.h, w, off, 1, 0, z)
     assert "word id" in str(e.value)
+
+
+def test_noalloc_matches_infer_against_a_dirichlet_phi():
+    """The same equality when the handle draws Algorithm 1's Dirichlet Phi."""
+    import torch
+    import paper_1704_03581_gb300 as P
+    from paper_1704_03581_gb300 import synth
+    c = synth.tiny()
+    s = P.Sampler(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=12, phi_mode=1).sweep(2)
+    new = c.slice_docs(100, 400)
+    z_ref = s.infer(new.w, new.doc_off, 5, seed=9)
+    w_dev = torch.from_numpy(new.w).cuda()
+    off_dev = torch.from_numpy(new.doc_off).cuda()
+    z_dev = torch.full((new.N,), -1, dtype=torch.int16, device="cuda")
+    torch.cuda.synchronize()
+    P.pulda_infer_noalloc(s.h, w_dev, off_dev, 5, 9, z_dev)
+    assert np.array_equal(z_dev.cpu().numpy(), z_ref)
+    s.close()
