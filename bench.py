@@ -18,6 +18,7 @@ host cores instead (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import csv
 import hashlib
 import io
@@ -325,18 +326,22 @@ def run_pulda(args, corpus, rank: int, world: int):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
-                       stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp,
-                  phi_mode=args.phi_mode)
-        s2.sweep(K)
-        zh = s2.z()   # e2e covers sweeps 1..K from the uniform start
+                       stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp, phi_mode=args.phi_mode)
+        stats_bytes = ctypes.sizeof(P.SweepStats)
+        for _ in range(K):
+            s2.sweep(1)
+            s2.stats()      # the sweep's counters read back to the host (its result)
+        zh = s2.z()         # e2e covers sweeps 1..K from the uniform start
         dt = time.perf_counter() - t0
         s2.close()
         h2d = corpus.w.nbytes + corpus.doc_off.nbytes + 4 * K_TOPICS
-        d2h = zh.nbytes
+        d2h = zh.nbytes + K * stats_bytes
         dt_max = reduce_max(dt, world)
         e2e = {"value": aggregate_tokens_per_s(corpus.N, K, world, 1000.0 * dt_max), "unit": "tokens/s",
                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
-               "note": "pulda_init from host buffers + K sweeps + pulda_get_z to host, host clock"}
+               "note": "pulda_init from host buffers (the corpus crosses once: every sweep reads it on the "
+                       "device), then per sweep the sweep and a read of its counters to the host, then the "
+                       "topics to the host; host clock"}
 
     if rank != 0:
         return
