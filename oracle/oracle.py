@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
             "or_phi_draw": (i32, [P, P, i32, i32, u64, u32, P, P, P]),
             "or_word_tables": (None, [P, P, P, i32, i32, P, P, P, P, P, P, P]),
             "or_z_step": (i32, [P, i64, P, P, i32, i32, P, P, P, P, P, P, u64, u32, i64, P]),
+            "or_z_step_sliced": (i32, [P, i64, P, P, i32, i32, P, P, P, P, P, P, u64, u32, i64, i64, P]),
             "or_log_posterior": (i32, [P, i64, P, P, i32, i32, P, f64, P]),
             "or_logf": (f32, [f32]),
             "or_expf": (f32, [f32]),
@@ -288,15 +289,17 @@ class WordTables:
 
 
 def z_step(doc_off: np.ndarray, w: np.ndarray, z: np.ndarray, tables: WordTables, seed: int, sweep: int,
-           index_base: int = 0) -> tuple[np.ndarray, np.ndarray]:
-    """One z-step; returns (new z, stats[tokens, a_branch, sum_min, zero_mass, sum_inter, docside])."""
+           index_base: int = 0, slice_len: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """One z-step; returns (new z, stats[tokens, a_branch, sum_min, zero_mass, sum_inter, docside]).
+    slice_len > 0 splits longer documents into concurrent slices with stale counts (not Algorithm 2)."""
     z = np.array(z, dtype=np.int16, copy=True)
     doc_off = np.ascontiguousarray(doc_off, dtype=np.int64)
     w = np.ascontiguousarray(w, dtype=np.int32)
     stats = np.zeros(6, dtype=np.int64)
     t = tables
-    rc = lib().or_z_step(_p(doc_off), doc_off.shape[0] - 1, _p(w), _p(z), t.K, t.V, _p(t.ncol), _p(t.topic),
-                         _p(t.q), _p(t.A), _p(t.athr), _p(t.atopic), seed, sweep, index_base, _p(stats))
+    rc = lib().or_z_step_sliced(_p(doc_off), doc_off.shape[0] - 1, _p(w), _p(z), t.K, t.V, _p(t.ncol), _p(t.topic),
+                                _p(t.q), _p(t.A), _p(t.athr), _p(t.atopic), seed, sweep, index_base, slice_len,
+                                _p(stats))
     if rc != 0:
         raise RuntimeError("z-step failed")
     return z, stats
@@ -311,7 +314,7 @@ class Chain:
     """
 
     def __init__(self, w, doc_off, K: int, V: int, alpha, beta: float, seed: int, z=None, sweep: int = 0,
-                 dirichlet: bool = False):
+                 dirichlet: bool = False, slice_len: int = 0):
         self.w = np.ascontiguousarray(w, dtype=np.int32)
         self.doc_off = np.ascontiguousarray(doc_off, dtype=np.int64)
         self.K, self.V, self.seed = K, V, int(seed)
@@ -326,6 +329,7 @@ class Chain:
         self.stats = np.zeros(6, dtype=np.int64)
         self.dead_rows = 0
         self.dirichlet = dirichlet      # Algorithm 1's Dirichlet Phi instead of the Polya urn
+        self.slice_len = slice_len      # > 0: long documents in concurrent slices with stale counts
 
     def phi_step(self, sweep: int):
         n = count_n(self.w, self.z, self.K, self.V)
@@ -340,7 +344,8 @@ class Chain:
         for _ in range(n_sweeps):
             self.sweep_index += 1
             self.phi_step(self.sweep_index)
-            self.z, self.stats = z_step(self.doc_off, self.w, self.z, self.tables, self.seed, self.sweep_index)
+            self.z, self.stats = z_step(self.doc_off, self.w, self.z, self.tables, self.seed, self.sweep_index,
+                                        slice_len=self.slice_len)
         return self
 
     def n(self) -> np.ndarray:

@@ -479,63 +479,99 @@ void or_word_tables(const uint32_t *c_vk, const int64_t *S, const float *alpha, 
 /* |J| (topics nonzero in both m^{-i} and the column), stats[5] += tokens    */
 /* with K_d < K_v.                                                           */
 /* ------------------------------------------------------------------------ */
+/* One token's step (Algorithm 2, second bullet): remove token i from the
+ * document counts m (K_d = *kd nonzero entries), draw its topic from
+ * p(k) proportional to phi_{k,v}(alpha_k + m^{-i}_k) in the exact integer
+ * form of "Efficient sampling of z", add it back.  Returns the new topic, or
+ * -1 if the search ran past the total (which cannot happen). */
+static int32_t z_token(int64_t i, int32_t v, int32_t kold, int64_t *m, int64_t *kd, int32_t K,
+                       const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
+                       const uint32_t *athr, const int16_t *atopic,
+                       uint64_t seed, uint32_t sweep, int64_t index_base, int64_t *stats)
+{
+    if (--m[kold] == 0) (*kd)--;           /* m^{-i}: remove token i */
+    int64_t base = (int64_t)v * K;
+    int32_t nv = ncol[v];
+    /* sigma_b = sum_k q_{k,v} m^{-i}_{d,k}; every term is exact */
+    uint64_t B = 0;
+    for (int32_t j = 0; j < nv; j++) {
+        B += (uint64_t)q[base + j] * (uint64_t)m[topic[base + j]];
+        if (m[topic[base + j]] > 0) stats[4]++;
+    }
+    if (*kd < nv) stats[5]++;
+    uint64_t T = A[v] + (B << OR_FRAC_BITS);
+    int32_t knew = kold;
+    uint64_t t = (uint64_t)(index_base + i);
+    uint32_t x[4];
+    draw4(seed, (uint32_t)t, (uint32_t)(t >> 32), sweep, OR_TAG_Z, 0, x);
+    if (T == 0) {
+        stats[3]++;
+    } else {
+        uint64_t U = ((uint64_t)x[0] << 32) | x[1];
+        uint64_t r = (uint64_t)(((unsigned __int128)U * T) >> 64);   /* u (sigma_a + sigma_b) */
+        if (r < A[v]) {
+            uint32_t s = scale32(x[2], (uint32_t)nv);
+            knew = x[3] < athr[base + s] ? topic[base + s] : atopic[base + s];
+            stats[1]++;
+        } else {
+            uint64_t rb = (r - A[v]) >> OR_FRAC_BITS;
+            uint64_t C = 0;
+            knew = -1;
+            for (int32_t j = 0; j < nv; j++) {
+                C += (uint64_t)q[base + j] * (uint64_t)m[topic[base + j]];
+                if (rb < C) { knew = topic[base + j]; break; }
+            }
+            if (knew < 0) return -1;           /* cannot happen: rb < B */
+        }
+    }
+    stats[0]++;
+    stats[2] += *kd < nv ? *kd : nv;
+    if (m[knew]++ == 0) (*kd)++;
+    return knew;
+}
+
 int32_t or_z_step(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *z, int32_t K, int32_t V,
                   const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
                   const uint32_t *athr, const int16_t *atopic,
                   uint64_t seed, uint32_t sweep, int64_t index_base, int64_t *stats)
 {
+    return or_z_step_sliced(doc_off, D, w, z, K, V, ncol, topic, q, A, athr, atopic, seed, sweep, index_base, 0, stats);
+}
+
+/* The z-step with long documents split into concurrent slices (a different
+ * sampler from Algorithm 2, outside the paper: within a document, AD-LDA's
+ * stale counts).  A document longer than slice_len tokens is cut into slices
+ * of slice_len tokens; each slice starts from m0, the document's counts at the
+ * start of the pass, and updates only its own copy, in position order.  With
+ * slice_len = 0, or no document longer than it, this is Algorithm 2 exactly. */
+int32_t or_z_step_sliced(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *z, int32_t K, int32_t V,
+                         const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
+                         const uint32_t *athr, const int16_t *atopic,
+                         uint64_t seed, uint32_t sweep, int64_t index_base, int64_t slice_len, int64_t *stats)
+{
     (void)V;
+    int64_t *m0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
     int64_t *m = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
     for (int64_t d = 0; d < D; d++) {
-        memset(m, 0, sizeof(int64_t) * (size_t)K);
-        int64_t kd = 0;                    /* number of nonzero m_{d,k} */
-        for (int64_t i = doc_off[d]; i < doc_off[d + 1]; i++) {
-            if (m[z[i]]++ == 0) kd++;
-        }
-        for (int64_t i = doc_off[d]; i < doc_off[d + 1]; i++) {
-            int32_t v = w[i];
-            int32_t kold = z[i];
-            if (--m[kold] == 0) kd--;      /* m^{-i}: remove token i */
-            int64_t base = (int64_t)v * K;
-            int32_t nv = ncol[v];
-            /* sigma_b = sum_k q_{k,v} m^{-i}_{d,k}; every term is exact */
-            uint64_t B = 0;
-            for (int32_t j = 0; j < nv; j++) {
-                B += (uint64_t)q[base + j] * (uint64_t)m[topic[base + j]];
-                if (m[topic[base + j]] > 0) stats[4]++;
+        memset(m0, 0, sizeof(int64_t) * (size_t)K);
+        int64_t kd0 = 0;                    /* number of nonzero m_{d,k} */
+        for (int64_t i = doc_off[d]; i < doc_off[d + 1]; i++)
+            if (m0[z[i]]++ == 0) kd0++;
+        int64_t len = doc_off[d + 1] - doc_off[d];
+        int64_t step = (slice_len > 0 && len > slice_len) ? slice_len : len;
+        for (int64_t a = doc_off[d]; a < doc_off[d + 1]; a += step) {
+            memcpy(m, m0, sizeof(int64_t) * (size_t)K);
+            int64_t kd = kd0;
+            int64_t b = a + step < doc_off[d + 1] ? a + step : doc_off[d + 1];
+            for (int64_t i = a; i < b; i++) {
+                int32_t knew = z_token(i, w[i], z[i], m, &kd, K, ncol, topic, q, A, athr, atopic,
+                                       seed, sweep, index_base, stats);
+                if (knew < 0) { free(m0); free(m); return -1; }
+                z[i] = (int16_t)knew;
             }
-            if (kd < nv) stats[5]++;
-            uint64_t T = A[v] + (B << OR_FRAC_BITS);
-            int32_t knew = kold;
-            uint64_t t = (uint64_t)(index_base + i);
-            uint32_t x[4];
-            draw4(seed, (uint32_t)t, (uint32_t)(t >> 32), sweep, OR_TAG_Z, 0, x);
-            if (T == 0) {
-                stats[3]++;
-            } else {
-                uint64_t U = ((uint64_t)x[0] << 32) | x[1];
-                uint64_t r = (uint64_t)(((unsigned __int128)U * T) >> 64);   /* u (sigma_a + sigma_b) */
-                if (r < A[v]) {
-                    uint32_t s = scale32(x[2], (uint32_t)nv);
-                    knew = x[3] < athr[base + s] ? topic[base + s] : atopic[base + s];
-                    stats[1]++;
-                } else {
-                    uint64_t rb = (r - A[v]) >> OR_FRAC_BITS;
-                    uint64_t C = 0;
-                    knew = -1;
-                    for (int32_t j = 0; j < nv; j++) {
-                        C += (uint64_t)q[base + j] * (uint64_t)m[topic[base + j]];
-                        if (rb < C) { knew = topic[base + j]; break; }
-                    }
-                    if (knew < 0) { free(m); return -1; }   /* cannot happen: rb < B */
-                }
-            }
-            stats[0]++;
-            stats[2] += kd < nv ? kd : nv;
-            if (m[knew]++ == 0) kd++;
-            z[i] = (int16_t)knew;
         }
     }
+    free(m0);
     free(m);
     return 0;
 }

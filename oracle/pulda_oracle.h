@@ -49,6 +49,10 @@ int32_t or_z_step(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *
                   const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
                   const uint32_t *athr, const int16_t *atopic,
                   uint64_t seed, uint32_t sweep, int64_t index_base, int64_t *stats);
+int32_t or_z_step_sliced(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *z, int32_t K, int32_t V,
+                         const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
+                         const uint32_t *athr, const int16_t *atopic,
+                         uint64_t seed, uint32_t sweep, int64_t index_base, int64_t slice_len, int64_t *stats);
 int32_t or_log_posterior(const int64_t *doc_off, int64_t D, const int32_t *w, const int16_t *z,
                          int32_t K, int32_t V, const float *alpha, double beta, double out[3]);
 float or_logf(float x);

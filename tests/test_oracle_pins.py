@@ -568,3 +568,50 @@ def test_dirichlet_chain_invariants():
     assert ch.z.min() >= 0 and ch.z.max() < 7
     assert ch.m().sum(axis=1).tolist() == lengths.tolist()
     assert ch.n().sum() == off[-1]
+
+
+# ------------------------------------------------- stale-count slices (outside the paper)
+# Long documents cut into slices that start from the pass-start counts m0 and
+# update only their own copy.  Pinned to Algorithm 2 (one slice per document)
+# and to the stale conditional p(k) ~ phi_{k,v}(alpha_k + m0_k - [k = z_i]).
+
+def test_sliced_z_step_with_whole_documents_is_algorithm_2():
+    rng = np.random.default_rng(31)
+    K, V = 7, 30
+    c = (rng.poisson(0.6, size=(V, K)) * rng.integers(1, 200, size=(V, K))).astype(np.uint32)
+    S = np.maximum(c.sum(axis=0).astype(np.int64), 1)
+    t = O.WordTables(c, S, rng.uniform(0.05, 1.0, K).astype(np.float32))
+    lengths = rng.integers(0, 60, size=25)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    w = rng.integers(0, V, int(off[-1])).astype(np.int32)
+    z = rng.integers(0, K, int(off[-1])).astype(np.int16)
+    exact = O.z_step(off, w, z, t, 5, 3)
+    for L in (0, int(lengths.max()), 10 ** 6):
+        got = O.z_step(off, w, z, t, 5, 3, slice_len=L)
+        assert np.array_equal(got[0], exact[0]) and np.array_equal(got[1], exact[1])
+    # shorter slices change the chain but keep every count consistent
+    got = O.z_step(off, w, z, t, 5, 3, slice_len=7)
+    assert got[1][0] == off[-1] and got[0].min() >= 0 and got[0].max() < K
+
+
+def test_sliced_z_step_uses_the_pass_start_counts():
+    """One-token slices: token 5 of a six-token document draws from phi(alpha + m0 - e_{z_5}) whatever
+    tokens 0-4 draw.  Phi strongly prefers topic 1 while every token starts in topic 0, so the
+    exact sampler (which sees tokens 0-4 move) gives a clearly different law."""
+    K = 2
+    phi = np.array([[0.1], [0.9]])
+    alpha = np.array([0.5, 0.5], np.float32)
+    t, phi_x = _tables_from_phi(phi, alpha)
+    w = np.zeros(6, np.int32)
+    z0 = np.zeros(6, np.int16)
+    off = np.array([0, 6], np.int64)
+    m0 = np.array([5.0, 0.0])                       # pass-start counts without token 5
+    p = phi_x[:, 0] * (alpha.astype(np.float64) + m0)
+    p /= p.sum()
+    n = 20000
+    sliced = np.array([O.z_step(off, w, z0, t, 7, s, slice_len=1)[0][5] for s in range(1, n + 1)])
+    obs = np.bincount(sliced, minlength=K)
+    chi = ((obs - p * n) ** 2 / (p * n)).sum()
+    assert stats.chi2.sf(chi, K - 1) > 1e-4
+    exact = np.array([O.z_step(off, w, z0, t, 7, s)[0][5] for s in range(1, n + 1)])
+    assert abs(np.mean(exact == 1) - p[1]) > 0.1     # the exact law is far from the stale one
