@@ -76,6 +76,8 @@ def parse():
                     help="sweep: the large corpus (the headline line); batched: 32 uneven chains in one graph "
                          "launch per sweep against 32 sequential single-chain runs; trace: the log posterior "
                          "after every sweep, Polya urn against Dirichlet Phi, on the same corpus and seed")
+    ap.add_argument("--slice-len", type=int, default=0,
+                    help="sweep/trace forms: documents longer than this in stale-count slices (0 = Algorithm 2)")
     ap.add_argument("--trace-corpus", choices=["small", "large"], default="small")
     ap.add_argument("--trace-sweeps", type=int, default=100)
     ap.add_argument("--batch-scale", type=float, default=0.25,
@@ -275,7 +277,7 @@ def run_pulda(args, corpus, rank: int, world: int):
     torch.cuda.set_stream(stream)
     s = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                   stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp,
-                  phi_mode=args.phi_mode)
+                  phi_mode=args.phi_mode, slice_len=args.slice_len)
     s.sweep(args.burnin + args.warmup)
     s.sync()
     lp_before = s.log_posterior()[0]          # the diagnostic, outside the timed region
@@ -326,7 +328,8 @@ def run_pulda(args, corpus, rank: int, world: int):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
-                       stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp, phi_mode=args.phi_mode)
+                       stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp, phi_mode=args.phi_mode,
+                       slice_len=args.slice_len)
         stats_bytes = ctypes.sizeof(P.SweepStats)
         for _ in range(K):
             s2.sweep(1)
@@ -372,7 +375,9 @@ def run_pulda(args, corpus, rank: int, world: int):
                    "alpha": ALPHA, "beta": BETA, "parallelism": f"{world} independent chains (replicas)",
                    "l2": "inputs larger than L2 (word ids 396 MB + topics 198 MB read every sweep)",
                    "timed_sweeps": [first_timed, first_timed + K - 1],
-                   "phi": "Dirichlet (Algorithm 1)" if args.phi_mode == 1 else "Poisson Polya urn (Algorithm 2)"},
+                   "phi": "Dirichlet (Algorithm 1)" if args.phi_mode == 1 else "Poisson Polya urn (Algorithm 2)",
+                   "z": (f"documents over {args.slice_len} tokens in stale-count slices (not the paper's sampler)"
+                         if args.slice_len > 0 else "every document in order (Algorithm 2)")},
         "z_step": {"tokens_per_s": K * corpus.N / (z_ms / 1000.0), "ms_per_launch": z_ms / K,
                    "mean_min_kd_kv": sum_min / tokens, "mean_intersection": sum_int / tokens,
                    "docside_frac": docside / tokens, "a_branch_frac": a_br / tokens},
@@ -410,9 +415,13 @@ def run_trace(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     out = {}
-    for mode, name in ((0, "polya_urn"), (1, "dirichlet")):
+    if args.slice_len > 0:      # Algorithm 2 against its stale-count slices
+        runs = ((0, 0, "algorithm_2"), (0, args.slice_len, "slices"))
+    else:                       # the Polya urn against Algorithm 1's Dirichlet Phi
+        runs = ((0, 0, "polya_urn"), (1, 0, "dirichlet"))
+    for mode, sl, name in runs:
         s = P.Sampler(corpus.w, corpus.doc_off, K, corpus.V, ALPHA, BETA, seed=0, stream=stream.cuda_stream,
-                      phi_mode=mode)
+                      phi_mode=mode, slice_len=sl)
         lp, phi_ms, z_ms, nnz = [float(s.log_posterior()[0])], [], [], []
         for _ in range(args.trace_sweeps):
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -429,19 +438,22 @@ def run_trace(args):
         tail = max(1, args.trace_sweeps // 5)
         out[name] = {"log_posterior": lp, "phi_ms": float(np.median(phi_ms)), "z_ms": float(np.median(z_ms)),
                      "nnz_phi_last": int(nnz[-1]), "mean_last_fifth": float(np.mean(lp[-tail:]))}
-    a, b = out["polya_urn"], out["dirichlet"]
+    na, nb = runs[0][2], runs[1][2]
+    a, b = out[na], out[nb]
     line = {
-        "metric": "log-posterior trace per sweep: Polya urn (Algorithm 2) vs Dirichlet (Algorithm 1)",
+        "metric": ("log-posterior trace per sweep: Algorithm 2 vs stale-count slices of "
+                   f"{args.slice_len} tokens" if args.slice_len > 0 else
+                   "log-posterior trace per sweep: Polya urn (Algorithm 2) vs Dirichlet (Algorithm 1)"),
         "value": (a["mean_last_fifth"] - b["mean_last_fifth"]) / abs(b["mean_last_fifth"]),
         "unit": "relative difference of the mean log posterior over the last fifth of the sweeps",
         "n_gpus": 1, "steps": args.trace_sweeps, "higher_is_better": False, "dtype": "int64",
         "data": "synthetic (LDA generative process)",
         "config": {"workload": corpus.name, "D": corpus.D, "V": corpus.V, "N": corpus.N, "K": K,
                    "alpha": ALPHA, "beta": BETA, "seed": 0},
-        "phi_step_ms": {"polya_urn": a["phi_ms"], "dirichlet": b["phi_ms"], "ratio": b["phi_ms"] / a["phi_ms"]},
-        "z_step_ms": {"polya_urn": a["z_ms"], "dirichlet": b["z_ms"], "ratio": b["z_ms"] / a["z_ms"]},
-        "nnz_phi_last": {"polya_urn": a["nnz_phi_last"], "dirichlet": b["nnz_phi_last"]},
-        "traces": {"polya_urn": a["log_posterior"], "dirichlet": b["log_posterior"]},
+        "phi_step_ms": {na: a["phi_ms"], nb: b["phi_ms"], "ratio": b["phi_ms"] / a["phi_ms"]},
+        "z_step_ms": {na: a["z_ms"], nb: b["z_ms"], "ratio": b["z_ms"] / a["z_ms"]},
+        "nnz_phi_last": {na: a["nnz_phi_last"], nb: b["nnz_phi_last"]},
+        "traces": {na: a["log_posterior"], nb: b["log_posterior"]},
     }
     print(json.dumps(line), flush=True)
 

@@ -63,7 +63,15 @@ typedef struct {
     int32_t phi_mode;       /* 0 = Poisson Polya urn (Algorithm 2), 1 = Dirichlet (Algorithm 1:
                                phi_k ~ Dir(n_k + beta) through Gamma draws, entries below 2^-24
                                of their column's maximum dropped); the batched form takes 0 only */
-    int32_t reserved[4];
+    int32_t slice_len;      /* 0 = every document's tokens in order (Algorithm 2).  > 0: in the
+                               corpus z-step (pulda_z_step, pulda_sweep) a document longer than
+                               this is cut into slices of this many tokens, resampled
+                               concurrently, each from the document's counts at the start of
+                               the pass updated by its own tokens only -- stale counts across
+                               slices, a different sampler from the paper's (AD-LDA's
+                               approximation within a document).  Needs docs_per_warp 0 or 1;
+                               fold-in, serving and the batched form ignore/reject it */
+    int32_t reserved[3];
 } pulda_options;
 
 /* Counters of the most recent z-step (and Phi-step), and running totals. */

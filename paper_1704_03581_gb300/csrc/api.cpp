@@ -242,6 +242,10 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
         fail(h, PULDA_ERR_INVALID, "docs_per_warp must be 0 (auto), 1 or 4");
         return reject(PULDA_ERR_INVALID);
     }
+    if (h->opt.slice_len < 0 || (h->opt.slice_len > 0 && h->opt.docs_per_warp == 4)) {
+        fail(h, PULDA_ERR_INVALID, "slice_len must be >= 0, and slices need docs_per_warp 0 or 1");
+        return reject(PULDA_ERR_INVALID);
+    }
     if (h->opt.docs_per_warp == 4 && K > kMaxKBitmap) {
         fail(h, PULDA_ERR_INVALID, "docs_per_warp = 4 needs K <= 1024");
         return reject(PULDA_ERR_INVALID);
@@ -285,6 +289,40 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     CUI(cudaMemcpyAsync(h->doc_off, D > 0 ? doc_offsets : off0.data(), sizeof(int64_t) * (D + 1), cudaMemcpyHostToDevice, st));
     std::vector<int32_t> dord = length_order(doc_offsets, D);
     CUI(cudaMemcpyAsync(h->doc_order, dord.data(), sizeof(int32_t) * D, cudaMemcpyHostToDevice, st));
+    if (h->opt.slice_len > 0) {
+        // documents longer than slice_len become slices {document, row, first token, tokens}
+        const int64_t S = h->opt.slice_len;
+        std::vector<int32_t> sdocs, shortd;
+        std::vector<int4> items;
+        for (int32_t d : dord) {
+            const int64_t len = doc_offsets[d + 1] - doc_offsets[d];
+            if (len > S) {
+                const int row = static_cast<int>(sdocs.size());
+                sdocs.push_back(d);
+                for (int64_t a0 = 0; a0 < len; a0 += S)
+                    items.push_back(make_int4(d, row, static_cast<int>(a0), static_cast<int>(std::min(S, len - a0))));
+            } else {
+                shortd.push_back(d);
+            }
+        }
+        std::stable_sort(items.begin(), items.end(), [](const int4 &x, const int4 &y) { return x.w > y.w; });
+        if (!sdocs.empty()) {
+            ALLOC(h->sliced_docs, sdocs.size());
+            ALLOC(h->slices, items.size());
+            ALLOC(h->m0, sdocs.size() * static_cast<size_t>(K));
+            CUI(cudaMemcpyAsync(h->sliced_docs, sdocs.data(), sizeof(int32_t) * sdocs.size(), cudaMemcpyHostToDevice, st));
+            CUI(cudaMemcpyAsync(h->slices, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, st));
+            if (!shortd.empty()) {
+                ALLOC(h->doc_order_short, shortd.size());
+                CUI(cudaMemcpyAsync(h->doc_order_short, shortd.data(), sizeof(int32_t) * shortd.size(),
+                                    cudaMemcpyHostToDevice, st));
+            }
+            CUI(cudaStreamSynchronize(st));
+            h->n_sliced = static_cast<int>(sdocs.size());
+            h->n_slices = static_cast<int>(items.size());
+            h->D_short = static_cast<int64_t>(shortd.size());
+        }
+    }
     CUI(cudaMemcpyAsync(h->alpha, alpha, sizeof(float) * K, cudaMemcpyHostToDevice, st));
     CUI(cudaMemcpyAsync(h->t_thr, tab.thr.data(), sizeof(uint32_t) * tab.thr.size(), cudaMemcpyHostToDevice, st));
     CUI(cudaMemcpyAsync(h->t_alias, tab.alias.data(), sizeof(uint16_t) * tab.alias.size(), cudaMemcpyHostToDevice, st));
@@ -404,6 +442,20 @@ pulda_status pulda_z_step(pulda_handle *h) {
     if (!h) return PULDA_ERR_INVALID;
     if (!h->have_phi) return fail(h, PULDA_ERR_INVALID, "no Phi drawn yet: call pulda_phi_step or pulda_sweep first");
     CU(h, clear_z_counters(h));
+    if (h->n_slices > 0) {
+        // long documents in stale-count slices: their pass-start counts, then
+        // one launch over the slices and the other documents
+        CU(h, cudaMemsetAsync(h->work + 1, 0, 2 * sizeof(int), h->stream));
+        launch_slice_counts(h->doc_off, h->sliced_docs, h->n_sliced, h->z, h->K, h->m0, h->stream);
+        ZArgs a = z_args(h, h->doc_off, h->doc_order_short, h->D_short, h->w, h->z, h->seed,
+                         static_cast<uint32_t>(h->sweep), 0);
+        a.slices = h->slices;
+        a.n_slices = h->n_slices;
+        a.m0 = h->m0;
+        launch_z_step(a, h->z_warps, h->z_grid, h->stream);
+        CU(h, cudaGetLastError());
+        return PULDA_OK;
+    }
     return run_z(h, h->doc_off, h->doc_order, h->D, h->n_long, h->w, h->z, h->seed, static_cast<uint32_t>(h->sweep), 0);
 }
 

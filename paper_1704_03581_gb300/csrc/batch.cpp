@@ -93,6 +93,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = "batched chains draw the Polya-urn Phi (phi_mode must be 0)";
         return bail(PULDA_ERR_INVALID);
     }
+    if (o.slice_len != 0) {
+        b->err = "batched chains resample every document in order (slice_len must be 0)";
+        return bail(PULDA_ERR_INVALID);
+    }
     if (o.warps_per_block < 0 || o.warps_per_block > kMultiWarps) {
         b->err = "warps_per_block must be in [0, " + std::to_string(kMultiWarps) + "] (got " +
                  std::to_string(o.warps_per_block) + ")";

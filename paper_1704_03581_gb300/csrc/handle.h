@@ -38,6 +38,12 @@ struct pulda_handle {
     uint16_t *nst_k = nullptr; uint32_t *nst_n = nullptr; int32_t *nnz_n = nullptr;
     uint16_t *cst_k = nullptr; uint32_t *cst_c = nullptr; int32_t *nnz_c = nullptr;
     unsigned long long *S = nullptr; uint32_t *rowbuf = nullptr; int64_t *col_ptr = nullptr;
+    // stale-count slices (slice_len > 0): the documents longer than it, their
+    // slices, their pass-start counts, and the order of the other documents
+    int32_t *sliced_docs = nullptr; int n_sliced = 0;
+    int4 *slices = nullptr; int n_slices = 0;
+    uint32_t *m0 = nullptr;
+    int32_t *doc_order_short = nullptr; int64_t D_short = 0;
     // dense q rows of the most frequent words (z-step document side)
     uint32_t *qdense = nullptr; int32_t *dense_slot = nullptr; int n_dense = 0;
     // Dirichlet Phi (Algorithm 1), allocated in that mode only

@@ -646,14 +646,21 @@ struct DocRun {
 // current topics first: with positions < pos already resampled in this pass
 // that is exactly m of the sequential sampler at `pos`.  Returns the run's
 // final (sweep, pos) through r.
-__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st) {
+// With m0 set, m starts from those K counts (a slice of a longer document,
+// from the document's counts at the start of the pass) instead of the run's
+// own topics.
+__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, const uint32_t *m0 = nullptr) {
     const int lane = threadIdx.x & 31;
     const int K = a.K;
     const bool use_bm = a.bitmap != nullptr && a.path != 1;
     if (r.len == 0 || r.budget <= 0) return;
-    for (int k = lane; k < K; k += 32) m[mi(k)] = 0;
-    __syncwarp();
-    for (int i = lane; i < r.len; i += 32) atomicAdd(&m[mi(r.z[i])], 1u);
+    if (m0) {
+        for (int k = lane; k < K; k += 32) m[mi(k)] = m0[k];
+    } else {
+        for (int k = lane; k < K; k += 32) m[mi(k)] = 0;
+        __syncwarp();
+        for (int i = lane; i < r.len; i += 32) atomicAdd(&m[mi(r.z[i])], 1u);
+    }
     __syncwarp();
     uint32_t mbits = 0;
     int kd = 0;
@@ -894,14 +901,41 @@ __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs
         int item = 0;
         if (lane == 0) item = atomicAdd(a.work, 1);
         item = __shfl_sync(0xFFFFFFFFu, item, 0);
-        if (item >= a.D) break;
-        const int d = a.doc_order[item];
-        const int64_t s = a.doc_off[d];
-        DocRun r{a.w + s, a.z + s, static_cast<int>(a.doc_off[d + 1] - s), a.seed, a.index_base + s, sweep, 0,
-                 a.doc_off[d + 1] - s, 1};
-        z_doc_warp(a, m, r, st);
+        if (item >= a.n_slices + a.D) break;
+        int64_t s;
+        int len;
+        const uint32_t *m0 = nullptr;
+        if (item < a.n_slices) {
+            // a slice of a long document: {document, its row in m0, first token, tokens}
+            const int4 sl = a.slices[item];
+            s = a.doc_off[sl.x] + sl.z;
+            len = sl.w;
+            m0 = a.m0 + static_cast<int64_t>(sl.y) * a.K;
+        } else {
+            const int d = a.doc_order[item - a.n_slices];
+            s = a.doc_off[d];
+            len = static_cast<int>(a.doc_off[d + 1] - s);
+        }
+        DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep, 0, len, 1};
+        z_doc_warp(a, m, r, st, m0);
     }
     flush_warp_z_stats(a.stats, st);
+}
+
+// m0[j * K + k] = the topic-k count of document sliced_docs[j] (one warp per
+// document): the pass-start counts its slices start from.
+__global__ void k_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int n, const int16_t *z, int K,
+                               uint32_t *m0) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += nwarps) {
+        uint32_t *row = m0 + static_cast<int64_t>(j) * K;
+        for (int k = lane; k < K; k += 32) row[k] = 0;
+        __syncwarp();
+        const int d = sliced_docs[j];
+        for (int64_t i = doc_off[d] + lane; i < doc_off[d + 1]; i += 32) atomicAdd(&row[z[i]], 1u);
+        __syncwarp();
+    }
 }
 
 // Many chains: the work list holds (chain, document) pairs, longest first
@@ -1428,6 +1462,13 @@ int z_groups_blocks_per_sm(int K) {
 void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st) {
     if (a.D <= 0) return;
     k_z_step_groups<<<grid, 256, z_groups_smem(a.K), st>>>(a);
+}
+
+void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int n, const int16_t *z, int K,
+                         uint32_t *m0, cudaStream_t st) {
+    if (n <= 0) return;
+    const int grid = std::max(1, std::min((n + 7) / 8, 4 * sm_count()));
+    k_slice_counts<<<grid, 256, 0, st>>>(doc_off, sliced_docs, n, z, K, m0);
 }
 
 void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st) {

@@ -158,6 +158,11 @@ struct ZArgs {
     const uint2 *bitmap;        // null when K > kMaxKBitmap
     const uint32_t *qdense;     // dense q rows of the most frequent words, or null
     const int32_t *dense_slot;  // [V] row in qdense or -1
+    // stale-count slices of long documents (k_z_step only): {row in m0, the
+    // document, first token, tokens} is {y, x, z, w}; taken before the D documents
+    const int4 *slices;
+    int n_slices;
+    const uint32_t *m0;         // [rows * K] pass-start counts of the sliced documents
     int K, KW;
     uint64_t seed;
     uint32_t sweep;
@@ -177,6 +182,9 @@ void launch_phi_fixup(const PhiArgs &a, cudaStream_t st);
 void launch_colptr_scan(const PhiArgs &a, cudaStream_t st);
 void launch_phi_tables(const PhiArgs &a, cudaStream_t st);
 void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st);
+// Pass-start topic counts of the documents that the z-step takes in slices.
+void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int n, const int16_t *z, int K,
+                         uint32_t *m0, cudaStream_t st);
 size_t z_step_smem(int K, int warps_per_block);
 size_t phi_counts_smem(int K);
 void launch_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K, int32_t *m_dk, cudaStream_t st);

@@ -57,12 +57,13 @@ def first_mismatch(z_gpu: np.ndarray, z_or: np.ndarray, doc_off: np.ndarray) -> 
 
 
 def lockstep(w, doc_off, K: int, V: int, alpha, beta: float, seed: int, sweeps: int, path: int = 0,
-             check_tables: bool = True, check_counts_every: int = 0, docs_per_warp: int = 0, phi_mode: int = 0):
+             check_tables: bool = True, check_counts_every: int = 0, docs_per_warp: int = 0, phi_mode: int = 0,
+             slice_len: int = 0):
     """Run both sides for `sweeps` sweeps, comparing after each half-sweep.
-    phi_mode 1 runs both in Algorithm 1's Dirichlet mode."""
+    phi_mode 1 runs both in Algorithm 1's Dirichlet mode; slice_len > 0 both in stale-count slices."""
     s = P.Sampler(w, doc_off, K, V, alpha, beta, seed, zstep_path=path, docs_per_warp=docs_per_warp,
-                  phi_mode=phi_mode)
-    ch = O.Chain(w, doc_off, K, V, alpha, beta, seed, dirichlet=phi_mode == 1)
+                  phi_mode=phi_mode, slice_len=slice_len)
+    ch = O.Chain(w, doc_off, K, V, alpha, beta, seed, dirichlet=phi_mode == 1, slice_len=slice_len)
     try:
         zg = s.z()
         assert np.array_equal(zg, ch.z), "initial topics differ: " + first_mismatch(zg, ch.z, doc_off)
@@ -73,7 +74,8 @@ def lockstep(w, doc_off, K: int, V: int, alpha, beta: float, seed: int, sweeps: 
             if check_tables:
                 compare_tables(s.word_tables(), ch, f"sweep {it}")
             s.z_step()
-            ch.z, ch.stats = O.z_step(ch.doc_off, ch.w, ch.z, ch.tables, ch.seed, ch.sweep_index)
+            ch.z, ch.stats = O.z_step(ch.doc_off, ch.w, ch.z, ch.tables, ch.seed, ch.sweep_index,
+                                      slice_len=slice_len)
             zg = s.z()
             msg = first_mismatch(zg, ch.z, doc_off)
             assert not msg, f"sweep {it}: " + msg
