@@ -145,11 +145,20 @@ def peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+def code_hash(text: str) -> str:
+    """Hash of a source's code: // comments, trailing blanks and empty lines do not count."""
+    lines = []
+    for line in text.splitlines():
+        i = line.find("//")
+        code = (line[:i] if i >= 0 else line).rstrip()
+        if code:
+            lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
+
+
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1704_03581_gb300", "csrc", "kernels.cu"), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()[:16]
+    with open(os.path.join(ROOT, "paper_1704_03581_gb300", "csrc", "kernels.cu")) as f:
+        return code_hash(f.read())
 
 
 def recorded_profile() -> dict:

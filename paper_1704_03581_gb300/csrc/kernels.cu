@@ -1,17 +1,23 @@
 // CUDA kernels of the Polya-urn partially collapsed LDA sampler, sm_103a.
 //
 // One sweep = Algorithm 2 (Section 3):
-//   Phi-step  k_phi_counts   per word v: rebuild n_{.,v} from z (shared-memory
+//   Phi-step  k_heavy_hist   words with more than 2^17 tokens histogrammed in
+//                            chunks by many CTAs.
+//             k_phi_counts   per word v: rebuild n_{.,v} from z (shared-memory
 //                            histogram over the word's tokens), draw
 //                            c_{k,v} ~ Pois(beta + n_{k,v}) for every k (Eq. 9,
 //                            "Efficient sampling of Phi"), accumulate S_k.
 //             k_phi_fixup    rows with S_k = 0 are redrawn until nonzero
 //                            (Definition "Poisson Polya Urn").
-//             k_colptr_scan  column offsets of the sparse Phi.
-//             k_phi_tables   phi = c/S, fixed-point weights, sigma_a and the
-//                            per-word alias table ("Efficient sampling of z").
+//             k_scan_single  column offsets of the sparse Phi.
+//             k_phi_tables   phi = c/S, fixed-point weights, sigma_a, the
+//                            per-word alias table, bitmaps and dense q rows
+//                            ("Efficient sampling of z").
 //   z-step    k_z_step       one warp per document, tokens in order, the
-//                            doubly sparse a/b draw.
+//                            doubly sparse a/b draw (k_slice_counts first
+//                            when long documents run in stale-count slices).
+// The *_multi kernels do the same over many chains; k_serve_step folds in
+// requests; Algorithm 1's Dirichlet Phi-step is in dirichlet.cu.
 // The arithmetic that decides any draw is integer or IEEE double with
 // explicit rounding, so results are independent of launch shapes.
 #include <algorithm>
@@ -581,10 +587,10 @@ __global__ void k_phi_tables_multi(const PhiArgs *chains, const int2 *items, int
 #ifndef PULDA_ZMINBLOCKS
 #define PULDA_ZMINBLOCKS 8
 #endif
-// The document side is iterated when K_d * kDocRatio < K_v * 16.  An element
-// of the document side costs about twice one of the column side (a bit scan
-// and a rank per element) and the lanes' shares of it are uneven, while the
-// column side splits evenly; either side gives the same exact sums.
+// The document side (for a word with a dense q row) is iterated when
+// K_d * kDocRatio < K_v * 16: the paper's "iterate over the smaller" at 16.
+// Either side gives the same exact sums; the column side's topic -> m loads
+// depend on each other, which makes it the costlier side per element.
 #ifndef PULDA_ZDOCRATIO
 #define PULDA_ZDOCRATIO 16
 #endif
@@ -593,7 +599,8 @@ constexpr int kDocRatio = PULDA_ZDOCRATIO;
 
 // One warp per document (dynamically scheduled, longest first).  m_d lives
 // in shared memory as a dense count array; for K <= 1024 each lane also holds
-// the 32-topic bitmap word of m_d's nonzero topics it owns.  Tokens are
+// the 32-topic bitmap word of m_d's nonzero topics it owns, and the document
+// side reads q of topic 32 lane + b from the word's dense q row.  Tokens are
 // visited in position order: remove token i (m^{-i}), compute
 // sigma_b = sum_k q_{k,v} m_k over the smaller of {k : m_k > 0} and
 // {k : phi_{k,v} > 0} (complexity theorem), draw r = floor(u (A + 2^16 B)),
