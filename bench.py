@@ -72,10 +72,12 @@ def parse():
     ap.add_argument("--serve-sweeps", type=int, default=50, help="serving: z-sweeps per request")
     ap.add_argument("--plain-requests", type=int, default=150,
                     help="serving: requests the one-at-a-time baseline serves (the first ones, at the lowest rate)")
-    ap.add_argument("--form", choices=["sweep", "batched", "serving", "trace"], default="sweep",
+    ap.add_argument("--form", choices=["sweep", "batched", "serving", "trace", "sparsity"], default="sweep",
                     help="sweep: the large corpus (the headline line); batched: 32 uneven chains in one graph "
                          "launch per sweep against 32 sequential single-chain runs; trace: the log posterior "
-                         "after every sweep, Polya urn against Dirichlet Phi, on the same corpus and seed")
+                         "after every sweep, Polya urn against Dirichlet Phi, on the same corpus and seed; sparsity: "
+                         "both Phi-steps timed on the large corpus pruned by vocabulary size, rare-word "
+                         "threshold and data size")
     ap.add_argument("--slice-len", type=int, default=0,
                     help="sweep/trace forms: documents longer than this in stale-count slices (0 = Algorithm 2)")
     ap.add_argument("--trace-corpus", choices=["small", "large"], default="small")
@@ -467,6 +469,72 @@ def run_trace(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sparsity(args):
+    """The paper's runtime study over vocabulary sizes, rare-word thresholds and
+    data sizes (Section 5, the figure on sparsity): the large corpus pruned to
+    its top-TF-IDF words, with its rare words removed, or cut to its first
+    documents, each sampled from the same seed under the Polya-urn Phi
+    (Algorithm 2) and the Dirichlet Phi (Algorithm 1).  After ``--burnin``
+    sweeps the Phi- and z-steps of the next ``--steps`` sweeps are timed with
+    CUDA events on the sampler's stream."""
+    import torch
+    import paper_1704_03581_gb300 as P
+    from paper_1704_03581_gb300 import synth
+
+    base = synth.large(D=args.docs)
+    scores = synth.tfidf(base)
+    cases = [("vocabulary", base.V, base)]
+    cases += [("vocabulary", v, synth.tfidf_pruned(base, v, scores)) for v in (50_000, 20_000, 5_000)]
+    cases += [("rare_threshold", t, synth.rare_word_pruned(base, t)) for t in (50, 200, 1000)]
+    cases += [("documents", d, base.slice_docs(0, d)) for d in (base.D // 8, base.D // 4, base.D // 2)]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def measure(c, mode):
+        s = P.Sampler(c.w, c.doc_off, K_TOPICS, c.V, ALPHA, BETA, seed=0, stream=stream.cuda_stream, phi_mode=mode)
+        s.sweep(args.burnin)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        mins = []
+        for e in ev:
+            e[0].record(stream)
+            P.pulda_phi_step(s.h)
+            e[1].record(stream)
+            P.pulda_z_step(s.h)
+            e[2].record(stream)
+            st = s.stats()                                   # synchronises; outside the events
+            mins.append(st["sum_min"] / max(1, st["tokens"]))
+        phi = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+        z = float(np.median([e[1].elapsed_time(e[2]) for e in ev]))
+        out = {"phi_ms": phi, "z_ms": z, "sweep_ms": phi + z, "nnz_phi": int(st["nnz_phi"]),
+               "mean_min_kd_kv": float(np.mean(mins))}
+        s.close()
+        return out
+
+    rows = []
+    for axis, setting, c in cases:
+        a, b = measure(c, 0), measure(c, 1)
+        rows.append({"axis": axis, "setting": setting, "V": c.V, "D": c.D, "N": c.N, "polya_urn": a, "dirichlet": b,
+                     "ratio_sweep": b["sweep_ms"] / a["sweep_ms"], "ratio_z": b["z_ms"] / a["z_ms"],
+                     "ratio_phi": b["phi_ms"] / a["phi_ms"]})
+        print(json.dumps({"progress": f"{axis}={setting}", "ratio_sweep": rows[-1]["ratio_sweep"]}),
+              file=sys.stderr, flush=True)
+    full = rows[0]
+    line = {
+        "metric": "sweep time vs vocabulary size, rare-word threshold and data size: Dirichlet Phi (Algorithm 1) "
+                  "over Polya urn (Algorithm 2)",
+        "value": full["ratio_sweep"],
+        "unit": "ratio of median sweep times (Dirichlet / Polya urn) on the unpruned corpus",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.burnin, "higher_is_better": True, "dtype": "int64",
+        "data": "synthetic (LDA generative process, Zipf(1.05) vocabulary), pruned on the host",
+        "config": {"workload": base.name, "K": K_TOPICS, "alpha": ALPHA, "beta": BETA, "seed": 0,
+                   "vocabulary": "top words by corpus TF-IDF (count x ln(D/df))",
+                   "rare_threshold": "words with fewer occurrences removed",
+                   "documents": "the first D documents"},
+        "rows": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
     """32 independent corpora (uneven D, N, K, V) advanced together by one
     CUDA-graph launch per sweep, against the same 32 chains run one after
@@ -646,11 +714,12 @@ def main():
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if args.form in ("batched", "serving", "trace"):
+    if args.form in ("batched", "serving", "trace", "sparsity"):
         from paper_1704_03581_gb300 import build
         build.build()
         if rank == 0:
-            {"batched": run_batched, "serving": run_serving, "trace": run_trace}[args.form](args)
+            {"batched": run_batched, "serving": run_serving, "trace": run_trace,
+             "sparsity": run_sparsity}[args.form](args)
         return
     if world > 1:
         import torch.distributed as dist

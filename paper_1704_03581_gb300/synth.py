@@ -217,3 +217,61 @@ def serving_requests(n: int, V: int, seed: int = 5, mean_len: float = 300.0, log
                         phi_seed=3 + 11)                          # and its topics
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
     return corpus, arrivals
+
+
+# ------------------------------------------------------------------ vocabulary pruning
+# The paper's runtime study over rare-word thresholds, vocabulary sizes and data
+# sizes (Section 5, the figure on sparsity) prunes a corpus before sampling:
+# words seen fewer than a threshold number of times are removed, or only the
+# words with the highest TF-IDF values are kept.  These helpers apply the same
+# pruning to a synthetic corpus.
+
+def keep_words(c: Corpus, keep: np.ndarray, name: str) -> Corpus:
+    """The corpus restricted to the words with ``keep[v]`` true, renumbered
+    0..V'-1 in ascending original id.  Tokens of dropped words are removed
+    from their documents (positions close up); every document is kept, so a
+    document may become empty."""
+    keep = np.asarray(keep, dtype=bool)
+    assert keep.shape == (c.V,)
+    new_id = np.cumsum(keep, dtype=np.int64) - 1
+    mask = keep[c.w]
+    kept_before = np.zeros(c.N + 1, np.int64)          # kept tokens before each position
+    np.cumsum(mask, out=kept_before[1:])
+    off = kept_before[c.doc_off]
+    return Corpus(new_id[c.w[mask]].astype(np.int32), off, int(keep.sum()), name)
+
+
+def word_counts(c: Corpus) -> np.ndarray:
+    return np.bincount(c.w, minlength=c.V).astype(np.int64)
+
+
+def document_frequency(c: Corpus) -> np.ndarray:
+    """df[v] = number of documents that contain word v at least once."""
+    import scipy.sparse
+    m = scipy.sparse.csr_matrix((np.ones(c.N, np.int32), c.w, c.doc_off), shape=(c.D, c.V), copy=True)
+    m.sum_duplicates()           # one entry per (document, word) pair; sorts the copy, not c.w
+    return np.bincount(m.indices, minlength=c.V).astype(np.int64)
+
+
+def tfidf(c: Corpus) -> np.ndarray:
+    """Corpus-level TF-IDF of each word: its count times ln(D / df), 0 for a
+    word that does not occur."""
+    n, df = word_counts(c), document_frequency(c)
+    out = np.zeros(c.V, np.float64)
+    seen = df > 0
+    out[seen] = n[seen] * np.log(c.D / df[seen])
+    return out
+
+
+def rare_word_pruned(c: Corpus, threshold: int) -> Corpus:
+    """Words that occur fewer than ``threshold`` times removed."""
+    return keep_words(c, word_counts(c) >= threshold, f"{c.name} rare<{threshold} removed")
+
+
+def tfidf_pruned(c: Corpus, V_keep: int, scores: np.ndarray | None = None) -> Corpus:
+    """The ``V_keep`` words of highest TF-IDF kept (ties: the smaller id)."""
+    s = tfidf(c) if scores is None else scores
+    order = np.lexsort((np.arange(c.V), -s))
+    keep = np.zeros(c.V, bool)
+    keep[order[:min(V_keep, c.V)]] = True
+    return keep_words(c, keep, f"{c.name} top-{V_keep} TF-IDF")
