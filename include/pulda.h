@@ -71,7 +71,16 @@ typedef struct {
                                slices, a different sampler from the paper's (AD-LDA's
                                approximation within a document).  Needs docs_per_warp 0 or 1;
                                fold-in, serving and the batched form ignore/reject it */
-    int32_t reserved[3];
+    int32_t coop_min_len;   /* corpus z-step and pulda_infer: a document at least this long is
+                               resampled by the 4 warps of one CTA together, token by token
+                               (its intersections split over 128 lanes), concurrently with the
+                               other documents' one-warp kernel; results are identical.
+                               0 = auto (documents longer than max(256, N / 6000) tokens:
+                               those that would outlast the rest of the pass on one warp),
+                               -1 = never, > 0 = this length.  Not used with docs_per_warp 4
+                               or slice_len > 0; the batched form takes 0 or -1 (one warp
+                               per document) and serving ignores it */
+    int32_t reserved[2];
 } pulda_options;
 
 /* Counters of the most recent z-step (and Phi-step), and running totals. */

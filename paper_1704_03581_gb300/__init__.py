@@ -41,7 +41,7 @@ class PuldaError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("zstep_path", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("docs_per_warp", ctypes.c_int32), ("phi_mode", ctypes.c_int32),
-                ("slice_len", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("slice_len", ctypes.c_int32), ("coop_min_len", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class SweepStats(ctypes.Structure):
@@ -133,7 +133,7 @@ def _check(h, status: int):
 
 def pulda_init(word_ids, doc_offsets, K: int, V: int, alpha, beta: float, seed: int, stream=None,
                zstep_path: int = 0, warps_per_block: int = 0, docs_per_warp: int = 0, phi_mode: int = 0,
-               slice_len: int = 0) -> int:
+               slice_len: int = 0, coop_min_len: int = 0) -> int:
     w = np.ascontiguousarray(word_ids, dtype=np.int32)
     off = np.ascontiguousarray(doc_offsets, dtype=np.int64)
     a = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, dtype=np.float32), (K,)))
@@ -144,6 +144,7 @@ def pulda_init(word_ids, doc_offsets, K: int, V: int, alpha, beta: float, seed: 
     opt.docs_per_warp = docs_per_warp
     opt.phi_mode = phi_mode
     opt.slice_len = slice_len
+    opt.coop_min_len = coop_min_len
     h = ctypes.c_void_p()
     st = lib().pulda_init(ctypes.byref(h), _ptr(w), _ptr(off), off.shape[0] - 1, K, V, _ptr(a), float(beta),
                           int(seed) & (2 ** 64 - 1), ctypes.byref(opt))
@@ -258,15 +259,17 @@ class Sampler:
 
     def __init__(self, word_ids, doc_offsets, K: int, V: int, alpha=0.1, beta: float = 0.01, seed: int = 0,
                  stream=None, zstep_path: int = 0, warps_per_block: int = 0, docs_per_warp: int = 0,
-                 phi_mode: int = 0, slice_len: int = 0):
+                 phi_mode: int = 0, slice_len: int = 0, coop_min_len: int = 0):
         """phi_mode 0: Poisson Polya urn (Algorithm 2); 1: Dirichlet Phi (Algorithm 1).
-        slice_len > 0: documents longer than it resampled in concurrent stale-count slices (not the paper's)."""
+        slice_len > 0: documents longer than it resampled in concurrent stale-count slices (not the paper's).
+        coop_min_len: documents at least this long resampled by a whole CTA (0 = automatic, -1 = never);
+        the topics are the same either way."""
         self.K, self.V = K, V
         self.phi_mode = phi_mode
         self.N = int(np.asarray(doc_offsets)[-1])
         self.D = int(np.asarray(doc_offsets).shape[0] - 1)
         self.h = pulda_init(word_ids, doc_offsets, K, V, alpha, beta, seed, stream, zstep_path, warps_per_block,
-                            docs_per_warp, phi_mode, slice_len)
+                            docs_per_warp, phi_mode, slice_len, coop_min_len)
 
     def close(self):
         if self.h:

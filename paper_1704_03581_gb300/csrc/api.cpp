@@ -133,13 +133,40 @@ int64_t count_long(const int64_t *off, const std::vector<int32_t> &order) {
     return n;
 }
 
-// One z-step over the documents doc_order[0..D): the documents too long for
+// Number of leading documents of a length-ordered schedule that the
+// cooperative z-step takes: at least coop_min_len tokens (0 = automatic:
+// longer than max(256, N / 6000)); none with coop_min_len < 0, the grouped
+// z-step or slices.
+int64_t count_coop(const pulda_handle *h, const int64_t *off, const std::vector<int32_t> &order, int64_t N) {
+    if (h->opt.coop_min_len < 0 || h->z_groups || h->opt.slice_len > 0) return 0;
+    const int64_t L = h->opt.coop_min_len > 0 ? h->opt.coop_min_len
+                                              : std::max<int64_t>(kCoopAutoMin, N / kCoopAutoDiv + 1);
+    int64_t n = 0;
+    while (n < static_cast<int64_t>(order.size()) && off[order[n] + 1] - off[order[n]] >= L) ++n;
+    return n;
+}
+
+// One z-step over the documents doc_order[0..D): the first n_coop by the
+// cooperative kernel on the handle's stream while the others run one per warp
+// on a second stream (joined back); or, grouped, the documents too long for
 // the grouped kernel (the first n_long) one per warp, the rest four per warp.
 pulda_status run_z(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, int64_t n_long,
-                   const int32_t *w, int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
-    CU(h, cudaMemsetAsync(h->work + 1, 0, 2 * sizeof(int), h->stream));
+                   int64_t n_coop, const int32_t *w, int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
+    CU(h, cudaMemsetAsync(h->work + 1, 0, 3 * sizeof(int), h->stream));
     ZArgs a = z_args(h, doc_off, doc_order, D, w, z, seed, sweep, index_base);
-    if (!h->z_groups) {
+    if (!h->z_groups && n_coop > 0) {
+        CU(h, cudaEventRecord(h->ev_fork, h->stream));
+        launch_z_step_coop(a, static_cast<int>(n_coop), h->work + 3, h->coop_grid, h->stream);
+        CU(h, cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
+        if (D > n_coop) {
+            ZArgs ar = a;
+            ar.doc_order = doc_order + n_coop;
+            ar.D = D - n_coop;
+            launch_z_step(ar, h->z_warps, h->z_grid, h->stream2);
+        }
+        CU(h, cudaEventRecord(h->ev_join, h->stream2));
+        CU(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    } else if (!h->z_groups) {
         launch_z_step(a, h->z_warps, h->z_grid, h->stream);
     } else {
         if (n_long > 0) {
@@ -244,6 +271,10 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     }
     if (h->opt.slice_len < 0 || (h->opt.slice_len > 0 && h->opt.docs_per_warp == 4)) {
         fail(h, PULDA_ERR_INVALID, "slice_len must be >= 0, and slices need docs_per_warp 0 or 1");
+        return reject(PULDA_ERR_INVALID);
+    }
+    if (h->opt.coop_min_len < -1) {
+        fail(h, PULDA_ERR_INVALID, "coop_min_len must be -1 (never), 0 (auto) or a length");
         return reject(PULDA_ERR_INVALID);
     }
     if (h->opt.docs_per_warp == 4 && K > kMaxKBitmap) {
@@ -402,6 +433,12 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     // longer chains of dependent loads.  It is kept for small intersections.
     h->z_groups = h->opt.docs_per_warp == 4;
     h->n_long = count_long(doc_offsets, dord);
+    h->n_coop = count_coop(h, doc_offsets, dord, N);
+    h->coop_grid = sms * z_coop_blocks_per_sm(K);
+    CUI(cudaGetLastError());
+    CUI(cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
+    CUI(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CUI(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     if (h->z_groups) {
         h->zg_grid = sms * z_groups_blocks_per_sm(K);
         CUI(cudaGetLastError());
@@ -456,7 +493,8 @@ pulda_status pulda_z_step(pulda_handle *h) {
         CU(h, cudaGetLastError());
         return PULDA_OK;
     }
-    return run_z(h, h->doc_off, h->doc_order, h->D, h->n_long, h->w, h->z, h->seed, static_cast<uint32_t>(h->sweep), 0);
+    return run_z(h, h->doc_off, h->doc_order, h->D, h->n_long, h->n_coop, h->w, h->z, h->seed,
+                 static_cast<uint32_t>(h->sweep), 0);
 }
 
 pulda_status pulda_sweep(pulda_handle *h, int32_t n_sweeps) {
@@ -625,8 +663,9 @@ pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids, const int64_t
     launch_init_z(N, h->K, seed, 0, dz, st);
     CU(h, clear_z_counters(h));
     const int64_t n_long = count_long(doc_offsets, ord);
+    const int64_t n_coop = count_coop(h, doc_offsets, ord, N);
     for (int32_t sw = 1; sw <= n_sweeps; ++sw) {
-        s = run_z(h, doff, dord, D_new, n_long, dw, dz, seed, static_cast<uint32_t>(sw), 0);
+        s = run_z(h, doff, dord, D_new, n_long, n_coop, dw, dz, seed, static_cast<uint32_t>(sw), 0);
         if (s != PULDA_OK) return s;
     }
     if (z_out) CU(h, cudaMemcpyAsync(z_out, dz, sizeof(int16_t) * N, cudaMemcpyDeviceToHost, st));
@@ -671,6 +710,12 @@ void pulda_free(pulda_handle *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void *p : h->allocs) cudaFree(p);
+    if (h->stream2) {
+        cudaStreamSynchronize(h->stream2);
+        cudaStreamDestroy(h->stream2);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

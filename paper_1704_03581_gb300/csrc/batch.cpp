@@ -97,6 +97,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = "batched chains resample every document in order (slice_len must be 0)";
         return bail(PULDA_ERR_INVALID);
     }
+    if (o.coop_min_len > 0 || o.coop_min_len < -1) {
+        b->err = "batched chains run each document on one warp (coop_min_len must be 0 or -1)";
+        return bail(PULDA_ERR_INVALID);
+    }
     if (o.warps_per_block < 0 || o.warps_per_block > kMultiWarps) {
         b->err = "warps_per_block must be in [0, " + std::to_string(kMultiWarps) + "] (got " +
                  std::to_string(o.warps_per_block) + ")";

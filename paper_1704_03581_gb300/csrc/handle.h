@@ -26,6 +26,10 @@ struct pulda_handle {
     bool z_groups = false;      // grouped z-step (four documents per warp) in use
     int zg_grid = 0;
     int64_t n_long = 0;         // documents too long for the grouped z-step (first in doc_order)
+    int64_t n_coop = 0;         // documents the cooperative z-step takes (first in doc_order)
+    int coop_grid = 0;
+    cudaStream_t stream2 = nullptr;                       // the one-warp z-step beside the cooperative one
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<void *> allocs;
     // corpus and state
     int32_t *w = nullptr; int64_t *doc_off = nullptr; int16_t *z = nullptr; int32_t *doc_order = nullptr;

@@ -647,6 +647,30 @@ struct DocRun {
     int max_pass_end;        // stop when the pass counter reaches sweep + this many passes
 };
 
+// Stages what depends only on token i of run r (see z_doc_warp for the
+// record layout) and returns its current topic.
+__device__ __forceinline__ int stage_token(const ZArgs &a, const DocRun &r, int i, uint4 *rec2, uint32_t *drow) {
+    const int wv = r.w[i];
+    const int zo = r.z[i];
+    const uint64_t t = static_cast<uint64_t>(r.index_base + i);
+    const U4 x = draw(r.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), r.sweep, TAG_Z, 0);
+    const int64_t cb = a.col_ptr[wv];
+    const int nw = static_cast<int>(a.col_ptr[wv + 1] - cb);
+    const u64 Av = a.A[wv];
+    int ta = 0;
+    if (nw > 0) {
+        const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
+        ta = x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl];
+    }
+    rec2[0] = make_uint4(static_cast<uint32_t>(cb),
+                         static_cast<uint32_t>(static_cast<u64>(cb) >> 32) | (static_cast<uint32_t>(ta) << 16),
+                         static_cast<uint32_t>(Av), static_cast<uint32_t>(Av >> 32));
+    rec2[1] = make_uint4(x.x, x.y, static_cast<uint32_t>(wv), static_cast<uint32_t>(nw) | (static_cast<uint32_t>(zo) << 16));
+    const int ds = a.dense_slot ? a.dense_slot[wv] : -1;
+    *drow = ds >= 0 ? static_cast<uint32_t>(ds) * static_cast<uint32_t>(a.K) : 0xFFFFFFFFu;
+    return zo;
+}
+
 // Resamples the tokens of one document, by one warp, in position order,
 // pass after pass, until `budget` tokens are done or `max_pass_end` passes
 // have been completed.  m (K entries of shared memory) is rebuilt from the
@@ -700,28 +724,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
         // (column starts are below 2^48, K_v <= 16384, topics < 16384).
         uint4 *rec = reinterpret_cast<uint4 *>(m + z_m_words(K));
         uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);   // q row offset of the token's word, or ~0
-        if (valid) {
-            const int wv = r.w[i];
-            const int zo = r.z[i];
-            znew = zo;
-            const uint64_t t = static_cast<uint64_t>(r.index_base + i);
-            const U4 x = draw(r.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), r.sweep, TAG_Z, 0);
-            const int64_t cb = a.col_ptr[wv];
-            const int nw = static_cast<int>(a.col_ptr[wv + 1] - cb);
-            const u64 Av = a.A[wv];
-            int ta = 0;
-            if (nw > 0) {
-                const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
-                ta = x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl];
-            }
-            rec[2 * lane] = make_uint4(static_cast<uint32_t>(cb),
-                                       static_cast<uint32_t>(static_cast<u64>(cb) >> 32) | (static_cast<uint32_t>(ta) << 16),
-                                       static_cast<uint32_t>(Av), static_cast<uint32_t>(Av >> 32));
-            rec[2 * lane + 1] = make_uint4(x.x, x.y, static_cast<uint32_t>(wv),
-                                           static_cast<uint32_t>(nw) | (static_cast<uint32_t>(zo) << 16));
-            const int ds = a.dense_slot ? a.dense_slot[wv] : -1;
-            drow_of[lane] = ds >= 0 ? static_cast<uint32_t>(ds) * static_cast<uint32_t>(K) : 0xFFFFFFFFu;
-        }
+        if (valid) znew = stage_token(a, r, i, rec + 2 * lane, drow_of + lane);
         __syncwarp();
         // the bits half of the word's bitmap entries (32 topics per lane)
         const uint32_t *bits = reinterpret_cast<const uint32_t *>(a.bitmap);
@@ -925,6 +928,253 @@ __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs
         }
         DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep, 0, len, 1};
         z_doc_warp(a, m, r, st, m0);
+    }
+    flush_warp_z_stats(a.stats, st);
+}
+
+// ============================================================== cooperative z-step
+// A document's tokens are strictly sequential, so on one warp the longest
+// documents outlast the rest of the z-step: a few microseconds per token
+// (every token waits on its q gathers, its scan and its draw in turn) times
+// thousands of tokens, while the other warps have long finished.  Here the
+// kCoopWarps warps of a CTA share one document, token by token.  The token's
+// intersection is split over the CTA's kCoopSlots lanes ("slots") in
+// ascending topic order: on the document side slot g owns the R consecutive
+// topics [g R, g R + R) (R the smallest power of two with 32 KW <= R slots),
+// on the column side a contiguous segment of the word's column.  Each slot
+// gathers its few q values at once, every warp scans its slots, the warps'
+// totals meet in shared memory (barrier A), and the slot whose prefix passes
+// the draw reads off the topic, updates m and publishes it (barrier B).  The
+// sums are the same exact integers in the same topic order as the one-warp
+// kernel's, so every draw, and every topic, is identical.
+constexpr int kCoopWarps = 4;
+constexpr int kCoopSlots = 32 * kCoopWarps;
+constexpr int kCoopGather = 4;     // document-side q loads per round
+
+struct CoopXch {
+    u64 tot[kCoopWarps];    // each warp's sum of q m over its slots (this token)
+    int kdp[kCoopWarps];    // each warp's share of K_d when the document starts
+    int item;               // the document the CTA takes next
+    int knew;               // this token's new topic
+    uint32_t mkn;           // m^{-i} of the new topic, before the token is added back
+};
+// Shared memory of a cooperative CTA, in 32-bit words: m_d, the records of
+// 32 tokens, the exchange area.
+__host__ __device__ __forceinline__ int z_coop_words(int K) {
+    return z_m_words(K) + 32 * kTokRecWords + static_cast<int>((sizeof(CoopXch) + 15) / 16) * 4;
+}
+
+__device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = a.K;
+    uint32_t *m = sm;
+    uint4 *rec = reinterpret_cast<uint4 *>(sm + z_m_words(K));
+    uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);
+    CoopXch &x = *reinterpret_cast<CoopXch *>(drow_of + 32);
+    const bool use_bm = a.bitmap != nullptr && a.path != 1;
+    int R = 1;
+    while (32 * a.KW > R * kCoopSlots) R <<= 1;
+    const bool own = use_bm && tid < 32 * a.KW / R;      // this slot owns topics on the document side
+    const int wi = own ? (tid * R) >> 5 : 0;              // its bitmap word
+    const int sh = (tid * R) & 31;
+    const uint32_t mask = own ? (R >= 32 ? 0xFFFFFFFFu : ((1u << R) - 1u) << sh) : 0u;
+    if (r.len == 0 || r.budget <= 0) return;
+    for (int k = tid; k < K; k += kCoopSlots) m[mi(k)] = 0;
+    __syncthreads();
+    for (int i = tid; i < r.len; i += kCoopSlots) atomicAdd(&m[mi(r.z[i])], 1u);
+    __syncthreads();
+    uint32_t mb = 0;        // this slot's bits of m_d's nonzero topics
+    int c = 0;
+    if (use_bm) {
+        for (int t = 0; t < R && own; ++t) {
+            const int k = wi * 32 + sh + t;
+            if (k < K && m[mi(k)] > 0) mb |= 1u << (sh + t);
+        }
+        c = __popc(mb);
+    } else {
+        for (int k = tid; k < K; k += kCoopSlots) c += m[mi(k)] > 0 ? 1 : 0;
+    }
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if (lane == 0) x.kdp[warp] = c;
+    __syncthreads();
+    int kd = 0;
+#pragma unroll
+    for (int j = 0; j < kCoopWarps; ++j) kd += x.kdp[j];
+    const uint32_t *bits = reinterpret_cast<const uint32_t *>(a.bitmap);
+    const uint32_t sweep_end = r.sweep + static_cast<uint32_t>(r.max_pass_end);
+    while (r.budget > 0 && r.sweep != sweep_end) {
+        const int i0 = r.pos;
+        const int cnt = static_cast<int>(min(static_cast<int64_t>(32), min(static_cast<int64_t>(r.len - i0), r.budget)));
+        if (warp == 0 && lane < cnt) stage_token(a, r, i0 + lane, rec + 2 * lane, drow_of + lane);
+        __syncthreads();
+        uint32_t bm_next = own ? bits[2 * (static_cast<int64_t>(rec[1].z) * a.KW + wi)] & mask : 0u;
+        for (int tt = 0; tt < cnt; ++tt) {
+            const uint4 t0 = rec[2 * tt], t1 = rec[2 * tt + 1];
+            const int kold = static_cast<int>(t1.w >> 16);
+            const int64_t col = static_cast<int64_t>((static_cast<u64>(t0.y & 0xFFFFu) << 32) | t0.x);
+            const int n_w = static_cast<int>(t1.w & 0xFFFFu);
+            const u64 At = (static_cast<u64>(t0.w) << 32) | t0.z;
+            const u64 U = (static_cast<u64>(t1.x) << 32) | t1.y;
+            const int ka = static_cast<int>(t0.y >> 16);
+            const uint32_t bm = bm_next;
+            if (own && tt + 1 < cnt) bm_next = bits[2 * (static_cast<int64_t>(rec[2 * tt + 3].z) * a.KW + wi)] & mask;
+            // m^{-i}: the old topic's count less one, applied as each count is read
+            const uint32_t mko = m[mi(kold)];
+            const int kdi = kd - (mko == 1u ? 1 : 0);
+            if (mko == 1u && own && (kold >> 5) == wi) mb &= ~(1u << (kold & 31));
+            if (warp == 0) {
+                st.add(2, static_cast<u64>(kdi < n_w ? kdi : n_w));
+                st.add(5, kdi < n_w ? 1u : 0u);
+            }
+            const uint32_t drow = drow_of[tt];
+            const bool docside = use_bm && drow != 0xFFFFFFFFu && (a.path == 2 || kdi * kDocRatio < n_w * 16);
+            const uint32_t *qrow = a.qdense + drow + 32 * wi;
+            u64 acc = 0;
+            uint32_t rem = 0;
+            int j0 = 0, j1 = 0;
+            if (docside) {
+                rem = bm & mb;
+                st.inter += static_cast<u64>(__popc(rem));
+                for (uint32_t bb = rem; bb;) {
+                    uint32_t qv[kCoopGather];
+                    int bp[kCoopGather];
+#pragma unroll
+                    for (int t = 0; t < kCoopGather; ++t) {
+                        bp[t] = -1;
+                        qv[t] = 0;
+                        if (bb) {
+                            const int b = __ffs(bb) - 1;
+                            bb &= bb - 1;
+                            bp[t] = b;
+                            qv[t] = qrow[b];
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < kCoopGather; ++t) {
+                        if (bp[t] >= 0) {
+                            const int k = 32 * wi + bp[t];
+                            acc += static_cast<u64>(qv[t]) * (m[33 * wi + bp[t]] - (k == kold ? 1u : 0u));
+                        }
+                    }
+                }
+            } else {
+                const int seg = (n_w + kCoopSlots - 1) / kCoopSlots;
+                j0 = min(seg * tid, n_w);
+                j1 = min(j0 + seg, n_w);
+                unsigned nj = 0;
+#pragma unroll 4
+                for (int j = j0; j < j1; ++j) {
+                    const int k = a.topic[col + j];
+                    const uint32_t mk = m[mi(k)] - (k == kold ? 1u : 0u);
+                    acc += static_cast<u64>(a.q[col + j]) * mk;
+                    nj += mk != 0u;
+                }
+                st.inter += static_cast<u64>(nj);
+            }
+            const u64 incl = warp_incl_scan64(acc);
+            if (lane == 31) x.tot[warp] = incl;
+            __syncthreads();                                  // A: the warps' totals
+            u64 B = 0;
+            u64 tot[kCoopWarps];
+#pragma unroll
+            for (int j = 0; j < kCoopWarps; ++j) {
+                tot[j] = x.tot[j];
+                B += tot[j];
+            }
+            const u64 T = At + (B << kFracBits);
+            int knew = kold;
+            bool upd = tid == 0;        // who updates m and publishes the topic
+            if (T == 0) {
+                if (warp == 0) st.add(3, 1);
+            } else {
+                const u64 rr = __umul64hi(U, T);
+                if (rr < At) {
+                    knew = ka;
+                    if (warp == 0) st.add(1, 1);
+                } else {
+                    const u64 rb = (rr - At) >> kFracBits;   // < B
+                    int selw = kCoopWarps;
+                    u64 lo = 0;
+#pragma unroll
+                    for (int j = 0; j < kCoopWarps; ++j) {
+                        if (selw == kCoopWarps) {
+                            if (rb < lo + tot[j]) selw = j;
+                            else lo += tot[j];
+                        }
+                    }
+                    if (selw == kCoopWarps) {
+                        if (tid == 0) atomicOr(&a.stats[ST_ERROR], ERR_INTERNAL);
+                    } else {
+                        upd = false;
+                        if (warp == selw) {
+                            const u64 rbl = rb - lo;
+                            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, rbl < incl);   // lane 31 at least
+                            if (lane == (bal ? __ffs(bal) - 1 : 31)) {
+                                upd = true;
+                                int f = -1;
+                                u64 run = incl - acc;
+                                if (docside) {
+                                    for (uint32_t bb = rem; f < 0 && bb; bb &= bb - 1) {
+                                        const int b = __ffs(bb) - 1;
+                                        const int k = 32 * wi + b;
+                                        run += static_cast<u64>(qrow[b]) * (m[33 * wi + b] - (k == kold ? 1u : 0u));
+                                        if (rbl < run) f = k;
+                                    }
+                                } else {
+                                    for (int j = j0; j < j1; ++j) {
+                                        const int k = a.topic[col + j];
+                                        run += static_cast<u64>(a.q[col + j]) * (m[mi(k)] - (k == kold ? 1u : 0u));
+                                        if (rbl < run) { f = k; break; }
+                                    }
+                                }
+                                if (f < 0) atomicOr(&a.stats[ST_ERROR], ERR_INTERNAL);
+                                else knew = f;
+                            }
+                        }
+                    }
+                }
+            }
+            if (upd) {
+                const uint32_t mkn = knew == kold ? mko - 1u : m[mi(knew)];
+                if (knew != kold) {
+                    m[mi(kold)] = mko - 1u;
+                    m[mi(knew)] = mkn + 1u;
+                }
+                x.knew = knew;
+                x.mkn = mkn;
+                r.z[i0 + tt] = static_cast<int16_t>(knew);
+            }
+            __syncthreads();                                  // B: the new topic, m updated
+            const int kn = x.knew;
+            const uint32_t mkn = x.mkn;
+            kd = kdi + (mkn == 0u ? 1 : 0);
+            if (mkn == 0u && own && (kn >> 5) == wi && ((mask >> (kn & 31)) & 1u)) mb |= 1u << (kn & 31);
+        }
+        if (warp == 0) st.add(0, static_cast<u64>(cnt));
+        r.budget -= cnt;
+        r.pos += cnt;
+        if (r.pos == r.len) { r.pos = 0; r.sweep += 1; }
+    }
+}
+
+// The longest documents of a pass, one CTA each (dynamically scheduled,
+// longest first): doc_order[0 .. n_coop).
+__global__ void __launch_bounds__(kCoopSlots, PULDA_ZMINBLOCKS) k_z_step_coop(ZArgs a, int n_coop, int *work) {
+    extern __shared__ uint32_t zsm[];
+    CoopXch &x = *reinterpret_cast<CoopXch *>(zsm + z_m_words(a.K) + 32 * kTokRecWords);
+    ZCount st;
+    const uint32_t sweep = sweep_of(a);
+    for (;;) {
+        if (threadIdx.x == 0) x.item = atomicAdd(work, 1);
+        __syncthreads();
+        const int item = x.item;
+        __syncthreads();
+        if (item >= n_coop) break;
+        const int d = a.doc_order[item];
+        const int64_t s = a.doc_off[d];
+        const int len = static_cast<int>(a.doc_off[d + 1] - s);
+        DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep, 0, len, 1};
+        z_doc_coop(a, zsm, r, st);
     }
     flush_warp_z_stats(a.stats, st);
 }
@@ -1480,6 +1730,20 @@ void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int
 
 void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st) {
     k_z_step<<<grid, 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(a);
+}
+
+size_t z_coop_smem(int K) { return sizeof(uint32_t) * static_cast<size_t>(z_coop_words(K)); }
+
+int z_coop_blocks_per_sm(int K) {
+    allow_dynamic_smem(k_z_step_coop);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_z_step_coop, kCoopSlots, z_coop_smem(K));
+    return b > 0 ? b : 1;
+}
+
+void launch_z_step_coop(const ZArgs &a, int n_coop, int *work, int grid, cudaStream_t st) {
+    if (n_coop <= 0) return;
+    k_z_step_coop<<<std::max(1, std::min(grid, n_coop)), kCoopSlots, z_coop_smem(a.K), st>>>(a, n_coop, work);
 }
 
 void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {

@@ -182,6 +182,15 @@ void launch_phi_fixup(const PhiArgs &a, cudaStream_t st);
 void launch_colptr_scan(const PhiArgs &a, cudaStream_t st);
 void launch_phi_tables(const PhiArgs &a, cudaStream_t st);
 void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st);
+// The longest documents, doc_order[0 .. n_coop), one CTA of four warps each;
+// `work` is a counter zeroed before the launch.
+void launch_z_step_coop(const ZArgs &a, int n_coop, int *work, int grid, cudaStream_t st);
+int z_coop_blocks_per_sm(int K);
+// Automatic threshold of the cooperative z-step: a document on one warp takes
+// about 2.5 us per token while the whole pass streams ~2.4 G tokens/s, so one
+// longer than N / 6000 tokens would outlast the pass.
+constexpr int64_t kCoopAutoDiv = 6000;
+constexpr int64_t kCoopAutoMin = 256;
 // Pass-start topic counts of the documents that the z-step takes in slices.
 void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int n, const int16_t *z, int K,
                          uint32_t *m0, cudaStream_t st);
