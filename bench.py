@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--trace-sweeps", type=int, default=100)
     ap.add_argument("--batch-scale", type=float, default=0.25,
                     help="fraction of each batched chain's documents (1.0 = the full 267M-token workload)")
+    ap.add_argument("--coop-min-len", type=int, default=0,
+                    help="documents (serving: requests) at least this long resampled by a CTA of four warps "
+                         "(0 = automatic, -1 = never); results are identical")
     ap.add_argument("--docs", type=int, default=300_000,
                     help="documents of the large corpus (300,000 = the full workload; fewer for profiling)")
     return ap.parse_args()
@@ -288,7 +291,7 @@ def run_pulda(args, corpus, rank: int, world: int):
     torch.cuda.set_stream(stream)
     s = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                   stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp,
-                  phi_mode=args.phi_mode, slice_len=args.slice_len)
+                  phi_mode=args.phi_mode, slice_len=args.slice_len, coop_min_len=args.coop_min_len)
     s.sweep(args.burnin + args.warmup)
     s.sync()
     lp_before = s.log_posterior()[0]          # the diagnostic, outside the timed region
@@ -340,7 +343,7 @@ def run_pulda(args, corpus, rank: int, world: int):
         t0 = time.perf_counter()
         s2 = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                        stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp, phi_mode=args.phi_mode,
-                       slice_len=args.slice_len)
+                       slice_len=args.slice_len, coop_min_len=args.coop_min_len)
         stats_bytes = ctypes.sizeof(P.SweepStats)
         for _ in range(K):
             s2.sweep(1)
@@ -610,7 +613,8 @@ def run_serving(args):
     from paper_1704_03581_gb300 import synth
 
     corpus = synth.large()
-    model = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=0)
+    model = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=0,
+                      coop_min_len=args.coop_min_len)
     model.sweep(30)
     model.sync()
     rates = [float(r) for r in args.rates.split(",")]
@@ -648,7 +652,9 @@ def run_serving(args):
         t_end = max(r["done_ns"] for r in done.values())
         lat = np.array([(done[j]["done_ns"] - t0) / 1e6 - arrivals[j] * 1e3 for j in range(n)])
         toks = int(lens[:n].sum())
+        sst = srv.stats()
         results.append({"rate_docs_per_s": rate, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
+                        "max_active": int(sst["max_active"]), "launches": int(sst["launches"]),
                         "p99_ms": float(np.percentile(lat, 99)),
                         "docs_per_s": n / ((t_end - t0) / 1e9),
                         "token_sweeps_per_s": toks * args.serve_sweeps / ((t_end - t0) / 1e9)})
@@ -690,6 +696,7 @@ def run_serving(args):
         "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic requests, lognormal(300, 1.2) tokens clipped to [10, 20000], Poisson arrivals",
         "config": {"workload": "fold-in against the large model's Phi after 30 sweeps", "slice_tokens": args.slice,
+                   "coop_min_len": args.coop_min_len,
                    "sweeps_per_request": args.serve_sweeps},
         "continuous_batching": results,
         "one_at_a_time": plain,

@@ -79,7 +79,8 @@ typedef struct {
                                those that would outlast the rest of the pass on one warp),
                                -1 = never, > 0 = this length.  Not used with docs_per_warp 4
                                or slice_len > 0; the batched form takes 0 or -1 (one warp
-                               per document) and serving ignores it */
+                               per document); a server on the handle uses it for requests
+                               (0 = requests of at least 1,024 tokens) */
     int32_t reserved[2];
 } pulda_options;
 
@@ -269,8 +270,11 @@ void pulda_batch_free(pulda_batch *b);
  * worker thread admits waiting requests while a slot and a contiguous range
  * of the token arena are free (memory-based admission, first come first
  * served), advances every admitted request by up to `slice_tokens` tokens per
- * launch (one warp per request, sweeps continuing within a launch) and copies
- * finished topics out.  A request's result equals pulda_infer on that
+ * launch (one warp per request; one CTA of the cooperative z-step per request
+ * of at least the handle's coop_min_len tokens -- 1,024 when it is 0, none
+ * when -1 -- on a second stream while the active requests fill at most an
+ * eighth of the resident warps; sweeps continuing within a launch) and
+ * copies finished topics out.  A request's result equals pulda_infer on that
  * document alone with the same seed and n_sweeps: its random streams are keyed
  * by its own seed and token positions, never by its neighbours.
  * Do not run pulda_sweep / pulda_phi_step on the handle while a server is open
@@ -288,10 +292,13 @@ typedef struct {
 /* pulda_serve_open -- token_budget: tokens the arena holds (6 bytes each on
  * the device, 6 pinned on the host); max_slots: requests in flight;
  * slice_tokens: tokens a request
- * advances per launch, or 0 to let the server tune it toward launches of
- * about 2 ms (results do not depend on it).  Errors: PULDA_ERR_INVALID (no
+ * advances per launch, or 0 for launches of about 2 ms in which every request
+ * advances as far as it gets (at least 32 tokens, in whole 32-token blocks,
+ * while a 2 ms window from when a warp or CTA takes it up is open); results do
+ * not depend on it.  Waits for the work queued on the handle's stream (the sweeps that
+ * drew Phi) before the server's first launch.  Errors: PULDA_ERR_INVALID (no
  * Phi yet, token_budget or max_slots < 1, slice_tokens < 0),
- * PULDA_ERR_OOM, PULDA_ERR_CUDA. */
+ * PULDA_ERR_OOM, PULDA_ERR_CUDA, or a device error pulda_sync reports. */
 pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max_slots, int64_t slice_tokens,
                               pulda_server **out);
 /* pulda_serve_submit -- enqueue one document (thread safe).  words_host

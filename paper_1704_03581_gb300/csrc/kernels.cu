@@ -645,7 +645,14 @@ struct DocRun {
     int pos;                 // first position to resample
     int64_t budget;          // tokens to resample in this call (passes continue past the end)
     int max_pass_end;        // stop when the pass counter reaches sweep + this many passes
+    uint64_t deadline = ~0ull;   // global timer (ns): no 32-token block starts after it, but the first
 };
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Stages what depends only on token i of run r (see z_doc_warp for the
 // record layout) and returns its current topic.
@@ -710,7 +717,14 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
         kd = cnt;
     }
     const uint32_t sweep_end = r.sweep + static_cast<uint32_t>(r.max_pass_end);
+    bool first = true;
     while (r.budget > 0 && r.sweep != sweep_end) {
+        if (r.deadline != ~0ull && !first) {
+            uint64_t now = 0;
+            if (lane == 0) now = global_ns();
+            if (__shfl_sync(0xFFFFFFFFu, now, 0) >= r.deadline) break;
+        }
+        first = false;
         const int i0 = r.pos;
         const int64_t left = static_cast<int64_t>(r.len - i0);
         const int cnt = static_cast<int>(min(static_cast<int64_t>(32), min(left, r.budget)));
@@ -955,6 +969,7 @@ struct CoopXch {
     u64 tot[kCoopWarps];    // each warp's sum of q m over its slots (this token)
     int kdp[kCoopWarps];    // each warp's share of K_d when the document starts
     int item;               // the document the CTA takes next
+    int go;                 // thread 0's reading of the deadline for the next block
     int knew;               // this token's new topic
     uint32_t mkn;           // m^{-i} of the new topic, before the token is added back
 };
@@ -1002,11 +1017,15 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
     for (int j = 0; j < kCoopWarps; ++j) kd += x.kdp[j];
     const uint32_t *bits = reinterpret_cast<const uint32_t *>(a.bitmap);
     const uint32_t sweep_end = r.sweep + static_cast<uint32_t>(r.max_pass_end);
+    bool first = true;
     while (r.budget > 0 && r.sweep != sweep_end) {
         const int i0 = r.pos;
         const int cnt = static_cast<int>(min(static_cast<int64_t>(32), min(static_cast<int64_t>(r.len - i0), r.budget)));
+        if (tid == 0) x.go = r.deadline == ~0ull || first || global_ns() < r.deadline;
         if (warp == 0 && lane < cnt) stage_token(a, r, i0 + lane, rec + 2 * lane, drow_of + lane);
         __syncthreads();
+        if (!x.go) break;     // the same value in every thread: read before any thread can write it again
+        first = false;
         uint32_t bm_next = own ? bits[2 * (static_cast<int64_t>(rec[1].z) * a.KW + wi)] & mask : 0u;
         for (int tt = 0; tt < cnt; ++tt) {
             const uint4 t0 = rec[2 * tt], t1 = rec[2 * tt + 1];
@@ -1537,18 +1556,27 @@ __global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_
 // (pass, position) is written back for the host's completion check.
 // Its slot bookkeeping needs a few more registers than k_z_step: 7 CTAs per
 // SM keep it free of spills.
+// With window_ns > 0 a slot also stops at the first 32-token block boundary
+// window_ns after its warp took it up, having done at least one block (a slot
+// taken up in a later wave of a crowded launch gets the same time as the first).
 __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSlot *slots, const int32_t *active,
                                                                      int n_active, const int32_t *arena_w,
-                                                                     int16_t *arena_z, int64_t slice, int *work) {
+                                                                     int16_t *arena_z, int64_t slice, int *work,
+                                                                     uint64_t window_ns) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
     uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
     ZCount st;
     for (;;) {
         int item = 0;
-        if (lane == 0) item = atomicAdd(work, 1);
+        uint64_t t0 = 0;
+        if (lane == 0) {
+            item = atomicAdd(work, 1);
+            if (window_ns) t0 = global_ns();
+        }
         item = __shfl_sync(0xFFFFFFFFu, item, 0);
         if (item >= n_active) break;
+        const uint64_t deadline = window_ns ? __shfl_sync(0xFFFFFFFFu, t0, 0) + window_ns : ~0ull;
         const int idx = active[item];
         const ServeSlot sl = slots[idx];
         int16_t *z = arena_z + sl.off;
@@ -1564,9 +1592,53 @@ __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSl
             pos = 0;
         }
         DocRun r{arena_w + sl.off, z, sl.len, sl.seed, 0, sweep, pos, slice,
-                 static_cast<int>(sl.sweep_end - sweep)};
+                 static_cast<int>(sl.sweep_end - sweep), deadline};
         z_doc_warp(a, m, r, st);
         if (lane == 0) {
+            slots[idx].sweep = r.sweep;
+            slots[idx].pos = r.pos;
+        }
+    }
+    flush_warp_z_stats(a.stats, st);
+}
+
+// The same for the long requests, one CTA of kCoopWarps warps each (the
+// cooperative z-step): active[0 .. n_active) are those slots.
+__global__ void __launch_bounds__(kCoopSlots, 7) k_serve_step_coop(ZArgs a, ServeSlot *slots, const int32_t *active,
+                                                                     int n_active, const int32_t *arena_w,
+                                                                     int16_t *arena_z, int64_t slice, int *work,
+                                                                     uint64_t window_ns) {
+    extern __shared__ uint32_t zsm[];
+    CoopXch &x = *reinterpret_cast<CoopXch *>(zsm + z_m_words(a.K) + 32 * kTokRecWords);
+    ZCount st;
+    for (;;) {
+        __syncthreads();          // every thread has read the previous item and its deadline
+        if (threadIdx.x == 0) {
+            x.item = atomicAdd(work, 1);
+            x.tot[0] = window_ns ? global_ns() + window_ns : ~0ull;
+        }
+        __syncthreads();
+        const int item = x.item;
+        const uint64_t deadline = x.tot[0];
+        if (item >= n_active) break;
+        const int idx = active[item];
+        const ServeSlot sl = slots[idx];
+        int16_t *z = arena_z + sl.off;
+        uint32_t sweep = sl.sweep;
+        int pos = sl.pos;
+        if (sweep == 0) {
+            for (int i = threadIdx.x; i < sl.len; i += kCoopSlots) {
+                const U4 u = draw(sl.seed, static_cast<uint32_t>(i), 0u, 0u, TAG_INIT, 0);
+                z[i] = static_cast<int16_t>(__umulhi(u.x, static_cast<uint32_t>(a.K)));
+            }
+            __syncthreads();
+            sweep = 1;
+            pos = 0;
+        }
+        DocRun r{arena_w + sl.off, z, sl.len, sl.seed, 0, sweep, pos, slice,
+                 static_cast<int>(sl.sweep_end - sweep), deadline};
+        z_doc_coop(a, zsm, r, st);
+        if (threadIdx.x == 0) {
             slots[idx].sweep = r.sweep;
             slots[idx].pos = r.pos;
         }
@@ -1773,12 +1845,29 @@ int batch_z_blocks_per_sm(int kmax, int warps) {
 }
 
 void launch_serve_step(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active, const int32_t *arena_w,
-                       int16_t *arena_z, int64_t slice, int *work, int warps_per_block, int grid, cudaStream_t st) {
+                       int16_t *arena_z, int64_t slice, int *work, int warps_per_block, int grid, uint64_t window_ns,
+                       cudaStream_t st) {
     if (n_active <= 0) return;
     cudaMemsetAsync(work, 0, sizeof(int), st);
     const int need = (n_active + warps_per_block - 1) / warps_per_block;
     k_serve_step<<<std::min(grid, need), 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(
-        a, slots, active, n_active, arena_w, arena_z, slice, work);
+        a, slots, active, n_active, arena_w, arena_z, slice, work, window_ns);
+}
+
+void launch_serve_step_coop(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active,
+                            const int32_t *arena_w, int16_t *arena_z, int64_t slice, int *work, int grid,
+                            uint64_t window_ns, cudaStream_t st) {
+    if (n_active <= 0) return;
+    cudaMemsetAsync(work, 0, sizeof(int), st);
+    k_serve_step_coop<<<std::max(1, std::min(grid, n_active)), kCoopSlots, z_coop_smem(a.K), st>>>(
+        a, slots, active, n_active, arena_w, arena_z, slice, work, window_ns);
+}
+
+int serve_coop_blocks_per_sm(int K) {
+    allow_dynamic_smem(k_serve_step_coop);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_serve_step_coop, kCoopSlots, z_coop_smem(K));
+    return n > 0 ? n : 1;
 }
 
 int serve_blocks_per_sm(int K, int warps_per_block) {

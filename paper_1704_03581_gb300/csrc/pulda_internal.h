@@ -253,9 +253,21 @@ struct ServeSlot {
     uint32_t sweep_end;   // 1 + sweeps requested: done when sweep reaches it
     uint64_t seed;        // the request's Philox key
 };
+// Each active slot advances by up to `slice` tokens, one warp per slot; with
+// window_ns > 0 also stopping at the first 32-token block boundary window_ns
+// after the launch starts (every slot does at least one block).
 void launch_serve_step(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active, const int32_t *arena_w,
-                       int16_t *arena_z, int64_t slice, int *work, int warps_per_block, int grid, cudaStream_t st);
+                       int16_t *arena_z, int64_t slice, int *work, int warps_per_block, int grid, uint64_t window_ns,
+                       cudaStream_t st);
 int serve_blocks_per_sm(int K, int warps_per_block);
+// The same with one CTA (the cooperative z-step) per slot, for long requests.
+void launch_serve_step_coop(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active,
+                            const int32_t *arena_w, int16_t *arena_z, int64_t slice, int *work, int grid,
+                            uint64_t window_ns, cudaStream_t st);
+int serve_coop_blocks_per_sm(int K);
+// Requests at least this long are served by the cooperative kernel when the
+// handle's coop_min_len is 0 (automatic).
+constexpr int64_t kServeCoopAuto = 1024;
 
 // What another translation unit needs to launch the z-step on a handle's
 // current Phi (api.cpp).

@@ -3,8 +3,11 @@
 // arrive.  A worker thread owns the GPU side: it admits waiting requests while
 // a slot and a contiguous range of the token arena are free (memory-based
 // admission, first come first served), advances every admitted request by up
-// to `slice` tokens per launch -- one warp per request, passes continuing
-// within the launch -- and hands finished requests back.  Each request's
+// to `slice` tokens per launch -- one warp per request (one CTA of the
+// cooperative z-step per long request, on a second stream), passes continuing
+// within the launch -- and hands finished requests back.  With the automatic
+// slice a launch instead runs every request for a 2 ms window, so each
+// advances as far as its own speed allows.  Each request's
 // random streams are keyed by its own seed and token positions, so its result
 // does not depend on which other requests shared the GPU with it: it equals
 // pulda_infer on that document alone.
@@ -73,16 +76,23 @@ private:
 };
 
 constexpr size_t kMaxPending = size_t(1) << 22;
+#ifndef PULDA_SERVE_COOP_GATE
+#define PULDA_SERVE_COOP_GATE 8
+#endif
+constexpr int64_t kServeCoopGate = PULDA_SERVE_COOP_GATE;   // cooperative while n_active * this <= resident warps
 
 }  // namespace
 
 struct pulda_server {
     pulda_handle *h = nullptr;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr, stream2 = nullptr;   // the cooperative launch, the one-warp launch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t budget = 0, slice = 0;
+    int64_t coop_len = 0;                 // requests at least this long go to the cooperative kernel (0 = none)
+    uint64_t window_ns = 0;               // automatic slice: the launch's time window
     int32_t max_slots = 0;
-    int z_warps = 8, grid = 1;
+    int z_warps = 8, grid = 1, coop_grid = 1;
     ZArgs tabs{};
     // device state
     int32_t *arena_w = nullptr;
@@ -94,6 +104,7 @@ struct pulda_server {
     ServeSlot *h_slots = nullptr;        // pinned: slot states read back after each launch
     ServeSlot *h_new = nullptr;          // pinned: entries of newly admitted slots
     int32_t *h_active = nullptr;         // pinned: the active list of the next launch
+    std::vector<int32_t> h_slots_len;    // tokens of each slot's request
     int32_t *pin_w = nullptr;            // pinned mirror of the arena's word ids
     int16_t *pin_z = nullptr;            // pinned mirror of the arena's topics
     bool auto_slice = false;
@@ -138,6 +149,7 @@ void admit_locked(pulda_server *s, std::vector<int32_t> &newly) {
         r.off = off;
         std::memcpy(s->pin_w + off, r.words.data(), sizeof(int32_t) * len);
         s->h_new[slot] = ServeSlot{off, static_cast<int32_t>(len), 0, 0, static_cast<uint32_t>(1 + r.n_sweeps), r.seed};
+        s->h_slots_len[slot] = static_cast<int32_t>(len);
         s->slot_req[slot] = std::move(r);
         s->pending.pop_front();
         newly.push_back(slot);
@@ -175,12 +187,35 @@ void worker_loop(pulda_server *s) {
         for (int32_t slot : newly) s->active.push_back(slot);
         newly.clear();
         const int n = static_cast<int>(s->active.size());
-        std::memcpy(s->h_active, s->active.data(), sizeof(int32_t) * n);
+        // long requests first (the cooperative kernel's), then the others.  A
+        // cooperative token costs about four times the issue slots of a
+        // one-warp token, which pays while the SMs have idle issue slots: only
+        // while the active requests fill at most an eighth of the resident warps
+        // (measured: at a quarter, 20k requests/s doubled p50).
+        const bool coop = s->coop_len > 0 &&
+                          static_cast<int64_t>(n) * kServeCoopGate <= static_cast<int64_t>(s->grid) * s->z_warps;
+        int nc = 0;
+        for (int32_t slot : s->active)
+            if (coop && s->h_slots_len[slot] >= s->coop_len) s->h_active[nc++] = slot;
+        int j = nc;
+        for (int32_t slot : s->active)
+            if (!(coop && s->h_slots_len[slot] >= s->coop_len)) s->h_active[j++] = slot;
         if (!check(s, cudaMemcpyAsync(s->d_active, s->h_active, sizeof(int32_t) * n, cudaMemcpyHostToDevice,
                                       s->stream), "upload of the active list")) return;
         cudaEventRecord(s->ev0, s->stream);
-        launch_serve_step(s->tabs, s->d_slots, s->d_active, n, s->arena_w, s->arena_z, s->slice, s->d_work,
-                          s->z_warps, s->grid, s->stream);
+        if (nc > 0) {
+            cudaEventRecord(s->ev_fork, s->stream);
+            launch_serve_step_coop(s->tabs, s->d_slots, s->d_active, nc, s->arena_w, s->arena_z, s->slice,
+                                   s->d_work + 1, s->coop_grid, s->window_ns, s->stream);
+            cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
+            launch_serve_step(s->tabs, s->d_slots, s->d_active + nc, n - nc, s->arena_w, s->arena_z, s->slice,
+                              s->d_work, s->z_warps, s->grid, s->window_ns, s->stream2);
+            cudaEventRecord(s->ev_join, s->stream2);
+            cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+        } else {
+            launch_serve_step(s->tabs, s->d_slots, s->d_active, n, s->arena_w, s->arena_z, s->slice, s->d_work,
+                              s->z_warps, s->grid, s->window_ns, s->stream);
+        }
         if (!check(s, cudaGetLastError(), "serving launch")) return;
         cudaEventRecord(s->ev1, s->stream);
         if (!check(s, cudaMemcpyAsync(s->h_slots, s->d_slots, sizeof(ServeSlot) * s->max_slots, cudaMemcpyDeviceToHost,
@@ -197,14 +232,6 @@ void worker_loop(pulda_server *s) {
         s->ctr[0] += 1;
         s->ctr[4] += static_cast<int64_t>(kms * 1e6);
         s->ctr[6] = std::max<int64_t>(s->ctr[6], n);
-        if (s->auto_slice) {
-            // aim at launches of about 2 ms: long enough to amortise the loop,
-            // short enough that new requests start soon
-            const double target = 2.0;
-            double next = static_cast<double>(s->slice) * target / std::max(0.05, static_cast<double>(kms));
-            next = std::min(std::max(next, 0.5 * s->slice), 2.0 * s->slice);
-            s->slice = std::min<int64_t>(std::max<int64_t>(static_cast<int64_t>(next), 64), 1 << 16);
-        }
         s->ctr[5] = s->slice;
         finished.clear();
         still.clear();
@@ -261,12 +288,21 @@ pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max
     if (token_budget < 1 || max_slots < 1 || slice_tokens < 0)
         return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID,
                                                      "token_budget and max_slots must be >= 1, slice_tokens >= 0"));
+    // the server's launches run on its own streams: the sweeps still queued on
+    // the handle's stream must have written Phi and its tables first
+    const pulda_status ready = pulda_sync(h);
+    if (ready != PULDA_OK) return ready;
     pulda_server *s = new pulda_server();
     s->h = h;
     s->budget = token_budget;
     s->auto_slice = slice_tokens == 0;
-    s->slice = slice_tokens == 0 ? 1024 : slice_tokens;
+    // automatic: launches of about 2 ms (long enough to amortise the loop,
+    // short enough that new requests start soon), however far each request gets
+    s->slice = slice_tokens == 0 ? (int64_t(1) << 22) : slice_tokens;
+    s->window_ns = slice_tokens == 0 ? 2000000ull : 0ull;
+    s->coop_len = h->opt.coop_min_len < 0 ? 0 : (h->opt.coop_min_len > 0 ? h->opt.coop_min_len : kServeCoopAuto);
     s->max_slots = max_slots;
+    s->h_slots_len.assign(max_slots, 0);
     s->arena = Arena(token_budget);
     s->slot_req.resize(max_slots);
     for (int32_t i = max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
@@ -278,6 +314,10 @@ pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max
     };
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) { delete s; return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_CUDA, "stream creation failed")); }
+    if ((e = cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking)) != cudaSuccess) return bad(e, "stream creation failed");
+    if ((e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+        return bad(e, "event creation failed");
     if ((e = cudaMalloc(&s->arena_w, sizeof(int32_t) * token_budget)) != cudaSuccess) return bad(e, "arena allocation failed");
     if ((e = cudaMalloc(&s->arena_z, sizeof(int16_t) * token_budget)) != cudaSuccess) return bad(e, "arena allocation failed");
     if ((e = cudaMalloc(&s->d_slots, sizeof(ServeSlot) * max_slots)) != cudaSuccess) return bad(e, "slot table allocation failed");
@@ -301,6 +341,7 @@ pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     s->grid = sms * serve_blocks_per_sm(hv.K, hv.z_warps);
+    s->coop_grid = sms * serve_coop_blocks_per_sm(hv.K);
     if ((e = cudaGetLastError()) != cudaSuccess) return bad(e, "set-up failed");
     s->worker = std::thread(worker_loop, s);
     *out = s;
@@ -385,6 +426,7 @@ pulda_status pulda_serve_close(pulda_server *s) {
     if (s->worker.joinable()) s->worker.join();
     pulda_status st = s->err_status;
     if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->stream2) cudaStreamSynchronize(s->stream2);
     cudaFree(s->arena_w);
     cudaFree(s->arena_z);
     cudaFree(s->d_slots);
@@ -398,6 +440,9 @@ pulda_status pulda_serve_close(pulda_server *s) {
     if (s->pin_z) cudaFreeHost(s->pin_z);
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    if (s->stream2) cudaStreamDestroy(s->stream2);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return st;

@@ -38,7 +38,7 @@ def requests(c, n, rng):
     return out
 
 
-@pytest.mark.parametrize("budget,slots,slice_", [(3000, 8, 64), (10000, 64, 4096), (3000, 3, 1)])
+@pytest.mark.parametrize("budget,slots,slice_", [(3000, 8, 64), (10000, 64, 4096), (3000, 3, 1), (10000, 64, 0)])
 def test_mixed_requests_equal_each_alone(trained, budget, slots, slice_):
     P, s, ch, c = trained
     rng = np.random.default_rng(budget + slots + slice_)
@@ -99,3 +99,36 @@ def test_invalid_submissions(trained):
         with pytest.raises(P.PuldaError):
             srv.submit(1, 1, words, sweeps)
     srv.close()
+
+
+@pytest.mark.parametrize("coop,slice_", [(40, 0), (40, 33), (-1, 0)])
+def test_cooperative_requests_equal_each_alone(trained, coop, slice_):
+    """Requests of at least `coop` tokens on CTAs of the cooperative z-step while
+    the others run one per warp on the second stream; the 2 ms window (slice 0)
+    or 33-token slices split their sweeps across launches."""
+    P, s0, ch, c = trained
+    s = P.Sampler(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=3, coop_min_len=coop).sweep(3)
+    rng = np.random.default_rng(7 + coop + slice_)
+    reqs = requests(c, 30, rng)
+    srv = P.Server(s, token_budget=20000, max_slots=32, slice_tokens=slice_)
+    for r in reqs:
+        srv.submit(r["id"], r["seed"], r["words"], r["sweeps"])
+    got = {}
+    t0 = time.time()
+    while len(got) < len(reqs):
+        for res in srv.poll(timeout_ms=200):
+            assert res["status"] == 0
+            got[res["req_id"]] = res["z"]
+        assert time.time() - t0 < 120, "server made no progress"
+    srv.close()
+    for r in reqs:
+        alone = s0.infer(r["words"], np.array([0, len(r["words"])]), r["sweeps"], seed=r["seed"])
+        if not np.array_equal(got[r["id"]], alone):
+            zo = O.infer(ch.tables, r["words"], np.array([0, len(r["words"])]), r["sweeps"], r["seed"])
+            raise AssertionError(f"request {r['id']} ({len(r['words'])} tokens, {r['sweeps']} sweeps) differs from "
+                                 f"its run alone; served == oracle: {np.array_equal(got[r['id']], zo)}, "
+                                 f"alone == oracle: {np.array_equal(alone, zo)}")
+    for r in reqs[:4]:
+        zo = O.infer(ch.tables, r["words"], np.array([0, len(r["words"])]), r["sweeps"], r["seed"])
+        assert np.array_equal(got[r["id"]], zo)
+    s.close()
