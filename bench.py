@@ -553,10 +553,11 @@ def run_batched(args):
     N = sum(c.N for c in corpora)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    K, W = args.steps, max(args.warmup, 3)
-    b = P.Batch(chains, stream=stream.cuda_stream)
+    K, W = args.steps, max(args.warmup, 6)
+    b = P.Batch(chains, stream=stream.cuda_stream, coop_min_len=args.coop_min_len)
     b.sweep(W)                          # the first sweeps also time the tuning candidates
     b.sync()
+    assert b.tuning()[2], "tuning not over after the warm-up sweeps"
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -569,7 +570,7 @@ def run_batched(args):
     b.sync()
     ms_b = e0.elapsed_time(e1)
     zb = [b.z(i) for i in range(len(chains))]
-    warps, _ = b.tuning()
+    warps, coop_len, _ = b.tuning()
     b.close()
     # the same chains, one after another, one handle each
     singles = [P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"],
@@ -593,11 +594,12 @@ def run_batched(args):
         "ms_per_step": ms_b / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"32 chains, D scaled by {args.batch_scale}", "N": N,
-                   "K": sorted({sp['K'] for sp in specs}), "z_warps_tuned": warps},
+                   "K": sorted({sp['K'] for sp in specs}), "z_warps_tuned": warps,
+                   "coop_min_len_tuned": coop_len},
         "sequential": {"value": N * K / (ms_s / 1000.0), "ms_per_step": ms_s / K},
         "speedup_vs_sequential": ms_s / ms_b,
         "identical_topics": same,
-        "gpu_launches": 6 * K,
+        "gpu_launches": (6 + (1 if coop_len > 0 else 0)) * K,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -247,7 +247,11 @@ typedef struct pulda_batch pulda_batch;
 /* pulda_batch_init -- validate and set up every chain as pulda_init would
  * (same limits and errors, reported with the chain's index).  opt->stream, if
  * set, is used for all chains; opt->warps_per_block in 1..8 fixes the z-step
- * CTA size instead of tuning it over {2, 4, 8}; docs_per_warp must be 0 or 1. */
+ * CTA size instead of tuning it over {2, 4, 8}; opt->coop_min_len -1 keeps
+ * every document on one warp, > 0 sends the documents at least that long (of
+ * every chain) to the cooperative z-step, 0 tunes it: after the CTA sizes, the
+ * first sweeps also time the thresholds max(256, N / 6000) and a quarter of it
+ * (N = tokens of all chains) against none; docs_per_warp must be 0 or 1. */
 pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains, int32_t n_chains,
                               const pulda_options *opt);
 /* pulda_batch_sweep -- n_sweeps sweeps of every chain (asynchronous, except
@@ -258,8 +262,10 @@ pulda_status pulda_batch_sync(pulda_batch *b);
  * chain `chain` (0-based); PULDA_ERR_INVALID if out of range. */
 pulda_status pulda_batch_get_z(pulda_batch *b, int32_t chain, int16_t *z_host);
 pulda_status pulda_batch_stats(pulda_batch *b, int32_t chain, pulda_sweep_stats *out);
-/* pulda_batch_tuning -- the z-step warps per CTA in use and whether tuning is over. */
-pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *tuned);
+/* pulda_batch_tuning -- the z-step warps per CTA and the cooperative
+ * threshold in use (-1 = none), and whether tuning is over; any pointer may
+ * be NULL. */
+pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *coop_min_len, int32_t *tuned);
 /* pulda_batch_last_error -- as pulda_last_error; NULL = last failed pulda_batch_init. */
 const char *pulda_batch_last_error(const pulda_batch *b);
 void pulda_batch_free(pulda_batch *b);

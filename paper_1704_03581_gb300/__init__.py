@@ -90,7 +90,7 @@ def lib() -> ctypes.CDLL:
             "pulda_batch_sync": [P],
             "pulda_batch_get_z": [P, i32, P],
             "pulda_batch_stats": [P, i32, P],
-            "pulda_batch_tuning": [P, P, P],
+            "pulda_batch_tuning": [P, P, P, P],
             "pulda_serve_open": [P, i64, i32, i64, P],
             "pulda_serve_submit": [P, u64, u64, P, i32, i32, P],
             "pulda_serve_poll": [P, P, i32, P, i32],
@@ -343,8 +343,8 @@ def _bcheck(b, status: int):
         raise PuldaError(status, msg.decode() if msg else "")
 
 
-def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0):
-    """chains: dicts with w, doc_off, K, V, alpha, beta, seed."""
+def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0):
+    """chains: dicts with w, doc_off, K, V, alpha, beta, seed.  coop_min_len: 0 tuned, -1 never, > 0 fixed."""
     keep = []
     arr = (ChainDesc * len(chains))()
     for i, c in enumerate(chains):
@@ -357,6 +357,7 @@ def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0):
     opt = Options()
     opt.stream = stream
     opt.warps_per_block = warps_per_block
+    opt.coop_min_len = coop_min_len
     b = ctypes.c_void_p()
     _bcheck(None, lib().pulda_batch_init(ctypes.byref(b), arr, len(chains), ctypes.byref(opt)))
     return b.value
@@ -381,10 +382,11 @@ def pulda_batch_stats(b, chain: int) -> dict:
     return s.as_dict()
 
 
-def pulda_batch_tuning(b) -> tuple[int, bool]:
-    w, t = ctypes.c_int32(0), ctypes.c_int32(0)
-    _bcheck(b, lib().pulda_batch_tuning(b, ctypes.byref(w), ctypes.byref(t)))
-    return w.value, bool(t.value)
+def pulda_batch_tuning(b) -> tuple[int, int, bool]:
+    """(z-step warps per CTA, cooperative threshold or -1, tuning over)."""
+    w, c, t = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    _bcheck(b, lib().pulda_batch_tuning(b, ctypes.byref(w), ctypes.byref(c), ctypes.byref(t)))
+    return w.value, c.value, bool(t.value)
 
 
 def pulda_batch_last_error(b) -> str:
@@ -400,9 +402,9 @@ def pulda_batch_free(b):
 class Batch:
     """Many chains advanced together: ``Batch(chains).sweep(n)``."""
 
-    def __init__(self, chains: list[dict], stream=None, warps_per_block: int = 0):
+    def __init__(self, chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0):
         self.sizes = [int(np.asarray(c["doc_off"])[-1]) for c in chains]
-        self.b = pulda_batch_init(chains, stream, warps_per_block)
+        self.b = pulda_batch_init(chains, stream, warps_per_block, coop_min_len)
 
     def close(self):
         if self.b:

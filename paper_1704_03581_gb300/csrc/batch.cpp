@@ -24,9 +24,16 @@ struct pulda_batch {
     BatchLaunch bl{};
     int sms = 1;
     int64_t sweep = 0;
-    std::vector<int> cand;          // z-step warps per CTA to try
+    // tuning candidates (z-step warps per CTA, cooperative threshold; 0 = none),
+    // timed on real sweeps: first the CTA sizes, then thresholds at the best size
+    struct Cand { int warps; int64_t coop_len; };
+    std::vector<Cand> cand;
     std::vector<float> cand_ms;
+    std::vector<int64_t> coop_try;  // thresholds for the second phase
     bool tuned = false;
+    bool phase2 = false;
+    int64_t coop_len = 0;           // in use
+    std::vector<int64_t> dlen;      // document lengths in work-list order (longest first)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -57,6 +64,21 @@ cudaError_t balloc(pulda_batch *b, T **p, size_t n) {
 }
 
 thread_local std::string g_batch_init_error;
+
+// Documents the cooperative z-step takes at threshold L (the work list is longest first).
+int count_coop_items(const pulda_batch *b, int64_t L) {
+    if (L <= 0) return 0;
+    int n = 0;
+    while (n < static_cast<int>(b->dlen.size()) && b->dlen[n] >= L) ++n;
+    return n;
+}
+
+void apply_candidate(pulda_batch *b, const pulda_batch::Cand &c) {
+    b->bl.z_warps = c.warps;
+    b->bl.z_grid = b->sms * batch_z_blocks_per_sm(b->bl.kmax, c.warps);
+    b->coop_len = c.coop_len;
+    b->bl.n_coop = count_coop_items(b, c.coop_len);
+}
 
 pulda_status launch_one_sweep(pulda_batch *b) {
     launch_batch_sweep(b->bl, b->stream);
@@ -97,8 +119,8 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = "batched chains resample every document in order (slice_len must be 0)";
         return bail(PULDA_ERR_INVALID);
     }
-    if (o.coop_min_len > 0 || o.coop_min_len < -1) {
-        b->err = "batched chains run each document on one warp (coop_min_len must be 0 or -1)";
+    if (o.coop_min_len < -1) {
+        b->err = "coop_min_len must be -1 (never), 0 (tuned) or a length";
         return bail(PULDA_ERR_INVALID);
     }
     if (o.warps_per_block < 0 || o.warps_per_block > kMultiWarps) {
@@ -121,6 +143,7 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     // own kernel, whose CTA size is o.warps_per_block or tuned
     pulda_options oc = o;
     oc.warps_per_block = 0;
+    oc.coop_min_len = -1;
     for (int32_t c = 0; c < n_chains; ++c) {
         const pulda_chain_desc &d = chains[c];
         pulda_handle *h = nullptr;
@@ -178,6 +201,12 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     std::vector<int2> wlist(wi.size()), dlist(di.size());
     for (size_t i = 0; i < wi.size(); ++i) wlist[i] = wi[i].second;
     for (size_t i = 0; i < di.size(); ++i) dlist[i] = di[i].second;
+    b->dlen.resize(di.size());
+    int64_t n_tokens = 0;
+    for (size_t i = 0; i < di.size(); ++i) {
+        b->dlen[i] = di[i].first;
+        n_tokens += di[i].first;
+    }
     int2 *d_wl = nullptr, *d_dl = nullptr;
     HeavyChunk *d_heavy = nullptr;
     if (balloc(b, &d_wl, wlist.size()) != cudaSuccess || balloc(b, &d_dl, dlist.size()) != cudaSuccess ||
@@ -212,16 +241,29 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     bl.work = d_work;
     bl.kmax = kmax;
     bl.phi_grid = b->sms * batch_phi_blocks_per_sm(kmax);
-    for (int w : {2, 4, 8})
-        if (w <= kMultiWarps && z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back(w);
-    if (b->cand.empty()) b->cand.push_back(1);
-    if (o.warps_per_block > 0) {
-        b->cand.assign(1, o.warps_per_block);
-        b->tuned = true;
+    bl.coop_grid = b->sms * batch_coop_blocks_per_sm(kmax);
+    // cooperative thresholds: fixed, none, or tuned over the automatic rule of
+    // the single-chain z-step (documents that would outlast the pass on one
+    // warp) and a quarter of it
+    const int64_t fixed_coop = o.coop_min_len > 0 ? o.coop_min_len : 0;
+    if (o.coop_min_len == 0) {
+        const int64_t L1 = std::max<int64_t>(kCoopAutoMin, n_tokens / kCoopAutoDiv + 1);
+        for (int64_t L : {L1, std::max<int64_t>(kCoopAutoMin, L1 / 4)})
+            if (count_coop_items(b, L) > 0 && (b->coop_try.empty() || b->coop_try.back() != L)) b->coop_try.push_back(L);
     }
-    bl.z_warps = b->cand.front();
-    bl.z_grid = b->sms * batch_z_blocks_per_sm(kmax, bl.z_warps);
+    if (o.warps_per_block > 0) {
+        b->cand.push_back({o.warps_per_block, fixed_coop});
+    } else {
+        for (int w : {2, 4, 8})
+            if (w <= kMultiWarps && z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back({w, fixed_coop});
+        if (b->cand.empty()) b->cand.push_back({1, fixed_coop});
+    }
+    if (b->cand.size() == 1 && b->coop_try.empty()) b->tuned = true;
+    apply_candidate(b, b->cand.front());
     if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&bl.stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bl.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&bl.ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaGetLastError() != cudaSuccess) {
         b->err = "CUDA set-up of the batch failed";
         return bail(PULDA_ERR_CUDA);
@@ -236,9 +278,7 @@ pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps) {
     for (int32_t s = 0; s < n_sweeps; ++s) {
         if (!b->tuned) {
             // time the next candidate on a real sweep
-            const int w = b->cand[b->cand_ms.size()];
-            b->bl.z_warps = w;
-            b->bl.z_grid = b->sms * batch_z_blocks_per_sm(b->bl.kmax, w);
+            apply_candidate(b, b->cand[b->cand_ms.size()]);
             BCU(b, cudaEventRecord(b->ev0, b->stream));
             pulda_status r = launch_one_sweep(b);
             if (r != PULDA_OK) return r;
@@ -249,9 +289,14 @@ pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps) {
             b->cand_ms.push_back(ms);
             if (b->cand_ms.size() == b->cand.size()) {
                 const size_t best = std::min_element(b->cand_ms.begin(), b->cand_ms.end()) - b->cand_ms.begin();
-                b->bl.z_warps = b->cand[best];
-                b->bl.z_grid = b->sms * batch_z_blocks_per_sm(b->bl.kmax, b->bl.z_warps);
-                b->tuned = true;
+                if (!b->phase2 && !b->coop_try.empty()) {
+                    // second phase: the cooperative thresholds at the best CTA size
+                    b->phase2 = true;
+                    for (int64_t L : b->coop_try) b->cand.push_back({b->cand[best].warps, L});
+                } else {
+                    apply_candidate(b, b->cand[best]);
+                    b->tuned = true;
+                }
             }
         } else {
             if (!b->exec) {
@@ -298,9 +343,10 @@ pulda_status pulda_batch_stats(pulda_batch *b, int32_t chain, pulda_sweep_stats 
     return PULDA_OK;
 }
 
-pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *tuned) {
+pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *coop_min_len, int32_t *tuned) {
     if (!b) return PULDA_ERR_INVALID;
     if (z_warps) *z_warps = b->bl.z_warps;
+    if (coop_min_len) *coop_min_len = static_cast<int32_t>(b->coop_len > 0 ? b->coop_len : -1);
     if (tuned) *tuned = b->tuned ? 1 : 0;
     return PULDA_OK;
 }
@@ -314,6 +360,12 @@ void pulda_batch_free(pulda_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->bl.stream2) {
+        cudaStreamSynchronize(b->bl.stream2);
+        cudaStreamDestroy(b->bl.stream2);
+    }
+    if (b->bl.ev_fork) cudaEventDestroy(b->bl.ev_fork);
+    if (b->bl.ev_join) cudaEventDestroy(b->bl.ev_join);
     for (pulda_handle *h : b->ch) pulda_free(h);
     for (void *p : b->allocs) cudaFree(p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);

@@ -1237,6 +1237,30 @@ __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_m
     }
 }
 
+// Many chains: the longest documents of every chain, one CTA each (the
+// cooperative z-step); items[0 .. n_items) are (chain, document) pairs.
+__global__ void __launch_bounds__(kCoopSlots, PULDA_ZMINBLOCKS) k_z_step_coop_multi(const ZArgs *chains,
+                                                                                   const int2 *items, int n_items,
+                                                                                   int *work, int kmax) {
+    extern __shared__ uint32_t zsm[];
+    int *item_sh = reinterpret_cast<int *>(zsm + z_coop_words(kmax));    // beyond every chain's layout
+    for (;;) {
+        if (threadIdx.x == 0) *item_sh = atomicAdd(work, 1);
+        __syncthreads();
+        const int item = *item_sh;
+        __syncthreads();
+        if (item >= n_items) break;
+        const int2 it = items[item];
+        const ZArgs &a = chains[it.x];
+        const int64_t s = a.doc_off[it.y];
+        const int len = static_cast<int>(a.doc_off[it.y + 1] - s);
+        DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep_of(a), 0, len, 1};
+        ZCount st;
+        z_doc_coop(a, zsm, r, st);
+        flush_warp_z_stats(a.stats, st);
+    }
+}
+
 // ============================================================== z-step, grouped
 // Eight lanes per document, four documents per warp.  The per-token work of
 // the warp-per-document kernel is dominated by what every token costs
@@ -1826,8 +1850,30 @@ void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
     k_phi_fixup_multi<<<b.n_chains, kFixBlock, 0, st>>>(b.phi);
     k_colptr_scan_multi<<<b.n_chains, 1024, 0, st>>>(b.phi);
     launch_phi_tables_multi(b.phi, b.phi_items, b.n_phi_items, st);
-    k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), st>>>(
-        b.z, b.z_items, b.n_z_items, b.work + 1, b.kmax);
+    if (b.n_coop > 0) {
+        // the longest documents on CTAs, the rest one per warp beside them
+        cudaEventRecord(b.ev_fork, st);
+        k_z_step_coop_multi<<<std::max(1, std::min(b.coop_grid, b.n_coop)), kCoopSlots, z_coop_multi_smem(b.kmax), st>>>(
+            b.z, b.z_items, b.n_coop, b.work + 2, b.kmax);
+        cudaStreamWaitEvent(b.stream2, b.ev_fork, 0);
+        if (b.n_z_items > b.n_coop)
+            k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), b.stream2>>>(
+                b.z, b.z_items + b.n_coop, b.n_z_items - b.n_coop, b.work + 1, b.kmax);
+        cudaEventRecord(b.ev_join, b.stream2);
+        cudaStreamWaitEvent(st, b.ev_join, 0);
+    } else {
+        k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), st>>>(
+            b.z, b.z_items, b.n_z_items, b.work + 1, b.kmax);
+    }
+}
+
+size_t z_coop_multi_smem(int kmax) { return sizeof(uint32_t) * static_cast<size_t>(z_coop_words(kmax)) + 16; }
+
+int batch_coop_blocks_per_sm(int kmax) {
+    allow_dynamic_smem(k_z_step_coop_multi);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_z_step_coop_multi, kCoopSlots, z_coop_multi_smem(kmax));
+    return n > 0 ? n : 1;
 }
 
 int batch_phi_blocks_per_sm(int kmax) {

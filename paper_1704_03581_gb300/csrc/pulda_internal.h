@@ -239,10 +239,17 @@ struct BatchLaunch {
     int *work;                   // [4] dynamic work queues
     int kmax;                    // largest K of the chains
     int phi_grid, z_grid, z_warps;
+    // the first n_coop z_items go to the cooperative z-step on `st`, the rest
+    // to the one-warp kernel on stream2 (forked and joined with the events)
+    int n_coop, coop_grid;
+    cudaStream_t stream2;
+    cudaEvent_t ev_fork, ev_join;
 };
 void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st);
 int batch_phi_blocks_per_sm(int kmax);
 int batch_z_blocks_per_sm(int kmax, int warps);
+int batch_coop_blocks_per_sm(int kmax);
+size_t z_coop_multi_smem(int kmax);
 
 // A request being folded in by the server (device slot table entry).
 struct ServeSlot {

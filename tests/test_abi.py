@@ -78,7 +78,7 @@ def test_batch_rejects_bad_options_without_a_gpu():
     arr[0] = P.ChainDesc(P._ptr(w), P._ptr(off), 1, 3, 2, P._ptr(a), 0.01, 0)
     for field, value, frag in [("phi_mode", 1, b"phi_mode"), ("warps_per_block", 9, b"warps_per_block"),
                                ("docs_per_warp", 4, b"docs_per_warp"), ("slice_len", 64, b"slice_len"),
-                               ("coop_min_len", 100, b"coop_min_len")]:
+                               ("coop_min_len", -2, b"coop_min_len")]:
         opt = P.Options()
         setattr(opt, field, value)
         b = ctypes.c_void_p()

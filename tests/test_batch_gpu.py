@@ -36,15 +36,18 @@ def make_chains():
     return out
 
 
-@pytest.mark.parametrize("warps", [0, 4])
-def test_batch_equals_single_chains(warps):
+@pytest.mark.parametrize("warps,coop", [(0, 0), (4, -1), (4, 64), (2, 1)])
+def test_batch_equals_single_chains(warps, coop):
+    """CTA size tuned or fixed; the cooperative z-step tuned, off, or taking
+    every document of at least 64 tokens / every document."""
     import paper_1704_03581_gb300 as P
     chains = make_chains()
-    b = P.Batch(chains, warps_per_block=warps)
+    b = P.Batch(chains, warps_per_block=warps, coop_min_len=coop)
     b.sweep(2)
     b.sweep(4)            # tuning sweeps, then graph replays across two calls
-    w, tuned = b.tuning()
+    w, coop_len, tuned = b.tuning()
     assert tuned and w in (2, 4, 8)
+    assert coop_len == (coop if coop != 0 else coop_len) and (coop_len == -1 or coop_len >= 1)
     for i, c in enumerate(chains):
         s = P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"])
         s.sweep(6)
