@@ -161,9 +161,16 @@ def code_hash(text: str) -> str:
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
+# The sources the one-warp z-step kernel is compiled from.
+Z_STEP_SOURCES = ("kernels.cu", "zstep.cuh", "device_rng.cuh", "pulda_internal.h")
+
+
 def kernel_source_hash() -> str:
-    with open(os.path.join(ROOT, "paper_1704_03581_gb300", "csrc", "kernels.cu")) as f:
-        return code_hash(f.read())
+    text = []
+    for name in Z_STEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1704_03581_gb300", "csrc", name)) as f:
+            text.append(f.read())
+    return code_hash("\n".join(text))
 
 
 def recorded_profile() -> dict:
@@ -173,7 +180,7 @@ def recorded_profile() -> dict:
     try:
         with open(p) as f:
             rec = json.load(f)
-        if rec.get("kernels_cu_sha") == kernel_source_hash():
+        if rec.get("source_sha") == kernel_source_hash():
             return rec
     except Exception:
         pass

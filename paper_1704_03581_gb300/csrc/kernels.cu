@@ -17,7 +17,8 @@
 //                            doubly sparse a/b draw (k_slice_counts first
 //                            when long documents run in stale-count slices).
 // The *_multi kernels do the same over many chains; k_serve_step folds in
-// requests; Algorithm 1's Dirichlet Phi-step is in dirichlet.cu.
+// requests; the longest documents go to the cooperative z-step (one CTA per
+// document, coop.cu); Algorithm 1's Dirichlet Phi-step is in dirichlet.cu.
 // The arithmetic that decides any draw is integer or IEEE double with
 // explicit rounding, so results are independent of launch shapes.
 #include <algorithm>
@@ -25,11 +26,11 @@
 
 #include "device_rng.cuh"
 #include "pulda_internal.h"
+#include "zstep.cuh"
 
 namespace pulda {
 namespace {
 
-typedef unsigned long long u64;
 
 
 // ------------------------------------------------------- Phi-step draws
@@ -94,22 +95,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int *tmp /* >= BLOCK/32 + 
     return base + x - v;
 }
 
-__device__ __forceinline__ u64 warp_sum64(u64 v) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ u64 warp_incl_scan64(u64 v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const u64 y = __shfl_up_sync(0xFFFFFFFFu, v, o);
-        if (lane >= o) v += y;
-    }
-    return v;
-}
-
 // ================================================================= init
 __global__ void k_init_z(int64_t N, int K, uint64_t seed, int64_t base, int16_t *z) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < N;
@@ -164,7 +149,6 @@ constexpr int kPhiBlock = 256;
 // Sweep counter of a chain: from device memory when the launch is replayed
 // from a CUDA graph (one graph serves every sweep), else the launch value.
 __device__ __forceinline__ uint32_t sweep_of(const PhiArgs &a) { return a.sweep_ptr ? *a.sweep_ptr : a.sweep; }
-__device__ __forceinline__ uint32_t sweep_of(const ZArgs &a) { return a.sweep_ptr ? *a.sweep_ptr : a.sweep; }
 
 // One word v of one chain, by the whole CTA: histogram of the word's topics
 // -> n_{.,v}; compacted n column; when `draw`, the Poisson draws c_{.,v},
@@ -587,15 +571,7 @@ __global__ void k_phi_tables_multi(const PhiArgs *chains, const int2 *items, int
 #ifndef PULDA_ZMINBLOCKS
 #define PULDA_ZMINBLOCKS 8
 #endif
-// The document side (for a word with a dense q row) is iterated when
-// K_d * kDocRatio < K_v * 16: the paper's "iterate over the smaller" at 16.
-// Either side gives the same exact sums; the column side's topic -> m loads
-// depend on each other, which makes it the costlier side per element.
-#ifndef PULDA_ZDOCRATIO
-#define PULDA_ZDOCRATIO 16
-#endif
 constexpr int kGather = PULDA_ZGATHER;
-constexpr int kDocRatio = PULDA_ZDOCRATIO;
 
 // One warp per document (dynamically scheduled, longest first).  m_d lives
 // in shared memory as a dense count array; for K <= 1024 each lane also holds
@@ -612,72 +588,6 @@ constexpr int kDocRatio = PULDA_ZDOCRATIO;
 // depends only on the token (its word, Philox words, alias outcome, the
 // word's bitmap) is fetched ahead; the only loads on the critical path are
 // the q values of the intersection, issued together.
-// m_d is stored skewed, topic k at k + k/32, so the lanes of a warp reading
-// topics 32 l + b (lane l, bit b) hit distinct shared-memory banks.
-__host__ __device__ __forceinline__ int mi(int k) { return k + (k >> 5); }
-// Shared memory of one z-step warp, in 32-bit words: m_d (skewed, rounded up
-// to 16 bytes), then the staging records of the 32 tokens in flight.
-__host__ __device__ __forceinline__ int z_m_words(int K) { return (K + (K >> 5) + 1 + 3) & ~3; }
-constexpr int kTokRecWords = 9;     // two uint4 per token, and the offset of its word's dense q row
-__host__ __device__ __forceinline__ int z_warp_words(int K) { return z_m_words(K) + 32 * kTokRecWords; }
-
-// Counters of a z-step warp.  The warp-uniform ones are held one per lane
-// (lane j holds counter j), which keeps five 64-bit values out of every
-// lane's registers; the intersection size is summed per lane.
-// Counter order: tokens, a-branch draws, sum min(K_d,K_v), zero-mass tokens,
-// (lane 4 unused: sum |J| is `inter`), tokens with K_d < K_v.
-struct ZCount {
-    u64 mine = 0;     // this lane's warp-uniform counter
-    u64 inter = 0;    // this lane's share of sum |J|
-    __device__ __forceinline__ void add(int j, u64 x) {
-        if ((threadIdx.x & 31) == j) mine += x;
-    }
-};
-
-// One document's run: where its tokens live and where its Markov chain is.
-struct DocRun {
-    const int32_t *w;        // word ids, position 0 first
-    int16_t *z;              // topics, updated in place
-    int len;
-    uint64_t seed;
-    int64_t index_base;      // RNG index of position 0
-    uint32_t sweep;          // sweep counter of the pass that starts at `pos`
-    int pos;                 // first position to resample
-    int64_t budget;          // tokens to resample in this call (passes continue past the end)
-    int max_pass_end;        // stop when the pass counter reaches sweep + this many passes
-    uint64_t deadline = ~0ull;   // global timer (ns): no 32-token block starts after it, but the first
-};
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Stages what depends only on token i of run r (see z_doc_warp for the
-// record layout) and returns its current topic.
-__device__ __forceinline__ int stage_token(const ZArgs &a, const DocRun &r, int i, uint4 *rec2, uint32_t *drow) {
-    const int wv = r.w[i];
-    const int zo = r.z[i];
-    const uint64_t t = static_cast<uint64_t>(r.index_base + i);
-    const U4 x = draw(r.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), r.sweep, TAG_Z, 0);
-    const int64_t cb = a.col_ptr[wv];
-    const int nw = static_cast<int>(a.col_ptr[wv + 1] - cb);
-    const u64 Av = a.A[wv];
-    int ta = 0;
-    if (nw > 0) {
-        const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
-        ta = x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl];
-    }
-    rec2[0] = make_uint4(static_cast<uint32_t>(cb),
-                         static_cast<uint32_t>(static_cast<u64>(cb) >> 32) | (static_cast<uint32_t>(ta) << 16),
-                         static_cast<uint32_t>(Av), static_cast<uint32_t>(Av >> 32));
-    rec2[1] = make_uint4(x.x, x.y, static_cast<uint32_t>(wv), static_cast<uint32_t>(nw) | (static_cast<uint32_t>(zo) << 16));
-    const int ds = a.dense_slot ? a.dense_slot[wv] : -1;
-    *drow = ds >= 0 ? static_cast<uint32_t>(ds) * static_cast<uint32_t>(a.K) : 0xFFFFFFFFu;
-    return zo;
-}
-
 // Resamples the tokens of one document, by one warp, in position order,
 // pass after pass, until `budget` tokens are done or `max_pass_end` passes
 // have been completed.  m (K entries of shared memory) is rebuilt from the
@@ -885,34 +795,6 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
     }
 }
 
-// Adds a warp's z-step counters to the sweep's and the running totals.
-// c = {tokens, a-branch draws, sum min(K_d,K_v), zero-mass tokens,
-//      sum |J|, tokens with K_d < K_v}.
-__device__ void flush_z_stats(unsigned long long *stats, const u64 (&c)[6]) {
-    const int slot[6] = {ST_TOKENS, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_SUMINT, ST_DOCSIDE};
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        atomicAdd(&stats[slot[i]], c[i]);
-        atomicAdd(&stats[ST_COUNT + slot[i]], c[i]);
-    }
-}
-
-// The same from a warp running z_doc_warp: lanes 0-3 and 5 hold their
-// counters, sum |J| is summed over the lanes.  Every lane calls it.
-__device__ void flush_warp_z_stats(unsigned long long *stats, ZCount &c) {
-    const u64 inter = warp_sum64(c.inter);
-    const int lane = threadIdx.x & 31;
-    const int slot[6] = {ST_TOKENS, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_SUMINT, ST_DOCSIDE};
-    if (lane < 6) {
-        const u64 v = lane == 4 ? inter : c.mine;
-        if (v) {
-            atomicAdd(&stats[slot[lane]], v);
-            atomicAdd(&stats[ST_COUNT + slot[lane]], v);
-        }
-    }
-    c = ZCount{};
-}
-
 // One chain, one document per warp (dynamically scheduled, longest first),
 // one pass.
 __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
@@ -942,258 +824,6 @@ __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs
         }
         DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep, 0, len, 1};
         z_doc_warp(a, m, r, st, m0);
-    }
-    flush_warp_z_stats(a.stats, st);
-}
-
-// ============================================================== cooperative z-step
-// A document's tokens are strictly sequential, so on one warp the longest
-// documents outlast the rest of the z-step: a few microseconds per token
-// (every token waits on its q gathers, its scan and its draw in turn) times
-// thousands of tokens, while the other warps have long finished.  Here the
-// kCoopWarps warps of a CTA share one document, token by token.  The token's
-// intersection is split over the CTA's kCoopSlots lanes ("slots") in
-// ascending topic order: on the document side slot g owns the R consecutive
-// topics [g R, g R + R) (R the smallest power of two with 32 KW <= R slots),
-// on the column side a contiguous segment of the word's column.  Each slot
-// gathers its few q values at once, every warp scans its slots, the warps'
-// totals meet in shared memory (barrier A), and the slot whose prefix passes
-// the draw reads off the topic, updates m and publishes it (barrier B).  The
-// sums are the same exact integers in the same topic order as the one-warp
-// kernel's, so every draw, and every topic, is identical.
-constexpr int kCoopWarps = 4;
-constexpr int kCoopSlots = 32 * kCoopWarps;
-constexpr int kCoopGather = 4;     // document-side q loads per round
-
-struct CoopXch {
-    u64 tot[kCoopWarps];    // each warp's sum of q m over its slots (this token)
-    int kdp[kCoopWarps];    // each warp's share of K_d when the document starts
-    int item;               // the document the CTA takes next
-    int go;                 // thread 0's reading of the deadline for the next block
-    int knew;               // this token's new topic
-    uint32_t mkn;           // m^{-i} of the new topic, before the token is added back
-};
-// Shared memory of a cooperative CTA, in 32-bit words: m_d, the records of
-// 32 tokens, the exchange area.
-__host__ __device__ __forceinline__ int z_coop_words(int K) {
-    return z_m_words(K) + 32 * kTokRecWords + static_cast<int>((sizeof(CoopXch) + 15) / 16) * 4;
-}
-
-__device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = a.K;
-    uint32_t *m = sm;
-    uint4 *rec = reinterpret_cast<uint4 *>(sm + z_m_words(K));
-    uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);
-    CoopXch &x = *reinterpret_cast<CoopXch *>(drow_of + 32);
-    const bool use_bm = a.bitmap != nullptr && a.path != 1;
-    int R = 1;
-    while (32 * a.KW > R * kCoopSlots) R <<= 1;
-    const bool own = use_bm && tid < 32 * a.KW / R;      // this slot owns topics on the document side
-    const int wi = own ? (tid * R) >> 5 : 0;              // its bitmap word
-    const int sh = (tid * R) & 31;
-    const uint32_t mask = own ? (R >= 32 ? 0xFFFFFFFFu : ((1u << R) - 1u) << sh) : 0u;
-    if (r.len == 0 || r.budget <= 0) return;
-    for (int k = tid; k < K; k += kCoopSlots) m[mi(k)] = 0;
-    __syncthreads();
-    for (int i = tid; i < r.len; i += kCoopSlots) atomicAdd(&m[mi(r.z[i])], 1u);
-    __syncthreads();
-    uint32_t mb = 0;        // this slot's bits of m_d's nonzero topics
-    int c = 0;
-    if (use_bm) {
-        for (int t = 0; t < R && own; ++t) {
-            const int k = wi * 32 + sh + t;
-            if (k < K && m[mi(k)] > 0) mb |= 1u << (sh + t);
-        }
-        c = __popc(mb);
-    } else {
-        for (int k = tid; k < K; k += kCoopSlots) c += m[mi(k)] > 0 ? 1 : 0;
-    }
-    c = __reduce_add_sync(0xFFFFFFFFu, c);
-    if (lane == 0) x.kdp[warp] = c;
-    __syncthreads();
-    int kd = 0;
-#pragma unroll
-    for (int j = 0; j < kCoopWarps; ++j) kd += x.kdp[j];
-    const uint32_t *bits = reinterpret_cast<const uint32_t *>(a.bitmap);
-    const uint32_t sweep_end = r.sweep + static_cast<uint32_t>(r.max_pass_end);
-    bool first = true;
-    while (r.budget > 0 && r.sweep != sweep_end) {
-        const int i0 = r.pos;
-        const int cnt = static_cast<int>(min(static_cast<int64_t>(32), min(static_cast<int64_t>(r.len - i0), r.budget)));
-        if (tid == 0) x.go = r.deadline == ~0ull || first || global_ns() < r.deadline;
-        if (warp == 0 && lane < cnt) stage_token(a, r, i0 + lane, rec + 2 * lane, drow_of + lane);
-        __syncthreads();
-        if (!x.go) break;     // the same value in every thread: read before any thread can write it again
-        first = false;
-        uint32_t bm_next = own ? bits[2 * (static_cast<int64_t>(rec[1].z) * a.KW + wi)] & mask : 0u;
-        for (int tt = 0; tt < cnt; ++tt) {
-            const uint4 t0 = rec[2 * tt], t1 = rec[2 * tt + 1];
-            const int kold = static_cast<int>(t1.w >> 16);
-            const int64_t col = static_cast<int64_t>((static_cast<u64>(t0.y & 0xFFFFu) << 32) | t0.x);
-            const int n_w = static_cast<int>(t1.w & 0xFFFFu);
-            const u64 At = (static_cast<u64>(t0.w) << 32) | t0.z;
-            const u64 U = (static_cast<u64>(t1.x) << 32) | t1.y;
-            const int ka = static_cast<int>(t0.y >> 16);
-            const uint32_t bm = bm_next;
-            if (own && tt + 1 < cnt) bm_next = bits[2 * (static_cast<int64_t>(rec[2 * tt + 3].z) * a.KW + wi)] & mask;
-            // m^{-i}: the old topic's count less one, applied as each count is read
-            const uint32_t mko = m[mi(kold)];
-            const int kdi = kd - (mko == 1u ? 1 : 0);
-            if (mko == 1u && own && (kold >> 5) == wi) mb &= ~(1u << (kold & 31));
-            if (warp == 0) {
-                st.add(2, static_cast<u64>(kdi < n_w ? kdi : n_w));
-                st.add(5, kdi < n_w ? 1u : 0u);
-            }
-            const uint32_t drow = drow_of[tt];
-            const bool docside = use_bm && drow != 0xFFFFFFFFu && (a.path == 2 || kdi * kDocRatio < n_w * 16);
-            const uint32_t *qrow = a.qdense + drow + 32 * wi;
-            u64 acc = 0;
-            uint32_t rem = 0;
-            int j0 = 0, j1 = 0;
-            if (docside) {
-                rem = bm & mb;
-                st.inter += static_cast<u64>(__popc(rem));
-                for (uint32_t bb = rem; bb;) {
-                    uint32_t qv[kCoopGather];
-                    int bp[kCoopGather];
-#pragma unroll
-                    for (int t = 0; t < kCoopGather; ++t) {
-                        bp[t] = -1;
-                        qv[t] = 0;
-                        if (bb) {
-                            const int b = __ffs(bb) - 1;
-                            bb &= bb - 1;
-                            bp[t] = b;
-                            qv[t] = qrow[b];
-                        }
-                    }
-#pragma unroll
-                    for (int t = 0; t < kCoopGather; ++t) {
-                        if (bp[t] >= 0) {
-                            const int k = 32 * wi + bp[t];
-                            acc += static_cast<u64>(qv[t]) * (m[33 * wi + bp[t]] - (k == kold ? 1u : 0u));
-                        }
-                    }
-                }
-            } else {
-                const int seg = (n_w + kCoopSlots - 1) / kCoopSlots;
-                j0 = min(seg * tid, n_w);
-                j1 = min(j0 + seg, n_w);
-                unsigned nj = 0;
-#pragma unroll 4
-                for (int j = j0; j < j1; ++j) {
-                    const int k = a.topic[col + j];
-                    const uint32_t mk = m[mi(k)] - (k == kold ? 1u : 0u);
-                    acc += static_cast<u64>(a.q[col + j]) * mk;
-                    nj += mk != 0u;
-                }
-                st.inter += static_cast<u64>(nj);
-            }
-            const u64 incl = warp_incl_scan64(acc);
-            if (lane == 31) x.tot[warp] = incl;
-            __syncthreads();                                  // A: the warps' totals
-            u64 B = 0;
-            u64 tot[kCoopWarps];
-#pragma unroll
-            for (int j = 0; j < kCoopWarps; ++j) {
-                tot[j] = x.tot[j];
-                B += tot[j];
-            }
-            const u64 T = At + (B << kFracBits);
-            int knew = kold;
-            bool upd = tid == 0;        // who updates m and publishes the topic
-            if (T == 0) {
-                if (warp == 0) st.add(3, 1);
-            } else {
-                const u64 rr = __umul64hi(U, T);
-                if (rr < At) {
-                    knew = ka;
-                    if (warp == 0) st.add(1, 1);
-                } else {
-                    const u64 rb = (rr - At) >> kFracBits;   // < B
-                    int selw = kCoopWarps;
-                    u64 lo = 0;
-#pragma unroll
-                    for (int j = 0; j < kCoopWarps; ++j) {
-                        if (selw == kCoopWarps) {
-                            if (rb < lo + tot[j]) selw = j;
-                            else lo += tot[j];
-                        }
-                    }
-                    if (selw == kCoopWarps) {
-                        if (tid == 0) atomicOr(&a.stats[ST_ERROR], ERR_INTERNAL);
-                    } else {
-                        upd = false;
-                        if (warp == selw) {
-                            const u64 rbl = rb - lo;
-                            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, rbl < incl);   // lane 31 at least
-                            if (lane == (bal ? __ffs(bal) - 1 : 31)) {
-                                upd = true;
-                                int f = -1;
-                                u64 run = incl - acc;
-                                if (docside) {
-                                    for (uint32_t bb = rem; f < 0 && bb; bb &= bb - 1) {
-                                        const int b = __ffs(bb) - 1;
-                                        const int k = 32 * wi + b;
-                                        run += static_cast<u64>(qrow[b]) * (m[33 * wi + b] - (k == kold ? 1u : 0u));
-                                        if (rbl < run) f = k;
-                                    }
-                                } else {
-                                    for (int j = j0; j < j1; ++j) {
-                                        const int k = a.topic[col + j];
-                                        run += static_cast<u64>(a.q[col + j]) * (m[mi(k)] - (k == kold ? 1u : 0u));
-                                        if (rbl < run) { f = k; break; }
-                                    }
-                                }
-                                if (f < 0) atomicOr(&a.stats[ST_ERROR], ERR_INTERNAL);
-                                else knew = f;
-                            }
-                        }
-                    }
-                }
-            }
-            if (upd) {
-                const uint32_t mkn = knew == kold ? mko - 1u : m[mi(knew)];
-                if (knew != kold) {
-                    m[mi(kold)] = mko - 1u;
-                    m[mi(knew)] = mkn + 1u;
-                }
-                x.knew = knew;
-                x.mkn = mkn;
-                r.z[i0 + tt] = static_cast<int16_t>(knew);
-            }
-            __syncthreads();                                  // B: the new topic, m updated
-            const int kn = x.knew;
-            const uint32_t mkn = x.mkn;
-            kd = kdi + (mkn == 0u ? 1 : 0);
-            if (mkn == 0u && own && (kn >> 5) == wi && ((mask >> (kn & 31)) & 1u)) mb |= 1u << (kn & 31);
-        }
-        if (warp == 0) st.add(0, static_cast<u64>(cnt));
-        r.budget -= cnt;
-        r.pos += cnt;
-        if (r.pos == r.len) { r.pos = 0; r.sweep += 1; }
-    }
-}
-
-// The longest documents of a pass, one CTA each (dynamically scheduled,
-// longest first): doc_order[0 .. n_coop).
-__global__ void __launch_bounds__(kCoopSlots, PULDA_ZMINBLOCKS) k_z_step_coop(ZArgs a, int n_coop, int *work) {
-    extern __shared__ uint32_t zsm[];
-    CoopXch &x = *reinterpret_cast<CoopXch *>(zsm + z_m_words(a.K) + 32 * kTokRecWords);
-    ZCount st;
-    const uint32_t sweep = sweep_of(a);
-    for (;;) {
-        if (threadIdx.x == 0) x.item = atomicAdd(work, 1);
-        __syncthreads();
-        const int item = x.item;
-        __syncthreads();
-        if (item >= n_coop) break;
-        const int d = a.doc_order[item];
-        const int64_t s = a.doc_off[d];
-        const int len = static_cast<int>(a.doc_off[d + 1] - s);
-        DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep, 0, len, 1};
-        z_doc_coop(a, zsm, r, st);
     }
     flush_warp_z_stats(a.stats, st);
 }
@@ -1233,30 +863,6 @@ __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_m
                  0, a.doc_off[it.y + 1] - s, 1};
         ZCount st;
         z_doc_warp(a, m, r, st);
-        flush_warp_z_stats(a.stats, st);
-    }
-}
-
-// Many chains: the longest documents of every chain, one CTA each (the
-// cooperative z-step); items[0 .. n_items) are (chain, document) pairs.
-__global__ void __launch_bounds__(kCoopSlots, PULDA_ZMINBLOCKS) k_z_step_coop_multi(const ZArgs *chains,
-                                                                                   const int2 *items, int n_items,
-                                                                                   int *work, int kmax) {
-    extern __shared__ uint32_t zsm[];
-    int *item_sh = reinterpret_cast<int *>(zsm + z_coop_words(kmax));    // beyond every chain's layout
-    for (;;) {
-        if (threadIdx.x == 0) *item_sh = atomicAdd(work, 1);
-        __syncthreads();
-        const int item = *item_sh;
-        __syncthreads();
-        if (item >= n_items) break;
-        const int2 it = items[item];
-        const ZArgs &a = chains[it.x];
-        const int64_t s = a.doc_off[it.y];
-        const int len = static_cast<int>(a.doc_off[it.y + 1] - s);
-        DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep_of(a), 0, len, 1};
-        ZCount st;
-        z_doc_coop(a, zsm, r, st);
         flush_warp_z_stats(a.stats, st);
     }
 }
@@ -1626,50 +1232,6 @@ __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSl
     flush_warp_z_stats(a.stats, st);
 }
 
-// The same for the long requests, one CTA of kCoopWarps warps each (the
-// cooperative z-step): active[0 .. n_active) are those slots.
-__global__ void __launch_bounds__(kCoopSlots, 7) k_serve_step_coop(ZArgs a, ServeSlot *slots, const int32_t *active,
-                                                                     int n_active, const int32_t *arena_w,
-                                                                     int16_t *arena_z, int64_t slice, int *work,
-                                                                     uint64_t window_ns) {
-    extern __shared__ uint32_t zsm[];
-    CoopXch &x = *reinterpret_cast<CoopXch *>(zsm + z_m_words(a.K) + 32 * kTokRecWords);
-    ZCount st;
-    for (;;) {
-        __syncthreads();          // every thread has read the previous item and its deadline
-        if (threadIdx.x == 0) {
-            x.item = atomicAdd(work, 1);
-            x.tot[0] = window_ns ? global_ns() + window_ns : ~0ull;
-        }
-        __syncthreads();
-        const int item = x.item;
-        const uint64_t deadline = x.tot[0];
-        if (item >= n_active) break;
-        const int idx = active[item];
-        const ServeSlot sl = slots[idx];
-        int16_t *z = arena_z + sl.off;
-        uint32_t sweep = sl.sweep;
-        int pos = sl.pos;
-        if (sweep == 0) {
-            for (int i = threadIdx.x; i < sl.len; i += kCoopSlots) {
-                const U4 u = draw(sl.seed, static_cast<uint32_t>(i), 0u, 0u, TAG_INIT, 0);
-                z[i] = static_cast<int16_t>(__umulhi(u.x, static_cast<uint32_t>(a.K)));
-            }
-            __syncthreads();
-            sweep = 1;
-            pos = 0;
-        }
-        DocRun r{arena_w + sl.off, z, sl.len, sl.seed, 0, sweep, pos, slice,
-                 static_cast<int>(sl.sweep_end - sweep), deadline};
-        z_doc_coop(a, zsm, r, st);
-        if (threadIdx.x == 0) {
-            slots[idx].sweep = r.sweep;
-            slots[idx].pos = r.pos;
-        }
-    }
-    flush_warp_z_stats(a.stats, st);
-}
-
 // ============================================================== exports
 // m_{d,k}, dense row-major [D, K]: one warp per document.
 __global__ void k_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K, int32_t *m_dk) {
@@ -1745,16 +1307,6 @@ int smem_optin() {
     return v;
 }
 
-// Opt a kernel in to the largest dynamic shared memory it can use next to
-// its static shared memory.
-template <typename F>
-void allow_dynamic_smem(F *kernel) {
-    cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
-    const int room = smem_optin() - static_cast<int>(fa.sharedSizeBytes);
-    if (room > 0) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
-}
-
 int phi_counts_blocks_per_sm(int K) {
     const size_t smem = phi_counts_smem(K);
     allow_dynamic_smem(k_phi_counts);
@@ -1828,20 +1380,6 @@ void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t s
     k_z_step<<<grid, 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(a);
 }
 
-size_t z_coop_smem(int K) { return sizeof(uint32_t) * static_cast<size_t>(z_coop_words(K)); }
-
-int z_coop_blocks_per_sm(int K) {
-    allow_dynamic_smem(k_z_step_coop);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_z_step_coop, kCoopSlots, z_coop_smem(K));
-    return b > 0 ? b : 1;
-}
-
-void launch_z_step_coop(const ZArgs &a, int n_coop, int *work, int grid, cudaStream_t st) {
-    if (n_coop <= 0) return;
-    k_z_step_coop<<<std::max(1, std::min(grid, n_coop)), kCoopSlots, z_coop_smem(a.K), st>>>(a, n_coop, work);
-}
-
 void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
     k_batch_begin_sweep<<<1, 256, 0, st>>>(b.phi, b.n_chains, b.sweep, b.work);
     launch_heavy_hist(b.phi, b.heavy, b.n_heavy, b.kmax, st);
@@ -1853,8 +1391,7 @@ void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
     if (b.n_coop > 0) {
         // the longest documents on CTAs, the rest one per warp beside them
         cudaEventRecord(b.ev_fork, st);
-        k_z_step_coop_multi<<<std::max(1, std::min(b.coop_grid, b.n_coop)), kCoopSlots, z_coop_multi_smem(b.kmax), st>>>(
-            b.z, b.z_items, b.n_coop, b.work + 2, b.kmax);
+        launch_z_step_coop_multi(b.z, b.z_items, b.n_coop, b.work + 2, b.kmax, b.coop_grid, st);
         cudaStreamWaitEvent(b.stream2, b.ev_fork, 0);
         if (b.n_z_items > b.n_coop)
             k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), b.stream2>>>(
@@ -1865,15 +1402,6 @@ void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
         k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), st>>>(
             b.z, b.z_items, b.n_z_items, b.work + 1, b.kmax);
     }
-}
-
-size_t z_coop_multi_smem(int kmax) { return sizeof(uint32_t) * static_cast<size_t>(z_coop_words(kmax)) + 16; }
-
-int batch_coop_blocks_per_sm(int kmax) {
-    allow_dynamic_smem(k_z_step_coop_multi);
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_z_step_coop_multi, kCoopSlots, z_coop_multi_smem(kmax));
-    return n > 0 ? n : 1;
 }
 
 int batch_phi_blocks_per_sm(int kmax) {
@@ -1898,22 +1426,6 @@ void launch_serve_step(const ZArgs &a, ServeSlot *slots, const int32_t *active, 
     const int need = (n_active + warps_per_block - 1) / warps_per_block;
     k_serve_step<<<std::min(grid, need), 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(
         a, slots, active, n_active, arena_w, arena_z, slice, work, window_ns);
-}
-
-void launch_serve_step_coop(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active,
-                            const int32_t *arena_w, int16_t *arena_z, int64_t slice, int *work, int grid,
-                            uint64_t window_ns, cudaStream_t st) {
-    if (n_active <= 0) return;
-    cudaMemsetAsync(work, 0, sizeof(int), st);
-    k_serve_step_coop<<<std::max(1, std::min(grid, n_active)), kCoopSlots, z_coop_smem(a.K), st>>>(
-        a, slots, active, n_active, arena_w, arena_z, slice, work, window_ns);
-}
-
-int serve_coop_blocks_per_sm(int K) {
-    allow_dynamic_smem(k_serve_step_coop);
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_serve_step_coop, kCoopSlots, z_coop_smem(K));
-    return n > 0 ? n : 1;
 }
 
 int serve_blocks_per_sm(int K, int warps_per_block) {

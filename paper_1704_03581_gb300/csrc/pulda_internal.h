@@ -250,6 +250,9 @@ int batch_phi_blocks_per_sm(int kmax);
 int batch_z_blocks_per_sm(int kmax, int warps);
 int batch_coop_blocks_per_sm(int kmax);
 size_t z_coop_multi_smem(int kmax);
+// The cooperative z-step over (chain, document) items (coop.cu).
+void launch_z_step_coop_multi(const ZArgs *chains, const int2 *items, int n_items, int *work, int kmax, int grid,
+                              cudaStream_t st);
 
 // A request being folded in by the server (device slot table entry).
 struct ServeSlot {

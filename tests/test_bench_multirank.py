@@ -63,6 +63,6 @@ def test_launch_count_and_profile_record_follow_the_source(tmp_path, monkeypatch
     assert bench.kernels_per_sweep(np.arange(10, dtype=np.int32), 1) == 8
     rec = bench.recorded_profile()
     if rec:
-        assert rec["kernels_cu_sha"] == bench.kernel_source_hash()
+        assert rec["source_sha"] == bench.kernel_source_hash()
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
     assert bench.recorded_profile() == {} and bench.recorded_traffic() is None
