@@ -394,7 +394,8 @@ def run_pulda(args, corpus, rank: int, world: int):
         "data": "synthetic (LDA generative process, Zipf(1.05) vocabulary)",
         "config": {"workload": corpus.name, "D": corpus.D, "V": corpus.V, "N": corpus.N, "K": K_TOPICS,
                    "alpha": ALPHA, "beta": BETA, "parallelism": f"{world} independent chains (replicas)",
-                   "l2": "inputs larger than L2 (word ids 396 MB + topics 198 MB read every sweep)",
+                   "l2": (f"inputs {'larger' if 6 * corpus.N > 129e6 else 'smaller'} than L2 (word ids "
+                          f"{4 * corpus.N / 1e6:.0f} MB + topics {2 * corpus.N / 1e6:.0f} MB read every sweep)"),
                    "timed_sweeps": [first_timed, first_timed + K - 1],
                    "phi": "Dirichlet (Algorithm 1)" if args.phi_mode == 1 else "Poisson Polya urn (Algorithm 2)",
                    "z": (f"documents over {args.slice_len} tokens in stale-count slices (not the paper's sampler)"
