@@ -75,7 +75,7 @@ typedef struct {
                                resampled by the 4 warps of one CTA together, token by token
                                (its intersections split over 128 lanes), concurrently with the
                                other documents' one-warp kernel; results are identical.
-                               0 = auto (documents longer than max(256, N / 6000) tokens:
+                               0 = auto (documents longer than max(256, N / 8000) tokens:
                                those that would outlast the rest of the pass on one warp),
                                -1 = never, > 0 = this length.  Not used with docs_per_warp 4
                                or slice_len > 0; the batched form takes 0 or -1 (one warp
@@ -250,7 +250,7 @@ typedef struct pulda_batch pulda_batch;
  * CTA size instead of tuning it over {2, 4, 8}; opt->coop_min_len -1 keeps
  * every document on one warp, > 0 sends the documents at least that long (of
  * every chain) to the cooperative z-step, 0 tunes it: after the CTA sizes, the
- * first sweeps also time the thresholds max(256, N / 6000) and a quarter of it
+ * first sweeps also time the thresholds max(256, N / 8000) and a quarter of it
  * (N = tokens of all chains) against none; docs_per_warp must be 0 or 1. */
 pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains, int32_t n_chains,
                               const pulda_options *opt);

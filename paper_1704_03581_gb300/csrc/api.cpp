@@ -135,7 +135,7 @@ int64_t count_long(const int64_t *off, const std::vector<int32_t> &order) {
 
 // Number of leading documents of a length-ordered schedule that the
 // cooperative z-step takes: at least coop_min_len tokens (0 = automatic:
-// longer than max(256, N / 6000)); none with coop_min_len < 0, the grouped
+// longer than max(256, N / 8000)); none with coop_min_len < 0, the grouped
 // z-step or slices.
 int64_t count_coop(const pulda_handle *h, const int64_t *off, const std::vector<int32_t> &order, int64_t N) {
     if (h->opt.coop_min_len < 0 || h->z_groups || h->opt.slice_len > 0) return 0;

@@ -26,11 +26,16 @@ namespace {
 // the draw reads off the topic, updates m and publishes it (barrier B).  The
 // sums are the same exact integers in the same topic order as the one-warp
 // kernel's, so every draw, and every topic, is identical.
-constexpr int kCoopWarps = 4;
+#ifndef PULDA_COOP_WARPS
+#define PULDA_COOP_WARPS 4
+#endif
+constexpr int kCoopWarps = PULDA_COOP_WARPS;
 constexpr int kCoopSlots = 32 * kCoopWarps;
 constexpr int kCoopGather = 4;     // document-side q loads per round
-// 64 registers, as the one-warp kernel: 8 CTAs per SM fit beside it.
-constexpr int kCoopMinBlocks = 8;
+// 64 registers, as the one-warp kernel (8 CTAs of four warps per SM); the
+// serving form needs 72 (7 CTAs of four warps).
+constexpr int kCoopMinBlocks = 32 / kCoopWarps;
+constexpr int kCoopServeMinBlocks = 28 / kCoopWarps > 0 ? 28 / kCoopWarps : 1;
 
 struct CoopXch {
     u64 tot[kCoopWarps];    // each warp's sum of q m over its slots (this token)
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(kCoopSlots, kCoopMinBlocks) k_z_step_coop_mult
 
 // The same for the long requests, one CTA of kCoopWarps warps each (the
 // cooperative z-step): active[0 .. n_active) are those slots.
-__global__ void __launch_bounds__(kCoopSlots, 7) k_serve_step_coop(ZArgs a, ServeSlot *slots, const int32_t *active,
+__global__ void __launch_bounds__(kCoopSlots, kCoopServeMinBlocks) k_serve_step_coop(ZArgs a, ServeSlot *slots, const int32_t *active,
                                                                      int n_active, const int32_t *arena_w,
                                                                      int16_t *arena_z, int64_t slice, int *work,
                                                                      uint64_t window_ns) {

@@ -186,10 +186,11 @@ void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t s
 // `work` is a counter zeroed before the launch.
 void launch_z_step_coop(const ZArgs &a, int n_coop, int *work, int grid, cudaStream_t st);
 int z_coop_blocks_per_sm(int K);
-// Automatic threshold of the cooperative z-step: a document on one warp takes
-// about 2.5 us per token while the whole pass streams ~2.4 G tokens/s, so one
-// longer than N / 6000 tokens would outlast the pass.
-constexpr int64_t kCoopAutoDiv = 6000;
+// Automatic threshold of the cooperative z-step: a document on one warp that
+// shares its SM with the rest of the pass takes about 3.3 us per token while
+// the pass streams ~2.4 G tokens/s, so one longer than N / 8000 tokens would
+// outlast the pass.
+constexpr int64_t kCoopAutoDiv = 8000;
 constexpr int64_t kCoopAutoMin = 256;
 // Pass-start topic counts of the documents that the z-step takes in slices.
 void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int n, const int16_t *z, int K,
