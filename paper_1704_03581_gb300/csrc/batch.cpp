@@ -1,8 +1,9 @@
 // Many independent chains (corpora of uneven D, N, K, V) advanced together:
 // every kernel of a sweep runs once over all chains' work items, and the six
 // launches of a sweep are captured once into a CUDA graph and replayed.  The
-// z-step CTA size is picked by timing the candidates on the first sweeps (a
-// launch shape never changes a result, so tuning costs no extra sweeps).
+// z-step CTA size, then the cooperative threshold, are picked by timing the
+// candidates on the first sweeps (a launch shape never changes a result, so
+// tuning costs no extra sweeps).
 #include <algorithm>
 #include <cstdio>
 #include <numeric>
@@ -26,9 +27,15 @@ struct pulda_batch {
     int64_t sweep = 0;
     // tuning candidates (z-step warps per CTA, cooperative threshold; 0 = none),
     // timed on real sweeps: first the CTA sizes, then thresholds at the best size
+    // Each phase times its candidates twice, in order and then in reverse, so
+    // the falling cost of the first sweeps after the uniform start does not
+    // favour the candidates timed later.
     struct Cand { int warps; int64_t coop_len; };
     std::vector<Cand> cand;
-    std::vector<float> cand_ms;
+    std::vector<float> cand_ms;     // summed over the candidate's timed sweeps
+    std::vector<int> sched;         // candidate indices still to time in this phase
+    size_t sched_pos = 0;
+    int phase_first = 0;            // first candidate index of the current phase
     std::vector<int64_t> coop_try;  // thresholds for the second phase
     bool tuned = false;
     bool phase2 = false;
@@ -71,6 +78,26 @@ int count_coop_items(const pulda_batch *b, int64_t L) {
     int n = 0;
     while (n < static_cast<int>(b->dlen.size()) && b->dlen[n] >= L) ++n;
     return n;
+}
+
+// Starts a tuning phase over candidates [first, cand.size()): forward, then backward.
+void schedule_phase(pulda_batch *b, int first) {
+    b->phase_first = first;
+    b->sched.clear();
+    b->sched_pos = 0;
+    const int n = static_cast<int>(b->cand.size());
+    for (int c = first; c < n; ++c) b->sched.push_back(c);
+    for (int c = n - 1; c >= first; --c) b->sched.push_back(c);
+    b->cand_ms.resize(b->cand.size(), 0.0f);
+}
+
+// The second phase: the best CTA size without and with each cooperative threshold.
+void start_coop_phase(pulda_batch *b, int warps) {
+    b->phase2 = true;
+    const int first = static_cast<int>(b->cand.size());
+    b->cand.push_back({warps, 0});
+    for (int64_t L : b->coop_try) b->cand.push_back({warps, L});
+    schedule_phase(b, first);
 }
 
 void apply_candidate(pulda_batch *b, const pulda_batch::Cand &c) {
@@ -259,6 +286,8 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         if (b->cand.empty()) b->cand.push_back({1, fixed_coop});
     }
     if (b->cand.size() == 1 && b->coop_try.empty()) b->tuned = true;
+    else if (b->cand.size() == 1) start_coop_phase(b, b->cand.front().warps);   // only the threshold to tune
+    else schedule_phase(b, 0);
     apply_candidate(b, b->cand.front());
     if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
         cudaStreamCreateWithFlags(&bl.stream2, cudaStreamNonBlocking) != cudaSuccess ||
@@ -277,8 +306,9 @@ pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps) {
     if (n_sweeps < 0) return bfail(b, PULDA_ERR_INVALID, "n_sweeps must be >= 0");
     for (int32_t s = 0; s < n_sweeps; ++s) {
         if (!b->tuned) {
-            // time the next candidate on a real sweep
-            apply_candidate(b, b->cand[b->cand_ms.size()]);
+            // time the next scheduled candidate on a real sweep
+            const int c = b->sched[b->sched_pos];
+            apply_candidate(b, b->cand[c]);
             BCU(b, cudaEventRecord(b->ev0, b->stream));
             pulda_status r = launch_one_sweep(b);
             if (r != PULDA_OK) return r;
@@ -286,13 +316,13 @@ pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps) {
             BCU(b, cudaEventSynchronize(b->ev1));
             float ms = 0;
             BCU(b, cudaEventElapsedTime(&ms, b->ev0, b->ev1));
-            b->cand_ms.push_back(ms);
-            if (b->cand_ms.size() == b->cand.size()) {
-                const size_t best = std::min_element(b->cand_ms.begin(), b->cand_ms.end()) - b->cand_ms.begin();
+            b->cand_ms[c] += ms;
+            if (++b->sched_pos == b->sched.size()) {
+                int best = b->phase_first;
+                for (int k = b->phase_first; k < static_cast<int>(b->cand.size()); ++k)
+                    if (b->cand_ms[k] < b->cand_ms[best]) best = k;
                 if (!b->phase2 && !b->coop_try.empty()) {
-                    // second phase: the cooperative thresholds at the best CTA size
-                    b->phase2 = true;
-                    for (int64_t L : b->coop_try) b->cand.push_back({b->cand[best].warps, L});
+                    start_coop_phase(b, b->cand[best].warps);
                 } else {
                     apply_candidate(b, b->cand[best]);
                     b->tuned = true;
