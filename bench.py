@@ -665,6 +665,7 @@ def run_serving(args):
         sst = srv.stats()
         results.append({"rate_docs_per_s": rate, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
                         "max_active": int(sst["max_active"]), "launches": int(sst["launches"]),
+                        "gpu_busy_frac": sst["kernel_ns"] / max(1, t_end - t0),
                         "p99_ms": float(np.percentile(lat, 99)),
                         "docs_per_s": n / ((t_end - t0) / 1e9),
                         "token_sweeps_per_s": toks * args.serve_sweeps / ((t_end - t0) / 1e9)})
