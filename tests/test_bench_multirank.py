@@ -61,6 +61,12 @@ def test_launch_count_and_profile_record_follow_the_source(tmp_path, monkeypatch
     assert bench.kernels_per_sweep(np.zeros(10, np.int32), 0) == 5
     assert bench.kernels_per_sweep(np.zeros(1 << 18, np.int32), 0) == 6
     assert bench.kernels_per_sweep(np.arange(10, dtype=np.int32), 1) == 8
+    # the cooperative z-step beside the one-warp kernel once a document reaches the threshold
+    off = np.array([0, 300, 310], np.int64)
+    assert bench.kernels_per_sweep(np.zeros(310, np.int32), 0, off) == 6
+    assert bench.kernels_per_sweep(np.zeros(310, np.int32), 0, off, coop_min_len=-1) == 5
+    assert bench.kernels_per_sweep(np.zeros(310, np.int32), 0, off, coop_min_len=400) == 5
+    assert bench.kernels_per_sweep(np.zeros(310, np.int32), 0, off, slice_len=100) == 6
     rec = bench.recorded_profile()
     if rec:
         assert rec["source_sha"] == bench.kernel_source_hash()
