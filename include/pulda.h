@@ -135,6 +135,11 @@ pulda_status pulda_z_step(pulda_handle *h);
 /* pulda_sync -- wait for the handle's stream and report device-side errors
  * (PULDA_ERR_DEGENERATE, PULDA_ERR_CUDA). */
 pulda_status pulda_sync(pulda_handle *h);
+/* pulda_sync_timeout -- as pulda_sync, but gives up after timeout_ms
+ * milliseconds of waiting (polling the stream) and returns PULDA_ERR_TIMEOUT;
+ * the work keeps running and a later pulda_sync waits for it.  Errors:
+ * PULDA_ERR_INVALID (timeout_ms < 0), PULDA_ERR_TIMEOUT, as pulda_sync. */
+pulda_status pulda_sync_timeout(pulda_handle *h, int32_t timeout_ms);
 
 /* pulda_get_z -- copy z (int16[N], corpus order) to host / device memory. */
 pulda_status pulda_get_z(pulda_handle *h, int16_t *z_host);

@@ -22,7 +22,8 @@ PULDA_OK = 0
 STATUS = {0: "PULDA_OK", -1: "PULDA_ERR_INVALID", -2: "PULDA_ERR_OOM", -3: "PULDA_ERR_CUDA",
           -4: "PULDA_ERR_TIMEOUT", -5: "PULDA_ERR_DEGENERATE", -6: "PULDA_ERR_BUSY"}
 
-EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "pulda_sync", "pulda_get_z",
+EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "pulda_sync", "pulda_sync_timeout",
+            "pulda_get_z",
             "pulda_get_z_dev", "pulda_set_z", "pulda_get_counts", "pulda_log_posterior", "pulda_get_phi",
             "pulda_get_word_tables",
             "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_last_error", "pulda_free",
@@ -73,6 +74,7 @@ def lib() -> ctypes.CDLL:
             "pulda_phi_step": [P],
             "pulda_z_step": [P],
             "pulda_sync": [P],
+            "pulda_sync_timeout": [P, ctypes.c_int32],
             "pulda_get_z": [P, P],
             "pulda_get_z_dev": [P, P],
             "pulda_set_z": [P, P, i64],
@@ -166,6 +168,15 @@ def pulda_z_step(h):
 
 def pulda_sync(h):
     _check(h, lib().pulda_sync(h))
+
+
+def pulda_sync_timeout(h, timeout_ms: int) -> bool:
+    """True when the handle's work finished within timeout_ms, False on PULDA_ERR_TIMEOUT."""
+    st = lib().pulda_sync_timeout(h, int(timeout_ms))
+    if st == -4:
+        return False
+    _check(h, st)
+    return True
 
 
 def pulda_get_z(h, out: np.ndarray):

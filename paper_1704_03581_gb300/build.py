@@ -87,5 +87,16 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     return lib
 
 
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+
+
+def build_checked(force: bool = False) -> str:
+    """The library with PULDA_CHECKED defined: indices read from device data
+    (topics) are bounds-checked in the kernels, and a bad one raises an error
+    that pulda_sync reports instead of an out-of-bounds access.  For tests and
+    debugging; load it through PULDA_LIB."""
+    return build(force=force, extra=["-DPULDA_CHECKED"], out_dir=BUILD_CHECKED)
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))

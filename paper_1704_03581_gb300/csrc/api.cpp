@@ -1,6 +1,7 @@
 // C ABI of the pulda sampler: argument validation, device buffers, and the
 // order of kernel launches that makes one sweep (Algorithm 2, Section 3).
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -9,6 +10,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pulda.h"
 #include "handle.h"
 #include "pulda_internal.h"
@@ -16,6 +19,13 @@
 using namespace pulda;
 
 namespace {
+
+// An NVTX range over a scope (a no-op unless a profiler listens).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 
 thread_local std::string g_init_error;
 
@@ -452,6 +462,7 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
 
 pulda_status pulda_phi_step(pulda_handle *h) {
     if (!h) return PULDA_ERR_INVALID;
+    NvtxRange nv("pulda_phi_step");
     h->sweep += 1;
     cudaStream_t st = h->stream;
     CU(h, cudaMemsetAsync(h->stats, 0, sizeof(unsigned long long) * ST_COUNT, st));
@@ -477,6 +488,7 @@ pulda_status pulda_phi_step(pulda_handle *h) {
 
 pulda_status pulda_z_step(pulda_handle *h) {
     if (!h) return PULDA_ERR_INVALID;
+    NvtxRange nv("pulda_z_step");
     if (!h->have_phi) return fail(h, PULDA_ERR_INVALID, "no Phi drawn yet: call pulda_phi_step or pulda_sweep first");
     CU(h, clear_z_counters(h));
     if (h->n_slices > 0) {
@@ -509,6 +521,21 @@ pulda_status pulda_sweep(pulda_handle *h, int32_t n_sweeps) {
     return PULDA_OK;
 }
 
+pulda_status pulda_sync_timeout(pulda_handle *h, int32_t timeout_ms) {
+    if (!h) return PULDA_ERR_INVALID;
+    if (timeout_ms < 0) return fail(h, PULDA_ERR_INVALID, "timeout_ms must be >= 0");
+    const auto t_end = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+        const cudaError_t q = cudaStreamQuery(h->stream);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) CU(h, q);
+        if (std::chrono::steady_clock::now() >= t_end)
+            return fail(h, PULDA_ERR_TIMEOUT, "the handle's work did not finish within %d ms", timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    return pulda_sync(h);
+}
+
 pulda_status pulda_sync(pulda_handle *h) {
     if (!h) return PULDA_ERR_INVALID;
     CU(h, cudaStreamSynchronize(h->stream));
@@ -517,6 +544,7 @@ pulda_status pulda_sync(pulda_handle *h) {
     if (e & ERR_DEGENERATE) return fail(h, PULDA_ERR_DEGENERATE, "a Phi row stayed all-zero after 2^20 redraws");
     if (e & ERR_INTERNAL) return fail(h, PULDA_ERR_CUDA, "z-step invariant violated (draw beyond the total mass)");
     if (e & ERR_GAMMA) return fail(h, PULDA_ERR_DEGENERATE, "a Gamma draw was rejected 2^16 times");
+    if (e & ERR_BOUNDS) return fail(h, PULDA_ERR_CUDA, "an index read from device data was out of range (checked build)");
     return PULDA_OK;
 }
 
@@ -572,6 +600,7 @@ pulda_status pulda_get_counts(pulda_handle *h, int32_t *n_kv, int32_t *m_dk) {
 }
 
 pulda_status pulda_log_posterior(pulda_handle *h, double *out) {
+    NvtxRange nv("pulda_log_posterior");
     if (!h) return PULDA_ERR_INVALID;
     if (!out) return fail(h, PULDA_ERR_INVALID, "out is NULL");
     cudaStream_t st = h->stream;
@@ -641,6 +670,7 @@ pulda_status pulda_get_phi(pulda_handle *h, int64_t *col_ptr, int16_t *topic, fl
 
 pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids, const int64_t *doc_offsets, int64_t D_new,
                          int32_t n_sweeps, uint64_t seed, int16_t *z_out, int32_t *m_out) {
+    NvtxRange nv("pulda_infer");
     if (!h) return PULDA_ERR_INVALID;
     if (!h->have_phi) return fail(h, PULDA_ERR_INVALID, "no Phi drawn yet: run a sweep before pulda_infer");
     if (n_sweeps < 0) return fail(h, PULDA_ERR_INVALID, "n_sweeps must be >= 0");

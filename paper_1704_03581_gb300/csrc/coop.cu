@@ -7,6 +7,7 @@
 #include "device_rng.cuh"
 #include "pulda_internal.h"
 #include "zstep.cuh"
+#include "checks.cuh"
 
 namespace pulda {
 namespace {
@@ -68,7 +69,7 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
     if (r.len == 0 || r.budget <= 0) return;
     for (int k = tid; k < K; k += kCoopSlots) m[mi(k)] = 0;
     __syncthreads();
-    for (int i = tid; i < r.len; i += kCoopSlots) atomicAdd(&m[mi(r.z[i])], 1u);
+    for (int i = tid; i < r.len; i += kCoopSlots) atomicAdd(&m[mi(guard_index(r.z[i], K, a.stats))], 1u);
     __syncthreads();
     uint32_t mb = 0;        // this slot's bits of m_d's nonzero topics
     int c = 0;
@@ -155,7 +156,7 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
                 unsigned nj = 0;
 #pragma unroll 4
                 for (int j = j0; j < j1; ++j) {
-                    const int k = a.topic[col + j];
+                    const int k = guard_index(a.topic[col + j], K, a.stats);
                     const uint32_t mk = m[mi(k)] - (k == kold ? 1u : 0u);
                     acc += static_cast<u64>(a.q[col + j]) * mk;
                     nj += mk != 0u;
@@ -213,7 +214,7 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
                                     }
                                 } else {
                                     for (int j = j0; j < j1; ++j) {
-                                        const int k = a.topic[col + j];
+                                        const int k = guard_index(a.topic[col + j], K, a.stats);
                                         run += static_cast<u64>(a.q[col + j]) * (m[mi(k)] - (k == kold ? 1u : 0u));
                                         if (rbl < run) { f = k; break; }
                                     }
@@ -226,6 +227,7 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
                 }
             }
             if (upd) {
+                knew = guard_index(knew, K, a.stats);
                 const uint32_t mkn = knew == kold ? mko - 1u : m[mi(knew)];
                 if (knew != kold) {
                     m[mi(kold)] = mko - 1u;

@@ -27,6 +27,7 @@
 #include "device_rng.cuh"
 #include "pulda_internal.h"
 #include "zstep.cuh"
+#include "checks.cuh"
 
 namespace pulda {
 namespace {
@@ -167,7 +168,8 @@ __device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, 
     } else {
         for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
         __syncthreads();
-        for (int64_t t = wbeg + threadIdx.x; t < wend; t += kPhiBlock) atomicAdd(&hist[a.z[a.perm[t]]], 1u);
+        for (int64_t t = wbeg + threadIdx.x; t < wend; t += kPhiBlock)
+            atomicAdd(&hist[guard_index(a.z[a.perm[t]], K, a.stats)], 1u);
         __syncthreads();
     }
     if (do_draw) {
@@ -286,7 +288,8 @@ __global__ void __launch_bounds__(kPhiBlock) k_heavy_hist(const PhiArgs *chains,
     const int K = a.K;
     for (int k = threadIdx.x; k < K; k += kPhiBlock) hs[k] = 0;
     __syncthreads();
-    for (int64_t t = c.begin + threadIdx.x; t < c.end; t += kPhiBlock) atomicAdd(&hs[a.z[a.perm[t]]], 1u);
+    for (int64_t t = c.begin + threadIdx.x; t < c.end; t += kPhiBlock)
+        atomicAdd(&hs[guard_index(a.z[a.perm[t]], K, a.stats)], 1u);
     __syncthreads();
     uint32_t *row = a.heavy_hist + static_cast<int64_t>(c.row) * K;
     for (int k = threadIdx.x; k < K; k += kPhiBlock)
@@ -607,7 +610,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
     } else {
         for (int k = lane; k < K; k += 32) m[mi(k)] = 0;
         __syncwarp();
-        for (int i = lane; i < r.len; i += 32) atomicAdd(&m[mi(r.z[i])], 1u);
+        for (int i = lane; i < r.len; i += 32) atomicAdd(&m[mi(guard_index(r.z[i], K, a.stats))], 1u);
     }
     __syncwarp();
     uint32_t mbits = 0;
@@ -717,7 +720,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
                 unsigned nj = 0;
 #pragma unroll 4
                 for (int j = seg0; j < seg1; ++j) {
-                    const uint32_t mk = m[mi(a.topic[col + j])];
+                    const uint32_t mk = m[mi(guard_index(a.topic[col + j], K, a.stats))];
                     acc += static_cast<u64>(qcol[j]) * mk;
                     nj += mk != 0u;
                 }
@@ -760,7 +763,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
                             } else {
                                 const int seg1 = min(seg0 + seg, n_w);
                                 for (int j = seg0; j < seg1; ++j) {
-                                    const int k = a.topic[col + j];
+                                    const int k = guard_index(a.topic[col + j], K, a.stats);
                                     run += static_cast<u64>(qcol[j]) * m[mi(k)];
                                     if (rb < run) { f = k; break; }
                                 }
@@ -776,6 +779,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
                 }
             }
             // add token i back with its new topic
+            knew = guard_index(knew, K, a.stats);
             const uint32_t old2 = m[mi(knew)];
             __syncwarp();
             if (lane == 0) m[mi(knew)] = old2 + 1;
@@ -924,7 +928,7 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
         for (int k = gl; k < Kp / 2; k += kGroup) m32[k] = 0u;
         __syncwarp();
         for (int t = gl; t < len; t += kGroup) {
-            const int k = a.z[s + t];
+            const int k = guard_index(a.z[s + t], K, a.stats);
             atomicAdd(&m32[k >> 1], 1u << ((k & 1) * 16));
         }
         __syncwarp();
@@ -961,7 +965,7 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
             if (valid) {
                 const int64_t i = s + tl;
                 wv = a.w[i];
-                zo = a.z[i];
+                zo = guard_index(a.z[i], K, a.stats);
                 const uint64_t t = static_cast<uint64_t>(a.index_base + i);
                 x = draw(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), a.sweep, TAG_Z, 0);
                 cb = a.col_ptr[wv];
@@ -1062,7 +1066,8 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
                     }
                 } else if (act) {
 #pragma unroll 4
-                    for (int j = j0; j < j1; ++j) s0 += static_cast<u64>(a.q[col + j]) * m[a.topic[col + j]];
+                    for (int j = j0; j < j1; ++j)
+                        s0 += static_cast<u64>(a.q[col + j]) * m[guard_index(a.topic[col + j], K, a.stats)];
                 }
                 {
                     // |J| of this token: the group's count of intersection entries
@@ -1070,7 +1075,7 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
                     if (docside) {
                         nj = __popc(c0.x & mb0) + __popc(c1.x & mb1) + __popc(c2.x & mb2) + __popc(c3.x & mb3);
                     } else if (act) {
-                        for (int j = j0; j < j1; ++j) nj += m[a.topic[col + j]] != 0;
+                        for (int j = j0; j < j1; ++j) nj += m[guard_index(a.topic[col + j], K, a.stats)] != 0;
                     }
 #pragma unroll
                     for (int o = 1; o < kGroup; o <<= 1) nj += __shfl_xor_sync(0xFFFFFFFFu, nj, o);
@@ -1119,7 +1124,7 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
                         }
                     } else {
                         for (int j = j0; j < j1; ++j) {
-                            const int k = a.topic[col + j];
+                            const int k = guard_index(a.topic[col + j], K, a.stats);
                             run += static_cast<u64>(a.q[col + j]) * m[k];
                             if (rb < run) { f = k; break; }
                         }
@@ -1136,6 +1141,7 @@ __global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs
                 }
                 // add token i back with its new topic
                 uint32_t old2 = 0;
+                knew = guard_index(knew, K, a.stats);
                 if (act) old2 = m[knew];
                 __syncwarp();
                 if (act) {

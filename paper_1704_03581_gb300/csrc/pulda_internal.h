@@ -63,7 +63,7 @@ enum : int { ST_TOKENS = 0, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_DEADROWS, ST_
 // Running totals of the z-step slots live at ST_COUNT + slot and are cleared
 // only at pulda_init.
 constexpr int ST_TOTAL_SLOTS = 2 * ST_COUNT;
-enum : unsigned long long { ERR_DEGENERATE = 1, ERR_INTERNAL = 2, ERR_GAMMA = 4 };
+enum : unsigned long long { ERR_DEGENERATE = 1, ERR_INTERNAL = 2, ERR_GAMMA = 4, ERR_BOUNDS = 8 };
 
 // Fixed tables of one beta, built on the host once.
 struct HostTables {

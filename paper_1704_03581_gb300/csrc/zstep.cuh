@@ -9,6 +9,7 @@
 
 #include "device_rng.cuh"
 #include "pulda_internal.h"
+#include "checks.cuh"
 
 namespace pulda {
 
@@ -89,7 +90,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 // record layout) and returns its current topic.
 __device__ __forceinline__ int stage_token(const ZArgs &a, const DocRun &r, int i, uint4 *rec2, uint32_t *drow) {
     const int wv = r.w[i];
-    const int zo = r.z[i];
+    const int zo = guard_index(r.z[i], a.K, a.stats);
     const uint64_t t = static_cast<uint64_t>(r.index_base + i);
     const U4 x = draw(r.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), r.sweep, TAG_Z, 0);
     const int64_t cb = a.col_ptr[wv];
@@ -98,7 +99,7 @@ __device__ __forceinline__ int stage_token(const ZArgs &a, const DocRun &r, int 
     int ta = 0;
     if (nw > 0) {
         const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
-        ta = x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl];
+        ta = guard_index(x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl], a.K, a.stats);
     }
     rec2[0] = make_uint4(static_cast<uint32_t>(cb),
                          static_cast<uint32_t>(static_cast<u64>(cb) >> 32) | (static_cast<uint32_t>(ta) << 16),
