@@ -178,7 +178,7 @@ def code_hash(text: str) -> str:
 
 
 # The sources the one-warp z-step kernel is compiled from.
-Z_STEP_SOURCES = ("kernels.cu", "zstep.cuh", "device_rng.cuh", "pulda_internal.h")
+Z_STEP_SOURCES = ("kernels.cu", "zstep.cuh", "device_rng.cuh", "checks.cuh", "pulda_internal.h")
 
 
 def kernel_source_hash() -> str:
