@@ -37,11 +37,11 @@ def test_tiny_corpus_every_document_cooperative(path):
     s.close()
 
 
-@pytest.mark.parametrize("K", [1, 31, 33, 129, 200, 513, 1000, 1024, 1025, 3000])
+@pytest.mark.parametrize("K", [1, 31, 33, 129, 200, 513, 1000, 1024, 1025, 3000, 16384])
 def test_topic_counts_around_slot_edges(K):
-    """K around the 32-topic words, the 128 slots (R = 1, 2, 4, 8 topics per slot)
-    and the 1024 limit of the document side; empty, one-token and 32/33-token
-    documents beside long ones."""
+    """K around the 32-topic words, the 128 slots (R = 1, 2, 4, 8 topics per slot),
+    the 1024 limit of the document side and the largest K (m_d beyond 48 KB of
+    shared memory); empty, one-token and 32/33-token documents beside long ones."""
     rng = np.random.default_rng(100 + K)
     lengths = rng.integers(0, 700, size=40)
     lengths[[3, 5, 7, 9]] = [0, 1, 32, 33]
