@@ -159,7 +159,8 @@ def test_large_corpus_sampled_parity():
     """The large workload (D=300,000, V=100,000, ~99M tokens, K=1,000) in the
     launch configuration the benchmark times: one full sweep on the GPU; the
     oracle recomputes the whole Phi-step and the z-step of 3,000 sampled
-    documents (documents are independent given Phi)."""
+    documents (documents are independent given Phi), then a fold-in of the
+    corpus's longest documents (cooperative z-step) against that Phi."""
     import paper_1704_03581_gb300 as P
     c = synth.large()
     K = 1000
@@ -186,4 +187,14 @@ def test_large_corpus_sampled_parity():
         a, b = int(c.doc_off[d]), int(c.doc_off[d + 1])
         zo, _ = O.z_step(np.array([0, b - a], np.int64), c.w[a:b], z0[a:b], tab, 0, 1, index_base=a)
         assert np.array_equal(z1[a:b], zo), f"document {d} differs"
+    # fold-in against this Phi at full size: the six longest documents of the
+    # corpus go to the cooperative z-step (CTAs), two short ones to one warp each
+    L = np.diff(c.doc_off)
+    pick = list(np.argsort(-L, kind="stable")[:6]) + [int(docs[0]), int(docs[1])]
+    w_new = np.concatenate([c.w[c.doc_off[d]:c.doc_off[d + 1]] for d in pick])
+    off_new = np.zeros(len(pick) + 1, np.int64)
+    np.cumsum(L[pick], out=off_new[1:])
+    zg = s.infer(w_new, off_new, 2, seed=13)
+    zo = O.infer(tab, w_new, off_new, 2, 13)
+    assert not first_mismatch(zg, zo, off_new)
     s.close()
