@@ -578,7 +578,7 @@ def run_batched(args):
     N = sum(c.N for c in corpora)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    K, W = args.steps, max(args.warmup, 12)
+    K, W = args.steps, max(args.warmup, 6)
     b = P.Batch(chains, stream=stream.cuda_stream, coop_min_len=args.coop_min_len)
     b.sweep(W)                          # the first sweeps also time the tuning candidates
     b.sync()

@@ -254,11 +254,10 @@ typedef struct pulda_batch pulda_batch;
  * set, is used for all chains; opt->warps_per_block in 1..8 fixes the z-step
  * CTA size instead of tuning it over {2, 4, 8}; opt->coop_min_len -1 keeps
  * every document on one warp, > 0 sends the documents at least that long (of
- * every chain) to the cooperative z-step, 0 tunes it: after the CTA sizes, the
- * first sweeps also time the thresholds max(256, N / 8000) and a quarter of it
- * (N = tokens of all chains) against none; docs_per_warp must be 0 or 1.
- * Tuning times each candidate on two real sweeps (in order, then in reverse):
- * up to 12 sweeps with everything tuned. */
+ * every chain) to the cooperative z-step, 0 sends those of at least
+ * max(256, N / 8000) tokens (N = tokens of all chains), the single-chain rule;
+ * docs_per_warp must be 0 or 1.  Tuning times each CTA size on two real sweeps
+ * (in order, then in reverse): it ends after sweep 6. */
 pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains, int32_t n_chains,
                               const pulda_options *opt);
 /* pulda_batch_sweep -- n_sweeps sweeps of every chain (asynchronous, except

@@ -1,9 +1,9 @@
 // Many independent chains (corpora of uneven D, N, K, V) advanced together:
 // every kernel of a sweep runs once over all chains' work items, and the six
 // launches of a sweep are captured once into a CUDA graph and replayed.  The
-// z-step CTA size, then the cooperative threshold, are picked by timing the
-// candidates on the first sweeps (a launch shape never changes a result, so
-// tuning costs no extra sweeps).
+// z-step CTA size is picked by timing the candidates on the first sweeps (a
+// launch shape never changes a result, so tuning costs no extra sweeps); the
+// longest documents go to the cooperative z-step by the single-chain rule.
 #include <algorithm>
 #include <cstdio>
 #include <numeric>
@@ -27,18 +27,16 @@ struct pulda_batch {
     int64_t sweep = 0;
     // tuning candidates (z-step warps per CTA, cooperative threshold; 0 = none),
     // timed on real sweeps: first the CTA sizes, then thresholds at the best size
-    // Each phase times its candidates twice, in order and then in reverse, so
-    // the falling cost of the first sweeps after the uniform start does not
-    // favour the candidates timed later.
+    // The candidates are timed twice, in order and then in reverse, so the
+    // falling cost of the first sweeps after the uniform start does not favour
+    // the candidates timed later.
     struct Cand { int warps; int64_t coop_len; };
     std::vector<Cand> cand;
     std::vector<float> cand_ms;     // summed over the candidate's timed sweeps
     std::vector<int> sched;         // candidate indices still to time in this phase
     size_t sched_pos = 0;
     int phase_first = 0;            // first candidate index of the current phase
-    std::vector<int64_t> coop_try;  // thresholds for the second phase
     bool tuned = false;
-    bool phase2 = false;
     int64_t coop_len = 0;           // in use
     std::vector<int64_t> dlen;      // document lengths in work-list order (longest first)
     cudaGraph_t graph = nullptr;
@@ -89,15 +87,6 @@ void schedule_phase(pulda_batch *b, int first) {
     for (int c = first; c < n; ++c) b->sched.push_back(c);
     for (int c = n - 1; c >= first; --c) b->sched.push_back(c);
     b->cand_ms.resize(b->cand.size(), 0.0f);
-}
-
-// The second phase: the best CTA size without and with each cooperative threshold.
-void start_coop_phase(pulda_batch *b, int warps) {
-    b->phase2 = true;
-    const int first = static_cast<int>(b->cand.size());
-    b->cand.push_back({warps, 0});
-    for (int64_t L : b->coop_try) b->cand.push_back({warps, L});
-    schedule_phase(b, first);
 }
 
 void apply_candidate(pulda_batch *b, const pulda_batch::Cand &c) {
@@ -269,14 +258,16 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     bl.kmax = kmax;
     bl.phi_grid = b->sms * batch_phi_blocks_per_sm(kmax);
     bl.coop_grid = b->sms * batch_coop_blocks_per_sm(kmax);
-    // cooperative thresholds: fixed, none, or tuned over the automatic rule of
-    // the single-chain z-step (documents that would outlast the pass on one
-    // warp) and a quarter of it
-    const int64_t fixed_coop = o.coop_min_len > 0 ? o.coop_min_len : 0;
+    // The cooperative threshold: fixed, none, or the automatic rule of the
+    // single-chain z-step over all chains' tokens (documents that would outlast
+    // the pass on one warp).  It is not timed: on the 32-chain workload, timing
+    // thresholds on a few sweeps chose a quarter of the rule's (and once none),
+    // while over the steady sweeps the rule's threshold ran at 42.9 ms per sweep
+    // against 47.2 (a quarter) and 53.0 (none).
+    int64_t fixed_coop = o.coop_min_len > 0 ? o.coop_min_len : 0;
     if (o.coop_min_len == 0) {
-        const int64_t L1 = std::max<int64_t>(kCoopAutoMin, n_tokens / kCoopAutoDiv + 1);
-        for (int64_t L : {L1, std::max<int64_t>(kCoopAutoMin, L1 / 4)})
-            if (count_coop_items(b, L) > 0 && (b->coop_try.empty() || b->coop_try.back() != L)) b->coop_try.push_back(L);
+        const int64_t L = std::max<int64_t>(kCoopAutoMin, n_tokens / kCoopAutoDiv + 1);
+        if (count_coop_items(b, L) > 0) fixed_coop = L;
     }
     if (o.warps_per_block > 0) {
         b->cand.push_back({o.warps_per_block, fixed_coop});
@@ -285,8 +276,7 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
             if (w <= kMultiWarps && z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back({w, fixed_coop});
         if (b->cand.empty()) b->cand.push_back({1, fixed_coop});
     }
-    if (b->cand.size() == 1 && b->coop_try.empty()) b->tuned = true;
-    else if (b->cand.size() == 1) start_coop_phase(b, b->cand.front().warps);   // only the threshold to tune
+    if (b->cand.size() == 1) b->tuned = true;
     else schedule_phase(b, 0);
     apply_candidate(b, b->cand.front());
     if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
@@ -321,12 +311,8 @@ pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps) {
                 int best = b->phase_first;
                 for (int k = b->phase_first; k < static_cast<int>(b->cand.size()); ++k)
                     if (b->cand_ms[k] < b->cand_ms[best]) best = k;
-                if (!b->phase2 && !b->coop_try.empty()) {
-                    start_coop_phase(b, b->cand[best].warps);
-                } else {
-                    apply_candidate(b, b->cand[best]);
-                    b->tuned = true;
-                }
+                apply_candidate(b, b->cand[best]);
+                b->tuned = true;
             }
         } else {
             if (!b->exec) {

@@ -600,7 +600,7 @@ constexpr int kGather = PULDA_ZGATHER;
 // With m0 set, m starts from those K counts (a slice of a longer document,
 // from the document's counts at the start of the pass) instead of the run's
 // own topics.
-__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, const uint32_t *m0 = nullptr) {
+__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, const uint32_t *m0 = nullptr) {
     const int lane = threadIdx.x & 31;
     const int K = a.K;
     const bool use_bm = a.bitmap != nullptr && a.path != 1;
@@ -657,6 +657,13 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
         const uint32_t *bits = reinterpret_cast<const uint32_t *>(a.bitmap);
         uint32_t bm_next = 0u;
         if (use_bm && lane < a.KW) bm_next = bits[2 * (static_cast<int64_t>(rec[1].z) * a.KW + lane)];
+        // this block's counters, in 32 bits (at most 32 tokens of K <= 16384),
+        // added to the warp's 64-bit counters once per block
+        // (c_min: sum of min(K_d, K_v), the same in every lane; c_cnt: tokens
+        // with K_d < K_v in bits 0-5, alias draws in 6-11, zero-mass tokens in
+        // 12-17 -- each at most 32 -- and this lane's share of |J| (at most
+        // 32 x 32) from bit 18)
+        uint32_t c_min = 0, c_cnt = 0;
         for (int tt = 0; tt < cnt; ++tt) {
             const uint4 t0 = rec[2 * tt], t1 = rec[2 * tt + 1];
             const int kold = static_cast<int>(t1.w >> 16);
@@ -677,8 +684,11 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
                 if (use_bm && lane == (kold >> 5)) mbits &= ~(1u << (kold & 31));
             }
             __syncwarp();
-            st.add(2, static_cast<u64>(kd < n_w ? kd : n_w));
-            st.add(5, kd < n_w ? 1u : 0u);
+            c_min += static_cast<uint32_t>(kd < n_w ? kd : n_w);
+            c_cnt += kd < n_w ? 1u : 0u;
+            // |J| from the bitmaps on either side (the column side's topics with
+            // m > 0 are the same set); without bitmaps the column loop counts it
+            if (use_bm) c_cnt += static_cast<uint32_t>(__popc(bm & mbits)) << 18;
             // The document side needs the word's dense q row (q of topic 32 lane + b
             // at qd[b]); a word without one is iterated on the column side.
             const uint32_t drow = drow_of[tt];
@@ -693,7 +703,6 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
             int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
             if (docside) {
                 uint32_t rem = bm & mbits;
-                st.inter += static_cast<u64>(__popc(rem));
 #pragma unroll
                 for (int t = 0; t < kGather; ++t) {
                     bp[t] = -1;
@@ -722,21 +731,21 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
                 for (int j = seg0; j < seg1; ++j) {
                     const uint32_t mk = m[mi(guard_index(a.topic[col + j], K, a.stats))];
                     acc += static_cast<u64>(qcol[j]) * mk;
-                    nj += mk != 0u;
+                    if (!use_bm) nj += mk != 0u;
                 }
-                st.inter += static_cast<u64>(nj);
+                if (!use_bm) c_cnt += nj << 18;
             }
             const u64 incl = warp_incl_scan64(acc);
             const u64 B = __shfl_sync(0xFFFFFFFFu, incl, 31);
             const u64 T = At + (B << kFracBits);
             int knew = kold;
             if (T == 0) {
-                st.add(3, 1);
+                c_cnt += 1u << 12;
             } else {
                 const u64 rr = __umul64hi(U, T);
                 if (rr < At) {
                     knew = ka;
-                    st.add(1, 1);
+                    c_cnt += 1u << 6;
                 } else {
                     const u64 rb = (rr - At) >> kFracBits;
                     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, rb < incl);
@@ -791,7 +800,15 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, ZCount &st, c
             if (lane == tt) znew = knew;
         }
         if (valid) r.z[i] = static_cast<int16_t>(znew);
-        st.add(0, static_cast<u64>(cnt));
+        {   // the block's counts into the warp's 64-bit counters, lane j its counter j
+            const uint32_t jsum = __reduce_add_sync(0xFFFFFFFFu, c_cnt >> 18);
+            const uint32_t v = lane == 0 ? static_cast<uint32_t>(cnt)
+                             : lane == 1 ? (c_cnt >> 6) & 63u
+                             : lane == 2 ? c_min
+                             : lane == 3 ? (c_cnt >> 12) & 63u
+                             : lane == 4 ? jsum : c_cnt & 63u;
+            if (lane < 6) wcnt[lane] += v;
+        }
         r.budget -= cnt;
         r.pos += cnt;
         if (r.pos == r.len) { r.pos = 0; r.sweep += 1; }
@@ -805,7 +822,8 @@ __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
     uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
-    ZCount st;
+    u64 *wcnt = z_warp_counters(m, a.K);
+    zero_warp_counters(wcnt);
     const uint32_t sweep = sweep_of(a);
     for (;;) {
         int item = 0;
@@ -827,9 +845,9 @@ __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs
             len = static_cast<int>(a.doc_off[d + 1] - s);
         }
         DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep, 0, len, 1};
-        z_doc_warp(a, m, r, st, m0);
+        z_doc_warp(a, m, r, wcnt, m0);
     }
-    flush_warp_z_stats(a.stats, st);
+    flush_warp_counters(a.stats, wcnt);
 }
 
 // m0[j * K + k] = the topic-k count of document sliced_docs[j] (one warp per
@@ -855,6 +873,8 @@ __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_m
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
     uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(kmax);
+    u64 *wcnt = z_warp_counters(m, kmax);     // beyond every chain's m and token records
+    zero_warp_counters(wcnt);
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(work, 1);
@@ -865,9 +885,8 @@ __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_m
         const int64_t s = a.doc_off[it.y];
         DocRun r{a.w + s, a.z + s, static_cast<int>(a.doc_off[it.y + 1] - s), a.seed, a.index_base + s, sweep_of(a),
                  0, a.doc_off[it.y + 1] - s, 1};
-        ZCount st;
-        z_doc_warp(a, m, r, st);
-        flush_warp_z_stats(a.stats, st);
+        z_doc_warp(a, m, r, wcnt);
+        flush_warp_counters(a.stats, wcnt);
     }
 }
 
@@ -1202,7 +1221,8 @@ __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSl
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
     uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
-    ZCount st;
+    u64 *wcnt = z_warp_counters(m, a.K);
+    zero_warp_counters(wcnt);
     for (;;) {
         int item = 0;
         uint64_t t0 = 0;
@@ -1229,13 +1249,13 @@ __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSl
         }
         DocRun r{arena_w + sl.off, z, sl.len, sl.seed, 0, sweep, pos, slice,
                  static_cast<int>(sl.sweep_end - sweep), deadline};
-        z_doc_warp(a, m, r, st);
+        z_doc_warp(a, m, r, wcnt);
         if (lane == 0) {
             slots[idx].sweep = r.sweep;
             slots[idx].pos = r.pos;
         }
     }
-    flush_warp_z_stats(a.stats, st);
+    flush_warp_counters(a.stats, wcnt);
 }
 
 // ============================================================== exports

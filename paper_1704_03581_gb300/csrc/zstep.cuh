@@ -51,7 +51,15 @@ __host__ __device__ __forceinline__ int mi(int k) { return k + (k >> 5); }
 // to 16 bytes), then the staging records of the 32 tokens in flight.
 __host__ __device__ __forceinline__ int z_m_words(int K) { return (K + (K >> 5) + 1 + 3) & ~3; }
 constexpr int kTokRecWords = 9;     // two uint4 per token, and the offset of its word's dense q row
-__host__ __device__ __forceinline__ int z_warp_words(int K) { return z_m_words(K) + 32 * kTokRecWords; }
+// ... then the warp's six 64-bit counters (z_doc_warp's, 16-byte aligned).
+constexpr int kWarpCountWords = 16;
+__host__ __device__ __forceinline__ int z_warp_words(int K) { return z_m_words(K) + 32 * kTokRecWords + kWarpCountWords; }
+// The counters of a warp whose shared-memory region starts at m and was sized
+// for K topics: {tokens, alias draws, sum min(K_d, K_v), zero-mass tokens,
+// sum |J|, tokens with K_d < K_v}, lane j updating counter j.
+__device__ __forceinline__ unsigned long long *z_warp_counters(uint32_t *m, int K) {
+    return reinterpret_cast<unsigned long long *>(m + z_m_words(K) + 32 * kTokRecWords);
+}
 
 // Counters of a z-step warp.  The warp-uniform ones are held one per lane
 // (lane j holds counter j), which keeps five 64-bit values out of every
@@ -125,6 +133,28 @@ __device__ inline void flush_z_stats(unsigned long long *stats, const u64 (&c)[6
 
 // The same from a warp running z_doc_warp: lanes 0-3 and 5 hold their
 // counters, sum |J| is summed over the lanes.  Every lane calls it.
+// Zeroes, and adds to the sweep's and the running totals, a warp's counters
+// kept in its shared memory (z_warp_counters).  Every lane calls them.
+__device__ __forceinline__ void zero_warp_counters(unsigned long long *cnt) {
+    if ((threadIdx.x & 31) < 6) cnt[threadIdx.x & 31] = 0;
+    __syncwarp();
+}
+
+__device__ inline void flush_warp_counters(unsigned long long *stats, unsigned long long *cnt) {
+    const int lane = threadIdx.x & 31;
+    const int slot[6] = {ST_TOKENS, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_SUMINT, ST_DOCSIDE};
+    __syncwarp();
+    if (lane < 6) {
+        const unsigned long long v = cnt[lane];
+        if (v) {
+            atomicAdd(&stats[slot[lane]], v);
+            atomicAdd(&stats[ST_COUNT + slot[lane]], v);
+        }
+        cnt[lane] = 0;
+    }
+    __syncwarp();
+}
+
 __device__ inline void flush_warp_z_stats(unsigned long long *stats, ZCount &c) {
     const u64 inter = warp_sum64(c.inter);
     const int lane = threadIdx.x & 31;
