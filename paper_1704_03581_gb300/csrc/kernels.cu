@@ -629,18 +629,24 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
         for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
         kd = cnt;
     }
-    const uint32_t sweep_end = r.sweep + static_cast<uint32_t>(r.max_pass_end);
+    // The run's state lives in the warp's shared memory while its tokens are
+    // drawn (it is read and advanced once per 32-token block), which keeps it
+    // out of the registers of the token loop.
+    DocRun &rs = *z_warp_run(wcnt);
+    if (lane == 0) rs = r;
+    __syncwarp();
+    const uint32_t sweep_end = rs.sweep + static_cast<uint32_t>(rs.max_pass_end);
     bool first = true;
-    while (r.budget > 0 && r.sweep != sweep_end) {
-        if (r.deadline != ~0ull && !first) {
+    while (rs.budget > 0 && rs.sweep != sweep_end) {
+        if (rs.deadline != ~0ull && !first) {
             uint64_t now = 0;
             if (lane == 0) now = global_ns();
-            if (__shfl_sync(0xFFFFFFFFu, now, 0) >= r.deadline) break;
+            if (__shfl_sync(0xFFFFFFFFu, now, 0) >= rs.deadline) break;
         }
         first = false;
-        const int i0 = r.pos;
-        const int64_t left = static_cast<int64_t>(r.len - i0);
-        const int cnt = static_cast<int>(min(static_cast<int64_t>(32), min(left, r.budget)));
+        const int i0 = rs.pos;
+        const int64_t left = static_cast<int64_t>(rs.len - i0);
+        const int cnt = static_cast<int>(min(static_cast<int64_t>(32), min(left, rs.budget)));
         const int i = i0 + lane;
         const bool valid = lane < cnt;
         int znew = 0;
@@ -651,7 +657,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
         // (column starts are below 2^48, K_v <= 16384, topics < 16384).
         uint4 *rec = reinterpret_cast<uint4 *>(m + z_m_words(K));
         uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);   // q row offset of the token's word, or ~0
-        if (valid) znew = stage_token(a, r, i, rec + 2 * lane, drow_of + lane);
+        if (valid) znew = stage_token(a, rs, i, rec + 2 * lane, drow_of + lane);
         __syncwarp();
         // the bits half of the word's bitmap entries (32 topics per lane)
         const uint32_t *bits = reinterpret_cast<const uint32_t *>(a.bitmap);
@@ -799,7 +805,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             __syncwarp();
             if (lane == tt) znew = knew;
         }
-        if (valid) r.z[i] = static_cast<int16_t>(znew);
+        if (valid) rs.z[i] = static_cast<int16_t>(znew);
         {   // the block's counts into the warp's 64-bit counters, lane j its counter j
             const uint32_t jsum = __reduce_add_sync(0xFFFFFFFFu, c_cnt >> 18);
             const uint32_t v = lane == 0 ? static_cast<uint32_t>(cnt)
@@ -809,11 +815,16 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
                              : lane == 4 ? jsum : c_cnt & 63u;
             if (lane < 6) wcnt[lane] += v;
         }
-        r.budget -= cnt;
-        r.pos += cnt;
-        if (r.pos == r.len) { r.pos = 0; r.sweep += 1; }
+        __syncwarp();
+        if (lane == 0) {
+            rs.budget -= cnt;
+            rs.pos += cnt;
+            if (rs.pos == rs.len) { rs.pos = 0; rs.sweep += 1; }
+        }
         __syncwarp();
     }
+    r = rs;
+    __syncwarp();
 }
 
 // One chain, one document per warp (dynamically scheduled, longest first),

@@ -51,8 +51,9 @@ __host__ __device__ __forceinline__ int mi(int k) { return k + (k >> 5); }
 // to 16 bytes), then the staging records of the 32 tokens in flight.
 __host__ __device__ __forceinline__ int z_m_words(int K) { return (K + (K >> 5) + 1 + 3) & ~3; }
 constexpr int kTokRecWords = 9;     // two uint4 per token, and the offset of its word's dense q row
-// ... then the warp's six 64-bit counters (z_doc_warp's, 16-byte aligned).
-constexpr int kWarpCountWords = 16;
+// ... then the warp's six 64-bit counters (z_doc_warp's, 16-byte aligned) and
+// the document run it is working on.
+constexpr int kWarpCountWords = 32;
 __host__ __device__ __forceinline__ int z_warp_words(int K) { return z_m_words(K) + 32 * kTokRecWords + kWarpCountWords; }
 // The counters of a warp whose shared-memory region starts at m and was sized
 // for K topics: {tokens, alias draws, sum min(K_d, K_v), zero-mass tokens,
@@ -87,6 +88,12 @@ struct DocRun {
     int max_pass_end;        // stop when the pass counter reaches sweep + this many passes
     uint64_t deadline = ~0ull;   // global timer (ns): no 32-token block starts after it, but the first
 };
+// The run a z-step warp is working on, kept after its six counters (8-byte
+// aligned: the counter area starts 16-byte aligned).
+static_assert(6 * sizeof(unsigned long long) + sizeof(DocRun) <= kWarpCountWords * sizeof(uint32_t),
+              "the warp's counters and document run must fit its counter area");
+__device__ __forceinline__ DocRun *z_warp_run(unsigned long long *wcnt) { return reinterpret_cast<DocRun *>(wcnt + 6); }
+
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
