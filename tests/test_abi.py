@@ -86,3 +86,40 @@ def test_batch_rejects_bad_options_without_a_gpu():
         assert st == -1 and not b.value
         assert frag in P.lib().pulda_batch_last_error(None), P.lib().pulda_batch_last_error(None)
 
+
+
+def test_binding_structures_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the C header's sizes and field
+    offsets (a C probe compiled against include/pulda.h prints them)."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"pulda_options": P.Options, "pulda_sweep_stats": P.SweepStats, "pulda_chain_desc": P.ChainDesc,
+               "pulda_result": P.ServeResult}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pulda.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, key, val = line.split()
+            got[(name, key)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
