@@ -220,10 +220,13 @@ pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids_host, const in
  * the process exits), so D_new is limited to 65,536 documents per call; larger
  * D_new returns PULDA_ERR_INVALID.  The first call on each device looks up
  * that array's device address once; make that first call before any stream
- * capture.  All calls on a device share the array: calls that overlap on the
- * GPU race and must be serialised by the caller.  Synchronous on the handle's
- * stream.  Errors: PULDA_ERR_INVALID (limits, NULL pointers, no Phi yet, bad
- * ids or offsets -- checked on the device), PULDA_ERR_CUDA. */
+ * capture.  The calling thread's current device must be the one the handle
+ * was created on.  All calls on a device share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller.  The call waits for
+ * the handle's stream before it returns.  Errors: PULDA_ERR_INVALID (limits,
+ * NULL pointers, another current device, no Phi yet, bad ids or offsets --
+ * checked on the device; the message names the first bad token or document),
+ * PULDA_ERR_CUDA. */
 pulda_status pulda_infer_noalloc(pulda_handle *h, const int32_t *word_ids_dev, const int64_t *doc_offsets_dev,
                                  int64_t D_new, int64_t N_new, int32_t n_sweeps, uint64_t seed,
                                  int16_t *z_out_dev);

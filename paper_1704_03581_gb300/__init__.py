@@ -240,10 +240,42 @@ def pulda_infer(h, word_ids, doc_offsets, n_sweeps: int, seed: int, K: int, want
     return (z[:w.shape[0]], m) if want_m else z[:w.shape[0]]
 
 
-def pulda_infer_noalloc(h, word_ids_dev, doc_offsets_dev, n_sweeps: int, seed: int, z_out_dev):
-    """Device tensors in and out; nothing is allocated (see include/pulda.h)."""
+def _check_noalloc_tensors(word_ids_dev, doc_offsets_dev, z_out_dev) -> tuple[int, int]:
+    """(D, N) of pulda_infer_noalloc's device tensors, or ValueError: the C
+    call trusts the sizes it is given, so a wrong dtype, a strided view or a
+    short output would make its kernels read or write past a buffer."""
+    want = (("word_ids_dev", word_ids_dev, "int32"), ("doc_offsets_dev", doc_offsets_dev, "int64"),
+            ("z_out_dev", z_out_dev, "int16"))
+    for name, t, dt in want:
+        if not hasattr(t, "data_ptr") or not hasattr(t, "is_cuda"):
+            raise ValueError(f"{name} must be a torch tensor")
+        if str(t.dtype) != f"torch.{dt}":
+            raise ValueError(f"{name} must be {dt} (got {t.dtype})")
+        if t.dim() != 1:
+            raise ValueError(f"{name} must be one-dimensional (got shape {tuple(t.shape)})")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
     D = int(doc_offsets_dev.shape[0]) - 1
     N = int(word_ids_dev.shape[0])
+    if D < 0:
+        raise ValueError("doc_offsets_dev needs at least one entry (D + 1 offsets)")
+    if int(z_out_dev.shape[0]) < N:
+        raise ValueError(f"z_out_dev holds {int(z_out_dev.shape[0])} topics, fewer than the {N} word ids")
+    for name, t, _ in want:
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+    devs = {t.device.index for _, t, _ in want}
+    if len(devs) != 1:
+        raise ValueError(f"the three tensors must be on one device (got {sorted(devs)})")
+    return D, N
+
+
+def pulda_infer_noalloc(h, word_ids_dev, doc_offsets_dev, n_sweeps: int, seed: int, z_out_dev):
+    """Device tensors in and out; nothing is allocated (see include/pulda.h).
+    word_ids_dev int32[N], doc_offsets_dev int64[D+1], z_out_dev int16[>= N],
+    contiguous CUDA tensors on the handle's device (the library checks the
+    device; the values of ids and offsets are checked on the GPU)."""
+    D, N = _check_noalloc_tensors(word_ids_dev, doc_offsets_dev, z_out_dev)
     _check(h, lib().pulda_infer_noalloc(h, _ptr(word_ids_dev), _ptr(doc_offsets_dev), D, N, n_sweeps,
                                         int(seed) & (2 ** 64 - 1), _ptr(z_out_dev)))
     return z_out_dev

@@ -230,6 +230,7 @@ ZArgs z_args(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, 
 bool handle_view(pulda_handle *h, HandleView *out) {
     if (!h || !out) return false;
     out->stream = h->stream;
+    out->device = h->device;
     out->K = h->K;
     out->V = h->V;
     out->have_phi = h->have_phi;

@@ -15,6 +15,7 @@
 // streams) race on it and must be serialised by the caller.  What must start
 // at zero is cleared by each call.
 #include <cstdint>
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/pulda.h"
@@ -29,9 +30,12 @@ constexpr int64_t kNoAllocMaxDocs = 65536;
 // Layout of the scratch array (bytes, each part 256-byte aligned).
 constexpr size_t kOffStats = 0;                                       // u64[ST_TOTAL_SLOTS]
 constexpr size_t kOffWork = 256;                                      // int[4]: z-step work counter
-constexpr size_t kOffFlag = 512;                                      // int[4]: input check result
+constexpr size_t kOffFlag = 512;                                      // u64[2]: first bad token, first bad document
 constexpr size_t kOffOrder = 768;                                     // int32[kNoAllocMaxDocs]
 constexpr size_t kScratchBytes = kOffOrder + sizeof(int32_t) * kNoAllocMaxDocs;   // 262,912 bytes
+static_assert(ST_TOTAL_SLOTS * sizeof(unsigned long long) <= kOffWork, "the counters overlap the work counter");
+static_assert(4 * sizeof(int) <= kOffFlag - kOffWork, "the work counters overlap the input check");
+static_assert(2 * sizeof(unsigned long long) <= kOffOrder - kOffFlag, "the input check overlaps the schedule");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -40,15 +44,14 @@ constexpr int kMaxDevices = 64;
 unsigned char *g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-// One-time set-up, with the calling thread's current device: look up where
-// the array lives on that device.  The host-side symbol g_noalloc_scratch is
-// only a stand-in and must never be handed to a kernel.
-cudaError_t scratch_on_current_device(unsigned char **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+// One-time set-up per device, with that device current (the caller checks
+// that it is the handle's): look up where the array lives on it.  The
+// host-side symbol g_noalloc_scratch is only a stand-in and must never be
+// handed to a kernel.
+cudaError_t scratch_on_device(int dev, unsigned char **out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
+    cudaError_t e = cudaSuccess;
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -60,21 +63,20 @@ cudaError_t scratch_on_current_device(unsigned char **out) {
 }
 
 // Checks the caller's device inputs (ids in [0, V), offsets nondecreasing from
-// 0 to N) and writes the identity document schedule.  flag[0] != 0 on a bad
-// input; flag[1] = the offending index.
-__global__ void k_noalloc_check(const int32_t *w, int64_t N, const int64_t *off, int64_t D, int V, int *flag,
-                                int32_t *order) {
+// 0 to N) and writes the identity document schedule.  first[0] becomes the
+// smallest position of a word id outside [0, V), first[1] the smallest
+// document with bad offsets; both start at ~0 (none).
+__global__ void k_noalloc_check(const int32_t *w, int64_t N, const int64_t *off, int64_t D, int V,
+                                unsigned long long *first, int32_t *order) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     const int64_t t0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     for (int64_t i = t0; i < N; i += stride)
-        if (w[i] < 0 || w[i] >= V) { atomicExch(&flag[0], 1); atomicExch(&flag[1], static_cast<int>(i)); }
+        if (w[i] < 0 || w[i] >= V) atomicMin(&first[0], static_cast<unsigned long long>(i));
     for (int64_t d = t0; d < D; d += stride) {
         order[d] = static_cast<int32_t>(d);
         const int64_t a = off[d], b = off[d + 1];
-        if (a < 0 || b < a || b > N || (d == 0 && a != 0) || (d == D - 1 && b != N) || b - a > (int64_t(1) << 22)) {
-            atomicExch(&flag[0], 2);
-            atomicExch(&flag[1], static_cast<int>(d));
-        }
+        if (a < 0 || b < a || b > N || (d == 0 && a != 0) || (d == D - 1 && b != N) || b - a > (int64_t(1) << 22))
+            atomicMin(&first[1], static_cast<unsigned long long>(d));
     }
 }
 
@@ -99,30 +101,46 @@ extern "C" pulda_status pulda_infer_noalloc(pulda_handle *h, const int32_t *word
     if (D_new == 0) return PULDA_OK;
     if (!word_ids_dev || !doc_offsets_dev || !z_out_dev)
         return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID, "a device pointer is NULL"));
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_CUDA, cudaGetErrorString(e)));
+    if (dev != hv.device) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "the calling thread's current device (%d) is not the handle's (%d)", dev, hv.device);
+        return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID, msg));
+    }
     unsigned char *scratch = nullptr;
-    cudaError_t e = scratch_on_current_device(&scratch);
+    e = scratch_on_device(dev, &scratch);
     if (e != cudaSuccess)
         return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_CUDA, cudaGetErrorString(e)));
     cudaStream_t st = hv.stream;
     auto *stats = reinterpret_cast<unsigned long long *>(scratch + kOffStats);
     auto *work = reinterpret_cast<int *>(scratch + kOffWork);
-    auto *flag = reinterpret_cast<int *>(scratch + kOffFlag);
+    auto *first = reinterpret_cast<unsigned long long *>(scratch + kOffFlag);
     auto *order = reinterpret_cast<int32_t *>(scratch + kOffOrder);
-    // the array keeps the previous call's contents: clear what counts from zero
-    e = cudaMemsetAsync(scratch, 0, kOffOrder, st);
+    // the array keeps the previous call's contents: clear what counts from
+    // zero, and set the input check's "first bad index" slots to ~0 (none)
+    e = cudaMemsetAsync(scratch, 0, kOffFlag, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(first, 0xFF, 2 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) {
-        k_noalloc_check<<<64, 256, 0, st>>>(word_ids_dev, N_new, doc_offsets_dev, D_new, hv.V, flag, order);
+        k_noalloc_check<<<64, 256, 0, st>>>(word_ids_dev, N_new, doc_offsets_dev, D_new, hv.V, first, order);
         e = cudaGetLastError();
     }
-    int hflag[2] = {0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hflag, flag, sizeof hflag, cudaMemcpyDeviceToHost, st);
+    unsigned long long hfirst[2] = {~0ull, ~0ull};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hfirst, first, sizeof hfirst, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_CUDA, cudaGetErrorString(e)));
-    if (hflag[0] == 1)
-        return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID, "a word id is outside [0, V)"));
-    if (hflag[0] == 2)
-        return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID,
-            "doc offsets must rise from 0 to N_new, each document at most 2^22 tokens"));
+    if (hfirst[1] != ~0ull) {
+        char msg[200];
+        snprintf(msg, sizeof msg, "doc offsets must rise from 0 to N_new, each document at most 2^22 tokens "
+                 "(first bad document: %llu)", hfirst[1]);
+        return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID, msg));
+    }
+    if (hfirst[0] != ~0ull) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "the word id at token %llu is outside [0, %d)", hfirst[0], hv.V);
+        return static_cast<pulda_status>(handle_fail(h, PULDA_ERR_INVALID, msg));
+    }
     launch_init_z(N_new, hv.K, seed, 0, z_out_dev, st);
     ZArgs a = hv.zargs;
     a.doc_off = doc_offsets_dev;

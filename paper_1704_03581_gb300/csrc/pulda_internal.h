@@ -284,6 +284,7 @@ constexpr int64_t kServeCoopAuto = 1024;
 // current Phi (api.cpp).
 struct HandleView {
     cudaStream_t stream;
+    int device;      // the device the handle was created on
     int K, V;
     bool have_phi;
     int z_warps, z_grid;

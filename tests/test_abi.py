@@ -123,3 +123,28 @@ def test_binding_structures_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_the_call():
+    """pulda_infer_noalloc hands raw device pointers to C, which trusts the
+    sizes: the binding refuses wrong dtypes, shapes, strides, a short output
+    and host tensors before anything reaches the library (no handle needed)."""
+    import pytest
+    import torch
+    w = torch.zeros(6, dtype=torch.int32)
+    off = torch.tensor([0, 2, 6], dtype=torch.int64)
+    z = torch.zeros(6, dtype=torch.int16)
+    cases = [
+        ((w.to(torch.int64), off, z), "word_ids_dev must be int32"),
+        ((w, off.to(torch.int32), z), "doc_offsets_dev must be int64"),
+        ((w, off, z.to(torch.int32)), "z_out_dev must be int16"),
+        ((w.view(2, 3), off, z), "one-dimensional"),
+        ((torch.zeros(12, dtype=torch.int32)[::2], off, z), "contiguous"),
+        ((w, off, z[:5]), "fewer than the 6 word ids"),
+        ((w, torch.zeros(0, dtype=torch.int64), z), "at least one entry"),
+        ((w, off, z), "must be a CUDA tensor"),
+        (([0, 1], off, z), "must be a torch tensor"),
+    ]
+    for (a, b, c), frag in cases:
+        with pytest.raises(ValueError, match=frag):
+            P.pulda_infer_noalloc(None, a, b, 1, 0, c)
