@@ -184,6 +184,129 @@ def test_phi_entries_follow_poisson_beta_plus_n():
     assert _chi2_counts(zero, lambda j: stats.poisson.pmf(j, b)) > 1e-4
 
 
+def _geo_pmf(j, p):
+    return p * (1.0 - p) ** j
+
+
+def test_beta_field_chains_past_the_gap_table():
+    """Eq. (9) with n = 0: every entry is an independent Pois(beta), so the
+    positions of the nonzero ones are i.i.d. Bernoulli(1 - e^-beta).  At
+    beta = 0.001 a gap exceeds the 1024-entry table of the skip-ahead walk
+    with probability e^-1.02 ~ 0.36, so the walk's chaining past the table
+    (a run of 1024 misses, then a fresh gap) is taken in about a third of the
+    gaps, often several times in a row.  Pinned three ways: the number of
+    hits (binomial), the gaps between hits (chi-square against
+    Geometric(1 - e^-beta), gaps of 1023/1024 and 2047/2048 binned alone so an
+    off-by-one in the chaining shows), and the hit rate at every position
+    (flat; the positions where chained runs end are binned alone)."""
+    beta, K, V, sweeps = 0.001, 4096, 1000, 50
+    b = float(np.float32(beta))
+    p = -math.expm1(-b)
+    n = np.zeros((V, K), dtype=np.int32)
+    n[0, :] = 100           # word 0 keeps every row alive; words 1.. are pure beta-field walks
+    ctx = O.Ctx(beta)
+    G = 3072                # gaps of at least G are binned together (censoring)
+    edges = [0, 64, 256, 512, 768, 1000, 1023, 1024, 1025, 1100, 1500, 2047, 2048, 2049, 2600, G]
+    gap_obs = np.zeros(len(edges), np.float64)      # bins [e_i, e_{i+1}) and [G, inf)
+    pos_hits = np.zeros(K, np.int64)
+    hits = ones = 0
+    cols = 0
+    for s in range(1, sweeps + 1):
+        c, S, dead = O.phi_draw(ctx, n, 41, s)
+        assert dead == 0
+        f = c[1:, :]
+        cols += f.shape[0]
+        nz = f > 0
+        pos_hits += nz.sum(axis=0)
+        hits += int(nz.sum())
+        ones += int((f == 1).sum())
+        for row in nz:
+            h = np.flatnonzero(row)
+            # starts: the walk's origin (-1) and every hit early enough that a
+            # gap of G fits before the end (a stopping time: the next gap is
+            # Geometric, independent of the past)
+            starts = np.concatenate([[-1], h[h <= K - 1 - G]])
+            nxt = np.searchsorted(h, starts, side="right")
+            if h.size == 0:
+                g = np.full(starts.shape, G)
+            else:
+                g = np.where(nxt < h.size, h[np.minimum(nxt, h.size - 1)] - starts - 1, G)
+            g = np.minimum(g, G)
+            gap_obs += np.bincount(np.searchsorted(edges, g, side="right") - 1, minlength=len(edges))
+    # 1. number of hits
+    assert stats.binomtest(hits, cols * K, p).pvalue > 1e-4
+    # values at hits are zero-truncated Pois(beta): P(c = 1 | c > 0) = beta e^-beta / (1 - e^-beta)
+    assert stats.binomtest(ones, hits, b * math.exp(-b) / p).pvalue > 1e-4
+    # 2. gaps
+    tot = gap_obs.sum()
+    cdf = lambda j: 1.0 - (1.0 - p) ** j           # P(gap < j)
+    probs = np.array([cdf(edges[i + 1]) - cdf(edges[i]) for i in range(len(edges) - 1)] + [(1.0 - p) ** G])
+    assert abs(probs.sum() - 1.0) < 1e-12
+    exp = probs * tot
+    assert gap_obs[-1] > 1000 and gap_obs[edges.index(1024)] > 10      # the chained branch is exercised
+    chi = ((gap_obs - exp) ** 2 / exp).sum()
+    assert stats.chi2.sf(chi, len(exp) - 1) > 1e-4, (gap_obs, exp)
+    # 3. hit rate by position: single positions around the ends of chained runs
+    singles = [1022, 1023, 1024, 1025, 2046, 2047, 2048, 2049, 3070, 3071, 3072, 3073]
+    o, e = [], []
+    mask = np.ones(K, bool)
+    for j in singles:
+        o.append(pos_hits[j]); e.append(cols * p); mask[j] = False
+    for lo in range(0, K, 256):
+        sel = np.flatnonzero(mask[lo:lo + 256]) + lo
+        o.append(pos_hits[sel].sum()); e.append(cols * p * sel.size)
+    o, e = np.array(o, np.float64), np.array(e)
+    chi = ((o - e) ** 2 / e).sum()
+    assert stats.chi2.sf(chi, len(o) - 1) > 1e-4
+
+
+def test_dead_row_redraw_walk_chains_past_the_gap_table():
+    """A redrawn row walks the beta field across V words with the same
+    skip-ahead; with V = 6000 and beta = 0.0002 its gaps pass the table in most
+    rows.  Given S_k > 0 the hit positions are i.i.d. Bernoulli(1 - e^-beta)
+    conditioned on at least one hit, so every position has the same hit rate
+    and the number of hits is a zero-truncated binomial."""
+    beta, V, K, sweeps = 0.0002, 6000, 40, 60
+    b = float(np.float32(beta))
+    p = -math.expm1(-b)
+    n = np.zeros((V, K), dtype=np.int32)
+    ctx = O.Ctx(beta)
+    pos_hits = np.zeros(V, np.int64)
+    counts = []
+    dead_total = 0
+    for s in range(1, sweeps + 1):
+        c, S, dead = O.phi_draw(ctx, n, 43, s)
+        dead_total += dead
+        assert (S > 0).all()
+        nz = c > 0                      # [V, K]
+        pos_hits += nz.sum(axis=1)
+        counts.extend(nz.sum(axis=0).tolist())
+    rows = sweeps * K
+    assert dead_total > rows // 4                   # P(S_k = 0) = e^{-V beta} ~ 0.30
+    q0 = (1.0 - p) ** V
+    # hits per row: Binomial(V, p) given >= 1
+    counts = np.array(counts)
+    kk = np.arange(1, 8)
+    pmf = stats.binom.pmf(kk, V, p) / (1 - q0)
+    o = np.append(np.bincount(counts, minlength=9)[1:8], (counts >= 8).sum()).astype(np.float64)
+    e = np.append(pmf, 1 - pmf.sum()) * rows
+    chi = ((o - e) ** 2 / e).sum()
+    assert stats.chi2.sf(chi, len(o) - 1) > 1e-4
+    # every position equally likely: E[hits at v] = rows * p / (1 - q0)
+    rate = rows * p / (1 - q0)
+    singles = [1022, 1023, 1024, 1025, 2046, 2047, 2048, 2049]
+    mask = np.ones(V, bool)
+    o, e = [], []
+    for j in singles:
+        o.append(pos_hits[j]); e.append(rate); mask[j] = False
+    for lo in range(0, V, 500):
+        sel = np.flatnonzero(mask[lo:lo + 500]) + lo
+        o.append(pos_hits[sel].sum()); e.append(rate * sel.size)
+    o, e = np.array(o, np.float64), np.array(e)
+    chi = ((o - e) ** 2 / e).sum()
+    assert stats.chi2.sf(chi, len(o) - 1) > 1e-4
+
+
 def test_phi_row_sums_and_normalisation():
     beta = 0.01
     rng = np.random.default_rng(3)

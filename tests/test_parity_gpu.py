@@ -62,6 +62,19 @@ def test_topic_counts_around_tile_edges(K, dpw):
     s.close()
 
 
+def test_beta_field_chaining_lockstep():
+    """beta = 0.001 over K = 3,000 topics and V = 5,000 words: the skip-ahead
+    walks of the beta-only entries pass the 1024-entry gap table in about a
+    third of their gaps (per word over K, and per dead row over V), so the
+    device walk's chaining is compared entry by entry with the oracle's."""
+    rng = np.random.default_rng(1001)
+    lengths = rng.poisson(40, size=250)
+    w, off = corpus_from_lengths(rng, lengths, 5000)
+    s, ch = lockstep(w, off, 3000, 5000, 0.1, 0.001, seed=9, sweeps=2, check_counts_every=2)
+    assert s.stats()["dead_rows"] > 0
+    s.close()
+
+
 @pytest.mark.parametrize("path", [0, 1, 2])
 def test_documents_longer_than_the_grouped_kernel_takes(path):
     """Documents over 65,535 tokens go to the one-document-per-warp kernel in
