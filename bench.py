@@ -38,28 +38,21 @@ sys.path.insert(0, ROOT)
 METRIC = "z-step tokens/s/GPU at K=1000 (% HBM roofline); serving p50/p99 vs plain"
 K_TOPICS = 1000
 ALPHA, BETA = 0.1, 0.01
-def kernels_per_sweep(w: np.ndarray, phi_mode: int, doc_off: np.ndarray | None = None, coop_min_len: int = 0,
-                      slice_len: int = 0, docs_per_warp: int = 0) -> int:
+def kernels_per_sweep(w: np.ndarray, phi_mode: int, layout: dict | None = None, slice_docs: int = 0) -> int:
     """Library kernels one sweep launches: the frequent-word histogram (when a
     word has more than 2^17 tokens), then Polya urn: counts+draws, dead-row
     fix-up, column scan, per-word tables; Dirichlet: counts, Gamma draws, two
-    row-sum passes, selection, column scan, per-word tables; then the z-step,
-    and the cooperative z-step beside it when some document reaches its
-    threshold (automatic: more than max(256, N / 8000) tokens), or the
-    pass-start counts before it when documents run in slices (four documents
-    per warp: the grouped kernel, and the one-warp kernel for documents over
-    65,535 tokens)."""
+    row-sum passes, selection, column scan, per-word tables; then the z-step
+    as the handle laid it out (pulda_z_layout): its main kernel, the
+    cooperative kernel when some document is on CTAs, the one-warp kernel for
+    documents too long for four per warp, or the pass-start counts before a
+    z-step in slices."""
     heavy = 1 if np.bincount(w).max(initial=0) > (1 << 17) else 0
-    extra = 0
-    if doc_off is not None:
-        longest = int(np.diff(doc_off).max(initial=0))
-        if docs_per_warp == 4:
-            extra = 1 if longest > 65535 else 0
-        elif slice_len > 0:
-            extra = 1 if longest > slice_len else 0
-        elif coop_min_len >= 0:
-            L = coop_min_len if coop_min_len > 0 else max(256, int(w.shape[0]) // 8000 + 1)
-            extra = 1 if longest >= L else 0
+    extra = 1 if slice_docs > 0 else 0
+    if layout is not None:
+        extra += (1 if layout["coop_docs"] > 0 else 0)
+        if layout["docs_per_warp"] == 4:
+            extra += 1 if layout["one_warp_docs"] > 0 else 0
     return heavy + (4 if phi_mode == 0 else 7) + 1 + extra
 
 
@@ -315,6 +308,7 @@ def run_pulda(args, corpus, rank: int, world: int):
     s = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                   stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp,
                   phi_mode=args.phi_mode, slice_len=args.slice_len, coop_min_len=args.coop_min_len)
+    layout = s.z_layout()
     s.sweep(args.burnin + args.warmup)
     s.sync()
     lp_before = s.log_posterior()[0]          # the diagnostic, outside the timed region
@@ -427,9 +421,10 @@ def run_pulda(args, corpus, rank: int, world: int):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_z_step", "peak_kind": f"{peak_kind} HBM copy bandwidth",
                      "algorithmic_bytes_per_launch": zbytes / K},
-        "gpu_launches": kernels_per_sweep(corpus.w, args.phi_mode, corpus.doc_off, args.coop_min_len,
-                                          args.slice_len, args.docs_per_warp) * K,
-        "z_kernel": "four documents per warp" if args.docs_per_warp == 4 else "one document per warp",
+        "gpu_launches": kernels_per_sweep(corpus.w, args.phi_mode, layout,
+                                          int(args.slice_len > 0 and np.diff(corpus.doc_off).max() > args.slice_len)) * K,
+        "z_kernel": (f"{'four documents' if layout['docs_per_warp'] == 4 else 'one document'} per warp; "
+                     f"{layout['coop_docs']} longest documents on one CTA each"),
         "clocks": clk,
         "cpu_baseline": cpu,
         "e2e": e2e,

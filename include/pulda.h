@@ -57,9 +57,12 @@ typedef struct {
                                column, 2 = iterate the document's topics whenever K <= 1024 */
     int32_t warps_per_block;/* warp-per-document z-step: warps per CTA, 1..4; 0 = 4, halved
                                while the CTA's shared memory would pass 160 KB */
-    int32_t docs_per_warp;  /* z-step documents per warp: 0 = auto (one), 1 = one, 4 = four
-                               (needs K <= 1024; documents longer than 65,535 tokens still
-                               go one per warp); results are identical */
+    int32_t docs_per_warp;  /* z-step documents per warp: 0 = auto (four when K <= 256 and
+                               every word's dense q row fits 2 GB -- measured faster there --
+                               else one), 1 = one, 4 = four (needs K <= 1024; falls back to
+                               one when the rows do not fit; documents longer than 65,535
+                               tokens still go one per warp, the longest to CTAs as
+                               coop_min_len says); results are identical */
     int32_t phi_mode;       /* 0 = Poisson Polya urn (Algorithm 2), 1 = Dirichlet (Algorithm 1:
                                phi_k ~ Dir(n_k + beta) through Gamma draws, entries below 2^-24
                                of their column's maximum dropped); the batched form takes 0 only */
@@ -75,12 +78,12 @@ typedef struct {
                                resampled by the 4 warps of one CTA together, token by token
                                (its intersections split over 128 lanes), concurrently with the
                                other documents' one-warp kernel; results are identical.
-                               0 = auto (documents longer than max(256, N / 8000) tokens:
-                               those that would outlast the rest of the pass on one warp),
-                               -1 = never, > 0 = this length.  Not used with docs_per_warp 4
-                               or slice_len > 0; the batched form takes 0 or -1 (one warp
-                               per document); a server on the handle uses it for requests
-                               (0 = requests of at least 1,024 tokens) */
+                               0 = auto (documents longer than max(256, N / 8000) tokens,
+                               N / 16000 beside four documents per warp: those that would
+                               outlast the rest of the pass), -1 = never, > 0 = this length.
+                               Not used with slice_len > 0; the batched form takes 0 or -1
+                               (one warp per document); a server on the handle uses it for
+                               requests (0 = requests of at least 1,024 tokens) */
     int32_t reserved[2];
 } pulda_options;
 
@@ -340,6 +343,14 @@ pulda_status pulda_serve_stats(pulda_server *s, int64_t *out);
 /* pulda_serve_close -- stop accepting, finish every submitted request, release
  * the server.  Returns the worker's error status, if any. */
 pulda_status pulda_serve_close(pulda_server *s);
+
+/* pulda_z_layout -- how the handle's corpus z-step is laid out (launch shape
+ * only: results never depend on it): documents per warp of the main z-step
+ * kernel (1 or 4), the number of (longest) documents resampled by one CTA
+ * each, and, beside four per warp, the documents too long for it that run one
+ * per warp (otherwise every document not on a CTA).  Any pointer may be NULL.
+ * Errors: PULDA_ERR_INVALID (NULL handle). */
+pulda_status pulda_z_layout(pulda_handle *h, int32_t *docs_per_warp, int64_t *coop_docs, int64_t *one_warp_docs);
 
 /* pulda_stats -- counters of the most recent sweep (synchronises). */
 pulda_status pulda_stats(pulda_handle *h, pulda_sweep_stats *out);

@@ -26,7 +26,7 @@ EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "puld
             "pulda_get_z",
             "pulda_get_z_dev", "pulda_set_z", "pulda_get_counts", "pulda_log_posterior", "pulda_get_phi",
             "pulda_get_word_tables",
-            "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_last_error", "pulda_free",
+            "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_z_layout", "pulda_last_error", "pulda_free",
             "pulda_batch_init", "pulda_batch_sweep", "pulda_batch_sync", "pulda_batch_get_z", "pulda_batch_stats",
             "pulda_batch_tuning", "pulda_batch_last_error", "pulda_batch_free",
             "pulda_serve_open", "pulda_serve_submit", "pulda_serve_poll", "pulda_serve_pending", "pulda_serve_stats",
@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "pulda_infer": [P, P, P, i64, i32, u64, P, P],
             "pulda_infer_noalloc": [P, P, P, i64, i64, i32, u64, P],
             "pulda_stats": [P, P],
+            "pulda_z_layout": [P, P, P, P],
         }
         sig.update({
             "pulda_batch_init": [P, P, i32, P],
@@ -287,6 +288,14 @@ def pulda_stats(h) -> dict:
     return s.as_dict()
 
 
+def pulda_z_layout(h) -> dict:
+    """The corpus z-step's launch layout: documents per warp of the main kernel,
+    documents on cooperative CTAs, documents one per warp beside them."""
+    d, c, o = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(h, lib().pulda_z_layout(h, ctypes.byref(d), ctypes.byref(c), ctypes.byref(o)))
+    return {"docs_per_warp": d.value, "coop_docs": c.value, "one_warp_docs": o.value}
+
+
 def pulda_last_error(h) -> str:
     m = lib().pulda_last_error(h)
     return m.decode() if m else ""
@@ -370,6 +379,9 @@ class Sampler:
 
     def stats(self) -> dict:
         return pulda_stats(self.h)
+
+    def z_layout(self) -> dict:
+        return pulda_z_layout(self.h)
 
 
 # ------------------------------------------------------------------ batches

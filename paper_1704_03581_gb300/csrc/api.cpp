@@ -145,50 +145,55 @@ int64_t count_long(const int64_t *off, const std::vector<int32_t> &order) {
 
 // Number of leading documents of a length-ordered schedule that the
 // cooperative z-step takes: at least coop_min_len tokens (0 = automatic:
-// longer than max(256, N / 8000)); none with coop_min_len < 0, the grouped
-// z-step or slices.
+// longer than max(256, N / 8000), or N / 16000 beside the grouped z-step);
+// none with coop_min_len < 0 or slices.
 int64_t count_coop(const pulda_handle *h, const int64_t *off, const std::vector<int32_t> &order, int64_t N) {
-    if (h->opt.coop_min_len < 0 || h->z_groups || h->opt.slice_len > 0) return 0;
-    const int64_t L = h->opt.coop_min_len > 0 ? h->opt.coop_min_len
-                                              : std::max<int64_t>(kCoopAutoMin, N / kCoopAutoDiv + 1);
+    if (h->opt.coop_min_len < 0 || h->opt.slice_len > 0) return 0;
+    const int64_t div = h->z_groups ? kCoopAutoDivGrouped : kCoopAutoDiv;
+    const int64_t L = h->opt.coop_min_len > 0 ? h->opt.coop_min_len : std::max<int64_t>(kCoopAutoMin, N / div + 1);
     int64_t n = 0;
     while (n < static_cast<int64_t>(order.size()) && off[order[n] + 1] - off[order[n]] >= L) ++n;
     return n;
 }
 
-// One z-step over the documents doc_order[0..D): the first n_coop by the
-// cooperative kernel on the handle's stream while the others run one per warp
-// on a second stream (joined back); or, grouped, the documents too long for
-// the grouped kernel (the first n_long) one per warp, the rest four per warp.
+// One z-step over the documents doc_order[0..D) (longest first).  The
+// first n_coop go to the cooperative kernel (a CTA each); with the grouped
+// kernel, the documents after them that are too long for it (up to n_long)
+// then run one per warp on the same stream, while the rest run four per warp
+// (grouped) or one per warp on a second stream, joined back before the next
+// step.
 pulda_status run_z(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, int64_t n_long,
                    int64_t n_coop, const int32_t *w, int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
     CU(h, cudaMemsetAsync(h->work + 1, 0, 3 * sizeof(int), h->stream));
     ZArgs a = z_args(h, doc_off, doc_order, D, w, z, seed, sweep, index_base);
-    if (!h->z_groups && n_coop > 0) {
-        CU(h, cudaEventRecord(h->ev_fork, h->stream));
-        launch_z_step_coop(a, static_cast<int>(n_coop), h->work + 3, h->coop_grid, h->stream);
-        CU(h, cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
-        if (D > n_coop) {
-            ZArgs ar = a;
-            ar.doc_order = doc_order + n_coop;
-            ar.D = D - n_coop;
-            launch_z_step(ar, h->z_warps, h->z_grid, h->stream2);
+    const int64_t n_head = h->z_groups ? std::max(n_coop, n_long) : n_coop;
+    auto launch_rest = [&](cudaStream_t st) {
+        if (D <= n_head) return;
+        ZArgs ar = a;
+        ar.doc_order = doc_order + n_head;
+        ar.D = D - n_head;
+        if (h->z_groups) {
+            ar.work = h->work + 2;
+            launch_z_step_groups(ar, h->zg_grid, st);
+        } else {
+            launch_z_step(ar, h->z_warps, h->z_grid, st);
         }
-        CU(h, cudaEventRecord(h->ev_join, h->stream2));
-        CU(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-    } else if (!h->z_groups) {
-        launch_z_step(a, h->z_warps, h->z_grid, h->stream);
-    } else {
-        if (n_long > 0) {
+    };
+    if (n_head > 0) {
+        CU(h, cudaEventRecord(h->ev_fork, h->stream));
+        if (n_coop > 0) launch_z_step_coop(a, static_cast<int>(n_coop), h->work + 3, h->coop_grid, h->stream);
+        if (n_head > n_coop) {
             ZArgs al = a;
-            al.D = n_long;
+            al.doc_order = doc_order + n_coop;
+            al.D = n_head - n_coop;
             launch_z_step(al, h->z_warps, h->z_grid, h->stream);
         }
-        ZArgs ag = a;
-        ag.doc_order = doc_order + n_long;
-        ag.D = D - n_long;
-        ag.work = h->work + 2;
-        launch_z_step_groups(ag, h->zg_grid, h->stream);
+        CU(h, cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
+        launch_rest(h->stream2);
+        CU(h, cudaEventRecord(h->ev_join, h->stream2));
+        CU(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    } else {
+        launch_rest(h->stream);
     }
     CU(h, cudaGetLastError());
     return PULDA_OK;
@@ -206,7 +211,7 @@ PhiArgs phi_args(pulda_handle *h) {
     a.cst_k = h->cst_k; a.cst_c = h->cst_c; a.nnz_c = h->nnz_c;
     a.S = h->S; a.rowbuf = h->rowbuf; a.col_ptr = h->col_ptr;
     a.topic = h->topic; a.c = h->c; a.q = h->q; a.athr = h->athr; a.atopic = h->atopic;
-    a.A = h->A; a.vose_p = h->vose_p; a.vose_stack = h->vose_stack; a.bitmap = h->bitmap; a.KW = h->KW;
+    a.A = h->A; a.vose_p = h->vose_p; a.vose_stack = h->vose_stack; a.bits = h->bits; a.KW = h->KW; a.KWp = h->KWp;
     a.qdense = h->qdense; a.dense_slot = h->dense_slot;
     a.alpha = h->alpha; a.work = h->work; a.stats = h->stats;
     a.heavy_row = h->heavy_row; a.heavy_hist = h->heavy_hist; a.n_heavy = h->n_heavy;
@@ -219,7 +224,7 @@ ZArgs z_args(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, 
     ZArgs a{};
     a.doc_off = doc_off; a.doc_order = doc_order; a.D = D; a.w = w; a.z = z;
     a.col_ptr = h->col_ptr; a.topic = h->topic; a.q = h->q; a.A = h->A; a.athr = h->athr; a.atopic = h->atopic;
-    a.bitmap = h->bitmap; a.K = h->K; a.KW = h->KW; a.seed = seed; a.sweep = sweep; a.index_base = index_base;
+    a.bits = h->bits; a.K = h->K; a.KW = h->KW; a.KWp = h->KWp; a.seed = seed; a.sweep = sweep; a.index_base = index_base;
     a.qdense = h->qdense; a.dense_slot = h->dense_slot;
     a.path = h->opt.zstep_path; a.work = h->work + 1; a.stats = h->stats;
     return a;
@@ -295,6 +300,7 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     h->N = N; h->D = D; h->K = K; h->V = V; h->seed = seed; h->beta = beta;
     for (int k = 0; k < K; ++k) h->alpha_sum += static_cast<double>(alpha[k]);
     h->KW = (K + 31) / 32;
+    h->KWp = bitmap_row_words(K);
     h->cap = static_cast<int64_t>(K) * V;
     cudaGetDevice(&h->device);
     if (h->opt.stream) {
@@ -319,7 +325,7 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     ALLOC(h->S, K); ALLOC(h->rowbuf, V); ALLOC(h->col_ptr, V + 1);
     ALLOC(h->topic, h->cap); ALLOC(h->c, h->cap); ALLOC(h->q, h->cap); ALLOC(h->athr, h->cap); ALLOC(h->atopic, h->cap);
     ALLOC(h->A, V); ALLOC(h->vose_p, h->cap); ALLOC(h->vose_stack, h->cap);
-    if (K <= kMaxKBitmap) ALLOC(h->bitmap, static_cast<size_t>(V) * h->KW);
+    if (K <= kMaxKBitmap) ALLOC(h->bits, static_cast<size_t>(V) * h->KWp);
     if (h->opt.phi_mode == 1) {
         ALLOC(h->gam, h->cap); ALLOC(h->Sd, K); ALLOC(h->invS, K); ALLOC(h->invSf, K);
         ALLOC(h->dpart, dir_part_count(V, K));
@@ -390,8 +396,8 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
         const int64_t cap = std::min<int64_t>(V, kDenseBytes / (static_cast<int64_t>(sizeof(uint32_t)) * K));
         std::vector<int32_t> slot(V, -1);
         int32_t n = 0;
-        for (int32_t v : word_order) {
-            if (n >= cap || woff[v + 1] - woff[v] < kDenseMinTokens) break;
+        for (int32_t v : word_order) {   // every word, most frequent first, while the budget lasts
+            if (n >= cap) break;
             slot[v] = n++;
         }
         if (n > 0) {
@@ -439,10 +445,16 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     h->z_warps = wpb;
     h->z_grid = sms * z_step_blocks_per_sm(K, wpb);
     CUI(cudaGetLastError());
-    // Measured on the large workload (sweeps 31-50, |J| ~ 130 per token) one
-    // document per warp is 2x faster: the grouped kernel's lanes each carry 4x
-    // longer chains of dependent loads.  It is kept for small intersections.
-    h->z_groups = h->opt.docs_per_warp == 4;
+    // Four documents per warp share each token's fixed work (record, count
+    // updates, scan, draw) over four tokens, but each lane then walks four
+    // times the topics, so a token's intersection costs more and a document's
+    // tokens advance about 3x slower.  Measured (sweep ms, 100,000 documents of
+    // the large corpus): K = 100 15.5 vs 17.4 one per warp, K = 300 19.3 vs
+    // 16.1, K = 1000 26.0 vs 15.4.  So auto takes four per warp only while one
+    // bitmap word per lane covers K (K <= 256).  Needs every word's dense q
+    // row; not with slices or the column-only path.
+    const bool groups_ok = K <= kMaxKBitmap && h->n_dense == V && h->opt.slice_len == 0 && h->opt.zstep_path != 1;
+    h->z_groups = groups_ok && (h->opt.docs_per_warp == 4 || (h->opt.docs_per_warp == 0 && h->KWp == 8));
     h->n_long = count_long(doc_offsets, dord);
     h->n_coop = count_coop(h, doc_offsets, dord, N);
     h->coop_grid = sms * z_coop_blocks_per_sm(K);
@@ -709,6 +721,17 @@ pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids, const int64_t
     cudaFreeAsync(dw, st); cudaFreeAsync(doff, st); cudaFreeAsync(dord, st); cudaFreeAsync(dz, st);
     CU(h, cudaGetLastError());
     return pulda_sync(h);
+}
+
+pulda_status pulda_z_layout(pulda_handle *h, int32_t *docs_per_warp, int64_t *coop_docs, int64_t *one_warp_docs) {
+    if (!h) return PULDA_ERR_INVALID;
+    if (docs_per_warp) *docs_per_warp = h->z_groups ? 4 : 1;
+    if (coop_docs) *coop_docs = h->n_coop;
+    if (one_warp_docs) {
+        const int64_t head = h->z_groups ? std::max(h->n_coop, h->n_long) : h->n_coop;
+        *one_warp_docs = h->z_groups ? head - h->n_coop : h->D - h->n_coop;
+    }
+    return PULDA_OK;
 }
 
 pulda_status pulda_stats(pulda_handle *h, pulda_sweep_stats *out) {

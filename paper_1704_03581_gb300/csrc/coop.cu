@@ -59,7 +59,7 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
     uint4 *rec = reinterpret_cast<uint4 *>(sm + z_m_words(K));
     uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);
     CoopXch &x = *reinterpret_cast<CoopXch *>(drow_of + 32);
-    const bool use_bm = a.bitmap != nullptr && a.path != 1;
+    const bool use_bm = a.bits != nullptr && a.path != 1;
     int R = 1;
     while (32 * a.KW > R * kCoopSlots) R <<= 1;
     const bool own = use_bm && tid < 32 * a.KW / R;      // this slot owns topics on the document side
@@ -88,7 +88,7 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
     int kd = 0;
 #pragma unroll
     for (int j = 0; j < kCoopWarps; ++j) kd += x.kdp[j];
-    const uint32_t *bits = reinterpret_cast<const uint32_t *>(a.bitmap);
+    const uint32_t *bits = a.bits;
     const uint32_t sweep_end = r.sweep + static_cast<uint32_t>(r.max_pass_end);
     bool first = true;
     while (r.budget > 0 && r.sweep != sweep_end) {
@@ -99,7 +99,7 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
         __syncthreads();
         if (!x.go) break;     // the same value in every thread: read before any thread can write it again
         first = false;
-        uint32_t bm_next = own ? bits[2 * (static_cast<int64_t>(rec[1].z) * a.KW + wi)] & mask : 0u;
+        uint32_t bm_next = own ? bits[static_cast<int64_t>(rec[1].z) * a.KWp + wi] & mask : 0u;
         for (int tt = 0; tt < cnt; ++tt) {
             const uint4 t0 = rec[2 * tt], t1 = rec[2 * tt + 1];
             const int kold = static_cast<int>(t1.w >> 16);
@@ -109,7 +109,7 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
             const u64 U = (static_cast<u64>(t1.x) << 32) | t1.y;
             const int ka = static_cast<int>(t0.y >> 16);
             const uint32_t bm = bm_next;
-            if (own && tt + 1 < cnt) bm_next = bits[2 * (static_cast<int64_t>(rec[2 * tt + 3].z) * a.KW + wi)] & mask;
+            if (own && tt + 1 < cnt) bm_next = bits[static_cast<int64_t>(rec[2 * tt + 3].z) * a.KWp + wi] & mask;
             // m^{-i}: the old topic's count less one, applied as each count is read
             const uint32_t mko = m[mi(kold)];
             const int kdi = kd - (mko == 1u ? 1 : 0);

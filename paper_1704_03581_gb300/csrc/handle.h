@@ -16,7 +16,7 @@ struct pulda_handle {
     pulda_options opt{};
     int device = 0;
     int64_t N = 0, D = 0;
-    int K = 0, V = 0, KW = 0;
+    int K = 0, V = 0, KW = 0, KWp = 0;
     uint64_t seed = 0;
     int64_t sweep = 0;
     bool have_phi = false;
@@ -53,7 +53,7 @@ struct pulda_handle {
     // Dirichlet Phi (Algorithm 1), allocated in that mode only
     float *gam = nullptr, *invSf = nullptr; double *Sd = nullptr, *invS = nullptr, *dpart = nullptr;
     uint16_t *topic = nullptr; uint32_t *c = nullptr, *q = nullptr, *athr = nullptr; uint16_t *atopic = nullptr;
-    unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint2 *bitmap = nullptr;
+    unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint32_t *bits = nullptr;
     int *work = nullptr;
     unsigned long long *stats = nullptr;
     int64_t cap = 0;   // capacity of the per-word tables: K * V entries

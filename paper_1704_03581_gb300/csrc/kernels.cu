@@ -440,14 +440,15 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
     const int n = a.nnz_c[v];
     const int64_t src = static_cast<int64_t>(v) * a.K;
     const int64_t out = a.col_ptr[v];
-    if (a.bitmap) {
-        uint2 *bm = a.bitmap + static_cast<int64_t>(v) * a.KW;
-        for (int wi = lane; wi < a.KW; wi += 32) {
+    if (a.bits) {
+        // a row of KWp words (KW rounded up; the words past KW stay zero)
+        uint32_t *bm = a.bits + static_cast<int64_t>(v) * a.KWp;
+        for (int wi = lane; wi < a.KWp; wi += 32) {
             int lo = 0, hi = n;                       // first entry with topic >= 32 wi
             while (lo < hi) { const int mid = (lo + hi) >> 1; if (a.cst_k[src + mid] < 32 * wi) lo = mid + 1; else hi = mid; }
             uint32_t bits = 0;
             for (int j = lo; j < n && (a.cst_k[src + j] >> 5) == wi; ++j) bits |= 1u << (a.cst_k[src + j] & 31);
-            bm[wi] = make_uint2(bits, static_cast<uint32_t>(lo));
+            bm[wi] = bits;
         }
     }
     // a word with a dense q row: zero it (the column's entries are written below)
@@ -603,7 +604,7 @@ constexpr int kGather = PULDA_ZGATHER;
 __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, const uint32_t *m0 = nullptr) {
     const int lane = threadIdx.x & 31;
     const int K = a.K;
-    const bool use_bm = a.bitmap != nullptr && a.path != 1;
+    const bool use_bm = a.bits != nullptr && a.path != 1;
     if (r.len == 0 || r.budget <= 0) return;
     if (m0) {
         for (int k = lane; k < K; k += 32) m[mi(k)] = m0[k];
@@ -659,10 +660,10 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
         uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);   // q row offset of the token's word, or ~0
         if (valid) znew = stage_token(a, rs, i, rec + 2 * lane, drow_of + lane);
         __syncwarp();
-        // the bits half of the word's bitmap entries (32 topics per lane)
-        const uint32_t *bits = reinterpret_cast<const uint32_t *>(a.bitmap);
+        // the word's bitmap row (32 topics per lane)
+        const uint32_t *bits = a.bits;
         uint32_t bm_next = 0u;
-        if (use_bm && lane < a.KW) bm_next = bits[2 * (static_cast<int64_t>(rec[1].z) * a.KW + lane)];
+        if (use_bm && lane < a.KW) bm_next = bits[static_cast<int64_t>(rec[1].z) * a.KWp + lane];
         // this block's counters, in 32 bits (at most 32 tokens of K <= 16384),
         // added to the warp's 64-bit counters once per block
         // (c_min: sum of min(K_d, K_v), the same in every lane; c_cnt: tokens
@@ -680,7 +681,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             const int ka = static_cast<int>(t0.y >> 16);
             const uint32_t bm = bm_next;
             if (use_bm && tt + 1 < cnt && lane < a.KW)   // the next token's bitmap word, fetched while this one is drawn
-                bm_next = bits[2 * (static_cast<int64_t>(rec[2 * tt + 3].z) * a.KW + lane)];
+                bm_next = bits[static_cast<int64_t>(rec[2 * tt + 3].z) * a.KWp + lane];
             // remove token i: m^{-i}
             const uint32_t old = m[mi(kold)];
             __syncwarp();
@@ -901,304 +902,6 @@ __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_m
     }
 }
 
-// ============================================================== z-step, grouped
-// Eight lanes per document, four documents per warp.  The per-token work of
-// the warp-per-document kernel is dominated by what every token costs
-// regardless of its intersection (broadcasts, m updates, the draw, the scan);
-// here four documents share each of those instructions.  Documents are taken
-// four at a time in length order, so the four run for about as many tokens.
-// Requires K <= 1024 (each lane owns 4 consecutive 32-topic bitmap words)
-// and documents of at most 65,535 tokens (m is held as uint16); the
-// warp-per-document kernel covers everything else.
-constexpr int kGroup = 8;                  // lanes per document
-constexpr int kGroups = 32 / kGroup;       // documents per warp
-constexpr int kWordsPerLane = 4;           // 32-topic words owned by a lane (K <= 1024)
-
-#ifndef PULDA_ZG_MINBLOCKS
-#define PULDA_ZG_MINBLOCKS 3
-#endif
-
-__device__ __forceinline__ uint32_t sel4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, int w) {
-    return w == 0 ? a0 : w == 1 ? a1 : w == 2 ? a2 : a3;
-}
-
-__device__ __forceinline__ u64 group_incl_scan64(u64 v, int gl) {
-#pragma unroll
-    for (int o = 1; o < kGroup; o <<= 1) {
-        const u64 y = __shfl_up_sync(0xFFFFFFFFu, v, o, kGroup);
-        if (gl >= o) v += y;
-    }
-    return v;
-}
-
-__global__ void __launch_bounds__(256, PULDA_ZG_MINBLOCKS) k_z_step_groups(ZArgs a) {
-    extern __shared__ uint32_t zg_sm[];
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int g = lane / kGroup;               // document slot in the warp
-    const int gl = lane % kGroup;              // lane within the document's group
-    const int K = a.K, KW = a.KW;
-    const int Kp = (K + 1) & ~1;               // uint16 counts, padded to whole 32-bit words
-    uint16_t *m = reinterpret_cast<uint16_t *>(zg_sm) + static_cast<size_t>(warp * kGroups + g) * Kp;
-    uint32_t *m32 = reinterpret_cast<uint32_t *>(m);
-    const bool use_bm = a.bitmap != nullptr && a.path != 1;
-    const int w0 = gl * kWordsPerLane;         // first bitmap word of this lane
-    u64 st_tok = 0, st_ab = 0, st_min = 0, st_zero = 0, st_int = 0, st_doc = 0;
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.work, 1);
-        item = __shfl_sync(0xFFFFFFFFu, item, 0);
-        if (static_cast<int64_t>(item) * kGroups >= a.D) break;
-        const int64_t di = static_cast<int64_t>(item) * kGroups + g;
-        const bool has = di < a.D;
-        const int d = has ? a.doc_order[di] : 0;
-        const int64_t s = has ? a.doc_off[d] : 0;
-        const int len = has ? static_cast<int>(a.doc_off[d + 1] - s) : 0;
-        // m_d from the document's current topics
-        for (int k = gl; k < Kp / 2; k += kGroup) m32[k] = 0u;
-        __syncwarp();
-        for (int t = gl; t < len; t += kGroup) {
-            const int k = guard_index(a.z[s + t], K, a.stats);
-            atomicAdd(&m32[k >> 1], 1u << ((k & 1) * 16));
-        }
-        __syncwarp();
-        // nonzero-topic bits of the four words this lane owns, and K_d
-        uint32_t mb0 = 0, mb1 = 0, mb2 = 0, mb3 = 0;
-        if (use_bm) {
-#pragma unroll
-            for (int w = 0; w < kWordsPerLane; ++w) {
-                uint32_t bits = 0;
-                const int base = (w0 + w) * 32;
-                if (w0 + w < KW)
-                    for (int b = 0; b < 32 && base + b < K; ++b) bits |= (m[base + b] != 0 ? 1u : 0u) << b;
-                if (w == 0) mb0 = bits; else if (w == 1) mb1 = bits; else if (w == 2) mb2 = bits; else mb3 = bits;
-            }
-        }
-        int kd = 0;
-        {
-            int cnt = 0;
-            if (use_bm) cnt = __popc(mb0) + __popc(mb1) + __popc(mb2) + __popc(mb3);
-            else for (int k = gl; k < K; k += kGroup) cnt += m[k] != 0;
-#pragma unroll
-            for (int o = 1; o < kGroup; o <<= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-            kd = cnt;
-        }
-        const int maxlen = __reduce_max_sync(0xFFFFFFFFu, len);
-        for (int t0 = 0; t0 < maxlen; t0 += kGroup) {
-            // per-token data of the group's next 8 tokens, one token per lane
-            const int tl = t0 + gl;
-            const bool valid = tl < len;
-            int wv = 0, zo = 0, nw = 0, ta = 0;
-            int64_t cb = 0;
-            u64 Av = 0;
-            U4 x{0, 0, 0, 0};
-            if (valid) {
-                const int64_t i = s + tl;
-                wv = a.w[i];
-                zo = guard_index(a.z[i], K, a.stats);
-                const uint64_t t = static_cast<uint64_t>(a.index_base + i);
-                x = draw(a.seed, static_cast<uint32_t>(t), static_cast<uint32_t>(t >> 32), a.sweep, TAG_Z, 0);
-                cb = a.col_ptr[wv];
-                nw = static_cast<int>(a.col_ptr[wv + 1] - cb);
-                Av = a.A[wv];
-                if (nw > 0) {
-                    const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
-                    ta = x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl];
-                }
-            }
-            int znew = zo;
-            // bitmap words of the first token, then one token ahead
-            uint2 n0 = make_uint2(0u, 0u), n1 = n0, n2 = n0, n3 = n0;
-            {
-                const int vf = __shfl_sync(0xFFFFFFFFu, wv, g * kGroup);
-                if (use_bm && t0 < len) {
-                    const uint2 *bp = a.bitmap + static_cast<int64_t>(vf) * KW + w0;
-                    if (w0 + 0 < KW) n0 = bp[0];
-                    if (w0 + 1 < KW) n1 = bp[1];
-                    if (w0 + 2 < KW) n2 = bp[2];
-                    if (w0 + 3 < KW) n3 = bp[3];
-                }
-            }
-            for (int tt = 0; tt < kGroup; ++tt) {
-                const int src = g * kGroup + tt;
-                const bool act = t0 + tt < len;               // uniform within the group
-                const int v = __shfl_sync(0xFFFFFFFFu, wv, src);
-                const int kold = __shfl_sync(0xFFFFFFFFu, zo, src);
-                const int64_t col = __shfl_sync(0xFFFFFFFFu, cb, src);
-                const int n_w = __shfl_sync(0xFFFFFFFFu, nw, src);
-                const u64 At = __shfl_sync(0xFFFFFFFFu, Av, src);
-                const u64 U = (static_cast<u64>(__shfl_sync(0xFFFFFFFFu, x.x, src)) << 32) |
-                              __shfl_sync(0xFFFFFFFFu, x.y, src);
-                const int ka = __shfl_sync(0xFFFFFFFFu, ta, src);
-                const int vn = __shfl_sync(0xFFFFFFFFu, wv, g * kGroup + ((tt + 1) & (kGroup - 1)));
-                const uint2 c0 = n0, c1 = n1, c2 = n2, c3 = n3;
-                if (use_bm && tt + 1 < kGroup && t0 + tt + 1 < len) {
-                    const uint2 *bp = a.bitmap + static_cast<int64_t>(vn) * KW + w0;
-                    if (w0 + 0 < KW) n0 = bp[0];
-                    if (w0 + 1 < KW) n1 = bp[1];
-                    if (w0 + 2 < KW) n2 = bp[2];
-                    if (w0 + 3 < KW) n3 = bp[3];
-                }
-                // remove token i: m^{-i}
-                uint32_t old = 0;
-                if (act) old = m[kold];
-                __syncwarp();
-                if (act) {
-                    if (gl == 0) m[kold] = static_cast<uint16_t>(old - 1);
-                    if (old == 1) {
-                        --kd;
-                        if (use_bm) {
-                            const int wi = (kold >> 5) - w0;
-                            const uint32_t clr = ~(1u << (kold & 31));
-                            if (wi == 0) mb0 &= clr; else if (wi == 1) mb1 &= clr;
-                            else if (wi == 2) mb2 &= clr; else if (wi == 3) mb3 &= clr;
-                        }
-                    }
-                    if (gl == 0) st_min += static_cast<u64>(kd < n_w ? kd : n_w);
-                    if (gl == 0 && kd < n_w) ++st_doc;
-                }
-                __syncwarp();
-                const bool docside = act && use_bm && (a.path == 2 || kd < n_w);
-                // partial sums of q m, per owned word (docside) or per column segment
-                u64 s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-                const int seg = (n_w + kGroup - 1) / kGroup;
-                const int j0 = seg * gl, j1 = min(j0 + seg, n_w);
-                if (docside) {
-#pragma unroll
-                    for (int w = 0; w < kWordsPerLane; ++w) {
-                        const uint2 cw = w == 0 ? c0 : w == 1 ? c1 : w == 2 ? c2 : c3;
-                        uint32_t rem = cw.x & sel4(mb0, mb1, mb2, mb3, w);
-                        const int64_t rb0 = col + cw.y;
-                        const int kbase = (w0 + w) * 32;
-                        u64 sw = 0;
-                        // up to four independent loads, then the rest one by one
-                        uint32_t qv[4];
-                        int bp[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            bp[u] = -1;
-                            qv[u] = 0;
-                            if (rem) {
-                                const int b = __ffs(rem) - 1;
-                                rem &= rem - 1;
-                                bp[u] = b;
-                                qv[u] = a.q[rb0 + __popc(cw.x & ((1u << b) - 1u))];
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (bp[u] >= 0) sw += static_cast<u64>(qv[u]) * m[kbase + bp[u]];
-                        for (; rem; rem &= rem - 1) {
-                            const int b = __ffs(rem) - 1;
-                            sw += static_cast<u64>(a.q[rb0 + __popc(cw.x & ((1u << b) - 1u))]) * m[kbase + b];
-                        }
-                        if (w == 0) s0 = sw; else if (w == 1) s1 = sw; else if (w == 2) s2 = sw; else s3 = sw;
-                    }
-                } else if (act) {
-#pragma unroll 4
-                    for (int j = j0; j < j1; ++j)
-                        s0 += static_cast<u64>(a.q[col + j]) * m[guard_index(a.topic[col + j], K, a.stats)];
-                }
-                {
-                    // |J| of this token: the group's count of intersection entries
-                    int nj = 0;
-                    if (docside) {
-                        nj = __popc(c0.x & mb0) + __popc(c1.x & mb1) + __popc(c2.x & mb2) + __popc(c3.x & mb3);
-                    } else if (act) {
-                        for (int j = j0; j < j1; ++j) nj += m[guard_index(a.topic[col + j], K, a.stats)] != 0;
-                    }
-#pragma unroll
-                    for (int o = 1; o < kGroup; o <<= 1) nj += __shfl_xor_sync(0xFFFFFFFFu, nj, o);
-                    if (gl == 0 && act) st_int += static_cast<u64>(nj);
-                }
-                const u64 acc = s0 + s1 + s2 + s3;
-                const u64 incl = group_incl_scan64(acc, gl);
-                const u64 B = __shfl_sync(0xFFFFFFFFu, incl, g * kGroup + kGroup - 1);
-                const u64 T = At + (B << kFracBits);
-                int knew = kold;
-                bool need = false;
-                u64 rb = 0;
-                if (act) {
-                    if (T == 0) {
-                        if (gl == 0) ++st_zero;
-                    } else {
-                        const u64 r = __umul64hi(U, T);
-                        if (r < At) {
-                            knew = ka;
-                            if (gl == 0) ++st_ab;
-                        } else {
-                            need = true;
-                            rb = (r - At) >> kFracBits;
-                        }
-                    }
-                }
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, need && rb < incl);
-                const uint32_t gbal = (bal >> (g * kGroup)) & ((1u << kGroup) - 1u);
-                int f = -1;
-                if (need && gbal && gl == __ffs(gbal) - 1) {
-                    u64 run = incl - acc;
-                    if (docside) {
-                        // the word whose partial sum crosses rb, then its bits
-                        int w = 3;
-                        if (rb < run + s0) w = 0;
-                        else if (rb < run + s0 + s1) { w = 1; run += s0; }
-                        else if (rb < run + s0 + s1 + s2) { w = 2; run += s0 + s1; }
-                        else run += s0 + s1 + s2;
-                        const uint2 cw = w == 0 ? c0 : w == 1 ? c1 : w == 2 ? c2 : c3;
-                        const int kbase = (w0 + w) * 32;
-                        const int64_t rb0 = col + cw.y;
-                        for (uint32_t rem = cw.x & sel4(mb0, mb1, mb2, mb3, w); rem; rem &= rem - 1) {
-                            const int b = __ffs(rem) - 1;
-                            run += static_cast<u64>(a.q[rb0 + __popc(cw.x & ((1u << b) - 1u))]) * m[kbase + b];
-                            if (rb < run) { f = kbase + b; break; }
-                        }
-                    } else {
-                        for (int j = j0; j < j1; ++j) {
-                            const int k = guard_index(a.topic[col + j], K, a.stats);
-                            run += static_cast<u64>(a.q[col + j]) * m[k];
-                            if (rb < run) { f = k; break; }
-                        }
-                    }
-                }
-                const int fsrc = gbal ? g * kGroup + __ffs(gbal) - 1 : lane;
-                const int found = __shfl_sync(0xFFFFFFFFu, f, fsrc);
-                if (need) {
-                    if (found < 0) {
-                        if (gl == 0) atomicOr(&a.stats[ST_ERROR], ERR_INTERNAL);
-                    } else {
-                        knew = found;
-                    }
-                }
-                // add token i back with its new topic
-                uint32_t old2 = 0;
-                knew = guard_index(knew, K, a.stats);
-                if (act) old2 = m[knew];
-                __syncwarp();
-                if (act) {
-                    if (gl == 0) m[knew] = static_cast<uint16_t>(old2 + 1);
-                    if (old2 == 0) {
-                        ++kd;
-                        if (use_bm) {
-                            const int wi = (knew >> 5) - w0;
-                            const uint32_t setb = 1u << (knew & 31);
-                            if (wi == 0) mb0 |= setb; else if (wi == 1) mb1 |= setb;
-                            else if (wi == 2) mb2 |= setb; else if (wi == 3) mb3 |= setb;
-                        }
-                    }
-                }
-                __syncwarp();
-                if (gl == tt) znew = knew;
-            }
-            if (valid) a.z[s + tl] = static_cast<int16_t>(znew);
-            if (gl == 0) st_tok += static_cast<u64>(max(0, min(kGroup, len - t0)));
-        }
-    }
-    // one set of atomics per warp
-    const u64 c[6] = {warp_sum64(st_tok), warp_sum64(st_ab), warp_sum64(st_min), warp_sum64(st_zero),
-                      warp_sum64(st_int), warp_sum64(st_doc)};
-    if (lane == 0) flush_z_stats(a.stats, c);
-}
-
 // ============================================================ batches
 // Start of a sweep of many chains (one CTA): advance the shared sweep counter
 // and clear every chain's row sums, per-sweep counters and the work queues.
@@ -1388,22 +1091,6 @@ int z_step_blocks_per_sm(int K, int warps_per_block) {
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_z_step, 32 * warps_per_block, smem);
     return b > 0 ? b : 1;
-}
-
-size_t z_groups_smem(int K) {
-    return sizeof(uint16_t) * static_cast<size_t>((K + 1) & ~1) * kGroups * 8;   // 8 warps per CTA
-}
-
-int z_groups_blocks_per_sm(int K) {
-    allow_dynamic_smem(k_z_step_groups);
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_z_step_groups, 256, z_groups_smem(K));
-    return b > 0 ? b : 1;
-}
-
-void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st) {
-    if (a.D <= 0) return;
-    k_z_step_groups<<<grid, 256, z_groups_smem(a.K), st>>>(a);
 }
 
 void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int n, const int16_t *z, int K,

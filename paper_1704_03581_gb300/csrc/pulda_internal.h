@@ -23,6 +23,14 @@ constexpr uint32_t kMaxRedraw = 1u << 20;
 constexpr int kMaxK = 16384;
 // The bitmap intersection path of the z-step holds one 32-topic word per lane.
 constexpr int kMaxKBitmap = 1024;
+// Words of a word's bitmap row: ceil(K / 32) rounded up to 8 times a power
+// of two, so each of the grouped z-step's 8 lanes per document reads 1, 2 or
+// 4 consecutive words with one aligned load (the words past ceil(K / 32) are
+// zero).
+__host__ __device__ inline int bitmap_row_words(int K) {
+    const int per_lane = (((K + 31) / 32) + 7) / 8;
+    return 8 * (per_lane <= 1 ? 1 : per_lane <= 2 ? 2 : 4);
+}
 // Warps per CTA of the warp-per-document z-step: the default and the largest
 // accepted (the kernel's launch bounds are sized for it).
 #ifndef PULDA_ZWARPS
@@ -44,10 +52,9 @@ constexpr int kMultiWarps = PULDA_MULTI_WARPS;
 // the z-step's document side reads q at topic k there.  A word without a row
 // is always iterated on its column side (the same sums).
 #ifndef PULDA_DENSE_BYTES
-#define PULDA_DENSE_BYTES (256ll << 20)
+#define PULDA_DENSE_BYTES (2048ll << 20)
 #endif
 constexpr long long kDenseBytes = PULDA_DENSE_BYTES;
-constexpr int64_t kDenseMinTokens = 1;
 
 // Philox stream tags (counter word 3 = tag << 28 | aux).
 enum : uint32_t { TAG_INIT = 1, TAG_POIS = 2, TAG_BETA = 3, TAG_REDRAW_POIS = 4, TAG_REDRAW_BETA = 5, TAG_Z = 6,
@@ -111,8 +118,8 @@ struct PhiArgs {
     unsigned long long *A;      // [V]
     unsigned long long *vose_p; // [cap] scratch
     uint16_t *vose_stack;       // [cap] scratch
-    uint2 *bitmap;              // [V * KW] {nonzero-topic bits, entries before this word} or null
-    int KW;
+    uint32_t *bits;             // [V * KWp] nonzero-topic bits of each word's column, or null
+    int KW, KWp;
     uint32_t *qdense;           // [n_dense * K] q by topic (0 off the column) or null
     const int32_t *dense_slot;  // [V] row of the word in qdense, or -1
     const float *alpha;         // [K]
@@ -155,7 +162,7 @@ struct ZArgs {
     const unsigned long long *A;
     const uint32_t *athr;
     const uint16_t *atopic;
-    const uint2 *bitmap;        // null when K > kMaxKBitmap
+    const uint32_t *bits;       // [V * KWp] nonzero-topic bits of each word's column; null when K > kMaxKBitmap
     const uint32_t *qdense;     // dense q rows of the most frequent words, or null
     const int32_t *dense_slot;  // [V] row in qdense or -1
     // stale-count slices of long documents (k_z_step only): {row in m0, the
@@ -163,7 +170,7 @@ struct ZArgs {
     const int4 *slices;
     int n_slices;
     const uint32_t *m0;         // [rows * K] pass-start counts of the sliced documents
-    int K, KW;
+    int K, KW, KWp;
     uint64_t seed;
     uint32_t sweep;
     const uint32_t *sweep_ptr;  // if set, the sweep counter is read here (graph replay)
@@ -192,6 +199,12 @@ int z_coop_blocks_per_sm(int K);
 // outlast the pass.
 constexpr int64_t kCoopAutoDiv = 8000;
 constexpr int64_t kCoopAutoMin = 256;
+// The same beside the grouped z-step, whose pass is faster and whose
+// documents each advance more slowly (four share a warp's issue slots).
+#ifndef PULDA_COOP_DIV_GROUPED
+#define PULDA_COOP_DIV_GROUPED 16000
+#endif
+constexpr int64_t kCoopAutoDivGrouped = PULDA_COOP_DIV_GROUPED;
 // Pass-start topic counts of the documents that the z-step takes in slices.
 void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int n, const int16_t *z, int K,
                          uint32_t *m0, cudaStream_t st);
@@ -201,11 +214,11 @@ void launch_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K
 void launch_n_dense(const PhiArgs &a, int32_t *n_kv, cudaStream_t st);
 void launch_phi_values(const PhiArgs &a, float *phi, cudaStream_t st);
 int z_step_blocks_per_sm(int K, int warps_per_block);
-// Grouped z-step: 4 documents per warp, K <= kMaxKBitmap, documents of at
-// most kMaxGroupDocLen tokens; 8 warps per CTA.
+// Grouped z-step (zgroup.cu): 4 documents per warp, 8 lanes each, K <=
+// kMaxKBitmap, documents of at most kMaxGroupDocLen tokens, every word with a
+// dense q row; the warps of a CTA are z_groups_warps().
 constexpr int kMaxGroupDocLen = 65535;
 void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st);
-size_t z_groups_smem(int K);
 int z_groups_blocks_per_sm(int K);
 int phi_counts_blocks_per_sm(int K);
 

@@ -149,13 +149,15 @@ __device__ __forceinline__ void zero_warp_counters(unsigned long long *cnt) {
 
 __device__ inline void flush_warp_counters(unsigned long long *stats, unsigned long long *cnt) {
     const int lane = threadIdx.x & 31;
-    const int slot[6] = {ST_TOKENS, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_SUMINT, ST_DOCSIDE};
+    // lane j's counter goes to slot {tokens, a-branch, sum min, zero mass, sum |J|, doc side}[j]
+    const int slot = lane == 0 ? ST_TOKENS : lane == 1 ? ST_ABRANCH : lane == 2 ? ST_SUMMIN
+                   : lane == 3 ? ST_ZEROMASS : lane == 4 ? ST_SUMINT : ST_DOCSIDE;
     __syncwarp();
     if (lane < 6) {
         const unsigned long long v = cnt[lane];
         if (v) {
-            atomicAdd(&stats[slot[lane]], v);
-            atomicAdd(&stats[ST_COUNT + slot[lane]], v);
+            atomicAdd(&stats[slot], v);
+            atomicAdd(&stats[ST_COUNT + slot], v);
         }
         cnt[lane] = 0;
     }

@@ -61,12 +61,16 @@ def test_launch_count_and_profile_record_follow_the_source(tmp_path, monkeypatch
     assert bench.kernels_per_sweep(np.zeros(10, np.int32), 0) == 5
     assert bench.kernels_per_sweep(np.zeros(1 << 18, np.int32), 0) == 6
     assert bench.kernels_per_sweep(np.arange(10, dtype=np.int32), 1) == 8
-    # the cooperative z-step beside the one-warp kernel once a document reaches the threshold
-    off = np.array([0, 300, 310], np.int64)
-    assert bench.kernels_per_sweep(np.zeros(310, np.int32), 0, off) == 6
-    assert bench.kernels_per_sweep(np.zeros(310, np.int32), 0, off, coop_min_len=-1) == 5
-    assert bench.kernels_per_sweep(np.zeros(310, np.int32), 0, off, coop_min_len=400) == 5
-    assert bench.kernels_per_sweep(np.zeros(310, np.int32), 0, off, slice_len=100) == 6
+    # the z-step as the handle laid it out: the cooperative kernel beside the main one when
+    # some document is on CTAs; beside four per warp, the one-warp kernel for over-long documents
+    w = np.zeros(310, np.int32)
+    one = {"docs_per_warp": 1, "coop_docs": 0, "one_warp_docs": 2}
+    assert bench.kernels_per_sweep(w, 0, one) == 5
+    assert bench.kernels_per_sweep(w, 0, dict(one, coop_docs=1)) == 6
+    four = {"docs_per_warp": 4, "coop_docs": 0, "one_warp_docs": 0}
+    assert bench.kernels_per_sweep(w, 0, four) == 5
+    assert bench.kernels_per_sweep(w, 0, dict(four, coop_docs=2, one_warp_docs=1)) == 7
+    assert bench.kernels_per_sweep(w, 0, one, slice_docs=1) == 6
     rec = bench.recorded_profile()
     if rec:
         assert rec["source_sha"] == bench.kernel_source_hash()

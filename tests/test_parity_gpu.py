@@ -211,3 +211,20 @@ def test_large_corpus_sampled_parity():
     zo = O.infer(tab, w_new, off_new, 2, 13)
     assert not first_mismatch(zg, zo, off_new)
     s.close()
+
+
+def test_z_layout_follows_the_measured_rule():
+    """Auto takes four documents per warp while one bitmap word per lane
+    covers K (K <= 256), one per warp above; 4 forces four (K <= 1024), the
+    column-only path one; the longest documents go to CTAs either way."""
+    import paper_1704_03581_gb300 as P
+    rng = np.random.default_rng(5)
+    lengths = np.concatenate([[4000], rng.integers(1, 200, size=200)])
+    w, off = corpus_from_lengths(rng, lengths, 800)
+    for K, kw, dpw in [(20, {}, 4), (256, {}, 4), (257, {}, 1), (1000, {}, 1), (1000, dict(docs_per_warp=4), 4),
+                       (100, dict(docs_per_warp=1), 1), (100, dict(zstep_path=1), 1)]:
+        s = P.Sampler(w, off, K, 800, 0.1, 0.01, seed=1, **kw)
+        lay = s.z_layout()
+        assert lay["docs_per_warp"] == dpw, (K, kw, lay)
+        assert lay["coop_docs"] == 1, (K, kw, lay)          # the 4,000-token document is above max(256, N / div)
+        s.close()

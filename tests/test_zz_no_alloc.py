@@ -124,6 +124,6 @@ def test_noalloc_matches_infer_when_infer_uses_its_other_kernels(kw):
         assert not first_mismatch(z, z_ref, off), kw
     for d in np.argsort(-lengths, kind="stable")[:2]:
         a, b = int(off[d]), int(off[d + 1])
-        zo = O.infer(ch.tables, w[a:b], np.array([0, b - a], np.int64), 4, 21)
+        zo = O.infer(ch.tables, w[a:b], np.array([0, b - a], np.int64), 4, 21, index_base=a)
         assert np.array_equal(z_ref[a:b], zo), int(d)
     s.close()
