@@ -32,7 +32,7 @@ def build(force: bool = False) -> str:
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-           *SRC, "-o", tmp, "-lm"]
+           "-pthread", *SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
@@ -75,6 +75,10 @@ def lib() -> ctypes.CDLL:
             "or_gamma_draw": (f32, [P, f32, u64, u32, u32, u32, P]),
             "or_phi_draw_dir": (i32, [P, P, i32, i32, u64, u32, P, P]),
             "or_word_tables_dir": (None, [P, P, P, i32, i32, P, P, P, P, P, P, P]),
+            "or_count_n_mt": (None, [i64, P, P, i32, i32, P, i32]),
+            "or_phi_draw_mt": (i32, [P, P, i32, i32, u64, u32, P, P, P, i32]),
+            "or_word_tables_mt": (None, [P, P, P, i32, i32, P, P, P, P, P, P, P, i32]),
+            "or_z_step_mt": (i32, [P, i64, P, P, i32, i32, P, P, P, P, P, P, u64, u32, i64, P, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -174,8 +178,22 @@ def init_z(N: int, K: int, seed: int, index_base: int = 0) -> np.ndarray:
     return z
 
 
-def count_n(w: np.ndarray, z: np.ndarray, K: int, V: int) -> np.ndarray:
+def host_threads() -> int:
+    """The host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def count_n(w: np.ndarray, z: np.ndarray, K: int, V: int, threads: int = 1) -> np.ndarray:
     """Dense n, word-major: ``n[v, k]``."""
+    if threads > 1:
+        w = np.ascontiguousarray(w, dtype=np.int32)
+        z = np.ascontiguousarray(z, dtype=np.int16)
+        n = np.empty((V, K), dtype=np.int32)
+        lib().or_count_n_mt(w.shape[0], _p(w), _p(z), K, V, _p(n), threads)
+        return n
     n = np.zeros((V, K), dtype=np.int32)
     w = np.ascontiguousarray(w, dtype=np.int32)
     z = np.ascontiguousarray(z, dtype=np.int16)
@@ -205,14 +223,18 @@ def log_posterior(doc_off, w, z, K: int, V: int, alpha, beta: float) -> np.ndarr
     return out
 
 
-def phi_draw(ctx: Ctx, n_vk: np.ndarray, seed: int, sweep: int) -> tuple[np.ndarray, np.ndarray, int]:
+def phi_draw(ctx: Ctx, n_vk: np.ndarray, seed: int, sweep: int,
+             threads: int = 1) -> tuple[np.ndarray, np.ndarray, int]:
     """c[v, k] ~ Pois(beta + n[v, k]); S[k] = sum_v c[v, k]."""
     V, K = n_vk.shape
     n_vk = np.ascontiguousarray(n_vk, dtype=np.int32)
     c = np.zeros((V, K), dtype=np.uint32)
     S = np.zeros(K, dtype=np.int64)
     dead = np.zeros(1, dtype=np.int32)
-    rc = lib().or_phi_draw(ctx.h, _p(n_vk), K, V, seed, sweep, _p(c), _p(S), _p(dead))
+    if threads > 1:
+        rc = lib().or_phi_draw_mt(ctx.h, _p(n_vk), K, V, seed, sweep, _p(c), _p(S), _p(dead), threads)
+    else:
+        rc = lib().or_phi_draw(ctx.h, _p(n_vk), K, V, seed, sweep, _p(c), _p(S), _p(dead))
     if rc != 0:
         raise RuntimeError("dead-row redraw did not terminate")
     return c, S, int(dead[0])
@@ -253,7 +275,8 @@ class WordTables:
     From Polya-urn counts c (uint32) and row sums S (int64), or, with
     ``dirichlet=True``, from Gamma draws (float32) and row sums S (float64)."""
 
-    def __init__(self, c_vk: np.ndarray, S: np.ndarray, alpha: np.ndarray, dirichlet: bool = False):
+    def __init__(self, c_vk: np.ndarray, S: np.ndarray, alpha: np.ndarray, dirichlet: bool = False,
+                 threads: int = 1):
         V, K = c_vk.shape
         self.V, self.K = V, K
         self.ncol = np.zeros(V, dtype=np.int32)
@@ -272,8 +295,12 @@ class WordTables:
             g = np.ascontiguousarray(c_vk, dtype=np.uint32)
             S = np.ascontiguousarray(S, dtype=np.int64)
             fn = lib().or_word_tables
-        fn(_p(g), _p(S), _p(alpha), K, V, _p(self.ncol), _p(self.topic), _p(self.q),
-           _p(self.A), _p(self.athr), _p(self.atopic), _p(self.phi32))
+        args = [_p(g), _p(S), _p(alpha), K, V, _p(self.ncol), _p(self.topic), _p(self.q),
+                _p(self.A), _p(self.athr), _p(self.atopic), _p(self.phi32)]
+        if threads > 1 and not dirichlet:
+            lib().or_word_tables_mt(*args, threads)
+        else:
+            fn(*args)
 
     def column(self, v: int):
         n = int(self.ncol[v])
@@ -289,14 +316,22 @@ class WordTables:
 
 
 def z_step(doc_off: np.ndarray, w: np.ndarray, z: np.ndarray, tables: WordTables, seed: int, sweep: int,
-           index_base: int = 0, slice_len: int = 0) -> tuple[np.ndarray, np.ndarray]:
+           index_base: int = 0, slice_len: int = 0, threads: int = 1) -> tuple[np.ndarray, np.ndarray]:
     """One z-step; returns (new z, stats[tokens, a_branch, sum_min, zero_mass, sum_inter, docside]).
-    slice_len > 0 splits longer documents into concurrent slices with stale counts (not Algorithm 2)."""
+    slice_len > 0 splits longer documents into concurrent slices with stale counts (not Algorithm 2);
+    threads > 1 resamples whole documents on that many host threads (the same results)."""
     z = np.array(z, dtype=np.int16, copy=True)
     doc_off = np.ascontiguousarray(doc_off, dtype=np.int64)
     w = np.ascontiguousarray(w, dtype=np.int32)
     stats = np.zeros(6, dtype=np.int64)
     t = tables
+    if threads > 1 and slice_len == 0:
+        rc = lib().or_z_step_mt(_p(doc_off), doc_off.shape[0] - 1, _p(w), _p(z), t.K, t.V, _p(t.ncol), _p(t.topic),
+                                _p(t.q), _p(t.A), _p(t.athr), _p(t.atopic), seed, sweep, index_base, _p(stats),
+                                threads)
+        if rc != 0:
+            raise RuntimeError("z-step failed")
+        return z, stats
     rc = lib().or_z_step_sliced(_p(doc_off), doc_off.shape[0] - 1, _p(w), _p(z), t.K, t.V, _p(t.ncol), _p(t.topic),
                                 _p(t.q), _p(t.A), _p(t.athr), _p(t.atopic), seed, sweep, index_base, slice_len,
                                 _p(stats))
@@ -314,7 +349,7 @@ class Chain:
     """
 
     def __init__(self, w, doc_off, K: int, V: int, alpha, beta: float, seed: int, z=None, sweep: int = 0,
-                 dirichlet: bool = False, slice_len: int = 0):
+                 dirichlet: bool = False, slice_len: int = 0, threads: int = 1):
         self.w = np.ascontiguousarray(w, dtype=np.int32)
         self.doc_off = np.ascontiguousarray(doc_off, dtype=np.int64)
         self.K, self.V, self.seed = K, V, int(seed)
@@ -330,22 +365,23 @@ class Chain:
         self.dead_rows = 0
         self.dirichlet = dirichlet      # Algorithm 1's Dirichlet Phi instead of the Polya urn
         self.slice_len = slice_len      # > 0: long documents in concurrent slices with stale counts
+        self.threads = threads          # host threads of the Polya-urn steps (results are the same)
 
     def phi_step(self, sweep: int):
-        n = count_n(self.w, self.z, self.K, self.V)
+        n = count_n(self.w, self.z, self.K, self.V, threads=self.threads)
         if self.dirichlet:
             self.c, self.S = phi_draw_dir(self.ctx, n, self.seed, sweep)
             self.dead_rows = 0
         else:
-            self.c, self.S, self.dead_rows = phi_draw(self.ctx, n, self.seed, sweep)
-        self.tables = WordTables(self.c, self.S, self.alpha, dirichlet=self.dirichlet)
+            self.c, self.S, self.dead_rows = phi_draw(self.ctx, n, self.seed, sweep, threads=self.threads)
+        self.tables = WordTables(self.c, self.S, self.alpha, dirichlet=self.dirichlet, threads=self.threads)
 
     def sweep(self, n_sweeps: int = 1):
         for _ in range(n_sweeps):
             self.sweep_index += 1
             self.phi_step(self.sweep_index)
             self.z, self.stats = z_step(self.doc_off, self.w, self.z, self.tables, self.seed, self.sweep_index,
-                                        slice_len=self.slice_len)
+                                        slice_len=self.slice_len, threads=self.threads)
         return self
 
     def n(self) -> np.ndarray:

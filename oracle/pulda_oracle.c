@@ -46,6 +46,7 @@
  *        pulda_oracle.c -lm
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -376,21 +377,31 @@ static void beta_field(const or_ctx *c, uint64_t seed, uint32_t sweep, uint32_t 
     }
 }
 
+/* Word v's entries c_{k,v}, k = 0..K-1 (its row of c_vk, zeroed first). */
+static void phi_word(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t v,
+                     uint64_t seed, uint32_t sweep, uint32_t *c_vk)
+{
+    const int32_t *nv = n_vk + (int64_t)v * K;
+    uint32_t *cv = c_vk + (int64_t)v * K;
+    memset(cv, 0, sizeof(uint32_t) * (size_t)K);
+    for (int32_t k = 0; k < K; k++) {
+        if (nv[k] == 0) continue;
+        uint32_t x[4];
+        draw4(seed, (uint32_t)v, (uint32_t)k, sweep, OR_TAG_POIS, 0, x);
+        cv[k] = or_draw_entry(c, nv[k], x[0], x[1]);
+    }
+    beta_field(c, seed, sweep, OR_TAG_BETA, 0, (uint32_t)v, K, nv, 1, cv, 1);
+}
+
+/* Row k of Phi redrawn until its sum is nonzero (R-DEAD); returns the sum,
+   or 0 if it stayed zero for OR_MAX_REDRAW attempts. */
+static int64_t phi_redraw_row(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V, int32_t k,
+                              uint64_t seed, uint32_t sweep, uint32_t *c_vk);
+
 int32_t or_phi_draw(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V,
                     uint64_t seed, uint32_t sweep, uint32_t *c_vk, int64_t *S, int32_t *dead_rows)
 {
-    memset(c_vk, 0, sizeof(uint32_t) * (size_t)K * (size_t)V);
-    for (int32_t v = 0; v < V; v++) {
-        const int32_t *nv = n_vk + (int64_t)v * K;
-        uint32_t *cv = c_vk + (int64_t)v * K;
-        for (int32_t k = 0; k < K; k++) {
-            if (nv[k] == 0) continue;
-            uint32_t x[4];
-            draw4(seed, (uint32_t)v, (uint32_t)k, sweep, OR_TAG_POIS, 0, x);
-            cv[k] = or_draw_entry(c, nv[k], x[0], x[1]);
-        }
-        beta_field(c, seed, sweep, OR_TAG_BETA, 0, (uint32_t)v, K, nv, 1, cv, 1);
-    }
+    for (int32_t v = 0; v < V; v++) phi_word(c, n_vk, K, v, seed, sweep, c_vk);
     for (int32_t k = 0; k < K; k++) {
         S[k] = 0;
         for (int32_t v = 0; v < V; v++) S[k] += c_vk[(int64_t)v * K + k];
@@ -399,6 +410,17 @@ int32_t or_phi_draw(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V,
     for (int32_t k = 0; k < K; k++) {
         if (S[k] != 0) continue;
         dead++;
+        S[k] = phi_redraw_row(c, n_vk, K, V, k, seed, sweep, c_vk);
+        if (S[k] == 0) return -1;
+    }
+    *dead_rows = dead;
+    return 0;
+}
+
+static int64_t phi_redraw_row(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V, int32_t k,
+                              uint64_t seed, uint32_t sweep, uint32_t *c_vk)
+{
+    {
         uint32_t a;
         for (a = 1; a <= OR_MAX_REDRAW; a++) {
             for (int32_t v = 0; v < V; v++) {
@@ -415,11 +437,9 @@ int32_t or_phi_draw(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V,
                        n_vk + k, K, c_vk + k, K);
             int64_t s = 0;
             for (int32_t v = 0; v < V; v++) s += c_vk[(int64_t)v * K + k];
-            if (s > 0) { S[k] = s; break; }
+            if (s > 0) return s;
         }
-        if (a > OR_MAX_REDRAW) return -1;
     }
-    if (dead_rows) *dead_rows = dead;
     return 0;
 }
 
@@ -429,14 +449,12 @@ int32_t or_phi_draw(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V,
 /* q, the alpha-part weights a = q * alpha (in 2^-16 units), sigma_a = A and */
 /* the alias table over a.  phi32 = fp32(c / S) is the exported Phi.        */
 /* ------------------------------------------------------------------------ */
-void or_word_tables(const uint32_t *c_vk, const int64_t *S, const float *alpha, int32_t K, int32_t V,
-                    int32_t *ncol, int16_t *topic, uint32_t *q, uint64_t *A,
-                    uint32_t *athr, int16_t *atopic, float *phi32)
+/* Word v's tables; phi64, a and al are scratch of K entries. */
+static void word_table(const uint32_t *c_vk, const int64_t *S, const float *alpha, int32_t K, int32_t v,
+                       int32_t *ncol, int16_t *topic, uint32_t *q, uint64_t *A,
+                       uint32_t *athr, int16_t *atopic, float *phi32, double *phi64, uint64_t *a, int32_t *al)
 {
-    double *phi64 = (double *)malloc(sizeof(double) * (size_t)K);
-    uint64_t *a = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K);
-    int32_t *al = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
-    for (int32_t v = 0; v < V; v++) {
+    {
         const uint32_t *cv = c_vk + (int64_t)v * K;
         int64_t base = (int64_t)v * K;
         int32_t n = 0;
@@ -451,7 +469,7 @@ void or_word_tables(const uint32_t *c_vk, const int64_t *S, const float *alpha, 
             n++;
         }
         ncol[v] = n;
-        if (n == 0) { A[v] = 0; continue; }
+        if (n == 0) { A[v] = 0; return; }
         int e;
         frexp(phimax, &e);                 /* phimax = f 2^e, f in [1/2, 1) */
         uint64_t tot = 0;
@@ -467,6 +485,17 @@ void or_word_tables(const uint32_t *c_vk, const int64_t *S, const float *alpha, 
         or_vose(a, n, athr + base, al);
         for (int32_t j = 0; j < n; j++) atopic[base + j] = topic[base + al[j]];
     }
+}
+
+void or_word_tables(const uint32_t *c_vk, const int64_t *S, const float *alpha, int32_t K, int32_t V,
+                    int32_t *ncol, int16_t *topic, uint32_t *q, uint64_t *A,
+                    uint32_t *athr, int16_t *atopic, float *phi32)
+{
+    double *phi64 = (double *)malloc(sizeof(double) * (size_t)K);
+    uint64_t *a = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K);
+    int32_t *al = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
+    for (int32_t v = 0; v < V; v++)
+        word_table(c_vk, S, alpha, K, v, ncol, topic, q, A, athr, atopic, phi32, phi64, a, al);
     free(phi64); free(a); free(al);
 }
 
@@ -530,6 +559,34 @@ static int32_t z_token(int64_t i, int32_t v, int32_t kold, int64_t *m, int64_t *
     return knew;
 }
 
+/* Document d's tokens in order (in slices of slice_len with stale counts
+   when slice_len > 0 and the document is longer); m0 and m are scratch of K
+   entries. */
+static int32_t z_doc(int64_t d, const int64_t *doc_off, const int32_t *w, int16_t *z, int32_t K,
+                     const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
+                     const uint32_t *athr, const int16_t *atopic, uint64_t seed, uint32_t sweep,
+                     int64_t index_base, int64_t slice_len, int64_t *stats, int64_t *m0, int64_t *m)
+{
+    memset(m0, 0, sizeof(int64_t) * (size_t)K);
+    int64_t kd0 = 0;                    /* number of nonzero m_{d,k} */
+    for (int64_t i = doc_off[d]; i < doc_off[d + 1]; i++)
+        if (m0[z[i]]++ == 0) kd0++;
+    int64_t len = doc_off[d + 1] - doc_off[d];
+    int64_t step = (slice_len > 0 && len > slice_len) ? slice_len : len;
+    for (int64_t a = doc_off[d]; a < doc_off[d + 1]; a += step) {
+        memcpy(m, m0, sizeof(int64_t) * (size_t)K);
+        int64_t kd = kd0;
+        int64_t b = a + step < doc_off[d + 1] ? a + step : doc_off[d + 1];
+        for (int64_t i = a; i < b; i++) {
+            int32_t knew = z_token(i, w[i], z[i], m, &kd, K, ncol, topic, q, A, athr, atopic,
+                                   seed, sweep, index_base, stats);
+            if (knew < 0) return -1;
+            z[i] = (int16_t)knew;
+        }
+    }
+    return 0;
+}
+
 int32_t or_z_step(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *z, int32_t K, int32_t V,
                   const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
                   const uint32_t *athr, const int16_t *atopic,
@@ -552,28 +609,13 @@ int32_t or_z_step_sliced(const int64_t *doc_off, int64_t D, const int32_t *w, in
     (void)V;
     int64_t *m0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
     int64_t *m = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
-    for (int64_t d = 0; d < D; d++) {
-        memset(m0, 0, sizeof(int64_t) * (size_t)K);
-        int64_t kd0 = 0;                    /* number of nonzero m_{d,k} */
-        for (int64_t i = doc_off[d]; i < doc_off[d + 1]; i++)
-            if (m0[z[i]]++ == 0) kd0++;
-        int64_t len = doc_off[d + 1] - doc_off[d];
-        int64_t step = (slice_len > 0 && len > slice_len) ? slice_len : len;
-        for (int64_t a = doc_off[d]; a < doc_off[d + 1]; a += step) {
-            memcpy(m, m0, sizeof(int64_t) * (size_t)K);
-            int64_t kd = kd0;
-            int64_t b = a + step < doc_off[d + 1] ? a + step : doc_off[d + 1];
-            for (int64_t i = a; i < b; i++) {
-                int32_t knew = z_token(i, w[i], z[i], m, &kd, K, ncol, topic, q, A, athr, atopic,
-                                       seed, sweep, index_base, stats);
-                if (knew < 0) { free(m0); free(m); return -1; }
-                z[i] = (int16_t)knew;
-            }
-        }
-    }
+    int32_t rc = 0;
+    for (int64_t d = 0; d < D && rc == 0; d++)
+        rc = z_doc(d, doc_off, w, z, K, ncol, topic, q, A, athr, atopic, seed, sweep, index_base, slice_len,
+                   stats, m0, m);
     free(m0);
     free(m);
-    return 0;
+    return rc;
 }
 
 /* ------------------------------------------------------------------ Dirichlet Phi (Algorithm 1)
@@ -788,4 +830,161 @@ int32_t or_log_posterior(const int64_t *doc_off, int64_t D, const int32_t *w, co
     out[1] = docs;
     out[2] = topics;
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same steps over several host threads.  Algorithm 2 resamples the      */
+/* documents independently ("in parallel for d"), and the Phi-step draws     */
+/* every word's entries independently; here each thread runs the per-word    */
+/* and per-document steps above on whole words and documents, taken from a   */
+/* shared counter.  Every draw is keyed by (token | word, topic, sweep) and  */
+/* every count and sum is an exact integer, so the results are bit for bit   */
+/* the single-threaded functions' whatever the thread count and schedule.    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int kind;                     /* 0 counts, 1 Phi rows of words, 2 dead-row redraws, 3 tables, 4 documents */
+    int64_t total, chunk;         /* work items and how many a thread takes at once */
+    int64_t next;                 /* shared counter (atomic) */
+    int32_t err;                  /* set (atomic) by a failing item */
+    /* arguments */
+    const or_ctx *c;
+    int64_t N; int32_t K, V;
+    const int32_t *w; int16_t *z; const int64_t *doc_off;
+    const int32_t *n_vk; uint32_t *c_vk; int64_t *S; const int32_t *dead_k;
+    const float *alpha; int32_t *ncol; int16_t *topic; uint32_t *q; uint64_t *A; uint32_t *athr;
+    int16_t *atopic; float *phi32;
+    uint64_t seed; uint32_t sweep; int64_t index_base;
+    int64_t stats[6];             /* summed (atomic) from the threads' own counters */
+} mt_job;
+
+static void *mt_worker(void *arg)
+{
+    mt_job *j = (mt_job *)arg;
+    const int32_t K = j->K;
+    double *phi64 = NULL; uint64_t *a = NULL; int32_t *al = NULL; int64_t *m0 = NULL, *m = NULL;
+    if (j->kind == 3) {
+        phi64 = (double *)malloc(sizeof(double) * (size_t)K);
+        a = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)K);
+        al = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
+        if (!phi64 || !a || !al) { __atomic_store_n(&j->err, 1, __ATOMIC_RELAXED); goto out; }
+    }
+    if (j->kind == 4) {
+        m0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+        m = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+        if (!m0 || !m) { __atomic_store_n(&j->err, 1, __ATOMIC_RELAXED); goto out; }
+    }
+    int64_t st[6] = {0, 0, 0, 0, 0, 0};
+    for (;;) {
+        int64_t lo = __atomic_fetch_add(&j->next, j->chunk, __ATOMIC_RELAXED);
+        if (lo >= j->total) break;
+        int64_t hi = lo + j->chunk < j->total ? lo + j->chunk : j->total;
+        for (int64_t i = lo; i < hi; i++) {
+            switch (j->kind) {
+            case 0:
+                __atomic_fetch_add(&((int32_t *)j->n_vk)[(int64_t)j->w[i] * K + j->z[i]], 1, __ATOMIC_RELAXED);
+                break;
+            case 1:
+                phi_word(j->c, j->n_vk, K, (int32_t)i, j->seed, j->sweep, j->c_vk);
+                break;
+            case 2: {
+                int32_t k = j->dead_k[i];
+                j->S[k] = phi_redraw_row(j->c, j->n_vk, K, j->V, k, j->seed, j->sweep, j->c_vk);
+                if (j->S[k] == 0) __atomic_store_n(&j->err, 1, __ATOMIC_RELAXED);
+                break;
+            }
+            case 3:
+                word_table(j->c_vk, j->S, j->alpha, K, (int32_t)i, j->ncol, j->topic, j->q, j->A, j->athr,
+                           j->atopic, j->phi32, phi64, a, al);
+                break;
+            default:
+                if (z_doc(i, j->doc_off, j->w, j->z, K, j->ncol, j->topic, j->q, j->A, j->athr, j->atopic,
+                          j->seed, j->sweep, j->index_base, 0, st, m0, m) != 0)
+                    __atomic_store_n(&j->err, 1, __ATOMIC_RELAXED);
+            }
+        }
+    }
+    for (int t = 0; t < 6; t++) __atomic_fetch_add(&j->stats[t], st[t], __ATOMIC_RELAXED);
+out:
+    free(phi64); free(a); free(al); free(m0); free(m);
+    return NULL;
+}
+
+/* Runs job j on n_threads threads (the calling one included); 0 on success. */
+static int32_t mt_run(mt_job *j, int32_t n_threads)
+{
+    if (n_threads < 1) n_threads = 1;
+    j->next = 0;
+    j->err = 0;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    if (!th) return -1;
+    int32_t started = 0;
+    for (int32_t t = 1; t < n_threads; t++)
+        if (pthread_create(&th[t], NULL, mt_worker, j) == 0) started = t;
+        else break;
+    mt_worker(j);
+    for (int32_t t = 1; t <= started; t++) pthread_join(th[t], NULL);
+    free(th);
+    return j->err ? -1 : 0;
+}
+
+void or_count_n_mt(int64_t N, const int32_t *w, const int16_t *z, int32_t K, int32_t V, int32_t *n_vk,
+                   int32_t n_threads)
+{
+    memset(n_vk, 0, sizeof(int32_t) * (size_t)K * (size_t)V);
+    mt_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = 0; j.total = N; j.chunk = 1 << 16; j.K = K; j.V = V; j.w = w; j.z = (int16_t *)z; j.n_vk = n_vk;
+    mt_run(&j, n_threads);
+}
+
+int32_t or_phi_draw_mt(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V, uint64_t seed, uint32_t sweep,
+                       uint32_t *c_vk, int64_t *S, int32_t *dead_rows, int32_t n_threads)
+{
+    mt_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = 1; j.total = V; j.chunk = 16; j.c = c; j.K = K; j.V = V; j.n_vk = n_vk; j.c_vk = c_vk;
+    j.seed = seed; j.sweep = sweep;
+    if (mt_run(&j, n_threads) != 0) return -1;
+    for (int32_t k = 0; k < K; k++) S[k] = 0;
+    for (int32_t v = 0; v < V; v++)
+        for (int32_t k = 0; k < K; k++) S[k] += c_vk[(int64_t)v * K + k];
+    int32_t *dead = (int32_t *)malloc(sizeof(int32_t) * (size_t)K);
+    if (!dead) return -1;
+    int32_t nd = 0;
+    for (int32_t k = 0; k < K; k++)
+        if (S[k] == 0) dead[nd++] = k;
+    j.kind = 2; j.total = nd; j.chunk = 1; j.S = S; j.dead_k = dead;
+    int32_t rc = mt_run(&j, n_threads);
+    free(dead);
+    if (rc != 0) return -1;
+    *dead_rows = nd;
+    return 0;
+}
+
+void or_word_tables_mt(const uint32_t *c_vk, const int64_t *S, const float *alpha, int32_t K, int32_t V,
+                       int32_t *ncol, int16_t *topic, uint32_t *q, uint64_t *A,
+                       uint32_t *athr, int16_t *atopic, float *phi32, int32_t n_threads)
+{
+    mt_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = 3; j.total = V; j.chunk = 64; j.K = K; j.V = V; j.c_vk = (uint32_t *)c_vk; j.S = (int64_t *)S;
+    j.alpha = alpha; j.ncol = ncol; j.topic = topic; j.q = q; j.A = A; j.athr = athr; j.atopic = atopic;
+    j.phi32 = phi32;
+    mt_run(&j, n_threads);
+}
+
+int32_t or_z_step_mt(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *z, int32_t K, int32_t V,
+                     const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
+                     const uint32_t *athr, const int16_t *atopic,
+                     uint64_t seed, uint32_t sweep, int64_t index_base, int64_t *stats, int32_t n_threads)
+{
+    mt_job j;
+    memset(&j, 0, sizeof j);
+    j.kind = 4; j.total = D; j.chunk = 16; j.K = K; j.V = V; j.doc_off = doc_off; j.w = w; j.z = z;
+    j.ncol = (int32_t *)ncol; j.topic = (int16_t *)topic; j.q = (uint32_t *)q; j.A = (uint64_t *)A;
+    j.athr = (uint32_t *)athr; j.atopic = (int16_t *)atopic; j.seed = seed; j.sweep = sweep;
+    j.index_base = index_base;
+    int32_t rc = mt_run(&j, n_threads);
+    for (int t = 0; t < 6; t++) stats[t] += j.stats[t];
+    return rc;
 }

@@ -63,4 +63,18 @@ int32_t or_phi_draw_dir(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t
 void or_word_tables_dir(const float *g_vk, const double *S, const float *alpha, int32_t K, int32_t V,
                         int32_t *ncol, int16_t *topic, uint32_t *q, uint64_t *A,
                         uint32_t *athr, int16_t *atopic, float *phi32);
+/* The same steps over n_threads host threads: results identical to the
+   single-threaded functions (words, dead rows and documents are independent
+   work items; every draw is keyed, every count exact). */
+void or_count_n_mt(int64_t N, const int32_t *w, const int16_t *z, int32_t K, int32_t V, int32_t *n_vk,
+                   int32_t n_threads);
+int32_t or_phi_draw_mt(const or_ctx *c, const int32_t *n_vk, int32_t K, int32_t V, uint64_t seed, uint32_t sweep,
+                       uint32_t *c_vk, int64_t *S, int32_t *dead_rows, int32_t n_threads);
+void or_word_tables_mt(const uint32_t *c_vk, const int64_t *S, const float *alpha, int32_t K, int32_t V,
+                       int32_t *ncol, int16_t *topic, uint32_t *q, uint64_t *A,
+                       uint32_t *athr, int16_t *atopic, float *phi32, int32_t n_threads);
+int32_t or_z_step_mt(const int64_t *doc_off, int64_t D, const int32_t *w, int16_t *z, int32_t K, int32_t V,
+                     const int32_t *ncol, const int16_t *topic, const uint32_t *q, const uint64_t *A,
+                     const uint32_t *athr, const int16_t *atopic,
+                     uint64_t seed, uint32_t sweep, int64_t index_base, int64_t *stats, int32_t n_threads);
 #endif

@@ -738,3 +738,34 @@ def test_sliced_z_step_uses_the_pass_start_counts():
     assert stats.chi2.sf(chi, K - 1) > 1e-4
     exact = np.array([O.z_step(off, w, z0, t, 7, s)[0][5] for s in range(1, n + 1)])
     assert abs(np.mean(exact == 1) - p[1]) > 0.1     # the exact law is far from the stale one
+
+
+# ------------------------------------------------- the oracle on many threads
+
+def test_threaded_oracle_equals_the_single_threaded_one():
+    """The document- and word-parallel oracle (Algorithm 2's documents are
+    independent given Phi; each word's Phi entries are independent) gives the
+    single-threaded results bit for bit: topics, counts, Poisson counts, row
+    sums, dead rows, tables and every z-step counter, on a corpus whose
+    small V and beta kill rows (so the parallel redraw runs too)."""
+    from paper_1704_03581_gb300 import synth
+    c = synth.tiny()
+    rng = np.random.default_rng(9)
+    cases = [(c.w, c.doc_off, 20, c.V, 0.1, 0.01),
+             (rng.integers(0, 40, size=1500).astype(np.int32), np.arange(0, 1501, 30, dtype=np.int64), 2000, 40,
+              0.2, 0.002)]
+    for w, off, K, V, alpha, beta in cases:
+        a = O.Chain(w, off, K, V, alpha, beta, seed=4)
+        b = O.Chain(w, off, K, V, alpha, beta, seed=4, threads=5)
+        dead = 0
+        for _ in range(3):
+            a.sweep(1)
+            b.sweep(1)
+            assert np.array_equal(a.z, b.z) and np.array_equal(a.stats, b.stats)
+            assert np.array_equal(a.c, b.c) and np.array_equal(a.S, b.S) and a.dead_rows == b.dead_rows
+            for k in ("ncol", "topic", "q", "A", "athr", "atopic", "phi32"):
+                assert np.array_equal(getattr(a.tables, k), getattr(b.tables, k)), k
+            assert np.array_equal(O.count_n(a.w, a.z, K, V), O.count_n(b.w, b.z, K, V, threads=3))
+            dead += a.dead_rows
+        if beta < 0.01:
+            assert dead > 0
