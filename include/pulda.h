@@ -85,6 +85,24 @@ typedef struct {
                                (one warp per document); a server on the handle uses it for
                                requests (0 = requests of at least 1,024 tokens) */
     int32_t reserved[2];
+    /* Device memory.  With alloc set, every device buffer the library takes
+     * -- the handle's state in pulda_init, the temporaries of pulda_infer,
+     * pulda_get_counts, pulda_get_phi and pulda_log_posterior, a server's
+     * arenas and slot tables, a batch's tables -- comes from
+     * alloc(bytes, stream, alloc_ctx) and goes back through
+     * free(ptr, stream, alloc_ctx); `stream` is the handle's (or the
+     * server's) cudaStream_t.  alloc must return device memory of the
+     * handle's device aligned to 256 bytes, or NULL: the call then returns
+     * PULDA_ERR_OOM after giving back everything it had taken (a misaligned
+     * pointer is given back and reported as PULDA_ERR_CUDA).  A temporary
+     * may be given back while work that reads it is still queued on
+     * `stream`, so free must order the release after that work, as
+     * cudaFreeAsync does (a stream-aware caching allocator does; otherwise
+     * synchronise the stream first).  Both NULL = cudaMalloc for the state,
+     * cudaMallocAsync for temporaries; only one set = PULDA_ERR_INVALID. */
+    void *(*alloc)(size_t bytes, void *stream, void *alloc_ctx);
+    void (*free)(void *ptr, void *stream, void *alloc_ctx);
+    void *alloc_ctx;
 } pulda_options;
 
 /* Counters of the most recent z-step (and Phi-step), and running totals. */

@@ -39,10 +39,34 @@ class PuldaError(RuntimeError):
         self.status = status
 
 
+# pulda_options' device-allocator callbacks: alloc(bytes, stream, ctx) -> pointer or NULL,
+# free(ptr, stream, ctx)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("zstep_path", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("docs_per_warp", ctypes.c_int32), ("phi_mode", ctypes.c_int32),
-                ("slice_len", ctypes.c_int32), ("coop_min_len", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("slice_len", ctypes.c_int32), ("coop_min_len", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+def allocator_callbacks(allocator) -> tuple:
+    """C callbacks for an object with ``alloc(nbytes, stream) -> int`` (a
+    device pointer, 0 when it cannot) and ``free(ptr, stream)``.  Keep the
+    returned pair alive while the library may call it (until the handle,
+    server or batch is freed)."""
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(allocator.alloc(int(nbytes), stream)) or None
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        allocator.free(int(ptr), stream)
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
 
 
 class SweepStats(ctypes.Structure):
@@ -136,7 +160,8 @@ def _check(h, status: int):
 
 def pulda_init(word_ids, doc_offsets, K: int, V: int, alpha, beta: float, seed: int, stream=None,
                zstep_path: int = 0, warps_per_block: int = 0, docs_per_warp: int = 0, phi_mode: int = 0,
-               slice_len: int = 0, coop_min_len: int = 0) -> int:
+               slice_len: int = 0, coop_min_len: int = 0, callbacks: tuple | None = None) -> int:
+    """``callbacks`` = allocator_callbacks(...) routes the handle's device memory through them."""
     w = np.ascontiguousarray(word_ids, dtype=np.int32)
     off = np.ascontiguousarray(doc_offsets, dtype=np.int64)
     a = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, dtype=np.float32), (K,)))
@@ -148,6 +173,8 @@ def pulda_init(word_ids, doc_offsets, K: int, V: int, alpha, beta: float, seed: 
     opt.phi_mode = phi_mode
     opt.slice_len = slice_len
     opt.coop_min_len = coop_min_len
+    if callbacks is not None:
+        opt.alloc, opt.free = callbacks
     h = ctypes.c_void_p()
     st = lib().pulda_init(ctypes.byref(h), _ptr(w), _ptr(off), off.shape[0] - 1, K, V, _ptr(a), float(beta),
                           int(seed) & (2 ** 64 - 1), ctypes.byref(opt))
@@ -311,17 +338,21 @@ class Sampler:
 
     def __init__(self, word_ids, doc_offsets, K: int, V: int, alpha=0.1, beta: float = 0.01, seed: int = 0,
                  stream=None, zstep_path: int = 0, warps_per_block: int = 0, docs_per_warp: int = 0,
-                 phi_mode: int = 0, slice_len: int = 0, coop_min_len: int = 0):
+                 phi_mode: int = 0, slice_len: int = 0, coop_min_len: int = 0, allocator=None):
         """phi_mode 0: Poisson Polya urn (Algorithm 2); 1: Dirichlet Phi (Algorithm 1).
         slice_len > 0: documents longer than it resampled in concurrent stale-count slices (not the paper's).
         coop_min_len: documents at least this long resampled by a whole CTA (0 = automatic, -1 = never);
-        the topics are the same either way."""
+        the topics are the same either way.  allocator: an object with alloc(nbytes, stream) -> device
+        pointer (0 if it cannot) and free(ptr, stream) that supplies every device buffer of the handle,
+        its temporaries and its servers (see pulda_options in include/pulda.h)."""
         self.K, self.V = K, V
         self.phi_mode = phi_mode
         self.N = int(np.asarray(doc_offsets)[-1])
         self.D = int(np.asarray(doc_offsets).shape[0] - 1)
+        self.h = None
+        self._callbacks = allocator_callbacks(allocator) if allocator is not None else None
         self.h = pulda_init(word_ids, doc_offsets, K, V, alpha, beta, seed, stream, zstep_path, warps_per_block,
-                            docs_per_warp, phi_mode, slice_len, coop_min_len)
+                            docs_per_warp, phi_mode, slice_len, coop_min_len, self._callbacks)
 
     def close(self):
         if self.h:
@@ -398,8 +429,10 @@ def _bcheck(b, status: int):
         raise PuldaError(status, msg.decode() if msg else "")
 
 
-def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0):
-    """chains: dicts with w, doc_off, K, V, alpha, beta, seed.  coop_min_len: 0 tuned, -1 never, > 0 fixed."""
+def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0,
+                     callbacks: tuple | None = None):
+    """chains: dicts with w, doc_off, K, V, alpha, beta, seed.  coop_min_len: 0 tuned, -1 never, > 0 fixed.
+    callbacks = allocator_callbacks(...) routes every device buffer of the batch through them."""
     keep = []
     arr = (ChainDesc * len(chains))()
     for i, c in enumerate(chains):
@@ -413,6 +446,8 @@ def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0, 
     opt.stream = stream
     opt.warps_per_block = warps_per_block
     opt.coop_min_len = coop_min_len
+    if callbacks is not None:
+        opt.alloc, opt.free = callbacks
     b = ctypes.c_void_p()
     _bcheck(None, lib().pulda_batch_init(ctypes.byref(b), arr, len(chains), ctypes.byref(opt)))
     return b.value
@@ -457,9 +492,12 @@ def pulda_batch_free(b):
 class Batch:
     """Many chains advanced together: ``Batch(chains).sweep(n)``."""
 
-    def __init__(self, chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0):
+    def __init__(self, chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0,
+                 allocator=None):
         self.sizes = [int(np.asarray(c["doc_off"])[-1]) for c in chains]
-        self.b = pulda_batch_init(chains, stream, warps_per_block, coop_min_len)
+        self.b = None
+        self._callbacks = allocator_callbacks(allocator) if allocator is not None else None
+        self.b = pulda_batch_init(chains, stream, warps_per_block, coop_min_len, self._callbacks)
 
     def close(self):
         if self.b:

@@ -63,7 +63,7 @@ pulda_status fail(pulda_handle *h, pulda_status s, const char *fmt, ...) {
 template <typename T>
 cudaError_t dalloc(pulda_handle *h, T **p, size_t count) {
     void *ptr = nullptr;
-    cudaError_t e = cudaMalloc(&ptr, sizeof(T) * std::max<size_t>(count, 1));
+    cudaError_t e = dev_alloc(h->opt, h->stream, sizeof(T) * std::max<size_t>(count, 1), &ptr, false);
     if (e == cudaSuccess) h->allocs.push_back(ptr);
     *p = static_cast<T *>(ptr);
     return e;
@@ -202,6 +202,28 @@ pulda_status run_z(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_o
 }  // namespace
 
 namespace pulda {
+cudaError_t dev_alloc(const pulda_options &o, cudaStream_t st, size_t bytes, void **out, bool stream_ordered) {
+    *out = nullptr;
+    if (o.alloc) {
+        void *p = o.alloc(bytes, st, o.alloc_ctx);
+        if (!p) return cudaErrorMemoryAllocation;
+        if (reinterpret_cast<uintptr_t>(p) & 255u) {
+            o.free(p, st, o.alloc_ctx);
+            return cudaErrorMisalignedAddress;
+        }
+        *out = p;
+        return cudaSuccess;
+    }
+    return stream_ordered ? cudaMallocAsync(out, bytes, st) : cudaMalloc(out, bytes);
+}
+
+void dev_free(const pulda_options &o, cudaStream_t st, void *p, bool stream_ordered) {
+    if (!p) return;
+    if (o.alloc) o.free(p, st, o.alloc_ctx);
+    else if (stream_ordered) cudaFreeAsync(p, st);
+    else cudaFree(p);
+}
+
 PhiArgs phi_args(pulda_handle *h) {
     PhiArgs a{};
     a.K = h->K; a.V = h->V; a.seed = h->seed; a.sweep = static_cast<uint32_t>(h->sweep);
@@ -272,6 +294,12 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     int64_t N = 0;
     if (check_corpus(h, word_ids, doc_offsets, D, V, &N) != PULDA_OK) return reject(PULDA_ERR_INVALID);
     if (opt) h->opt = *opt;
+    if ((h->opt.alloc == nullptr) != (h->opt.free == nullptr)) {
+        fail(h, PULDA_ERR_INVALID, "alloc and free must be set together");
+        h->opt.alloc = nullptr;          // nothing was allocated: free nothing through it
+        h->opt.free = nullptr;
+        return reject(PULDA_ERR_INVALID);
+    }
     if (h->opt.zstep_path < 0 || h->opt.zstep_path > 2) { fail(h, PULDA_ERR_INVALID, "zstep_path must be 0, 1 or 2"); return reject(PULDA_ERR_INVALID); }
     if (h->opt.phi_mode != 0 && h->opt.phi_mode != 1) {
         fail(h, PULDA_ERR_INVALID, "phi_mode must be 0 (Polya urn) or 1 (Dirichlet)");
@@ -313,8 +341,9 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     if (build_host_tables(beta, &tab) != 0) { fail(h, PULDA_ERR_INVALID, "Poisson table construction failed"); return bail(PULDA_ERR_INVALID); }
 
 #define ALLOC(ptr, n) do { cudaError_t e_ = dalloc(h, &(ptr), (n)); if (e_ != cudaSuccess) { \
-        fail(h, PULDA_ERR_OOM, "cudaMalloc of %s (%zu entries) failed: %s", #ptr, (size_t)(n), cudaGetErrorString(e_)); \
-        return bail(PULDA_ERR_OOM); } } while (0)
+        const pulda_status s_ = e_ == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA; \
+        fail(h, s_, "allocation of %s (%zu entries) failed: %s", #ptr, (size_t)(n), cudaGetErrorString(e_)); \
+        return bail(s_); } } while (0)
     ALLOC(h->w, N); ALLOC(h->doc_off, D + 1); ALLOC(h->z, N); ALLOC(h->doc_order, D);
     ALLOC(h->perm, N); ALLOC(h->word_off, V + 1); ALLOC(h->word_order, V); ALLOC(h->fill, V);
     ALLOC(h->alpha, K);
@@ -594,19 +623,17 @@ pulda_status pulda_get_counts(pulda_handle *h, int32_t *n_kv, int32_t *m_dk) {
         CU(h, run_heavy(h));
         launch_phi_counts(a, false, h->phi_grid, st);
         int32_t *dn = nullptr;
-        CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dn), sizeof(int32_t) * static_cast<size_t>(h->K) * h->V, st));
+        DevTemp tn(h->opt, st);
+        CU(h, tn.get(&dn, static_cast<size_t>(h->K) * h->V));
         launch_n_dense(a, dn, st);
-        cudaError_t e = cudaMemcpyAsync(n_kv, dn, sizeof(int32_t) * static_cast<size_t>(h->K) * h->V, cudaMemcpyDeviceToHost, st);
-        cudaFreeAsync(dn, st);
-        CU(h, e);
+        CU(h, cudaMemcpyAsync(n_kv, dn, sizeof(int32_t) * static_cast<size_t>(h->K) * h->V, cudaMemcpyDeviceToHost, st));
     }
     if (m_dk && h->D > 0) {
         int32_t *dm = nullptr;
-        CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dm), sizeof(int32_t) * static_cast<size_t>(h->K) * h->D, st));
+        DevTemp tm(h->opt, st);
+        CU(h, tm.get(&dm, static_cast<size_t>(h->K) * h->D));
         launch_doc_topic(h->doc_off, h->D, h->z, h->K, dm, st);
-        cudaError_t e = cudaMemcpyAsync(m_dk, dm, sizeof(int32_t) * static_cast<size_t>(h->K) * h->D, cudaMemcpyDeviceToHost, st);
-        cudaFreeAsync(dm, st);
-        CU(h, e);
+        CU(h, cudaMemcpyAsync(m_dk, dm, sizeof(int32_t) * static_cast<size_t>(h->K) * h->D, cudaMemcpyDeviceToHost, st));
     }
     CU(h, cudaGetLastError());
     return pulda_sync(h);
@@ -622,13 +649,12 @@ pulda_status pulda_log_posterior(pulda_handle *h, double *out) {
     CU(h, cudaMemsetAsync(h->work, 0, sizeof(int), st));
     CU(h, run_heavy(h));
     launch_phi_counts(a, false, h->phi_grid, st);
-    void *scratch = nullptr;
-    CU(h, cudaMallocAsync(&scratch, log_posterior_scratch_bytes(h->D, h->V, h->K), st));
+    unsigned char *scratch = nullptr;
+    DevTemp ts(h->opt, st);
+    CU(h, ts.get(&scratch, log_posterior_scratch_bytes(h->D, h->V, h->K)));
     launch_log_posterior(h->doc_off, h->D, h->z, h->K, h->alpha, h->alpha_sum, a, static_cast<double>(h->beta), scratch, st);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, scratch, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(scratch, st);
-    CU(h, e);
+    CU(h, cudaGetLastError());
+    CU(h, cudaMemcpyAsync(out, scratch, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     return pulda_sync(h);
 }
 
@@ -670,12 +696,11 @@ pulda_status pulda_get_phi(pulda_handle *h, int64_t *col_ptr, int16_t *topic, fl
         if (cap < nnz) return fail(h, PULDA_ERR_INVALID, "capacity %lld < nnz %lld", (long long)cap, (long long)nnz);
         cudaStream_t st = h->stream;
         float *dp = nullptr;
-        CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dp), sizeof(float) * std::max<int64_t>(nnz, 1), st));
+        DevTemp tp(h->opt, st);
+        CU(h, tp.get(&dp, static_cast<size_t>(nnz)));
         PhiArgs a = phi_args(h);
         launch_phi_values(a, dp, st);
-        cudaError_t e = cudaMemcpyAsync(phi, dp, sizeof(float) * nnz, cudaMemcpyDeviceToHost, st);
-        cudaFreeAsync(dp, st);
-        CU(h, e);
+        CU(h, cudaMemcpyAsync(phi, dp, sizeof(float) * nnz, cudaMemcpyDeviceToHost, st));
         return pulda_sync(h);
     }
     return PULDA_OK;
@@ -695,10 +720,11 @@ pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids, const int64_t
     int32_t *dw = nullptr, *dord = nullptr, *dm = nullptr;
     int64_t *doff = nullptr;
     int16_t *dz = nullptr;
-    CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dw), sizeof(int32_t) * std::max<int64_t>(N, 1), st));
-    CU(h, cudaMallocAsync(reinterpret_cast<void **>(&doff), sizeof(int64_t) * (D_new + 1), st));
-    CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dord), sizeof(int32_t) * D_new, st));
-    CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dz), sizeof(int16_t) * std::max<int64_t>(N, 1), st));
+    DevTemp tw(h->opt, st), toff(h->opt, st), tord(h->opt, st), tz(h->opt, st), tm(h->opt, st);
+    CU(h, tw.get(&dw, static_cast<size_t>(N)));
+    CU(h, toff.get(&doff, static_cast<size_t>(D_new + 1)));
+    CU(h, tord.get(&dord, static_cast<size_t>(D_new)));
+    CU(h, tz.get(&dz, static_cast<size_t>(N)));
     std::vector<int32_t> ord = length_order(doc_offsets, D_new);
     CU(h, cudaMemcpyAsync(dw, word_ids, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
     CU(h, cudaMemcpyAsync(doff, doc_offsets, sizeof(int64_t) * (D_new + 1), cudaMemcpyHostToDevice, st));
@@ -713,12 +739,10 @@ pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids, const int64_t
     }
     if (z_out) CU(h, cudaMemcpyAsync(z_out, dz, sizeof(int16_t) * N, cudaMemcpyDeviceToHost, st));
     if (m_out) {
-        CU(h, cudaMallocAsync(reinterpret_cast<void **>(&dm), sizeof(int32_t) * static_cast<size_t>(D_new) * h->K, st));
+        CU(h, tm.get(&dm, static_cast<size_t>(D_new) * h->K));
         launch_doc_topic(doff, D_new, dz, h->K, dm, st);
         CU(h, cudaMemcpyAsync(m_out, dm, sizeof(int32_t) * static_cast<size_t>(D_new) * h->K, cudaMemcpyDeviceToHost, st));
-        cudaFreeAsync(dm, st);
     }
-    cudaFreeAsync(dw, st); cudaFreeAsync(doff, st); cudaFreeAsync(dord, st); cudaFreeAsync(dz, st);
     CU(h, cudaGetLastError());
     return pulda_sync(h);
 }
@@ -763,7 +787,7 @@ const char *pulda_last_error(const pulda_handle *h) { return h ? h->err.c_str() 
 void pulda_free(pulda_handle *h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (void *p : h->allocs) cudaFree(p);
+    for (void *p : h->allocs) dev_free(h->opt, h->stream, p, false);
     if (h->stream2) {
         cudaStreamSynchronize(h->stream2);
         cudaStreamDestroy(h->stream2);

@@ -20,6 +20,7 @@ struct pulda_batch {
     std::string err;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    pulda_options opt{};            // the caller's options (device allocator among them)
     std::vector<pulda_handle *> ch;
     std::vector<void *> allocs;
     BatchLaunch bl{};
@@ -62,7 +63,7 @@ pulda_status bfail(pulda_batch *b, pulda_status s, const std::string &msg) {
 template <typename T>
 cudaError_t balloc(pulda_batch *b, T **p, size_t n) {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, sizeof(T) * std::max<size_t>(n, 1));
+    cudaError_t e = dev_alloc(b->opt, b->stream, sizeof(T) * std::max<size_t>(n, 1), &q, false);
     if (e == cudaSuccess) b->allocs.push_back(q);
     *p = static_cast<T *>(q);
     return e;
@@ -123,6 +124,11 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     };
     pulda_options o{};
     if (opt) o = *opt;
+    if ((o.alloc == nullptr) != (o.free == nullptr)) {
+        b->err = "alloc and free must be set together";
+        return bail(PULDA_ERR_INVALID);
+    }
+    b->opt = o;
     if (o.docs_per_warp == 4) {
         b->err = "batched chains run one document per warp (docs_per_warp must be 0 or 1)";
         return bail(PULDA_ERR_INVALID);
@@ -179,10 +185,11 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     int *d_work = nullptr;
     PhiArgs *d_phi = nullptr;
     ZArgs *d_z = nullptr;
-    if (balloc(b, &d_sweep, 1) != cudaSuccess || balloc(b, &d_work, 4) != cudaSuccess ||
-        balloc(b, &d_phi, n_chains) != cudaSuccess || balloc(b, &d_z, n_chains) != cudaSuccess) {
-        b->err = "device allocation of the batch descriptors failed";
-        return bail(PULDA_ERR_OOM);
+    cudaError_t ea = cudaSuccess;
+    if ((ea = balloc(b, &d_sweep, 1)) != cudaSuccess || (ea = balloc(b, &d_work, 4)) != cudaSuccess ||
+        (ea = balloc(b, &d_phi, n_chains)) != cudaSuccess || (ea = balloc(b, &d_z, n_chains)) != cudaSuccess) {
+        b->err = std::string("device allocation of the batch descriptors failed: ") + cudaGetErrorString(ea);
+        return bail(ea == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA);
     }
     std::vector<PhiArgs> hp(n_chains);
     std::vector<ZArgs> hz(n_chains);
@@ -225,10 +232,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     }
     int2 *d_wl = nullptr, *d_dl = nullptr;
     HeavyChunk *d_heavy = nullptr;
-    if (balloc(b, &d_wl, wlist.size()) != cudaSuccess || balloc(b, &d_dl, dlist.size()) != cudaSuccess ||
-        balloc(b, &d_heavy, heavy.size()) != cudaSuccess) {
-        b->err = "device allocation of the work lists failed";
-        return bail(PULDA_ERR_OOM);
+    if ((ea = balloc(b, &d_wl, wlist.size())) != cudaSuccess || (ea = balloc(b, &d_dl, dlist.size())) != cudaSuccess ||
+        (ea = balloc(b, &d_heavy, heavy.size())) != cudaSuccess) {
+        b->err = std::string("device allocation of the work lists failed: ") + cudaGetErrorString(ea);
+        return bail(ea == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA);
     }
     cudaStream_t st = b->stream;
     const uint32_t zero = 0;
@@ -383,7 +390,8 @@ void pulda_batch_free(pulda_batch *b) {
     if (b->bl.ev_fork) cudaEventDestroy(b->bl.ev_fork);
     if (b->bl.ev_join) cudaEventDestroy(b->bl.ev_join);
     for (pulda_handle *h : b->ch) pulda_free(h);
-    for (void *p : b->allocs) cudaFree(p);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (void *p : b->allocs) dev_free(b->opt, b->stream, p, false);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }

@@ -68,6 +68,30 @@ struct pulda_handle {
 
 
 namespace pulda {
+// Device memory through the caller's allocator (o.alloc / o.free) when set,
+// else cudaMallocAsync / cudaFreeAsync on st (stream_ordered) or cudaMalloc /
+// cudaFree.  A NULL or misaligned pointer from the caller's allocator is
+// cudaErrorMemoryAllocation / cudaErrorMisalignedAddress (the latter given
+// back first).
+cudaError_t dev_alloc(const pulda_options &o, cudaStream_t st, size_t bytes, void **out, bool stream_ordered);
+void dev_free(const pulda_options &o, cudaStream_t st, void *p, bool stream_ordered);
+// A temporary device buffer of a call, given back (stream-ordered) when the
+// call returns, on success or failure alike.
+struct DevTemp {
+    const pulda_options *o;
+    cudaStream_t st;
+    void *p = nullptr;
+    DevTemp(const pulda_options &opt, cudaStream_t s) : o(&opt), st(s) {}
+    DevTemp(const DevTemp &) = delete;
+    DevTemp &operator=(const DevTemp &) = delete;
+    ~DevTemp() { dev_free(*o, st, p, true); }
+    template <typename T>
+    cudaError_t get(T **out, size_t count) {
+        cudaError_t e = dev_alloc(*o, st, sizeof(T) * (count > 0 ? count : 1), &p, true);
+        *out = static_cast<T *>(p);
+        return e;
+    }
+};
 PhiArgs phi_args(pulda_handle *h);
 ZArgs z_args(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, const int32_t *w,
              int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base);

@@ -20,6 +20,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include <time.h>
@@ -318,12 +319,19 @@ pulda_status pulda_serve_open(pulda_handle *h, int64_t token_budget, int32_t max
     if ((e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming)) != cudaSuccess)
         return bad(e, "event creation failed");
-    if ((e = cudaMalloc(&s->arena_w, sizeof(int32_t) * token_budget)) != cudaSuccess) return bad(e, "arena allocation failed");
-    if ((e = cudaMalloc(&s->arena_z, sizeof(int16_t) * token_budget)) != cudaSuccess) return bad(e, "arena allocation failed");
-    if ((e = cudaMalloc(&s->d_slots, sizeof(ServeSlot) * max_slots)) != cudaSuccess) return bad(e, "slot table allocation failed");
-    if ((e = cudaMalloc(&s->d_active, sizeof(int32_t) * max_slots)) != cudaSuccess) return bad(e, "slot table allocation failed");
-    if ((e = cudaMalloc(&s->d_work, sizeof(int) * 4)) != cudaSuccess) return bad(e, "allocation failed");
-    if ((e = cudaMalloc(&s->d_stats, sizeof(unsigned long long) * ST_TOTAL_SLOTS)) != cudaSuccess) return bad(e, "allocation failed");
+    // device buffers through the handle's allocator (the caller's, if it set one)
+    auto dalloc = [&](auto **p, size_t bytes) {
+        void *q = nullptr;
+        const cudaError_t r = dev_alloc(h->opt, s->stream, bytes, &q, false);
+        *p = static_cast<std::remove_pointer_t<std::remove_reference_t<decltype(p)>>>(q);
+        return r;
+    };
+    if ((e = dalloc(&s->arena_w, sizeof(int32_t) * token_budget)) != cudaSuccess) return bad(e, "arena allocation failed");
+    if ((e = dalloc(&s->arena_z, sizeof(int16_t) * token_budget)) != cudaSuccess) return bad(e, "arena allocation failed");
+    if ((e = dalloc(&s->d_slots, sizeof(ServeSlot) * max_slots)) != cudaSuccess) return bad(e, "slot table allocation failed");
+    if ((e = dalloc(&s->d_active, sizeof(int32_t) * max_slots)) != cudaSuccess) return bad(e, "slot table allocation failed");
+    if ((e = dalloc(&s->d_work, sizeof(int) * 4)) != cudaSuccess) return bad(e, "allocation failed");
+    if ((e = dalloc(&s->d_stats, sizeof(unsigned long long) * ST_TOTAL_SLOTS)) != cudaSuccess) return bad(e, "allocation failed");
     if ((e = cudaMallocHost(&s->h_slots, sizeof(ServeSlot) * max_slots)) != cudaSuccess) return bad(e, "pinned allocation failed");
     if ((e = cudaMallocHost(&s->h_new, sizeof(ServeSlot) * max_slots)) != cudaSuccess) return bad(e, "pinned allocation failed");
     if ((e = cudaMallocHost(&s->h_active, sizeof(int32_t) * max_slots)) != cudaSuccess) return bad(e, "pinned allocation failed");
@@ -427,12 +435,13 @@ pulda_status pulda_serve_close(pulda_server *s) {
     pulda_status st = s->err_status;
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->stream2) cudaStreamSynchronize(s->stream2);
-    cudaFree(s->arena_w);
-    cudaFree(s->arena_z);
-    cudaFree(s->d_slots);
-    cudaFree(s->d_active);
-    cudaFree(s->d_work);
-    cudaFree(s->d_stats);
+    const pulda_options &o = s->h->opt;
+    dev_free(o, s->stream, s->arena_w, false);
+    dev_free(o, s->stream, s->arena_z, false);
+    dev_free(o, s->stream, s->d_slots, false);
+    dev_free(o, s->stream, s->d_active, false);
+    dev_free(o, s->stream, s->d_work, false);
+    dev_free(o, s->stream, s->d_stats, false);
     if (s->h_slots) cudaFreeHost(s->h_slots);
     if (s->h_new) cudaFreeHost(s->h_new);
     if (s->h_active) cudaFreeHost(s->h_active);

@@ -148,3 +148,29 @@ def test_noalloc_binding_rejects_bad_tensors_before_the_call():
     for (a, b, c), frag in cases:
         with pytest.raises(ValueError, match=frag):
             P.pulda_infer_noalloc(None, a, b, 1, 0, c)
+
+
+def test_allocator_callbacks_must_come_in_pairs():
+    """pulda_options' alloc and free are set together or not at all; the
+    check comes before any device work (handle and batch)."""
+    import ctypes
+    import numpy as np
+    w = np.array([0, 1, 2], np.int32)
+    off = np.array([0, 3], np.int64)
+    a = np.full(4, 0.1, np.float32)
+    alloc_only = P.ALLOC_FN(lambda n, s, c: None)
+    free_only = P.FREE_FN(lambda p, s, c: None)
+    for field, fn in (("alloc", alloc_only), ("free", free_only)):
+        opt = P.Options()
+        setattr(opt, field, fn)
+        h = ctypes.c_void_p()
+        st = P.lib().pulda_init(ctypes.byref(h), P._ptr(w), P._ptr(off), 1, 4, 3, P._ptr(a), 0.01, 0,
+                                ctypes.byref(opt))
+        assert st == -1 and not h.value
+        assert b"alloc and free" in P.lib().pulda_last_error(None)
+        arr = (P.ChainDesc * 1)()
+        arr[0] = P.ChainDesc(P._ptr(w), P._ptr(off), 1, 4, 3, P._ptr(a), 0.01, 0)
+        b = ctypes.c_void_p()
+        st = P.lib().pulda_batch_init(ctypes.byref(b), arr, 1, ctypes.byref(opt))
+        assert st == -1 and not b.value
+        assert b"alloc and free" in P.lib().pulda_batch_last_error(None)
