@@ -70,6 +70,13 @@ def parse():
     ap.add_argument("--ref-docs", type=int, default=5000,
                     help="documents in each step of the reference (oracle) arm's bounded sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving keys of the sweep line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched keys of the sweep line")
+    ap.add_argument("--serve-low-requests", type=int, default=150,
+                    help="serving keys: requests of the trace both arms serve at half the plain arm's capacity")
+    ap.add_argument("--serve-high-rate", type=float, default=5000.0, help="serving keys: the continuous arm's high rate")
+    ap.add_argument("--serve-high-seconds", type=float, default=2.0, help="serving keys: its arrival window")
+    ap.add_argument("--batch-steps", type=int, default=10, help="batched keys: timed sweeps of each arm")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--docs-per-warp", type=int, default=0, help="z-step documents per warp: 0 auto, 1 or 4")
     ap.add_argument("--phi-mode", type=int, default=0, choices=[0, 1],
@@ -92,7 +99,7 @@ def parse():
                     help="sweep/trace forms: documents longer than this in stale-count slices (0 = Algorithm 2)")
     ap.add_argument("--trace-corpus", choices=["small", "large"], default="small")
     ap.add_argument("--trace-sweeps", type=int, default=100)
-    ap.add_argument("--batch-scale", type=float, default=0.25,
+    ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fraction of each batched chain's documents (1.0 = the full 267M-token workload)")
     ap.add_argument("--coop-min-len", type=int, default=0,
                     help="documents (serving: requests) at least this long resampled by a CTA of four warps "
@@ -374,6 +381,11 @@ def run_pulda(args, corpus, rank: int, world: int):
     t_lp = time.perf_counter()
     lp_after = s.log_posterior()[0]
     lp_ms = 1000.0 * (time.perf_counter() - t_lp)
+    serving = None
+    if world == 1 and not args.no_serving:
+        # fold-in serving against this chain's Phi after its sweeps (not timed above)
+        serving = serving_probe(s, corpus.V, args.serve_sweeps, args.slice, args.serve_low_requests,
+                                args.serve_high_rate, args.serve_high_seconds)
     s.close()
 
     e2e = None
@@ -400,6 +412,9 @@ def run_pulda(args, corpus, rank: int, world: int):
                        "device), then per sweep the sweep and a read of its counters to the host, then the "
                        "topics to the host; host clock"}
 
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = batched_probe(args.batch_scale, args.batch_steps, 6, args.coop_min_len)
     if rank != 0:
         return
     peak, peak_kind = peaks()
@@ -458,6 +473,8 @@ def run_pulda(args, corpus, rank: int, world: int):
         "clocks": clk,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "serving": serving,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
 
@@ -588,173 +605,244 @@ def run_sparsity(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args):
-    """32 independent corpora (uneven D, N, K, V) advanced together by one
-    CUDA-graph launch per sweep, against the same 32 chains run one after
-    another through single-chain handles; both must give identical topics."""
+def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, clocks_too: bool = False) -> dict:
+    """32 independent corpora (uneven D, N, K, V; D scaled by `scale`) advanced
+    together by one CUDA-graph launch per sweep, against the same 32 chains
+    run one after another through single-chain handles (each with its own
+    best launch layout); both must give identical topics.  Sweeps 1..warmup
+    (the batch times its tuning candidates there) are not timed."""
     import torch
     import paper_1704_03581_gb300 as P
     from paper_1704_03581_gb300 import synth
 
+    t_gen = time.monotonic()
     specs = synth.batched_specs(32)
-    corpora = [synth.batched_corpus(sp, args.batch_scale) for sp in specs]
+    corpora = synth.batched_corpora(specs, scale)
+    t_gen = time.monotonic() - t_gen
     chains = [dict(w=c.w, doc_off=c.doc_off, K=sp["K"], V=sp["V"], alpha=ALPHA, beta=BETA, seed=sp["seed"])
               for c, sp in zip(corpora, specs)]
     N = sum(c.N for c in corpora)
     stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    K, W = args.steps, max(args.warmup, 6)
-    b = P.Batch(chains, stream=stream.cuda_stream, coop_min_len=args.coop_min_len)
+    K, W = steps, max(warmup, 6)
+    b = P.Batch(chains, stream=stream.cuda_stream, coop_min_len=coop_min_len)
     b.sweep(W)                          # the first sweeps also time the tuning candidates
     b.sync()
     assert b.tuning()[2], "tuning not over after the warm-up sweeps"
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
+    clocks = ClockSampler(torch.cuda.current_device()) if clocks_too else None
+    if clocks:
+        clocks.start()
     e0.record(stream)
     b.sweep(K)
     e1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     b.sync()
     ms_b = e0.elapsed_time(e1)
     zb = [b.z(i) for i in range(len(chains))]
     warps, coop_len, _ = b.tuning()
     b.close()
+    del b
     # the same chains, one after another, one handle each
-    singles = [P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"],
-                         stream=stream.cuda_stream) for c in chains]
-    for s in singles:
-        s.sweep(W)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for s in singles:
-        s.sweep(K)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_s = e0.elapsed_time(e1)
-    same = all(np.array_equal(zb[i], s.z()) for i, s in enumerate(singles))
-    for s in singles:
-        s.close()
+    same = True
+    ms_s = 0.0
+    for i, c in enumerate(chains):
+        s1 = P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"],
+                       stream=stream.cuda_stream)
+        s1.sweep(W)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s1.sweep(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s += e0.elapsed_time(e1)
+        same &= bool(np.array_equal(zb[i], s1.z()))
+        s1.close()
+    return {"workload": f"32 chains, D log-uniform [1e3, 1e5] scaled by {scale}, mean length log-uniform "
+                        f"[50, 2000], V log-uniform [5e3, 5e4], K in {{50, 100, 200, 500}}",
+            "N": N, "timed_sweeps": [W + 1, W + K], "tokens_per_s": N * K / (ms_b / 1000.0),
+            "ms_per_sweep": ms_b / K, "sequential_tokens_per_s": N * K / (ms_s / 1000.0),
+            "sequential_ms_per_sweep": ms_s / K, "speedup_vs_sequential": ms_s / ms_b,
+            "identical_topics": same, "z_warps_tuned": warps, "coop_min_len_tuned": coop_len,
+            "gpu_launches": (6 + (1 if coop_len > 0 else 0)) * K, "generation_s": t_gen, "clocks": clk}
+
+
+def run_batched(args):
+    """The batched-chains form alone (config 4)."""
+    r = batched_probe(args.batch_scale, args.steps, args.warmup, args.coop_min_len, clocks_too=True)
     line = {
         "metric": "batched chains: tokens/s of 32 uneven chains in one graph launch per sweep vs 32 sequential "
                   "single-chain runs",
-        "value": N * K / (ms_b / 1000.0), "unit": "tokens/s", "n_gpus": 1, "steps": K, "warmup": W,
-        "ms_per_step": ms_b / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "value": r["tokens_per_s"], "unit": "tokens/s", "n_gpus": 1, "steps": args.steps, "warmup": r["timed_sweeps"][0] - 1,
+        "ms_per_step": r["ms_per_sweep"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"32 chains, D scaled by {args.batch_scale}", "N": N,
-                   "K": sorted({sp['K'] for sp in specs}), "z_warps_tuned": warps,
-                   "coop_min_len_tuned": coop_len},
-        "sequential": {"value": N * K / (ms_s / 1000.0), "ms_per_step": ms_s / K},
-        "speedup_vs_sequential": ms_s / ms_b,
-        "identical_topics": same,
-        "gpu_launches": (6 + (1 if coop_len > 0 else 0)) * K,
-        "clocks": clk,
+        "config": {"workload": r["workload"], "N": r["N"], "z_warps_tuned": r["z_warps_tuned"],
+                   "coop_min_len_tuned": r["coop_min_len_tuned"]},
+        "sequential": {"value": r["sequential_tokens_per_s"], "ms_per_step": r["sequential_ms_per_sweep"]},
+        "speedup_vs_sequential": r["speedup_vs_sequential"],
+        "identical_topics": r["identical_topics"],
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
     }
     print(json.dumps(line), flush=True)
+
+
+def serve_continuous(model, reqs, arrivals, sweeps: int, slice_tokens: int, check: int = 10) -> dict:
+    """The continuous-batching server fed the requests at their arrival times
+    (seconds from the start); latency = arrival to result on the host.  A
+    sample of `check` requests is re-run alone (pulda_infer) and must give the
+    same topics."""
+    import threading
+    import paper_1704_03581_gb300 as P
+    n = len(arrivals)
+    srv = P.Server(model, token_budget=1 << 25, max_slots=8192, slice_tokens=slice_tokens)
+    done = {}
+    stop = threading.Event()
+
+    def poller():
+        deadline = time.monotonic() + 300.0
+        while (not stop.is_set() or len(done) < n) and time.monotonic() < deadline:
+            for r in srv.poll(max_results=4096, timeout_ms=50):
+                done[r["req_id"]] = r
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.monotonic_ns()
+    i = 0
+    while i < n:
+        now = (time.monotonic_ns() - t0) / 1e9
+        while i < n and arrivals[i] <= now:
+            a, b = int(reqs.doc_off[i]), int(reqs.doc_off[i + 1])
+            srv.submit(i, 7919 * i + 1, reqs.w[a:b], sweeps)
+            i += 1
+        if i < n:
+            time.sleep(max(0.0, min(arrivals[i] - now, 0.001)))
+    stop.set()
+    th.join()
+    t_end = max(r["done_ns"] for r in done.values())
+    lat = np.array([(done[j]["done_ns"] - t0) / 1e6 - arrivals[j] * 1e3 for j in range(n)])
+    toks = int(np.diff(reqs.doc_off)[:n].sum())
+    st = srv.stats()
+    srv.close()
+    same = True
+    for j in list(range(0, n, max(1, n // check)))[:check]:
+        a, b = int(reqs.doc_off[j]), int(reqs.doc_off[j + 1])
+        alone = model.infer(reqs.w[a:b], np.array([0, b - a]), sweeps, seed=7919 * j + 1)
+        same &= bool(np.array_equal(alone, done[j]["z"]))
+    return {"requests": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "docs_per_s": n / ((t_end - t0) / 1e9), "token_sweeps_per_s": toks * sweeps / ((t_end - t0) / 1e9),
+            "identical_to_alone": same,
+            "server": {"launches": st["launches"], "final_slice": st["slice"],
+                       "max_requests_per_launch": st["max_active"],
+                       "kernel_share": st["kernel_ns"] / max(1, t_end - t0)}}
+
+
+def serve_plain(model, reqs, arrivals, sweeps: int, first: int = 0) -> dict:
+    """One request at a time through pulda_infer, requests first..first+n-1
+    arriving at the given times: latency = arrival to result (queueing
+    included); service = the call's own duration."""
+    n = len(arrivals)
+    t0 = time.monotonic_ns()
+    lat, svc = [], []
+    for j in range(n):
+        now = (time.monotonic_ns() - t0) / 1e9
+        if arrivals[j] > now:
+            time.sleep(arrivals[j] - now)
+        a, b = int(reqs.doc_off[first + j]), int(reqs.doc_off[first + j + 1])
+        t1 = time.monotonic_ns()
+        model.infer(reqs.w[a:b], np.array([0, b - a]), sweeps, seed=7919 * (first + j) + 1)
+        t2 = time.monotonic_ns()
+        svc.append((t2 - t1) / 1e6)
+        lat.append((t2 - t0) / 1e6 - arrivals[j] * 1e3)
+    t_all = (time.monotonic_ns() - t0) / 1e9
+    return {"requests": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "service_p50_ms": float(np.percentile(svc, 50)), "service_p99_ms": float(np.percentile(svc, 99)),
+            "service_mean_ms": float(np.mean(svc)), "docs_per_s": n / t_all}
+
+
+def plain_capacity(model, reqs, sweeps: int, n: int = 30) -> float:
+    """Requests per second that one-at-a-time serving completes back to back
+    (the first n requests, no waiting): the highest rate it can sustain."""
+    t0 = time.monotonic()
+    for j in range(n):
+        a, b = int(reqs.doc_off[j]), int(reqs.doc_off[j + 1])
+        model.infer(reqs.w[a:b], np.array([0, b - a]), sweeps, seed=7919 * j + 1)
+    return n / (time.monotonic() - t0)
+
+
+def serving_probe(model, V: int, sweeps: int, slice_tokens: int, low_requests: int, high_rate: float,
+                  high_seconds: float) -> dict:
+    """Both arms on one seeded Poisson trace at half the one-at-a-time arm's
+    measured capacity (a rate it sustains), then the continuous arm at a high
+    rate: p50/p99 latency, service times, requests served per second."""
+    from paper_1704_03581_gb300 import synth
+    n_high = int(high_rate * high_seconds)
+    reqs, _ = synth.serving_requests(low_requests + n_high + 30, V, rate=1.0)
+    cap = plain_capacity(model, reqs, sweeps)
+    rate = max(1.0, round(0.5 * cap))
+    arrivals = np.cumsum(np.random.default_rng(12).exponential(1.0 / rate, size=low_requests))
+    cont_low = serve_continuous(model, reqs, arrivals, sweeps, slice_tokens)
+    plain_low = serve_plain(model, reqs, arrivals, sweeps)
+    hi_arr = np.cumsum(np.random.default_rng(13).exponential(1.0 / high_rate, size=n_high))
+    sub = synth.Corpus(reqs.w[int(reqs.doc_off[low_requests]):],
+                       reqs.doc_off[low_requests:] - reqs.doc_off[low_requests], reqs.V, reqs.name)
+    cont_high = serve_continuous(model, sub, hi_arr, sweeps, slice_tokens)
+    return {"trace": f"Poisson arrivals, lengths lognormal(300, 1.2) clipped to [10, 20000], {sweeps} sweeps per "
+                     f"request, the model's Phi after its sweeps",
+            "one_at_a_time_capacity_docs_per_s": cap,
+            "rate_docs_per_s": rate,
+            "continuous": cont_low, "one_at_a_time": plain_low,
+            "p99_ratio_plain_over_continuous": plain_low["p99_ms"] / cont_low["p99_ms"],
+            "high_rate": dict(cont_high, rate_docs_per_s=high_rate),
+            "throughput_ratio_high_over_plain_capacity": cont_high["docs_per_s"] / cap,
+            "identical_to_alone": bool(cont_low["identical_to_alone"] and cont_high["identical_to_alone"])}
 
 
 def run_serving(args):
     """Fold-in requests (lognormal(300, 1.2) tokens clipped to [10, 20000], 50
     sweeps each) arriving as a Poisson process, served against the large
-    model's Phi: continuous batching vs one request at a time."""
-    import threading
-    import torch
+    model's Phi after 50 sweeps: continuous batching at every rate, and one
+    request at a time at rates below its measured capacity, on the same
+    seeded traces."""
     import paper_1704_03581_gb300 as P
     from paper_1704_03581_gb300 import synth
 
     corpus = synth.large()
     model = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=0,
                       coop_min_len=args.coop_min_len)
-    model.sweep(30)
+    model.sweep(50)
     model.sync()
     rates = [float(r) for r in args.rates.split(",")]
-    n_max = int(max(rates) * args.serve_seconds) + args.plain_requests
+    n_max = int(max(rates) * args.serve_seconds) + args.plain_requests + 30
     reqs, _ = synth.serving_requests(n_max, corpus.V, rate=1.0)
-    lens = np.diff(reqs.doc_off)
-    rng = np.random.default_rng(11)
-    results = []
+    cap = plain_capacity(model, reqs, args.serve_sweeps)
+    plain_rates = [max(1.0, round(f * cap)) for f in (0.25, 0.5, 0.75)]
+    results, plains = [], []
+    for rate in plain_rates:
+        arrivals = np.cumsum(np.random.default_rng(12).exponential(1.0 / rate, size=args.plain_requests))
+        c = serve_continuous(model, reqs, arrivals, args.serve_sweeps, args.slice)
+        p = serve_plain(model, reqs, arrivals, args.serve_sweeps)
+        results.append(dict(c, rate_docs_per_s=rate))
+        plains.append(dict(p, rate_docs_per_s=rate))
     for rate in rates:
         n = int(rate * args.serve_seconds)
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
-        srv = P.Server(model, token_budget=1 << 25, max_slots=8192, slice_tokens=args.slice)
-        done = {}
-        stop = threading.Event()
-
-        def poller():
-            deadline = time.monotonic() + 300.0
-            while (not stop.is_set() or len(done) < n) and time.monotonic() < deadline:
-                for r in srv.poll(max_results=4096, timeout_ms=50):
-                    done[r["req_id"]] = r
-        th = threading.Thread(target=poller)
-        th.start()
-        t0 = time.monotonic_ns()
-        i = 0
-        while i < n:
-            now = (time.monotonic_ns() - t0) / 1e9
-            while i < n and arrivals[i] <= now:
-                a, b = int(reqs.doc_off[i]), int(reqs.doc_off[i + 1])
-                srv.submit(i, 7919 * i + 1, reqs.w[a:b], args.serve_sweeps)
-                i += 1
-            if i < n:
-                time.sleep(max(0.0, min(arrivals[i] - now, 0.001)))
-        stop.set()
-        th.join()
-        t_end = max(r["done_ns"] for r in done.values())
-        lat = np.array([(done[j]["done_ns"] - t0) / 1e6 - arrivals[j] * 1e3 for j in range(n)])
-        toks = int(lens[:n].sum())
-        sst = srv.stats()
-        results.append({"rate_docs_per_s": rate, "requests": n, "p50_ms": float(np.percentile(lat, 50)),
-                        "max_active": int(sst["max_active"]), "launches": int(sst["launches"]),
-                        "gpu_busy_frac": sst["kernel_ns"] / max(1, t_end - t0),
-                        "p99_ms": float(np.percentile(lat, 99)),
-                        "docs_per_s": n / ((t_end - t0) / 1e9),
-                        "token_sweeps_per_s": toks * args.serve_sweeps / ((t_end - t0) / 1e9)})
-        # a sample of requests re-run alone must give the same topics
-        check = list(range(0, n, max(1, n // 20)))[:20]
-        same = True
-        for j in check:
-            a, b = int(reqs.doc_off[j]), int(reqs.doc_off[j + 1])
-            alone = model.infer(reqs.w[a:b], np.array([0, b - a]), args.serve_sweeps, seed=7919 * j + 1)
-            same &= bool(np.array_equal(alone, done[j]["z"]))
-        results[-1]["identical_to_alone"] = same
-        st = srv.stats()
-        results[-1]["server"] = {"launches": st["launches"], "final_slice": st["slice"],
-                                 "max_requests_per_launch": st["max_active"],
-                                 "kernel_share": st["kernel_ns"] / max(1, t_end - t0)}
-        srv.close()
-    # one request at a time (pulda_infer), the first requests at the lowest rate
-    rate = min(rates)
-    m = args.plain_requests
-    arrivals = np.cumsum(np.random.default_rng(12).exponential(1.0 / rate, size=m))
-    t0 = time.monotonic_ns()
-    lat = []
-    for j in range(m):
-        now = (time.monotonic_ns() - t0) / 1e9
-        if arrivals[j] > now:
-            time.sleep(arrivals[j] - now)
-        a, b = int(reqs.doc_off[j]), int(reqs.doc_off[j + 1])
-        model.infer(reqs.w[a:b], np.array([0, b - a]), args.serve_sweeps, seed=7919 * j + 1)
-        lat.append((time.monotonic_ns() - t0) / 1e6 - arrivals[j] * 1e3)
-    t_plain = (time.monotonic_ns() - t0) / 1e9
-    plain = {"rate_docs_per_s": rate, "requests": m, "p50_ms": float(np.percentile(lat, 50)),
-             "p99_ms": float(np.percentile(lat, 99)), "docs_per_s": m / t_plain,
-             "token_sweeps_per_s": int(lens[:m].sum()) * args.serve_sweeps / t_plain}
+        arrivals = np.cumsum(np.random.default_rng(11).exponential(1.0 / rate, size=n))
+        results.append(dict(serve_continuous(model, reqs, arrivals, args.serve_sweeps, args.slice),
+                            rate_docs_per_s=rate))
     model.close()
     low = results[0]
     line = {
         "metric": "serving p50/p99 vs plain (fold-in, 50 sweeps per request, K=1000, V=100000)",
-        "value": low["p99_ms"], "unit": "ms (p99 at the lowest rate)", "n_gpus": 1, "steps": len(rates),
+        "value": low["p99_ms"], "unit": "ms (p99 at the lowest rate)", "n_gpus": 1, "steps": len(results),
         "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic requests, lognormal(300, 1.2) tokens clipped to [10, 20000], Poisson arrivals",
-        "config": {"workload": "fold-in against the large model's Phi after 30 sweeps", "slice_tokens": args.slice,
-                   "coop_min_len": args.coop_min_len,
-                   "sweeps_per_request": args.serve_sweeps},
+        "config": {"workload": "fold-in against the large model's Phi after 50 sweeps", "slice_tokens": args.slice,
+                   "coop_min_len": args.coop_min_len, "sweeps_per_request": args.serve_sweeps},
+        "one_at_a_time_capacity_docs_per_s": cap,
         "continuous_batching": results,
-        "one_at_a_time": plain,
-        "p99_speedup_at_lowest_rate": plain["p99_ms"] / low["p99_ms"],
-        "throughput_speedup": max(r["docs_per_s"] for r in results) / plain["docs_per_s"],
+        "one_at_a_time": plains,
+        "p99_ratio_plain_over_continuous": [p["p99_ms"] / c["p99_ms"] for p, c in zip(plains, results)],
+        "throughput_ratio_vs_plain_capacity": max(r["docs_per_s"] for r in results) / cap,
     }
     print(json.dumps(line), flush=True)
 

@@ -200,8 +200,32 @@ def batched_specs(n_chains: int = 32, seed: int = 4) -> list[dict]:
 
 def batched_corpus(spec: dict, scale: float = 1.0) -> Corpus:
     D = max(1, int(round(spec["D"] * scale)))
-    return zipf_corpus(spec["seed"], spec["K"], spec["V"], D, spec["mean_len"], 0.8, 1.0,
-                       f"chain{spec['seed']} D={D} V={spec['V']} K={spec['K']}")
+    key = f"chain_s{spec['seed']}_D{D}_V{spec['V']}_K{spec['K']}_L{spec['mean_len']:.6g}"
+    return _cached(key, lambda: zipf_corpus(spec["seed"], spec["K"], spec["V"], D, spec["mean_len"], 0.8, 1.0,
+                                            f"chain{spec['seed']} D={D} V={spec['V']} K={spec['K']}"))
+
+
+def _batched_one(args) -> int:
+    spec, scale = args
+    return batched_corpus(spec, scale).N
+
+
+def batched_corpora(specs: list[dict], scale: float = 1.0, workers: int = 0) -> list[Corpus]:
+    """Every chain's corpus, drawn by ``workers`` processes at once (0 = the
+    host's cores, at most one per chain) into the on-disk cache, then loaded.
+    The pool uses the spawn start method, so it is safe after CUDA has started
+    in this process."""
+    import multiprocessing as mp
+    if workers == 0:
+        try:
+            workers = len(os.sched_getaffinity(0))
+        except AttributeError:
+            workers = os.cpu_count() or 1
+    workers = max(1, min(workers, len(specs)))
+    if workers > 1:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map(_batched_one, [(sp, scale) for sp in sorted(specs, key=lambda x: -x["D"] * x["mean_len"])])
+    return [batched_corpus(sp, scale) for sp in specs]
 
 
 def serving_requests(n: int, V: int, seed: int = 5, mean_len: float = 300.0, log_sd: float = 1.2,

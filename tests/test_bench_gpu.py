@@ -27,7 +27,9 @@ def run(*args):
 
 
 def test_sweep_line_has_the_contract():
-    d = run("--docs", "20000", "--burnin", "2", "--steps", "3", "--warmup", "3", "--cpu-docs", "300")
+    d = run("--docs", "20000", "--burnin", "2", "--steps", "3", "--warmup", "3", "--cpu-docs", "300",
+            "--serve-low-requests", "20", "--serve-high-rate", "400", "--serve-high-seconds", "0.5",
+            "--batch-scale", "0.02", "--batch-steps", "2")
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
               "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
         assert k in d, k
@@ -42,6 +44,13 @@ def test_sweep_line_has_the_contract():
     e = d["e2e"]
     assert e["value"] > 0 and e["unit"] == d["unit"] and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
+    sv = d["serving"]
+    assert sv["identical_to_alone"] is True and sv["rate_docs_per_s"] <= sv["one_at_a_time_capacity_docs_per_s"]
+    for arm in ("continuous", "one_at_a_time", "high_rate"):
+        assert sv[arm]["p99_ms"] >= sv[arm]["p50_ms"] > 0 and sv[arm]["docs_per_s"] > 0, arm
+    assert sv["one_at_a_time"]["service_p99_ms"] >= sv["one_at_a_time"]["service_p50_ms"] > 0
+    bt = d["batched"]
+    assert bt["identical_topics"] is True and bt["N"] > 0 and bt["speedup_vs_sequential"] > 0
 
 
 def test_reference_line_has_the_contract():
