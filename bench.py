@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--cpu-docs", type=int, default=20000, help="documents in the CPU oracle's bounded sample")
     ap.add_argument("--ref-docs", type=int, default=5000,
                     help="documents in each step of the reference (oracle) arm's bounded sample")
+    ap.add_argument("--count-path", type=int, default=0, choices=[0, 1],
+                    help="Phi-step count rebuild: 0 shared-memory histograms, 1 radix sort of (word, topic) keys")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving keys of the sweep line")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched keys of the sweep line")
@@ -337,7 +339,8 @@ def run_pulda(args, corpus, rank: int, world: int):
     torch.cuda.set_stream(stream)
     s = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                   stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp,
-                  phi_mode=args.phi_mode, slice_len=args.slice_len, coop_min_len=args.coop_min_len)
+                  phi_mode=args.phi_mode, slice_len=args.slice_len, coop_min_len=args.coop_min_len,
+                  count_path=args.count_path)
     layout = s.z_layout()
     s.sweep(args.burnin + args.warmup)
     s.sync()

@@ -84,7 +84,11 @@ typedef struct {
                                Not used with slice_len > 0; the batched form takes 0 or -1
                                (one warp per document); a server on the handle uses it for
                                requests (0 = requests of at least 1,024 tokens) */
-    int32_t reserved[2];
+    int32_t count_path;     /* how the Phi-step rebuilds n_{k,v}: 0 = shared-memory histogram of
+                               each word's topics (the default, measured faster), 1 = radix sort
+                               of every token's key w K + z and its runs (needs V K < 2^32; the
+                               batched form takes 0); the counts are identical */
+    int32_t reserved;
     /* Device memory.  With alloc set, every device buffer the library takes
      * -- the handle's state in pulda_init, the temporaries of pulda_infer,
      * pulda_get_counts, pulda_get_phi and pulda_log_posterior, a server's

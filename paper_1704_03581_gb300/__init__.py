@@ -48,7 +48,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void
 class Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("zstep_path", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("docs_per_warp", ctypes.c_int32), ("phi_mode", ctypes.c_int32),
-                ("slice_len", ctypes.c_int32), ("coop_min_len", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+                ("slice_len", ctypes.c_int32), ("coop_min_len", ctypes.c_int32), ("count_path", ctypes.c_int32),
+                ("reserved", ctypes.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -160,7 +161,8 @@ def _check(h, status: int):
 
 def pulda_init(word_ids, doc_offsets, K: int, V: int, alpha, beta: float, seed: int, stream=None,
                zstep_path: int = 0, warps_per_block: int = 0, docs_per_warp: int = 0, phi_mode: int = 0,
-               slice_len: int = 0, coop_min_len: int = 0, callbacks: tuple | None = None) -> int:
+               slice_len: int = 0, coop_min_len: int = 0, callbacks: tuple | None = None,
+               count_path: int = 0) -> int:
     """``callbacks`` = allocator_callbacks(...) routes the handle's device memory through them."""
     w = np.ascontiguousarray(word_ids, dtype=np.int32)
     off = np.ascontiguousarray(doc_offsets, dtype=np.int64)
@@ -173,6 +175,7 @@ def pulda_init(word_ids, doc_offsets, K: int, V: int, alpha, beta: float, seed: 
     opt.phi_mode = phi_mode
     opt.slice_len = slice_len
     opt.coop_min_len = coop_min_len
+    opt.count_path = count_path
     if callbacks is not None:
         opt.alloc, opt.free = callbacks
     h = ctypes.c_void_p()
@@ -338,7 +341,8 @@ class Sampler:
 
     def __init__(self, word_ids, doc_offsets, K: int, V: int, alpha=0.1, beta: float = 0.01, seed: int = 0,
                  stream=None, zstep_path: int = 0, warps_per_block: int = 0, docs_per_warp: int = 0,
-                 phi_mode: int = 0, slice_len: int = 0, coop_min_len: int = 0, allocator=None):
+                 phi_mode: int = 0, slice_len: int = 0, coop_min_len: int = 0, allocator=None,
+                 count_path: int = 0):
         """phi_mode 0: Poisson Polya urn (Algorithm 2); 1: Dirichlet Phi (Algorithm 1).
         slice_len > 0: documents longer than it resampled in concurrent stale-count slices (not the paper's).
         coop_min_len: documents at least this long resampled by a whole CTA (0 = automatic, -1 = never);
@@ -352,7 +356,7 @@ class Sampler:
         self.h = None
         self._callbacks = allocator_callbacks(allocator) if allocator is not None else None
         self.h = pulda_init(word_ids, doc_offsets, K, V, alpha, beta, seed, stream, zstep_path, warps_per_block,
-                            docs_per_warp, phi_mode, slice_len, coop_min_len, self._callbacks)
+                            docs_per_warp, phi_mode, slice_len, coop_min_len, self._callbacks, count_path)
 
     def close(self):
         if self.h:

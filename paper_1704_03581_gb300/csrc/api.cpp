@@ -317,6 +317,14 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
         fail(h, PULDA_ERR_INVALID, "slice_len must be >= 0, and slices need docs_per_warp 0 or 1");
         return reject(PULDA_ERR_INVALID);
     }
+    if (h->opt.count_path != 0 && h->opt.count_path != 1) {
+        fail(h, PULDA_ERR_INVALID, "count_path must be 0 (histogram) or 1 (sort)");
+        return reject(PULDA_ERR_INVALID);
+    }
+    if (h->opt.count_path == 1 && static_cast<uint64_t>(K) * static_cast<uint64_t>(V) >= (uint64_t(1) << 32)) {
+        fail(h, PULDA_ERR_INVALID, "count_path 1 needs V K < 2^32 (sort keys are 32-bit)");
+        return reject(PULDA_ERR_INVALID);
+    }
     if (h->opt.coop_min_len < -1) {
         fail(h, PULDA_ERR_INVALID, "coop_min_len must be -1 (never), 0 (auto) or a length");
         return reject(PULDA_ERR_INVALID);
@@ -360,6 +368,7 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
         ALLOC(h->dpart, dir_part_count(V, K));
     }
     ALLOC(h->work, 4); ALLOC(h->stats, ST_TOTAL_SLOTS);
+    if (h->opt.count_path == 1) ALLOC(h->sort_scratch, count_sort_scratch_words(N));
     cudaStream_t st = h->stream;
     CUI(cudaMemcpyAsync(h->w, word_ids, sizeof(int32_t) * N, cudaMemcpyHostToDevice, st));
     std::vector<int64_t> off0(1, 0);
@@ -511,10 +520,17 @@ pulda_status pulda_phi_step(pulda_handle *h) {
     CU(h, cudaMemsetAsync(h->work, 0, sizeof(int), st));
     CU(h, cudaMemsetAsync(h->S, 0, sizeof(unsigned long long) * h->K, st));
     PhiArgs a = phi_args(h);
-    CU(h, run_heavy(h));
+    if (h->opt.count_path == 1) {
+        // n columns by sorting the tokens' (word, topic) keys
+        launch_count_sort(h->w, h->z, h->N, h->K, h->V, h->word_off, h->nst_k, h->nst_n, h->nnz_n, h->sort_scratch,
+                          h->stats, st);
+        a.counted = 1;
+    } else {
+        CU(h, run_heavy(h));
+    }
     if (h->gam) {
         // Algorithm 1: n columns, every Gamma draw, row sums, kept entries
-        launch_phi_counts(a, false, h->phi_grid, st);
+        if (!a.counted) launch_phi_counts(a, false, h->phi_grid, st);
         launch_dir_phi(a, st);
     } else {
         // Algorithm 2: n columns with the Poisson draws, dead rows redrawn

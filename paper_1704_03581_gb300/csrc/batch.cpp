@@ -137,6 +137,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = "batched chains draw the Polya-urn Phi (phi_mode must be 0)";
         return bail(PULDA_ERR_INVALID);
     }
+    if (o.count_path != 0) {
+        b->err = "batched chains rebuild their counts by histogram (count_path must be 0)";
+        return bail(PULDA_ERR_INVALID);
+    }
     if (o.slice_len != 0) {
         b->err = "batched chains resample every document in order (slice_len must be 0)";
         return bail(PULDA_ERR_INVALID);

@@ -56,6 +56,7 @@ struct pulda_handle {
     unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint32_t *bits = nullptr;
     int *work = nullptr;
     unsigned long long *stats = nullptr;
+    uint32_t *sort_scratch = nullptr;   // count_path 1: keys, run ids, scan sums
     int64_t cap = 0;   // capacity of the per-word tables: K * V entries
     // words histogrammed by several CTAs (more than kHeavyWord tokens)
     int32_t *heavy_row = nullptr;

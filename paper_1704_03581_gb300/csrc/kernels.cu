@@ -161,7 +161,15 @@ __device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, 
     const int per = (K + kPhiBlock - 1) / kPhiBlock;     // bins owned by each thread, contiguous
     const int64_t wbeg = a.word_off[v], wend = a.word_off[v + 1];
     const int hrow = a.heavy_row ? a.heavy_row[v] : -1;
-    if (hrow >= 0) {
+    if (a.counted) {
+        // the n column was built by the sort path (countsort.cu)
+        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
+        __syncthreads();
+        const int nn = a.nnz_n[v];
+        for (int j = threadIdx.x; j < nn; j += kPhiBlock)
+            hist[guard_index(a.nst_k[wbeg + j], K, a.stats)] = a.nst_n[wbeg + j];
+        __syncthreads();
+    } else if (hrow >= 0) {
         const uint32_t *hh = a.heavy_hist + static_cast<int64_t>(hrow) * K;
         for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = hh[k]; cbin[k] = 0; }
         __syncthreads();

@@ -136,6 +136,7 @@ struct PhiArgs {
     double *invS;               // [K] 1 / S_k (0 for an all-zero row)
     float *invSf;               // [K] 1 / S_k rounded to float (screening only)
     double *dpart;              // [ceil(V / kDirChunk) * K] chunk sums of the rows
+    int counted;                // the n columns are already built (sort path): read them, do not histogram
 };
 
 // A word with more tokens than this is histogrammed in chunks of kHeavyChunk
@@ -221,6 +222,15 @@ constexpr int kMaxGroupDocLen = 65535;
 void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st);
 int z_groups_blocks_per_sm(int K);
 int phi_counts_blocks_per_sm(int K);
+
+// The count rebuild by sorting (countsort.cu): every token's key w K + z
+// radix-sorted, runs of equal keys -> the n columns (nst_k, nst_n at
+// word_off, nnz_n), bit-identical to the histogram pass's.  Needs V K < 2^32
+// and count_sort_scratch_words(N) words of scratch.
+size_t count_sort_scratch_words(int64_t N);
+void launch_count_sort(const int32_t *w, const int16_t *z, int64_t N, int K, int V, const int64_t *word_off,
+                       uint16_t *nst_k, uint32_t *nst_n, int32_t *nnz_n, uint32_t *scratch,
+                       unsigned long long *stats, cudaStream_t st);
 
 // Dirichlet Phi-step (dirichlet.cu), after the count-only pass has built the
 // n columns: Gamma draws, row sums, and the kept entries staged in cst_k /

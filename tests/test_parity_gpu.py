@@ -213,6 +213,73 @@ def test_large_corpus_sampled_parity():
     s.close()
 
 
+def test_large_corpus_steady_state_parity():
+    """The large workload in the benchmark's launch configuration after 30
+    sweeps on the GPU (the benchmark times sweeps 31-50): Phi is sparser than
+    after the uniform start, the document/column sides and the dense rows fall
+    as in the timed window.  From the GPU's topics after sweep 30 the oracle,
+    on all host cores, recomputes sweep 31 in full: every Poisson count, row
+    sum and table, then the z-step of every document -- all 99M topics and the
+    six z-step counters compared exactly (the 100 longest documents and the
+    cooperative ones among them)."""
+    import paper_1704_03581_gb300 as P
+    c = synth.large()
+    K = 1000
+    T = O.host_threads()
+    s = P.Sampler(c.w, c.doc_off, K, c.V, 0.1, 0.01, seed=0)
+    s.sweep(30)
+    z30 = s.z()
+    assert s.stats()["sweep"] == 30
+    s.phi_step()
+    ctx = O.Ctx(0.01)
+    n = O.count_n(c.w, z30, K, c.V, threads=T)
+    cc, S, dead = O.phi_draw(ctx, n, 0, 31, threads=T)
+    del n
+    tab = O.WordTables(cc, S, np.full(K, 0.1, np.float32), threads=T)
+
+    class _Ch:
+        pass
+    ch = _Ch()
+    ch.K, ch.V, ch.S, ch.c, ch.tables = K, c.V, S, cc, tab
+    compare_tables(s.word_tables(), ch, "large sweep 31")
+    assert s.stats()["dead_rows"] == dead
+    s.z_step()
+    z31, st = s.z(), s.stats()
+    zo, sto = O.z_step(c.doc_off, c.w, z30, tab, 0, 31, threads=T)
+    L = np.diff(c.doc_off)
+    longest = np.argsort(-L, kind="stable")[:100]
+    for d in longest:
+        a, b = int(c.doc_off[d]), int(c.doc_off[d + 1])
+        assert np.array_equal(z31[a:b], zo[a:b]), f"long document {d} ({b - a} tokens) differs"
+    assert not first_mismatch(z31, zo, c.doc_off)
+    assert [st["tokens"], st["a_branch"], st["sum_min"], st["zero_mass"], st["sum_inter"], st["docside"]] == \
+        [int(x) for x in sto]
+    s.close()
+
+
+@pytest.mark.parametrize("K,phi_mode", [(20, 0), (1000, 0), (33, 1)])
+def test_sort_count_path_lockstep(K, phi_mode):
+    """count_path 1: n rebuilt by radix-sorting the tokens' (word, topic)
+    keys instead of per-word histograms; every count, draw, table and topic
+    as the oracle's (empty documents and unused words included; keys of 15,
+    20 and 15 bits: two or three 8-bit digit passes)."""
+    rng = np.random.default_rng(70 + K)
+    lengths = rng.integers(0, 300, size=150)
+    lengths[[2, 4]] = [0, 1]
+    w, off = corpus_from_lengths(rng, lengths, 900)
+    s, _ = lockstep(w, off, K, 900, 0.1, 0.01, seed=K, sweeps=3, check_counts_every=3, phi_mode=phi_mode,
+                    count_path=1)
+    s.close()
+
+
+def test_sort_count_path_small_corpus():
+    """The small corpus (1.9M tokens, K=100): words with up to ~10^5 tokens,
+    the sort's multi-block scans over every tile."""
+    c = synth.small()
+    s, _ = lockstep(c.w, c.doc_off, 100, c.V, 0.1, 0.01, seed=1, sweeps=2, count_path=1)
+    s.close()
+
+
 def test_z_layout_follows_the_measured_rule():
     """Auto takes four documents per warp while one bitmap word per lane
     covers K (K <= 256), one per warp above; 4 forces four (K <= 1024), the
