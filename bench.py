@@ -230,11 +230,18 @@ def issue_roofline(tokens_per_s: float, sm_mhz: float | None) -> dict | None:
 
 
 def z_bytes(tokens: int, sum_min: int, a_branch: int, docs: int) -> int:
-    """Algorithmic HBM bytes of z-steps over `tokens` tokens: per token the
-    word id (4) and topic in/out (2+2), the word's sigma_a (8) and column
-    offset (8); per intersection element one topic id and one fixed-point
-    weight (2+4) -- min(K_d, K_v) of them (complexity theorem); per alias
-    draw one slot (4+2); per document its offset (8)."""
+    """Algorithmic HBM bytes of z-steps over `tokens` tokens, the survey's
+    model of what the method must touch: per token the word id (4), its topic
+    in and out (2+2) and sigma_a of its word (4); per element of the smaller
+    of the document's and the word's nonzero topics one topic id and one
+    weight (2+4) -- min(K_d, K_v) of them (complexity theorem); per alias draw
+    one slot (threshold and topic, padded to 8); per document its offset (8)."""
+    return 12 * tokens + 6 * sum_min + 8 * a_branch + 8 * docs
+
+
+def z_bytes_impl(tokens: int, sum_min: int, a_branch: int, docs: int) -> int:
+    """The same with this implementation's widths: sigma_a held as a 64-bit
+    integer (8) and the column offset read per token (8); an alias slot 4+2."""
     return 24 * tokens + 6 * sum_min + 6 * a_branch + 8 * docs
 
 
@@ -423,6 +430,7 @@ def run_pulda(args, corpus, rank: int, world: int):
     peak, peak_kind = peaks()
     zbytes = z_bytes(tokens, sum_min, a_br, K * corpus.D)
     achieved = zbytes / K / (z_ms / K / 1000.0) / 1e9
+    achieved_impl = z_bytes_impl(tokens, sum_min, a_br, K * corpus.D) / K / (z_ms / K / 1000.0) / 1e9
     traffic = recorded_traffic()
     cpu = None
     if world == 1 and not args.no_cpu:
@@ -467,8 +475,14 @@ def run_pulda(args, corpus, rank: int, world: int):
         "roofline_issue": issue_roofline(K * corpus.N / (z_ms / 1000.0), (clk or {}).get("sm_mhz")),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_z_step", "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                     "algorithmic_bytes_per_launch": zbytes / K},
+                     "kernel": "k_z_step" if layout["docs_per_warp"] == 1 else "k_z_step_grouped",
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                     "algorithmic_bytes_per_launch": zbytes / K,
+                     "bytes_model": "12 B per token + 6 B per min(K_d, K_v) element + 8 B per alias draw + "
+                                    "8 B per document",
+                     "frac_implementation_bytes": achieved_impl / peak,
+                     "implementation_bytes_model": "24 B per token (64-bit sigma_a, column offset) + 6 B per "
+                                                   "min(K_d, K_v) element + 6 B per alias draw + 8 B per document"},
         "gpu_launches": kernels_per_sweep(corpus.w, args.phi_mode, layout,
                                           int(args.slice_len > 0 and np.diff(corpus.doc_off).max() > args.slice_len)) * K,
         "z_kernel": (f"{'four documents' if layout['docs_per_warp'] == 4 else 'one document'} per warp; "
