@@ -71,6 +71,10 @@ def parse():
                     help="documents in each step of the reference (oracle) arm's bounded sample")
     ap.add_argument("--count-path", type=int, default=0, choices=[0, 1],
                     help="Phi-step count rebuild: 0 shared-memory histograms, 1 radix sort of (word, topic) keys")
+    ap.add_argument("--heaps-sizes", type=str, default="1000000,4000000,16000000,64000000",
+                    help="heaps form: corpus sizes (tokens)")
+    ap.add_argument("--heaps-xi", type=float, default=20.0, help="heaps form: V = xi N^psi")
+    ap.add_argument("--heaps-psi", type=float, default=0.5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving keys of the sweep line")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched keys of the sweep line")
@@ -91,7 +95,7 @@ def parse():
     ap.add_argument("--serve-sweeps", type=int, default=50, help="serving: z-sweeps per request")
     ap.add_argument("--plain-requests", type=int, default=150,
                     help="serving: requests the one-at-a-time baseline serves (the first ones, at the lowest rate)")
-    ap.add_argument("--form", choices=["sweep", "batched", "serving", "trace", "sparsity"], default="sweep",
+    ap.add_argument("--form", choices=["sweep", "batched", "serving", "trace", "sparsity", "heaps"], default="sweep",
                     help="sweep: the large corpus (the headline line); batched: 32 uneven chains in one graph "
                          "launch per sweep against 32 sequential single-chain runs; trace: the log posterior "
                          "after every sweep, Polya urn against Dirichlet Phi, on the same corpus and seed; sparsity: "
@@ -424,7 +428,7 @@ def run_pulda(args, corpus, rank: int, world: int):
 
     batched = None
     if world == 1 and not args.no_batched:
-        batched = batched_probe(args.batch_scale, args.batch_steps, 6, args.coop_min_len)
+        batched = batched_probe(args.batch_scale, args.batch_steps, 8, args.coop_min_len)
     if rank != 0:
         return
     peak, peak_kind = peaks()
@@ -640,7 +644,7 @@ def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, cloc
               for c, sp in zip(corpora, specs)]
     N = sum(c.N for c in corpora)
     stream = torch.cuda.Stream()
-    K, W = steps, max(warmup, 6)
+    K, W = steps, max(warmup, 8)
     b = P.Batch(chains, stream=stream.cuda_stream, coop_min_len=coop_min_len)
     b.sweep(W)                          # the first sweeps also time the tuning candidates
     b.sync()
@@ -658,7 +662,7 @@ def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, cloc
     b.sync()
     ms_b = e0.elapsed_time(e1)
     zb = [b.z(i) for i in range(len(chains))]
-    warps, coop_len, _ = b.tuning()
+    warps, coop_len, _, one_launch = b.tuning()
     b.close()
     del b
     # the same chains, one after another, one handle each
@@ -682,7 +686,9 @@ def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, cloc
             "ms_per_sweep": ms_b / K, "sequential_tokens_per_s": N * K / (ms_s / 1000.0),
             "sequential_ms_per_sweep": ms_s / K, "speedup_vs_sequential": ms_s / ms_b,
             "identical_topics": same, "z_warps_tuned": warps, "coop_min_len_tuned": coop_len,
-            "gpu_launches": (6 + (1 if coop_len > 0 else 0)) * K, "generation_s": t_gen, "clocks": clk}
+            "launch_form": "one persistent launch per sweep" if one_launch else "six launches per sweep (a graph)",
+            "gpu_launches": (1 if one_launch else 6 + (1 if coop_len > 0 else 0)) * K, "generation_s": t_gen,
+            "clocks": clk}
 
 
 def run_batched(args):
@@ -701,6 +707,53 @@ def run_batched(args):
         "identical_topics": r["identical_topics"],
         "gpu_launches": r["gpu_launches"],
         "clocks": r["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_heaps(args):
+    """The complexity theorem's setting: corpora growing 4x at a time with a
+    vocabulary that follows Heaps' law (V = xi N^psi), K fixed.  The theorem
+    bounds a sweep's work by sum_i min(K_d, K_v) (the z-step) once the Phi-step,
+    whose work grows with K V, is small beside it: reported per token are the
+    z-step time and min(K_d, K_v), and the Phi-step's share of the sweep."""
+    import torch
+    import paper_1704_03581_gb300 as P
+    from paper_1704_03581_gb300 import synth
+
+    stream = torch.cuda.Stream()
+    rows = []
+    for n in [int(x) for x in args.heaps_sizes.split(",")]:
+        c = synth.heaps_corpus(n, args.heaps_xi, args.heaps_psi)
+        s = P.Sampler(c.w, c.doc_off, K_TOPICS, c.V, ALPHA, BETA, seed=0, stream=stream.cuda_stream)
+        s.sweep(args.burnin)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        mins = []
+        for e in ev:
+            e[0].record(stream)
+            P.pulda_phi_step(s.h)
+            e[1].record(stream)
+            P.pulda_z_step(s.h)
+            e[2].record(stream)
+            st = s.stats()
+            mins.append(st["sum_min"] / max(1, st["tokens"]))
+        phi = float(np.median([e[0].elapsed_time(e[1]) for e in ev]))
+        z = float(np.median([e[1].elapsed_time(e[2]) for e in ev]))
+        rows.append({"N": c.N, "V": c.V, "distinct_words": int(np.count_nonzero(np.bincount(c.w, minlength=c.V))),
+                     "D": c.D, "z_ns_per_token": 1e6 * z / c.N, "phi_ms": phi, "z_ms": z,
+                     "phi_share": phi / (phi + z), "mean_min_kd_kv": float(np.mean(mins)),
+                     "nnz_phi": int(st["nnz_phi"]), "sweep_tokens_per_s": c.N / ((phi + z) / 1000.0)})
+        s.close()
+        print(json.dumps({"progress": f"N={c.N}", "z_ns_per_token": rows[-1]["z_ns_per_token"]}), file=sys.stderr,
+              flush=True)
+    line = {
+        "metric": "sweep cost as the corpus grows with a Heaps'-law vocabulary (complexity theorem)",
+        "value": rows[-1]["sweep_tokens_per_s"], "unit": "tokens/s at the largest size", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.burnin, "higher_is_better": True, "dtype": "int64",
+        "data": "synthetic (LDA generative process, Zipf(1.05) over a V = xi N^psi vocabulary)",
+        "config": {"workload": f"N in {args.heaps_sizes}, xi={args.heaps_xi}, psi={args.heaps_psi}",
+                   "K": K_TOPICS, "alpha": ALPHA, "beta": BETA, "documents": "lognormal(330, 0.8)"},
+        "rows": rows,
     }
     print(json.dumps(line), flush=True)
 
@@ -879,12 +932,12 @@ def main():
     import torch
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if args.form in ("batched", "serving", "trace", "sparsity"):
+    if args.form in ("batched", "serving", "trace", "sparsity", "heaps"):
         from paper_1704_03581_gb300 import build
         build.build()
         if rank == 0:
             {"batched": run_batched, "serving": run_serving, "trace": run_trace,
-             "sparsity": run_sparsity}[args.form](args)
+             "sparsity": run_sparsity, "heaps": run_heaps}[args.form](args)
         return
     if world > 1:
         import torch.distributed as dist

@@ -88,7 +88,11 @@ typedef struct {
                                each word's topics (the default, measured faster), 1 = radix sort
                                of every token's key w K + z and its runs (needs V K < 2^32; the
                                batched form takes 0); the counts are identical */
-    int32_t reserved;
+    int32_t batch_form;     /* batched form only: how a sweep is launched -- 0 = tuned (timed on
+                               the first sweeps with the CTA sizes), 1 = six launches (a CUDA
+                               graph), 2 = one persistent cooperative launch whose phases are
+                               separated by grid barriers (every document one per warp; not
+                               with coop_min_len > 0); the chains' results are identical */
     /* Device memory.  With alloc set, every device buffer the library takes
      * -- the handle's state in pulda_init, the temporaries of pulda_infer,
      * pulda_get_counts, pulda_get_phi and pulda_log_posterior, a server's
@@ -284,8 +288,10 @@ typedef struct pulda_batch pulda_batch;
  * every document on one warp, > 0 sends the documents at least that long (of
  * every chain) to the cooperative z-step, 0 sends those of at least
  * max(256, N / 8000) tokens (N = tokens of all chains), the single-chain rule;
- * docs_per_warp must be 0 or 1.  Tuning times each CTA size on two real sweeps
- * (in order, then in reverse): it ends after sweep 6. */
+ * docs_per_warp must be 0 or 1; batch_form picks the launch form (see
+ * pulda_options).  Tuning times each CTA size on two real sweeps
+ * (in order, then in reverse), together with the one-launch form when no
+ * document goes to cooperative CTAs: it ends after sweep 8 (6 without it). */
 pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains, int32_t n_chains,
                               const pulda_options *opt);
 /* pulda_batch_sweep -- n_sweeps sweeps of every chain (asynchronous, except
@@ -297,9 +303,10 @@ pulda_status pulda_batch_sync(pulda_batch *b);
 pulda_status pulda_batch_get_z(pulda_batch *b, int32_t chain, int16_t *z_host);
 pulda_status pulda_batch_stats(pulda_batch *b, int32_t chain, pulda_sweep_stats *out);
 /* pulda_batch_tuning -- the z-step warps per CTA and the cooperative
- * threshold in use (-1 = none), and whether tuning is over; any pointer may
- * be NULL. */
-pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *coop_min_len, int32_t *tuned);
+ * threshold in use (-1 = none), whether tuning is over, and whether a sweep
+ * is one persistent launch (1) or six launches (0); any pointer may be NULL. */
+pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *coop_min_len, int32_t *tuned,
+                                int32_t *one_launch);
 /* pulda_batch_last_error -- as pulda_last_error; NULL = last failed pulda_batch_init. */
 const char *pulda_batch_last_error(const pulda_batch *b);
 void pulda_batch_free(pulda_batch *b);

@@ -49,7 +49,7 @@ class Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("zstep_path", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("docs_per_warp", ctypes.c_int32), ("phi_mode", ctypes.c_int32),
                 ("slice_len", ctypes.c_int32), ("coop_min_len", ctypes.c_int32), ("count_path", ctypes.c_int32),
-                ("reserved", ctypes.c_int32),
+                ("batch_form", ctypes.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -118,7 +118,7 @@ def lib() -> ctypes.CDLL:
             "pulda_batch_sync": [P],
             "pulda_batch_get_z": [P, i32, P],
             "pulda_batch_stats": [P, i32, P],
-            "pulda_batch_tuning": [P, P, P, P],
+            "pulda_batch_tuning": [P, P, P, P, P],
             "pulda_serve_open": [P, i64, i32, i64, P],
             "pulda_serve_submit": [P, u64, u64, P, i32, i32, P],
             "pulda_serve_poll": [P, P, i32, P, i32],
@@ -434,7 +434,7 @@ def _bcheck(b, status: int):
 
 
 def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0,
-                     callbacks: tuple | None = None):
+                     callbacks: tuple | None = None, batch_form: int = 0):
     """chains: dicts with w, doc_off, K, V, alpha, beta, seed.  coop_min_len: 0 tuned, -1 never, > 0 fixed.
     callbacks = allocator_callbacks(...) routes every device buffer of the batch through them."""
     keep = []
@@ -450,6 +450,7 @@ def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0, 
     opt.stream = stream
     opt.warps_per_block = warps_per_block
     opt.coop_min_len = coop_min_len
+    opt.batch_form = batch_form
     if callbacks is not None:
         opt.alloc, opt.free = callbacks
     b = ctypes.c_void_p()
@@ -476,11 +477,11 @@ def pulda_batch_stats(b, chain: int) -> dict:
     return s.as_dict()
 
 
-def pulda_batch_tuning(b) -> tuple[int, int, bool]:
-    """(z-step warps per CTA, cooperative threshold or -1, tuning over)."""
-    w, c, t = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
-    _bcheck(b, lib().pulda_batch_tuning(b, ctypes.byref(w), ctypes.byref(c), ctypes.byref(t)))
-    return w.value, c.value, bool(t.value)
+def pulda_batch_tuning(b) -> tuple[int, int, bool, bool]:
+    """(z-step warps per CTA, cooperative threshold or -1, tuning over, one persistent launch per sweep)."""
+    w, c, t, o = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    _bcheck(b, lib().pulda_batch_tuning(b, ctypes.byref(w), ctypes.byref(c), ctypes.byref(t), ctypes.byref(o)))
+    return w.value, c.value, bool(t.value), bool(o.value)
 
 
 def pulda_batch_last_error(b) -> str:
@@ -497,11 +498,12 @@ class Batch:
     """Many chains advanced together: ``Batch(chains).sweep(n)``."""
 
     def __init__(self, chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0,
-                 allocator=None):
+                 allocator=None, batch_form: int = 0):
+        """batch_form 0: the launch form is tuned; 1: six launches per sweep; 2: one persistent launch."""
         self.sizes = [int(np.asarray(c["doc_off"])[-1]) for c in chains]
         self.b = None
         self._callbacks = allocator_callbacks(allocator) if allocator is not None else None
-        self.b = pulda_batch_init(chains, stream, warps_per_block, coop_min_len, self._callbacks)
+        self.b = pulda_batch_init(chains, stream, warps_per_block, coop_min_len, self._callbacks, batch_form)
 
     def close(self):
         if self.b:

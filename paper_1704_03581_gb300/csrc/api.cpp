@@ -603,6 +603,7 @@ pulda_status pulda_sync(pulda_handle *h) {
     if (e & ERR_INTERNAL) return fail(h, PULDA_ERR_CUDA, "z-step invariant violated (draw beyond the total mass)");
     if (e & ERR_GAMMA) return fail(h, PULDA_ERR_DEGENERATE, "a Gamma draw was rejected 2^16 times");
     if (e & ERR_BOUNDS) return fail(h, PULDA_ERR_CUDA, "an index read from device data was out of range (checked build)");
+    if (e & ERR_BARRIER) return fail(h, PULDA_ERR_TIMEOUT, "a grid barrier of the one-launch batched sweep waited 2 s");
     return PULDA_OK;
 }
 

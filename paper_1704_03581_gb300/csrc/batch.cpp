@@ -31,13 +31,14 @@ struct pulda_batch {
     // The candidates are timed twice, in order and then in reverse, so the
     // falling cost of the first sweeps after the uniform start does not favour
     // the candidates timed later.
-    struct Cand { int warps; int64_t coop_len; };
+    struct Cand { int warps; int64_t coop_len; bool one_launch; };
     std::vector<Cand> cand;
     std::vector<float> cand_ms;     // summed over the candidate's timed sweeps
     std::vector<int> sched;         // candidate indices still to time in this phase
     size_t sched_pos = 0;
     int phase_first = 0;            // first candidate index of the current phase
     bool tuned = false;
+    bool one_launch = false;        // in use: one persistent launch per sweep
     int64_t coop_len = 0;           // in use
     std::vector<int64_t> dlen;      // document lengths in work-list order (longest first)
     cudaGraph_t graph = nullptr;
@@ -95,10 +96,15 @@ void apply_candidate(pulda_batch *b, const pulda_batch::Cand &c) {
     b->bl.z_grid = b->sms * batch_z_blocks_per_sm(b->bl.kmax, c.warps);
     b->coop_len = c.coop_len;
     b->bl.n_coop = count_coop_items(b, c.coop_len);
+    b->one_launch = c.one_launch;
 }
 
 pulda_status launch_one_sweep(pulda_batch *b) {
-    launch_batch_sweep(b->bl, b->stream);
+    if (b->one_launch) {
+        BCU(b, launch_batch_sweep_persistent(b->bl, b->stream));
+    } else {
+        launch_batch_sweep(b->bl, b->stream);
+    }
     BCU(b, cudaGetLastError());
     return PULDA_OK;
 }
@@ -149,6 +155,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = "coop_min_len must be -1 (never), 0 (tuned) or a length";
         return bail(PULDA_ERR_INVALID);
     }
+    if (o.batch_form < 0 || o.batch_form > 2 || (o.batch_form == 2 && o.coop_min_len > 0)) {
+        b->err = "batch_form must be 0 (tuned), 1 (six launches) or 2 (one launch, without coop_min_len > 0)";
+        return bail(PULDA_ERR_INVALID);
+    }
     if (o.warps_per_block < 0 || o.warps_per_block > kMultiWarps) {
         b->err = "warps_per_block must be in [0, " + std::to_string(kMultiWarps) + "] (got " +
                  std::to_string(o.warps_per_block) + ")";
@@ -185,12 +195,14 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     // per-chain descriptors, reading the sweep counter from device memory
+    GridBarrier *d_bar = nullptr;
     uint32_t *d_sweep = nullptr;
     int *d_work = nullptr;
     PhiArgs *d_phi = nullptr;
     ZArgs *d_z = nullptr;
     cudaError_t ea = cudaSuccess;
-    if ((ea = balloc(b, &d_sweep, 1)) != cudaSuccess || (ea = balloc(b, &d_work, 4)) != cudaSuccess ||
+    if ((ea = balloc(b, &d_bar, 1)) != cudaSuccess || (ea = balloc(b, &d_sweep, 1)) != cudaSuccess ||
+        (ea = balloc(b, &d_work, 4)) != cudaSuccess ||
         (ea = balloc(b, &d_phi, n_chains)) != cudaSuccess || (ea = balloc(b, &d_z, n_chains)) != cudaSuccess) {
         b->err = std::string("device allocation of the batch descriptors failed: ") + cudaGetErrorString(ea);
         return bail(ea == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA);
@@ -248,6 +260,7 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         cudaMemcpyAsync(d_wl, wlist.data(), sizeof(int2) * wlist.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(d_dl, dlist.data(), sizeof(int2) * dlist.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(d_sweep, &zero, sizeof zero, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(d_bar, 0, sizeof(GridBarrier), st) != cudaSuccess ||
         (!heavy.empty() && cudaMemcpyAsync(d_heavy, heavy.data(), sizeof(HeavyChunk) * heavy.size(),
                                            cudaMemcpyHostToDevice, st) != cudaSuccess) ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -269,6 +282,8 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     bl.kmax = kmax;
     bl.phi_grid = b->sms * batch_phi_blocks_per_sm(kmax);
     bl.coop_grid = b->sms * batch_coop_blocks_per_sm(kmax);
+    bl.bar = d_bar;
+    bl.persist_grid = b->sms * batch_persistent_blocks_per_sm(kmax);
     // The cooperative threshold: fixed, none, or the automatic rule of the
     // single-chain z-step over all chains' tokens (documents that would outlast
     // the pass on one warp).  It is not timed: on the 32-chain workload, timing
@@ -280,13 +295,23 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         const int64_t L = std::max<int64_t>(kCoopAutoMin, n_tokens / kCoopAutoDiv + 1);
         if (count_coop_items(b, L) > 0) fixed_coop = L;
     }
-    if (o.warps_per_block > 0) {
-        b->cand.push_back({o.warps_per_block, fixed_coop});
+    // Launch forms: six launches per sweep with a CTA size for the z-step, and
+    // (without cooperative CTAs) one persistent launch; tuned forms are timed.
+    const bool one_ok = bl.persist_grid > 0 && fixed_coop == 0;
+    if (o.batch_form == 2) {
+        if (!one_ok) {
+            b->err = "the one-launch form needs no document on cooperative CTAs and a resident grid";
+            return bail(PULDA_ERR_INVALID);
+        }
+        b->cand.push_back({kMultiWarps, 0, true});
+    } else if (o.warps_per_block > 0) {
+        b->cand.push_back({o.warps_per_block, fixed_coop, false});
     } else {
         for (int w : {2, 4, 8})
-            if (w <= kMultiWarps && z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back({w, fixed_coop});
-        if (b->cand.empty()) b->cand.push_back({1, fixed_coop});
+            if (w <= kMultiWarps && z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back({w, fixed_coop, false});
+        if (b->cand.empty()) b->cand.push_back({1, fixed_coop, false});
     }
+    if (o.batch_form == 0 && o.warps_per_block == 0 && one_ok) b->cand.push_back({kMultiWarps, 0, true});
     if (b->cand.size() == 1) b->tuned = true;
     else schedule_phase(b, 0);
     apply_candidate(b, b->cand.front());
@@ -328,8 +353,11 @@ pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps) {
         } else {
             if (!b->exec) {
                 BCU(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-                launch_batch_sweep(b->bl, b->stream);
+                cudaError_t le = cudaSuccess;
+                if (b->one_launch) le = launch_batch_sweep_persistent(b->bl, b->stream);
+                else launch_batch_sweep(b->bl, b->stream);
                 cudaError_t ce = cudaStreamEndCapture(b->stream, &b->graph);
+                if (le != cudaSuccess) ce = le;
                 if (ce != cudaSuccess) return bfail(b, PULDA_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(ce));
                 BCU(b, cudaGraphInstantiate(&b->exec, b->graph, 0));
             }
@@ -370,9 +398,11 @@ pulda_status pulda_batch_stats(pulda_batch *b, int32_t chain, pulda_sweep_stats 
     return PULDA_OK;
 }
 
-pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *coop_min_len, int32_t *tuned) {
+pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *coop_min_len, int32_t *tuned,
+                                int32_t *one_launch) {
     if (!b) return PULDA_ERR_INVALID;
-    if (z_warps) *z_warps = b->bl.z_warps;
+    if (one_launch) *one_launch = b->one_launch ? 1 : 0;
+    if (z_warps) *z_warps = b->one_launch ? kMultiWarps : b->bl.z_warps;
     if (coop_min_len) *coop_min_len = static_cast<int32_t>(b->coop_len > 0 ? b->coop_len : -1);
     if (tuned) *tuned = b->tuned ? 1 : 0;
     return PULDA_OK;

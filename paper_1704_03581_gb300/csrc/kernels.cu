@@ -170,8 +170,8 @@ __device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, 
             hist[guard_index(a.nst_k[wbeg + j], K, a.stats)] = a.nst_n[wbeg + j];
         __syncthreads();
     } else if (hrow >= 0) {
-        const uint32_t *hh = a.heavy_hist + static_cast<int64_t>(hrow) * K;
-        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = hh[k]; cbin[k] = 0; }
+        const uint32_t *hh = a.heavy_hist + static_cast<int64_t>(hrow) * K;   // from L2: just summed by other CTAs
+        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = __ldcg(&hh[k]); cbin[k] = 0; }
         __syncthreads();
     } else {
         for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
@@ -289,9 +289,7 @@ __global__ void __launch_bounds__(kPhiBlock) k_phi_counts_multi(const PhiArgs *c
 
 // Topic histograms of the most frequent words, one chunk of a word's tokens
 // per CTA, added into the word's row of heavy_hist (zeroed before).
-__global__ void __launch_bounds__(kPhiBlock) k_heavy_hist(const PhiArgs *chains, const HeavyChunk *chunks, int kmax) {
-    extern __shared__ uint32_t hs[];
-    const HeavyChunk c = chunks[blockIdx.x];
+__device__ void heavy_chunk(const PhiArgs *chains, const HeavyChunk &c, uint32_t *hs) {
     const PhiArgs &a = chains[c.chain];
     const int K = a.K;
     for (int k = threadIdx.x; k < K; k += kPhiBlock) hs[k] = 0;
@@ -302,6 +300,12 @@ __global__ void __launch_bounds__(kPhiBlock) k_heavy_hist(const PhiArgs *chains,
     uint32_t *row = a.heavy_hist + static_cast<int64_t>(c.row) * K;
     for (int k = threadIdx.x; k < K; k += kPhiBlock)
         if (hs[k]) atomicAdd(&row[k], hs[k]);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPhiBlock) k_heavy_hist(const PhiArgs *chains, const HeavyChunk *chunks, int kmax) {
+    extern __shared__ uint32_t hs[];
+    heavy_chunk(chains, chunks[blockIdx.x], hs);
     (void)kmax;
 }
 
@@ -322,17 +326,20 @@ constexpr int kFixBlock = 1024;
 // Rows whose Poisson counts summed to zero are redrawn whole (attempt
 // a = 1, 2, ...) until the sum is nonzero: the urn total is Pois+ (the
 // hierarchical representation, Eq. 8).  Accepted rows are inserted into the
-// word columns.  Single block; almost always just checks S and exits.
+// word columns.  One block of BLOCK threads; almost always just checks S and
+// exits.  S is read from L2 (other CTAs of the same launch may have just
+// summed it).
+template <int BLOCK>
 __device__ void phi_fixup_chain(const PhiArgs &a, u64 *red, u64 *s_sum_p) {
     u64 &s_sum = *s_sum_p;
     const uint32_t sweep = sweep_of(a);
     for (int k = 0; k < a.K; ++k) {
-        if (a.S[k] != 0) continue;
+        if (__ldcg(&a.S[k]) != 0) continue;
         if (threadIdx.x == 0) atomicAdd(&a.stats[ST_DEADROWS], 1ull);
         uint32_t att = 1;
         for (; att <= kMaxRedraw; ++att) {
             u64 part = 0;
-            for (int v = threadIdx.x; v < a.V; v += kFixBlock) {
+            for (int v = threadIdx.x; v < a.V; v += BLOCK) {
                 const uint32_t l = lookup_n(a, v, k);
                 uint32_t val = 0;
                 if (l) {
@@ -359,19 +366,19 @@ __device__ void phi_fixup_chain(const PhiArgs &a, u64 *red, u64 *s_sum_p) {
                 }
             }
             __syncthreads();
-            for (int v = threadIdx.x; v < a.V; v += kFixBlock) part += a.rowbuf[v];
+            for (int v = threadIdx.x; v < a.V; v += BLOCK) part += a.rowbuf[v];
             part = warp_sum64(part);
             if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
             __syncthreads();
             if (threadIdx.x == 0) {
                 u64 s = 0;
-                for (int i = 0; i < kFixBlock / 32; ++i) s += red[i];
+                for (int i = 0; i < BLOCK / 32; ++i) s += red[i];
                 s_sum = s;
             }
             __syncthreads();
             const u64 sum = s_sum;
             if (sum > 0) {
-                for (int v = threadIdx.x; v < a.V; v += kFixBlock) {
+                for (int v = threadIdx.x; v < a.V; v += BLOCK) {
                     const uint32_t val = a.rowbuf[v];
                     if (!val) continue;
                     const int64_t base = static_cast<int64_t>(v) * a.K;
@@ -402,20 +409,18 @@ __device__ void phi_fixup_chain(const PhiArgs &a, u64 *red, u64 *s_sum_p) {
 __global__ void __launch_bounds__(kFixBlock) k_phi_fixup(PhiArgs a) {
     __shared__ u64 red[kFixBlock / 32];
     __shared__ u64 s_sum;
-    phi_fixup_chain(a, red, &s_sum);
+    phi_fixup_chain<kFixBlock>(a, red, &s_sum);
 }
 
 // Many chains: one CTA per chain.
 __global__ void __launch_bounds__(kFixBlock) k_phi_fixup_multi(const PhiArgs *chains) {
     __shared__ u64 red[kFixBlock / 32];
     __shared__ u64 s_sum;
-    phi_fixup_chain(chains[blockIdx.x], red, &s_sum);
+    phi_fixup_chain<kFixBlock>(chains[blockIdx.x], red, &s_sum);
 }
 
-// Column offsets of every chain's Phi: one CTA per chain.
-__global__ void k_colptr_scan_multi(const PhiArgs *chains) {
-    const PhiArgs &a = chains[blockIdx.x];
-    __shared__ int64_t part[1024];
+// Column offsets of one chain's Phi by one CTA (part: blockDim entries).
+__device__ void colptr_chain(const PhiArgs &a, int64_t *part) {
     const int t = threadIdx.x;
     const int64_t n = a.V;
     const int64_t per = (n + blockDim.x - 1) / blockDim.x;
@@ -433,6 +438,13 @@ __global__ void k_colptr_scan_multi(const PhiArgs *chains) {
     __syncthreads();
     int64_t run = part[t];
     for (int64_t i = lo; i < hi; ++i) { a.col_ptr[i] = run; run += a.nnz_c[i]; }
+    __syncthreads();
+}
+
+// Column offsets of every chain's Phi: one CTA per chain.
+__global__ void k_colptr_scan_multi(const PhiArgs *chains) {
+    __shared__ int64_t part[1024];
+    colptr_chain(chains[blockIdx.x], part);
 }
 
 // =================================================== Phi-step: tables
@@ -478,7 +490,7 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
         const int k = a.cst_k[src + j];
         // Polya urn: c / S_k; Dirichlet: gamma (1 / S_k), gamma's float bits staged in cst_c
         const double p = a.gam ? __dmul_rn(static_cast<double>(__uint_as_float(a.cst_c[src + j])), a.invS[k])
-                               : __ddiv_rn(static_cast<double>(a.cst_c[src + j]), static_cast<double>(a.S[k]));
+                               : __ddiv_rn(static_cast<double>(a.cst_c[src + j]), static_cast<double>(__ldcg(&a.S[k])));
         a.vose_p[out + j] = static_cast<u64>(__double_as_longlong(p));    // phi, kept for the second pass
         phimax = p > phimax ? p : phimax;
     }
@@ -913,7 +925,7 @@ __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_m
 // ============================================================ batches
 // Start of a sweep of many chains (one CTA): advance the shared sweep counter
 // and clear every chain's row sums, per-sweep counters and the work queues.
-__global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_t *sweep, int *work) {
+__device__ void batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_t *sweep, int *work) {
     if (threadIdx.x == 0) *sweep += 1u;
     if (threadIdx.x < 4) work[threadIdx.x] = 0;
     for (int c = 0; c < n_chains; ++c) {
@@ -923,6 +935,10 @@ __global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_
         if (a.heavy_hist)
             for (int64_t i = threadIdx.x; i < static_cast<int64_t>(a.n_heavy) * a.K; i += blockDim.x) a.heavy_hist[i] = 0;
     }
+}
+
+__global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_t *sweep, int *work) {
+    batch_begin_sweep(chains, n_chains, sweep, work);
 }
 
 // ============================================================ serving
@@ -1134,6 +1150,152 @@ void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
         k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), st>>>(
             b.z, b.z_items, b.n_z_items, b.work + 1, b.kmax);
     }
+}
+
+// ---------------------------------------------------------- one persistent launch per sweep
+// The same sweep of many chains as launch_batch_sweep, in one cooperative
+// launch whose CTAs are all resident: the phases (counter reset, heavy-word
+// histograms, counts and draws, dead-row redraws, column offsets, per-word
+// tables, z-step) run one after another, each over the whole grid, separated
+// by a grid barrier.  Nothing a phase reads was read earlier in the launch by
+// another SM before its writers finished (so no stale L1 line is read), except
+// the row sums and heavy-word histograms, which are read from L2.
+constexpr int kPersistThreads = 256;
+constexpr int kPersistWarps = kPersistThreads / 32;
+#ifndef PULDA_PERSIST_MINB
+#define PULDA_PERSIST_MINB 4
+#endif
+
+// A grid barrier with a bounded wait: thread 0 of each CTA arrives; the last
+// to arrive opens the next generation.  A CTA that has waited 2 s sets
+// ERR_BARRIER in err and returns false (the launch then ends with an error
+// instead of waiting forever).
+__device__ bool grid_barrier(GridBarrier *bar, unsigned nblocks, unsigned long long *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        volatile unsigned *gen = &bar->gen;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (*gen == g) {
+                if (global_ns() - t0 > 2000000000ull) {
+                    atomicOr(err, ERR_BARRIER);
+                    s_ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kPersistThreads, PULDA_PERSIST_MINB) k_batch_sweep_persistent(BatchLaunch b) {
+    extern __shared__ uint32_t psm[];
+    __shared__ int scan_tmp[kPersistThreads / 32 + 1];
+    __shared__ int s_item;
+    __shared__ uint32_t geo[kGeoLen];
+    __shared__ u64 red[kPersistThreads / 32];
+    __shared__ u64 s_sum;
+    __shared__ int64_t part[kPersistThreads];
+    const unsigned nb = gridDim.x;
+    unsigned long long *err = b.phi[0].stats + ST_ERROR;
+    // counters of the sweep
+    if (blockIdx.x == 0) batch_begin_sweep(b.phi, b.n_chains, b.sweep, b.work);
+    if (!grid_barrier(b.bar, nb, err)) return;
+    // histograms of the most frequent words, chunk by chunk
+    for (int c = blockIdx.x; c < b.n_heavy; c += nb) heavy_chunk(b.phi, b.heavy[c], psm);
+    if (!grid_barrier(b.bar, nb, err)) return;
+    // counts and Poisson draws, (chain, word) items most frequent first
+    {
+        int geo_chain = -1;
+        for (;;) {
+            if (threadIdx.x == 0) s_item = atomicAdd(&b.work[0], 1);
+            __syncthreads();
+            const int item = s_item;
+            __syncthreads();
+            if (item >= b.n_phi_items) break;
+            const int2 it = b.phi_items[item];
+            if (it.x != geo_chain) {
+                for (int i = threadIdx.x; i < kGeoLen; i += kPersistThreads) geo[i] = b.phi[it.x].tab.geo[i];
+                geo_chain = it.x;
+                __syncthreads();
+            }
+            phi_word(b.phi[it.x], it.y, true, psm, psm + b.kmax, scan_tmp, geo);
+        }
+    }
+    if (!grid_barrier(b.bar, nb, err)) return;
+    // rows whose draws summed to zero, one CTA per chain
+    for (int c = blockIdx.x; c < b.n_chains; c += nb) phi_fixup_chain<kPersistThreads>(b.phi[c], red, &s_sum);
+    if (!grid_barrier(b.bar, nb, err)) return;
+    for (int c = blockIdx.x; c < b.n_chains; c += nb) colptr_chain(b.phi[c], part);
+    if (!grid_barrier(b.bar, nb, err)) return;
+    // per-word tables, one warp per (chain, word)
+    {
+        const int wid = static_cast<int>(blockIdx.x) * kPersistWarps + (threadIdx.x >> 5);
+        const int nw = static_cast<int>(nb) * kPersistWarps;
+        for (int i = wid; i < b.n_phi_items; i += nw) {
+            const int2 it = b.phi_items[i];
+            phi_tables_word_warp(b.phi[it.x], it.y);
+        }
+    }
+    if (!grid_barrier(b.bar, nb, err)) return;
+    // z-step, one warp per (chain, document), longest first
+    {
+        const int lane = threadIdx.x & 31;
+        uint32_t *m = psm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(b.kmax);
+        u64 *wcnt = z_warp_counters(m, b.kmax);
+        zero_warp_counters(wcnt);
+        for (;;) {
+            int item = 0;
+            if (lane == 0) item = atomicAdd(&b.work[1], 1);
+            item = __shfl_sync(0xFFFFFFFFu, item, 0);
+            if (item >= b.n_z_items) break;
+            const int2 it = b.z_items[item];
+            const ZArgs &a = b.z[it.x];
+            const int64_t s0 = a.doc_off[it.y];
+            DocRun r{a.w + s0, a.z + s0, static_cast<int>(a.doc_off[it.y + 1] - s0), a.seed, a.index_base + s0,
+                     sweep_of(a), 0, a.doc_off[it.y + 1] - s0, 1};
+            z_doc_warp(a, m, r, wcnt);
+            flush_warp_counters(a.stats, wcnt);
+        }
+    }
+}
+
+size_t batch_persistent_smem(int kmax) {
+    return std::max({phi_counts_smem(kmax), sizeof(uint32_t) * static_cast<size_t>(kmax),
+                     z_step_smem(kmax, kPersistWarps)});
+}
+
+int batch_persistent_blocks_per_sm(int kmax) {
+    allow_dynamic_smem(k_batch_sweep_persistent);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep_persistent, kPersistThreads,
+                                                  batch_persistent_smem(kmax));
+    return n;
+}
+
+cudaError_t launch_batch_sweep_persistent(const BatchLaunch &b, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(b.persist_grid));
+    cfg.blockDim = dim3(kPersistThreads);
+    cfg.dynamicSmemBytes = batch_persistent_smem(b.kmax);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_sweep_persistent, b);
 }
 
 int batch_phi_blocks_per_sm(int kmax) {

@@ -70,7 +70,7 @@ enum : int { ST_TOKENS = 0, ST_ABRANCH, ST_SUMMIN, ST_ZEROMASS, ST_DEADROWS, ST_
 // Running totals of the z-step slots live at ST_COUNT + slot and are cleared
 // only at pulda_init.
 constexpr int ST_TOTAL_SLOTS = 2 * ST_COUNT;
-enum : unsigned long long { ERR_DEGENERATE = 1, ERR_INTERNAL = 2, ERR_GAMMA = 4, ERR_BOUNDS = 8 };
+enum : unsigned long long { ERR_DEGENERATE = 1, ERR_INTERNAL = 2, ERR_GAMMA = 4, ERR_BOUNDS = 8, ERR_BARRIER = 16 };
 
 // Fixed tables of one beta, built on the host once.
 struct HostTables {
@@ -247,8 +247,15 @@ size_t log_posterior_scratch_bytes(int64_t D, int V, int K);
 void launch_log_posterior(const int64_t *doc_off, int64_t D, const int16_t *z, int K, const float *alpha, double asum,
                           const PhiArgs &counts, double beta, void *scratch, cudaStream_t st);
 
+// The grid barrier of the one-launch batched sweep (device memory, zeroed).
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+};
+
 // One sweep of many chains: six launches, every kernel over all chains'
-// work items.  Pointers are device memory.
+// work items, or one persistent launch doing the same.  Pointers are device
+// memory.
 struct BatchLaunch {
     const HeavyChunk *heavy;     // heavy-word histogram chunks of every chain
     int n_heavy;
@@ -268,8 +275,16 @@ struct BatchLaunch {
     int n_coop, coop_grid;
     cudaStream_t stream2;
     cudaEvent_t ev_fork, ev_join;
+    // the one-launch form: its grid (all CTAs resident) and barrier
+    int persist_grid;
+    GridBarrier *bar;
 };
 void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st);
+// The same sweep as one cooperative launch (no cooperative z-step: every
+// document one per warp); needs persist_grid <= SMs x
+// batch_persistent_blocks_per_sm(kmax).
+cudaError_t launch_batch_sweep_persistent(const BatchLaunch &b, cudaStream_t st);
+int batch_persistent_blocks_per_sm(int kmax);
 int batch_phi_blocks_per_sm(int kmax);
 int batch_z_blocks_per_sm(int kmax, int warps);
 int batch_coop_blocks_per_sm(int kmax);

@@ -181,6 +181,24 @@ def large(seed: int = 3, D: int = 300_000) -> Corpus:
                                                               f"large D={D} V=100000 K=1000"))
 
 
+def heaps_vocabulary(N: int, xi: float = 20.0, psi: float = 0.5) -> int:
+    """Heaps' law, the assumption of the paper's complexity theorem: a corpus
+    of N tokens has V = xi N^psi distinct words (for most languages
+    5 < xi < 50 and 0.4 < psi < 0.6)."""
+    return max(1, int(round(xi * float(N) ** psi)))
+
+
+def heaps_corpus(N_target: int, xi: float = 20.0, psi: float = 0.5, K: int = 1000, mean_len: float = 330.0,
+                 log_sd: float = 0.8, s: float = 1.05, seed: int = 6) -> Corpus:
+    """A corpus of about N_target tokens whose vocabulary follows Heaps' law:
+    V = heaps_vocabulary(N_target, xi, psi) words with Zipf(s) frequencies,
+    documents lognormal(mean_len, log_sd), drawn from the LDA generative
+    process with K topics (the large corpus's recipe at another size)."""
+    D = max(1, int(round(N_target / mean_len)))
+    V = heaps_vocabulary(N_target, xi, psi)
+    return zipf_corpus(seed, K, V, D, mean_len, log_sd, s, f"heaps N~{N_target} V={V} xi={xi} psi={psi}")
+
+
 def batched_specs(n_chains: int = 32, seed: int = 4) -> list[dict]:
     """Shapes of the batched-chains workload: D log-uniform in [1e3, 1e5],
     mean length log-uniform in [50, 2000], V log-uniform in [5e3, 5e4],

@@ -36,21 +36,28 @@ def make_chains():
     return out
 
 
-@pytest.mark.parametrize("warps,coop", [(0, 0), (4, -1), (4, 64), (2, 1)])
-def test_batch_equals_single_chains(warps, coop):
+@pytest.mark.parametrize("warps,coop,form", [(0, 0, 0), (0, -1, 0), (4, -1, 0), (4, 64, 0), (2, 1, 0),
+                                             (0, -1, 2), (0, 0, 1)])
+def test_batch_equals_single_chains(warps, coop, form):
     """CTA size tuned or fixed; the cooperative z-step by the automatic rule,
-    off, or taking every document of at least 64 tokens / every document."""
+    off, or taking every document of at least 64 tokens / every document; the
+    launch form tuned, one persistent launch per sweep (grid barriers between
+    the phases), or six launches."""
     import paper_1704_03581_gb300 as P
     chains = make_chains()
-    b = P.Batch(chains, warps_per_block=warps, coop_min_len=coop)
+    b = P.Batch(chains, warps_per_block=warps, coop_min_len=coop, batch_form=form)
     b.sweep(4)
-    b.sweep(6)            # tuning sweeps (6), then graph replays across two calls
-    w, coop_len, tuned = b.tuning()
+    b.sweep(8)            # tuning sweeps (up to 8), then graph replays across two calls
+    w, coop_len, tuned, one = b.tuning()
     assert tuned and w in (2, 4, 8)
     assert coop_len == (coop if coop != 0 else coop_len) and (coop_len == -1 or coop_len >= 1)
+    if form == 2:
+        assert one
+    if form == 1 or coop > 0:
+        assert not one
     for i, c in enumerate(chains):
         s = P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"])
-        s.sweep(10)
+        s.sweep(12)
         assert np.array_equal(b.z(i), s.z()), f"chain {i} differs from its single-chain run"
         sb, ss = b.stats(i), s.stats()
         for k in ("tokens", "a_branch", "sum_min", "zero_mass", "dead_rows", "nnz_phi", "sweep",

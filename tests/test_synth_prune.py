@@ -57,3 +57,17 @@ def test_tfidf_and_top_words():
     kept = sorted(range(c.V), key=lambda v: (-s[v], v))[:10]
     ids = {v: i for i, v in enumerate(sorted(kept))}
     assert p.V == 10 and _docs(p) == [[ids[v] for v in doc if v in ids] for doc in docs]
+
+
+def test_heaps_corpus_follows_the_law():
+    """V = xi N^psi words (the complexity theorem's assumption), about the
+    target number of tokens, and no word id outside the vocabulary."""
+    from paper_1704_03581_gb300 import synth
+    assert synth.heaps_vocabulary(10 ** 6, 20.0, 0.5) == 20000
+    assert synth.heaps_vocabulary(4 * 10 ** 6, 20.0, 0.5) == 40000
+    c = synth.heaps_corpus(250_000, 20.0, 0.5, K=50)
+    assert c.V == synth.heaps_vocabulary(250_000, 20.0, 0.5) == 10000
+    assert abs(c.N - 250_000) / 250_000 < 0.1
+    assert c.w.min() >= 0 and c.w.max() < c.V
+    d = synth.heaps_corpus(1_000_000, 20.0, 0.5, K=50)
+    assert d.V == 2 * c.V                     # 4x the tokens, 2x the words at psi = 1/2
