@@ -307,6 +307,16 @@ pulda_status pulda_batch_stats(pulda_batch *b, int32_t chain, pulda_sweep_stats 
  * is one persistent launch (1) or six launches (0); any pointer may be NULL. */
 pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *coop_min_len, int32_t *tuned,
                                 int32_t *one_launch);
+/* pulda_barrier_selftest -- checks the grid barrier of the one-launch
+ * batched sweep on the current device (the paper has no counterpart: this is
+ * failure detection of the launch form).  `blocks` CTAs (at most one per SM,
+ * so all resident) pass `rounds` barriers that expect blocks + missing
+ * arrivals; *passed receives the barriers passed, summed over the CTAs.  With
+ * missing = 0 every barrier opens: PULDA_OK, *passed = blocks * rounds.  With
+ * missing > 0 none does: each CTA gives up after waiting 2 s and the call
+ * returns PULDA_ERR_TIMEOUT, the device still usable.  Synchronous; allocates
+ * 256 bytes.  Errors: PULDA_ERR_INVALID (sizes), PULDA_ERR_OOM, PULDA_ERR_CUDA. */
+pulda_status pulda_barrier_selftest(int32_t blocks, int32_t missing, int32_t rounds, int32_t *passed);
 /* pulda_batch_last_error -- as pulda_last_error; NULL = last failed pulda_batch_init. */
 const char *pulda_batch_last_error(const pulda_batch *b);
 void pulda_batch_free(pulda_batch *b);

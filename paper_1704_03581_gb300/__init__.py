@@ -28,7 +28,7 @@ EXPORTED = ["pulda_init", "pulda_sweep", "pulda_phi_step", "pulda_z_step", "puld
             "pulda_get_word_tables",
             "pulda_infer", "pulda_infer_noalloc", "pulda_stats", "pulda_z_layout", "pulda_last_error", "pulda_free",
             "pulda_batch_init", "pulda_batch_sweep", "pulda_batch_sync", "pulda_batch_get_z", "pulda_batch_stats",
-            "pulda_batch_tuning", "pulda_batch_last_error", "pulda_batch_free",
+            "pulda_batch_tuning", "pulda_batch_last_error", "pulda_batch_free", "pulda_barrier_selftest",
             "pulda_serve_open", "pulda_serve_submit", "pulda_serve_poll", "pulda_serve_pending", "pulda_serve_stats",
             "pulda_serve_close"]
 
@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
             "pulda_batch_get_z": [P, i32, P],
             "pulda_batch_stats": [P, i32, P],
             "pulda_batch_tuning": [P, P, P, P, P],
+            "pulda_barrier_selftest": [i32, i32, i32, P],
             "pulda_serve_open": [P, i64, i32, i64, P],
             "pulda_serve_submit": [P, u64, u64, P, i32, i32, P],
             "pulda_serve_poll": [P, P, i32, P, i32],
@@ -482,6 +483,13 @@ def pulda_batch_tuning(b) -> tuple[int, int, bool, bool]:
     w, c, t, o = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
     _bcheck(b, lib().pulda_batch_tuning(b, ctypes.byref(w), ctypes.byref(c), ctypes.byref(t), ctypes.byref(o)))
     return w.value, c.value, bool(t.value), bool(o.value)
+
+
+def pulda_barrier_selftest(blocks: int, missing: int, rounds: int = 4) -> tuple[int, int]:
+    """(status, barriers passed) of the one-launch form's grid barrier self-test."""
+    n = ctypes.c_int32(0)
+    st = lib().pulda_barrier_selftest(blocks, missing, rounds, ctypes.byref(n))
+    return st, n.value
 
 
 def pulda_batch_last_error(b) -> str:

@@ -430,4 +430,31 @@ void pulda_batch_free(pulda_batch *b) {
     delete b;
 }
 
+pulda_status pulda_barrier_selftest(int32_t blocks, int32_t missing, int32_t rounds, int32_t *passed) {
+    if (blocks < 1 || missing < 0 || rounds < 1 || !passed) return PULDA_ERR_INVALID;
+    int sms = 1, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks > sms) return PULDA_ERR_INVALID;            // one 32-thread CTA per SM at most: all resident
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, 256) != cudaSuccess) return PULDA_ERR_OOM;
+    auto *bar = static_cast<GridBarrier *>(mem);
+    auto *err = reinterpret_cast<unsigned long long *>(static_cast<char *>(mem) + 64);
+    auto *cnt = reinterpret_cast<unsigned *>(static_cast<char *>(mem) + 128);
+    pulda_status st = PULDA_OK;
+    unsigned long long herr = 0;
+    unsigned hcnt = 0;
+    if (cudaMemset(mem, 0, 256) != cudaSuccess ||
+        launch_barrier_selftest(bar, blocks, missing, rounds, err, cnt, nullptr) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&herr, err, sizeof herr, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&hcnt, cnt, sizeof hcnt, cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = PULDA_ERR_CUDA;
+    else if (herr & ERR_BARRIER)
+        st = PULDA_ERR_TIMEOUT;
+    cudaFree(mem);
+    *passed = static_cast<int32_t>(hcnt);
+    return st;
+}
+
 }  // extern "C"

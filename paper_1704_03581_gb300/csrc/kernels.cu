@@ -1199,6 +1199,16 @@ __device__ bool grid_barrier(GridBarrier *bar, unsigned nblocks, unsigned long l
     return s_ok != 0;
 }
 
+// The barrier alone, for its self-test: every CTA passes `rounds` barriers
+// that expect `expect` arrivals.
+__global__ void k_barrier_selftest(GridBarrier *bar, unsigned expect, int rounds, unsigned long long *err,
+                                   unsigned *passed) {
+    for (int r = 0; r < rounds; ++r) {
+        if (!grid_barrier(bar, expect, err)) return;
+        if (threadIdx.x == 0) atomicAdd(passed, 1u);
+    }
+}
+
 __global__ void __launch_bounds__(kPersistThreads, PULDA_PERSIST_MINB) k_batch_sweep_persistent(BatchLaunch b) {
     extern __shared__ uint32_t psm[];
     __shared__ int scan_tmp[kPersistThreads / 32 + 1];
@@ -1269,6 +1279,21 @@ __global__ void __launch_bounds__(kPersistThreads, PULDA_PERSIST_MINB) k_batch_s
             flush_warp_counters(a.stats, wcnt);
         }
     }
+}
+
+cudaError_t launch_barrier_selftest(GridBarrier *bar, int blocks, int missing, int rounds, unsigned long long *err,
+                                    unsigned *passed, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(blocks));
+    cfg.blockDim = dim3(32);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_barrier_selftest, bar, static_cast<unsigned>(blocks + missing), rounds, err,
+                              passed);
 }
 
 size_t batch_persistent_smem(int kmax) {

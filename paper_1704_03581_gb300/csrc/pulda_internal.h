@@ -285,6 +285,10 @@ void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st);
 // batch_persistent_blocks_per_sm(kmax).
 cudaError_t launch_batch_sweep_persistent(const BatchLaunch &b, cudaStream_t st);
 int batch_persistent_blocks_per_sm(int kmax);
+// The grid barrier's self-test: `blocks` resident CTAs pass `rounds`
+// barriers that expect blocks + missing arrivals.
+cudaError_t launch_barrier_selftest(GridBarrier *bar, int blocks, int missing, int rounds, unsigned long long *err,
+                                    unsigned *passed, cudaStream_t st);
 int batch_phi_blocks_per_sm(int kmax);
 int batch_z_blocks_per_sm(int kmax, int warps);
 int batch_coop_blocks_per_sm(int kmax);

@@ -86,3 +86,23 @@ def test_batch_reports_the_failing_chain():
     with pytest.raises(P.PuldaError) as e:
         P.Batch(chains)
     assert "chain 2" in str(e.value)
+
+
+def test_grid_barrier_times_out_and_reports():
+    """The one-launch form's grid barrier: with every CTA present each of the
+    rounds opens; with one CTA short none does, every CTA gives up after its
+    2 s limit and the host reads PULDA_ERR_TIMEOUT -- and the device still
+    runs a batch afterwards."""
+    import time
+    import paper_1704_03581_gb300 as P
+    st, n = P.pulda_barrier_selftest(64, 0, 5)
+    assert st == 0 and n == 64 * 5
+    t0 = time.monotonic()
+    st, n = P.pulda_barrier_selftest(64, 1, 5)
+    dt = time.monotonic() - t0
+    assert st == -4 and n == 0 and 1.5 < dt < 30.0
+    chains = make_chains()[:3]
+    b = P.Batch(chains, batch_form=2)
+    b.sweep(3)
+    b.sync()
+    b.close()
