@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--cpu-docs", type=int, default=20000, help="documents in the CPU oracle's bounded sample")
     ap.add_argument("--ref-docs", type=int, default=5000,
                     help="documents in each step of the reference (oracle) arm's bounded sample")
+    ap.add_argument("--K", type=int, default=1000,
+                    help="topics the sampler runs with (the corpora are drawn with K=1000 topics either way)")
     ap.add_argument("--count-path", type=int, default=0, choices=[0, 1],
                     help="Phi-step count rebuild: 0 shared-memory histograms, 1 radix sort of (word, topic) keys")
     ap.add_argument("--heaps-sizes", type=str, default="1000000,4000000,16000000,64000000",
@@ -326,7 +328,7 @@ def run_reference(args, corpus):
         tot_tok += sub.N
     v = tot_tok / tot_t
     sample = (f"one oracle sweep per step over the first {sub.D} documents ({sub.N} tokens) of the large "
-              f"corpus, K=1000, on {cores} host threads (results equal the single-threaded oracle's)")
+              f"corpus, K={K_TOPICS}, on {cores} host threads (results equal the single-threaded oracle's)")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "tokens/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * tot_t / steps, "higher_is_better": True,
@@ -445,7 +447,7 @@ def run_pulda(args, corpus, rank: int, world: int):
         cpu = {"value": n_tok / dt, "unit": "tokens/s", "cores": cores, "kind": "oracle",
                "cpu_model": cpu_model(),
                "sample": f"one oracle sweep (Phi-step + z-step) over the first {min(args.cpu_docs, corpus.D)} "
-                         f"documents ({n_tok} tokens) of the same corpus, K=1000, on {cores} host threads "
+                         f"documents ({n_tok} tokens) of the same corpus, K={K_TOPICS}, on {cores} host threads "
                          f"(words and documents split over the threads; results equal the single-threaded "
                          f"oracle's)",
                "single_core": {"value": n1 / dt1, "unit": "tokens/s", "cores": 1}}
@@ -918,7 +920,9 @@ def run_serving(args):
 
 
 def main():
+    global K_TOPICS
     args = parse()
+    K_TOPICS = args.K
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     from paper_1704_03581_gb300 import synth

@@ -102,7 +102,7 @@ def test_grid_barrier_times_out_and_reports():
     dt = time.monotonic() - t0
     assert st == -4 and n == 0 and 1.5 < dt < 30.0
     chains = make_chains()[:3]
-    b = P.Batch(chains, batch_form=2)
+    b = P.Batch(chains, coop_min_len=-1, batch_form=2)
     b.sweep(3)
     b.sync()
     b.close()
