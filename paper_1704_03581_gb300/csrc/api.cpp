@@ -440,7 +440,11 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
         }
         if (n > 0) {
             ALLOC(h->dense_slot, V);
-            ALLOC(h->qdense, static_cast<size_t>(n) * K);
+            // 32 words before the first row: the document side's empty gather
+            // slots read the word before a lane's segment (times a zero count)
+            ALLOC(h->qdense, static_cast<size_t>(n) * K + 32);
+            CUI(cudaMemsetAsync(h->qdense, 0, 32 * sizeof(uint32_t), st));
+            h->qdense += 32;
             CUI(cudaMemcpyAsync(h->dense_slot, slot.data(), sizeof(int32_t) * V, cudaMemcpyHostToDevice, st));
             CUI(cudaStreamSynchronize(st));
         }

@@ -626,26 +626,36 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
     const int K = a.K;
     const bool use_bm = a.bits != nullptr && a.path != 1;
     if (r.len == 0 || r.budget <= 0) return;
+    // Topic k's count is mt[mi(k)]: lane l's 32 topics sit at mt[33 l + b],
+    // and the word before each lane's slots is a zero (m[0] for lane 0 and
+    // for the lanes without topics, the gap word after lane l - 1's slots
+    // otherwise), so an empty gather slot (bit -1) reads a zero count.
+    uint32_t *mt = m + 1;
+    const bool own = lane < a.KW;
+    const int mo = own ? 33 * lane : 0;      // this lane's count slots (document side)
+    const int qo = own ? 32 * lane : 0;      // and its segment of a dense q row
     if (m0) {
-        for (int k = lane; k < K; k += 32) m[mi(k)] = m0[k];
+        for (int k = lane; k < K; k += 32) mt[mi(k)] = m0[k];
     } else {
-        for (int k = lane; k < K; k += 32) m[mi(k)] = 0;
+        for (int k = lane; k < K; k += 32) mt[mi(k)] = 0;
         __syncwarp();
-        for (int i = lane; i < r.len; i += 32) atomicAdd(&m[mi(guard_index(r.z[i], K, a.stats))], 1u);
+        for (int i = lane; i < r.len; i += 32) atomicAdd(&mt[mi(guard_index(r.z[i], K, a.stats))], 1u);
     }
+    if (lane == 0) m[0] = 0;
+    if (lane + 1 < a.KW) mt[33 * lane + 32] = 0;
     __syncwarp();
     uint32_t mbits = 0;
     int kd = 0;
     if (use_bm) {
         for (int g = 0; g < a.KW; ++g) {
             const int k = g * 32 + lane;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k < K && m[mi(k)] > 0);
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k < K && mt[mi(k)] > 0);
             if (lane == g) mbits = bal;
             kd += __popc(bal);
         }
     } else {
         int cnt = 0;
-        for (int k = lane; k < K; k += 32) cnt += m[mi(k)] > 0;
+        for (int k = lane; k < K; k += 32) cnt += mt[mi(k)] > 0;
 #pragma unroll
         for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
         kd = cnt;
@@ -683,7 +693,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
         // the word's bitmap row (32 topics per lane)
         const uint32_t *bits = a.bits;
         uint32_t bm_next = 0u;
-        if (use_bm && lane < a.KW) bm_next = bits[static_cast<int64_t>(rec[1].z) * a.KWp + lane];
+        if (use_bm && own) bm_next = bits[static_cast<int64_t>(rec[1].z) * a.KWp + lane];
         // this block's counters, in 32 bits (at most 32 tokens of K <= 16384),
         // added to the warp's 64-bit counters once per block
         // (c_min: sum of min(K_d, K_v), the same in every lane; c_cnt: tokens
@@ -700,12 +710,12 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             const u64 U = (static_cast<u64>(t1.x) << 32) | t1.y;
             const int ka = static_cast<int>(t0.y >> 16);
             const uint32_t bm = bm_next;
-            if (use_bm && tt + 1 < cnt && lane < a.KW)   // the next token's bitmap word, fetched while this one is drawn
+            if (use_bm && tt + 1 < cnt && own)   // the next token's bitmap word, fetched while this one is drawn
                 bm_next = bits[static_cast<int64_t>(rec[2 * tt + 3].z) * a.KWp + lane];
             // remove token i: m^{-i}
-            const uint32_t old = m[mi(kold)];
+            const uint32_t old = mt[mi(kold)];
             __syncwarp();
-            if (lane == 0) m[mi(kold)] = old - 1;
+            if (lane == 0) mt[mi(kold)] = old - 1;
             if (old == 1) {
                 --kd;
                 if (use_bm && lane == (kold >> 5)) mbits &= ~(1u << (kold & 31));
@@ -721,33 +731,33 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             const uint32_t drow = drow_of[tt];
             const bool docside = use_bm && drow != 0xFFFFFFFFu && (a.path == 2 || kd * kDocRatio < n_w * 16);
             const uint32_t *qcol = a.q + col;
-            const uint32_t *qd = a.qdense + drow + lane * 32;
+            const uint32_t *qd = a.qdense + drow + qo;
+            const uint32_t *ml = mt + mo;
             // per-lane partial sums of q m, in ascending topic order across lanes
             u64 acc = 0;
             uint32_t qv[kGather];
             int bp[kGather];
-            uint32_t rest = 0;         // docside: bits beyond the first kGather
+            uint32_t rest = 0;         // docside: bits below the first kGather
             int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
             if (docside) {
+                // The lane's bits from the highest down; a slot past the last
+                // bit gets b = -1 and q = 0 (no load), and its count read hits
+                // the zero before the lane's slots.
                 uint32_t rem = bm & mbits;
 #pragma unroll
                 for (int t = 0; t < kGather; ++t) {
-                    bp[t] = -1;
-                    qv[t] = 0;
-                    if (rem) {
-                        const int b = __ffs(rem) - 1;
-                        rem &= rem - 1;
-                        bp[t] = b;
-                        qv[t] = qd[b];
-                    }
+                    const int b = msb_or_neg1(rem);
+                    rem ^= bit_or_zero(b);
+                    bp[t] = b;
+                    qv[t] = b >= 0 ? qd[b] : 0u;
                 }
 #pragma unroll
-                for (int t = 0; t < kGather; ++t)
-                    if (bp[t] >= 0) acc += static_cast<u64>(qv[t]) * m[lane * 33 + bp[t]];
+                for (int t = 0; t < kGather; ++t) acc += static_cast<u64>(qv[t]) * ml[bp[t]];
                 rest = rem;
-                for (uint32_t bb = rest; bb; bb &= bb - 1) {
-                    const int b = __ffs(bb) - 1;
-                    acc += static_cast<u64>(qd[b]) * m[lane * 33 + b];
+                for (uint32_t bb = rest; bb;) {
+                    const int b = msb_or_neg1(bb);
+                    bb ^= bit_or_zero(b);
+                    acc += static_cast<u64>(qd[b]) * ml[b];
                 }
             } else {
                 seg = (n_w + 31) >> 5;
@@ -756,7 +766,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
                 unsigned nj = 0;
 #pragma unroll 4
                 for (int j = seg0; j < seg1; ++j) {
-                    const uint32_t mk = m[mi(guard_index(a.topic[col + j], K, a.stats))];
+                    const uint32_t mk = mt[mi(guard_index(a.topic[col + j], K, a.stats))];
                     acc += static_cast<u64>(qcol[j]) * mk;
                     if (!use_bm) nj += mk != 0u;
                 }
@@ -781,26 +791,29 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
                         const int L = __ffs(bal) - 1;
                         int f = -1;
                         if (lane == L) {
-                            u64 run = incl - acc;
                             if (docside) {
+                                // walk down from the lane's inclusive sum: the
+                                // topic whose term takes it to rb or below
+                                u64 run = incl;
 #pragma unroll
                                 for (int t = 0; t < kGather; ++t) {
-                                    if (f >= 0 || bp[t] < 0) break;
-                                    {
-                                        run += static_cast<u64>(qv[t]) * m[lane * 33 + bp[t]];
-                                        if (rb < run) f = lane * 32 + bp[t];
+                                    if (f < 0) {
+                                        run -= static_cast<u64>(qv[t]) * ml[bp[t]];
+                                        if (rb >= run) f = 32 * lane + bp[t];
                                     }
                                 }
-                                for (uint32_t bb = rest; f < 0 && bb; bb &= bb - 1) {
-                                    const int b = __ffs(bb) - 1;
-                                    run += static_cast<u64>(qd[b]) * m[lane * 33 + b];
-                                    if (rb < run) f = lane * 32 + b;
+                                for (uint32_t bb = rest; f < 0 && bb;) {
+                                    const int b = msb_or_neg1(bb);
+                                    bb ^= bit_or_zero(b);
+                                    run -= static_cast<u64>(qd[b]) * ml[b];
+                                    if (rb >= run) f = 32 * lane + b;
                                 }
                             } else {
+                                u64 run = incl - acc;
                                 const int seg1 = min(seg0 + seg, n_w);
                                 for (int j = seg0; j < seg1; ++j) {
                                     const int k = guard_index(a.topic[col + j], K, a.stats);
-                                    run += static_cast<u64>(qcol[j]) * m[mi(k)];
+                                    run += static_cast<u64>(qcol[j]) * mt[mi(k)];
                                     if (rb < run) { f = k; break; }
                                 }
                             }
@@ -816,9 +829,9 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             }
             // add token i back with its new topic
             knew = guard_index(knew, K, a.stats);
-            const uint32_t old2 = m[mi(knew)];
+            const uint32_t old2 = mt[mi(knew)];
             __syncwarp();
-            if (lane == 0) m[mi(knew)] = old2 + 1;
+            if (lane == 0) mt[mi(knew)] = old2 + 1;
             if (old2 == 0) {
                 ++kd;
                 if (use_bm && lane == (knew >> 5)) mbits |= 1u << (knew & 31);

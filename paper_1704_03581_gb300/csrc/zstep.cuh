@@ -31,6 +31,20 @@ __device__ __forceinline__ u64 warp_incl_scan64(u64 v) {
     return v;
 }
 
+// Position of the highest set bit of x, or -1 when x is 0 (PTX bfind).
+__device__ __forceinline__ int msb_or_neg1(uint32_t x) {
+    int b;
+    asm("bfind.u32 %0, %1;" : "=r"(b) : "r"(x));
+    return b;
+}
+
+// 1 << b for b in [0, 32), 0 for b = -1 (PTX shl clamps the shift at 32).
+__device__ __forceinline__ uint32_t bit_or_zero(int b) {
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(1u), "r"(b));
+    return r;
+}
+
 __device__ __forceinline__ uint32_t sweep_of(const ZArgs &a) { return a.sweep_ptr ? *a.sweep_ptr : a.sweep; }
 
 // The document side (for a word with a dense q row) is iterated when
