@@ -587,7 +587,7 @@ __global__ void k_phi_tables_multi(const PhiArgs *chains, const int2 *items, int
 // Entries of the document-side intersection each lane gathers with
 // independent loads before consuming them.
 #ifndef PULDA_ZGATHER
-#define PULDA_ZGATHER 6
+#define PULDA_ZGATHER 7
 #endif
 // 4-warp CTAs, 8 per SM: the kernel fits 64 registers without
 // spilling and 32 warps share each SM (issue slots are what bound it; fewer
@@ -713,14 +713,22 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             if (use_bm && tt + 1 < cnt && own)   // the next token's bitmap word, fetched while this one is drawn
                 bm_next = bits[static_cast<int64_t>(rec[2 * tt + 3].z) * a.KWp + lane];
             // remove token i: m^{-i}
-            const uint32_t old = mt[mi(kold)];
-            __syncwarp();
-            if (lane == 0) mt[mi(kold)] = old - 1;
-            if (old == 1) {
-                --kd;
-                if (use_bm && lane == (kold >> 5)) mbits &= ~(1u << (kold & 31));
+            if (use_bm) {
+                // the lane owning topic kold updates its count and bitmap word
+                // (lanes read only their own counts on the document side)
+                const bool me = lane == (kold >> 5);
+                const uint32_t old = me ? mt[mi(kold)] : 0u;
+                if (me) mt[mi(kold)] = old - 1;
+                const bool died = me && old == 1;
+                if (died) mbits &= ~(1u << (kold & 31));
+                kd -= __any_sync(0xFFFFFFFFu, died) ? 1 : 0;
+            } else {
+                const uint32_t old = mt[mi(kold)];
+                __syncwarp();
+                if (lane == 0) mt[mi(kold)] = old - 1;
+                if (old == 1) --kd;
+                __syncwarp();
             }
-            __syncwarp();
             c_min += static_cast<uint32_t>(kd < n_w ? kd : n_w);
             c_cnt += kd < n_w ? 1u : 0u;
             // |J| from the bitmaps on either side (the column side's topics with
@@ -760,6 +768,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
                     acc += static_cast<u64>(qd[b]) * ml[b];
                 }
             } else {
+                __syncwarp();   // the column side reads every lane's counts
                 seg = (n_w + 31) >> 5;
                 seg0 = seg * lane;
                 const int seg1 = min(seg0 + seg, n_w);
@@ -793,14 +802,14 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
                         if (lane == L) {
                             if (docside) {
                                 // walk down from the lane's inclusive sum: the
-                                // topic whose term takes it to rb or below
+                                // topic whose term takes it to rb or below (an
+                                // empty slot adds nothing, so the walk stops at
+                                // one of the lane's bits)
                                 u64 run = incl;
 #pragma unroll
                                 for (int t = 0; t < kGather; ++t) {
-                                    if (f < 0) {
-                                        run -= static_cast<u64>(qv[t]) * ml[bp[t]];
-                                        if (rb >= run) f = 32 * lane + bp[t];
-                                    }
+                                    run -= static_cast<u64>(qv[t]) * ml[bp[t]];
+                                    if (rb >= run) { f = 32 * lane + bp[t]; break; }
                                 }
                                 for (uint32_t bb = rest; f < 0 && bb;) {
                                     const int b = msb_or_neg1(bb);
@@ -829,14 +838,20 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             }
             // add token i back with its new topic
             knew = guard_index(knew, K, a.stats);
-            const uint32_t old2 = mt[mi(knew)];
-            __syncwarp();
-            if (lane == 0) mt[mi(knew)] = old2 + 1;
-            if (old2 == 0) {
-                ++kd;
-                if (use_bm && lane == (knew >> 5)) mbits |= 1u << (knew & 31);
+            if (use_bm) {
+                const bool me = lane == (knew >> 5);
+                const uint32_t old2 = me ? mt[mi(knew)] : 0u;
+                if (me) mt[mi(knew)] = old2 + 1;
+                const bool born = me && old2 == 0;
+                if (born) mbits |= 1u << (knew & 31);
+                kd += __any_sync(0xFFFFFFFFu, born) ? 1 : 0;
+            } else {
+                const uint32_t old2 = mt[mi(knew)];
+                __syncwarp();
+                if (lane == 0) mt[mi(knew)] = old2 + 1;
+                if (old2 == 0) ++kd;
+                __syncwarp();
             }
-            __syncwarp();
             if (lane == tt) znew = knew;
         }
         if (valid) rs.z[i] = static_cast<int16_t>(znew);
