@@ -146,43 +146,77 @@ __global__ void k_word_scatter(int64_t N, const int32_t *w, const int64_t *word_
 
 // ======================================================== Phi-step: counts
 constexpr int kPhiBlock = 256;
+#ifndef PULDA_PHI_COUNT_BLOCK
+#define PULDA_PHI_COUNT_BLOCK 128
+#endif
+constexpr int kPhiCountBlock = PULDA_PHI_COUNT_BLOCK;
 
 // Sweep counter of a chain: from device memory when the launch is replayed
 // from a CUDA graph (one graph serves every sweep), else the launch value.
 __device__ __forceinline__ uint32_t sweep_of(const PhiArgs &a) { return a.sweep_ptr ? *a.sweep_ptr : a.sweep; }
 
-// One word v of one chain, by the whole CTA: histogram of the word's topics
-// -> n_{.,v}; compacted n column; when `draw`, the Poisson draws c_{.,v},
-// the compacted c column, and S_k += c_{k,v}.  hist/cbin hold K entries each.
+// Adds the topics of the word-ordered tokens [b, e) into hist (shared
+// memory), by a CTA of BLOCK threads.  The topics are gathered through perm
+// from all over the corpus, so each thread issues kHistBatch of those loads
+// before the first atomic: latency, not bandwidth, bounds a loop that waits
+// on one at a time.
+#ifndef PULDA_HIST_BATCH
+#define PULDA_HIST_BATCH 8
+#endif
+constexpr int kHistBatch = PULDA_HIST_BATCH;
+template <int BLOCK>
+__device__ __forceinline__ void hist_tokens(const PhiArgs &a, int64_t b, int64_t e, uint32_t *hist) {
+    const int K = a.K;
+    int64_t t = b + threadIdx.x;
+    for (; t + (kHistBatch - 1) * BLOCK < e; t += kHistBatch * BLOCK) {
+        int32_t p[kHistBatch];
+        int zz[kHistBatch];
+#pragma unroll
+        for (int u = 0; u < kHistBatch; ++u) p[u] = a.perm[t + u * BLOCK];
+#pragma unroll
+        for (int u = 0; u < kHistBatch; ++u) zz[u] = a.z[p[u]];
+#pragma unroll
+        for (int u = 0; u < kHistBatch; ++u) atomicAdd(&hist[guard_index(zz[u], K, a.stats)], 1u);
+    }
+    for (; t < e; t += BLOCK) atomicAdd(&hist[guard_index(a.z[a.perm[t]], K, a.stats)], 1u);
+}
+
+// One word v of one chain, by the whole CTA of BLOCK threads: histogram of
+// the word's topics -> n_{.,v}; compacted n column; when `draw`, the Poisson
+// draws c_{.,v}, the compacted c column, and S_k += c_{k,v}.  hist/cbin hold
+// K entries each.  With `next` set, thread 0 takes the CTA's next work item
+// from `work` once every thread is past reading the current one; the last
+// barrier publishes it.
+template <int BLOCK>
 __device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, uint32_t *cbin, int *scan_tmp,
-                         const uint32_t *geo) {
+                         const uint32_t *geo, int *next = nullptr, int *work = nullptr) {
     const int K = a.K;
     const uint32_t sweep = sweep_of(a);
-    const int per = (K + kPhiBlock - 1) / kPhiBlock;     // bins owned by each thread, contiguous
+    const int per = (K + BLOCK - 1) / BLOCK;     // bins owned by each thread, contiguous
     const int64_t wbeg = a.word_off[v], wend = a.word_off[v + 1];
     const int hrow = a.heavy_row ? a.heavy_row[v] : -1;
     if (a.counted) {
         // the n column was built by the sort path (countsort.cu)
-        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
+        for (int k = threadIdx.x; k < K; k += BLOCK) { hist[k] = 0; cbin[k] = 0; }
         __syncthreads();
         const int nn = a.nnz_n[v];
-        for (int j = threadIdx.x; j < nn; j += kPhiBlock)
+        for (int j = threadIdx.x; j < nn; j += BLOCK)
             hist[guard_index(a.nst_k[wbeg + j], K, a.stats)] = a.nst_n[wbeg + j];
         __syncthreads();
     } else if (hrow >= 0) {
         const uint32_t *hh = a.heavy_hist + static_cast<int64_t>(hrow) * K;   // from L2: just summed by other CTAs
-        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = __ldcg(&hh[k]); cbin[k] = 0; }
+        for (int k = threadIdx.x; k < K; k += BLOCK) { hist[k] = __ldcg(&hh[k]); cbin[k] = 0; }
         __syncthreads();
     } else {
-        for (int k = threadIdx.x; k < K; k += kPhiBlock) { hist[k] = 0; cbin[k] = 0; }
+        for (int k = threadIdx.x; k < K; k += BLOCK) { hist[k] = 0; cbin[k] = 0; }
         __syncthreads();
-        for (int64_t t = wbeg + threadIdx.x; t < wend; t += kPhiBlock)
-            atomicAdd(&hist[guard_index(a.z[a.perm[t]], K, a.stats)], 1u);
+        hist_tokens<BLOCK>(a, wbeg, wend, hist);
         __syncthreads();
     }
+    if (next && threadIdx.x == 0) *next = atomicAdd(work, 1);
     if (do_draw) {
         // entries with n_{k,v} = l >= 1: c ~ Pois(beta + l)
-        for (int k = threadIdx.x; k < K; k += kPhiBlock) {
+        for (int k = threadIdx.x; k < K; k += BLOCK) {
             const uint32_t l = hist[k];
             if (l) {
                 const U4 x = draw(a.seed, static_cast<uint32_t>(v), static_cast<uint32_t>(k), sweep, TAG_POIS, 0);
@@ -221,9 +255,12 @@ __device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, 
     const int k0 = threadIdx.x * per, k1 = min(K, k0 + per);
     int cn = 0, cc = 0;
     for (int k = k0; k < k1; ++k) { cn += hist[k] != 0; cc += cbin[k] != 0; }
-    int tn, tc;
-    int pn = block_excl_scan<kPhiBlock>(cn, scan_tmp, tn);
-    int pc = block_excl_scan<kPhiBlock>(cc, scan_tmp, tc);
+    // one scan of both counts, n's in the low and c's in the high 16 bits
+    // (each at most K <= 16384)
+    int tboth;
+    const int pboth = block_excl_scan<BLOCK>(cn | (cc << 16), scan_tmp, tboth);
+    int pn = pboth & 0xFFFF, pc = pboth >> 16;
+    const int tn = tboth & 0xFFFF, tc = tboth >> 16;
     for (int k = k0; k < k1; ++k) {
         const uint32_t l = hist[k];
         if (l) { a.nst_k[wbeg + pn] = static_cast<uint16_t>(k); a.nst_n[wbeg + pn] = l; ++pn; }
@@ -245,20 +282,21 @@ __device__ void phi_word(const PhiArgs &a, int v, bool do_draw, uint32_t *hist, 
     __syncthreads();
 }
 
-// One chain's words, dynamically scheduled, most frequent first.
-__global__ void __launch_bounds__(kPhiBlock) k_phi_counts(PhiArgs a, bool do_draw) {
+// One chain's words, dynamically scheduled, most frequent first; CTAs of
+// kPhiCountBlock threads (more words in flight per SM than 256-thread CTAs;
+// a word's barriers then wait on fewer warps).
+__global__ void __launch_bounds__(kPhiCountBlock) k_phi_counts(PhiArgs a, bool do_draw) {
     extern __shared__ uint32_t sm[];
-    __shared__ int scan_tmp[kPhiBlock / 32 + 1];
+    __shared__ int scan_tmp[kPhiCountBlock / 32 + 1];
     __shared__ int s_item;
     __shared__ uint32_t geo[kGeoLen];
-    for (int i = threadIdx.x; i < kGeoLen; i += kPhiBlock) geo[i] = a.tab.geo[i];
+    for (int i = threadIdx.x; i < kGeoLen; i += kPhiCountBlock) geo[i] = a.tab.geo[i];
+    if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
+        const int item = s_item;      // published by the barrier above, then by phi_word's last one
         if (item >= a.V) break;
-        phi_word(a, a.word_order[item], do_draw, sm, sm + a.K, scan_tmp, geo);
+        phi_word<kPhiCountBlock>(a, a.word_order[item], do_draw, sm, sm + a.K, scan_tmp, geo, &s_item, a.work);
     }
 }
 
@@ -283,7 +321,7 @@ __global__ void __launch_bounds__(kPhiBlock) k_phi_counts_multi(const PhiArgs *c
             geo_chain = it.x;
             __syncthreads();
         }
-        phi_word(chains[it.x], it.y, do_draw, sm, sm + kmax, scan_tmp, geo);
+        phi_word<kPhiBlock>(chains[it.x], it.y, do_draw, sm, sm + kmax, scan_tmp, geo);
     }
 }
 
@@ -294,8 +332,7 @@ __device__ void heavy_chunk(const PhiArgs *chains, const HeavyChunk &c, uint32_t
     const int K = a.K;
     for (int k = threadIdx.x; k < K; k += kPhiBlock) hs[k] = 0;
     __syncthreads();
-    for (int64_t t = c.begin + threadIdx.x; t < c.end; t += kPhiBlock)
-        atomicAdd(&hs[guard_index(a.z[a.perm[t]], K, a.stats)], 1u);
+    hist_tokens<kPhiBlock>(a, c.begin, c.end, hs);
     __syncthreads();
     uint32_t *row = a.heavy_hist + static_cast<int64_t>(c.row) * K;
     for (int k = threadIdx.x; k < K; k += kPhiBlock)
@@ -333,6 +370,10 @@ template <int BLOCK>
 __device__ void phi_fixup_chain(const PhiArgs &a, u64 *red, u64 *s_sum_p) {
     u64 &s_sum = *s_sum_p;
     const uint32_t sweep = sweep_of(a);
+    // almost always no row is dead: one parallel look at S first
+    int dead = 0;
+    for (int k = threadIdx.x; k < a.K; k += BLOCK) dead |= __ldcg(&a.S[k]) == 0 ? 1 : 0;
+    if (!__syncthreads_or(dead)) return;
     for (int k = 0; k < a.K; ++k) {
         if (__ldcg(&a.S[k]) != 0) continue;
         if (threadIdx.x == 0) atomicAdd(&a.stats[ST_DEADROWS], 1ull);
@@ -1103,13 +1144,13 @@ int phi_counts_blocks_per_sm(int K) {
     const size_t smem = phi_counts_smem(K);
     allow_dynamic_smem(k_phi_counts);
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_phi_counts, kPhiBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_phi_counts, kPhiCountBlock, smem);
     return b > 0 ? b : 1;
 }
 
 void launch_phi_counts(const PhiArgs &a, bool draw, int grid, cudaStream_t st) {
     const size_t smem = phi_counts_smem(a.K);
-    k_phi_counts<<<grid, kPhiBlock, smem, st>>>(a, draw);
+    k_phi_counts<<<grid, kPhiCountBlock, smem, st>>>(a, draw);
 }
 
 void launch_phi_fixup(const PhiArgs &a, cudaStream_t st) { k_phi_fixup<<<1, kFixBlock, 0, st>>>(a); }
@@ -1268,7 +1309,7 @@ __global__ void __launch_bounds__(kPersistThreads, PULDA_PERSIST_MINB) k_batch_s
                 geo_chain = it.x;
                 __syncthreads();
             }
-            phi_word(b.phi[it.x], it.y, true, psm, psm + b.kmax, scan_tmp, geo);
+            phi_word<kPersistThreads>(b.phi[it.x], it.y, true, psm, psm + b.kmax, scan_tmp, geo);
         }
     }
     if (!grid_barrier(b.bar, nb, err)) return;
