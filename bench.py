@@ -218,6 +218,32 @@ def recorded_traffic() -> float | None:
     return float(rec["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in rec else None
 
 
+def count_word_topic_pairs(w: np.ndarray, z: np.ndarray, K: int) -> int:
+    """nnz(n): distinct (word, topic) pairs among the tokens, counted on the
+    device (a sort of the N keys w K + z; a diagnostic, outside any timing)."""
+    import torch
+    key = torch.from_numpy(np.ascontiguousarray(w)).cuda().long() * K + torch.from_numpy(
+        np.ascontiguousarray(z)).cuda().long()
+    n = int(torch.unique(key).numel())
+    del key
+    return n
+
+
+def phi_bytes(N: int, nnz_phi: int, nnz_n: int) -> float:
+    """Algorithmic bytes of one Phi-step with its count rebuild: each token's
+    topic gathered through the word-major permutation (4 + 2 B), 14 B per
+    nonzero of Phi (its draw and tables) and 8 B per nonzero of n."""
+    return 6.0 * N + 14.0 * nnz_phi + 8.0 * nnz_n
+
+
+def phi_roofline(ms_per_sweep: float, N: int, nnz_phi: int, nnz_n: int, peak: float) -> dict:
+    b = phi_bytes(N, nnz_phi, nnz_n)
+    achieved = b / (ms_per_sweep / 1000.0) / 1e9
+    return {"ms_per_sweep": ms_per_sweep, "nnz_phi": nnz_phi, "nnz_n": nnz_n, "bytes_per_sweep": b,
+            "bytes_model": "6 B per token + 14 B per nonzero of Phi + 8 B per nonzero of n",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}
+
+
 def issue_roofline(tokens_per_s: float, sm_mhz: float | None) -> dict | None:
     """The z-step against the SMs' instruction-issue rate: warp instructions per
     token (ncu, one full-size launch) times the measured tokens/s, against
@@ -393,6 +419,7 @@ def run_pulda(args, corpus, rank: int, world: int):
     docside = st1["cum_docside"] - st0["cum_docside"]
     assert tokens == K * corpus.N, (tokens, K * corpus.N)
     nnz_phi = st1["nnz_phi"]
+    nnz_n = count_word_topic_pairs(corpus.w, s.z(), K_TOPICS)   # for the Phi-step's byte model, not timed
     torch.cuda.synchronize()
     t_lp = time.perf_counter()
     lp_after = s.log_posterior()[0]
@@ -475,7 +502,12 @@ def run_pulda(args, corpus, rank: int, world: int):
         "z_step": {"tokens_per_s": K * corpus.N / (z_ms / 1000.0), "ms_per_launch": z_ms / K,
                    "mean_min_kd_kv": sum_min / tokens, "mean_intersection": sum_int / tokens,
                    "docside_frac": docside / tokens, "a_branch_frac": a_br / tokens},
-        "phi_step": {"ms_per_sweep": phi_ms / K, "nnz_phi": nnz_phi},
+        "phi_step": phi_roofline(phi_ms / K, corpus.N, nnz_phi, nnz_n, peak),
+        "sweep_roofline": {"bytes_per_sweep": zbytes / K + phi_bytes(corpus.N, nnz_phi, nnz_n),
+                           "achieved": (zbytes / K + phi_bytes(corpus.N, nnz_phi, nnz_n)) / (ms_max / K / 1000.0) / 1e9,
+                           "peak": peak, "unit": "GB/s",
+                           "frac": (zbytes / K + phi_bytes(corpus.N, nnz_phi, nnz_n)) / (ms_max / K / 1000.0) / 1e9 / peak,
+                           "bytes_model": "the z-step's and the Phi-step's algorithmic bytes over the whole sweep"},
         "log_posterior": {"before_timed": lp_before, "after_timed": lp_after, "ms_per_evaluation": lp_ms,
                           "note": "collapsed log p(w, z | alpha, beta), not timed"},
         "roofline_issue": issue_roofline(K * corpus.N / (z_ms / 1000.0), (clk or {}).get("sm_mhz")),

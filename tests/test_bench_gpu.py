@@ -39,6 +39,13 @@ def test_sweep_line_has_the_contract():
     r = d["roofline"]
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] > 0
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    ph = d["phi_step"]
+    assert 0 < ph["nnz_n"] <= d["config"]["N"] and ph["nnz_phi"] > 0
+    assert ph["bytes_per_sweep"] == pytest.approx(6 * d["config"]["N"] + 14 * ph["nnz_phi"] + 8 * ph["nnz_n"])
+    assert ph["frac"] == pytest.approx(ph["achieved"] / ph["peak"])
+    sw = d["sweep_roofline"]
+    assert sw["bytes_per_sweep"] == pytest.approx(r["algorithmic_bytes_per_launch"] + ph["bytes_per_sweep"])
+    assert sw["frac"] == pytest.approx(sw["achieved"] / sw["peak"])
     c = d["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0 and c["sample"]
     e = d["e2e"]
