@@ -57,12 +57,12 @@ typedef struct {
                                column, 2 = iterate the document's topics whenever K <= 1024 */
     int32_t warps_per_block;/* warp-per-document z-step: warps per CTA, 1..4; 0 = 4, halved
                                while the CTA's shared memory would pass 160 KB */
-    int32_t docs_per_warp;  /* z-step documents per warp: 0 = auto (four when K <= 256 and
-                               every word's dense q row fits 2 GB -- measured faster there --
-                               else one), 1 = one, 4 = four (needs K <= 1024; falls back to
-                               one when the rows do not fit; documents longer than 65,535
-                               tokens still go one per warp, the longest to CTAs as
-                               coop_min_len says); results are identical */
+    int32_t docs_per_warp;  /* z-step documents per warp: 0 = auto (one: measured faster at
+                               every K), 1 = one, 4 = four (needs K <= 1024; falls back to
+                               one when every word's dense q row does not fit 2 GB;
+                               documents longer than 65,535 tokens still go one per warp,
+                               the longest to CTAs as coop_min_len says); results are
+                               identical */
     int32_t phi_mode;       /* 0 = Poisson Polya urn (Algorithm 2), 1 = Dirichlet (Algorithm 1:
                                phi_k ~ Dir(n_k + beta) through Gamma draws, entries below 2^-24
                                of their column's maximum dropped); the batched form takes 0 only */

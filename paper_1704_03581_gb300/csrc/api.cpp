@@ -490,13 +490,14 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     // Four documents per warp share each token's fixed work (record, count
     // updates, scan, draw) over four tokens, but each lane then walks four
     // times the topics, so a token's intersection costs more and a document's
-    // tokens advance about 3x slower.  Measured (sweep ms, 100,000 documents of
-    // the large corpus): K = 100 15.5 vs 17.4 one per warp, K = 300 19.3 vs
-    // 16.1, K = 1000 26.0 vs 15.4.  So auto takes four per warp only while one
-    // bitmap word per lane covers K (K <= 256).  Needs every word's dense q
-    // row; not with slices or the column-only path.
+    // tokens advance about 3x slower.  Once the one-warp z-step spread small K
+    // over 8 or 16 topics per lane it was faster at every K measured (z-step
+    // ms, 100,000 documents of the large corpus: K = 50 10.2 vs 14.7 four per
+    // warp, K = 100 10.4 vs 13.7, K = 200 10.3 vs 13.0), so auto takes one
+    // per warp and four per warp is an explicit choice.  That needs every
+    // word's dense q row; not with slices or the column-only path.
     const bool groups_ok = K <= kMaxKBitmap && h->n_dense == V && h->opt.slice_len == 0 && h->opt.zstep_path != 1;
-    h->z_groups = groups_ok && (h->opt.docs_per_warp == 4 || (h->opt.docs_per_warp == 0 && h->KWp == 8));
+    h->z_groups = groups_ok && h->opt.docs_per_warp == 4;
     h->n_long = count_long(doc_offsets, dord);
     h->n_coop = count_coop(h, doc_offsets, dord, N);
     h->coop_grid = sms * z_coop_blocks_per_sm(K);

@@ -637,11 +637,35 @@ __global__ void k_phi_tables_multi(const PhiArgs *chains, const int2 *items, int
 #define PULDA_ZMINBLOCKS 8
 #endif
 constexpr int kGather = PULDA_ZGATHER;
+// the same for 16 and 8 topics per lane (fewer bits per lane)
+#ifndef PULDA_ZGATHER16
+#define PULDA_ZGATHER16 5
+#endif
+#ifndef PULDA_ZGATHER8
+#define PULDA_ZGATHER8 4
+#endif
+constexpr int kGather16 = PULDA_ZGATHER16;
+constexpr int kGather8 = PULDA_ZGATHER8;
+
+// Index of topic k's count with TPL topics per lane: a gap word after each
+// lane's TPL slots keeps the lanes' slots on distinct banks.
+template <int TPL>
+__device__ __forceinline__ int mit(int k) { return k + k / TPL; }
+
+// This lane's TPL bits of a bitmap row starting at word `row`.
+template <int TPL>
+__device__ __forceinline__ uint32_t lane_bits(const uint32_t *bits, int64_t row, int lane) {
+    if (TPL == 32) return bits[row + lane];
+    const uint32_t w = bits[row + (lane * TPL >> 5)];
+    return (w >> ((lane * TPL) & 31)) & ((1u << (TPL & 31)) - 1u);
+}
 
 // One warp per document (dynamically scheduled, longest first).  m_d lives
 // in shared memory as a dense count array; for K <= 1024 each lane also holds
-// the 32-topic bitmap word of m_d's nonzero topics it owns, and the document
-// side reads q of topic 32 lane + b from the word's dense q row.  Tokens are
+// the bits of m_d's nonzero topics among the TPL it owns (TPL = 32, or 16 /
+// 8 for K <= 512 / 256, so that small K still spreads over the warp), and
+// the document side reads q of topic TPL lane + b from the word's dense q
+// row.  Tokens are
 // visited in position order: remove token i (m^{-i}), compute
 // sigma_b = sum_k q_{k,v} m_k over the smaller of {k : m_k > 0} and
 // {k : phi_{k,v} > 0} (complexity theorem), draw r = floor(u (A + 2^16 B)),
@@ -662,41 +686,55 @@ constexpr int kGather = PULDA_ZGATHER;
 // With m0 set, m starts from those K counts (a slice of a longer document,
 // from the document's counts at the start of the pass) instead of the run's
 // own topics.
-__device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, const uint32_t *m0 = nullptr) {
+template <int TPL>
+__device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, const uint32_t *m0) {
+    static_assert(TPL == 8 || TPL == 16 || TPL == 32, "8, 16 or 32 topics per lane");
+    constexpr int G = TPL == 32 ? kGather : TPL == 16 ? kGather16 : kGather8;
     const int lane = threadIdx.x & 31;
     const int K = a.K;
     const bool use_bm = a.bits != nullptr && a.path != 1;
     if (r.len == 0 || r.budget <= 0) return;
-    // Topic k's count is mt[mi(k)]: lane l's 32 topics sit at mt[33 l + b],
-    // and the word before each lane's slots is a zero (m[0] for lane 0 and
-    // for the lanes without topics, the gap word after lane l - 1's slots
-    // otherwise), so an empty gather slot (bit -1) reads a zero count.
+    // Lane l owns topics [TPL l, TPL l + TPL) (TPL = 32, 16 or 8 by K, so
+    // that small K spreads over more lanes).  Topic k's count is
+    // mt[mit<TPL>(k)]: lane l's topics sit at mt[(TPL + 1) l + b], and the word
+    // before each lane's slots is a zero (m[0] for lane 0 and for the lanes
+    // without topics, the gap word after lane l - 1's slots otherwise), so an
+    // empty gather slot (bit -1) reads a zero count.
     uint32_t *mt = m + 1;
-    const bool own = lane < a.KW;
-    const int mo = own ? 33 * lane : 0;      // this lane's count slots (document side)
-    const int qo = own ? 32 * lane : 0;      // and its segment of a dense q row
+    const int nl = TPL == 32 ? a.KW : (K + TPL - 1) / TPL;      // lanes that own topics
+    const bool own = lane < nl;
+    const int mo = own ? (TPL + 1) * lane : 0;   // this lane's count slots (document side)
+    const int qo = own ? TPL * lane : 0;         // and its segment of a dense q row
     if (m0) {
-        for (int k = lane; k < K; k += 32) mt[mi(k)] = m0[k];
+        for (int k = lane; k < K; k += 32) mt[mit<TPL>(k)] = m0[k];
     } else {
-        for (int k = lane; k < K; k += 32) mt[mi(k)] = 0;
+        for (int k = lane; k < K; k += 32) mt[mit<TPL>(k)] = 0;
         __syncwarp();
-        for (int i = lane; i < r.len; i += 32) atomicAdd(&mt[mi(guard_index(r.z[i], K, a.stats))], 1u);
+        for (int i = lane; i < r.len; i += 32) atomicAdd(&mt[mit<TPL>(guard_index(r.z[i], K, a.stats))], 1u);
     }
     if (lane == 0) m[0] = 0;
-    if (lane + 1 < a.KW) mt[33 * lane + 32] = 0;
+    if (lane + 1 < nl) mt[(TPL + 1) * lane + TPL] = 0;
     __syncwarp();
     uint32_t mbits = 0;
     int kd = 0;
-    if (use_bm) {
+    if (use_bm && TPL == 32) {
         for (int g = 0; g < a.KW; ++g) {
             const int k = g * 32 + lane;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k < K && mt[mi(k)] > 0);
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, k < K && mt[mit<TPL>(k)] > 0);
             if (lane == g) mbits = bal;
             kd += __popc(bal);
         }
+    } else if (use_bm) {
+        if (own) {
+            for (int b = 0; b < TPL; ++b) {
+                const int k = TPL * lane + b;
+                if (k < K && mt[mit<TPL>(k)] > 0) mbits |= 1u << b;
+            }
+        }
+        kd = static_cast<int>(__reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(__popc(mbits))));
     } else {
         int cnt = 0;
-        for (int k = lane; k < K; k += 32) cnt += mt[mi(k)] > 0;
+        for (int k = lane; k < K; k += 32) cnt += mt[mit<TPL>(k)] > 0;
 #pragma unroll
         for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
         kd = cnt;
@@ -731,10 +769,10 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
         uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);   // q row offset of the token's word, or ~0
         if (valid) znew = stage_token(a, rs, i, rec + 2 * lane, drow_of + lane);
         __syncwarp();
-        // the word's bitmap row (32 topics per lane)
+        // the word's bitmap row (TPL topics per lane)
         const uint32_t *bits = a.bits;
         uint32_t bm_next = 0u;
-        if (use_bm && own) bm_next = bits[static_cast<int64_t>(rec[1].z) * a.KWp + lane];
+        if (use_bm && own) bm_next = lane_bits<TPL>(bits, static_cast<int64_t>(rec[1].z) * a.KWp, lane);
         // this block's counters, in 32 bits (at most 32 tokens of K <= 16384),
         // added to the warp's 64-bit counters once per block
         // (c_min: sum of min(K_d, K_v), the same in every lane; c_cnt: tokens
@@ -752,21 +790,21 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             const int ka = static_cast<int>(t0.y >> 16);
             const uint32_t bm = bm_next;
             if (use_bm && tt + 1 < cnt && own)   // the next token's bitmap word, fetched while this one is drawn
-                bm_next = bits[static_cast<int64_t>(rec[2 * tt + 3].z) * a.KWp + lane];
+                bm_next = lane_bits<TPL>(bits, static_cast<int64_t>(rec[2 * tt + 3].z) * a.KWp, lane);
             // remove token i: m^{-i}
             if (use_bm) {
                 // the lane owning topic kold updates its count and bitmap word
                 // (lanes read only their own counts on the document side)
-                const bool me = lane == (kold >> 5);
-                const uint32_t old = me ? mt[mi(kold)] : 0u;
-                if (me) mt[mi(kold)] = old - 1;
+                const bool me = lane == kold / TPL;
+                const uint32_t old = me ? mt[mit<TPL>(kold)] : 0u;
+                if (me) mt[mit<TPL>(kold)] = old - 1;
                 const bool died = me && old == 1;
-                if (died) mbits &= ~(1u << (kold & 31));
+                if (died) mbits &= ~(1u << (kold % TPL));
                 kd -= __any_sync(0xFFFFFFFFu, died) ? 1 : 0;
             } else {
-                const uint32_t old = mt[mi(kold)];
+                const uint32_t old = mt[mit<TPL>(kold)];
                 __syncwarp();
-                if (lane == 0) mt[mi(kold)] = old - 1;
+                if (lane == 0) mt[mit<TPL>(kold)] = old - 1;
                 if (old == 1) --kd;
                 __syncwarp();
             }
@@ -775,7 +813,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             // |J| from the bitmaps on either side (the column side's topics with
             // m > 0 are the same set); without bitmaps the column loop counts it
             if (use_bm) c_cnt += static_cast<uint32_t>(__popc(bm & mbits)) << 18;
-            // The document side needs the word's dense q row (q of topic 32 lane + b
+            // The document side needs the word's dense q row (q of topic TPL lane + b
             // at qd[b]); a word without one is iterated on the column side.
             const uint32_t drow = drow_of[tt];
             const bool docside = use_bm && drow != 0xFFFFFFFFu && (a.path == 2 || kd * kDocRatio < n_w * 16);
@@ -784,9 +822,9 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             const uint32_t *ml = mt + mo;
             // per-lane partial sums of q m, in ascending topic order across lanes
             u64 acc = 0;
-            uint32_t qv[kGather];
-            int bp[kGather];
-            uint32_t rest = 0;         // docside: bits below the first kGather
+            uint32_t qv[G];
+            int bp[G];
+            uint32_t rest = 0;         // docside: bits below the first G
             int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
             if (docside) {
                 // The lane's bits from the highest down; a slot past the last
@@ -794,14 +832,14 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
                 // the zero before the lane's slots.
                 uint32_t rem = bm & mbits;
 #pragma unroll
-                for (int t = 0; t < kGather; ++t) {
+                for (int t = 0; t < G; ++t) {
                     const int b = msb_or_neg1(rem);
                     rem ^= bit_or_zero(b);
                     bp[t] = b;
                     qv[t] = b >= 0 ? qd[b] : 0u;
                 }
 #pragma unroll
-                for (int t = 0; t < kGather; ++t) acc += static_cast<u64>(qv[t]) * ml[bp[t]];
+                for (int t = 0; t < G; ++t) acc += static_cast<u64>(qv[t]) * ml[bp[t]];
                 rest = rem;
                 for (uint32_t bb = rest; bb;) {
                     const int b = msb_or_neg1(bb);
@@ -816,7 +854,7 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
                 unsigned nj = 0;
 #pragma unroll 4
                 for (int j = seg0; j < seg1; ++j) {
-                    const uint32_t mk = mt[mi(guard_index(a.topic[col + j], K, a.stats))];
+                    const uint32_t mk = mt[mit<TPL>(guard_index(a.topic[col + j], K, a.stats))];
                     acc += static_cast<u64>(qcol[j]) * mk;
                     if (!use_bm) nj += mk != 0u;
                 }
@@ -848,22 +886,22 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
                                 // one of the lane's bits)
                                 u64 run = incl;
 #pragma unroll
-                                for (int t = 0; t < kGather; ++t) {
+                                for (int t = 0; t < G; ++t) {
                                     run -= static_cast<u64>(qv[t]) * ml[bp[t]];
-                                    if (rb >= run) { f = 32 * lane + bp[t]; break; }
+                                    if (rb >= run) { f = TPL * lane + bp[t]; break; }
                                 }
                                 for (uint32_t bb = rest; f < 0 && bb;) {
                                     const int b = msb_or_neg1(bb);
                                     bb ^= bit_or_zero(b);
                                     run -= static_cast<u64>(qd[b]) * ml[b];
-                                    if (rb >= run) f = 32 * lane + b;
+                                    if (rb >= run) f = TPL * lane + b;
                                 }
                             } else {
                                 u64 run = incl - acc;
                                 const int seg1 = min(seg0 + seg, n_w);
                                 for (int j = seg0; j < seg1; ++j) {
                                     const int k = guard_index(a.topic[col + j], K, a.stats);
-                                    run += static_cast<u64>(qcol[j]) * mt[mi(k)];
+                                    run += static_cast<u64>(qcol[j]) * mt[mit<TPL>(k)];
                                     if (rb < run) { f = k; break; }
                                 }
                             }
@@ -880,16 +918,16 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
             // add token i back with its new topic
             knew = guard_index(knew, K, a.stats);
             if (use_bm) {
-                const bool me = lane == (knew >> 5);
-                const uint32_t old2 = me ? mt[mi(knew)] : 0u;
-                if (me) mt[mi(knew)] = old2 + 1;
+                const bool me = lane == knew / TPL;
+                const uint32_t old2 = me ? mt[mit<TPL>(knew)] : 0u;
+                if (me) mt[mit<TPL>(knew)] = old2 + 1;
                 const bool born = me && old2 == 0;
-                if (born) mbits |= 1u << (knew & 31);
+                if (born) mbits |= 1u << (knew % TPL);
                 kd += __any_sync(0xFFFFFFFFu, born) ? 1 : 0;
             } else {
-                const uint32_t old2 = mt[mi(knew)];
+                const uint32_t old2 = mt[mit<TPL>(knew)];
                 __syncwarp();
-                if (lane == 0) mt[mi(knew)] = old2 + 1;
+                if (lane == 0) mt[mit<TPL>(knew)] = old2 + 1;
                 if (old2 == 0) ++kd;
                 __syncwarp();
             }
@@ -919,6 +957,8 @@ __device__ void z_doc_warp(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, co
 
 // One chain, one document per warp (dynamically scheduled, longest first),
 // one pass.
+// TPL topics per lane (z_lane_topics(K)), one instantiation per kernel.
+template <int TPL>
 __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
@@ -946,7 +986,7 @@ __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs
             len = static_cast<int>(a.doc_off[d + 1] - s);
         }
         DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep, 0, len, 1};
-        z_doc_warp(a, m, r, wcnt, m0);
+        z_doc_warp_t<TPL>(a, m, r, wcnt, m0);
     }
     flush_warp_counters(a.stats, wcnt);
 }
@@ -969,6 +1009,8 @@ __global__ void k_slice_counts(const int64_t *doc_off, const int32_t *sliced_doc
 
 // Many chains: the work list holds (chain, document) pairs, longest first
 // across all chains; shared memory per warp is sized for the largest K.
+// TPL = z_lane_topics(kmax): every chain of the batch has K <= kmax <= 32 TPL.
+template <int TPL>
 __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_multi(const ZArgs *chains, const int2 *items,
                                                                         int n_items, int *work, int kmax) {
     extern __shared__ uint32_t zsm[];
@@ -986,7 +1028,7 @@ __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_m
         const int64_t s = a.doc_off[it.y];
         DocRun r{a.w + s, a.z + s, static_cast<int>(a.doc_off[it.y + 1] - s), a.seed, a.index_base + s, sweep_of(a),
                  0, a.doc_off[it.y + 1] - s, 1};
-        z_doc_warp(a, m, r, wcnt);
+        z_doc_warp_t<TPL>(a, m, r, wcnt, nullptr);
         flush_warp_counters(a.stats, wcnt);
     }
 }
@@ -1021,6 +1063,7 @@ __global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_
 // With window_ns > 0 a slot also stops at the first 32-token block boundary
 // window_ns after its warp took it up, having done at least one block (a slot
 // taken up in a later wave of a crowded launch gets the same time as the first).
+template <int TPL>
 __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSlot *slots, const int32_t *active,
                                                                      int n_active, const int32_t *arena_w,
                                                                      int16_t *arena_z, int64_t slice, int *work,
@@ -1056,7 +1099,7 @@ __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSl
         }
         DocRun r{arena_w + sl.off, z, sl.len, sl.seed, 0, sweep, pos, slice,
                  static_cast<int>(sl.sweep_end - sweep), deadline};
-        z_doc_warp(a, m, r, wcnt);
+        z_doc_warp_t<TPL>(a, m, r, wcnt, nullptr);
         if (lane == 0) {
             slots[idx].sweep = r.sweep;
             slots[idx].pos = r.pos;
@@ -1180,9 +1223,11 @@ size_t z_step_smem(int K, int warps_per_block) { return sizeof(uint32_t) * stati
 
 int z_step_blocks_per_sm(int K, int warps_per_block) {
     const size_t smem = z_step_smem(K, warps_per_block);
-    allow_dynamic_smem(k_z_step);
+    const int tpl = z_lane_topics(K);
+    auto *kern = tpl == 8 ? k_z_step<8> : tpl == 16 ? k_z_step<16> : k_z_step<32>;
+    allow_dynamic_smem(kern);
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_z_step, 32 * warps_per_block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * warps_per_block, smem);
     return b > 0 ? b : 1;
 }
 
@@ -1194,7 +1239,21 @@ void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int
 }
 
 void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st) {
-    k_z_step<<<grid, 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(a);
+    const size_t smem = z_step_smem(a.K, warps_per_block);
+    switch (z_lane_topics(a.K)) {
+        case 8: k_z_step<8><<<grid, 32 * warps_per_block, smem, st>>>(a); break;
+        case 16: k_z_step<16><<<grid, 32 * warps_per_block, smem, st>>>(a); break;
+        default: k_z_step<32><<<grid, 32 * warps_per_block, smem, st>>>(a); break;
+    }
+}
+
+static void launch_z_step_multi(const BatchLaunch &b, const int2 *items, int n, cudaStream_t st) {
+    const size_t smem = z_step_smem(b.kmax, b.z_warps);
+    switch (z_lane_topics(b.kmax)) {
+        case 8: k_z_step_multi<8><<<b.z_grid, 32 * b.z_warps, smem, st>>>(b.z, items, n, b.work + 1, b.kmax); break;
+        case 16: k_z_step_multi<16><<<b.z_grid, 32 * b.z_warps, smem, st>>>(b.z, items, n, b.work + 1, b.kmax); break;
+        default: k_z_step_multi<32><<<b.z_grid, 32 * b.z_warps, smem, st>>>(b.z, items, n, b.work + 1, b.kmax); break;
+    }
 }
 
 void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
@@ -1211,13 +1270,11 @@ void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
         launch_z_step_coop_multi(b.z, b.z_items, b.n_coop, b.work + 2, b.kmax, b.coop_grid, st);
         cudaStreamWaitEvent(b.stream2, b.ev_fork, 0);
         if (b.n_z_items > b.n_coop)
-            k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), b.stream2>>>(
-                b.z, b.z_items + b.n_coop, b.n_z_items - b.n_coop, b.work + 1, b.kmax);
+            launch_z_step_multi(b, b.z_items + b.n_coop, b.n_z_items - b.n_coop, b.stream2);
         cudaEventRecord(b.ev_join, b.stream2);
         cudaStreamWaitEvent(st, b.ev_join, 0);
     } else {
-        k_z_step_multi<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps), st>>>(
-            b.z, b.z_items, b.n_z_items, b.work + 1, b.kmax);
+        launch_z_step_multi(b, b.z_items, b.n_z_items, st);
     }
 }
 
@@ -1278,6 +1335,7 @@ __global__ void k_barrier_selftest(GridBarrier *bar, unsigned expect, int rounds
     }
 }
 
+template <int TPL>
 __global__ void __launch_bounds__(kPersistThreads, PULDA_PERSIST_MINB) k_batch_sweep_persistent(BatchLaunch b) {
     extern __shared__ uint32_t psm[];
     __shared__ int scan_tmp[kPersistThreads / 32 + 1];
@@ -1344,7 +1402,7 @@ __global__ void __launch_bounds__(kPersistThreads, PULDA_PERSIST_MINB) k_batch_s
             const int64_t s0 = a.doc_off[it.y];
             DocRun r{a.w + s0, a.z + s0, static_cast<int>(a.doc_off[it.y + 1] - s0), a.seed, a.index_base + s0,
                      sweep_of(a), 0, a.doc_off[it.y + 1] - s0, 1};
-            z_doc_warp(a, m, r, wcnt);
+            z_doc_warp_t<TPL>(a, m, r, wcnt, nullptr);
             flush_warp_counters(a.stats, wcnt);
         }
     }
@@ -1370,11 +1428,16 @@ size_t batch_persistent_smem(int kmax) {
                      z_step_smem(kmax, kPersistWarps)});
 }
 
+static auto persistent_kernel(int kmax) {
+    const int tpl = z_lane_topics(kmax);
+    return tpl == 8 ? k_batch_sweep_persistent<8> : tpl == 16 ? k_batch_sweep_persistent<16> : k_batch_sweep_persistent<32>;
+}
+
 int batch_persistent_blocks_per_sm(int kmax) {
-    allow_dynamic_smem(k_batch_sweep_persistent);
+    auto *kern = persistent_kernel(kmax);
+    allow_dynamic_smem(kern);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep_persistent, kPersistThreads,
-                                                  batch_persistent_smem(kmax));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kPersistThreads, batch_persistent_smem(kmax));
     return n;
 }
 
@@ -1389,7 +1452,7 @@ cudaError_t launch_batch_sweep_persistent(const BatchLaunch &b, cudaStream_t st)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_sweep_persistent, b);
+    return cudaLaunchKernelEx(&cfg, persistent_kernel(b.kmax), b);
 }
 
 int batch_phi_blocks_per_sm(int kmax) {
@@ -1400,9 +1463,11 @@ int batch_phi_blocks_per_sm(int kmax) {
 }
 
 int batch_z_blocks_per_sm(int kmax, int warps) {
-    allow_dynamic_smem(k_z_step_multi);
+    const int tpl = z_lane_topics(kmax);
+    auto *kern = tpl == 8 ? k_z_step_multi<8> : tpl == 16 ? k_z_step_multi<16> : k_z_step_multi<32>;
+    allow_dynamic_smem(kern);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_z_step_multi, 32 * warps, z_step_smem(kmax, warps));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * warps, z_step_smem(kmax, warps));
     return n > 0 ? n : 1;
 }
 
@@ -1412,14 +1477,18 @@ void launch_serve_step(const ZArgs &a, ServeSlot *slots, const int32_t *active, 
     if (n_active <= 0) return;
     cudaMemsetAsync(work, 0, sizeof(int), st);
     const int need = (n_active + warps_per_block - 1) / warps_per_block;
-    k_serve_step<<<std::min(grid, need), 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(
+    const int tpl = z_lane_topics(a.K);
+    auto *kern = tpl == 8 ? k_serve_step<8> : tpl == 16 ? k_serve_step<16> : k_serve_step<32>;
+    kern<<<std::min(grid, need), 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(
         a, slots, active, n_active, arena_w, arena_z, slice, work, window_ns);
 }
 
 int serve_blocks_per_sm(int K, int warps_per_block) {
-    allow_dynamic_smem(k_serve_step);
+    const int tpl = z_lane_topics(K);
+    auto *kern = tpl == 8 ? k_serve_step<8> : tpl == 16 ? k_serve_step<16> : k_serve_step<32>;
+    allow_dynamic_smem(kern);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_serve_step, 32 * warps_per_block, z_step_smem(K, warps_per_block));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * warps_per_block, z_step_smem(K, warps_per_block));
     return n > 0 ? n : 1;
 }
 

@@ -67,6 +67,24 @@ def test_batch_equals_single_chains(warps, coop, form):
     b.close()
 
 
+@pytest.mark.parametrize("n,form", [(3, 2), (3, 1), (4, 2), (4, 1)])
+def test_batch_lane_widths(n, form):
+    """The batched z-step gives each lane z_lane_topics(largest K) topics: a
+    batch of the first three chains (K up to 100: 8 per lane) or four (K up to
+    500: 16 per lane), in either launch form, equals each chain run alone
+    (whose own lane width follows its own K)."""
+    import paper_1704_03581_gb300 as P
+    chains = make_chains()[:n]
+    b = P.Batch(chains, coop_min_len=-1, batch_form=form)
+    b.sweep(5)
+    for i, c in enumerate(chains):
+        s = P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"], coop_min_len=-1)
+        s.sweep(5)
+        assert np.array_equal(b.z(i), s.z()), f"chain {i} differs from its single-chain run"
+        s.close()
+    b.close()
+
+
 def test_batch_chain_matches_oracle():
     import paper_1704_03581_gb300 as P
     chains = make_chains()

@@ -45,10 +45,11 @@ def test_small_corpus_lockstep(dpw):
 
 
 @pytest.mark.parametrize("dpw", [4, 1], ids=["4docs-per-warp", "1doc-per-warp"])
-@pytest.mark.parametrize("K", [1, 31, 33, 200, 1000, 1024, 1025, 3000])
+@pytest.mark.parametrize("K", [1, 31, 33, 200, 256, 257, 500, 513, 1000, 1024, 1025, 3000])
 def test_topic_counts_around_tile_edges(K, dpw):
     """K around the 32-topic words, the 128 topics a lane owns in the grouped
-    kernel, and the 1024 limit of the bitmap paths."""
+    kernel, the one-warp kernel's switches from 8 to 16 to 32 topics per lane
+    (256 / 512), and the 1024 limit of the bitmap paths."""
     if dpw == 4 and K > 1024:
         pytest.skip("four documents per warp needs K <= 1024")
     rng = np.random.default_rng(K)
@@ -281,15 +282,15 @@ def test_sort_count_path_small_corpus():
 
 
 def test_z_layout_follows_the_measured_rule():
-    """Auto takes four documents per warp while one bitmap word per lane
-    covers K (K <= 256), one per warp above; 4 forces four (K <= 1024), the
-    column-only path one; the longest documents go to CTAs either way."""
+    """Auto takes one document per warp at every K; 4 forces four
+    (K <= 1024), the column-only path one; the longest documents go to CTAs
+    either way."""
     import paper_1704_03581_gb300 as P
     rng = np.random.default_rng(5)
     lengths = np.concatenate([[4000], rng.integers(1, 200, size=200)])
     w, off = corpus_from_lengths(rng, lengths, 800)
-    for K, kw, dpw in [(20, {}, 4), (256, {}, 4), (257, {}, 1), (1000, {}, 1), (1000, dict(docs_per_warp=4), 4),
-                       (100, dict(docs_per_warp=1), 1), (100, dict(zstep_path=1), 1)]:
+    for K, kw, dpw in [(20, {}, 1), (256, {}, 1), (257, {}, 1), (1000, {}, 1), (1000, dict(docs_per_warp=4), 4),
+                       (20, dict(docs_per_warp=4), 4), (100, dict(docs_per_warp=1), 1), (100, dict(zstep_path=1), 1)]:
         s = P.Sampler(w, off, K, 800, 0.1, 0.01, seed=1, **kw)
         lay = s.z_layout()
         assert lay["docs_per_warp"] == dpw, (K, kw, lay)
