@@ -439,6 +439,8 @@ def run_pulda(args, corpus, rank: int, world: int):
         s2 = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                        stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp, phi_mode=args.phi_mode,
                        slice_len=args.slice_len, coop_min_len=args.coop_min_len)
+        s2.sync()
+        t_init = time.perf_counter() - t0
         stats_bytes = ctypes.sizeof(P.SweepStats)
         for _ in range(K):
             s2.sweep(1)
@@ -451,6 +453,7 @@ def run_pulda(args, corpus, rank: int, world: int):
         dt_max = reduce_max(dt, world)
         e2e = {"value": aggregate_tokens_per_s(corpus.N, K, world, 1000.0 * dt_max), "unit": "tokens/s",
                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+               "init_ms": 1000.0 * t_init,
                "note": "pulda_init from host buffers (the corpus crosses once: every sweep reads it on the "
                        "device), then per sweep the sweep and a read of its counters to the host, then the "
                        "topics to the host; host clock"}

@@ -565,8 +565,11 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
     asum = warp_sum64(asum);
     if (lane == 0) a.A[v] = asum;
     __syncwarp();
-    if (lane != 0 || asum == 0) return;
-    // Vose: small stack grows up from 0, large stack down from n-1.
+    if (asum == 0) return;
+    // Vose: small stack grows up from 0, large stack down from n-1, each in
+    // ascending slot order.  The warp builds the two stacks with a ballot per
+    // 32 slots; lane 0 pairs (sequential by definition); then every lane
+    // computes the thresholds of its paired slots.
     // Thresholds floor(P 2^32 / A) divide by the word's invariant A:
     // Moller and Granlund's 2/1 division with a reciprocal of the normalised
     // divisor, one 128-bit division per word instead of one per slot (exact).
@@ -576,35 +579,51 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
     u64 *P = a.vose_p + out;
     uint16_t *stk = a.vose_stack + out;
     int ns = 0, nl = 0;
-    for (int j = 0; j < n; ++j) {
-        if (P[j] < asum) stk[ns++] = static_cast<uint16_t>(j);
-        else { stk[n - 1 - nl] = static_cast<uint16_t>(j); ++nl; }
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        const int j = j0 + lane;
+        const bool in = j < n;
+        const bool small = in && P[j] < asum;
+        const uint32_t bs = __ballot_sync(0xFFFFFFFFu, small), bl = __ballot_sync(0xFFFFFFFFu, in && !small);
+        const uint32_t below = (1u << lane) - 1u;
+        if (small) stk[ns + __popc(bs & below)] = static_cast<uint16_t>(j);
+        else if (in) stk[n - 1 - (nl + __popc(bl & below))] = static_cast<uint16_t>(j);
+        ns += __popc(bs);
+        nl += __popc(bl);
     }
-    while (ns > 0 && nl > 0) {
-        const int s = stk[--ns];
-        --nl;
-        const int l = stk[n - 1 - nl];
-        const u64 ps = P[s];
-        {   // (u1, u0) = ps 2^32 2^sh, u1 < dn since ps < asum
-            const u64 hi = ps >> 32, lo = ps << 32;
-            const u64 u1 = sh ? (hi << sh) | (lo >> (64 - sh)) : hi;
-            const u64 u0 = lo << sh;
-            u64 q0 = vinv * u1;
-            u64 q1 = __umul64hi(vinv, u1);
-            const u64 t = q0 + u0;
-            q1 += u1 + (t < q0 ? 1ull : 0ull);
-            q0 = t;
-            q1 += 1;
-            u64 r = u0 - q1 * dn;
-            if (r > q0) { q1 -= 1; r += dn; }
-            if (r >= dn) q1 += 1;
-            a.athr[out + s] = static_cast<uint32_t>(q1);
+    __syncwarp();
+    if (lane == 0) {
+        while (ns > 0 && nl > 0) {
+            const int s = stk[--ns];
+            --nl;
+            const int l = stk[n - 1 - nl];
+            const u64 ps = P[s];             // final: s is not pushed again
+            a.atopic[out + s] = a.topic[out + l];
+            const u64 pl = P[l] - (asum - ps);
+            P[l] = pl;
+            if (pl < asum) stk[ns++] = static_cast<uint16_t>(l);
+            else { stk[n - 1 - nl] = static_cast<uint16_t>(l); ++nl; }
         }
-        a.atopic[out + s] = a.topic[out + l];
-        const u64 pl = P[l] - (asum - ps);
-        P[l] = pl;
-        if (pl < asum) stk[ns++] = static_cast<uint16_t>(l);
-        else { stk[n - 1 - nl] = static_cast<uint16_t>(l); ++nl; }
+    }
+    __syncwarp();
+    // a paired slot's alias is another topic of the column; the rest keep
+    // their own topic and threshold 2^32 - 1
+    for (int j = lane; j < n; j += 32) {
+        if (a.atopic[out + j] == a.topic[out + j]) continue;
+        const u64 ps = P[j];
+        // (u1, u0) = ps 2^32 2^sh, u1 < dn since ps < asum
+        const u64 hi = ps >> 32, lo = ps << 32;
+        const u64 u1 = sh ? (hi << sh) | (lo >> (64 - sh)) : hi;
+        const u64 u0 = lo << sh;
+        u64 q0 = vinv * u1;
+        u64 q1 = __umul64hi(vinv, u1);
+        const u64 t = q0 + u0;
+        q1 += u1 + (t < q0 ? 1ull : 0ull);
+        q0 = t;
+        q1 += 1;
+        u64 r = u0 - q1 * dn;
+        if (r > q0) { q1 -= 1; r += dn; }
+        if (r >= dn) q1 += 1;
+        a.athr[out + j] = static_cast<uint32_t>(q1);
     }
 }
 
