@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--serve-high-rate", type=float, default=5000.0, help="serving keys: the continuous arm's high rate")
     ap.add_argument("--serve-high-seconds", type=float, default=2.0, help="serving keys: its arrival window")
     ap.add_argument("--batch-steps", type=int, default=10, help="batched keys: timed sweeps of each arm")
+    ap.add_argument("--batch-form", type=int, default=0, choices=[0, 1, 2],
+                    help="batched launch form: 0 tuned, 1 six launches per sweep, 2 one persistent launch")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--docs-per-warp", type=int, default=0, help="z-step documents per warp: 0 auto, 1 or 4")
     ap.add_argument("--phi-mode", type=int, default=0, choices=[0, 1],
@@ -460,7 +462,7 @@ def run_pulda(args, corpus, rank: int, world: int):
 
     batched = None
     if world == 1 and not args.no_batched:
-        batched = batched_probe(args.batch_scale, args.batch_steps, 8, args.coop_min_len)
+        batched = batched_probe(args.batch_scale, args.batch_steps, 8, args.coop_min_len, batch_form=args.batch_form)
     if rank != 0:
         return
     peak, peak_kind = peaks()
@@ -663,7 +665,8 @@ def run_sparsity(args):
     print(json.dumps(line), flush=True)
 
 
-def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, clocks_too: bool = False) -> dict:
+def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, clocks_too: bool = False,
+                  batch_form: int = 0) -> dict:
     """32 independent corpora (uneven D, N, K, V; D scaled by `scale`) advanced
     together by one CUDA-graph launch per sweep, against the same 32 chains
     run one after another through single-chain handles (each with its own
@@ -682,7 +685,7 @@ def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, cloc
     N = sum(c.N for c in corpora)
     stream = torch.cuda.Stream()
     K, W = steps, max(warmup, 8)
-    b = P.Batch(chains, stream=stream.cuda_stream, coop_min_len=coop_min_len)
+    b = P.Batch(chains, stream=stream.cuda_stream, coop_min_len=coop_min_len, batch_form=batch_form)
     b.sweep(W)                          # the first sweeps also time the tuning candidates
     b.sync()
     assert b.tuning()[2], "tuning not over after the warm-up sweeps"
@@ -730,7 +733,8 @@ def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, cloc
 
 def run_batched(args):
     """The batched-chains form alone (config 4)."""
-    r = batched_probe(args.batch_scale, args.steps, args.warmup, args.coop_min_len, clocks_too=True)
+    r = batched_probe(args.batch_scale, args.steps, args.warmup, args.coop_min_len, clocks_too=True,
+                      batch_form=args.batch_form)
     line = {
         "metric": "batched chains: tokens/s of 32 uneven chains in one graph launch per sweep vs 32 sequential "
                   "single-chain runs",
