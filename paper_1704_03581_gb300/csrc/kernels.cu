@@ -684,9 +684,8 @@ __device__ __forceinline__ uint32_t lane_bits(const uint32_t *bits, int64_t row,
 // the bits of m_d's nonzero topics among the TPL it owns (TPL = 32, or 16 /
 // 8 for K <= 512 / 256, so that small K still spreads over the warp), and
 // the document side reads q of topic TPL lane + b from the word's dense q
-// row.  Tokens are
-// visited in position order: remove token i (m^{-i}), compute
-// sigma_b = sum_k q_{k,v} m_k over the smaller of {k : m_k > 0} and
+// row.  Tokens are visited in position order: remove token i (m^{-i}),
+// compute sigma_b = sum_k q_{k,v} m_k over the smaller of {k : m_k > 0} and
 // {k : phi_{k,v} > 0} (complexity theorem), draw r = floor(u (A + 2^16 B)),
 // take the alias draw if r < A, else the first topic where the running sum
 // of q m passes (r - A) / 2^16; add the token back.

@@ -59,17 +59,18 @@ constexpr int kDocRatio = PULDA_ZDOCRATIO;
 
 
 // m_d is stored skewed, topic k at k + k/32, so the lanes of a warp reading
-// topics 32 l + b (lane l, bit b) hit distinct shared-memory banks.
+// topics 32 l + b (lane l, bit b) hit distinct shared-memory banks (the
+// cooperative kernel's layout; the one-warp kernel skews by its own topics
+// per lane, see z_lane_topics).
 __host__ __device__ __forceinline__ int mi(int k) { return k + (k >> 5); }
-// Shared memory of one z-step warp, in 32-bit words: m_d (skewed, rounded up
-// to 16 bytes), then the staging records of the 32 tokens in flight.
 // Topics per lane of the one-warp z-step: 8 for K <= 256, 16 for K <= 512,
 // else 32.
 __host__ __device__ __forceinline__ int z_lane_topics(int K) { return K <= 256 ? 8 : K <= 512 ? 16 : 32; }
-// The count words of one z-step warp: K counts, the gap words after the
-// lanes' slots (K / 32 + 32 of them covers (K - 1) / TPL for every
-// z_lane_topics(K), and grows with K) and a leading zero, rounded up to 16
-// bytes.
+// Shared memory of one z-step warp, in 32-bit words: m_d, then the staging
+// records of the 32 tokens in flight.  The count words: K counts, the gap
+// words after the lanes' slots (K / 32 + 32 of them covers (K - 1) / TPL for
+// every z_lane_topics(K), and grows with K) and a leading zero, rounded up to
+// 16 bytes.
 __host__ __device__ __forceinline__ int z_m_words(int K) { return (K + (K >> 5) + 32 + 1 + 3) & ~3; }
 constexpr int kTokRecWords = 9;     // two uint4 per token, and the offset of its word's dense q row
 // ... then the warp's six 64-bit counters (z_doc_warp's, 16-byte aligned) and

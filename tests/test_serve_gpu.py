@@ -38,6 +38,31 @@ def requests(c, n, rng):
     return out
 
 
+@pytest.mark.parametrize("K", [300, 1000])
+def test_server_lane_widths(trained, K):
+    """Models whose K gives the server 16 (K = 300) and 32 (K = 1000) topics
+    per lane: every request equals its run alone."""
+    P, _, _, c = trained
+    s = P.Sampler(c.w, c.doc_off, K, c.V, 0.1, 0.01, seed=4).sweep(2)
+    rng = np.random.default_rng(K)
+    reqs = requests(c, 16, rng)
+    srv = P.Server(s, token_budget=4000, max_slots=8, slice_tokens=64)
+    for r in reqs:
+        srv.submit(r["id"], r["seed"], r["words"], r["sweeps"])
+    got = {}
+    t0 = time.time()
+    while len(got) < len(reqs):
+        for res in srv.poll(timeout_ms=200):
+            assert res["status"] == 0
+            got[res["req_id"]] = res["z"]
+        assert time.time() - t0 < 120, "server made no progress"
+    srv.close()
+    for r in reqs:
+        alone = s.infer(r["words"], np.array([0, len(r["words"])]), r["sweeps"], seed=r["seed"])
+        assert np.array_equal(got[r["id"]], alone), f"request {r['id']} differs from its run alone"
+    s.close()
+
+
 @pytest.mark.parametrize("budget,slots,slice_", [(3000, 8, 64), (10000, 64, 4096), (3000, 3, 1), (10000, 64, 0)])
 def test_mixed_requests_equal_each_alone(trained, budget, slots, slice_):
     P, s, ch, c = trained
