@@ -34,7 +34,7 @@ def main():
     s, _ = lockstep(c.w, c.doc_off, 20, c.V, 0.1, 0.01, seed=4, sweeps=2, docs_per_warp=4)
     s.close()
     rng = np.random.default_rng(9)
-    for K in (1, 33, 1000, 1025):
+    for K in (1, 33, 300, 1000, 1025):
         lengths = rng.integers(0, 400, size=30)
         lengths[:3] = [0, 1, 1500]
         w, off = corpus(rng, lengths, 600)
