@@ -220,15 +220,13 @@ def recorded_traffic() -> float | None:
     return float(rec["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in rec else None
 
 
-def count_word_topic_pairs(w: np.ndarray, z: np.ndarray, K: int) -> int:
-    """nnz(n): distinct (word, topic) pairs among the tokens, counted on the
-    device (a sort of the N keys w K + z; a diagnostic, outside any timing)."""
-    import torch
-    key = torch.from_numpy(np.ascontiguousarray(w)).cuda().long() * K + torch.from_numpy(
-        np.ascontiguousarray(z)).cuda().long()
-    n = int(torch.unique(key).numel())
-    del key
-    return n
+def count_word_topic_pairs(s, K: int, V: int) -> int:
+    """nnz(n): the nonzero (word, topic) counts of the sampler's current topics,
+    from the library's own count export (a diagnostic, outside any timing)."""
+    import paper_1704_03581_gb300 as P
+    n = np.empty(K * V, np.int32)
+    P.pulda_get_counts(s.h, n, None)
+    return int(np.count_nonzero(n))
 
 
 def phi_bytes(N: int, nnz_phi: int, nnz_n: int) -> float:
@@ -421,7 +419,7 @@ def run_pulda(args, corpus, rank: int, world: int):
     docside = st1["cum_docside"] - st0["cum_docside"]
     assert tokens == K * corpus.N, (tokens, K * corpus.N)
     nnz_phi = st1["nnz_phi"]
-    nnz_n = count_word_topic_pairs(corpus.w, s.z(), K_TOPICS)   # for the Phi-step's byte model, not timed
+    nnz_n = count_word_topic_pairs(s, K_TOPICS, corpus.V)   # for the Phi-step's byte model, not timed
     torch.cuda.synchronize()
     t_lp = time.perf_counter()
     lp_after = s.log_posterior()[0]
