@@ -32,7 +32,10 @@ namespace {
 #endif
 constexpr int kCoopWarps = PULDA_COOP_WARPS;
 constexpr int kCoopSlots = 32 * kCoopWarps;
-constexpr int kCoopGather = 4;     // document-side q loads per round
+#ifndef PULDA_COOP_GATHER
+#define PULDA_COOP_GATHER 3
+#endif
+constexpr int kCoopGather = PULDA_COOP_GATHER;   // document-side q loads issued together per slot
 // 64 registers, as the one-warp kernel (8 CTAs of four warps per SM); the
 // serving form needs 72 (7 CTAs of four warps).
 constexpr int kCoopMinBlocks = 32 / kCoopWarps;
@@ -55,7 +58,10 @@ __host__ __device__ __forceinline__ int z_coop_words(int K) {
 __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = a.K;
-    uint32_t *m = sm;
+    // topic k's count at m[mi(k)], with a zero word before each 32-topic
+    // word's counts (sm[0] before word 0, the gap word of word w - 1 before
+    // word w): a gather slot past a slot's last bit reads a zero there
+    uint32_t *m = sm + 1;
     uint4 *rec = reinterpret_cast<uint4 *>(sm + z_m_words(K));
     uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);
     CoopXch &x = *reinterpret_cast<CoopXch *>(drow_of + 32);
@@ -68,6 +74,8 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
     const uint32_t mask = own ? (R >= 32 ? 0xFFFFFFFFu : ((1u << R) - 1u) << sh) : 0u;
     if (r.len == 0 || r.budget <= 0) return;
     for (int k = tid; k < K; k += kCoopSlots) m[mi(k)] = 0;
+    if (tid == 0) sm[0] = 0;
+    for (int w = tid; w + 1 < a.KW; w += kCoopSlots) m[33 * w + 32] = 0;
     __syncthreads();
     for (int i = tid; i < r.len; i += kCoopSlots) atomicAdd(&m[mi(guard_index(r.z[i], K, a.stats))], 1u);
     __syncthreads();
@@ -124,30 +132,33 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
             u64 acc = 0;
             uint32_t rem = 0;
             int j0 = 0, j1 = 0;
+            uint32_t qv[kCoopGather];
+            int bp[kCoopGather];
+            uint32_t rest = 0;
             if (docside) {
                 rem = bm & mb;
                 st.inter += static_cast<u64>(__popc(rem));
-                for (uint32_t bb = rem; bb;) {
-                    uint32_t qv[kCoopGather];
-                    int bp[kCoopGather];
+                // the slot's bits from the highest down; a slot past the last
+                // bit gets b = -1, q = 0 (no load) and the zero before the word
+                uint32_t bb = rem;
 #pragma unroll
-                    for (int t = 0; t < kCoopGather; ++t) {
-                        bp[t] = -1;
-                        qv[t] = 0;
-                        if (bb) {
-                            const int b = __ffs(bb) - 1;
-                            bb &= bb - 1;
-                            bp[t] = b;
-                            qv[t] = qrow[b];
-                        }
-                    }
+                for (int t = 0; t < kCoopGather; ++t) {
+                    const int b = msb_or_neg1(bb);
+                    bb ^= bit_or_zero(b);
+                    bp[t] = b;
+                    qv[t] = b >= 0 ? qrow[b] : 0u;
+                }
 #pragma unroll
-                    for (int t = 0; t < kCoopGather; ++t) {
-                        if (bp[t] >= 0) {
-                            const int k = 32 * wi + bp[t];
-                            acc += static_cast<u64>(qv[t]) * (m[33 * wi + bp[t]] - (k == kold ? 1u : 0u));
-                        }
-                    }
+                for (int t = 0; t < kCoopGather; ++t) {
+                    const int k = 32 * wi + bp[t];
+                    acc += static_cast<u64>(qv[t]) * (m[33 * wi + bp[t]] - (k == kold ? 1u : 0u));
+                }
+                rest = bb;
+                for (uint32_t b2 = rest; b2;) {
+                    const int b = msb_or_neg1(b2);
+                    b2 ^= bit_or_zero(b);
+                    const int k = 32 * wi + b;
+                    acc += static_cast<u64>(qrow[b]) * (m[33 * wi + b] - (k == kold ? 1u : 0u));
                 }
             } else {
                 const int seg = (n_w + kCoopSlots - 1) / kCoopSlots;
@@ -204,15 +215,25 @@ __device__ void z_doc_coop(const ZArgs &a, uint32_t *sm, DocRun &r, ZCount &st) 
                             if (lane == (bal ? __ffs(bal) - 1 : 31)) {
                                 upd = true;
                                 int f = -1;
-                                u64 run = incl - acc;
                                 if (docside) {
-                                    for (uint32_t bb = rem; f < 0 && bb; bb &= bb - 1) {
-                                        const int b = __ffs(bb) - 1;
+                                    // down from the slot's inclusive sum: the topic whose
+                                    // term takes it to rbl or below
+                                    u64 run = incl;
+#pragma unroll
+                                    for (int t = 0; t < kCoopGather; ++t) {
+                                        const int k = 32 * wi + bp[t];
+                                        run -= static_cast<u64>(qv[t]) * (m[33 * wi + bp[t]] - (k == kold ? 1u : 0u));
+                                        if (rbl >= run) { f = k; break; }
+                                    }
+                                    for (uint32_t b2 = rest; f < 0 && b2;) {
+                                        const int b = msb_or_neg1(b2);
+                                        b2 ^= bit_or_zero(b);
                                         const int k = 32 * wi + b;
-                                        run += static_cast<u64>(qrow[b]) * (m[33 * wi + b] - (k == kold ? 1u : 0u));
-                                        if (rbl < run) f = k;
+                                        run -= static_cast<u64>(qrow[b]) * (m[33 * wi + b] - (k == kold ? 1u : 0u));
+                                        if (rbl >= run) f = k;
                                     }
                                 } else {
+                                    u64 run = incl - acc;
                                     for (int j = j0; j < j1; ++j) {
                                         const int k = guard_index(a.topic[col + j], K, a.stats);
                                         run += static_cast<u64>(a.q[col + j]) * (m[mi(k)] - (k == kold ? 1u : 0u));
