@@ -73,7 +73,7 @@ __host__ __device__ __forceinline__ int z_lane_topics(int K) { return K <= 256 ?
 // 16 bytes.
 __host__ __device__ __forceinline__ int z_m_words(int K) { return (K + (K >> 5) + 32 + 1 + 3) & ~3; }
 constexpr int kTokRecWords = 9;     // two uint4 per token, and the offset of its word's dense q row
-// ... then the warp's six 64-bit counters (z_doc_warp's, 16-byte aligned) and
+// ... then the warp's six 64-bit counters (z_doc_warp_t's, 16-byte aligned) and
 // the document run it is working on.
 constexpr int kWarpCountWords = 32;
 __host__ __device__ __forceinline__ int z_warp_words(int K) { return z_m_words(K) + 32 * kTokRecWords + kWarpCountWords; }
@@ -123,7 +123,7 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Stages what depends only on token i of run r (see z_doc_warp for the
+// Stages what depends only on token i of run r (see z_doc_warp_t for the
 // record layout) and returns its current topic.
 __device__ __forceinline__ int stage_token(const ZArgs &a, const DocRun &r, int i, uint4 *rec2, uint32_t *drow) {
     const int wv = r.w[i];
@@ -160,8 +160,6 @@ __device__ inline void flush_z_stats(unsigned long long *stats, const u64 (&c)[6
     }
 }
 
-// The same from a warp running z_doc_warp: lanes 0-3 and 5 hold their
-// counters, sum |J| is summed over the lanes.  Every lane calls it.
 // Zeroes, and adds to the sweep's and the running totals, a warp's counters
 // kept in its shared memory (z_warp_counters).  Every lane calls them.
 __device__ __forceinline__ void zero_warp_counters(unsigned long long *cnt) {
@@ -186,6 +184,9 @@ __device__ inline void flush_warp_counters(unsigned long long *stats, unsigned l
     __syncwarp();
 }
 
+// The same from a warp of the cooperative kernel holding its counters in a
+// ZCount: lanes 0-3 and 5 hold theirs, sum |J| is summed over the lanes.
+// Every lane calls it.
 __device__ inline void flush_warp_z_stats(unsigned long long *stats, ZCount &c) {
     const u64 inter = warp_sum64(c.inter);
     const int lane = threadIdx.x & 31;
