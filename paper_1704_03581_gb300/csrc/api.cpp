@@ -128,6 +128,15 @@ cudaError_t clear_z_counters(pulda_handle *h) {
 
 // Documents in decreasing length (ties by index), so the persistent z-step
 // starts the long ones first.
+// Whether every document from position `from` of a length order (longest
+// first) has at most kNarrowMaxLen tokens: the one-warp z-step over them can
+// hold its counts in 16 bits.
+bool narrow_from(const int64_t *off, const std::vector<int32_t> &order, int64_t from) {
+    if (from >= static_cast<int64_t>(order.size())) return true;
+    const int32_t d = order[static_cast<size_t>(from)];
+    return off[d + 1] - off[d] <= kNarrowMaxLen;
+}
+
 std::vector<int32_t> length_order(const int64_t *off, int64_t D) {
     std::vector<int32_t> o(D);
     std::iota(o.begin(), o.end(), 0);
@@ -162,10 +171,14 @@ int64_t count_coop(const pulda_handle *h, const int64_t *off, const std::vector<
 // then run one per warp on the same stream, while the rest run four per warp
 // (grouped) or one per warp on a second stream, joined back before the next
 // step.
+// `narrow`: every document the one-warp kernel gets (those after the first
+// n_coop) has at most kNarrowMaxLen tokens.
 pulda_status run_z(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, int64_t D, int64_t n_long,
-                   int64_t n_coop, const int32_t *w, int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base) {
+                   int64_t n_coop, const int32_t *w, int16_t *z, uint64_t seed, uint32_t sweep, int64_t index_base,
+                   bool narrow) {
     CU(h, cudaMemsetAsync(h->work + 1, 0, 3 * sizeof(int), h->stream));
     ZArgs a = z_args(h, doc_off, doc_order, D, w, z, seed, sweep, index_base);
+    a.narrow = narrow ? 1 : 0;
     const int64_t n_head = h->z_groups ? std::max(n_coop, n_long) : n_coop;
     auto launch_rest = [&](cudaStream_t st) {
         if (D <= n_head) return;
@@ -500,6 +513,8 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     h->z_groups = groups_ok && h->opt.docs_per_warp == 4;
     h->n_long = count_long(doc_offsets, dord);
     h->n_coop = count_coop(h, doc_offsets, dord, N);
+    h->narrow_z = narrow_from(doc_offsets, dord, h->n_coop);
+    h->narrow_all = narrow_from(doc_offsets, dord, 0);
     h->coop_grid = sms * z_coop_blocks_per_sm(K);
     CUI(cudaGetLastError());
     CUI(cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
@@ -564,12 +579,13 @@ pulda_status pulda_z_step(pulda_handle *h) {
         a.slices = h->slices;
         a.n_slices = h->n_slices;
         a.m0 = h->m0;
+        a.narrow = h->narrow_all ? 1 : 0;      // the slices start from whole documents' counts
         launch_z_step(a, h->z_warps, h->z_grid, h->stream);
         CU(h, cudaGetLastError());
         return PULDA_OK;
     }
     return run_z(h, h->doc_off, h->doc_order, h->D, h->n_long, h->n_coop, h->w, h->z, h->seed,
-                 static_cast<uint32_t>(h->sweep), 0);
+                 static_cast<uint32_t>(h->sweep), 0, h->narrow_z);
 }
 
 pulda_status pulda_sweep(pulda_handle *h, int32_t n_sweeps) {
@@ -755,8 +771,9 @@ pulda_status pulda_infer(pulda_handle *h, const int32_t *word_ids, const int64_t
     CU(h, clear_z_counters(h));
     const int64_t n_long = count_long(doc_offsets, ord);
     const int64_t n_coop = count_coop(h, doc_offsets, ord, N);
+    const bool narrow = narrow_from(doc_offsets, ord, n_coop);
     for (int32_t sw = 1; sw <= n_sweeps; ++sw) {
-        s = run_z(h, doff, dord, D_new, n_long, n_coop, dw, dz, seed, static_cast<uint32_t>(sw), 0);
+        s = run_z(h, doff, dord, D_new, n_long, n_coop, dw, dz, seed, static_cast<uint32_t>(sw), 0, narrow);
         if (s != PULDA_OK) return s;
     }
     if (z_out) CU(h, cudaMemcpyAsync(z_out, dz, sizeof(int16_t) * N, cudaMemcpyDeviceToHost, st));

@@ -93,7 +93,7 @@ void schedule_phase(pulda_batch *b, int first) {
 
 void apply_candidate(pulda_batch *b, const pulda_batch::Cand &c) {
     b->bl.z_warps = c.warps;
-    b->bl.z_grid = b->sms * batch_z_blocks_per_sm(b->bl.kmax, c.warps);
+    b->bl.z_grid = b->sms * batch_z_blocks_per_sm(b->bl.kmax, c.warps, b->bl.narrow != 0);
     b->coop_len = c.coop_len;
     b->bl.n_coop = count_coop_items(b, c.coop_len);
     b->one_launch = c.one_launch;
@@ -212,6 +212,7 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     std::vector<HeavyChunk> heavy;
     std::vector<std::pair<int64_t, int2>> wi, di;    // (weight, (chain, item))
     int kmax = 1;
+    bool narrow = true;     // every document of every chain fits 16-bit counts
     for (int32_t c = 0; c < n_chains; ++c) {
         pulda_handle *h = b->ch[c];
         hp[c] = phi_args(h);
@@ -219,6 +220,7 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         hz[c] = z_args(h, h->doc_off, h->doc_order, h->D, h->w, h->z, h->seed, 0, 0);
         hz[c].sweep_ptr = d_sweep;
         kmax = std::max(kmax, h->K);
+        narrow = narrow && h->narrow_all;
         for (HeavyChunk hc : h->heavy_chunks) {
             hc.chain = c;
             heavy.push_back(hc);
@@ -280,10 +282,11 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     bl.sweep = d_sweep;
     bl.work = d_work;
     bl.kmax = kmax;
+    bl.narrow = narrow ? 1 : 0;
     bl.phi_grid = b->sms * batch_phi_blocks_per_sm(kmax);
     bl.coop_grid = b->sms * batch_coop_blocks_per_sm(kmax);
     bl.bar = d_bar;
-    bl.persist_grid = b->sms * batch_persistent_blocks_per_sm(kmax);
+    bl.persist_grid = b->sms * batch_persistent_blocks_per_sm(kmax, narrow);
     // The cooperative threshold: fixed, none, or the automatic rule of the
     // single-chain z-step over all chains' tokens (documents that would outlast
     // the pass on one warp).  It is not timed: on the 32-chain workload, timing

@@ -27,6 +27,8 @@ struct pulda_handle {
     int zg_grid = 0;
     int64_t n_long = 0;         // documents too long for the grouped z-step (first in doc_order)
     int64_t n_coop = 0;         // documents the cooperative z-step takes (first in doc_order)
+    bool narrow_z = false;      // the one-warp z-step's documents (after n_coop) fit 16-bit counts
+    bool narrow_all = false;    // every document does
     int coop_grid = 0;
     cudaStream_t stream2 = nullptr;                       // the one-warp z-step beside the cooperative one
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;

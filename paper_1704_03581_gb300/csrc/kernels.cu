@@ -22,6 +22,7 @@
 // The arithmetic that decides any draw is integer or IEEE double with
 // explicit rounding, so results are independent of launch shapes.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "device_rng.cuh"
@@ -704,9 +705,11 @@ __device__ __forceinline__ uint32_t lane_bits(const uint32_t *bits, int64_t row,
 // With m0 set, m starts from those K counts (a slice of a longer document,
 // from the document's counts at the start of the pass) instead of the run's
 // own topics.
-template <int TPL>
+template <int TPL, typename CT>
 __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, const uint32_t *m0) {
     static_assert(TPL == 8 || TPL == 16 || TPL == 32, "8, 16 or 32 topics per lane");
+    static_assert(sizeof(CT) == 2 || sizeof(CT) == 4, "16- or 32-bit counts");
+    constexpr int kLead = 4 / static_cast<int>(sizeof(CT));    // counts before mt[0]: the leading zero's word
     constexpr int G = TPL == 32 ? kGather : TPL == 16 ? kGather16 : kGather8;
     const int lane = threadIdx.x & 31;
     const int K = a.K;
@@ -715,10 +718,11 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
     // Lane l owns topics [TPL l, TPL l + TPL) (TPL = 32, 16 or 8 by K, so
     // that small K spreads over more lanes).  Topic k's count is
     // mt[mit<TPL>(k)]: lane l's topics sit at mt[(TPL + 1) l + b], and the word
-    // before each lane's slots is a zero (m[0] for lane 0 and for the lanes
+    // before each lane's slots is a zero (mt[-1] for lane 0 and for the lanes
     // without topics, the gap word after lane l - 1's slots otherwise), so an
-    // empty gather slot (bit -1) reads a zero count.
-    uint32_t *mt = m + 1;
+    // empty gather slot (bit -1) reads a zero count.  Counts are CT (16-bit
+    // when every document of the launch is shorter than 2^16 tokens).
+    CT *mt = reinterpret_cast<CT *>(m) + kLead;
     const int nl = TPL == 32 ? a.KW : (K + TPL - 1) / TPL;      // lanes that own topics
     const bool own = lane < nl;
     const int mo = own ? (TPL + 1) * lane : 0;   // this lane's count slots (document side)
@@ -728,9 +732,17 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
     } else {
         for (int k = lane; k < K; k += 32) mt[mit<TPL>(k)] = 0;
         __syncwarp();
-        for (int i = lane; i < r.len; i += 32) atomicAdd(&mt[mit<TPL>(guard_index(r.z[i], K, a.stats))], 1u);
+        for (int i = lane; i < r.len; i += 32) {
+            const int k = guard_index(r.z[i], K, a.stats);
+            if (sizeof(CT) == 4) {
+                atomicAdd(reinterpret_cast<uint32_t *>(&mt[mit<TPL>(k)]), 1u);
+            } else {        // the 32-bit word holding the count: no carry, counts stay below 2^16
+                const int h = mit<TPL>(k) + kLead;
+                atomicAdd(m + (h >> 1), 1u << ((h & 1) * 16));
+            }
+        }
     }
-    if (lane == 0) m[0] = 0;
+    if (lane == 0) mt[-1] = 0;
     if (lane + 1 < nl) mt[(TPL + 1) * lane + TPL] = 0;
     __syncwarp();
     uint32_t mbits = 0;
@@ -783,7 +795,7 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
         //   rec[2t]   = {column start (low 32), column start >> 32 | alias outcome << 16, sigma_a (lo, hi)}
         //   rec[2t+1] = {Philox x0, x1, word, K_v | old topic << 16}
         // (column starts are below 2^48, K_v <= 16384, topics < 16384).
-        uint4 *rec = reinterpret_cast<uint4 *>(m + z_m_words(K));
+        uint4 *rec = reinterpret_cast<uint4 *>(m + z_count_words<CT>(K));
         uint32_t *drow_of = reinterpret_cast<uint32_t *>(rec + 64);   // q row offset of the token's word, or ~0
         if (valid) znew = stage_token(a, rs, i, rec + 2 * lane, drow_of + lane);
         __syncwarp();
@@ -837,7 +849,7 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
             const bool docside = use_bm && drow != 0xFFFFFFFFu && (a.path == 2 || kd * kDocRatio < n_w * 16);
             const uint32_t *qcol = a.q + col;
             const uint32_t *qd = a.qdense + drow + qo;
-            const uint32_t *ml = mt + mo;
+            const CT *ml = mt + mo;
             // per-lane partial sums of q m, in ascending topic order across lanes
             u64 acc = 0;
             uint32_t qv[G];
@@ -975,13 +987,14 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
 
 // One chain, one document per warp (dynamically scheduled, longest first),
 // one pass.
-// TPL topics per lane (z_lane_topics(K)), one instantiation per kernel.
-template <int TPL>
+// TPL topics per lane (z_lane_topics(K)) and CT counts, one instantiation
+// per kernel.
+template <int TPL, typename CT>
 __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs a) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
-    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
-    u64 *wcnt = z_warp_counters(m, a.K);
+    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words_t<CT>(a.K);
+    u64 *wcnt = z_warp_counters_t<CT>(m, a.K);
     zero_warp_counters(wcnt);
     const uint32_t sweep = sweep_of(a);
     for (;;) {
@@ -1004,7 +1017,7 @@ __global__ void __launch_bounds__(32 * kZWarps, PULDA_ZMINBLOCKS) k_z_step(ZArgs
             len = static_cast<int>(a.doc_off[d + 1] - s);
         }
         DocRun r{a.w + s, a.z + s, len, a.seed, a.index_base + s, sweep, 0, len, 1};
-        z_doc_warp_t<TPL>(a, m, r, wcnt, m0);
+        z_doc_warp_t<TPL, CT>(a, m, r, wcnt, m0);
     }
     flush_warp_counters(a.stats, wcnt);
 }
@@ -1027,14 +1040,15 @@ __global__ void k_slice_counts(const int64_t *doc_off, const int32_t *sliced_doc
 
 // Many chains: the work list holds (chain, document) pairs, longest first
 // across all chains; shared memory per warp is sized for the largest K.
-// TPL = z_lane_topics(kmax): every chain of the batch has K <= kmax <= 32 TPL.
-template <int TPL>
+// TPL = z_lane_topics(kmax): every chain of the batch has K <= kmax <= 32 TPL;
+// CT 16-bit when every document of every chain is shorter than 2^16 tokens.
+template <int TPL, typename CT>
 __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_multi(const ZArgs *chains, const int2 *items,
                                                                         int n_items, int *work, int kmax) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
-    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(kmax);
-    u64 *wcnt = z_warp_counters(m, kmax);     // beyond every chain's m and token records
+    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words_t<CT>(kmax);
+    u64 *wcnt = z_warp_counters_t<CT>(m, kmax);     // beyond every chain's m and token records
     zero_warp_counters(wcnt);
     for (;;) {
         int item = 0;
@@ -1046,7 +1060,7 @@ __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_m
         const int64_t s = a.doc_off[it.y];
         DocRun r{a.w + s, a.z + s, static_cast<int>(a.doc_off[it.y + 1] - s), a.seed, a.index_base + s, sweep_of(a),
                  0, a.doc_off[it.y + 1] - s, 1};
-        z_doc_warp_t<TPL>(a, m, r, wcnt, nullptr);
+        z_doc_warp_t<TPL, CT>(a, m, r, wcnt, nullptr);
         flush_warp_counters(a.stats, wcnt);
     }
 }
@@ -1117,7 +1131,7 @@ __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSl
         }
         DocRun r{arena_w + sl.off, z, sl.len, sl.seed, 0, sweep, pos, slice,
                  static_cast<int>(sl.sweep_end - sweep), deadline};
-        z_doc_warp_t<TPL>(a, m, r, wcnt, nullptr);
+        z_doc_warp_t<TPL, uint32_t>(a, m, r, wcnt, nullptr);
         if (lane == 0) {
             slots[idx].sweep = r.sweep;
             slots[idx].pos = r.pos;
@@ -1237,12 +1251,22 @@ void launch_heavy_hist(const PhiArgs *chains, const HeavyChunk *chunks, int n_ch
     k_heavy_hist<<<n_chunks, kPhiBlock, sizeof(uint32_t) * static_cast<size_t>(kmax), st>>>(chains, chunks, kmax);
 }
 
-size_t z_step_smem(int K, int warps_per_block) { return sizeof(uint32_t) * static_cast<size_t>(z_warp_words(K)) * warps_per_block; }
+size_t z_step_smem(int K, int warps_per_block, bool narrow) {
+    return sizeof(uint32_t) * static_cast<size_t>(z_warp_words_n(K, narrow)) * warps_per_block;
+}
 
-int z_step_blocks_per_sm(int K, int warps_per_block) {
-    const size_t smem = z_step_smem(K, warps_per_block);
-    const int tpl = z_lane_topics(K);
-    auto *kern = tpl == 8 ? k_z_step<8> : tpl == 16 ? k_z_step<16> : k_z_step<32>;
+using ZStepKernel = void (*)(ZArgs);
+static ZStepKernel z_step_kernel(int K, bool narrow) {
+    switch (z_lane_topics(K)) {
+        case 8: return narrow ? k_z_step<8, uint16_t> : k_z_step<8, uint32_t>;
+        case 16: return narrow ? k_z_step<16, uint16_t> : k_z_step<16, uint32_t>;
+        default: return narrow ? k_z_step<32, uint16_t> : k_z_step<32, uint32_t>;
+    }
+}
+
+int z_step_blocks_per_sm(int K, int warps_per_block, bool narrow) {
+    const size_t smem = z_step_smem(K, warps_per_block, narrow);
+    ZStepKernel kern = z_step_kernel(K, narrow);
     allow_dynamic_smem(kern);
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * warps_per_block, smem);
@@ -1257,21 +1281,30 @@ void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int
 }
 
 void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st) {
-    const size_t smem = z_step_smem(a.K, warps_per_block);
-    switch (z_lane_topics(a.K)) {
-        case 8: k_z_step<8><<<grid, 32 * warps_per_block, smem, st>>>(a); break;
-        case 16: k_z_step<16><<<grid, 32 * warps_per_block, smem, st>>>(a); break;
-        default: k_z_step<32><<<grid, 32 * warps_per_block, smem, st>>>(a); break;
+    ZStepKernel kern = z_step_kernel(a.K, a.narrow != 0);
+    // each instantiation opts in to large dynamic shared memory once
+    static std::atomic<bool> opted[3][2];
+    std::atomic<bool> &o = opted[z_lane_topics(a.K) == 8 ? 0 : z_lane_topics(a.K) == 16 ? 1 : 2][a.narrow != 0];
+    if (!o.load(std::memory_order_acquire)) {
+        allow_dynamic_smem(kern);
+        o.store(true, std::memory_order_release);
+    }
+    kern<<<grid, 32 * warps_per_block, z_step_smem(a.K, warps_per_block, a.narrow != 0), st>>>(a);
+}
+
+using ZMultiKernel = void (*)(const ZArgs *, const int2 *, int, int *, int);
+static ZMultiKernel z_multi_kernel(int kmax, bool narrow) {
+    switch (z_lane_topics(kmax)) {
+        case 8: return narrow ? k_z_step_multi<8, uint16_t> : k_z_step_multi<8, uint32_t>;
+        case 16: return narrow ? k_z_step_multi<16, uint16_t> : k_z_step_multi<16, uint32_t>;
+        default: return narrow ? k_z_step_multi<32, uint16_t> : k_z_step_multi<32, uint32_t>;
     }
 }
 
 static void launch_z_step_multi(const BatchLaunch &b, const int2 *items, int n, cudaStream_t st) {
-    const size_t smem = z_step_smem(b.kmax, b.z_warps);
-    switch (z_lane_topics(b.kmax)) {
-        case 8: k_z_step_multi<8><<<b.z_grid, 32 * b.z_warps, smem, st>>>(b.z, items, n, b.work + 1, b.kmax); break;
-        case 16: k_z_step_multi<16><<<b.z_grid, 32 * b.z_warps, smem, st>>>(b.z, items, n, b.work + 1, b.kmax); break;
-        default: k_z_step_multi<32><<<b.z_grid, 32 * b.z_warps, smem, st>>>(b.z, items, n, b.work + 1, b.kmax); break;
-    }
+    ZMultiKernel kern = z_multi_kernel(b.kmax, b.narrow != 0);
+    kern<<<b.z_grid, 32 * b.z_warps, z_step_smem(b.kmax, b.z_warps, b.narrow != 0), st>>>(b.z, items, n, b.work + 1,
+                                                                                       b.kmax);
 }
 
 void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st) {
@@ -1353,7 +1386,7 @@ __global__ void k_barrier_selftest(GridBarrier *bar, unsigned expect, int rounds
     }
 }
 
-template <int TPL>
+template <int TPL, typename CT>
 __global__ void __launch_bounds__(kPersistThreads, PULDA_PERSIST_MINB) k_batch_sweep_persistent(BatchLaunch b) {
     extern __shared__ uint32_t psm[];
     __shared__ int scan_tmp[kPersistThreads / 32 + 1];
@@ -1407,8 +1440,8 @@ __global__ void __launch_bounds__(kPersistThreads, PULDA_PERSIST_MINB) k_batch_s
     // z-step, one warp per (chain, document), longest first
     {
         const int lane = threadIdx.x & 31;
-        uint32_t *m = psm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(b.kmax);
-        u64 *wcnt = z_warp_counters(m, b.kmax);
+        uint32_t *m = psm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words_t<CT>(b.kmax);
+        u64 *wcnt = z_warp_counters_t<CT>(m, b.kmax);
         zero_warp_counters(wcnt);
         for (;;) {
             int item = 0;
@@ -1420,7 +1453,7 @@ __global__ void __launch_bounds__(kPersistThreads, PULDA_PERSIST_MINB) k_batch_s
             const int64_t s0 = a.doc_off[it.y];
             DocRun r{a.w + s0, a.z + s0, static_cast<int>(a.doc_off[it.y + 1] - s0), a.seed, a.index_base + s0,
                      sweep_of(a), 0, a.doc_off[it.y + 1] - s0, 1};
-            z_doc_warp_t<TPL>(a, m, r, wcnt, nullptr);
+            z_doc_warp_t<TPL, CT>(a, m, r, wcnt, nullptr);
             flush_warp_counters(a.stats, wcnt);
         }
     }
@@ -1441,21 +1474,25 @@ cudaError_t launch_barrier_selftest(GridBarrier *bar, int blocks, int missing, i
                               passed);
 }
 
-size_t batch_persistent_smem(int kmax) {
+size_t batch_persistent_smem(int kmax, bool narrow) {
     return std::max({phi_counts_smem(kmax), sizeof(uint32_t) * static_cast<size_t>(kmax),
-                     z_step_smem(kmax, kPersistWarps)});
+                     z_step_smem(kmax, kPersistWarps, narrow)});
 }
 
-static auto persistent_kernel(int kmax) {
-    const int tpl = z_lane_topics(kmax);
-    return tpl == 8 ? k_batch_sweep_persistent<8> : tpl == 16 ? k_batch_sweep_persistent<16> : k_batch_sweep_persistent<32>;
+using PersistKernel = void (*)(BatchLaunch);
+static PersistKernel persistent_kernel(int kmax, bool narrow) {
+    switch (z_lane_topics(kmax)) {
+        case 8: return narrow ? k_batch_sweep_persistent<8, uint16_t> : k_batch_sweep_persistent<8, uint32_t>;
+        case 16: return narrow ? k_batch_sweep_persistent<16, uint16_t> : k_batch_sweep_persistent<16, uint32_t>;
+        default: return narrow ? k_batch_sweep_persistent<32, uint16_t> : k_batch_sweep_persistent<32, uint32_t>;
+    }
 }
 
-int batch_persistent_blocks_per_sm(int kmax) {
-    auto *kern = persistent_kernel(kmax);
+int batch_persistent_blocks_per_sm(int kmax, bool narrow) {
+    PersistKernel kern = persistent_kernel(kmax, narrow);
     allow_dynamic_smem(kern);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kPersistThreads, batch_persistent_smem(kmax));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kPersistThreads, batch_persistent_smem(kmax, narrow));
     return n;
 }
 
@@ -1463,14 +1500,14 @@ cudaError_t launch_batch_sweep_persistent(const BatchLaunch &b, cudaStream_t st)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(b.persist_grid));
     cfg.blockDim = dim3(kPersistThreads);
-    cfg.dynamicSmemBytes = batch_persistent_smem(b.kmax);
+    cfg.dynamicSmemBytes = batch_persistent_smem(b.kmax, b.narrow != 0);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, persistent_kernel(b.kmax), b);
+    return cudaLaunchKernelEx(&cfg, persistent_kernel(b.kmax, b.narrow != 0), b);
 }
 
 int batch_phi_blocks_per_sm(int kmax) {
@@ -1480,12 +1517,11 @@ int batch_phi_blocks_per_sm(int kmax) {
     return n > 0 ? n : 1;
 }
 
-int batch_z_blocks_per_sm(int kmax, int warps) {
-    const int tpl = z_lane_topics(kmax);
-    auto *kern = tpl == 8 ? k_z_step_multi<8> : tpl == 16 ? k_z_step_multi<16> : k_z_step_multi<32>;
+int batch_z_blocks_per_sm(int kmax, int warps, bool narrow) {
+    ZMultiKernel kern = z_multi_kernel(kmax, narrow);
     allow_dynamic_smem(kern);
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * warps, z_step_smem(kmax, warps));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * warps, z_step_smem(kmax, warps, narrow));
     return n > 0 ? n : 1;
 }
 

@@ -177,6 +177,7 @@ struct ZArgs {
     const uint32_t *sweep_ptr;  // if set, the sweep counter is read here (graph replay)
     int64_t index_base;         // RNG index of token 0
     int path;                   // 0 auto, 1 column, 2 document topics
+    int narrow;                 // 1: every document of the launch has fewer than 2^16 tokens (16-bit counts)
     int *work;
     unsigned long long *stats;
 };
@@ -209,16 +210,19 @@ constexpr int64_t kCoopAutoDivGrouped = PULDA_COOP_DIV_GROUPED;
 // Pass-start topic counts of the documents that the z-step takes in slices.
 void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int n, const int16_t *z, int K,
                          uint32_t *m0, cudaStream_t st);
-size_t z_step_smem(int K, int warps_per_block);
+size_t z_step_smem(int K, int warps_per_block, bool narrow = false);
 size_t phi_counts_smem(int K);
 void launch_doc_topic(const int64_t *doc_off, int64_t D, const int16_t *z, int K, int32_t *m_dk, cudaStream_t st);
 void launch_n_dense(const PhiArgs &a, int32_t *n_kv, cudaStream_t st);
 void launch_phi_values(const PhiArgs &a, float *phi, cudaStream_t st);
-int z_step_blocks_per_sm(int K, int warps_per_block);
+int z_step_blocks_per_sm(int K, int warps_per_block, bool narrow = false);
 // Grouped z-step (zgroup.cu): 4 documents per warp, 8 lanes each, K <=
 // kMaxKBitmap, documents of at most kMaxGroupDocLen tokens, every word with a
 // dense q row; the warps of a CTA are z_groups_warps().
 constexpr int kMaxGroupDocLen = 65535;
+// A one-warp z-step launch whose documents have at most this many tokens each
+// keeps m_d's counts in 16 bits (ZArgs::narrow).
+constexpr int64_t kNarrowMaxLen = 65535;
 void launch_z_step_groups(const ZArgs &a, int grid, cudaStream_t st);
 int z_groups_blocks_per_sm(int K);
 int phi_counts_blocks_per_sm(int K);
@@ -269,6 +273,7 @@ struct BatchLaunch {
     uint32_t *sweep;             // shared sweep counter, advanced by the first launch
     int *work;                   // [4] dynamic work queues
     int kmax;                    // largest K of the chains
+    int narrow;                  // 1: every document of every chain has fewer than 2^16 tokens
     int phi_grid, z_grid, z_warps;
     // the first n_coop z_items go to the cooperative z-step on `st`, the rest
     // to the one-warp kernel on stream2 (forked and joined with the events)
@@ -284,13 +289,13 @@ void launch_batch_sweep(const BatchLaunch &b, cudaStream_t st);
 // document one per warp); needs persist_grid <= SMs x
 // batch_persistent_blocks_per_sm(kmax).
 cudaError_t launch_batch_sweep_persistent(const BatchLaunch &b, cudaStream_t st);
-int batch_persistent_blocks_per_sm(int kmax);
+int batch_persistent_blocks_per_sm(int kmax, bool narrow);
 // The grid barrier's self-test: `blocks` resident CTAs pass `rounds`
 // barriers that expect blocks + missing arrivals.
 cudaError_t launch_barrier_selftest(GridBarrier *bar, int blocks, int missing, int rounds, unsigned long long *err,
                                     unsigned *passed, cudaStream_t st);
 int batch_phi_blocks_per_sm(int kmax);
-int batch_z_blocks_per_sm(int kmax, int warps);
+int batch_z_blocks_per_sm(int kmax, int warps, bool narrow);
 int batch_coop_blocks_per_sm(int kmax);
 size_t z_coop_multi_smem(int kmax);
 // The cooperative z-step over (chain, document) items (coop.cu).

@@ -84,6 +84,27 @@ __device__ __forceinline__ unsigned long long *z_warp_counters(uint32_t *m, int 
     return reinterpret_cast<unsigned long long *>(m + z_m_words(K) + 32 * kTokRecWords);
 }
 
+// The one-warp z-step holds m_d's counts as CT: 32-bit, or 16-bit when every
+// document of the launch has fewer than 65,536 tokens (half the shared
+// memory, which leaves L1 more room).  The same three sizes for CT: count
+// words (the counts, their gap words and a leading zero, in 32-bit words,
+// rounded up to 16 bytes), the warp's whole region, and its counters.
+template <typename CT>
+__host__ __device__ __forceinline__ int z_count_words(int K) {
+    return sizeof(CT) == 4 ? z_m_words(K) : ((K + (K >> 5) + 32 + 2 + 1) / 2 + 3) & ~3;
+}
+template <typename CT>
+__host__ __device__ __forceinline__ int z_warp_words_t(int K) {
+    return z_count_words<CT>(K) + 32 * kTokRecWords + kWarpCountWords;
+}
+template <typename CT>
+__device__ __forceinline__ unsigned long long *z_warp_counters_t(uint32_t *m, int K) {
+    return reinterpret_cast<unsigned long long *>(m + z_count_words<CT>(K) + 32 * kTokRecWords);
+}
+__host__ __device__ __forceinline__ int z_warp_words_n(int K, bool narrow) {
+    return narrow ? z_warp_words_t<uint16_t>(K) : z_warp_words_t<uint32_t>(K);
+}
+
 // Counters of a z-step warp.  The warp-uniform ones are held one per lane
 // (lane j holds counter j), which keeps five 64-bit values out of every
 // lane's registers; the intersection size is summed per lane.

@@ -88,6 +88,19 @@ def test_documents_longer_than_the_grouped_kernel_takes(path):
     s.close()
 
 
+@pytest.mark.parametrize("K", [1, 40])
+@pytest.mark.parametrize("longest", [70000, 65535])
+def test_count_width_of_the_one_warp_z_step(longest, K):
+    """Every document on the one-warp kernel (no cooperative CTAs): with one
+    of 70,000 tokens the launch keeps 32-bit counts, with the longest at
+    65,535 tokens 16-bit ones -- at K = 1 a count reaches 65,535."""
+    rng = np.random.default_rng(longest + K)
+    lengths = np.concatenate([[longest, 65535], rng.integers(1, 300, size=30)])
+    w, off = corpus_from_lengths(rng, lengths, 400)
+    s, _ = lockstep(w, off, K, 400, 0.1, 0.01, seed=6, sweeps=2, check_counts_every=2, coop_min_len=-1)
+    s.close()
+
+
 def test_ragged_and_degenerate_inputs():
     """Empty documents, unused words (empty Phi columns keep their tokens'
     topics), a long document spanning many 32-token batches, and tiny V with
