@@ -1095,15 +1095,15 @@ __global__ void k_batch_begin_sweep(const PhiArgs *chains, int n_chains, uint32_
 // With window_ns > 0 a slot also stops at the first 32-token block boundary
 // window_ns after its warp took it up, having done at least one block (a slot
 // taken up in a later wave of a crowded launch gets the same time as the first).
-template <int TPL>
+template <int TPL, typename CT>
 __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSlot *slots, const int32_t *active,
                                                                      int n_active, const int32_t *arena_w,
                                                                      int16_t *arena_z, int64_t slice, int *work,
                                                                      uint64_t window_ns) {
     extern __shared__ uint32_t zsm[];
     const int lane = threadIdx.x & 31;
-    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words(a.K);
-    u64 *wcnt = z_warp_counters(m, a.K);
+    uint32_t *m = zsm + static_cast<size_t>(threadIdx.x >> 5) * z_warp_words_t<CT>(a.K);
+    u64 *wcnt = z_warp_counters_t<CT>(m, a.K);
     zero_warp_counters(wcnt);
     for (;;) {
         int item = 0;
@@ -1131,7 +1131,7 @@ __global__ void __launch_bounds__(32 * kZWarps, 7) k_serve_step(ZArgs a, ServeSl
         }
         DocRun r{arena_w + sl.off, z, sl.len, sl.seed, 0, sweep, pos, slice,
                  static_cast<int>(sl.sweep_end - sweep), deadline};
-        z_doc_warp_t<TPL, uint32_t>(a, m, r, wcnt, nullptr);
+        z_doc_warp_t<TPL, CT>(a, m, r, wcnt, nullptr);
         if (lane == 0) {
             slots[idx].sweep = r.sweep;
             slots[idx].pos = r.pos;
@@ -1525,22 +1525,31 @@ int batch_z_blocks_per_sm(int kmax, int warps, bool narrow) {
     return n > 0 ? n : 1;
 }
 
+using ServeKernel = void (*)(ZArgs, ServeSlot *, const int32_t *, int, const int32_t *, int16_t *, int64_t, int *,
+                            uint64_t);
+static ServeKernel serve_kernel(int K, bool narrow) {
+    switch (z_lane_topics(K)) {
+        case 8: return narrow ? k_serve_step<8, uint16_t> : k_serve_step<8, uint32_t>;
+        case 16: return narrow ? k_serve_step<16, uint16_t> : k_serve_step<16, uint32_t>;
+        default: return narrow ? k_serve_step<32, uint16_t> : k_serve_step<32, uint32_t>;
+    }
+}
+
 void launch_serve_step(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active, const int32_t *arena_w,
                        int16_t *arena_z, int64_t slice, int *work, int warps_per_block, int grid, uint64_t window_ns,
-                       cudaStream_t st) {
+                       bool narrow, cudaStream_t st) {
     if (n_active <= 0) return;
     cudaMemsetAsync(work, 0, sizeof(int), st);
     const int need = (n_active + warps_per_block - 1) / warps_per_block;
-    const int tpl = z_lane_topics(a.K);
-    auto *kern = tpl == 8 ? k_serve_step<8> : tpl == 16 ? k_serve_step<16> : k_serve_step<32>;
-    kern<<<std::min(grid, need), 32 * warps_per_block, z_step_smem(a.K, warps_per_block), st>>>(
+    ServeKernel kern = serve_kernel(a.K, narrow);
+    kern<<<std::min(grid, need), 32 * warps_per_block, z_step_smem(a.K, warps_per_block, narrow), st>>>(
         a, slots, active, n_active, arena_w, arena_z, slice, work, window_ns);
 }
 
 int serve_blocks_per_sm(int K, int warps_per_block) {
-    const int tpl = z_lane_topics(K);
-    auto *kern = tpl == 8 ? k_serve_step<8> : tpl == 16 ? k_serve_step<16> : k_serve_step<32>;
-    allow_dynamic_smem(kern);
+    // the 32-bit instantiation: its shared memory bounds the 16-bit one's
+    for (bool narrow : {true, false}) allow_dynamic_smem(serve_kernel(K, narrow));
+    ServeKernel kern = serve_kernel(K, false);
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * warps_per_block, z_step_smem(K, warps_per_block));
     return n > 0 ? n : 1;

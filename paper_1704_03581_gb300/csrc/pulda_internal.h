@@ -314,9 +314,10 @@ struct ServeSlot {
 // Each active slot advances by up to `slice` tokens, one warp per slot; with
 // window_ns > 0 also stopping at the first 32-token block boundary window_ns
 // after the launch starts (every slot does at least one block).
+// `narrow`: every active request of the launch has at most kNarrowMaxLen tokens.
 void launch_serve_step(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active, const int32_t *arena_w,
                        int16_t *arena_z, int64_t slice, int *work, int warps_per_block, int grid, uint64_t window_ns,
-                       cudaStream_t st);
+                       bool narrow, cudaStream_t st);
 int serve_blocks_per_sm(int K, int warps_per_block);
 // The same with one CTA (the cooperative z-step) per slot, for long requests.
 void launch_serve_step_coop(const ZArgs &a, ServeSlot *slots, const int32_t *active, int n_active,

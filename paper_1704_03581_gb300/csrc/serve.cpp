@@ -199,8 +199,12 @@ void worker_loop(pulda_server *s) {
         for (int32_t slot : s->active)
             if (coop && s->h_slots_len[slot] >= s->coop_len) s->h_active[nc++] = slot;
         int j = nc;
+        bool narrow = true;     // every request on the one-warp kernel fits 16-bit counts
         for (int32_t slot : s->active)
-            if (!(coop && s->h_slots_len[slot] >= s->coop_len)) s->h_active[j++] = slot;
+            if (!(coop && s->h_slots_len[slot] >= s->coop_len)) {
+                s->h_active[j++] = slot;
+                narrow = narrow && s->h_slots_len[slot] <= kNarrowMaxLen;
+            }
         if (!check(s, cudaMemcpyAsync(s->d_active, s->h_active, sizeof(int32_t) * n, cudaMemcpyHostToDevice,
                                       s->stream), "upload of the active list")) return;
         cudaEventRecord(s->ev0, s->stream);
@@ -210,12 +214,12 @@ void worker_loop(pulda_server *s) {
                                    s->d_work + 1, s->coop_grid, s->window_ns, s->stream);
             cudaStreamWaitEvent(s->stream2, s->ev_fork, 0);
             launch_serve_step(s->tabs, s->d_slots, s->d_active + nc, n - nc, s->arena_w, s->arena_z, s->slice,
-                              s->d_work, s->z_warps, s->grid, s->window_ns, s->stream2);
+                              s->d_work, s->z_warps, s->grid, s->window_ns, narrow, s->stream2);
             cudaEventRecord(s->ev_join, s->stream2);
             cudaStreamWaitEvent(s->stream, s->ev_join, 0);
         } else {
             launch_serve_step(s->tabs, s->d_slots, s->d_active, n, s->arena_w, s->arena_z, s->slice, s->d_work,
-                              s->z_warps, s->grid, s->window_ns, s->stream);
+                              s->z_warps, s->grid, s->window_ns, narrow, s->stream);
         }
         if (!check(s, cudaGetLastError(), "serving launch")) return;
         cudaEventRecord(s->ev1, s->stream);
