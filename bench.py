@@ -262,8 +262,8 @@ def issue_roofline(tokens_per_s: float, sm_mhz: float | None) -> dict | None:
 
 
 def z_bytes(tokens: int, sum_min: int, a_branch: int, docs: int) -> int:
-    """Algorithmic HBM bytes of z-steps over `tokens` tokens, the survey's
-    model of what the method must touch: per token the word id (4), its topic
+    """Algorithmic HBM bytes of z-steps over `tokens` tokens, a model of what
+    the method must touch: per token the word id (4), its topic
     in and out (2+2) and sigma_a of its word (4); per element of the smaller
     of the document's and the word's nonzero topics one topic id and one
     weight (2+4) -- min(K_d, K_v) of them (complexity theorem); per alias draw

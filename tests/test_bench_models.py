@@ -1,4 +1,4 @@
-"""bench.py's byte models and roofline arithmetic, on CPU: the survey's
+"""bench.py's byte models and roofline arithmetic, on CPU: the
 algorithmic bytes of a z-step and of a Phi-step, and the fractions built on
 them (the GPU line's values come from these functions)."""
 import os
@@ -12,7 +12,7 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_z_step_bytes_follow_the_survey_model():
+def test_z_step_bytes_follow_the_algorithmic_model():
     # per token 4 (word) + 2 + 2 (topic in, out) + 4 (sigma_a); 6 per min(K_d, K_v)
     # element; 8 per alias draw; 8 per document
     assert bench.z_bytes(1, 0, 0, 0) == 12
