@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=10, help="batched keys: timed sweeps of each arm")
     ap.add_argument("--batch-form", type=int, default=0, choices=[0, 1, 2],
                     help="batched launch form: 0 tuned, 1 six launches per sweep, 2 one persistent launch")
+    ap.add_argument("--alias-layout", type=int, default=0, choices=[0, 1, 2],
+                    help="alias tables: 1 threshold and topic arrays, 2 packed slots, 0 = arrays for the sweep "
+                         "form and tuned for the batched one")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--docs-per-warp", type=int, default=0, help="z-step documents per warp: 0 auto, 1 or 4")
     ap.add_argument("--phi-mode", type=int, default=0, choices=[0, 1],
@@ -379,7 +382,7 @@ def run_pulda(args, corpus, rank: int, world: int):
     s = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                   stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp,
                   phi_mode=args.phi_mode, slice_len=args.slice_len, coop_min_len=args.coop_min_len,
-                  count_path=args.count_path)
+                  count_path=args.count_path, alias_layout=args.alias_layout)
     layout = s.z_layout()
     s.sweep(args.burnin + args.warmup)
     s.sync()
@@ -438,7 +441,7 @@ def run_pulda(args, corpus, rank: int, world: int):
         t0 = time.perf_counter()
         s2 = P.Sampler(corpus.w, corpus.doc_off, K_TOPICS, corpus.V, ALPHA, BETA, seed=rank,
                        stream=stream.cuda_stream, docs_per_warp=args.docs_per_warp, phi_mode=args.phi_mode,
-                       slice_len=args.slice_len, coop_min_len=args.coop_min_len)
+                       slice_len=args.slice_len, coop_min_len=args.coop_min_len, alias_layout=args.alias_layout)
         s2.sync()
         t_init = time.perf_counter() - t0
         stats_bytes = ctypes.sizeof(P.SweepStats)
@@ -460,7 +463,8 @@ def run_pulda(args, corpus, rank: int, world: int):
 
     batched = None
     if world == 1 and not args.no_batched:
-        batched = batched_probe(args.batch_scale, args.batch_steps, 8, args.coop_min_len, batch_form=args.batch_form)
+        batched = batched_probe(args.batch_scale, args.batch_steps, 12, args.coop_min_len, batch_form=args.batch_form,
+                                alias_layout=args.alias_layout)
     if rank != 0:
         return
     peak, peak_kind = peaks()
@@ -501,7 +505,8 @@ def run_pulda(args, corpus, rank: int, world: int):
                    "timed_sweeps": [first_timed, first_timed + K - 1],
                    "phi": "Dirichlet (Algorithm 1)" if args.phi_mode == 1 else "Poisson Polya urn (Algorithm 2)",
                    "z": (f"documents over {args.slice_len} tokens in stale-count slices (not the paper's sampler)"
-                         if args.slice_len > 0 else "every document in order (Algorithm 2)")},
+                         if args.slice_len > 0 else "every document in order (Algorithm 2)"),
+                   "alias": "packed 8-byte slots" if args.alias_layout == 2 else "threshold and topic arrays"},
         "z_step": {"tokens_per_s": K * corpus.N / (z_ms / 1000.0), "ms_per_launch": z_ms / K,
                    "mean_min_kd_kv": sum_min / tokens, "mean_intersection": sum_int / tokens,
                    "docside_frac": docside / tokens, "a_branch_frac": a_br / tokens},
@@ -664,7 +669,7 @@ def run_sparsity(args):
 
 
 def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, clocks_too: bool = False,
-                  batch_form: int = 0) -> dict:
+                  batch_form: int = 0, alias_layout: int = 0) -> dict:
     """32 independent corpora (uneven D, N, K, V; D scaled by `scale`) advanced
     together by one CUDA-graph launch per sweep, against the same 32 chains
     run one after another through single-chain handles (each with its own
@@ -682,8 +687,9 @@ def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, cloc
               for c, sp in zip(corpora, specs)]
     N = sum(c.N for c in corpora)
     stream = torch.cuda.Stream()
-    K, W = steps, max(warmup, 8)
-    b = P.Batch(chains, stream=stream.cuda_stream, coop_min_len=coop_min_len, batch_form=batch_form)
+    K, W = steps, max(warmup, 12)
+    b = P.Batch(chains, stream=stream.cuda_stream, coop_min_len=coop_min_len, batch_form=batch_form,
+                alias_layout=alias_layout)
     b.sweep(W)                          # the first sweeps also time the tuning candidates
     b.sync()
     assert b.tuning()[2], "tuning not over after the warm-up sweeps"
@@ -700,7 +706,7 @@ def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, cloc
     b.sync()
     ms_b = e0.elapsed_time(e1)
     zb = [b.z(i) for i in range(len(chains))]
-    warps, coop_len, _, one_launch = b.tuning()
+    warps, coop_len, _, one_launch, layout = b.tuning()
     b.close()
     del b
     # the same chains, one after another, one handle each
@@ -724,6 +730,7 @@ def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, cloc
             "ms_per_sweep": ms_b / K, "sequential_tokens_per_s": N * K / (ms_s / 1000.0),
             "sequential_ms_per_sweep": ms_s / K, "speedup_vs_sequential": ms_s / ms_b,
             "identical_topics": same, "z_warps_tuned": warps, "coop_min_len_tuned": coop_len,
+            "alias_layout": "packed 8-byte slots" if layout == 2 else "threshold and topic arrays",
             "launch_form": "one persistent launch per sweep" if one_launch else "six launches per sweep (a graph)",
             "gpu_launches": (1 if one_launch else 6 + (1 if coop_len > 0 else 0)) * K, "generation_s": t_gen,
             "clocks": clk}
@@ -732,7 +739,7 @@ def batched_probe(scale: float, steps: int, warmup: int, coop_min_len: int, cloc
 def run_batched(args):
     """The batched-chains form alone (config 4)."""
     r = batched_probe(args.batch_scale, args.steps, args.warmup, args.coop_min_len, clocks_too=True,
-                      batch_form=args.batch_form)
+                      batch_form=args.batch_form, alias_layout=args.alias_layout)
     line = {
         "metric": "batched chains: tokens/s of 32 uneven chains in one graph launch per sweep vs 32 sequential "
                   "single-chain runs",
@@ -740,7 +747,8 @@ def run_batched(args):
         "ms_per_step": r["ms_per_sweep"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
         "config": {"workload": r["workload"], "N": r["N"], "z_warps_tuned": r["z_warps_tuned"],
-                   "coop_min_len_tuned": r["coop_min_len_tuned"]},
+                   "coop_min_len_tuned": r["coop_min_len_tuned"], "alias_layout": r["alias_layout"],
+                   "launch_form": r["launch_form"]},
         "sequential": {"value": r["sequential_tokens_per_s"], "ms_per_step": r["sequential_ms_per_sweep"]},
         "speedup_vs_sequential": r["speedup_vs_sequential"],
         "identical_topics": r["identical_topics"],

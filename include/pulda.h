@@ -93,6 +93,15 @@ typedef struct {
                                graph), 2 = one persistent cooperative launch whose phases are
                                separated by grid barriers (every document one per warp; not
                                with coop_min_len > 0); the chains' results are identical */
+    int32_t alias_layout;   /* how the per-word alias tables of the a part ("Efficient sampling
+                               of z") are laid out for the z-step: 1 = a threshold array and an
+                               alias-topic array beside the column's topics (two loads per
+                               alias draw), 2 = also packed 8-byte slots {threshold, topic |
+                               alias topic << 16} that the z-step reads instead (one load; 8
+                               more bytes per entry of the table capacity K V); 0 = 1 on a
+                               handle, tuned (timed on two sweeps each, after the launch
+                               form) in the batched form; the tables' contents and every
+                               result are identical */
     /* Device memory.  With alloc set, every device buffer the library takes
      * -- the handle's state in pulda_init, the temporaries of pulda_infer,
      * pulda_get_counts, pulda_get_phi and pulda_log_posterior, a server's
@@ -288,10 +297,14 @@ typedef struct pulda_batch pulda_batch;
  * every document on one warp, > 0 sends the documents at least that long (of
  * every chain) to the cooperative z-step, 0 sends those of at least
  * max(256, N / 8000) tokens (N = tokens of all chains), the single-chain rule;
- * docs_per_warp must be 0 or 1; batch_form picks the launch form (see
- * pulda_options).  Tuning times each CTA size on two real sweeps
- * (in order, then in reverse), together with the one-launch form when no
- * document goes to cooperative CTAs: it ends after sweep 8 (6 without it). */
+ * docs_per_warp must be 0 or 1; batch_form picks the launch form and
+ * alias_layout the alias tables' layout (see pulda_options).  Tuning times
+ * each CTA size on two real sweeps (in order, then in reverse), together with
+ * the one-launch form when no document goes to cooperative CTAs, then (with
+ * alias_layout 0) the best of them with each alias layout on two sweeps each:
+ * it ends after sweep 12 (10 without the one-launch form, 8 without the
+ * layouts); every chain's tables then carry the packed slots (8 bytes per
+ * entry of its K V capacity) unless alias_layout is 1. */
 pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains, int32_t n_chains,
                               const pulda_options *opt);
 /* pulda_batch_sweep -- n_sweeps sweeps of every chain (asynchronous, except
@@ -303,10 +316,12 @@ pulda_status pulda_batch_sync(pulda_batch *b);
 pulda_status pulda_batch_get_z(pulda_batch *b, int32_t chain, int16_t *z_host);
 pulda_status pulda_batch_stats(pulda_batch *b, int32_t chain, pulda_sweep_stats *out);
 /* pulda_batch_tuning -- the z-step warps per CTA and the cooperative
- * threshold in use (-1 = none), whether tuning is over, and whether a sweep
- * is one persistent launch (1) or six launches (0); any pointer may be NULL. */
+ * threshold in use (-1 = none), whether tuning is over, whether a sweep is
+ * one persistent launch (1) or six launches (0), and the alias layout in use
+ * (1 = threshold and topic arrays, 2 = packed slots; see pulda_options); any
+ * pointer may be NULL. */
 pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *coop_min_len, int32_t *tuned,
-                                int32_t *one_launch);
+                                int32_t *one_launch, int32_t *alias_layout);
 /* pulda_barrier_selftest -- checks the grid barrier of the one-launch
  * batched sweep on the current device (the paper has no counterpart: this is
  * failure detection of the launch form).  `blocks` CTAs (at most one per SM,

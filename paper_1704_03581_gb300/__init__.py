@@ -49,7 +49,7 @@ class Options(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("zstep_path", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("docs_per_warp", ctypes.c_int32), ("phi_mode", ctypes.c_int32),
                 ("slice_len", ctypes.c_int32), ("coop_min_len", ctypes.c_int32), ("count_path", ctypes.c_int32),
-                ("batch_form", ctypes.c_int32),
+                ("batch_form", ctypes.c_int32), ("alias_layout", ctypes.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -118,7 +118,7 @@ def lib() -> ctypes.CDLL:
             "pulda_batch_sync": [P],
             "pulda_batch_get_z": [P, i32, P],
             "pulda_batch_stats": [P, i32, P],
-            "pulda_batch_tuning": [P, P, P, P, P],
+            "pulda_batch_tuning": [P, P, P, P, P, P],
             "pulda_barrier_selftest": [i32, i32, i32, P],
             "pulda_serve_open": [P, i64, i32, i64, P],
             "pulda_serve_submit": [P, u64, u64, P, i32, i32, P],
@@ -163,7 +163,7 @@ def _check(h, status: int):
 def pulda_init(word_ids, doc_offsets, K: int, V: int, alpha, beta: float, seed: int, stream=None,
                zstep_path: int = 0, warps_per_block: int = 0, docs_per_warp: int = 0, phi_mode: int = 0,
                slice_len: int = 0, coop_min_len: int = 0, callbacks: tuple | None = None,
-               count_path: int = 0) -> int:
+               count_path: int = 0, alias_layout: int = 0) -> int:
     """``callbacks`` = allocator_callbacks(...) routes the handle's device memory through them."""
     w = np.ascontiguousarray(word_ids, dtype=np.int32)
     off = np.ascontiguousarray(doc_offsets, dtype=np.int64)
@@ -177,6 +177,7 @@ def pulda_init(word_ids, doc_offsets, K: int, V: int, alpha, beta: float, seed: 
     opt.slice_len = slice_len
     opt.coop_min_len = coop_min_len
     opt.count_path = count_path
+    opt.alias_layout = alias_layout
     if callbacks is not None:
         opt.alloc, opt.free = callbacks
     h = ctypes.c_void_p()
@@ -343,13 +344,14 @@ class Sampler:
     def __init__(self, word_ids, doc_offsets, K: int, V: int, alpha=0.1, beta: float = 0.01, seed: int = 0,
                  stream=None, zstep_path: int = 0, warps_per_block: int = 0, docs_per_warp: int = 0,
                  phi_mode: int = 0, slice_len: int = 0, coop_min_len: int = 0, allocator=None,
-                 count_path: int = 0):
+                 count_path: int = 0, alias_layout: int = 0):
         """phi_mode 0: Poisson Polya urn (Algorithm 2); 1: Dirichlet Phi (Algorithm 1).
         slice_len > 0: documents longer than it resampled in concurrent stale-count slices (not the paper's).
         coop_min_len: documents at least this long resampled by a whole CTA (0 = automatic, -1 = never);
         the topics are the same either way.  allocator: an object with alloc(nbytes, stream) -> device
         pointer (0 if it cannot) and free(ptr, stream) that supplies every device buffer of the handle,
-        its temporaries and its servers (see pulda_options in include/pulda.h)."""
+        its temporaries and its servers (see pulda_options in include/pulda.h).  alias_layout 2: the
+        z-step reads packed alias slots (0 or 1: threshold and topic arrays); results are identical."""
         self.K, self.V = K, V
         self.phi_mode = phi_mode
         self.N = int(np.asarray(doc_offsets)[-1])
@@ -357,7 +359,8 @@ class Sampler:
         self.h = None
         self._callbacks = allocator_callbacks(allocator) if allocator is not None else None
         self.h = pulda_init(word_ids, doc_offsets, K, V, alpha, beta, seed, stream, zstep_path, warps_per_block,
-                            docs_per_warp, phi_mode, slice_len, coop_min_len, self._callbacks, count_path)
+                            docs_per_warp, phi_mode, slice_len, coop_min_len, self._callbacks, count_path,
+                            alias_layout)
 
     def close(self):
         if self.h:
@@ -435,8 +438,9 @@ def _bcheck(b, status: int):
 
 
 def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0,
-                     callbacks: tuple | None = None, batch_form: int = 0):
+                     callbacks: tuple | None = None, batch_form: int = 0, alias_layout: int = 0):
     """chains: dicts with w, doc_off, K, V, alpha, beta, seed.  coop_min_len: 0 tuned, -1 never, > 0 fixed.
+    alias_layout: 0 tuned, 1 threshold and topic arrays, 2 packed slots.
     callbacks = allocator_callbacks(...) routes every device buffer of the batch through them."""
     keep = []
     arr = (ChainDesc * len(chains))()
@@ -452,6 +456,7 @@ def pulda_batch_init(chains: list[dict], stream=None, warps_per_block: int = 0, 
     opt.warps_per_block = warps_per_block
     opt.coop_min_len = coop_min_len
     opt.batch_form = batch_form
+    opt.alias_layout = alias_layout
     if callbacks is not None:
         opt.alloc, opt.free = callbacks
     b = ctypes.c_void_p()
@@ -478,11 +483,13 @@ def pulda_batch_stats(b, chain: int) -> dict:
     return s.as_dict()
 
 
-def pulda_batch_tuning(b) -> tuple[int, int, bool, bool]:
-    """(z-step warps per CTA, cooperative threshold or -1, tuning over, one persistent launch per sweep)."""
-    w, c, t, o = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
-    _bcheck(b, lib().pulda_batch_tuning(b, ctypes.byref(w), ctypes.byref(c), ctypes.byref(t), ctypes.byref(o)))
-    return w.value, c.value, bool(t.value), bool(o.value)
+def pulda_batch_tuning(b) -> tuple[int, int, bool, bool, int]:
+    """(z-step warps per CTA, cooperative threshold or -1, tuning over, one persistent launch per sweep,
+    alias layout: 1 arrays, 2 packed slots)."""
+    w, c, t, o, al = (ctypes.c_int32(0) for _ in range(5))
+    _bcheck(b, lib().pulda_batch_tuning(b, ctypes.byref(w), ctypes.byref(c), ctypes.byref(t), ctypes.byref(o),
+                                        ctypes.byref(al)))
+    return w.value, c.value, bool(t.value), bool(o.value), al.value
 
 
 def pulda_barrier_selftest(blocks: int, missing: int, rounds: int = 4) -> tuple[int, int]:
@@ -506,12 +513,14 @@ class Batch:
     """Many chains advanced together: ``Batch(chains).sweep(n)``."""
 
     def __init__(self, chains: list[dict], stream=None, warps_per_block: int = 0, coop_min_len: int = 0,
-                 allocator=None, batch_form: int = 0):
-        """batch_form 0: the launch form is tuned; 1: six launches per sweep; 2: one persistent launch."""
+                 allocator=None, batch_form: int = 0, alias_layout: int = 0):
+        """batch_form 0: the launch form is tuned; 1: six launches per sweep; 2: one persistent launch.
+        alias_layout 0: tuned; 1: threshold and topic arrays; 2: packed slots."""
         self.sizes = [int(np.asarray(c["doc_off"])[-1]) for c in chains]
         self.b = None
         self._callbacks = allocator_callbacks(allocator) if allocator is not None else None
-        self.b = pulda_batch_init(chains, stream, warps_per_block, coop_min_len, self._callbacks, batch_form)
+        self.b = pulda_batch_init(chains, stream, warps_per_block, coop_min_len, self._callbacks, batch_form,
+                                  alias_layout)
 
     def close(self):
         if self.b:

@@ -245,7 +245,7 @@ PhiArgs phi_args(pulda_handle *h) {
     a.nst_k = h->nst_k; a.nst_n = h->nst_n; a.nnz_n = h->nnz_n;
     a.cst_k = h->cst_k; a.cst_c = h->cst_c; a.nnz_c = h->nnz_c;
     a.S = h->S; a.rowbuf = h->rowbuf; a.col_ptr = h->col_ptr;
-    a.topic = h->topic; a.c = h->c; a.q = h->q; a.athr = h->athr; a.atopic = h->atopic;
+    a.topic = h->topic; a.c = h->c; a.q = h->q; a.athr = h->athr; a.atopic = h->atopic; a.apack = h->apack;
     a.A = h->A; a.vose_p = h->vose_p; a.vose_stack = h->vose_stack; a.bits = h->bits; a.KW = h->KW; a.KWp = h->KWp;
     a.qdense = h->qdense; a.dense_slot = h->dense_slot;
     a.alpha = h->alpha; a.work = h->work; a.stats = h->stats;
@@ -259,6 +259,7 @@ ZArgs z_args(pulda_handle *h, const int64_t *doc_off, const int32_t *doc_order, 
     ZArgs a{};
     a.doc_off = doc_off; a.doc_order = doc_order; a.D = D; a.w = w; a.z = z;
     a.col_ptr = h->col_ptr; a.topic = h->topic; a.q = h->q; a.A = h->A; a.athr = h->athr; a.atopic = h->atopic;
+    a.apack = h->apack;
     a.bits = h->bits; a.K = h->K; a.KW = h->KW; a.KWp = h->KWp; a.seed = seed; a.sweep = sweep; a.index_base = index_base;
     a.qdense = h->qdense; a.dense_slot = h->dense_slot;
     a.path = h->opt.zstep_path; a.work = h->work + 1; a.stats = h->stats;
@@ -330,6 +331,10 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
         fail(h, PULDA_ERR_INVALID, "slice_len must be >= 0, and slices need docs_per_warp 0 or 1");
         return reject(PULDA_ERR_INVALID);
     }
+    if (h->opt.alias_layout < 0 || h->opt.alias_layout > 2) {
+        fail(h, PULDA_ERR_INVALID, "alias_layout must be 0 (default), 1 (threshold and topic arrays) or 2 (packed slots)");
+        return reject(PULDA_ERR_INVALID);
+    }
     if (h->opt.count_path != 0 && h->opt.count_path != 1) {
         fail(h, PULDA_ERR_INVALID, "count_path must be 0 (histogram) or 1 (sort)");
         return reject(PULDA_ERR_INVALID);
@@ -374,6 +379,7 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     ALLOC(h->cst_k, h->cap); ALLOC(h->cst_c, h->cap); ALLOC(h->nnz_c, V);
     ALLOC(h->S, K); ALLOC(h->rowbuf, V); ALLOC(h->col_ptr, V + 1);
     ALLOC(h->topic, h->cap); ALLOC(h->c, h->cap); ALLOC(h->q, h->cap); ALLOC(h->athr, h->cap); ALLOC(h->atopic, h->cap);
+    if (h->opt.alias_layout == 2) ALLOC(h->apack, h->cap);
     ALLOC(h->A, V); ALLOC(h->vose_p, h->cap); ALLOC(h->vose_stack, h->cap);
     if (K <= kMaxKBitmap) ALLOC(h->bits, static_cast<size_t>(V) * h->KWp);
     if (h->opt.phi_mode == 1) {

@@ -31,14 +31,22 @@ struct pulda_batch {
     // The candidates are timed twice, in order and then in reverse, so the
     // falling cost of the first sweeps after the uniform start does not favour
     // the candidates timed later.
-    struct Cand { int warps; int64_t coop_len; bool one_launch; };
+    struct Cand { int warps; int64_t coop_len; bool one_launch; bool packed; };
     std::vector<Cand> cand;
     std::vector<float> cand_ms;     // summed over the candidate's timed sweeps
     std::vector<int> sched;         // candidate indices still to time in this phase
     size_t sched_pos = 0;
     int phase_first = 0;            // first candidate index of the current phase
     bool tuned = false;
+    // the alias layout is timed after the launch form: the best form with the
+    // threshold and topic arrays, then with the packed slots
+    bool tune_layout = false, layout_phase = false;
     bool one_launch = false;        // in use: one persistent launch per sweep
+    bool packed = false;            // in use: the chains' tables carry packed alias slots
+    std::vector<PhiArgs> hp;        // the chains' descriptors (host copies of phi / z below)
+    std::vector<ZArgs> hz;
+    PhiArgs *d_phi = nullptr;
+    ZArgs *d_z = nullptr;
     int64_t coop_len = 0;           // in use
     std::vector<int64_t> dlen;      // document lengths in work-list order (longest first)
     cudaGraph_t graph = nullptr;
@@ -91,12 +99,28 @@ void schedule_phase(pulda_batch *b, int first) {
     b->cand_ms.resize(b->cand.size(), 0.0f);
 }
 
-void apply_candidate(pulda_batch *b, const pulda_batch::Cand &c) {
+// Puts candidate c in use.  A change of alias layout rewrites the chains'
+// descriptors on the stream, before the next sweep's launches: a sweep's
+// Phi-step writes the packed slots when its descriptor has them, and its
+// z-step reads whichever layout its own descriptor names.
+cudaError_t apply_candidate(pulda_batch *b, const pulda_batch::Cand &c) {
     b->bl.z_warps = c.warps;
     b->bl.z_grid = b->sms * batch_z_blocks_per_sm(b->bl.kmax, c.warps, b->bl.narrow != 0);
     b->coop_len = c.coop_len;
     b->bl.n_coop = count_coop_items(b, c.coop_len);
     b->one_launch = c.one_launch;
+    if (c.packed == b->packed) return cudaSuccess;
+    for (size_t i = 0; i < b->ch.size(); ++i) {
+        b->hp[i].apack = c.packed ? b->ch[i]->apack : nullptr;
+        b->hz[i].apack = c.packed ? b->ch[i]->apack : nullptr;
+    }
+    const size_t n = b->ch.size();
+    cudaError_t e = cudaMemcpyAsync(b->d_phi, b->hp.data(), sizeof(PhiArgs) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_z, b->hz.data(), sizeof(ZArgs) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // the host copies may change again
+    if (e == cudaSuccess) b->packed = c.packed;
+    return e;
 }
 
 pulda_status launch_one_sweep(pulda_batch *b) {
@@ -159,6 +183,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = "batch_form must be 0 (tuned), 1 (six launches) or 2 (one launch, without coop_min_len > 0)";
         return bail(PULDA_ERR_INVALID);
     }
+    if (o.alias_layout < 0 || o.alias_layout > 2) {
+        b->err = "alias_layout must be 0 (tuned), 1 (threshold and topic arrays) or 2 (packed slots)";
+        return bail(PULDA_ERR_INVALID);
+    }
     if (o.warps_per_block < 0 || o.warps_per_block > kMultiWarps) {
         b->err = "warps_per_block must be in [0, " + std::to_string(kMultiWarps) + "] (got " +
                  std::to_string(o.warps_per_block) + ")";
@@ -180,6 +208,7 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     pulda_options oc = o;
     oc.warps_per_block = 0;
     oc.coop_min_len = -1;
+    oc.alias_layout = o.alias_layout == 1 ? 1 : 2;     // the packed slots whenever they may be used
     for (int32_t c = 0; c < n_chains; ++c) {
         const pulda_chain_desc &d = chains[c];
         pulda_handle *h = nullptr;
@@ -207,8 +236,13 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         b->err = std::string("device allocation of the batch descriptors failed: ") + cudaGetErrorString(ea);
         return bail(ea == cudaErrorMemoryAllocation ? PULDA_ERR_OOM : PULDA_ERR_CUDA);
     }
-    std::vector<PhiArgs> hp(n_chains);
-    std::vector<ZArgs> hz(n_chains);
+    std::vector<PhiArgs> &hp = b->hp;
+    std::vector<ZArgs> &hz = b->hz;
+    hp.resize(n_chains);
+    hz.resize(n_chains);
+    b->d_phi = d_phi;
+    b->d_z = d_z;
+    b->packed = o.alias_layout == 2;
     std::vector<HeavyChunk> heavy;
     std::vector<std::pair<int64_t, int2>> wi, di;    // (weight, (chain, item))
     int kmax = 1;
@@ -219,6 +253,10 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
         hp[c].sweep_ptr = d_sweep;
         hz[c] = z_args(h, h->doc_off, h->doc_order, h->D, h->w, h->z, h->seed, 0, 0);
         hz[c].sweep_ptr = d_sweep;
+        if (!b->packed) {               // the launch forms are timed with the arrays
+            hp[c].apack = nullptr;
+            hz[c].apack = nullptr;
+        }
         kmax = std::max(kmax, h->K);
         narrow = narrow && h->narrow_all;
         for (HeavyChunk hc : h->heavy_chunks) {
@@ -301,23 +339,35 @@ pulda_status pulda_batch_init(pulda_batch **out, const pulda_chain_desc *chains,
     // Launch forms: six launches per sweep with a CTA size for the z-step, and
     // (without cooperative CTAs) one persistent launch; tuned forms are timed.
     const bool one_ok = bl.persist_grid > 0 && fixed_coop == 0;
+    const bool pk = b->packed;
     if (o.batch_form == 2) {
         if (!one_ok) {
             b->err = "the one-launch form needs no document on cooperative CTAs and a resident grid";
             return bail(PULDA_ERR_INVALID);
         }
-        b->cand.push_back({kMultiWarps, 0, true});
+        b->cand.push_back({kMultiWarps, 0, true, pk});
     } else if (o.warps_per_block > 0) {
-        b->cand.push_back({o.warps_per_block, fixed_coop, false});
+        b->cand.push_back({o.warps_per_block, fixed_coop, false, pk});
     } else {
         for (int w : {2, 4, 8})
-            if (w <= kMultiWarps && z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back({w, fixed_coop, false});
-        if (b->cand.empty()) b->cand.push_back({1, fixed_coop, false});
+            if (w <= kMultiWarps && z_step_smem(kmax, w) <= 160 * 1024) b->cand.push_back({w, fixed_coop, false, pk});
+        if (b->cand.empty()) b->cand.push_back({1, fixed_coop, false, pk});
     }
-    if (o.batch_form == 0 && o.warps_per_block == 0 && one_ok) b->cand.push_back({kMultiWarps, 0, true});
+    if (o.batch_form == 0 && o.warps_per_block == 0 && one_ok) b->cand.push_back({kMultiWarps, 0, true, pk});
+    b->tune_layout = o.alias_layout == 0;
+    if (b->cand.size() == 1 && b->tune_layout) {
+        // one launch form: time the two layouts only
+        pulda_batch::Cand c = b->cand.front();
+        c.packed = true;
+        b->cand.push_back(c);
+        b->layout_phase = true;
+    }
     if (b->cand.size() == 1) b->tuned = true;
     else schedule_phase(b, 0);
-    apply_candidate(b, b->cand.front());
+    if (apply_candidate(b, b->cand.front()) != cudaSuccess) {
+        b->err = "uploading the batch descriptors failed";
+        return bail(PULDA_ERR_CUDA);
+    }
     if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
         cudaStreamCreateWithFlags(&bl.stream2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&bl.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -337,7 +387,7 @@ pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps) {
         if (!b->tuned) {
             // time the next scheduled candidate on a real sweep
             const int c = b->sched[b->sched_pos];
-            apply_candidate(b, b->cand[c]);
+            BCU(b, apply_candidate(b, b->cand[c]));
             BCU(b, cudaEventRecord(b->ev0, b->stream));
             pulda_status r = launch_one_sweep(b);
             if (r != PULDA_OK) return r;
@@ -350,8 +400,20 @@ pulda_status pulda_batch_sweep(pulda_batch *b, int32_t n_sweeps) {
                 int best = b->phase_first;
                 for (int k = b->phase_first; k < static_cast<int>(b->cand.size()); ++k)
                     if (b->cand_ms[k] < b->cand_ms[best]) best = k;
-                apply_candidate(b, b->cand[best]);
-                b->tuned = true;
+                if (b->tune_layout && !b->layout_phase) {
+                    // the best launch form again with each alias layout
+                    pulda_batch::Cand c0 = b->cand[best], c1 = b->cand[best];
+                    c0.packed = false;
+                    c1.packed = true;
+                    const int first = static_cast<int>(b->cand.size());
+                    b->cand.push_back(c0);
+                    b->cand.push_back(c1);
+                    b->layout_phase = true;
+                    schedule_phase(b, first);
+                } else {
+                    BCU(b, apply_candidate(b, b->cand[best]));
+                    b->tuned = true;
+                }
             }
         } else {
             if (!b->exec) {
@@ -402,9 +464,10 @@ pulda_status pulda_batch_stats(pulda_batch *b, int32_t chain, pulda_sweep_stats 
 }
 
 pulda_status pulda_batch_tuning(pulda_batch *b, int32_t *z_warps, int32_t *coop_min_len, int32_t *tuned,
-                                int32_t *one_launch) {
+                                int32_t *one_launch, int32_t *alias_layout) {
     if (!b) return PULDA_ERR_INVALID;
     if (one_launch) *one_launch = b->one_launch ? 1 : 0;
+    if (alias_layout) *alias_layout = b->packed ? 2 : 1;
     if (z_warps) *z_warps = b->one_launch ? kMultiWarps : b->bl.z_warps;
     if (coop_min_len) *coop_min_len = static_cast<int32_t>(b->coop_len > 0 ? b->coop_len : -1);
     if (tuned) *tuned = b->tuned ? 1 : 0;

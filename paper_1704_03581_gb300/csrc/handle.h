@@ -55,6 +55,7 @@ struct pulda_handle {
     // Dirichlet Phi (Algorithm 1), allocated in that mode only
     float *gam = nullptr, *invSf = nullptr; double *Sd = nullptr, *invS = nullptr, *dpart = nullptr;
     uint16_t *topic = nullptr; uint32_t *c = nullptr, *q = nullptr, *athr = nullptr; uint16_t *atopic = nullptr;
+    uint2 *apack = nullptr;     // packed alias slots (alias_layout 2), else null
     unsigned long long *A = nullptr, *vose_p = nullptr; uint16_t *vose_stack = nullptr; uint32_t *bits = nullptr;
     int *work = nullptr;
     unsigned long long *stats = nullptr;

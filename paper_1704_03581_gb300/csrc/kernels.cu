@@ -561,6 +561,7 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
         a.vose_p[out + j] = am * static_cast<u64>(n);   // scaled so each slot holds A units
         a.athr[out + j] = 0xFFFFFFFFu;
         a.atopic[out + j] = static_cast<uint16_t>(k);
+        if (a.apack) a.apack[out + j] = make_uint2(0xFFFFFFFFu, static_cast<uint32_t>(k) * 0x10001u);
         asum += am;
     }
     asum = warp_sum64(asum);
@@ -625,6 +626,9 @@ __device__ void phi_tables_word_warp(const PhiArgs &a, int v) {
         if (r > q0) { q1 -= 1; r += dn; }
         if (r >= dn) q1 += 1;
         a.athr[out + j] = static_cast<uint32_t>(q1);
+        if (a.apack)
+            a.apack[out + j] = make_uint2(static_cast<uint32_t>(q1),
+                                          a.topic[out + j] | (static_cast<uint32_t>(a.atopic[out + j]) << 16));
     }
 }
 

@@ -115,6 +115,10 @@ struct PhiArgs {
     int64_t *col_ptr;           // [V+1]
     // final per-word tables, at col_ptr
     uint16_t *topic; uint32_t *c; uint32_t *q; uint32_t *athr; uint16_t *atopic;
+    // the alias slots packed as {threshold, column topic | alias topic << 16}
+    // (written beside athr / atopic when set; the z-step then reads one 8-byte
+    // slot per alias draw instead of a threshold and a topic)
+    uint2 *apack;
     unsigned long long *A;      // [V]
     unsigned long long *vose_p; // [cap] scratch
     uint16_t *vose_stack;       // [cap] scratch
@@ -163,6 +167,7 @@ struct ZArgs {
     const unsigned long long *A;
     const uint32_t *athr;
     const uint16_t *atopic;
+    const uint2 *apack;         // packed alias slots (PhiArgs::apack) or null: read athr / topic / atopic
     const uint32_t *bits;       // [V * KWp] nonzero-topic bits of each word's column; null when K > kMaxKBitmap
     const uint32_t *qdense;     // dense q rows of the most frequent words, or null
     const int32_t *dense_slot;  // [V] row in qdense or -1

@@ -107,7 +107,7 @@ __device__ __forceinline__ int zg_stage(const ZArgs &a, uint32_t sweep, int64_t 
     int ta = 0;
     if (nw > 0) {
         const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
-        ta = guard_index(x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl], a.K, a.stats);
+        ta = alias_outcome(a, cb + sl, x.w);
     }
     int ds = a.dense_slot[wv];
     if (ds < 0) {                 // the host sends only corpora whose every word has a row

@@ -146,6 +146,17 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Stages what depends only on token i of run r (see z_doc_warp_t for the
 // record layout) and returns its current topic.
+// The alias draw of the a part (Walker): slot e of the word's column keeps its
+// own topic when the uniform u is below the slot's threshold, else takes the
+// slot's alias topic.  Read from the packed slots when the tables carry them.
+__device__ __forceinline__ int alias_outcome(const ZArgs &a, int64_t e, uint32_t u) {
+    if (a.apack) {
+        const uint2 s = a.apack[e];
+        return guard_index(static_cast<int>(u < s.x ? s.y & 0xFFFFu : s.y >> 16), a.K, a.stats);
+    }
+    return guard_index(u < a.athr[e] ? a.topic[e] : a.atopic[e], a.K, a.stats);
+}
+
 __device__ __forceinline__ int stage_token(const ZArgs &a, const DocRun &r, int i, uint4 *rec2, uint32_t *drow) {
     const int wv = r.w[i];
     const int zo = guard_index(r.z[i], a.K, a.stats);
@@ -157,7 +168,7 @@ __device__ __forceinline__ int stage_token(const ZArgs &a, const DocRun &r, int 
     int ta = 0;
     if (nw > 0) {
         const uint32_t sl = __umulhi(x.z, static_cast<uint32_t>(nw));
-        ta = guard_index(x.w < a.athr[cb + sl] ? a.topic[cb + sl] : a.atopic[cb + sl], a.K, a.stats);
+        ta = alias_outcome(a, cb + sl, x.w);
     }
     rec2[0] = make_uint4(static_cast<uint32_t>(cb),
                          static_cast<uint32_t>(static_cast<u64>(cb) >> 32) | (static_cast<uint32_t>(ta) << 16),

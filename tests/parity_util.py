@@ -58,12 +58,14 @@ def first_mismatch(z_gpu: np.ndarray, z_or: np.ndarray, doc_off: np.ndarray) -> 
 
 def lockstep(w, doc_off, K: int, V: int, alpha, beta: float, seed: int, sweeps: int, path: int = 0,
              check_tables: bool = True, check_counts_every: int = 0, docs_per_warp: int = 0, phi_mode: int = 0,
-             slice_len: int = 0, coop_min_len: int = 0, count_path: int = 0):
+             slice_len: int = 0, coop_min_len: int = 0, count_path: int = 0, alias_layout: int = 0):
     """Run both sides for `sweeps` sweeps, comparing after each half-sweep.
     phi_mode 1 runs both in Algorithm 1's Dirichlet mode; slice_len > 0 both in stale-count slices;
-    coop_min_len sets which documents the GPU resamples with a whole CTA (the oracle has one way)."""
+    coop_min_len sets which documents the GPU resamples with a whole CTA (the oracle has one way);
+    alias_layout 2 has the GPU's z-step read packed alias slots (the oracle has one layout)."""
     s = P.Sampler(w, doc_off, K, V, alpha, beta, seed, zstep_path=path, docs_per_warp=docs_per_warp,
-                  phi_mode=phi_mode, slice_len=slice_len, coop_min_len=coop_min_len, count_path=count_path)
+                  phi_mode=phi_mode, slice_len=slice_len, coop_min_len=coop_min_len, count_path=count_path,
+                  alias_layout=alias_layout)
     ch = O.Chain(w, doc_off, K, V, alpha, beta, seed, dirichlet=phi_mode == 1, slice_len=slice_len)
     try:
         zg = s.z()

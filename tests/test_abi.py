@@ -51,7 +51,8 @@ def test_init_rejects_bad_arguments_without_a_gpu():
                          (dict(warps_per_block=-1), "warps_per_block"), (dict(docs_per_warp=2), "docs_per_warp"),
                          (dict(phi_mode=2), "phi_mode"), (dict(slice_len=-1), "slice_len"),
                          (dict(slice_len=50, docs_per_warp=4), "slice_len"), (dict(coop_min_len=-2), "coop_min_len"),
-                         (dict(count_path=2), "count_path")]:
+                         (dict(count_path=2), "count_path"), (dict(alias_layout=3), "alias_layout"),
+                         (dict(alias_layout=-1), "alias_layout")]:
         try:
             P.pulda_init(w, off, 4, 3, 0.1, 0.01, 0, **kwargs)
         except P.PuldaError as e:
@@ -79,7 +80,8 @@ def test_batch_rejects_bad_options_without_a_gpu():
     arr[0] = P.ChainDesc(P._ptr(w), P._ptr(off), 1, 3, 2, P._ptr(a), 0.01, 0)
     for field, value, frag in [("phi_mode", 1, b"phi_mode"), ("warps_per_block", 9, b"warps_per_block"),
                                ("docs_per_warp", 4, b"docs_per_warp"), ("slice_len", 64, b"slice_len"),
-                               ("coop_min_len", -2, b"coop_min_len"), ("count_path", 1, b"count_path")]:
+                               ("coop_min_len", -2, b"coop_min_len"), ("count_path", 1, b"count_path"),
+                               ("alias_layout", 3, b"alias_layout")]:
         opt = P.Options()
         setattr(opt, field, value)
         b = ctypes.c_void_p()

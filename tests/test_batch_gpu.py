@@ -47,8 +47,9 @@ def test_batch_equals_single_chains(warps, coop, form):
     chains = make_chains()
     b = P.Batch(chains, warps_per_block=warps, coop_min_len=coop, batch_form=form)
     b.sweep(4)
-    b.sweep(8)            # tuning sweeps (up to 8), then graph replays across two calls
-    w, coop_len, tuned, one = b.tuning()
+    b.sweep(10)           # tuning sweeps (up to 12), then graph replays across two calls
+    w, coop_len, tuned, one, layout = b.tuning()
+    assert layout in (1, 2)
     assert tuned and w in (2, 4, 8)
     assert coop_len == (coop if coop != 0 else coop_len) and (coop_len == -1 or coop_len >= 1)
     if form == 2:
@@ -57,7 +58,7 @@ def test_batch_equals_single_chains(warps, coop, form):
         assert not one
     for i, c in enumerate(chains):
         s = P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"])
-        s.sweep(12)
+        s.sweep(14)
         assert np.array_equal(b.z(i), s.z()), f"chain {i} differs from its single-chain run"
         sb, ss = b.stats(i), s.stats()
         for k in ("tokens", "a_branch", "sum_min", "zero_mass", "dead_rows", "nnz_phi", "sweep",
@@ -80,6 +81,27 @@ def test_batch_lane_widths(n, form):
     for i, c in enumerate(chains):
         s = P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"], coop_min_len=-1)
         s.sweep(5)
+        assert np.array_equal(b.z(i), s.z()), f"chain {i} differs from its single-chain run"
+        s.close()
+    b.close()
+
+
+@pytest.mark.parametrize("layout,form", [(1, 2), (2, 2), (2, 1), (0, 2)])
+def test_batch_alias_layouts(layout, form):
+    """The alias tables as threshold and topic arrays (1), as packed 8-byte
+    slots (2), or timed against each other on two sweeps each (0), in the
+    one-launch and the six-launch form: every chain equals its single-handle
+    run (arrays) and the batch reports the layout it uses."""
+    import paper_1704_03581_gb300 as P
+    chains = make_chains()
+    b = P.Batch(chains, coop_min_len=-1, batch_form=form, alias_layout=layout)
+    b.sweep(7)
+    w, coop_len, tuned, one, used = b.tuning()
+    assert tuned and one == (form == 2)
+    assert used == layout if layout else used in (1, 2)
+    for i, c in enumerate(chains):
+        s = P.Sampler(c["w"], c["doc_off"], c["K"], c["V"], c["alpha"], c["beta"], c["seed"], coop_min_len=-1)
+        s.sweep(7)
         assert np.array_equal(b.z(i), s.z()), f"chain {i} differs from its single-chain run"
         s.close()
     b.close()

@@ -286,6 +286,29 @@ def test_sort_count_path_lockstep(K, phi_mode):
     s.close()
 
 
+@pytest.mark.parametrize("K,dpw,phi_mode,coop", [(20, 1, 0, 0), (1000, 1, 0, 150), (3000, 1, 0, 0), (200, 4, 0, 0),
+                                                 (33, 1, 1, 0)])
+def test_packed_alias_slots_lockstep(K, dpw, phi_mode, coop):
+    """alias_layout 2: the z-step takes each alias draw from one packed
+    8-byte slot {threshold, topic | alias topic << 16} that the table pass
+    writes beside the threshold and topic arrays.  Every table, draw, count
+    and topic as the oracle's: the one-warp kernel at 8 and 32 topics per lane
+    and past the bitmap limit, the cooperative kernel on documents of at least
+    150 tokens, four documents per warp, the Dirichlet Phi; then a fold-in."""
+    rng = np.random.default_rng(90 + K)
+    lengths = rng.integers(0, 300, size=150)
+    lengths[[2, 4]] = [0, 1]
+    w, off = corpus_from_lengths(rng, lengths, 900)
+    s, ch = lockstep(w, off, K, 900, 0.1, 0.01, seed=K, sweeps=3, check_counts_every=3, phi_mode=phi_mode,
+                     docs_per_warp=dpw, coop_min_len=coop, alias_layout=2)
+    new_off = off[:21] - off[0]
+    new_w = w[:new_off[-1]]
+    zg = s.infer(new_w, new_off, 5, seed=5)
+    zo = O.infer(ch.tables, new_w, new_off, 5, 5)
+    assert not first_mismatch(zg, zo, new_off)
+    s.close()
+
+
 def test_sort_count_path_small_corpus():
     """The small corpus (1.9M tokens, K=100): words with up to ~10^5 tokens,
     the sort's multi-block scans over every tile."""
