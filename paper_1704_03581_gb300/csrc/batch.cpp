@@ -1,8 +1,9 @@
 // Many independent chains (corpora of uneven D, N, K, V) advanced together:
-// every kernel of a sweep runs once over all chains' work items, and the six
-// launches of a sweep are captured once into a CUDA graph and replayed.  The
-// z-step CTA size is picked by timing the candidates on the first sweeps (a
-// launch shape never changes a result, so tuning costs no extra sweeps); the
+// every kernel of a sweep runs once over all chains' work items, and a sweep
+// (six launches, or one persistent launch) is captured once into a CUDA graph
+// and replayed.  The z-step CTA size, the launch form and then the alias
+// tables' layout are picked by timing the candidates on the first sweeps
+// (none of them changes a result, so tuning costs no extra sweeps); the
 // longest documents go to the cooperative z-step by the single-chain rule.
 #include <algorithm>
 #include <cstdio>
