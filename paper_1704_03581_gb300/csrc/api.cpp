@@ -504,7 +504,6 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     if (wpb <= 0) wpb = kZWarps;
     while (wpb > 1 && z_step_smem(K, wpb) > 160 * 1024) wpb >>= 1;
     h->z_warps = wpb;
-    h->z_grid = sms * z_step_blocks_per_sm(K, wpb);
     CUI(cudaGetLastError());
     // Four documents per warp share each token's fixed work (record, count
     // updates, scan, draw) over four tokens, but each lane then walks four
@@ -521,6 +520,12 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     h->n_coop = count_coop(h, doc_offsets, dord, N);
     h->narrow_z = narrow_from(doc_offsets, dord, h->n_coop);
     h->narrow_all = narrow_from(doc_offsets, dord, 0);
+    // as many one-warp CTAs as fit with the corpus pass's count width (16-bit
+    // counts halve the shared memory, which limits residency at large K); a
+    // launch with 32-bit counts (a fold-in of long documents) queues the
+    // CTAs that do not fit, each taking documents from the same counter
+    h->z_grid = sms * z_step_blocks_per_sm(K, wpb, h->narrow_z);
+    CUI(cudaGetLastError());
     h->coop_grid = sms * z_coop_blocks_per_sm(K);
     CUI(cudaGetLastError());
     CUI(cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
