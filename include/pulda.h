@@ -54,7 +54,7 @@ typedef struct {
     void *stream;           /* cudaStream_t to run on; NULL = a stream the handle creates */
     int32_t zstep_path;     /* 0 = auto (iterate the smaller of the document's and the
                                word's nonzero topics), 1 = always iterate the word's Phi
-                               column, 2 = iterate the document's topics whenever K <= 1024 */
+                               column, 2 = iterate the document's topics whenever K <= 2048 */
     int32_t warps_per_block;/* warp-per-document z-step: warps per CTA, 1..4; 0 = 4, halved
                                while the CTA's shared memory would pass 160 KB */
     int32_t docs_per_warp;  /* z-step documents per warp: 0 = auto (one: measured faster at

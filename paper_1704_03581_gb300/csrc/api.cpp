@@ -347,7 +347,7 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
         fail(h, PULDA_ERR_INVALID, "coop_min_len must be -1 (never), 0 (auto) or a length");
         return reject(PULDA_ERR_INVALID);
     }
-    if (h->opt.docs_per_warp == 4 && K > kMaxKBitmap) {
+    if (h->opt.docs_per_warp == 4 && K > kMaxKGrouped) {
         fail(h, PULDA_ERR_INVALID, "docs_per_warp = 4 needs K <= 1024");
         return reject(PULDA_ERR_INVALID);
     }
@@ -514,7 +514,7 @@ pulda_status pulda_init(pulda_handle **out, const int32_t *word_ids, const int64
     // warp, K = 100 10.4 vs 13.7, K = 200 10.3 vs 13.0), so auto takes one
     // per warp and four per warp is an explicit choice.  That needs every
     // word's dense q row; not with slices or the column-only path.
-    const bool groups_ok = K <= kMaxKBitmap && h->n_dense == V && h->opt.slice_len == 0 && h->opt.zstep_path != 1;
+    const bool groups_ok = K <= kMaxKGrouped && h->n_dense == V && h->opt.slice_len == 0 && h->opt.zstep_path != 1;
     h->z_groups = groups_ok && h->opt.docs_per_warp == 4;
     h->n_long = count_long(doc_offsets, dord);
     h->n_coop = count_coop(h, doc_offsets, dord, N);

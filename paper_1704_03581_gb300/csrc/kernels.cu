@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <type_traits>
 
 #include "device_rng.cuh"
 #include "pulda_internal.h"
@@ -676,18 +677,45 @@ constexpr int kGather8 = PULDA_ZGATHER8;
 template <int TPL>
 __device__ __forceinline__ int mit(int k) { return k + k / TPL; }
 
+// A lane's bits of its TPL topics: 32 bits, or 64 for 64 topics per lane.
+template <int TPL>
+using lane_word_t = typename std::conditional<TPL == 64, uint64_t, uint32_t>::type;
+
 // This lane's TPL bits of a bitmap row starting at word `row`.
 template <int TPL>
-__device__ __forceinline__ uint32_t lane_bits(const uint32_t *bits, int64_t row, int lane) {
-    if (TPL == 32) return bits[row + lane];
-    const uint32_t w = bits[row + (lane * TPL >> 5)];
-    return (w >> ((lane * TPL) & 31)) & ((1u << (TPL & 31)) - 1u);
+__device__ __forceinline__ lane_word_t<TPL> lane_bits(const uint32_t *bits, int64_t row, int lane) {
+    if constexpr (TPL == 64) {
+        const uint32_t *p = bits + row + 2 * lane;
+        return static_cast<uint64_t>(p[0]) | (static_cast<uint64_t>(p[1]) << 32);
+    } else if constexpr (TPL == 32) {
+        return bits[row + lane];
+    } else {
+        const uint32_t w = bits[row + (lane * TPL >> 5)];
+        return (w >> ((lane * TPL) & 31)) & ((1u << (TPL & 31)) - 1u);
+    }
 }
 
+// 1 << b in a lane word, 0 for b = -1.
+template <int TPL>
+__device__ __forceinline__ lane_word_t<TPL> lane_bit(int b) {
+    if constexpr (TPL == 64) return bit_or_zero64(b);
+    else return bit_or_zero(b);
+}
+
+// 1 << b in a lane word for b in [0, TPL).
+template <int TPL>
+__device__ __forceinline__ lane_word_t<TPL> lane_bit_at(int b) {
+    return static_cast<lane_word_t<TPL>>(1) << b;
+}
+
+__device__ __forceinline__ int popc_word(uint32_t x) { return __popc(x); }
+__device__ __forceinline__ int popc_word(uint64_t x) { return __popcll(x); }
+
 // One warp per document (dynamically scheduled, longest first).  m_d lives
-// in shared memory as a dense count array; for K <= 1024 each lane also holds
-// the bits of m_d's nonzero topics among the TPL it owns (TPL = 32, or 16 /
-// 8 for K <= 512 / 256, so that small K still spreads over the warp), and
+// in shared memory as a dense count array; for K <= 2048 each lane also holds
+// the bits of m_d's nonzero topics among the TPL it owns (TPL = 64 above 1024
+// topics, 32, or 16 / 8 for K <= 512 / 256, so that small K still spreads
+// over the warp), and
 // the document side reads q of topic TPL lane + b from the word's dense q
 // row.  Tokens are visited in position order: remove token i (m^{-i}),
 // compute sigma_b = sum_k q_{k,v} m_k over the smaller of {k : m_k > 0} and
@@ -711,15 +739,16 @@ __device__ __forceinline__ uint32_t lane_bits(const uint32_t *bits, int64_t row,
 // own topics.
 template <int TPL, typename CT>
 __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, const uint32_t *m0) {
-    static_assert(TPL == 8 || TPL == 16 || TPL == 32, "8, 16 or 32 topics per lane");
+    static_assert(TPL == 8 || TPL == 16 || TPL == 32 || TPL == 64, "8, 16, 32 or 64 topics per lane");
+    using BT = lane_word_t<TPL>;
     static_assert(sizeof(CT) == 2 || sizeof(CT) == 4, "16- or 32-bit counts");
     constexpr int kLead = 4 / static_cast<int>(sizeof(CT));    // counts before mt[0]: the leading zero's word
-    constexpr int G = TPL == 32 ? kGather : TPL == 16 ? kGather16 : kGather8;
+    constexpr int G = TPL >= 32 ? kGather : TPL == 16 ? kGather16 : kGather8;
     const int lane = threadIdx.x & 31;
     const int K = a.K;
     const bool use_bm = a.bits != nullptr && a.path != 1;
     if (r.len == 0 || r.budget <= 0) return;
-    // Lane l owns topics [TPL l, TPL l + TPL) (TPL = 32, 16 or 8 by K, so
+    // Lane l owns topics [TPL l, TPL l + TPL) (TPL = 64, 32, 16 or 8 by K, so
     // that small K spreads over more lanes).  Topic k's count is
     // mt[mit<TPL>(k)]: lane l's topics sit at mt[(TPL + 1) l + b], and the word
     // before each lane's slots is a zero (mt[-1] for lane 0 and for the lanes
@@ -749,7 +778,7 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
     if (lane == 0) mt[-1] = 0;
     if (lane + 1 < nl) mt[(TPL + 1) * lane + TPL] = 0;
     __syncwarp();
-    uint32_t mbits = 0;
+    BT mbits = 0;
     int kd = 0;
     if (use_bm && TPL == 32) {
         for (int g = 0; g < a.KW; ++g) {
@@ -762,10 +791,10 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
         if (own) {
             for (int b = 0; b < TPL; ++b) {
                 const int k = TPL * lane + b;
-                if (k < K && mt[mit<TPL>(k)] > 0) mbits |= 1u << b;
+                if (k < K && mt[mit<TPL>(k)] > 0) mbits |= lane_bit_at<TPL>(b);
             }
         }
-        kd = static_cast<int>(__reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(__popc(mbits))));
+        kd = static_cast<int>(__reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(popc_word(mbits))));
     } else {
         int cnt = 0;
         for (int k = lane; k < K; k += 32) cnt += mt[mit<TPL>(k)] > 0;
@@ -805,7 +834,7 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
         __syncwarp();
         // the word's bitmap row (TPL topics per lane)
         const uint32_t *bits = a.bits;
-        uint32_t bm_next = 0u;
+        BT bm_next = 0u;
         if (use_bm && own) bm_next = lane_bits<TPL>(bits, static_cast<int64_t>(rec[1].z) * a.KWp, lane);
         // this block's counters, in 32 bits (at most 32 tokens of K <= 16384),
         // added to the warp's 64-bit counters once per block
@@ -822,7 +851,7 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
             const u64 At = (static_cast<u64>(t0.w) << 32) | t0.z;
             const u64 U = (static_cast<u64>(t1.x) << 32) | t1.y;
             const int ka = static_cast<int>(t0.y >> 16);
-            const uint32_t bm = bm_next;
+            const BT bm = bm_next;
             if (use_bm && tt + 1 < cnt && own)   // the next token's bitmap word, fetched while this one is drawn
                 bm_next = lane_bits<TPL>(bits, static_cast<int64_t>(rec[2 * tt + 3].z) * a.KWp, lane);
             // remove token i: m^{-i}
@@ -833,7 +862,7 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
                 const uint32_t old = me ? mt[mit<TPL>(kold)] : 0u;
                 if (me) mt[mit<TPL>(kold)] = old - 1;
                 const bool died = me && old == 1;
-                if (died) mbits &= ~(1u << (kold % TPL));
+                if (died) mbits &= ~lane_bit_at<TPL>(kold % TPL);
                 kd -= __any_sync(0xFFFFFFFFu, died) ? 1 : 0;
             } else {
                 const uint32_t old = mt[mit<TPL>(kold)];
@@ -846,7 +875,7 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
             c_cnt += kd < n_w ? 1u : 0u;
             // |J| from the bitmaps on either side (the column side's topics with
             // m > 0 are the same set); without bitmaps the column loop counts it
-            if (use_bm) c_cnt += static_cast<uint32_t>(__popc(bm & mbits)) << 18;
+            if (use_bm) c_cnt += static_cast<uint32_t>(popc_word(bm & mbits)) << 18;
             // The document side needs the word's dense q row (q of topic TPL lane + b
             // at qd[b]); a word without one is iterated on the column side.
             const uint32_t drow = drow_of[tt];
@@ -858,26 +887,26 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
             u64 acc = 0;
             uint32_t qv[G];
             int bp[G];
-            uint32_t rest = 0;         // docside: bits below the first G
+            BT rest = 0;               // docside: bits below the first G
             int seg = 0, seg0 = 0;     // column side: this lane's contiguous segment
             if (docside) {
                 // The lane's bits from the highest down; a slot past the last
                 // bit gets b = -1 and q = 0 (no load), and its count read hits
                 // the zero before the lane's slots.
-                uint32_t rem = bm & mbits;
+                BT rem = bm & mbits;
 #pragma unroll
                 for (int t = 0; t < G; ++t) {
                     const int b = msb_or_neg1(rem);
-                    rem ^= bit_or_zero(b);
+                    rem ^= lane_bit<TPL>(b);
                     bp[t] = b;
                     qv[t] = b >= 0 ? qd[b] : 0u;
                 }
 #pragma unroll
                 for (int t = 0; t < G; ++t) acc += static_cast<u64>(qv[t]) * ml[bp[t]];
                 rest = rem;
-                for (uint32_t bb = rest; bb;) {
+                for (BT bb = rest; bb;) {
                     const int b = msb_or_neg1(bb);
-                    bb ^= bit_or_zero(b);
+                    bb ^= lane_bit<TPL>(b);
                     acc += static_cast<u64>(qd[b]) * ml[b];
                 }
             } else {
@@ -924,9 +953,9 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
                                     run -= static_cast<u64>(qv[t]) * ml[bp[t]];
                                     if (rb >= run) { f = TPL * lane + bp[t]; break; }
                                 }
-                                for (uint32_t bb = rest; f < 0 && bb;) {
+                                for (BT bb = rest; f < 0 && bb;) {
                                     const int b = msb_or_neg1(bb);
-                                    bb ^= bit_or_zero(b);
+                                    bb ^= lane_bit<TPL>(b);
                                     run -= static_cast<u64>(qd[b]) * ml[b];
                                     if (rb >= run) f = TPL * lane + b;
                                 }
@@ -956,7 +985,7 @@ __device__ void z_doc_warp_t(const ZArgs &a, uint32_t *m, DocRun &r, u64 *wcnt, 
                 const uint32_t old2 = me ? mt[mit<TPL>(knew)] : 0u;
                 if (me) mt[mit<TPL>(knew)] = old2 + 1;
                 const bool born = me && old2 == 0;
-                if (born) mbits |= 1u << (knew % TPL);
+                if (born) mbits |= lane_bit_at<TPL>(knew % TPL);
                 kd += __any_sync(0xFFFFFFFFu, born) ? 1 : 0;
             } else {
                 const uint32_t old2 = mt[mit<TPL>(knew)];
@@ -1044,7 +1073,8 @@ __global__ void k_slice_counts(const int64_t *doc_off, const int32_t *sliced_doc
 
 // Many chains: the work list holds (chain, document) pairs, longest first
 // across all chains; shared memory per warp is sized for the largest K.
-// TPL = z_lane_topics(kmax): every chain of the batch has K <= kmax <= 32 TPL;
+// TPL = z_lane_topics(kmax): every chain of the batch that carries bitmaps has
+// K <= kmax <= 32 TPL (the others iterate their columns);
 // CT 16-bit when every document of every chain is shorter than 2^16 tokens.
 template <int TPL, typename CT>
 __global__ void __launch_bounds__(32 * kMultiWarps, PULDA_MULTI_MINB) k_z_step_multi(const ZArgs *chains, const int2 *items,
@@ -1264,7 +1294,8 @@ static ZStepKernel z_step_kernel(int K, bool narrow) {
     switch (z_lane_topics(K)) {
         case 8: return narrow ? k_z_step<8, uint16_t> : k_z_step<8, uint32_t>;
         case 16: return narrow ? k_z_step<16, uint16_t> : k_z_step<16, uint32_t>;
-        default: return narrow ? k_z_step<32, uint16_t> : k_z_step<32, uint32_t>;
+        case 32: return narrow ? k_z_step<32, uint16_t> : k_z_step<32, uint32_t>;
+        default: return narrow ? k_z_step<64, uint16_t> : k_z_step<64, uint32_t>;
     }
 }
 
@@ -1287,8 +1318,9 @@ void launch_slice_counts(const int64_t *doc_off, const int32_t *sliced_docs, int
 void launch_z_step(const ZArgs &a, int warps_per_block, int grid, cudaStream_t st) {
     ZStepKernel kern = z_step_kernel(a.K, a.narrow != 0);
     // each instantiation opts in to large dynamic shared memory once
-    static std::atomic<bool> opted[3][2];
-    std::atomic<bool> &o = opted[z_lane_topics(a.K) == 8 ? 0 : z_lane_topics(a.K) == 16 ? 1 : 2][a.narrow != 0];
+    static std::atomic<bool> opted[4][2];
+    const int tpl = z_lane_topics(a.K);
+    std::atomic<bool> &o = opted[tpl == 8 ? 0 : tpl == 16 ? 1 : tpl == 32 ? 2 : 3][a.narrow != 0];
     if (!o.load(std::memory_order_acquire)) {
         allow_dynamic_smem(kern);
         o.store(true, std::memory_order_release);
@@ -1301,7 +1333,8 @@ static ZMultiKernel z_multi_kernel(int kmax, bool narrow) {
     switch (z_lane_topics(kmax)) {
         case 8: return narrow ? k_z_step_multi<8, uint16_t> : k_z_step_multi<8, uint32_t>;
         case 16: return narrow ? k_z_step_multi<16, uint16_t> : k_z_step_multi<16, uint32_t>;
-        default: return narrow ? k_z_step_multi<32, uint16_t> : k_z_step_multi<32, uint32_t>;
+        case 32: return narrow ? k_z_step_multi<32, uint16_t> : k_z_step_multi<32, uint32_t>;
+        default: return narrow ? k_z_step_multi<64, uint16_t> : k_z_step_multi<64, uint32_t>;
     }
 }
 
@@ -1488,7 +1521,8 @@ static PersistKernel persistent_kernel(int kmax, bool narrow) {
     switch (z_lane_topics(kmax)) {
         case 8: return narrow ? k_batch_sweep_persistent<8, uint16_t> : k_batch_sweep_persistent<8, uint32_t>;
         case 16: return narrow ? k_batch_sweep_persistent<16, uint16_t> : k_batch_sweep_persistent<16, uint32_t>;
-        default: return narrow ? k_batch_sweep_persistent<32, uint16_t> : k_batch_sweep_persistent<32, uint32_t>;
+        case 32: return narrow ? k_batch_sweep_persistent<32, uint16_t> : k_batch_sweep_persistent<32, uint32_t>;
+        default: return narrow ? k_batch_sweep_persistent<64, uint16_t> : k_batch_sweep_persistent<64, uint32_t>;
     }
 }
 
@@ -1535,7 +1569,8 @@ static ServeKernel serve_kernel(int K, bool narrow) {
     switch (z_lane_topics(K)) {
         case 8: return narrow ? k_serve_step<8, uint16_t> : k_serve_step<8, uint32_t>;
         case 16: return narrow ? k_serve_step<16, uint16_t> : k_serve_step<16, uint32_t>;
-        default: return narrow ? k_serve_step<32, uint16_t> : k_serve_step<32, uint32_t>;
+        case 32: return narrow ? k_serve_step<32, uint16_t> : k_serve_step<32, uint32_t>;
+        default: return narrow ? k_serve_step<64, uint16_t> : k_serve_step<64, uint32_t>;
     }
 }
 

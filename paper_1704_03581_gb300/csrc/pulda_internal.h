@@ -21,15 +21,20 @@ constexpr int kFracBits = 16;
 constexpr uint32_t kMaxRedraw = 1u << 20;
 // Largest K the kernels' shared-memory layouts accept.
 constexpr int kMaxK = 16384;
-// The bitmap intersection path of the z-step holds one 32-topic word per lane.
-constexpr int kMaxKBitmap = 1024;
+// The bitmap intersection path of the z-step: the one-warp kernel's lane
+// holds up to two 32-topic words (64 topics), the cooperative kernel's slot
+// part of one.
+constexpr int kMaxKBitmap = 2048;
+// Four documents per warp: each of a document's 8 lanes holds up to four
+// words.
+constexpr int kMaxKGrouped = 1024;
 // Words of a word's bitmap row: ceil(K / 32) rounded up to 8 times a power
 // of two, so each of the grouped z-step's 8 lanes per document reads 1, 2 or
 // 4 consecutive words with one aligned load (the words past ceil(K / 32) are
-// zero).
+// zero); 64 above 1024 topics.
 __host__ __device__ inline int bitmap_row_words(int K) {
     const int per_lane = (((K + 31) / 32) + 7) / 8;
-    return 8 * (per_lane <= 1 ? 1 : per_lane <= 2 ? 2 : 4);
+    return 8 * (per_lane <= 1 ? 1 : per_lane <= 2 ? 2 : per_lane <= 4 ? 4 : 8);
 }
 // Warps per CTA of the warp-per-document z-step: the default and the largest
 // accepted (the kernel's launch bounds are sized for it).
@@ -222,7 +227,7 @@ void launch_n_dense(const PhiArgs &a, int32_t *n_kv, cudaStream_t st);
 void launch_phi_values(const PhiArgs &a, float *phi, cudaStream_t st);
 int z_step_blocks_per_sm(int K, int warps_per_block, bool narrow = false);
 // Grouped z-step (zgroup.cu): 4 documents per warp, 8 lanes each, K <=
-// kMaxKBitmap, documents of at most kMaxGroupDocLen tokens, every word with a
+// kMaxKGrouped, documents of at most kMaxGroupDocLen tokens, every word with a
 // dense q row; the warps of a CTA are z_groups_warps().
 constexpr int kMaxGroupDocLen = 65535;
 // A one-warp z-step launch whose documents have at most this many tokens each

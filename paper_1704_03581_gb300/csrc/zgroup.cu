@@ -22,7 +22,7 @@
 // r = floor(u (A + 2^16 B)) takes the alias table when r < A, else the lane
 // whose prefix passes (r - A) / 2^16 walks its bits to the topic.
 //
-// Requires K <= kMaxKBitmap, a dense q row for every word, and documents of at
+// Requires K <= kMaxKGrouped, a dense q row for every word, and documents of at
 // most kMaxGroupDocLen tokens (uint16 counts); the host routes anything else to
 // the one-warp and cooperative kernels.
 #include <algorithm>

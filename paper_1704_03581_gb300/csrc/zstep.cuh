@@ -45,6 +45,18 @@ __device__ __forceinline__ uint32_t bit_or_zero(int b) {
     return r;
 }
 
+// The same for a lane's 64 topics (two bitmap words).
+__device__ __forceinline__ int msb_or_neg1(uint64_t x) {
+    int b;
+    asm("bfind.u64 %0, %1;" : "=r"(b) : "l"(x));
+    return b;
+}
+__device__ __forceinline__ uint64_t bit_or_zero64(int b) {
+    uint64_t r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(1ull), "r"(b));
+    return r;
+}
+
 __device__ __forceinline__ uint32_t sweep_of(const ZArgs &a) { return a.sweep_ptr ? *a.sweep_ptr : a.sweep; }
 
 // The document side (for a word with a dense q row) is iterated when
@@ -64,8 +76,10 @@ constexpr int kDocRatio = PULDA_ZDOCRATIO;
 // per lane, see z_lane_topics).
 __host__ __device__ __forceinline__ int mi(int k) { return k + (k >> 5); }
 // Topics per lane of the one-warp z-step: 8 for K <= 256, 16 for K <= 512,
-// else 32.
-__host__ __device__ __forceinline__ int z_lane_topics(int K) { return K <= 256 ? 8 : K <= 512 ? 16 : 32; }
+// 32 for K <= 1024, else 64 (two bitmap words).
+__host__ __device__ __forceinline__ int z_lane_topics(int K) {
+    return K <= 256 ? 8 : K <= 512 ? 16 : K <= 1024 ? 32 : 64;
+}
 // Shared memory of one z-step warp, in 32-bit words: m_d, then the staging
 // records of the 32 tokens in flight.  The count words: K counts, the gap
 // words after the lanes' slots (K / 32 + 32 of them covers (K - 1) / TPL for

@@ -45,11 +45,12 @@ def test_small_corpus_lockstep(dpw):
 
 
 @pytest.mark.parametrize("dpw", [4, 1], ids=["4docs-per-warp", "1doc-per-warp"])
-@pytest.mark.parametrize("K", [1, 31, 33, 200, 256, 257, 500, 513, 1000, 1024, 1025, 3000])
+@pytest.mark.parametrize("K", [1, 31, 33, 200, 256, 257, 500, 513, 1000, 1024, 1025, 1500, 2048, 2049, 3000])
 def test_topic_counts_around_tile_edges(K, dpw):
     """K around the 32-topic words, the 128 topics a lane owns in the grouped
-    kernel, the one-warp kernel's switches from 8 to 16 to 32 topics per lane
-    (256 / 512), and the 1024 limit of the bitmap paths."""
+    kernel (1024 its limit), the one-warp kernel's switches from 8 to 16 to 32
+    to 64 topics per lane (256 / 512 / 1024), and the 2048 limit of the bitmap
+    paths."""
     if dpw == 4 and K > 1024:
         pytest.skip("four documents per warp needs K <= 1024")
     rng = np.random.default_rng(K)

@@ -38,10 +38,10 @@ def requests(c, n, rng):
     return out
 
 
-@pytest.mark.parametrize("K", [300, 1000])
+@pytest.mark.parametrize("K", [300, 1000, 1500])
 def test_server_lane_widths(trained, K):
-    """Models whose K gives the server 16 (K = 300) and 32 (K = 1000) topics
-    per lane: every request equals its run alone."""
+    """Models whose K gives the server 16 (K = 300), 32 (K = 1000) and 64
+    (K = 1500) topics per lane: every request equals its run alone."""
     P, _, _, c = trained
     s = P.Sampler(c.w, c.doc_off, K, c.V, 0.1, 0.01, seed=4).sweep(2)
     rng = np.random.default_rng(K)
