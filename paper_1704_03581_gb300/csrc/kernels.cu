@@ -715,9 +715,8 @@ __device__ __forceinline__ int popc_word(uint64_t x) { return __popcll(x); }
 // in shared memory as a dense count array; for K <= 2048 each lane also holds
 // the bits of m_d's nonzero topics among the TPL it owns (TPL = 64 above 1024
 // topics, 32, or 16 / 8 for K <= 512 / 256, so that small K still spreads
-// over the warp), and
-// the document side reads q of topic TPL lane + b from the word's dense q
-// row.  Tokens are visited in position order: remove token i (m^{-i}),
+// over the warp), and the document side reads q of topic TPL lane + b from
+// the word's dense q row.  Tokens are visited in position order: remove token i (m^{-i}),
 // compute sigma_b = sum_k q_{k,v} m_k over the smaller of {k : m_k > 0} and
 // {k : phi_{k,v} > 0} (complexity theorem), draw r = floor(u (A + 2^16 B)),
 // take the alias draw if r < A, else the first topic where the running sum
